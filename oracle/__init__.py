@@ -1,0 +1,172 @@
+"""CPU oracle for the sPEGG per-generation update -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference legs may import this package.  It wraps ``spegg_oracle.c`` (a plain,
+per-locus C statement of the model) through ctypes and shares no code with the
+CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+STATS_DTYPE = np.dtype([
+    ("gen", "<u4"), ("n", "<u4"), ("s", "<u4"), ("status", "<u4"),
+    ("sum_raw", "<i8"), ("sum_raw2", "<u8"), ("sum_raw_surv", "<i8"),
+    ("min_raw", "<i4"), ("max_raw", "<i4"),
+    ("het", "<u8"), ("allele", "<u8"), ("consumption", "<u8"),
+    ("R", "<f8"), ("f", "<u4"), ("pad", "<u4"),
+])
+OK, EXTINCT = 0, 1
+CERTAIN = 0xFFFFFFFF
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_philox4x32_10.restype = None
+        L.orc_mutation_cdf.argtypes = [ctypes.c_double, ctypes.c_uint32, u32p]
+        L.orc_mutation_cdf.restype = ctypes.c_uint32
+        L.orc_phenotype_packed.argtypes = [ctypes.c_void_p, ctypes.c_uint32, u32p]
+        L.orc_phenotype_packed.restype = ctypes.c_int32
+        L.orc_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                 ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double]
+        L.orc_create.restype = ctypes.c_void_p
+        L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_destroy.restype = None
+        L.orc_set_ecology.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
+        L.orc_set_ecology.restype = ctypes.c_int
+        L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
+        L.orc_step.restype = ctypes.c_int
+        L.orc_read_genotypes.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_read_genotypes.restype = ctypes.c_int
+        L.orc_read_survivors.argtypes = [ctypes.c_void_p, ctypes.c_void_p, u32p]
+        L.orc_read_survivors.restype = ctypes.c_int
+        L.orc_get_state.argtypes = [ctypes.c_void_p, u32p, u32p, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_double), u32p]
+        L.orc_get_state.restype = None
+        L.orc_stats_size.argtypes = []
+        L.orc_stats_size.restype = ctypes.c_uint32
+        L.orc_summarize.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
+        L.orc_summarize.restype = None
+        assert L.orc_stats_size() == STATS_DTYPE.itemsize
+        _lib = L
+    return _lib
+
+
+def _u32(a):
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = _u32(ctr); k = _u32(key); out = np.zeros(4, np.uint32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib().orc_philox4x32_10(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p), out.ctypes.data_as(u32p))
+    return out
+
+
+def mutation_cdf(mu: float, n_copies: int) -> np.ndarray:
+    buf = np.zeros(32, np.uint32)
+    k = lib().orc_mutation_cdf(float(mu), int(n_copies), buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    return buf[:k].copy()
+
+
+def phenotype(effects: np.ndarray, record: np.ndarray) -> int:
+    e = np.ascontiguousarray(effects, dtype=np.int16)
+    r = _u32(record)
+    return int(lib().orc_phenotype_packed(e.ctypes.data, len(e), r.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+
+
+def summarize(stats: np.ndarray, n_loci: int) -> np.ndarray:
+    """FP32 summaries (mean z, var z, survival fraction, heterozygosity,
+    allele-1 frequency) of each statistics record."""
+    stats = np.ascontiguousarray(stats, dtype=STATS_DTYPE)
+    out = np.zeros((len(stats), 5), np.float32)
+    for i in range(len(stats)):
+        lib().orc_summarize(stats[i:i + 1].ctypes.data, n_loci, out[i].ctypes.data)
+    return out
+
+
+class OraclePopulation:
+    """One population advanced generation by generation on the CPU."""
+
+    def __init__(self, n: int, n_loci: int, seed: int, replicate: int, effects, surv_table,
+                 bin_bias: int, bin_shift: int, mu: float, init_genotypes=None,
+                 p0_q32: int = 0x80000000):
+        self.n, self.n_loci = int(n), int(n_loci)
+        self.words = self.n_loci // 32
+        e = np.ascontiguousarray(effects, dtype=np.int16)
+        t = _u32(surv_table)
+        assert t.shape == (4096,) and e.shape == (self.n_loci,)
+        g = None
+        if init_genotypes is not None:
+            g = _u32(init_genotypes).reshape(self.n, 2 * self.words)
+        self._h = lib().orc_create(self.n, self.n_loci, int(seed), int(replicate), e.ctypes.data,
+                                   None if g is None else g.ctypes.data, int(p0_q32),
+                                   t.ctypes.data, int(bin_bias), int(bin_shift), float(mu))
+        if not self._h:
+            raise ValueError("oracle rejected the population description")
+
+    @classmethod
+    def from_workload(cls, w) -> "OraclePopulation":
+        p = cls(w.n, w.n_loci, w.seed, w.replicate, w.effects, w.surv_table, w.bias, w.shift, w.mu,
+                w.init_genotypes, w.p0_q32)
+        if w.has_ecology:
+            p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack)
+        return p
+
+    def set_ecology(self, r, K, R0, R_half, attack):
+        a = _u32(attack)
+        rc = lib().orc_set_ecology(self._h, float(r), float(K), float(R0), float(R_half), a.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle rejected the ecology description")
+
+    def step(self, n_gen: int) -> np.ndarray:
+        out = np.zeros(max(int(n_gen), 1), STATS_DTYPE)
+        done = lib().orc_step(self._h, int(n_gen), out.ctypes.data)
+        if done < 0:
+            raise RuntimeError(f"oracle step failed ({done})")
+        return out[:done]
+
+    def genotypes(self) -> np.ndarray:
+        out = np.zeros((self.n, 2 * self.words), np.uint32)
+        lib().orc_read_genotypes(self._h, out.ctypes.data)
+        return out
+
+    def survivors(self) -> np.ndarray:
+        S = ctypes.c_uint32(0)
+        lib().orc_read_survivors(self._h, None, ctypes.byref(S))
+        out = np.zeros(S.value, np.uint32)
+        if S.value:
+            lib().orc_read_survivors(self._h, out.ctypes.data, ctypes.byref(S))
+        return out
+
+    def state(self) -> dict:
+        g, S, f = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        st, R = ctypes.c_int32(), ctypes.c_double()
+        lib().orc_get_state(self._h, ctypes.byref(g), ctypes.byref(S), ctypes.byref(st), ctypes.byref(R),
+                            ctypes.byref(f))
+        return {"gen": g.value, "S": S.value, "status": st.value, "R": R.value, "f": f.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

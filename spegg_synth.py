@@ -1,0 +1,223 @@
+"""Seeded synthetic inputs for the sPEGG per-generation update.
+
+This module only *describes workloads*: it draws the allelic effects, builds the
+caller-supplied lookup tables (viability thresholds, attack rates), lays out
+special starting genotypes and lists the workload configurations.  It holds none
+of the update's arithmetic (mate sampling, transmission, mutation, phenotype,
+survival decisions, compaction, ecology); both the CUDA library and the CPU
+oracle consume what it returns as plain inputs.
+
+Conventions shared by every consumer (they are the library's input format, not
+its computation):
+
+* ``L`` loci per haplotype, ``W = L // 32`` uint32 words per haplotype; an
+  individual is a record of ``2W`` words: haplotype 0 words then haplotype 1
+  words; locus ``l`` is bit ``l % 32`` of word ``l // 32``.
+* Allelic effects are int16 in Q8 fixed point (value / 256 in trait units).  The
+  integer phenotype ``raw`` of an individual is the sum over loci of
+  ``effect * (allele count)`` and the trait is ``z = raw / 512`` (the offspring's
+  genetic value is the midpoint of its two gametes' allelic values, S2
+  "Genetics", eq. S2-phenval).
+* Phenotype bins: ``bin = clamp((raw + bias) >> shift, 0, 4095)``; tables are
+  uint32[4096] indexed by bin.  A viability entry ``t`` means survival with
+  probability ``t / 2**32``; ``0xFFFFFFFF`` means certain survival.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+N_BINS = 4096
+CERTAIN = 0xFFFFFFFF
+
+
+# --------------------------------------------------------------------------
+# allelic effects and the phenotype-bin map
+# --------------------------------------------------------------------------
+def effects_q8(n_loci: int, sd: float = 0.1, seed: int = 0) -> np.ndarray:
+    """Allelic effects drawn once from N(0, sd) (sd = standard deviation),
+    quantised to Q8 with round-half-even and clamped to int16."""
+    x = np.random.default_rng(seed).normal(0.0, sd, size=n_loci)
+    q = np.rint(x * 256.0)
+    return np.clip(q, -32768, 32767).astype(np.int16)
+
+
+def bin_map(effects: np.ndarray) -> tuple[int, int]:
+    """(bias, shift) such that every reachable raw phenotype maps into [0, 4096).
+
+    raw ranges over [2*sum(min(e,0)), 2*sum(max(e,0))]; bias = -raw_min and
+    shift is the smallest shift with (raw_max - raw_min) >> shift < 4096."""
+    e = effects.astype(np.int64)
+    raw_min = 2 * int(np.minimum(e, 0).sum())
+    raw_max = 2 * int(np.maximum(e, 0).sum())
+    span = raw_max - raw_min
+    shift = 0
+    while (span >> shift) >= N_BINS:
+        shift += 1
+    return -raw_min, shift
+
+
+def bin_centre_trait(bias: int, shift: int) -> np.ndarray:
+    """Trait value z at the centre of each of the 4096 bins."""
+    b = np.arange(N_BINS, dtype=np.float64)
+    raw_c = b * float(1 << shift) - float(bias) + (float(1 << shift) - 1.0) / 2.0
+    return raw_c / 512.0
+
+
+def stabilizing_table(bias: int, shift: int, s: float, theta: float = 0.0) -> np.ndarray:
+    """Gaussian stabilising viability w(z) = exp(-s (z - theta)^2) as uint32
+    thresholds: floor(w * 2^32) capped at 0xFFFFFFFE, and 0xFFFFFFFF exactly
+    where w == 1."""
+    z = bin_centre_trait(bias, shift)
+    w = np.exp(-s * (z - theta) ** 2)
+    t = np.floor(w * 4294967296.0)
+    t = np.minimum(t, 4294967294.0).astype(np.uint64)
+    t[w >= 1.0] = CERTAIN
+    return t.astype(np.uint32)
+
+
+def constant_table(value: int) -> np.ndarray:
+    return np.full(N_BINS, value, dtype=np.uint32)
+
+
+def attack_table(bias: int, shift: int, base: float = 1.0, amp: float = 0.5) -> np.ndarray:
+    """Trait-dependent attack rate a(z) = base + amp * tanh(z) in Q16 (uint32)."""
+    z = bin_centre_trait(bias, shift)
+    a = np.rint((base + amp * np.tanh(z)) * 65536.0)
+    return np.clip(a, 0, 2 ** 32 - 1).astype(np.uint32)
+
+
+def genotype_table(bias: int, shift: int, effects: np.ndarray,
+                   w_by_copies: List[float]) -> np.ndarray:
+    """Viability table for a one-locus model: locus 0 carries the only nonzero
+    effect; genotypes with 0/1/2 copies get viabilities w_by_copies[0..2]
+    (given as probabilities; 1.0 means certain)."""
+    t = constant_table(CERTAIN)
+    e0 = int(effects[0])
+    for copies, w in enumerate(w_by_copies):
+        raw = copies * e0
+        v = raw + bias
+        b = 0 if v < 0 else min(v >> shift, N_BINS - 1)
+        t[b] = CERTAIN if w >= 1.0 else min(int(math.floor(w * 4294967296.0)), 0xFFFFFFFE)
+    return t
+
+
+def p0_threshold(p0: float) -> int:
+    """Q32 threshold for initial allele frequency p0 (allele 1 iff u < thr)."""
+    return int(min(max(math.floor(p0 * 4294967296.0), 0), 0xFFFFFFFF))
+
+
+# --------------------------------------------------------------------------
+# special starting genotypes (packed records, uint32[n, 2W])
+# --------------------------------------------------------------------------
+def genotypes_uniform(n: int, n_loci: int, hap0_word: int, hap1_word: int) -> np.ndarray:
+    w = n_loci // 32
+    g = np.empty((n, 2 * w), dtype=np.uint32)
+    g[:, :w] = np.uint32(hap0_word)
+    g[:, w:] = np.uint32(hap1_word)
+    return g
+
+
+def genotypes_random_haplotype_pairs(n: int, n_loci: int, seed: int) -> np.ndarray:
+    """Each haplotype is independently all-0 or all-1 with probability 1/2:
+    allele frequency 1/2 at every locus, Hardy-Weinberg pairing of haplotypes,
+    and maximal linkage disequilibrium D = 1/4 between every pair of loci."""
+    w = n_loci // 32
+    rng = np.random.default_rng(seed)
+    which = rng.integers(0, 2, size=(n, 2))
+    g = np.empty((n, 2 * w), dtype=np.uint32)
+    g[:, :w] = np.where(which[:, :1] == 1, np.uint32(0xFFFFFFFF), np.uint32(0))
+    g[:, w:] = np.where(which[:, 1:] == 1, np.uint32(0xFFFFFFFF), np.uint32(0))
+    return g
+
+
+def genotypes_bernoulli(n: int, n_loci: int, p: float, seed: int) -> np.ndarray:
+    w = n_loci // 32
+    rng = np.random.default_rng(seed)
+    bits = (rng.random((n, 2, n_loci)) < p).astype(np.uint64)
+    bits = bits.reshape(n, 2, w, 32)
+    words = (bits << np.arange(32, dtype=np.uint64)).sum(axis=3).astype(np.uint32)
+    return words.reshape(n, 2 * w)
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Workload:
+    """One population's inputs.  All tables are uint32[4096]."""
+    name: str
+    n: int
+    n_loci: int
+    n_gen: int
+    seed: int
+    replicate: int
+    effects: np.ndarray
+    bias: int
+    shift: int
+    surv_table: np.ndarray
+    mu: float
+    p0_q32: int = 0x80000000
+    init_genotypes: Optional[np.ndarray] = None
+    # ecology (consumer-resource); None when the population has no resource
+    eco_r: Optional[float] = None
+    eco_K: Optional[float] = None
+    eco_R0: Optional[float] = None
+    eco_R_half: Optional[float] = None
+    attack: Optional[np.ndarray] = None
+    s: float = 0.0
+
+    @property
+    def words(self) -> int:
+        return self.n_loci // 32
+
+    @property
+    def has_ecology(self) -> bool:
+        return self.attack is not None
+
+
+def single_species(n: int = 10_000, n_loci: int = 32, n_gen: int = 100, mu: float = 1e-4,
+                   s: float = 0.5, seed: int = 0, replicate: int = 0,
+                   effects_seed: int = 0, name: str = "single-species") -> Workload:
+    """Single species, additive trait, Gaussian stabilising viability, random
+    mating, free recombination, per-locus mutation; defaults are the
+    N=10,000 / L=32 / 100-generation workload."""
+    e = effects_q8(n_loci, 0.1, effects_seed)
+    bias, shift = bin_map(e)
+    return Workload(name=name, n=n, n_loci=n_loci, n_gen=n_gen, seed=seed, replicate=replicate,
+                    effects=e, bias=bias, shift=shift,
+                    surv_table=stabilizing_table(bias, shift, s), mu=mu, s=s)
+
+
+def consumer_resource(n: int = 1_000_000, n_loci: int = 128, n_gen: int = 1000, mu: float = 1e-5,
+                      s: float = 0.5, r: float = 0.5, K: float = 1e7, seed: int = 0,
+                      replicate: int = 0, effects_seed: int = 1,
+                      name: str = "consumer-resource") -> Workload:
+    """One consumer species feeding on a logistic resource (r, K); survival =
+    stabilising viability x resource factor R/(R + K/10); trait-dependent
+    attack rate; defaults are the N=1,000,000 / L=128 / 1,000-generation
+    workload with R0 = K/2."""
+    w = single_species(n, n_loci, n_gen, mu, s, seed, replicate, effects_seed, name)
+    w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half = r, K, K / 2.0, K / 10.0
+    w.attack = attack_table(w.bias, w.shift)
+    return w
+
+
+def batch_replicates(count: int = 4096, n_gen: int = 500, n_min: int = 1_000, n_max: int = 200_000,
+                     loci_choices=(32, 64, 128), s_max: float = 0.5, mu: float = 1e-5,
+                     seed: int = 0, spec_seed: int = 12345) -> List[Workload]:
+    """Independent single-species replicates: N log-uniform in [n_min, n_max],
+    L uniform over loci_choices, selection strength uniform in [0, s_max];
+    replicate r uses Philox seed `seed` and replicate id r."""
+    rng = np.random.default_rng(spec_seed)
+    out = []
+    for r in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        L = int(rng.choice(loci_choices))
+        s = float(rng.uniform(0.0, s_max))
+        out.append(single_species(n, L, n_gen, mu, s, seed, r, effects_seed=1000 + r,
+                                  name=f"replicate-{r}"))
+    return out
