@@ -1,0 +1,293 @@
+"""Benchmark of the per-generation update on one GB300.
+
+A step is one pass of the hot path over the consumer-resource workload:
+N = 1,000,000 diploid individuals, L = 128 loci (4 words per haplotype),
+mu = 1e-5, Gaussian stabilising viability (s = 0.5), logistic resource
+(r = 0.5, K = 1e7, R0 = K/2, R_half = K/10), 1,000 generations.  The metric is
+individual-generations per second (N x generations / time).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (test infrastructure, single thread) on a
+bounded sample of the same workload.  Under torchrun (N > 1) every rank runs an
+independent replica of the workload (replicas only, no collective on the data
+path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import spegg_synth as S  # noqa: E402
+
+GENERATIONS = 1000
+# Algorithmic bytes per offspring-generation: two survivor-index reads (8 B),
+# two parent records (2 x 8W B), the child record (8W B), one survivor index
+# write (4 B) = 12 + 24W.
+def algorithmic_bytes(words: int) -> int:
+    return 12 + 24 * words
+
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
+# the hash of the kernel source it was taken on (null once the kernel changes).
+MEASURED_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1603_09255_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        loaded = [x for x in sm if smax and x > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+def reference_arm(args, workload):
+    """The CPU oracle timed on a bounded sample: each step is one generation of
+    the full-size population, single-threaded."""
+    import oracle
+    rank, _, ws = dist_env()
+    if rank != 0:
+        return
+    pop = oracle.OraclePopulation.from_workload(workload)
+    for _ in range(args.warmup):
+        pop.step(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pop.step(1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = workload.n * args.steps / total
+    sample = f"{args.steps} generation(s) of the N={workload.n}, L={workload.n_loci} population after {args.warmup} warm-up"
+    line = {
+        "impl": "reference", "metric": "individual-generations/s", "value": value,
+        "unit": "individual-generations/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": bench_config(workload, "none (CPU)"),
+        "cpu_baseline": {"value": value, "unit": "individual-generations/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "individual-generations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def bench_config(w, l2):
+    return {"workload": f"consumer-resource N={w.n} L={w.n_loci} mu={w.mu:g} s={w.s} r={w.eco_r} K={w.eco_K:g}, "
+                        f"{GENERATIONS} generations per step",
+            "n": w.n, "n_loci": w.n_loci, "generations_per_step": GENERATIONS, "l2": l2}
+
+
+def cpu_baseline(workload, target_seconds=12.0):
+    import oracle
+    pop = oracle.OraclePopulation.from_workload(workload)
+    t0 = time.perf_counter()
+    gens = 0
+    while time.perf_counter() - t0 < target_seconds and gens < 20:
+        pop.step(1)
+        gens += 1
+    dt = time.perf_counter() - t0
+    return {"value": workload.n * gens / dt, "unit": "individual-generations/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {gens} generations of the N={workload.n}, L={workload.n_loci} consumer-resource "
+                      f"population, single thread, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    workload = S.consumer_resource()
+    if args.impl == "reference":
+        reference_arm(args, workload)
+        return
+
+    import torch
+    from paper_1603_09255_gb300 import build as pkg_build
+    rank, local_rank, ws = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    pkg_build.build()
+    from paper_1603_09255_gb300 import spegg
+
+    workload.replicate = rank
+    stream = torch.cuda.Stream()
+    pop = spegg.Population.from_workload(workload, stats_capacity=GENERATIONS + 8, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        pop.step(GENERATIONS)
+    pop.synchronize()
+
+    # timed region: K steps, L2 flushed before each, CUDA events on the stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clocks:
+        barrier()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(stream)
+            pop.step(GENERATIONS)
+            with torch.cuda.stream(stream):
+                ev[i][1].record(stream)
+        stream.synchronize()
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = pop.state()
+    assert st["status"] == 0, f"population status {st['status']}"
+    ind_gen = workload.n * GENERATIONS * args.steps
+    value = ind_gen * ws / (total_ms / 1000.0)
+
+    # dominant kernel: the fused generation kernel, one launch per generation
+    launches = GENERATIONS * args.steps
+    avg_launch_s = total_ms / 1000.0 / launches
+    peak, peak_kind = load_peaks()
+    bytes_per_launch = algorithmic_bytes(workload.words) * workload.n
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    traffic = MEASURED_TRAFFIC.get(kernel_source_hash())
+
+    # kernel-only duration: direct launches bracketed by events (untimed pass)
+    k_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
+    for a, b in k_ev:
+        with torch.cuda.stream(stream):
+            a.record(stream)
+        pop.step(1)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+    stream.synchronize()
+    kernel_ms = statistics.median([a.elapsed_time(b) for a, b in k_ev])
+
+    # end to end through the C ABI with host buffers: restore the population
+    # from pinned host memory, run the generations, read the statistics back
+    blob = pop.checkpoint()
+    pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[:] = np.frombuffer(blob, dtype=np.uint8)
+    e2e_times = []
+    for i in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pop.restore_from(pinned.data_ptr(), len(blob))
+        g0 = pop.state()["gen"]
+        pop.step(GENERATIONS)
+        stats = pop.read_stats(g0 + 1, GENERATIONS)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = workload.n * GENERATIONS * ws / (sum(e2e_times) / len(e2e_times))
+    assert len(stats) == GENERATIONS
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "individual-generations/s", "value": value, "unit": "individual-generations/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "p50_ms_per_step": float(np.percentile(step_ms, 50)), "p99_ms_per_step": float(np.percentile(step_ms, 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": bench_config(workload, "flushed before every step (256 MB write)"),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": f"k_generation<W={workload.words}> (fused generation)",
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6,
+                     "isolated_launch_us": kernel_ms * 1000.0},
+        "e2e": {"value": e2e_value, "unit": "individual-generations/s", "h2d_bytes_per_step": len(blob),
+                "d2h_bytes_per_step": int(stats.nbytes)},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(workload)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * spegg.h -- C ABI of the GB300 (sm_103a) engine for the per-generation update
+ * of a forward-time, multi-locus population-genetics simulation (sPEGG,
+ * Okamoto & Amarasekare, arXiv:1603.09255).
+ *
+ * One generation of a population, in the order of the paper's Fig. 1:
+ *   (A) parents: every offspring draws a mother and a father uniformly, with
+ *       replacement, from the previous generation's survivors (Wright-Fisher,
+ *       constant N offspring);
+ *   (B) transmission: each gamete takes every locus from one of its parent's
+ *       two haplotypes by an independent fair bit (free recombination, S2
+ *       "Genetics"), then each allele copy mutates (flips) with probability mu;
+ *   (C) phenotype: raw = sum over loci of effect[l] * (copies of allele 1)
+ *       (additive map, eq. S2-phenval; the trait is z = raw / 512);
+ *   (D) survival: bin = clamp((raw + bin_bias) >> bin_shift, 0, 4095); the
+ *       offspring survives with probability table[bin] / 2^32 (0xFFFFFFFF =
+ *       certain), scaled by the resource factor f when an ecology is set;
+ *   (E) the survivors, in offspring order, become the next parents;
+ *   (F) ecology: a logistic resource is consumed by the survivors
+ *       (trait-dependent attack table) and sets the next factor f.
+ *
+ * Genotype layout: L loci (a multiple of 32; 32, 64, 128 or 256), W = L/32
+ * uint32 words per haplotype, one individual = 2W consecutive words
+ * (haplotype 0 words, then haplotype 1 words); locus l is bit l%32 of word
+ * l/32.  Haplotype 0 of an offspring is its mother's gamete.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key (seed low
+ * word, seed high word) and counter (i, g, replicate, purpose<<24 | sub),
+ * i = individual index, g = generation being formed (0 = founders):
+ *   founders  purpose 1: allele copy q = h*L + l is 1 iff lane q%4 of sub q/4
+ *             is < p0_q32;
+ *   parents   purpose 2, sub 0: lane 0 -> mother, lane 1 -> father (index
+ *             floor(u * S / 2^32) into the survivor list), lane 2 -> survival
+ *             draw u (survive iff u < threshold), lane 3 -> mutation count
+ *             k = number of Binomial(2L, mu) CDF entries <= u;
+ *   gametes   purpose 3: stream q = 2w + parent (0 mother, 1 father) is lane
+ *             q%4 of sub q/4; bit b set -> locus 32w+b comes from haplotype 1;
+ *   mutations purpose 4: draw a is lane a%4 of sub a/4, position
+ *             floor(u * 2L / 2^32) (p < L: haplotype 0 locus p, else
+ *             haplotype 1 locus p-L); draws a = 0..63 until k distinct.
+ * The Binomial CDF is tabulated in Q32 from mu with IEEE-double basic
+ * operations in a fixed order: P0 = (1-mu)^(2L) by repeated multiplication,
+ * P(k+1) = ((P(k) * (2L-k)) / (k+1)) * mu / (1-mu), cdf[k] = floor(2^32 *
+ * running sum), stopping at the first value >= 0xFFFFFFFF or after 32 entries.
+ *
+ * Conventions for every call:
+ *   - return value: SPG_OK (0), SPG_EXTINCT (1, informational), or a negative
+ *     SPG_ERR_* code; spg_last_error() gives a message for the calling thread;
+ *   - caller arrays are read (copied) during the call; the caller keeps them;
+ *   - device memory is owned by the library (through the caller's allocator
+ *     when one is given) and released by the matching destroy call;
+ *   - work is enqueued on the object's CUDA stream; only read_*, get_state,
+ *     checkpoint and synchronize wait for it.
+ */
+#ifndef SPEGG_H
+#define SPEGG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPG_ABI_VERSION 1u
+#define SPG_N_BINS 4096u
+#define SPG_CERTAIN 0xFFFFFFFFu
+#define SPG_MAX_LOCI 256u
+
+enum spg_status_code {
+    SPG_OK = 0,
+    SPG_EXTINCT = 1,        /* the population has no survivors; stepping stops */
+    SPG_ERR_INVALID = -1,   /* bad argument or description                      */
+    SPG_ERR_OOM = -2,       /* device allocation failed                         */
+    SPG_ERR_CUDA = -3,      /* a CUDA runtime call failed                       */
+    SPG_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up               */
+    SPG_ERR_RANGE = -5,     /* requested generations are not in the stats ring  */
+    SPG_ERR_BUDGET = -6     /* request exceeds the server's memory budget       */
+};
+
+typedef struct spg_pop spg_pop;
+
+/* Optional device-memory hooks (e.g. a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` (256-byte aligned) or NULL;
+ * free releases a pointer returned by alloc.  NULL hooks: cudaMallocAsync /
+ * cudaFreeAsync on the object's stream. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} spg_allocator;
+
+/* One population (one species, one replicate). */
+typedef struct {
+    uint32_t n;                     /* N individuals per generation, 1 .. 2^31-1        */
+    uint32_t n_loci;                /* L: 32, 64, 128 or 256                            */
+    uint64_t seed;                  /* Philox key                                       */
+    uint32_t replicate;             /* replicate id (Philox counter word 2)             */
+    const int16_t *effects;         /* [L] allelic effects of allele 1, Q8              */
+    const uint32_t *init_genotypes; /* [N * 2W] generation-0 records, or NULL           */
+    uint32_t p0_q32;                /* if NULL above: allele 1 iff Philox draw < p0_q32 */
+    const uint32_t *surv_table;     /* [4096] viability thresholds (Q32, 0xFFFFFFFF = 1)*/
+    int32_t bin_bias;               /* phenotype bin map (see above)                    */
+    uint32_t bin_shift;             /* 0 .. 31                                          */
+    double mu;                      /* per-locus mutation probability, 0 <= mu < 1      */
+    uint32_t stats_capacity;        /* generations kept in the stats ring (0: 1024)     */
+} spg_pop_desc;
+
+/* Consumer-resource ecology (Fig. 1F; S2 "Resource Consumption"): after the
+ * survivors of generation g are known,
+ *   C  = sum over survivors of attack[bin]            (Q16 units)
+ *   R' = (R + (r*R) * (1 - R/K)) - C * 2^-16, clamped at 0
+ *   f  = floor(2^32 * R' / (R' + R_half)), capped at 0xFFFFFFFE
+ * and generation g+1 survives with threshold floor(table[bin] * f / 2^32). */
+typedef struct {
+    double r, K, R0, R_half;   /* growth rate, carrying capacity, initial R, half-saturation */
+    const uint32_t *attack;    /* [4096] attack rate per phenotype bin, Q16 */
+} spg_ecology;
+
+/* Exact per-generation statistics (integer sums over the N offspring unless
+ * noted). 88 bytes. */
+typedef struct {
+    uint32_t gen;          /* generation index g (1-based)                    */
+    uint32_t n;            /* offspring                                       */
+    uint32_t s;            /* survivors                                       */
+    uint32_t status;       /* SPG_OK or SPG_EXTINCT after this generation      */
+    int64_t sum_raw;       /* sum of raw phenotypes                           */
+    uint64_t sum_raw2;     /* sum of raw^2                                    */
+    int64_t sum_raw_surv;  /* sum of raw over survivors                       */
+    int32_t min_raw, max_raw;
+    uint64_t het;          /* heterozygous loci, summed                       */
+    uint64_t allele;       /* copies of allele 1, summed                      */
+    uint64_t consumption;  /* C (0 without ecology)                           */
+    double R;              /* resource after this generation (0 without)     */
+    uint32_t f;            /* factor for the next generation (0xFFFFFFFF: none)*/
+    uint32_t pad;
+} spg_stats;
+
+typedef struct {
+    uint32_t gen;      /* generations completed                         */
+    uint32_t S;        /* current survivors (parents of the next one)   */
+    int32_t status;    /* SPG_OK, SPG_EXTINCT or SPG_ERR_TIMEOUT        */
+    uint32_t f;        /* current resource factor                       */
+    double R;          /* current resource                              */
+} spg_state;
+
+/* Create a population at generation 0 (Fig. S4, Initialize()): validates and
+ * copies the description, allocates its device state and builds its
+ * generation-0 genotypes (the caller's, or Philox draws at frequency p0).
+ * stream: a cudaStream_t, or NULL for a stream the library creates and owns.
+ * Errors: SPG_ERR_INVALID (bad description), SPG_ERR_OOM, SPG_ERR_CUDA. */
+int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, void *stream,
+                          spg_pop **out);
+
+/* Attach (or replace) the consumer-resource ecology; resets R to R0 and f to
+ * the factor of R0.  Errors: SPG_ERR_INVALID (K <= 0, R_half <= 0, R0 < 0,
+ * NULL attack). */
+int spg_set_ecology(spg_pop *pop, const spg_ecology *eco);
+
+/* Enqueue n_gen generations (Fig. 1 A-F each) on the population's stream and
+ * return without waiting.  Generations after an extinction do nothing;
+ * extinction and device wait time-outs are reported by spg_get_state and
+ * spg_read_stats. */
+int spg_step_generations(spg_pop *pop, uint32_t n_gen);
+
+/* Copy statistics of generations first_gen .. first_gen+count-1 to out
+ * (waits for the stream).  SPG_ERR_RANGE if any of them has not run or has
+ * left the ring. */
+int spg_read_stats(spg_pop *pop, uint32_t first_gen, uint32_t count, spg_stats *out);
+
+/* Copy the current generation's N records (N * 2W words) to host memory;
+ * n_words must be at least N * 2W.  Waits for the stream. */
+int spg_read_genotypes(spg_pop *pop, uint32_t *host, size_t n_words);
+
+/* Copy the current survivor list (ascending offspring indices) to host;
+ * *S receives its length; host may be NULL to query the length only. */
+int spg_read_survivors(spg_pop *pop, uint32_t *host, size_t capacity, uint32_t *S);
+
+/* Current generation, survivors, status and resource (waits for the stream). */
+int spg_get_state(spg_pop *pop, spg_state *out);
+
+/* Whole-state snapshot (genotypes, survivors, generation, resource) for exact
+ * resumption: counter-based draws make a restored run identical to an
+ * uninterrupted one.  spg_checkpoint_size gives the byte size. */
+int spg_checkpoint_size(spg_pop *pop, size_t *bytes);
+int spg_checkpoint(spg_pop *pop, void *host, size_t capacity);
+int spg_restore(spg_pop *pop, const void *host, size_t bytes);
+
+/* Wait for all work enqueued on the population's stream. */
+int spg_synchronize(spg_pop *pop);
+
+/* Release the population's device memory (after its stream's work). */
+void spg_destroy(spg_pop *pop);
+
+/* FP32 summaries of one statistics record from its exact integer sums:
+ * out = {mean z, variance of z, survival fraction, heterozygosity per locus,
+ * allele-1 frequency}. */
+void spg_summarize(const spg_stats *st, uint32_t n_loci, float out[5]);
+
+/* The Binomial(n_copies, mu) CDF table the library uses for mutation counts
+ * (construction stated above); writes up to 32 entries to cdf and returns
+ * how many.  Host only. */
+uint32_t spg_mutation_cdf(double mu, uint32_t n_copies, uint32_t cdf[32]);
+
+const char *spg_status_string(int code);
+const char *spg_last_error(void);
+uint32_t spg_abi_version(void);
+
+/* Diagnostic for the bounded device waits (no counterpart in the paper):
+ * runs the survivor-compaction look-back of a tile whose predecessor never
+ * publishes, with at most spin_limit polls, and stores the status the wait
+ * returned (SPG_ERR_TIMEOUT when it gave up) in *result.  Allocates and frees
+ * 64 bytes of device memory; waits for the device. */
+int spg_debug_lookback_timeout(uint32_t spin_limit, int32_t *result);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPEGG_H */

@@ -1,0 +1,628 @@
+// Host engine and C ABI of libspegg_gb300 (see include/spegg.h).
+//
+// A population owns one device arena holding its parameters, two genotype
+// buffers and two survivor lists (ping-pong by generation parity, chosen on
+// the device so every generation launch has identical arguments), its
+// look-back status words, its state and its statistics ring.  Generations are
+// enqueued as a cached CUDA graph of kGraphChunk back-to-back launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "spegg.h"
+#include "spegg_engine.h"
+#include "spegg_internal.h"
+
+namespace spg {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(SPG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ host tables
+// Binomial(n_copies, mu) CDF in Q32 with IEEE-double basic operations in the
+// fixed order stated in spegg.h (each product/quotient rounded separately).
+uint32_t mutation_cdf(double mu, uint32_t n_copies, uint32_t *cdf) {
+    const double q = 1.0 - mu;
+    double p_k = 1.0;
+    for (uint32_t i = 0; i < n_copies; ++i) p_k = p_k * q;
+    double running = 0.0;
+    uint32_t entries = 0;
+    for (uint32_t k = 0; k <= n_copies && entries < (uint32_t)kMaxKmax; ++k) {
+        running = running + p_k;
+        const double q32 = running * 4294967296.0;
+        if (q32 >= 4294967295.0) break;
+        cdf[entries++] = (uint32_t)q32;
+        const double t1 = p_k * (double)(n_copies - k);
+        const double t2 = t1 / (double)(k + 1);
+        const double t3 = t2 * mu;
+        p_k = t3 / q;
+    }
+    return entries;
+}
+
+// Effects in offset binary: e_l - e_min split into bit planes, plane b word w
+// holding bit b of the offsets of loci 32w .. 32w+31.
+void effect_planes(const int16_t *effects, uint32_t n_loci, PopParams &prm) {
+    const uint32_t W = n_loci / 32;
+    int32_t e_min = effects[0], e_max = effects[0];
+    for (uint32_t l = 1; l < n_loci; ++l) {
+        e_min = std::min<int32_t>(e_min, effects[l]);
+        e_max = std::max<int32_t>(e_max, effects[l]);
+    }
+    const uint32_t span = (uint32_t)(e_max - e_min);
+    uint32_t nplanes = 0;
+    while (nplanes < 32 && (span >> nplanes) != 0u) ++nplanes;
+    std::memset(prm.planes, 0, sizeof prm.planes);
+    for (uint32_t l = 0; l < n_loci; ++l) {
+        const uint32_t off = (uint32_t)((int32_t)effects[l] - e_min);
+        for (uint32_t b = 0; b < nplanes; ++b)
+            if ((off >> b) & 1u) prm.planes[b * W + l / 32] |= 1u << (l % 32);
+    }
+    prm.e_min = e_min;
+    prm.nplanes = nplanes;
+}
+
+// Resource factor of the ecology, same arithmetic as the device finalizer.
+uint32_t factor_q32_host(double R, double R_half) {
+    const double den = R + R_half;
+    const double q = R / den;
+    const double scaled = q * 4294967296.0;
+    if (scaled >= 4294967294.0) return 0xFFFFFFFEu;
+    if (!(scaled > 0.0)) return 0u;
+    return (uint32_t)scaled;
+}
+
+// ----------------------------------------------------------- device memory
+void *Allocator::alloc(size_t bytes, cudaStream_t s) const {
+    if (hooks.alloc) return hooks.alloc(bytes, hooks.ctx);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void Allocator::release(void *p, cudaStream_t s) const {
+    if (!p) return;
+    if (hooks.free) hooks.free(p, hooks.ctx);
+    else cudaFreeAsync(p, s);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ----------------------------------------------------------- validation
+int validate_desc(const spg_pop_desc *d) {
+    if (!d) return fail(SPG_ERR_INVALID, "population description is NULL");
+    if (d->n == 0 || d->n > 0x7FFFFFFFu) return fail(SPG_ERR_INVALID, "n must be in [1, 2^31-1] (got %u)", d->n);
+    if (!(d->n_loci == 32 || d->n_loci == 64 || d->n_loci == 128 || d->n_loci == 256))
+        return fail(SPG_ERR_INVALID, "n_loci must be 32, 64, 128 or 256 (got %u)", d->n_loci);
+    if (!d->effects) return fail(SPG_ERR_INVALID, "effects is NULL");
+    if (!d->surv_table) return fail(SPG_ERR_INVALID, "surv_table is NULL");
+    if (d->bin_shift > 31) return fail(SPG_ERR_INVALID, "bin_shift must be <= 31");
+    if (!(d->mu >= 0.0 && d->mu < 1.0)) return fail(SPG_ERR_INVALID, "mu must be in [0, 1)");
+    if (d->stats_capacity == 1) return fail(SPG_ERR_INVALID, "stats_capacity must be 0 or >= 2");
+    return SPG_OK;
+}
+
+int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
+    std::memset(&prm, 0, sizeof prm);
+    std::memcpy(prm.table, d->surv_table, sizeof prm.table);
+    effect_planes(d->effects, d->n_loci, prm);
+    if (prm.nplanes > (uint32_t)kMaxPlanes) return fail(SPG_ERR_INVALID, "effects span more than 16 bits");
+    prm.kmax = mutation_cdf(d->mu, 2 * d->n_loci, prm.cdf);
+    prm.bias = d->bin_bias;
+    prm.shift = d->bin_shift;
+    prm.n = d->n;
+    prm.n_loci = d->n_loci;
+    prm.words = d->n_loci / 32;
+    prm.key0 = (uint32_t)(d->seed & 0xFFFFFFFFull);
+    prm.key1 = (uint32_t)(d->seed >> 32);
+    prm.rep = d->replicate;
+    prm.has_eco = 0;
+    prm.ntiles = (d->n + tile_size(items) - 1) / tile_size(items);
+    prm.stats_cap = d->stats_capacity ? d->stats_capacity : 1024u;
+    return SPG_OK;
+}
+
+// ------------------------------------------------------------ population
+PopLayout layout_for(uint32_t n, uint32_t words, uint32_t ntiles, uint32_t cap) {
+    PopLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    L.params = take(sizeof(PopParams));
+    L.state = take(sizeof(DevState));
+    L.geno0 = take((size_t)n * 2 * words * 4);
+    L.geno1 = take((size_t)n * 2 * words * 4);
+    L.surv0 = take((size_t)n * 4);
+    L.surv1 = take((size_t)n * 4);
+    L.tiles = take((size_t)ntiles * 8);
+    L.ring = take((size_t)cap * sizeof(spg_stats));
+    L.segment = take(sizeof(Segment));
+    L.ctl = take(sizeof(LaunchCtl));
+    L.total = off;
+    return L;
+}
+
+Segment segment_at(char *base, const PopLayout &L, uint32_t ntiles, uint32_t tile_begin) {
+    Segment s{};
+    s.prm = reinterpret_cast<const PopParams *>(base + L.params);
+    s.geno[0] = reinterpret_cast<uint32_t *>(base + L.geno0);
+    s.geno[1] = reinterpret_cast<uint32_t *>(base + L.geno1);
+    s.surv[0] = reinterpret_cast<uint32_t *>(base + L.surv0);
+    s.surv[1] = reinterpret_cast<uint32_t *>(base + L.surv1);
+    s.tile_status = reinterpret_cast<unsigned long long *>(base + L.tiles);
+    s.state = reinterpret_cast<DevState *>(base + L.state);
+    s.ring = reinterpret_cast<spg_stats *>(base + L.ring);
+    s.tile_begin = tile_begin;
+    s.ntiles = ntiles;
+    return s;
+}
+
+uint32_t default_items(uint32_t words) { return words >= 8 ? 1u : words >= 4 ? 2u : 4u; }
+
+GraphChain::~GraphChain() { reset(); }
+
+void GraphChain::reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    length = 0;
+}
+
+// A graph of `len` dependent launches of `kern` with identical arguments.
+int GraphChain::build(GenKernel kern, const GenArgs &args, uint32_t grid, uint32_t len) {
+    reset();
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+    GenArgs a = args;
+    void *params[] = {&a};
+    cudaGraphNode_t prev = nullptr;
+    for (uint32_t i = 0; i < len; ++i) {
+        cudaKernelNodeParams kp{};
+        kp.func = reinterpret_cast<void *>(kern);
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(kBlock);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = params;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        if (e != cudaSuccess) {
+            reset();
+            return cuda_fail(e, "cudaGraphAddKernelNode");
+        }
+        prev = node;
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        reset();
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    length = len;
+    return SPG_OK;
+}
+
+int enqueue_generations(GenKernel kern, const GenArgs &args, uint32_t grid, uint32_t n_gen, GraphChain &chain,
+                        cudaStream_t stream) {
+    if (n_gen == 0) return SPG_OK;
+    if (n_gen >= kGraphChunk) {
+        if (!chain.exec) {
+            const int rc = chain.build(kern, args, grid, kGraphChunk);
+            if (rc != SPG_OK) return rc;
+        }
+        for (uint32_t i = 0; i + kGraphChunk <= n_gen; i += kGraphChunk) {
+            const cudaError_t e = cudaGraphLaunch(chain.exec, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        }
+    }
+    for (uint32_t i = 0; i < n_gen % kGraphChunk; ++i) {
+        kern<<<grid, kBlock, 0, stream>>>(args);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "generation launch");
+}
+
+}  // namespace spg
+
+using namespace spg;
+
+struct spg_pop {
+    uint32_t n = 0, n_loci = 0, words = 0, items = 0, ntiles = 0, cap = 0;
+    uint64_t seed = 0;
+    uint32_t rep = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Allocator alloc;
+    char *arena = nullptr;
+    PopLayout L{};
+    PopParams *host_prm = nullptr;  // host copy of the parameters
+    GenKernel kern = nullptr;
+    GenArgs args{};
+    GraphChain chain;
+    bool has_eco = false;
+    double R0 = 0.0;
+};
+
+namespace {
+
+int sync_stream(spg_pop *p) {
+    const cudaError_t e = cudaStreamSynchronize(p->stream);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
+
+int read_state(spg_pop *p, DevState &st) {
+    int rc = sync_stream(p);
+    if (rc != SPG_OK) return rc;
+    const cudaError_t e = cudaMemcpy(&st, p->arena + p->L.state, sizeof st, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read state");
+}
+
+int upload_params(spg_pop *p) {
+    const cudaError_t e = cudaMemcpyAsync(p->arena + p->L.params, p->host_prm, sizeof(PopParams),
+                                          cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload parameters");
+    // the host copy must stay valid until the copy has run
+    return sync_stream(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t spg_abi_version(void) { return SPG_ABI_VERSION; }
+
+uint32_t spg_mutation_cdf(double mu, uint32_t n_copies, uint32_t cdf[32]) {
+    if (!cdf || !(mu >= 0.0 && mu < 1.0)) return 0;
+    return mutation_cdf(mu, n_copies, cdf);
+}
+
+const char *spg_last_error(void) { return g_last_error.c_str(); }
+
+const char *spg_status_string(int code) {
+    switch (code) {
+        case SPG_OK: return "ok";
+        case SPG_EXTINCT: return "extinct: no survivors";
+        case SPG_ERR_INVALID: return "invalid argument";
+        case SPG_ERR_OOM: return "device allocation failed";
+        case SPG_ERR_CUDA: return "CUDA runtime error";
+        case SPG_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SPG_ERR_RANGE: return "generations not available";
+        case SPG_ERR_BUDGET: return "memory budget exceeded";
+        default: return "unknown status";
+    }
+}
+
+int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, void *stream, spg_pop **out) {
+    if (!out) return fail(SPG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int rc = validate_desc(desc);
+    if (rc != SPG_OK) return rc;
+    spg_pop *p = new (std::nothrow) spg_pop();
+    if (!p) return fail(SPG_ERR_OOM, "host allocation failed");
+    p->n = desc->n;
+    p->n_loci = desc->n_loci;
+    p->words = desc->n_loci / 32;
+    p->items = default_items(p->words);
+    p->seed = desc->seed;
+    p->rep = desc->replicate;
+    p->host_prm = new (std::nothrow) PopParams();
+    if (!p->host_prm) {
+        delete p;
+        return fail(SPG_ERR_OOM, "host allocation failed");
+    }
+    rc = build_params(desc, p->items, *p->host_prm);
+    if (rc != SPG_OK) {
+        delete p->host_prm;
+        delete p;
+        return rc;
+    }
+    p->ntiles = p->host_prm->ntiles;
+    p->cap = p->host_prm->stats_cap;
+    if (alloc) p->alloc.hooks = *alloc;
+    if (stream) {
+        p->stream = (cudaStream_t)stream;
+    } else {
+        const cudaError_t e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete p->host_prm;
+            delete p;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        p->own_stream = true;
+    }
+    p->L = layout_for(p->n, p->words, p->ntiles, p->cap);
+    p->arena = static_cast<char *>(p->alloc.alloc(p->L.total, p->stream));
+    if (!p->arena) {
+        spg_destroy(p);
+        return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", p->L.total);
+    }
+    p->kern = generation_kernel(p->words, p->items);
+    cudaError_t e = cudaMemsetAsync(p->arena + p->L.tiles, 0, (size_t)p->ntiles * 8, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->arena + p->L.ctl, 0, sizeof(LaunchCtl), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->arena + p->L.ring, 0, (size_t)p->cap * sizeof(spg_stats), p->stream);
+    if (e != cudaSuccess) {
+        spg_destroy(p);
+        return cuda_fail(e, "initialise device memory");
+    }
+    const Segment seg = segment_at(p->arena, p->L, p->ntiles, 0);
+    e = cudaMemcpyAsync(p->arena + p->L.segment, &seg, sizeof seg, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) {
+        spg_destroy(p);
+        return cuda_fail(e, "upload segment");
+    }
+    rc = upload_params(p);  // synchronises, so &seg above is no longer needed
+    if (rc != SPG_OK) {
+        spg_destroy(p);
+        return rc;
+    }
+    uint32_t *geno0 = reinterpret_cast<uint32_t *>(p->arena + p->L.geno0);
+    uint32_t *surv0 = reinterpret_cast<uint32_t *>(p->arena + p->L.surv0);
+    if (desc->init_genotypes) {
+        e = cudaMemcpyAsync(geno0, desc->init_genotypes, (size_t)p->n * 2 * p->words * 4, cudaMemcpyHostToDevice,
+                            p->stream);
+        if (e != cudaSuccess) {
+            spg_destroy(p);
+            return cuda_fail(e, "upload founders");
+        }
+        rc = launch_iota(surv0, p->n, p->stream);
+    } else {
+        rc = launch_founders(p->words, geno0, surv0, p->n, p->host_prm->key0, p->host_prm->key1, p->rep,
+                             desc->p0_q32, p->stream);
+    }
+    if (rc == SPG_OK)
+        rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
+                              reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap, 0, p->n, kCertain, 0.0,
+                              SPG_OK, p->stream);
+    if (rc == SPG_OK) rc = sync_stream(p);  // caller's founder array is read before returning
+    if (rc != SPG_OK) {
+        spg_destroy(p);
+        return rc == SPG_ERR_CUDA ? rc : fail(rc, "initialise population");
+    }
+    p->args.segs = reinterpret_cast<const Segment *>(p->arena + p->L.segment);
+    p->args.nsegs = 1;
+    p->args.total_tiles = p->ntiles;
+    p->args.ctl = reinterpret_cast<LaunchCtl *>(p->arena + p->L.ctl);
+    p->args.spin_limit = kSpinLimit;
+    *out = p;
+    return SPG_OK;
+}
+
+int spg_set_ecology(spg_pop *p, const spg_ecology *eco) {
+    if (!p || !eco) return fail(SPG_ERR_INVALID, "NULL argument");
+    if (!eco->attack) return fail(SPG_ERR_INVALID, "attack table is NULL");
+    if (!(eco->K > 0.0) || !(eco->R_half > 0.0) || !(eco->R0 >= 0.0) || !std::isfinite(eco->r) ||
+        !std::isfinite(eco->K) || !std::isfinite(eco->R0))
+        return fail(SPG_ERR_INVALID, "ecology needs K > 0, R_half > 0, R0 >= 0, finite r");
+    DevState st;
+    int rc = read_state(p, st);
+    if (rc != SPG_OK) return rc;
+    std::memcpy(p->host_prm->attack, eco->attack, sizeof p->host_prm->attack);
+    p->host_prm->has_eco = 1;
+    p->host_prm->r = eco->r;
+    p->host_prm->K = eco->K;
+    p->host_prm->R_half = eco->R_half;
+    p->has_eco = true;
+    p->R0 = eco->R0;
+    rc = upload_params(p);
+    if (rc != SPG_OK) return rc;
+    rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
+                          reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap, st.gen, st.S,
+                          factor_q32_host(eco->R0, eco->R_half), eco->R0, st.status, p->stream);
+    return rc;
+}
+
+int spg_step_generations(spg_pop *p, uint32_t n_gen) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    return enqueue_generations(p->kern, p->args, p->ntiles, n_gen, p->chain, p->stream);
+}
+
+int spg_read_stats(spg_pop *p, uint32_t first_gen, uint32_t count, spg_stats *out) {
+    if (!p || (!out && count)) return fail(SPG_ERR_INVALID, "NULL argument");
+    DevState st;
+    int rc = read_state(p, st);
+    if (rc != SPG_OK) return rc;
+    if (count == 0) return SPG_OK;
+    const uint64_t last = (uint64_t)first_gen + count - 1;
+    if (first_gen == 0 || last > st.gen || (uint64_t)st.gen - first_gen >= p->cap)
+        return fail(SPG_ERR_RANGE, "generations %u..%llu not in the ring (completed %u, capacity %u)", first_gen,
+                    (unsigned long long)last, st.gen, p->cap);
+    const spg_stats *ring = reinterpret_cast<const spg_stats *>(p->arena + p->L.ring);
+    for (uint32_t i = 0; i < count;) {
+        const uint32_t slot = (first_gen - 1 + i) % p->cap;
+        const uint32_t run = std::min(count - i, p->cap - slot);
+        const cudaError_t e = cudaMemcpy(out + i, ring + slot, run * sizeof(spg_stats), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read stats");
+        i += run;
+    }
+    return st.status < 0 ? fail(st.status, "device status %d", st.status) : SPG_OK;
+}
+
+int spg_read_genotypes(spg_pop *p, uint32_t *host, size_t n_words) {
+    if (!p || !host) return fail(SPG_ERR_INVALID, "NULL argument");
+    const size_t need = (size_t)p->n * 2 * p->words;
+    if (n_words < need) return fail(SPG_ERR_INVALID, "buffer holds %zu words, need %zu", n_words, need);
+    DevState st;
+    int rc = read_state(p, st);
+    if (rc != SPG_OK) return rc;
+    const char *src = p->arena + ((st.gen & 1u) ? p->L.geno1 : p->L.geno0);
+    const cudaError_t e = cudaMemcpy(host, src, need * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read genotypes");
+}
+
+int spg_read_survivors(spg_pop *p, uint32_t *host, size_t capacity, uint32_t *S) {
+    if (!p || !S) return fail(SPG_ERR_INVALID, "NULL argument");
+    DevState st;
+    int rc = read_state(p, st);
+    if (rc != SPG_OK) return rc;
+    *S = st.S;
+    if (!host) return SPG_OK;
+    if (capacity < st.S) return fail(SPG_ERR_INVALID, "buffer holds %zu, need %u", capacity, st.S);
+    const char *src = p->arena + ((st.gen & 1u) ? p->L.surv1 : p->L.surv0);
+    const cudaError_t e = cudaMemcpy(host, src, (size_t)st.S * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read survivors");
+}
+
+int spg_get_state(spg_pop *p, spg_state *out) {
+    if (!p || !out) return fail(SPG_ERR_INVALID, "NULL argument");
+    DevState st;
+    const int rc = read_state(p, st);
+    if (rc != SPG_OK) return rc;
+    out->gen = st.gen;
+    out->S = st.S;
+    out->status = st.status;
+    out->f = st.f;
+    out->R = st.R;
+    return SPG_OK;
+}
+
+int spg_checkpoint_size(spg_pop *p, size_t *bytes) {
+    if (!p || !bytes) return fail(SPG_ERR_INVALID, "NULL argument");
+    *bytes = sizeof(CheckpointHeader) + (size_t)p->n * 2 * p->words * 4 + (size_t)p->n * 4;
+    return SPG_OK;
+}
+
+int spg_checkpoint(spg_pop *p, void *host, size_t capacity) {
+    size_t need = 0;
+    int rc = spg_checkpoint_size(p, &need);
+    if (rc != SPG_OK) return rc;
+    if (!host || capacity < need) return fail(SPG_ERR_INVALID, "checkpoint buffer too small (need %zu)", need);
+    DevState st;
+    rc = read_state(p, st);
+    if (rc != SPG_OK) return rc;
+    CheckpointHeader h{};
+    h.magic = kCheckpointMagic;
+    h.version = SPG_ABI_VERSION;
+    h.n = p->n;
+    h.n_loci = p->n_loci;
+    h.gen = st.gen;
+    h.S = st.S;
+    h.status = st.status;
+    h.f = st.f;
+    h.R = st.R;
+    h.seed = p->seed;
+    h.replicate = p->rep;
+    char *dst = static_cast<char *>(host);
+    std::memcpy(dst, &h, sizeof h);
+    const size_t gbytes = (size_t)p->n * 2 * p->words * 4;
+    cudaError_t e = cudaMemcpy(dst + sizeof h, p->arena + ((st.gen & 1u) ? p->L.geno1 : p->L.geno0), gbytes,
+                               cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dst + sizeof h + gbytes, p->arena + ((st.gen & 1u) ? p->L.surv1 : p->L.surv0),
+                       (size_t)st.S * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "checkpoint copy");
+}
+
+int spg_restore(spg_pop *p, const void *host, size_t bytes) {
+    size_t need = 0;
+    int rc = spg_checkpoint_size(p, &need);
+    if (rc != SPG_OK) return rc;
+    if (!host || bytes < sizeof(CheckpointHeader)) return fail(SPG_ERR_INVALID, "checkpoint too small");
+    CheckpointHeader h;
+    std::memcpy(&h, host, sizeof h);
+    if (h.magic != kCheckpointMagic || h.n != p->n || h.n_loci != p->n_loci || h.S > p->n || bytes < need)
+        return fail(SPG_ERR_INVALID, "checkpoint does not match this population");
+    if ((h.S == 0) != (h.status == SPG_EXTINCT) || h.status < 0)
+        return fail(SPG_ERR_INVALID, "checkpoint state is inconsistent");
+    const char *src = static_cast<const char *>(host);
+    const size_t gbytes = (size_t)p->n * 2 * p->words * 4;
+    {
+        // survivors index parent records: strictly increasing and < n
+        const uint32_t *sv = reinterpret_cast<const uint32_t *>(src + sizeof h + gbytes);
+        uint32_t prev = 0;
+        for (uint32_t i = 0; i < h.S; ++i) {
+            uint32_t v;
+            std::memcpy(&v, sv + i, 4);
+            if (v >= p->n || (i > 0 && v <= prev)) return fail(SPG_ERR_INVALID, "checkpoint survivor list is invalid");
+            prev = v;
+        }
+    }
+    rc = sync_stream(p);
+    if (rc != SPG_OK) return rc;
+    cudaError_t e = cudaMemcpy(p->arena + ((h.gen & 1u) ? p->L.geno1 : p->L.geno0), src + sizeof h, gbytes,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->arena + ((h.gen & 1u) ? p->L.surv1 : p->L.surv0), src + sizeof h + gbytes,
+                       (size_t)h.S * 4, cudaMemcpyHostToDevice);
+    // look-back words of the replaced run could carry the tags of the
+    // generations about to be replayed
+    if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.tiles, 0, (size_t)p->ntiles * 8);
+    if (e != cudaSuccess) return cuda_fail(e, "restore copy");
+    rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
+                          reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap, h.gen, h.S, h.f, h.R,
+                          h.status, p->stream);
+    if (rc != SPG_OK) return rc;
+    return sync_stream(p);
+}
+
+int spg_synchronize(spg_pop *p) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    return sync_stream(p);
+}
+
+void spg_destroy(spg_pop *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    p->chain.reset();
+    if (p->arena) p->alloc.release(p->arena, p->stream);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    delete p->host_prm;
+    delete p;
+}
+
+void spg_summarize(const spg_stats *st, uint32_t n_loci, float out[5]) {
+    const double n = (double)st->n;
+    const double mean_raw = (double)st->sum_raw / n;
+    const double second = (double)st->sum_raw2 / n;
+    const double sq = mean_raw * mean_raw;
+    const double var_raw = second - sq;
+    out[0] = (float)(mean_raw / 512.0);
+    out[1] = (float)(var_raw / (512.0 * 512.0));
+    out[2] = (float)((double)st->s / n);
+    out[3] = (float)((double)st->het / (n * (double)n_loci));
+    out[4] = (float)((double)st->allele / (2.0 * n * (double)n_loci));
+}
+
+int spg_debug_lookback_timeout(uint32_t spin_limit, int32_t *result) {
+    if (!result) return fail(SPG_ERR_INVALID, "NULL argument");
+    void *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, 64);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    e = cudaMemset(mem, 0, 64);
+    int rc = e == cudaSuccess ? SPG_OK : cuda_fail(e, "cudaMemset");
+    if (rc == SPG_OK)
+        rc = launch_lookback_probe(static_cast<unsigned long long *>(mem),
+                                   reinterpret_cast<int32_t *>(static_cast<char *>(mem) + 32), spin_limit, nullptr);
+    if (rc == SPG_OK) {
+        e = cudaMemcpy(result, static_cast<char *>(mem) + 32, 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "read probe result");
+    }
+    cudaFree(mem);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Host-side helpers shared by the population, batch and server engines.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+
+#include "spegg.h"
+#include "spegg_internal.h"
+
+namespace spg {
+
+constexpr uint32_t kGraphChunk = 32;          // generations per cached graph
+constexpr uint32_t kSpinLimit = 1u << 22;     // look-back polls (~64 ns apart) before giving up
+constexpr uint32_t kCheckpointMagic = 0x43475053u;  // "SPGC"
+
+struct CheckpointHeader {
+    uint32_t magic, version, n, n_loci, gen, S;
+    int32_t status;
+    uint32_t f;
+    double R;
+    uint64_t seed;
+    uint32_t replicate, pad;
+};
+
+struct Allocator {
+    spg_allocator hooks{nullptr, nullptr, nullptr};
+    void *alloc(size_t bytes, cudaStream_t s) const;
+    void release(void *p, cudaStream_t s) const;
+};
+
+// Byte offsets of one population's buffers inside its arena.
+struct PopLayout {
+    size_t params, state, geno0, geno1, surv0, surv1, tiles, ring, segment, ctl, total;
+};
+
+// A cached CUDA graph of dependent generation launches.
+struct GraphChain {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t length = 0;
+    ~GraphChain();
+    void reset();
+    int build(GenKernel kern, const GenArgs &args, uint32_t grid, uint32_t len);
+};
+
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+uint32_t mutation_cdf(double mu, uint32_t n_copies, uint32_t *cdf);
+void effect_planes(const int16_t *effects, uint32_t n_loci, PopParams &prm);
+uint32_t factor_q32_host(double R, double R_half);
+size_t align_up(size_t x, size_t a);
+int validate_desc(const spg_pop_desc *d);
+int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm);
+PopLayout layout_for(uint32_t n, uint32_t words, uint32_t ntiles, uint32_t cap);
+Segment segment_at(char *base, const PopLayout &L, uint32_t ntiles, uint32_t tile_begin);
+uint32_t default_items(uint32_t words);
+int enqueue_generations(GenKernel kern, const GenArgs &args, uint32_t grid, uint32_t n_gen, GraphChain &chain,
+                        cudaStream_t stream);
+
+}  // namespace spg

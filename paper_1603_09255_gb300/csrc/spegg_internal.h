@@ -1,0 +1,101 @@
+// Internal types shared by the host engine and the kernels of libspegg_gb300.
+// Not part of the C ABI (include/spegg.h is).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "spegg.h"
+
+namespace spg {
+
+constexpr int kBins = 4096;
+constexpr int kMaxKmax = 32;      // entries of the Binomial(2L, mu) CDF table
+constexpr int kMutDraws = 64;     // position draws tried per offspring
+constexpr int kMaxPlanes = 16;    // bit planes of the offset-binary effects
+constexpr int kMaxWords = 8;      // W = L/32 <= 8
+constexpr int kBlock = 256;       // threads per block of the generation kernel
+constexpr uint32_t kCertain = 0xFFFFFFFFu;
+
+// Philox counter word 3 = purpose << 24 | sub
+enum Purpose : uint32_t { kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4 };
+
+// Read-only parameters of one population (device global memory).
+struct alignas(16) PopParams {
+    uint32_t table[kBins];                  // viability thresholds per bin
+    uint32_t attack[kBins];                 // Q16 attack rate per bin (ecology)
+    uint32_t planes[kMaxPlanes * kMaxWords];// plane b, word w at [b * W + w]
+    uint32_t cdf[kMaxKmax];                 // Binomial(2L, mu) CDF, Q32
+    int32_t e_min;                          // effects = e_min + sum_b 2^b * plane_b
+    uint32_t nplanes;
+    int32_t bias;
+    uint32_t shift;
+    uint32_t kmax;
+    uint32_t n;
+    uint32_t n_loci;
+    uint32_t words;
+    uint32_t key0, key1, rep;
+    uint32_t has_eco;
+    double r, K, R_half;
+    uint32_t ntiles;
+    uint32_t stats_cap;
+};
+
+// Mutable per-population state (device global memory).
+struct alignas(16) DevState {
+    uint32_t gen;     // generations completed
+    uint32_t S;       // survivors of generation `gen` (parents of the next)
+    uint32_t f;       // resource factor applied to the next generation
+    int32_t status;   // SPG_OK, SPG_EXTINCT, SPG_ERR_TIMEOUT
+    double R;         // resource density
+    uint32_t done;    // tiles of the running generation that have finished
+    uint32_t pad[3];
+};
+
+// One population as seen by a generation launch.
+struct alignas(16) Segment {
+    const PopParams *prm;
+    uint32_t *geno[2];                // ping-pong genotype buffers [N * 2W]
+    uint32_t *surv[2];                // ping-pong survivor lists [N]
+    unsigned long long *tile_status;  // decoupled look-back words [ntiles]
+    DevState *state;
+    spg_stats *ring;                  // [stats_cap]
+    uint32_t tile_begin;              // first launch-wide tile of this population
+    uint32_t ntiles;
+    uint32_t pad[2];
+};
+
+// Launch-wide counters: dynamic tile tickets and completion count.
+struct alignas(16) LaunchCtl {
+    uint32_t ticket;
+    uint32_t done;
+    uint32_t pad[2];
+};
+
+struct GenArgs {
+    const Segment *segs;
+    uint32_t nsegs;
+    uint32_t total_tiles;
+    LaunchCtl *ctl;
+    uint32_t spin_limit;
+};
+
+using GenKernel = void (*)(GenArgs);
+
+// Kernels of kernels.cu (host-callable handles).
+GenKernel generation_kernel(uint32_t words, uint32_t items);
+bool supported_items(uint32_t items);
+uint32_t tile_size(uint32_t items);
+// Enqueue founders: generation-0 records by Philox draws, survivors = 0..n-1.
+int launch_founders(uint32_t words, uint32_t *geno, uint32_t *surv, uint32_t n, uint32_t key0, uint32_t key1,
+                    uint32_t rep, uint32_t p0_q32, void *stream);
+// Enqueue survivors = 0..n-1 only (caller-supplied founders).
+int launch_iota(uint32_t *surv, uint32_t n, void *stream);
+// Enqueue a state reset: state fields and the ring slot of generation gen+1.
+int launch_set_state(DevState *st, spg_stats *ring, uint32_t cap, uint32_t gen, uint32_t S, uint32_t f,
+                     double R, int32_t status, void *stream);
+// Bounded look-back wait on a status word that is never published, with a
+// small spin limit; writes the status the wait returned to *out (device).
+int launch_lookback_probe(unsigned long long *status_words, int32_t *out, uint32_t spin_limit, void *stream);
+
+}  // namespace spg

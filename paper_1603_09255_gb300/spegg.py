@@ -1,0 +1,276 @@
+"""ctypes binding of libspegg_gb300 (include/spegg.h).
+
+Argument marshalling only: every step of a generation runs in the library's
+CUDA kernels.  PyTorch supplies device memory (through the library's allocator
+hooks, backed by the caching allocator) and the CUDA stream.  There is no CPU
+fallback: if the library or a GPU is missing, these calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libspegg_gb300.so")
+
+OK, EXTINCT = 0, 1
+ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_RANGE, ERR_BUDGET = -1, -2, -3, -4, -5, -6
+CERTAIN = 0xFFFFFFFF
+N_BINS = 4096
+
+STATS_DTYPE = np.dtype([
+    ("gen", "<u4"), ("n", "<u4"), ("s", "<u4"), ("status", "<u4"),
+    ("sum_raw", "<i8"), ("sum_raw2", "<u8"), ("sum_raw_surv", "<i8"),
+    ("min_raw", "<i4"), ("max_raw", "<i4"),
+    ("het", "<u8"), ("allele", "<u8"), ("consumption", "<u8"),
+    ("R", "<f8"), ("f", "<u4"), ("pad", "<u4"),
+])
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class spg_allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class spg_pop_desc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint32), ("n_loci", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+        ("replicate", ctypes.c_uint32), ("effects", ctypes.c_void_p), ("init_genotypes", ctypes.c_void_p),
+        ("p0_q32", ctypes.c_uint32), ("surv_table", ctypes.c_void_p), ("bin_bias", ctypes.c_int32),
+        ("bin_shift", ctypes.c_uint32), ("mu", ctypes.c_double), ("stats_capacity", ctypes.c_uint32),
+    ]
+
+
+class spg_ecology(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_double), ("K", ctypes.c_double), ("R0", ctypes.c_double),
+                ("R_half", ctypes.c_double), ("attack", ctypes.c_void_p)]
+
+
+class spg_state(ctypes.Structure):
+    _fields_ = [("gen", ctypes.c_uint32), ("S", ctypes.c_uint32), ("status", ctypes.c_int32),
+                ("f", ctypes.c_uint32), ("R", ctypes.c_double)]
+
+
+class SpeggError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGNATURES = {
+    "spg_abi_version": ([], ctypes.c_uint32),
+    "spg_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "spg_last_error": ([], ctypes.c_char_p),
+    "spg_create_population": ([ctypes.POINTER(spg_pop_desc), ctypes.POINTER(spg_allocator), ctypes.c_void_p,
+                               ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "spg_set_ecology": ([ctypes.c_void_p, ctypes.POINTER(spg_ecology)], ctypes.c_int),
+    "spg_step_generations": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "spg_read_stats": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
+    "spg_read_genotypes": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "spg_read_survivors": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint32)],
+                           ctypes.c_int),
+    "spg_get_state": ([ctypes.c_void_p, ctypes.POINTER(spg_state)], ctypes.c_int),
+    "spg_checkpoint_size": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "spg_checkpoint": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "spg_restore": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "spg_synchronize": ([ctypes.c_void_p], ctypes.c_int),
+    "spg_destroy": ([ctypes.c_void_p], None),
+    "spg_summarize": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p], None),
+    "spg_debug_lookback_timeout": ([ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "spg_mutation_cdf": ([ctypes.c_double, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_uint32),
+}
+
+
+def lib():
+    """Load libspegg_gb300.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1603_09255_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGNATURES)
+
+
+def check(code: int, where: str) -> int:
+    if code < 0:
+        msg = lib().spg_last_error().decode(errors="replace")
+        raise SpeggError(code, where, msg or lib().spg_status_string(code).decode())
+    return code
+
+
+def status_string(code: int) -> str:
+    return lib().spg_status_string(code).decode()
+
+
+# ------------------------------------------------------------ torch memory
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self, device: Optional[int] = None):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self._live = {}
+        self._alloc = _ALLOC_FN(self._do_alloc)
+        self._free = _FREE_FN(self._do_free)
+        self.struct = spg_allocator(self._alloc, self._free, None)
+
+    def _do_alloc(self, nbytes, ctx):
+        try:
+            t = self._torch.empty(int(nbytes) + 256, dtype=self._torch.uint8, device=self.device)
+        except Exception:
+            return None
+        ptr = t.data_ptr()
+        aligned = (ptr + 255) & ~255
+        self._live[aligned] = t
+        return aligned
+
+    def _do_free(self, ptr, ctx):
+        self._live.pop(ptr, None)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _u32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+class Population:
+    """A population advanced on the GPU (spg_create_population ...)."""
+
+    def __init__(self, n: int, n_loci: int, seed: int, replicate: int, effects, surv_table, bin_bias: int,
+                 bin_shift: int, mu: float, init_genotypes=None, p0_q32: int = 0x80000000,
+                 stats_capacity: int = 0, stream=None, allocator: Optional[TorchAllocator] = None):
+        L = lib()
+        self.n, self.n_loci, self.words = int(n), int(n_loci), int(n_loci) // 32
+        e = np.ascontiguousarray(effects, dtype=np.int16)
+        t = _u32(surv_table)
+        if t.shape != (N_BINS,) or e.shape != (self.n_loci,):
+            raise ValueError("surv_table must have 4096 entries and effects n_loci entries")
+        g = None if init_genotypes is None else _u32(init_genotypes).reshape(-1)
+        d = spg_pop_desc(self.n, self.n_loci, int(seed), int(replicate), e.ctypes.data,
+                         None if g is None else g.ctypes.data, int(p0_q32), t.ctypes.data, int(bin_bias),
+                         int(bin_shift), float(mu), int(stats_capacity))
+        self.allocator = allocator if allocator is not None else TorchAllocator()
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        check(L.spg_create_population(ctypes.byref(d), ctypes.byref(self.allocator.struct), self._stream,
+                                      ctypes.byref(h)), "spg_create_population")
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, w, **kw) -> "Population":
+        p = cls(w.n, w.n_loci, w.seed, w.replicate, w.effects, w.surv_table, w.bias, w.shift, w.mu,
+                w.init_genotypes, w.p0_q32, **kw)
+        if w.has_ecology:
+            p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack)
+        return p
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_ecology(self, r, K, R0, R_half, attack):
+        a = _u32(attack)
+        eco = spg_ecology(float(r), float(K), float(R0), float(R_half), a.ctypes.data)
+        check(lib().spg_set_ecology(self._h, ctypes.byref(eco)), "spg_set_ecology")
+
+    def step(self, n_gen: int) -> None:
+        check(lib().spg_step_generations(self._h, int(n_gen)), "spg_step_generations")
+
+    def read_stats(self, first_gen: int, count: int) -> np.ndarray:
+        out = np.zeros(max(int(count), 1), STATS_DTYPE)
+        check(lib().spg_read_stats(self._h, int(first_gen), int(count), out.ctypes.data), "spg_read_stats")
+        return out[:count]
+
+    def state(self) -> dict:
+        s = spg_state()
+        check(lib().spg_get_state(self._h, ctypes.byref(s)), "spg_get_state")
+        return {"gen": s.gen, "S": s.S, "status": s.status, "R": s.R, "f": s.f}
+
+    def genotypes(self) -> np.ndarray:
+        out = np.zeros((self.n, 2 * self.words), np.uint32)
+        check(lib().spg_read_genotypes(self._h, out.ctypes.data, out.size), "spg_read_genotypes")
+        return out
+
+    def survivors(self) -> np.ndarray:
+        S = ctypes.c_uint32(0)
+        check(lib().spg_read_survivors(self._h, None, 0, ctypes.byref(S)), "spg_read_survivors")
+        out = np.zeros(max(S.value, 1), np.uint32)
+        check(lib().spg_read_survivors(self._h, out.ctypes.data, out.size, ctypes.byref(S)), "spg_read_survivors")
+        return out[:S.value]
+
+    def checkpoint(self) -> bytes:
+        size = ctypes.c_size_t()
+        check(lib().spg_checkpoint_size(self._h, ctypes.byref(size)), "spg_checkpoint_size")
+        buf = ctypes.create_string_buffer(size.value)
+        check(lib().spg_checkpoint(self._h, buf, size.value), "spg_checkpoint")
+        return buf.raw
+
+    def restore(self, blob) -> None:
+        buf = (ctypes.c_char * len(blob)).from_buffer_copy(blob) if isinstance(blob, (bytes, bytearray)) else blob
+        check(lib().spg_restore(self._h, buf, len(blob)), "spg_restore")
+
+    def restore_from(self, ptr: int, nbytes: int) -> None:
+        """Restore from a raw host pointer (e.g. pinned memory)."""
+        check(lib().spg_restore(self._h, ctypes.c_void_p(ptr), int(nbytes)), "spg_restore")
+
+    def synchronize(self) -> None:
+        check(lib().spg_synchronize(self._h), "spg_synchronize")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().spg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def summarize(stats: np.ndarray, n_loci: int) -> np.ndarray:
+    stats = np.ascontiguousarray(stats, dtype=STATS_DTYPE)
+    out = np.zeros((len(stats), 5), np.float32)
+    for i in range(len(stats)):
+        lib().spg_summarize(stats[i:i + 1].ctypes.data, int(n_loci), out[i].ctypes.data)
+    return out
+
+
+def mutation_cdf(mu: float, n_copies: int) -> np.ndarray:
+    out = np.zeros(32, np.uint32)
+    k = lib().spg_mutation_cdf(float(mu), int(n_copies), out.ctypes.data)
+    return out[:k].copy()
+
+
+def debug_lookback_timeout(spin_limit: int) -> int:
+    r = ctypes.c_int32(99)
+    check(lib().spg_debug_lookback_timeout(int(spin_limit), ctypes.byref(r)), "spg_debug_lookback_timeout")
+    return r.value
