@@ -156,7 +156,7 @@ def test_consumer_resource_full_size_graph_path_invariants():
 def test_two_populations_on_one_stream_are_independent():
     sp = spegg()
     w1 = S.single_species(n=4000, n_loci=64, seed=1, mu=1e-3)
-    w2 = S.consumer_resource(n=3000, n_loci=128, seed=2, K=6000.0, mu=1e-3)
+    w2 = S.consumer_resource(n=3000, n_loci=128, seed=2, K=1e5, mu=1e-3)
     g1, g2 = sp.Population.from_workload(w1), sp.Population.from_workload(w2)
     o1, o2 = oracle.OraclePopulation.from_workload(w1), oracle.OraclePopulation.from_workload(w2)
     for _ in range(3):
@@ -169,7 +169,7 @@ def test_two_populations_on_one_stream_are_independent():
 
 def test_checkpoint_resume_is_exact():
     sp = spegg()
-    w = S.consumer_resource(n=5000, n_loci=128, K=1e4, mu=1e-3, seed=8)
+    w = S.consumer_resource(n=5000, n_loci=128, K=1e5, mu=1e-3, seed=8)
     a = sp.Population.from_workload(w, stats_capacity=64)
     a.step(10)
     blob = a.checkpoint()
