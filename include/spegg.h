@@ -103,7 +103,7 @@ typedef struct {
     int32_t bin_bias;               /* phenotype bin map (see above)                    */
     uint32_t bin_shift;             /* 0 .. 31                                          */
     double mu;                      /* per-locus mutation probability, 0 <= mu < 1      */
-    uint32_t stats_capacity;        /* generations kept in the stats ring (0: 1024)     */
+    uint32_t stats_capacity;        /* most recent generations kept readable (0: 1024)  */
 } spg_pop_desc;
 
 /* Consumer-resource ecology (Fig. 1F; S2 "Resource Consumption"): after the

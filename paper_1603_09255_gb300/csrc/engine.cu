@@ -120,7 +120,7 @@ int validate_desc(const spg_pop_desc *d) {
     if (!d->surv_table) return fail(SPG_ERR_INVALID, "surv_table is NULL");
     if (d->bin_shift > 31) return fail(SPG_ERR_INVALID, "bin_shift must be <= 31");
     if (!(d->mu >= 0.0 && d->mu < 1.0)) return fail(SPG_ERR_INVALID, "mu must be in [0, 1)");
-    if (d->stats_capacity == 1) return fail(SPG_ERR_INVALID, "stats_capacity must be 0 or >= 2");
+    if (d->stats_capacity > (1u << 24)) return fail(SPG_ERR_INVALID, "stats_capacity must be <= 2^24");
     return SPG_OK;
 }
 
@@ -140,7 +140,8 @@ int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
     prm.rep = d->replicate;
     prm.has_eco = 0;
     prm.ntiles = (d->n + tile_size(items) - 1) / tile_size(items);
-    prm.stats_cap = d->stats_capacity ? d->stats_capacity : 1024u;
+    // one spare slot: the slot of generation g+1 is reset when g closes
+    prm.stats_cap = (d->stats_capacity ? d->stats_capacity : 1024u) + 1u;
     return SPG_OK;
 }
 
@@ -160,7 +161,7 @@ PopLayout layout_for(uint32_t n, uint32_t words, uint32_t ntiles, uint32_t cap) 
     L.surv0 = take((size_t)n * 4);
     L.surv1 = take((size_t)n * 4);
     L.tiles = take((size_t)ntiles * 8);
-    L.ring = take((size_t)cap * sizeof(spg_stats));
+    L.ring = take((size_t)(cap + 1) * sizeof(spg_stats));
     L.segment = take(sizeof(Segment));
     L.ctl = take(sizeof(LaunchCtl));
     L.total = off;
@@ -341,7 +342,7 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         return rc;
     }
     p->ntiles = p->host_prm->ntiles;
-    p->cap = p->host_prm->stats_cap;
+    p->cap = p->host_prm->stats_cap - 1u;  // generations readable; the ring has cap + 1 slots
     if (alloc) p->alloc.hooks = *alloc;
     if (stream) {
         p->stream = (cudaStream_t)stream;
@@ -363,7 +364,8 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
     p->kern = generation_kernel(p->words, p->items);
     cudaError_t e = cudaMemsetAsync(p->arena + p->L.tiles, 0, (size_t)p->ntiles * 8, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->arena + p->L.ctl, 0, sizeof(LaunchCtl), p->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->arena + p->L.ring, 0, (size_t)p->cap * sizeof(spg_stats), p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(p->arena + p->L.ring, 0, (size_t)(p->cap + 1) * sizeof(spg_stats), p->stream);
     if (e != cudaSuccess) {
         spg_destroy(p);
         return cuda_fail(e, "initialise device memory");
@@ -395,7 +397,7 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
     }
     if (rc == SPG_OK)
         rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
-                              reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap, 0, p->n, kCertain, 0.0,
+                              reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap + 1u, 0, p->n, kCertain, 0.0,
                               SPG_OK, p->stream);
     if (rc == SPG_OK) rc = sync_stream(p);  // caller's founder array is read before returning
     if (rc != SPG_OK) {
@@ -430,7 +432,7 @@ int spg_set_ecology(spg_pop *p, const spg_ecology *eco) {
     rc = upload_params(p);
     if (rc != SPG_OK) return rc;
     rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
-                          reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap, st.gen, st.S,
+                          reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap + 1u, st.gen, st.S,
                           factor_q32_host(eco->R0, eco->R_half), eco->R0, st.status, p->stream);
     return rc;
 }
@@ -452,8 +454,9 @@ int spg_read_stats(spg_pop *p, uint32_t first_gen, uint32_t count, spg_stats *ou
                     (unsigned long long)last, st.gen, p->cap);
     const spg_stats *ring = reinterpret_cast<const spg_stats *>(p->arena + p->L.ring);
     for (uint32_t i = 0; i < count;) {
-        const uint32_t slot = (first_gen - 1 + i) % p->cap;
-        const uint32_t run = std::min(count - i, p->cap - slot);
+        const uint32_t slots = p->cap + 1u;
+        const uint32_t slot = (first_gen - 1 + i) % slots;
+        const uint32_t run = std::min(count - i, slots - slot);
         const cudaError_t e = cudaMemcpy(out + i, ring + slot, run * sizeof(spg_stats), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "read stats");
         i += run;
@@ -572,7 +575,7 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
     if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.tiles, 0, (size_t)p->ntiles * 8);
     if (e != cudaSuccess) return cuda_fail(e, "restore copy");
     rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
-                          reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap, h.gen, h.S, h.f, h.R,
+                          reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap + 1u, h.gen, h.S, h.f, h.R,
                           h.status, p->stream);
     if (rc != SPG_OK) return rc;
     return sync_stream(p);

@@ -64,7 +64,7 @@ def test_invalid_descriptions_are_rejected_before_any_device_work():
     for kw, frag in [(dict(n=0), "n must"), (dict(n_loci=48), "n_loci"), (dict(n_loci=512), "n_loci"),
                      (dict(effects=None), "effects"), (dict(surv_table=None), "surv_table"),
                      (dict(bin_shift=32), "bin_shift"), (dict(mu=1.0), "mu"), (dict(mu=-0.1), "mu"),
-                     (dict(stats_capacity=1), "stats_capacity")]:
+                     (dict(stats_capacity=1 << 25), "stats_capacity")]:
         rc, msg = create(**kw)
         assert rc == spegg.ERR_INVALID and frag in msg, (kw, rc, msg)
     assert L.spg_create_population(None, None, None, None) == spegg.ERR_INVALID

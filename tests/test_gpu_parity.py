@@ -202,6 +202,11 @@ def test_stats_ring_range_and_summaries():
         gpu.read_stats(21, 1)
     sg = gpu.read_stats(13, 8)
     assert sg.tobytes() == so[12:].tobytes()
+    one = sp.Population.from_workload(w, stats_capacity=1)
+    one.step(20)
+    assert one.read_stats(20, 1).tobytes() == so[19:].tobytes()
+    with pytest.raises(sp.SpeggError):
+        one.read_stats(19, 1)
     a = sp.summarize(sg, 64)
     b = oracle.summarize(so[12:], 64)
     assert np.allclose(a, b, rtol=1e-6, atol=0)
