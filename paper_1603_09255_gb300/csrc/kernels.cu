@@ -171,35 +171,48 @@ __device__ __forceinline__ unsigned long long status_word(unsigned long long fla
     return flag | ((unsigned long long)(tag & kTagMask) << 32) | (unsigned long long)v;
 }
 
-// Returns the exclusive prefix of tile t; sets *timed_out if a predecessor's
-// word did not appear within spin_limit polls (the tile then publishes its
-// own count as if it were first, so successors do not wait on it).
+// Exclusive prefix of tile t, computed by one full warp: each round reads the
+// status words of the 32 nearest unread predecessors, waits (bounded) until
+// every one of them up to the nearest inclusive prefix has been published,
+// and adds their values.  Sets *timed_out if the wait exceeded spin_limit
+// polls; the tile then publishes its own count as if it were first, so its
+// successors do not wait on it.
 __device__ uint32_t look_back(unsigned long long *status, uint32_t t, uint32_t count, uint32_t tag,
                               uint32_t spin_limit, bool *timed_out) {
+    const uint32_t lane = threadIdx.x & 31u;
     if (t == 0) {
-        st_relaxed(&status[0], status_word(kFlagPrefix, tag, count));
+        if (lane == 0) st_relaxed(&status[0], status_word(kFlagPrefix, tag, count));
         return 0;
     }
-    st_relaxed(&status[t], status_word(kFlagAgg, tag, count));
+    if (lane == 0) st_relaxed(&status[t], status_word(kFlagAgg, tag, count));
     uint32_t excl = 0, spins = 0;
-    int p = (int)t - 1;
+    long long nearest = (long long)t - 1;  // predecessor read by lane 0 this round
     while (true) {
-        const unsigned long long s = ld_relaxed(&status[p]);
-        const bool ready = (uint32_t)((s >> 32) & kTagMask) == (tag & kTagMask) && (s >> 62) != 0ull;
-        if (!ready) {
+        const long long idx = nearest - (long long)lane;
+        unsigned long long s = 0;
+        uint32_t upto, prefix;
+        while (true) {
+            s = idx >= 0 ? ld_relaxed(&status[idx]) : status_word(kFlagPrefix, tag, 0);
+            const bool ready = (uint32_t)((s >> 32) & kTagMask) == (tag & kTagMask) && (s >> 62) != 0ull;
+            const uint32_t not_ready = __ballot_sync(0xFFFFFFFFu, !ready);
+            prefix = __ballot_sync(0xFFFFFFFFu, ready && (s >> 62) == 2ull);
+            upto = prefix ? (((prefix & (0u - prefix)) << 1) - 1u) : 0xFFFFFFFFu;  // lanes <= nearest prefix
+            if ((not_ready & upto) == 0u) break;
             if (++spins > spin_limit) {
                 *timed_out = true;
-                excl = 0;
-                break;
+                if (lane == 0) st_relaxed(&status[t], status_word(kFlagPrefix, tag, count));
+                return 0;
             }
-            __nanosleep(64);
-            continue;
+            __nanosleep(32);
         }
-        excl += (uint32_t)s;
-        if ((s >> 62) == 2ull) break;
-        --p;
+        uint32_t v = ((upto >> lane) & 1u) ? (uint32_t)s : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        excl += v;
+        if (prefix != 0u) break;
+        nearest -= 32;
     }
-    st_relaxed(&status[t], status_word(kFlagPrefix, tag, excl + count));
+    if (lane == 0) st_relaxed(&status[t], status_word(kFlagPrefix, tag, excl + count));
     return excl;
 }
 
@@ -424,10 +437,11 @@ __global__ void __launch_bounds__(kBlock) k_generation(GenArgs a) {
             }
             if (lane < ITEMS * NW) s_cnt[lane / NW][lane % NW] = incl - v;
             const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            bool timed_out = false;
+            const uint32_t excl = look_back(sg.tile_status, t_local, total, g, a.spin_limit, &timed_out);
             if (lane == 0) {
                 s_total = total;
-                bool timed_out = false;
-                s_excl = look_back(sg.tile_status, t_local, total, g, a.spin_limit, &timed_out);
+                s_excl = excl;
                 if (timed_out)
                     atomicExch(reinterpret_cast<int *>(&sg.state->status), (int)SPG_ERR_TIMEOUT);
             }
@@ -551,10 +565,10 @@ __global__ void k_set_state(DevState *st, spg_stats *ring, uint32_t cap, uint32_
 }
 
 __global__ void k_lookback_probe(unsigned long long *status, int32_t *out, uint32_t spin_limit) {
-    // tile 1 of a generation whose tile 0 never publishes
+    // one warp: tile 1 of a generation whose tile 0 never publishes
     bool timed_out = false;
     (void)look_back(status, 1u, 5u, 7u, spin_limit, &timed_out);
-    *out = timed_out ? SPG_ERR_TIMEOUT : SPG_OK;
+    if (threadIdx.x == 0) *out = timed_out ? SPG_ERR_TIMEOUT : SPG_OK;
 }
 
 }  // namespace
@@ -599,7 +613,7 @@ int launch_set_state(DevState *st, spg_stats *ring, uint32_t cap, uint32_t gen, 
 }
 
 int launch_lookback_probe(unsigned long long *status_words, int32_t *out, uint32_t spin_limit, void *stream) {
-    k_lookback_probe<<<1, 1, 0, (cudaStream_t)stream>>>(status_words, out, spin_limit);
+    k_lookback_probe<<<1, 32, 0, (cudaStream_t)stream>>>(status_words, out, spin_limit);
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
 }
 
