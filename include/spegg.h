@@ -73,7 +73,7 @@ enum spg_status_code {
     SPG_ERR_INVALID = -1,   /* bad argument or description                      */
     SPG_ERR_OOM = -2,       /* device allocation failed                         */
     SPG_ERR_CUDA = -3,      /* a CUDA runtime call failed                       */
-    SPG_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up               */
+    SPG_ERR_TIMEOUT = -4,   /* reserved: a bounded wait gave up                 */
     SPG_ERR_RANGE = -5,     /* requested generations are not in the stats ring  */
     SPG_ERR_BUDGET = -6     /* request exceeds the server's memory budget       */
 };
@@ -139,7 +139,7 @@ typedef struct {
 typedef struct {
     uint32_t gen;      /* generations completed                         */
     uint32_t S;        /* current survivors (parents of the next one)   */
-    int32_t status;    /* SPG_OK, SPG_EXTINCT or SPG_ERR_TIMEOUT        */
+    int32_t status;    /* SPG_OK or SPG_EXTINCT                         */
     uint32_t f;        /* current resource factor                       */
     double R;          /* current resource                              */
 } spg_state;
@@ -159,8 +159,7 @@ int spg_set_ecology(spg_pop *pop, const spg_ecology *eco);
 
 /* Enqueue n_gen generations (Fig. 1 A-F each) on the population's stream and
  * return without waiting.  Generations after an extinction do nothing;
- * extinction and device wait time-outs are reported by spg_get_state and
- * spg_read_stats. */
+ * extinction is reported by spg_get_state and spg_read_stats. */
 int spg_step_generations(spg_pop *pop, uint32_t n_gen);
 
 /* Copy statistics of generations first_gen .. first_gen+count-1 to out
@@ -186,6 +185,12 @@ int spg_checkpoint_size(spg_pop *pop, size_t *bytes);
 int spg_checkpoint(spg_pop *pop, void *host, size_t capacity);
 int spg_restore(spg_pop *pop, const void *host, size_t bytes);
 
+/* Offspring per thread of the generation kernel (1, 2 or 4; default 4 for
+ * L <= 64, 2 for L = 128, 1 for L = 256).  A launch-shape choice only: every
+ * setting gives identical results.  Waits for the stream. */
+int spg_set_tiling(spg_pop *pop, uint32_t items_per_thread);
+int spg_get_tiling(spg_pop *pop, uint32_t *items_per_thread);
+
 /* Wait for all work enqueued on the population's stream. */
 int spg_synchronize(spg_pop *pop);
 
@@ -206,12 +211,6 @@ const char *spg_status_string(int code);
 const char *spg_last_error(void);
 uint32_t spg_abi_version(void);
 
-/* Diagnostic for the bounded device waits (no counterpart in the paper):
- * runs the survivor-compaction look-back of a tile whose predecessor never
- * publishes, with at most spin_limit polls, and stores the status the wait
- * returned (SPG_ERR_TIMEOUT when it gave up) in *result.  Allocates and frees
- * 64 bytes of device memory; waits for the device. */
-int spg_debug_lookback_timeout(uint32_t spin_limit, int32_t *result);
 
 #ifdef __cplusplus
 }

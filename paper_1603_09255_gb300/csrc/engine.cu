@@ -146,7 +146,9 @@ int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
 }
 
 // ------------------------------------------------------------ population
-PopLayout layout_for(uint32_t n, uint32_t words, uint32_t ntiles, uint32_t cap) {
+uint32_t bucket_count(uint32_t n) { return (n + kBucket - 1) / kBucket; }
+
+PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap) {
     PopLayout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -160,26 +162,30 @@ PopLayout layout_for(uint32_t n, uint32_t words, uint32_t ntiles, uint32_t cap) 
     L.geno1 = take((size_t)n * 2 * words * 4);
     L.surv0 = take((size_t)n * 4);
     L.surv1 = take((size_t)n * 4);
-    L.tiles = take((size_t)ntiles * 8);
+    L.alive = take((size_t)nbuckets * kBucketWords * 4);
+    L.buckets = take((size_t)2 * nbuckets * 4);
     L.ring = take((size_t)(cap + 1) * sizeof(spg_stats));
     L.segment = take(sizeof(Segment));
-    L.ctl = take(sizeof(LaunchCtl));
     L.total = off;
     return L;
 }
 
-Segment segment_at(char *base, const PopLayout &L, uint32_t ntiles, uint32_t tile_begin) {
+Segment segment_at(char *base, const PopLayout &L, uint32_t ntiles, uint32_t tile_begin, uint32_t nbuckets,
+                   uint32_t bucket_begin) {
     Segment s{};
     s.prm = reinterpret_cast<const PopParams *>(base + L.params);
     s.geno[0] = reinterpret_cast<uint32_t *>(base + L.geno0);
     s.geno[1] = reinterpret_cast<uint32_t *>(base + L.geno1);
     s.surv[0] = reinterpret_cast<uint32_t *>(base + L.surv0);
     s.surv[1] = reinterpret_cast<uint32_t *>(base + L.surv1);
-    s.tile_status = reinterpret_cast<unsigned long long *>(base + L.tiles);
+    s.alive = reinterpret_cast<uint32_t *>(base + L.alive);
+    s.bucket_sum = reinterpret_cast<uint32_t *>(base + L.buckets);
     s.state = reinterpret_cast<DevState *>(base + L.state);
     s.ring = reinterpret_cast<spg_stats *>(base + L.ring);
     s.tile_begin = tile_begin;
     s.ntiles = ntiles;
+    s.bucket_begin = bucket_begin;
+    s.nbuckets = nbuckets;
     return s;
 }
 
@@ -195,19 +201,20 @@ void GraphChain::reset() {
     length = 0;
 }
 
-// A graph of `len` dependent launches of `kern` with identical arguments.
-int GraphChain::build(GenKernel kern, const GenArgs &args, uint32_t grid, uint32_t len) {
+// A graph of `len` generations: offspring -> compaction -> offspring -> ...
+int GraphChain::build(const GenLaunch &gl, uint32_t len) {
     reset();
     cudaError_t e = cudaGraphCreate(&graph, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
-    GenArgs a = args;
+    GenArgs a = gl.args;
     void *params[] = {&a};
     cudaGraphNode_t prev = nullptr;
-    for (uint32_t i = 0; i < len; ++i) {
+    for (uint32_t i = 0; i < 2 * len; ++i) {
+        const bool off = (i % 2) == 0;
         cudaKernelNodeParams kp{};
-        kp.func = reinterpret_cast<void *>(kern);
-        kp.gridDim = dim3(grid);
-        kp.blockDim = dim3(kBlock);
+        kp.func = reinterpret_cast<void *>(off ? gl.offspring : gl.compact);
+        kp.gridDim = dim3(off ? gl.tiles : gl.buckets);
+        kp.blockDim = dim3(off ? kBlock : kBucketWords);
         kp.sharedMemBytes = 0;
         kp.kernelParams = params;
         cudaGraphNode_t node;
@@ -227,12 +234,18 @@ int GraphChain::build(GenKernel kern, const GenArgs &args, uint32_t grid, uint32
     return SPG_OK;
 }
 
-int enqueue_generations(GenKernel kern, const GenArgs &args, uint32_t grid, uint32_t n_gen, GraphChain &chain,
-                        cudaStream_t stream) {
-    if (n_gen == 0) return SPG_OK;
+int launch_generation(const GenLaunch &gl, cudaStream_t stream) {
+    gl.offspring<<<gl.tiles, kBlock, 0, stream>>>(gl.args);
+    gl.compact<<<gl.buckets, kBucketWords, 0, stream>>>(gl.args);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "generation launch");
+}
+
+int enqueue_generations(const GenLaunch &gl, uint32_t n_gen, GraphChain &chain, cudaStream_t stream) {
+    if (n_gen == 0 || gl.tiles == 0) return SPG_OK;
     if (n_gen >= kGraphChunk) {
         if (!chain.exec) {
-            const int rc = chain.build(kern, args, grid, kGraphChunk);
+            const int rc = chain.build(gl, kGraphChunk);
             if (rc != SPG_OK) return rc;
         }
         for (uint32_t i = 0; i + kGraphChunk <= n_gen; i += kGraphChunk) {
@@ -241,10 +254,10 @@ int enqueue_generations(GenKernel kern, const GenArgs &args, uint32_t grid, uint
         }
     }
     for (uint32_t i = 0; i < n_gen % kGraphChunk; ++i) {
-        kern<<<grid, kBlock, 0, stream>>>(args);
+        const int rc = launch_generation(gl, stream);
+        if (rc != SPG_OK) return rc;
     }
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "generation launch");
+    return SPG_OK;
 }
 
 }  // namespace spg
@@ -261,8 +274,8 @@ struct spg_pop {
     char *arena = nullptr;
     PopLayout L{};
     PopParams *host_prm = nullptr;  // host copy of the parameters
-    GenKernel kern = nullptr;
-    GenArgs args{};
+    uint32_t nbuckets = 0;
+    GenLaunch gl;
     GraphChain chain;
     bool has_eco = false;
     double R0 = 0.0;
@@ -355,22 +368,21 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         }
         p->own_stream = true;
     }
-    p->L = layout_for(p->n, p->words, p->ntiles, p->cap);
+    p->nbuckets = bucket_count(p->n);
+    p->L = layout_for(p->n, p->words, p->nbuckets, p->cap);
     p->arena = static_cast<char *>(p->alloc.alloc(p->L.total, p->stream));
     if (!p->arena) {
         spg_destroy(p);
         return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", p->L.total);
     }
-    p->kern = generation_kernel(p->words, p->items);
-    cudaError_t e = cudaMemsetAsync(p->arena + p->L.tiles, 0, (size_t)p->ntiles * 8, p->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->arena + p->L.ctl, 0, sizeof(LaunchCtl), p->stream);
+    cudaError_t e = cudaMemsetAsync(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4, p->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(p->arena + p->L.ring, 0, (size_t)(p->cap + 1) * sizeof(spg_stats), p->stream);
     if (e != cudaSuccess) {
         spg_destroy(p);
         return cuda_fail(e, "initialise device memory");
     }
-    const Segment seg = segment_at(p->arena, p->L, p->ntiles, 0);
+    const Segment seg = segment_at(p->arena, p->L, p->ntiles, 0, p->nbuckets, 0);
     e = cudaMemcpyAsync(p->arena + p->L.segment, &seg, sizeof seg, cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) {
         spg_destroy(p);
@@ -404,11 +416,14 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         spg_destroy(p);
         return rc == SPG_ERR_CUDA ? rc : fail(rc, "initialise population");
     }
-    p->args.segs = reinterpret_cast<const Segment *>(p->arena + p->L.segment);
-    p->args.nsegs = 1;
-    p->args.total_tiles = p->ntiles;
-    p->args.ctl = reinterpret_cast<LaunchCtl *>(p->arena + p->L.ctl);
-    p->args.spin_limit = kSpinLimit;
+    p->gl.offspring = offspring_kernel(p->words, p->items);
+    p->gl.compact = compact_kernel();
+    p->gl.args.segs = reinterpret_cast<const Segment *>(p->arena + p->L.segment);
+    p->gl.args.nsegs = 1;
+    p->gl.args.total_tiles = p->ntiles;
+    p->gl.args.total_buckets = p->nbuckets;
+    p->gl.tiles = p->ntiles;
+    p->gl.buckets = p->nbuckets;
     *out = p;
     return SPG_OK;
 }
@@ -439,7 +454,7 @@ int spg_set_ecology(spg_pop *p, const spg_ecology *eco) {
 
 int spg_step_generations(spg_pop *p, uint32_t n_gen) {
     if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
-    return enqueue_generations(p->kern, p->args, p->ntiles, n_gen, p->chain, p->stream);
+    return enqueue_generations(p->gl, n_gen, p->chain, p->stream);
 }
 
 int spg_read_stats(spg_pop *p, uint32_t first_gen, uint32_t count, spg_stats *out) {
@@ -570,15 +585,41 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
     if (e == cudaSuccess)
         e = cudaMemcpy(p->arena + ((h.gen & 1u) ? p->L.surv1 : p->L.surv0), src + sizeof h + gbytes,
                        (size_t)h.S * 4, cudaMemcpyHostToDevice);
-    // look-back words of the replaced run could carry the tags of the
+    // per-bucket survivor counts of the replaced run must not leak into the
     // generations about to be replayed
-    if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.tiles, 0, (size_t)p->ntiles * 8);
+    if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4);
     if (e != cudaSuccess) return cuda_fail(e, "restore copy");
     rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
                           reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap + 1u, h.gen, h.S, h.f, h.R,
                           h.status, p->stream);
     if (rc != SPG_OK) return rc;
     return sync_stream(p);
+}
+
+int spg_set_tiling(spg_pop *p, uint32_t items) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    if (!supported_items(items)) return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (got %u)", items);
+    int rc = sync_stream(p);
+    if (rc != SPG_OK) return rc;
+    p->items = items;
+    p->ntiles = (p->n + tile_size(items) - 1) / tile_size(items);
+    p->host_prm->ntiles = p->ntiles;
+    const Segment seg = segment_at(p->arena, p->L, p->ntiles, 0, p->nbuckets, 0);
+    const cudaError_t e = cudaMemcpy(p->arena + p->L.segment, &seg, sizeof seg, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload segment");
+    rc = upload_params(p);
+    if (rc != SPG_OK) return rc;
+    p->gl.offspring = offspring_kernel(p->words, p->items);
+    p->gl.args.total_tiles = p->ntiles;
+    p->gl.tiles = p->ntiles;
+    p->chain.reset();
+    return SPG_OK;
+}
+
+int spg_get_tiling(spg_pop *p, uint32_t *items) {
+    if (!p || !items) return fail(SPG_ERR_INVALID, "NULL argument");
+    *items = p->items;
+    return SPG_OK;
 }
 
 int spg_synchronize(spg_pop *p) {
@@ -608,24 +649,6 @@ void spg_summarize(const spg_stats *st, uint32_t n_loci, float out[5]) {
     out[2] = (float)((double)st->s / n);
     out[3] = (float)((double)st->het / (n * (double)n_loci));
     out[4] = (float)((double)st->allele / (2.0 * n * (double)n_loci));
-}
-
-int spg_debug_lookback_timeout(uint32_t spin_limit, int32_t *result) {
-    if (!result) return fail(SPG_ERR_INVALID, "NULL argument");
-    void *mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, 64);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    e = cudaMemset(mem, 0, 64);
-    int rc = e == cudaSuccess ? SPG_OK : cuda_fail(e, "cudaMemset");
-    if (rc == SPG_OK)
-        rc = launch_lookback_probe(static_cast<unsigned long long *>(mem),
-                                   reinterpret_cast<int32_t *>(static_cast<char *>(mem) + 32), spin_limit, nullptr);
-    if (rc == SPG_OK) {
-        e = cudaMemcpy(result, static_cast<char *>(mem) + 32, 4, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) rc = cuda_fail(e, "read probe result");
-    }
-    cudaFree(mem);
-    return rc;
 }
 
 }  // extern "C"

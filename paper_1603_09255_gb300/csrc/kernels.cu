@@ -1,17 +1,21 @@
 // Device kernels of the per-generation update (sm_103a).
 //
-// One launch advances every population of a launch group by one generation
-// (Fig. 1 A-F of the paper): each block takes a tile of kBlock*ITEMS
-// offspring of one population and, in one pass,
-//   draws both parents from the previous survivors,            (Fig. 1A)
-//   forms the two gametes by crossover masks + mutation XOR,   (Fig. 1B)
-//   sums the additive phenotype with bit-plane popcounts,      (Fig. 1C)
-//   decides survival from the threshold table,                  (Fig. 1D)
-//   writes the survivors' indices in offspring order through a
-//   ballot + block scan + decoupled look-back compaction,      (Fig. 1E)
-// and the last block of a population to finish reduces nothing more than a
-// few scalars: it closes the statistics record and updates the resource
-// (Fig. 1F) in IEEE double with explicitly rounded basic operations.
+// A generation of every population in a launch group is two launches
+// (Fig. 1 A-F of the paper):
+//   k_offspring  one block per tile of kBlock*ITEMS offspring: draws both
+//                parents from the previous survivors (A), forms the gametes
+//                by crossover masks and mutation XOR (B), sums the additive
+//                phenotype with bit-plane popcounts (C), decides survival
+//                from the threshold table (D), and writes the child records,
+//                the alive bitmap, per-bucket survivor counts and the exact
+//                integer statistics;
+//   k_compact    one block per bucket of kBucket offspring: turns the bitmap
+//                into the ordered survivor list (E) with a two-level scan
+//                (earlier buckets' counts + a block scan), and the block that
+//                finishes a population's last bucket closes its generation:
+//                statistics header, resource update in IEEE double with
+//                explicitly rounded basic operations (F), new state.
+// No block ever waits on another block.
 //
 // All random numbers are Philox4x32-10 lanes at counters that name
 // (individual, generation, replicate, purpose<<24 | sub); see spegg.h.
@@ -53,9 +57,6 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     uint32_t v;
@@ -161,61 +162,6 @@ __device__ __forceinline__ int32_t phenotype(const uint32_t (&c)[2 * W], const u
     return raw;
 }
 
-// ------------------------------------------------- decoupled look-back
-// Status word: [63:62] flag (1 aggregate, 2 inclusive prefix), [61:32] the
-// generation tag, [31:0] value.  Words of older generations never match.
-constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPrefix = 2ull << 62;
-constexpr uint32_t kTagMask = 0x3FFFFFFFu;
-
-__device__ __forceinline__ unsigned long long status_word(unsigned long long flag, uint32_t tag, uint32_t v) {
-    return flag | ((unsigned long long)(tag & kTagMask) << 32) | (unsigned long long)v;
-}
-
-// Exclusive prefix of tile t, computed by one full warp: each round reads the
-// status words of the 32 nearest unread predecessors, waits (bounded) until
-// every one of them up to the nearest inclusive prefix has been published,
-// and adds their values.  Sets *timed_out if the wait exceeded spin_limit
-// polls; the tile then publishes its own count as if it were first, so its
-// successors do not wait on it.
-__device__ uint32_t look_back(unsigned long long *status, uint32_t t, uint32_t count, uint32_t tag,
-                              uint32_t spin_limit, bool *timed_out) {
-    const uint32_t lane = threadIdx.x & 31u;
-    if (t == 0) {
-        if (lane == 0) st_relaxed(&status[0], status_word(kFlagPrefix, tag, count));
-        return 0;
-    }
-    if (lane == 0) st_relaxed(&status[t], status_word(kFlagAgg, tag, count));
-    uint32_t excl = 0, spins = 0;
-    long long nearest = (long long)t - 1;  // predecessor read by lane 0 this round
-    while (true) {
-        const long long idx = nearest - (long long)lane;
-        unsigned long long s = 0;
-        uint32_t upto, prefix;
-        while (true) {
-            s = idx >= 0 ? ld_relaxed(&status[idx]) : status_word(kFlagPrefix, tag, 0);
-            const bool ready = (uint32_t)((s >> 32) & kTagMask) == (tag & kTagMask) && (s >> 62) != 0ull;
-            const uint32_t not_ready = __ballot_sync(0xFFFFFFFFu, !ready);
-            prefix = __ballot_sync(0xFFFFFFFFu, ready && (s >> 62) == 2ull);
-            upto = prefix ? (((prefix & (0u - prefix)) << 1) - 1u) : 0xFFFFFFFFu;  // lanes <= nearest prefix
-            if ((not_ready & upto) == 0u) break;
-            if (++spins > spin_limit) {
-                *timed_out = true;
-                if (lane == 0) st_relaxed(&status[t], status_word(kFlagPrefix, tag, count));
-                return 0;
-            }
-            __nanosleep(32);
-        }
-        uint32_t v = ((upto >> lane) & 1u) ? (uint32_t)s : 0u;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        excl += v;
-        if (prefix != 0u) break;
-        nearest -= 32;
-    }
-    if (lane == 0) st_relaxed(&status[t], status_word(kFlagPrefix, tag, excl + count));
-    return excl;
-}
-
 // ------------------------------------------------------ ecology (Fig. 1F)
 __device__ double resource_update(double R, double r, double K, unsigned long long C) {
     const double ratio = __ddiv_rn(R, K);
@@ -286,241 +232,278 @@ __device__ void finalize(DevState *st, spg_stats *ring, const PopParams *P, uint
     st->gen = g;
 }
 
-// --------------------------------------------------- the generation kernel
-template <int W, int ITEMS>
-__global__ void __launch_bounds__(kBlock) k_generation(GenArgs a) {
-    static_assert(ITEMS * (kBlock / 32) <= 32, "scan of per-warp counts uses one warp");
-    constexpr int NW = kBlock / 32;
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_planes[kMaxPlanes * W];
-    __shared__ uint32_t s_cdf[kMaxKmax];
-    __shared__ uint32_t s_cnt[ITEMS][NW];
-    __shared__ uint32_t s_excl;
-    __shared__ long long s_red_ll[3][NW];
-    __shared__ unsigned long long s_red_ull[4][NW];
-    __shared__ uint32_t s_total;
-    __shared__ int s_red_i[2][NW];
+// --------------------------------------------------- warp reductions
+// Exact warp sums of per-lane integers through redux.sync on 16-bit limbs
+// (every limb sum stays far below 2^32).
+__device__ __forceinline__ long long warp_sum_i32(int v) {
+    const uint32_t lo = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)v & 0xFFFFu);
+    const int hi = __reduce_add_sync(0xFFFFFFFFu, v >> 16);
+    return (long long)hi * 65536ll + (long long)lo;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+    unsigned long long r = 0;
+#pragma unroll
+    for (int q = 3; q >= 0; --q)
+        r = (r << 16) + __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(v >> (16 * q)) & 0xFFFFu);
+    return r;
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(&a.ctl->ticket, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-
-    // population of this tile: last segment whose first tile <= tile
-    uint32_t lo = 0, hi = a.nsegs - 1;
+// Segment (population) owning launch-wide unit `u` given each segment's
+// first unit: last segment with first <= u.
+template <typename F>
+__device__ __forceinline__ uint32_t find_segment(const Segment *segs, uint32_t nsegs, uint32_t u, F first) {
+    uint32_t lo = 0, hi = nsegs - 1;
     while (lo < hi) {
         const uint32_t mid = (lo + hi + 1) >> 1;
-        if (a.segs[mid].tile_begin <= tile) lo = mid;
+        if (first(segs[mid]) <= u) lo = mid;
         else hi = mid - 1;
     }
-    const Segment sg = a.segs[lo];
+    return lo;
+}
+
+struct PopNow {
+    uint32_t gen, S, f;
+    bool active;
+};
+
+__device__ __forceinline__ PopNow read_state(const DevState *st) {
+    PopNow s;
+    s.gen = ld_relaxed_u32(&st->gen);
+    s.S = ld_relaxed_u32(&st->S);
+    s.f = ld_relaxed_u32(&st->f);
+    const int32_t status = (int32_t)ld_relaxed_u32(reinterpret_cast<const uint32_t *>(&st->status));
+    s.active = s.S > 0u && status == SPG_OK;
+    return s;
+}
+
+// --------------------------------------------- offspring kernel (Fig. 1A-D)
+// One block per tile of kBlock*ITEMS offspring; offspring j = base +
+// it*kBlock + tid.  Writes the child records, the alive bitmap (word j/32 is
+// the ballot of the warp holding j), the tile's survivor count into its
+// compaction bucket, and the integer statistics.
+template <int W, int ITEMS>
+__global__ void __launch_bounds__(kBlock) k_offspring(GenArgs a) {
+    constexpr int NW = kBlock / 32;
+    constexpr uint32_t TILE = (uint32_t)(kBlock * ITEMS);
+    __shared__ uint32_t s_planes[kMaxPlanes * W];
+    __shared__ uint32_t s_cdf[kMaxKmax];
+    __shared__ long long s_sum[2][NW];
+    __shared__ unsigned long long s_sum64[2][NW];
+    __shared__ uint32_t s_cnt[3][NW];
+    __shared__ int s_mm[2][NW];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t tile = blockIdx.x;
+    const Segment &sg = a.segs[find_segment(a.segs, a.nsegs, tile, [](const Segment &x) { return x.tile_begin; })];
+    const PopNow now = read_state(sg.state);
+    if (!now.active) return;
     const PopParams *__restrict__ P = sg.prm;
     const uint32_t t_local = tile - sg.tile_begin;
+    const uint32_t n = P->n, nplanes = P->nplanes, kmax = P->kmax, rep = P->rep;
+    const uint32_t k0 = P->key0, k1 = P->key1;
+    const int32_t e_min = P->e_min, bias = P->bias;
+    const uint32_t shift = P->shift, S = now.S, f = now.f;
+    const bool has_eco = P->has_eco != 0u;
+    const uint32_t gen = now.gen, g = gen + 1;
+    const uint32_t *__restrict__ par = sg.geno[gen & 1u];
+    uint32_t *__restrict__ chi = sg.geno[(gen + 1u) & 1u];
+    const uint32_t *__restrict__ sin = sg.surv[gen & 1u];
+    const uint32_t base = t_local * TILE;
+    uint32_t *bucket_now = sg.bucket_sum + (g & 1u) * sg.nbuckets;
+    uint32_t *bucket_next = sg.bucket_sum + ((g + 1u) & 1u) * sg.nbuckets;
 
-    const uint32_t gen = ld_relaxed_u32(&sg.state->gen);
-    const uint32_t S = ld_relaxed_u32(&sg.state->S);
-    const uint32_t f = ld_relaxed_u32(&sg.state->f);
-    const int32_t status0 = (int32_t)ld_relaxed_u32(reinterpret_cast<const uint32_t *>(&sg.state->status));
-    const bool active = (S > 0u) && (status0 == SPG_OK) && (t_local < sg.ntiles);
+    for (uint32_t i = tid; i < nplanes * W; i += kBlock) s_planes[i] = P->planes[i];
+    if (tid < kMaxKmax) s_cdf[tid] = tid < kmax ? P->cdf[tid] : 0u;
+    // the bucket this tile opens is cleared for the next generation
+    if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
+    __syncthreads();
 
-    if (active) {
-        const uint32_t n = P->n, nplanes = P->nplanes, kmax = P->kmax, rep = P->rep;
-        const uint32_t k0 = P->key0, k1 = P->key1;
-        const int32_t e_min = P->e_min, bias = P->bias;
-        const uint32_t shift = P->shift;
-        const bool has_eco = P->has_eco != 0u;
-        const uint32_t g = gen + 1;
-        const uint32_t *__restrict__ par = sg.geno[gen & 1u];
-        uint32_t *__restrict__ chi = sg.geno[(gen + 1u) & 1u];
-        const uint32_t *__restrict__ sin = sg.surv[gen & 1u];
-        uint32_t *__restrict__ sout = sg.surv[(gen + 1u) & 1u];
-
-        for (uint32_t i = tid; i < nplanes * W; i += kBlock) s_planes[i] = P->planes[i];
-        if (tid < kMaxKmax) s_cdf[tid] = tid < kmax ? P->cdf[tid] : 0u;
-        __syncthreads();
-
-        const uint32_t base = t_local * (uint32_t)(kBlock * ITEMS);
-
-        // (A) parents: Philox draws, then the survivor-list gathers
-        uint32_t mom[ITEMS], dad[ITEMS], u_surv[ITEMS], u_mut[ITEMS];
+    // (A) parents: Philox draws, then the survivor-list gathers
+    uint32_t mom[ITEMS], dad[ITEMS], u_surv[ITEMS], u_mut[ITEMS];
 #pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            const uint32_t j = base + it * kBlock + tid;
-            mom[it] = dad[it] = u_surv[it] = u_mut[it] = 0u;
-            if (j < n) {
-                const uint4 d = philox(make_uint4(j, g, rep, kMate << 24), k0, k1);
-                mom[it] = __ldg(sin + __umulhi(d.x, S));
-                dad[it] = __ldg(sin + __umulhi(d.y, S));
-                u_surv[it] = d.z;
-                u_mut[it] = d.w;
-            }
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t j = base + it * kBlock + tid;
+        mom[it] = dad[it] = u_surv[it] = u_mut[it] = 0u;
+        if (j < n) {
+            const uint4 d = philox(make_uint4(j, g, rep, kMate << 24), k0, k1);
+            mom[it] = __ldg(sin + __umulhi(d.x, S));
+            dad[it] = __ldg(sin + __umulhi(d.y, S));
+            u_surv[it] = d.z;
+            u_mut[it] = d.w;
         }
-        uint32_t pm[ITEMS][2 * W], pf[ITEMS][2 * W];
+    }
+    uint32_t pm[ITEMS][2 * W], pf[ITEMS][2 * W];
 #pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            const uint32_t j = base + it * kBlock + tid;
-            if (j < n) {
-                load_record<W>(par + (size_t)mom[it] * (2 * W), pm[it]);
-                load_record<W>(par + (size_t)dad[it] * (2 * W), pf[it]);
-            }
-        }
-
-        long long sum_raw = 0, sum_raw_s = 0;
-        unsigned long long sum_raw2 = 0, cons = 0, het_sum = 0, allele_sum = 0;
-        int mn = INT_MAX, mx = INT_MIN;
-        uint32_t alive_bits = 0;
-
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            const uint32_t j = base + it * kBlock + tid;
-            if (j < n) {
-                // (B) gametes: stream q = 2w + parent is lane q%4 of sub q/4
-                uint32_t c[2 * W];
-#pragma unroll
-                for (int q4 = 0; q4 < (2 * W + 3) / 4; ++q4) {
-                    const uint4 d = philox(make_uint4(j, g, rep, (kRecomb << 24) | (uint32_t)q4), k0, k1);
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) {
-                        const int q = 4 * q4 + l;
-                        if (q < 2 * W) {
-                            const int w = q >> 1;
-                            const uint32_t m = lane_of(d, l);
-                            if ((q & 1) == 0) c[w] = (pm[it][w] & ~m) | (pm[it][W + w] & m);
-                            else c[W + w] = (pf[it][w] & ~m) | (pf[it][W + w] & m);
-                        }
-                    }
-                }
-                // (B) mutation count from the CDF, positions on the rare path
-                uint32_t k = 0;
-                for (uint32_t i = 0; i < kmax; ++i) k += (u_mut[it] >= s_cdf[i]) ? 1u : 0u;
-                if (k != 0u) mutate<W>(c, k, j, g, rep, k0, k1);
-                store_record<W>(chi + (size_t)j * (2 * W), c);
-
-                // (C) phenotype, (D) survival
-                uint32_t allele, hz;
-                const int32_t raw = phenotype<W>(c, s_planes, nplanes, e_min, allele, hz);
-                const long long v = (long long)raw + (long long)bias;
-                const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> shift, (long long)(kBins - 1));
-                uint32_t thr = __ldg(&P->table[bin]);
-                if (f != kCertain) thr = __umulhi(thr, f);
-                const bool alive = (thr == kCertain) || (u_surv[it] < thr);
-
-                sum_raw += raw;
-                sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
-                mn = min(mn, raw);
-                mx = max(mx, raw);
-                het_sum += hz;
-                allele_sum += allele;
-                if (alive) {
-                    alive_bits |= 1u << it;
-                    sum_raw_s += raw;
-                    if (has_eco) cons += __ldg(&P->attack[bin]);
-                }
-            }
-        }
-
-        // (E) compaction: per-(item, warp) ballots scanned in offspring order
-        uint32_t bal[ITEMS];
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            bal[it] = __ballot_sync(0xFFFFFFFFu, (alive_bits >> it) & 1u);
-            if (lane == 0) s_cnt[it][warp] = __popc(bal[it]);
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t v = lane < ITEMS * NW ? s_cnt[lane / NW][lane % NW] : 0u;
-            uint32_t incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (lane < ITEMS * NW) s_cnt[lane / NW][lane % NW] = incl - v;
-            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-            bool timed_out = false;
-            const uint32_t excl = look_back(sg.tile_status, t_local, total, g, a.spin_limit, &timed_out);
-            if (lane == 0) {
-                s_total = total;
-                s_excl = excl;
-                if (timed_out)
-                    atomicExch(reinterpret_cast<int *>(&sg.state->status), (int)SPG_ERR_TIMEOUT);
-            }
-        }
-        __syncthreads();
-        const uint32_t lt_mask = (1u << lane) - 1u;
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            if ((alive_bits >> it) & 1u) {
-                const uint32_t j = base + it * kBlock + tid;
-                sout[s_excl + s_cnt[it][warp] + __popc(bal[it] & lt_mask)] = j;
-            }
-        }
-
-        // statistics: warp, then block reduction, then one atomic per field
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sum_raw += __shfl_xor_sync(0xFFFFFFFFu, sum_raw, o);
-            sum_raw_s += __shfl_xor_sync(0xFFFFFFFFu, sum_raw_s, o);
-            sum_raw2 += __shfl_xor_sync(0xFFFFFFFFu, sum_raw2, o);
-            cons += __shfl_xor_sync(0xFFFFFFFFu, cons, o);
-            het_sum += __shfl_xor_sync(0xFFFFFFFFu, het_sum, o);
-            allele_sum += __shfl_xor_sync(0xFFFFFFFFu, allele_sum, o);
-            mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
-            mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-        }
-        if (lane == 0) {
-            s_red_ll[0][warp] = sum_raw;
-            s_red_ll[1][warp] = sum_raw_s;
-            s_red_ull[0][warp] = sum_raw2;
-            s_red_ull[1][warp] = cons;
-            s_red_ull[2][warp] = het_sum;
-            s_red_ull[3][warp] = allele_sum;
-            s_red_i[0][warp] = mn;
-            s_red_i[1][warp] = mx;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            long long a0 = 0, a1 = 0;
-            unsigned long long b0 = 0, b1 = 0, hz = 0, al = 0;
-            int m0 = INT_MAX, m1 = INT_MIN;
-            for (int w = 0; w < NW; ++w) {
-                a0 += s_red_ll[0][w];
-                a1 += s_red_ll[1][w];
-                b0 += s_red_ull[0][w];
-                b1 += s_red_ull[1][w];
-                hz += s_red_ull[2][w];
-                al += s_red_ull[3][w];
-                m0 = min(m0, s_red_i[0][w]);
-                m1 = max(m1, s_red_i[1][w]);
-            }
-            spg_stats *rec = sg.ring + (g - 1) % P->stats_cap;
-            atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_raw), (unsigned long long)a0);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_raw_surv), (unsigned long long)a1);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_raw2), b0);
-            if (b1) atomicAdd(reinterpret_cast<unsigned long long *>(&rec->consumption), b1);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&rec->het), hz);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&rec->allele), al);
-            atomicMin(&rec->min_raw, m0);
-            atomicMax(&rec->max_raw, m1);
-            if (s_total) atomicAdd(&rec->s, s_total);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            const uint32_t d = atomicAdd(&sg.state->done, 1u);
-            if (d == sg.ntiles - 1u) {
-                __threadfence();
-                finalize(sg.state, sg.ring, P, g, f);
-            }
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t j = base + it * kBlock + tid;
+        if (j < n) {
+            load_record<W>(par + (size_t)mom[it] * (2 * W), pm[it]);
+            load_record<W>(par + (size_t)dad[it] * (2 * W), pf[it]);
         }
     }
 
+    int sum_raw = 0, sum_raw_s = 0, mn = INT_MAX, mx = INT_MIN;
+    unsigned long long sum_raw2 = 0, cons = 0;
+    uint32_t het_sum = 0, allele_sum = 0, tile_alive = 0;
+
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t j = base + it * kBlock + tid;
+        bool alive = false;
+        if (j < n) {
+            // (B) gametes: stream q = 2w + parent is lane q%4 of sub q/4
+            uint32_t c[2 * W];
+#pragma unroll
+            for (int q4 = 0; q4 < (2 * W + 3) / 4; ++q4) {
+                const uint4 d = philox(make_uint4(j, g, rep, (kRecomb << 24) | (uint32_t)q4), k0, k1);
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const int q = 4 * q4 + l;
+                    if (q < 2 * W) {
+                        const int w = q >> 1;
+                        const uint32_t m = lane_of(d, l);
+                        if ((q & 1) == 0) c[w] = (pm[it][w] & ~m) | (pm[it][W + w] & m);
+                        else c[W + w] = (pf[it][w] & ~m) | (pf[it][W + w] & m);
+                    }
+                }
+            }
+            // (B) mutation count from the CDF, positions on the rare path
+            uint32_t k = 0;
+            for (uint32_t i = 0; i < kmax; ++i) k += (u_mut[it] >= s_cdf[i]) ? 1u : 0u;
+            if (k != 0u) mutate<W>(c, k, j, g, rep, k0, k1);
+            store_record<W>(chi + (size_t)j * (2 * W), c);
+
+            // (C) phenotype, (D) survival
+            uint32_t allele, hz;
+            const int32_t raw = phenotype<W>(c, s_planes, nplanes, e_min, allele, hz);
+            const long long v = (long long)raw + (long long)bias;
+            const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> shift, (long long)(kBins - 1));
+            uint32_t thr = __ldg(&P->table[bin]);
+            if (f != kCertain) thr = __umulhi(thr, f);
+            alive = (thr == kCertain) || (u_surv[it] < thr);
+
+            sum_raw += raw;
+            sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
+            mn = min(mn, raw);
+            mx = max(mx, raw);
+            het_sum += hz;
+            allele_sum += allele;
+            if (alive) {
+                sum_raw_s += raw;
+                if (has_eco) cons += __ldg(&P->attack[bin]);
+            }
+        }
+        // (E, first half) the alive bitmap: word (base + it*kBlock + 32*warp)/32
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, alive);
+        if (lane == 0) sg.alive[(base >> 5) + it * NW + warp] = bal;
+        tile_alive += __popc(bal);
+    }
+
+    // statistics: exact warp sums, then one atomic per field and block
+    const long long w_raw = warp_sum_i32(sum_raw), w_raw_s = warp_sum_i32(sum_raw_s);
+    const unsigned long long w_raw2 = warp_sum_u64(sum_raw2), w_cons = warp_sum_u64(cons);
+    const uint32_t w_het = __reduce_add_sync(0xFFFFFFFFu, het_sum);
+    const uint32_t w_allele = __reduce_add_sync(0xFFFFFFFFu, allele_sum);
+    const int w_mn = __reduce_min_sync(0xFFFFFFFFu, mn), w_mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if (lane == 0) {
+        s_sum[0][warp] = w_raw;
+        s_sum[1][warp] = w_raw_s;
+        s_sum64[0][warp] = w_raw2;
+        s_sum64[1][warp] = w_cons;
+        s_cnt[0][warp] = w_het;
+        s_cnt[1][warp] = w_allele;
+        s_cnt[2][warp] = tile_alive;
+        s_mm[0][warp] = w_mn;
+        s_mm[1][warp] = w_mx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long a0 = 0, a1 = 0;
+        unsigned long long b0 = 0, b1 = 0, hz = 0, al = 0;
+        uint32_t alive_cnt = 0;
+        int m0 = INT_MAX, m1 = INT_MIN;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            a0 += s_sum[0][w];
+            a1 += s_sum[1][w];
+            b0 += s_sum64[0][w];
+            b1 += s_sum64[1][w];
+            hz += s_cnt[0][w];
+            al += s_cnt[1][w];
+            alive_cnt += s_cnt[2][w];
+            m0 = min(m0, s_mm[0][w]);
+            m1 = max(m1, s_mm[1][w]);
+        }
+        spg_stats *rec = sg.ring + (g - 1) % P->stats_cap;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_raw), (unsigned long long)a0);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_raw_surv), (unsigned long long)a1);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_raw2), b0);
+        if (b1) atomicAdd(reinterpret_cast<unsigned long long *>(&rec->consumption), b1);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->het), hz);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->allele), al);
+        atomicMin(&rec->min_raw, m0);
+        atomicMax(&rec->max_raw, m1);
+        if (alive_cnt) {
+            atomicAdd(&rec->s, alive_cnt);
+            atomicAdd(&bucket_now[base / kBucket], alive_cnt);
+        }
+    }
+}
+
+// ---------------------------------------- compaction kernel (Fig. 1E, 1F)
+// One block of kBucketWords threads per bucket of kBucket offspring: the
+// survivors' indices, in offspring order, at offset (survivors of all earlier
+// buckets) + (block scan of the bitmap words' popcounts).  The block that
+// finishes a population's last bucket closes its generation.
+__global__ void __launch_bounds__(kBucketWords) k_compact(GenArgs a) {
+    constexpr int NW = kBucketWords / 32;
+    __shared__ uint32_t s_warp[NW];
+    __shared__ uint32_t s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t bkt = blockIdx.x;
+    const Segment &sg =
+        a.segs[find_segment(a.segs, a.nsegs, bkt, [](const Segment &x) { return x.bucket_begin; })];
+    const PopNow now = read_state(sg.state);
+    if (!now.active) return;
+    const PopParams *__restrict__ P = sg.prm;
+    const uint32_t b = bkt - sg.bucket_begin;
+    const uint32_t g = now.gen + 1u;
+    const uint32_t valid_words = (P->n + 31u) >> 5;
+    const uint32_t w = b * kBucketWords + tid;
+    const uint32_t bits = w < valid_words ? __ldcg(sg.alive + w) : 0u;
+    const uint32_t cnt = __popc(bits);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    if (warp == 0) {
+        const uint32_t *bs = sg.bucket_sum + (g & 1u) * sg.nbuckets;
+        uint32_t acc = 0;
+        for (uint32_t i = lane; i < b; i += 32) acc += __ldcg(bs + i);
+        acc = __reduce_add_sync(0xFFFFFFFFu, acc);
+        if (lane == 0) s_base = acc;
+    }
+    __syncthreads();
+    uint32_t excl = s_base + incl - cnt;
+    for (int q = 0; q < warp; ++q) excl += s_warp[q];
+    uint32_t *__restrict__ sout = sg.surv[(now.gen + 1u) & 1u];
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t w0 = b * kBucketWords + (uint32_t)warp * 32u;
+    for (int k = 0; k < 32; ++k) {
+        const uint32_t word = __shfl_sync(0xFFFFFFFFu, bits, k);
+        const uint32_t r0 = __shfl_sync(0xFFFFFFFFu, excl, k);
+        if ((word >> lane) & 1u) sout[r0 + __popc(word & lt)] = (w0 + (uint32_t)k) * 32u + (uint32_t)lane;
+    }
+    __syncthreads();
     if (tid == 0) {
         __threadfence();
-        const uint32_t d = atomicAdd(&a.ctl->done, 1u);
-        if (d == a.total_tiles - 1u) {
-            atomicExch(&a.ctl->done, 0u);
-            atomicExch(&a.ctl->ticket, 0u);
+        const uint32_t d = atomicAdd(&sg.state->done, 1u);
+        if (d == sg.nbuckets - 1u) {
+            __threadfence();
+            finalize(sg.state, sg.ring, P, g, now.f);
         }
     }
 }
@@ -564,21 +547,16 @@ __global__ void k_set_state(DevState *st, spg_stats *ring, uint32_t cap, uint32_
     init_record(ring + gen % cap);
 }
 
-__global__ void k_lookback_probe(unsigned long long *status, int32_t *out, uint32_t spin_limit) {
-    // one warp: tile 1 of a generation whose tile 0 never publishes
-    bool timed_out = false;
-    (void)look_back(status, 1u, 5u, 7u, spin_limit, &timed_out);
-    if (threadIdx.x == 0) *out = timed_out ? SPG_ERR_TIMEOUT : SPG_OK;
-}
-
 }  // namespace
 
 bool supported_items(uint32_t items) { return items == 1 || items == 2 || items == 4; }
 uint32_t tile_size(uint32_t items) { return (uint32_t)kBlock * items; }
 
-GenKernel generation_kernel(uint32_t words, uint32_t items) {
+GenKernel compact_kernel() { return &k_compact; }
+
+GenKernel offspring_kernel(uint32_t words, uint32_t items) {
 #define SPG_CASE(Wv, Iv) \
-    if (words == Wv && items == Iv) return &k_generation<Wv, Iv>;
+    if (words == Wv && items == Iv) return &k_offspring<Wv, Iv>;
     SPG_CASE(1, 1) SPG_CASE(1, 2) SPG_CASE(1, 4)
     SPG_CASE(2, 1) SPG_CASE(2, 2) SPG_CASE(2, 4)
     SPG_CASE(4, 1) SPG_CASE(4, 2) SPG_CASE(4, 4)
@@ -609,11 +587,6 @@ int launch_iota(uint32_t *surv, uint32_t n, void *stream) {
 int launch_set_state(DevState *st, spg_stats *ring, uint32_t cap, uint32_t gen, uint32_t S, uint32_t f, double R,
                      int32_t status, void *stream) {
     k_set_state<<<1, 1, 0, (cudaStream_t)stream>>>(st, ring, cap, gen, S, f, R, status);
-    return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
-}
-
-int launch_lookback_probe(unsigned long long *status_words, int32_t *out, uint32_t spin_limit, void *stream) {
-    k_lookback_probe<<<1, 32, 0, (cudaStream_t)stream>>>(status_words, out, spin_limit);
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
 }
 

@@ -13,7 +13,6 @@
 namespace spg {
 
 constexpr uint32_t kGraphChunk = 32;          // generations per cached graph
-constexpr uint32_t kSpinLimit = 1u << 22;     // look-back polls (~64 ns apart) before giving up
 constexpr uint32_t kCheckpointMagic = 0x43475053u;  // "SPGC"
 
 struct CheckpointHeader {
@@ -33,17 +32,26 @@ struct Allocator {
 
 // Byte offsets of one population's buffers inside its arena.
 struct PopLayout {
-    size_t params, state, geno0, geno1, surv0, surv1, tiles, ring, segment, ctl, total;
+    size_t params, state, geno0, geno1, surv0, surv1, alive, buckets, ring, segment, total;
 };
 
-// A cached CUDA graph of dependent generation launches.
+// The two launches of one generation for a launch group.
+struct GenLaunch {
+    GenKernel offspring = nullptr;
+    GenKernel compact = nullptr;
+    GenArgs args{};
+    uint32_t tiles = 0;    // offspring grid
+    uint32_t buckets = 0;  // compaction grid
+};
+
+// A cached CUDA graph of `length` generations (2 dependent launches each).
 struct GraphChain {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint32_t length = 0;
     ~GraphChain();
     void reset();
-    int build(GenKernel kern, const GenArgs &args, uint32_t grid, uint32_t len);
+    int build(const GenLaunch &gl, uint32_t len);
 };
 
 int fail(int code, const char *fmt, ...);
@@ -54,10 +62,12 @@ uint32_t factor_q32_host(double R, double R_half);
 size_t align_up(size_t x, size_t a);
 int validate_desc(const spg_pop_desc *d);
 int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm);
-PopLayout layout_for(uint32_t n, uint32_t words, uint32_t ntiles, uint32_t cap);
-Segment segment_at(char *base, const PopLayout &L, uint32_t ntiles, uint32_t tile_begin);
+PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap);
+Segment segment_at(char *base, const PopLayout &L, uint32_t ntiles, uint32_t tile_begin, uint32_t nbuckets,
+                   uint32_t bucket_begin);
+uint32_t bucket_count(uint32_t n);
 uint32_t default_items(uint32_t words);
-int enqueue_generations(GenKernel kern, const GenArgs &args, uint32_t grid, uint32_t n_gen, GraphChain &chain,
-                        cudaStream_t stream);
+int launch_generation(const GenLaunch &gl, cudaStream_t stream);
+int enqueue_generations(const GenLaunch &gl, uint32_t n_gen, GraphChain &chain, cudaStream_t stream);
 
 }  // namespace spg

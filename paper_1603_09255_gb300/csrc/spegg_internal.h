@@ -14,7 +14,9 @@ constexpr int kMaxKmax = 32;      // entries of the Binomial(2L, mu) CDF table
 constexpr int kMutDraws = 64;     // position draws tried per offspring
 constexpr int kMaxPlanes = 16;    // bit planes of the offset-binary effects
 constexpr int kMaxWords = 8;      // W = L/32 <= 8
-constexpr int kBlock = 256;       // threads per block of the generation kernel
+constexpr int kBlock = 256;       // threads per block of the offspring kernel
+constexpr uint32_t kBucket = 4096;                 // offspring per compaction bucket
+constexpr uint32_t kBucketWords = kBucket / 32;    // bitmap words per bucket = compaction threads
 constexpr uint32_t kCertain = 0xFFFFFFFFu;
 
 // Philox counter word 3 = purpose << 24 | sub
@@ -46,9 +48,9 @@ struct alignas(16) DevState {
     uint32_t gen;     // generations completed
     uint32_t S;       // survivors of generation `gen` (parents of the next)
     uint32_t f;       // resource factor applied to the next generation
-    int32_t status;   // SPG_OK, SPG_EXTINCT, SPG_ERR_TIMEOUT
+    int32_t status;   // SPG_OK or SPG_EXTINCT
     double R;         // resource density
-    uint32_t done;    // tiles of the running generation that have finished
+    uint32_t done;    // compaction buckets of the running generation that have finished
     uint32_t pad[3];
 };
 
@@ -57,33 +59,29 @@ struct alignas(16) Segment {
     const PopParams *prm;
     uint32_t *geno[2];                // ping-pong genotype buffers [N * 2W]
     uint32_t *surv[2];                // ping-pong survivor lists [N]
-    unsigned long long *tile_status;  // decoupled look-back words [ntiles]
+    uint32_t *alive;                  // alive bitmap of the generation being formed [nbuckets * kBucketWords]
+    uint32_t *bucket_sum;             // survivors per bucket, by generation parity [2][nbuckets]
     DevState *state;
     spg_stats *ring;                  // [stats_cap]
     uint32_t tile_begin;              // first launch-wide tile of this population
     uint32_t ntiles;
-    uint32_t pad[2];
-};
-
-// Launch-wide counters: dynamic tile tickets and completion count.
-struct alignas(16) LaunchCtl {
-    uint32_t ticket;
-    uint32_t done;
-    uint32_t pad[2];
+    uint32_t bucket_begin;            // first launch-wide bucket of this population
+    uint32_t nbuckets;
 };
 
 struct GenArgs {
     const Segment *segs;
     uint32_t nsegs;
     uint32_t total_tiles;
-    LaunchCtl *ctl;
-    uint32_t spin_limit;
+    uint32_t total_buckets;
+    uint32_t pad;
 };
 
 using GenKernel = void (*)(GenArgs);
 
 // Kernels of kernels.cu (host-callable handles).
-GenKernel generation_kernel(uint32_t words, uint32_t items);
+GenKernel offspring_kernel(uint32_t words, uint32_t items);
+GenKernel compact_kernel();
 bool supported_items(uint32_t items);
 uint32_t tile_size(uint32_t items);
 // Enqueue founders: generation-0 records by Philox draws, survivors = 0..n-1.
@@ -94,8 +92,5 @@ int launch_iota(uint32_t *surv, uint32_t n, void *stream);
 // Enqueue a state reset: state fields and the ring slot of generation gen+1.
 int launch_set_state(DevState *st, spg_stats *ring, uint32_t cap, uint32_t gen, uint32_t S, uint32_t f,
                      double R, int32_t status, void *stream);
-// Bounded look-back wait on a status word that is never published, with a
-// small spin limit; writes the status the wait returned to *out (device).
-int launch_lookback_probe(unsigned long long *status_words, int32_t *out, uint32_t spin_limit, void *stream);
 
 }  // namespace spg

@@ -85,8 +85,9 @@ _SIGNATURES = {
     "spg_synchronize": ([ctypes.c_void_p], ctypes.c_int),
     "spg_destroy": ([ctypes.c_void_p], None),
     "spg_summarize": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p], None),
-    "spg_debug_lookback_timeout": ([ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "spg_mutation_cdf": ([ctypes.c_double, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_uint32),
+    "spg_set_tiling": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "spg_get_tiling": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
 }
 
 
@@ -241,6 +242,14 @@ class Population:
         """Restore from a raw host pointer (e.g. pinned memory)."""
         check(lib().spg_restore(self._h, ctypes.c_void_p(ptr), int(nbytes)), "spg_restore")
 
+    def set_tiling(self, items_per_thread: int) -> None:
+        check(lib().spg_set_tiling(self._h, int(items_per_thread)), "spg_set_tiling")
+
+    def tiling(self) -> int:
+        v = ctypes.c_uint32()
+        check(lib().spg_get_tiling(self._h, ctypes.byref(v)), "spg_get_tiling")
+        return v.value
+
     def synchronize(self) -> None:
         check(lib().spg_synchronize(self._h), "spg_synchronize")
 
@@ -268,9 +277,3 @@ def mutation_cdf(mu: float, n_copies: int) -> np.ndarray:
     out = np.zeros(32, np.uint32)
     k = lib().spg_mutation_cdf(float(mu), int(n_copies), out.ctypes.data)
     return out[:k].copy()
-
-
-def debug_lookback_timeout(spin_limit: int) -> int:
-    r = ctypes.c_int32(99)
-    check(lib().spg_debug_lookback_timeout(int(spin_limit), ctypes.byref(r)), "spg_debug_lookback_timeout")
-    return r.value

@@ -91,6 +91,21 @@ def test_tile_edges(n, n_loci):
     assert_identical(*run_both(w, 5))
 
 
+@pytest.mark.parametrize("items", [1, 2, 4])
+@pytest.mark.parametrize("n_loci", [32, 64, 128, 256])
+def test_every_tiling_gives_identical_results(items, n_loci):
+    sp = spegg()
+    w = S.consumer_resource(n=9001, n_loci=n_loci, n_gen=6, mu=1e-3, s=1.0, K=2e5, seed=4)
+    orc = oracle.OraclePopulation.from_workload(w)
+    gpu = sp.Population.from_workload(w, stats_capacity=16)
+    gpu.set_tiling(items)
+    assert gpu.tiling() == items
+    gpu.step(3)
+    gpu.set_tiling(1 if items != 1 else 4)
+    gpu.step(3)
+    assert_identical(orc, gpu, orc.step(6), gpu.read_stats(1, 6))
+
+
 @pytest.mark.parametrize("p0", [0.0, 0.3, 0.5])
 def test_founders_by_philox(p0):
     w = S.single_species(n=3000, n_loci=128, n_gen=3, mu=1e-3, seed=2)
@@ -210,12 +225,3 @@ def test_stats_ring_range_and_summaries():
     a = sp.summarize(sg, 64)
     b = oracle.summarize(so[12:], 64)
     assert np.allclose(a, b, rtol=1e-6, atol=0)
-
-
-def test_bounded_wait_reports_timeout():
-    """A look-back whose predecessor never publishes gives up after its poll
-    limit and reports SPG_ERR_TIMEOUT; the context stays usable."""
-    sp = spegg()
-    assert sp.debug_lookback_timeout(2000) == sp.ERR_TIMEOUT
-    w = S.single_species(n=500, n_loci=32)
-    assert_identical(*run_both(w, 3))
