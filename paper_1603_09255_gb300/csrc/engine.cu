@@ -140,8 +140,7 @@ int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
     prm.rep = d->replicate;
     prm.has_eco = 0;
     prm.ntiles = (d->n + tile_size(items) - 1) / tile_size(items);
-    // one spare slot: the slot of generation g+1 is reset when g closes
-    prm.stats_cap = (d->stats_capacity ? d->stats_capacity : 1024u) + 1u;
+    prm.stats_cap = d->stats_capacity ? d->stats_capacity : 1024u;
     return SPG_OK;
 }
 
@@ -158,21 +157,24 @@ PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap
     };
     L.params = take(sizeof(PopParams));
     L.state = take(sizeof(DevState));
+    L.acc = take(sizeof(StatAcc) * kAccCopies);
     L.geno0 = take((size_t)n * 2 * words * 4);
     L.geno1 = take((size_t)n * 2 * words * 4);
     L.surv0 = take((size_t)n * 4);
     L.surv1 = take((size_t)n * 4);
     L.alive = take((size_t)nbuckets * kBucketWords * 4);
     L.buckets = take((size_t)2 * nbuckets * 4);
-    L.ring = take((size_t)(cap + 1) * sizeof(spg_stats));
+    L.ring = take((size_t)cap * sizeof(spg_stats));
     L.segment = take(sizeof(Segment));
     L.total = off;
     return L;
 }
 
-Segment segment_at(char *base, const PopLayout &L, uint32_t ntiles, uint32_t tile_begin, uint32_t nbuckets,
-                   uint32_t bucket_begin) {
+Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, uint32_t tile_begin,
+                   uint32_t nbuckets, uint32_t bucket_begin) {
     Segment s{};
+    s.n = n;
+    s.acc = reinterpret_cast<StatAcc *>(base + L.acc);
     s.prm = reinterpret_cast<const PopParams *>(base + L.params);
     s.geno[0] = reinterpret_cast<uint32_t *>(base + L.geno0);
     s.geno[1] = reinterpret_cast<uint32_t *>(base + L.geno1);
@@ -189,7 +191,7 @@ Segment segment_at(char *base, const PopLayout &L, uint32_t ntiles, uint32_t til
     return s;
 }
 
-uint32_t default_items(uint32_t words) { return words >= 8 ? 1u : words >= 4 ? 2u : 4u; }
+uint32_t default_items(uint32_t words) { return words >= 4 ? 2u : 4u; }
 
 GraphChain::~GraphChain() { reset(); }
 
@@ -212,10 +214,10 @@ int GraphChain::build(const GenLaunch &gl, uint32_t len) {
     for (uint32_t i = 0; i < 2 * len; ++i) {
         const bool off = (i % 2) == 0;
         cudaKernelNodeParams kp{};
-        kp.func = reinterpret_cast<void *>(off ? gl.offspring : gl.compact);
-        kp.gridDim = dim3(off ? gl.tiles : gl.buckets);
+        kp.func = reinterpret_cast<void *>(off ? gl.offspring.fn : gl.compact);
+        kp.gridDim = dim3(off ? gl.blocks : gl.buckets);
         kp.blockDim = dim3(off ? kBlock : kBucketWords);
-        kp.sharedMemBytes = 0;
+        kp.sharedMemBytes = off ? gl.offspring.smem : 0;
         kp.kernelParams = params;
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
@@ -235,14 +237,14 @@ int GraphChain::build(const GenLaunch &gl, uint32_t len) {
 }
 
 int launch_generation(const GenLaunch &gl, cudaStream_t stream) {
-    gl.offspring<<<gl.tiles, kBlock, 0, stream>>>(gl.args);
+    gl.offspring.fn<<<gl.blocks, kBlock, gl.offspring.smem, stream>>>(gl.args);
     gl.compact<<<gl.buckets, kBucketWords, 0, stream>>>(gl.args);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "generation launch");
 }
 
 int enqueue_generations(const GenLaunch &gl, uint32_t n_gen, GraphChain &chain, cudaStream_t stream) {
-    if (n_gen == 0 || gl.tiles == 0) return SPG_OK;
+    if (n_gen == 0 || gl.blocks == 0) return SPG_OK;
     if (n_gen >= kGraphChunk) {
         if (!chain.exec) {
             const int rc = chain.build(gl, kGraphChunk);
@@ -355,7 +357,7 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         return rc;
     }
     p->ntiles = p->host_prm->ntiles;
-    p->cap = p->host_prm->stats_cap - 1u;  // generations readable; the ring has cap + 1 slots
+    p->cap = p->host_prm->stats_cap;
     if (alloc) p->alloc.hooks = *alloc;
     if (stream) {
         p->stream = (cudaStream_t)stream;
@@ -376,13 +378,12 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", p->L.total);
     }
     cudaError_t e = cudaMemsetAsync(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4, p->stream);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(p->arena + p->L.ring, 0, (size_t)(p->cap + 1) * sizeof(spg_stats), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->arena + p->L.ring, 0, (size_t)p->cap * sizeof(spg_stats), p->stream);
     if (e != cudaSuccess) {
         spg_destroy(p);
         return cuda_fail(e, "initialise device memory");
     }
-    const Segment seg = segment_at(p->arena, p->L, p->ntiles, 0, p->nbuckets, 0);
+    const Segment seg = segment_at(p->arena, p->L, p->n, p->ntiles, 0, p->nbuckets, 0);
     e = cudaMemcpyAsync(p->arena + p->L.segment, &seg, sizeof seg, cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) {
         spg_destroy(p);
@@ -409,20 +410,25 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
     }
     if (rc == SPG_OK)
         rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
-                              reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap + 1u, 0, p->n, kCertain, 0.0,
-                              SPG_OK, p->stream);
+                              reinterpret_cast<StatAcc *>(p->arena + p->L.acc), 0, p->n, kCertain, 0.0, SPG_OK,
+                              p->stream);
     if (rc == SPG_OK) rc = sync_stream(p);  // caller's founder array is read before returning
     if (rc != SPG_OK) {
         spg_destroy(p);
         return rc == SPG_ERR_CUDA ? rc : fail(rc, "initialise population");
     }
     p->gl.offspring = offspring_kernel(p->words, p->items);
+    rc = prepare_offspring(p->gl.offspring);
+    if (rc != SPG_OK) {
+        spg_destroy(p);
+        return fail(rc, "offspring kernel setup failed");
+    }
     p->gl.compact = compact_kernel();
     p->gl.args.segs = reinterpret_cast<const Segment *>(p->arena + p->L.segment);
     p->gl.args.nsegs = 1;
     p->gl.args.total_tiles = p->ntiles;
     p->gl.args.total_buckets = p->nbuckets;
-    p->gl.tiles = p->ntiles;
+    p->gl.blocks = std::min(p->ntiles, p->gl.offspring.resident);
     p->gl.buckets = p->nbuckets;
     *out = p;
     return SPG_OK;
@@ -447,7 +453,7 @@ int spg_set_ecology(spg_pop *p, const spg_ecology *eco) {
     rc = upload_params(p);
     if (rc != SPG_OK) return rc;
     rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
-                          reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap + 1u, st.gen, st.S,
+                          reinterpret_cast<StatAcc *>(p->arena + p->L.acc), st.gen, st.S,
                           factor_q32_host(eco->R0, eco->R_half), eco->R0, st.status, p->stream);
     return rc;
 }
@@ -469,7 +475,7 @@ int spg_read_stats(spg_pop *p, uint32_t first_gen, uint32_t count, spg_stats *ou
                     (unsigned long long)last, st.gen, p->cap);
     const spg_stats *ring = reinterpret_cast<const spg_stats *>(p->arena + p->L.ring);
     for (uint32_t i = 0; i < count;) {
-        const uint32_t slots = p->cap + 1u;
+        const uint32_t slots = p->cap;
         const uint32_t slot = (first_gen - 1 + i) % slots;
         const uint32_t run = std::min(count - i, slots - slot);
         const cudaError_t e = cudaMemcpy(out + i, ring + slot, run * sizeof(spg_stats), cudaMemcpyDeviceToHost);
@@ -590,28 +596,32 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
     if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4);
     if (e != cudaSuccess) return cuda_fail(e, "restore copy");
     rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
-                          reinterpret_cast<spg_stats *>(p->arena + p->L.ring), p->cap + 1u, h.gen, h.S, h.f, h.R,
-                          h.status, p->stream);
+                          reinterpret_cast<StatAcc *>(p->arena + p->L.acc), h.gen, h.S, h.f, h.R, h.status,
+                          p->stream);
     if (rc != SPG_OK) return rc;
     return sync_stream(p);
 }
 
 int spg_set_tiling(spg_pop *p, uint32_t items) {
     if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
-    if (!supported_items(items)) return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (got %u)", items);
+    if (!supported_items(p->words, items))
+        return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (1 or 2 for 256 loci); got %u", items);
+    OffspringKernel k = offspring_kernel(p->words, items);
+    int prc = prepare_offspring(k);
+    if (prc != SPG_OK) return fail(prc, "offspring kernel setup failed");
     int rc = sync_stream(p);
     if (rc != SPG_OK) return rc;
     p->items = items;
     p->ntiles = (p->n + tile_size(items) - 1) / tile_size(items);
     p->host_prm->ntiles = p->ntiles;
-    const Segment seg = segment_at(p->arena, p->L, p->ntiles, 0, p->nbuckets, 0);
+    const Segment seg = segment_at(p->arena, p->L, p->n, p->ntiles, 0, p->nbuckets, 0);
     const cudaError_t e = cudaMemcpy(p->arena + p->L.segment, &seg, sizeof seg, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload segment");
     rc = upload_params(p);
     if (rc != SPG_OK) return rc;
-    p->gl.offspring = offspring_kernel(p->words, p->items);
+    p->gl.offspring = k;
     p->gl.args.total_tiles = p->ntiles;
-    p->gl.tiles = p->ntiles;
+    p->gl.blocks = std::min(p->ntiles, k.resident);
     p->chain.reset();
     return SPG_OK;
 }

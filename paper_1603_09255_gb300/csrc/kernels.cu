@@ -2,13 +2,17 @@
 //
 // A generation of every population in a launch group is two launches
 // (Fig. 1 A-F of the paper):
-//   k_offspring  one block per tile of kBlock*ITEMS offspring: draws both
+//   k_offspring  persistent: each resident block walks a contiguous range of
+//                tiles of kBlock*ITEMS offspring.  Per offspring it draws both
 //                parents from the previous survivors (A), forms the gametes
 //                by crossover masks and mutation XOR (B), sums the additive
-//                phenotype with bit-plane popcounts (C), decides survival
-//                from the threshold table (D), and writes the child records,
-//                the alive bitmap, per-bucket survivor counts and the exact
-//                integer statistics;
+//                phenotype with bit-plane popcounts (C) and decides survival
+//                from the threshold table (D); it writes the child records,
+//                the alive bitmap, per-bucket survivor counts and exact
+//                integer statistics.  The parents' survivor indices are
+//                fetched two tiles ahead and their records are staged into
+//                shared memory with cp.async one tile ahead, so the random
+//                gathers overlap the arithmetic of the tile in hand;
 //   k_compact    one block per bucket of kBucket offspring: turns the bitmap
 //                into the ordered survivor list (E) with a two-level scan
 //                (earlier buckets' counts + a block scan), and the block that
@@ -184,61 +188,27 @@ __device__ uint32_t factor_q32(double R, double R_half) {
     return __double2uint_rz(scaled);
 }
 
-__device__ void init_record(spg_stats *rec) {
-    rec->gen = 0;
-    rec->n = 0;
-    rec->s = 0;
-    rec->status = 0;
-    rec->sum_raw = 0;
-    rec->sum_raw2 = 0;
-    rec->sum_raw_surv = 0;
-    rec->min_raw = INT_MAX;
-    rec->max_raw = INT_MIN;
-    rec->het = 0;
-    rec->allele = 0;
-    rec->consumption = 0;
-    rec->R = 0.0;
-    rec->f = 0;
-    rec->pad = 0;
-}
-
-// Close generation g of one population (run by one thread of the block that
-// finished last): statistics header, resource update, new state, next slot.
-__device__ void finalize(DevState *st, spg_stats *ring, const PopParams *P, uint32_t g, uint32_t f_used) {
-    const uint32_t cap = P->stats_cap;
-    spg_stats *rec = ring + (g - 1) % cap;
-    const uint32_t S_new = ld_relaxed_u32(&rec->s);
-    rec->gen = g;
-    rec->n = P->n;
-    uint32_t f_next = f_used;
-    double R = 0.0;
-    if (P->has_eco) {
-        const unsigned long long C =
-            ld_relaxed(reinterpret_cast<const unsigned long long *>(&rec->consumption));
-        R = resource_update(ld_relaxed_f64(&st->R), P->r, P->K, C);
-        f_next = factor_q32(R, P->R_half);
-        st->R = R;
-    }
-    rec->R = R;
-    rec->f = f_next;
-    const int32_t status = (S_new == 0u) ? SPG_EXTINCT : SPG_OK;
-    if (st->status == SPG_OK) st->status = status;
-    rec->status = (uint32_t)status;
-    st->f = f_next;
-    st->S = S_new;
-    init_record(ring + g % cap);
-    st->done = 0;
-    __threadfence();
-    st->gen = g;
+__device__ __forceinline__ void clear_acc(StatAcc *a) {
+    a->s = 0;
+    a->sum_raw = 0;
+    a->sum_raw_s = 0;
+    a->sum_raw2 = 0;
+    a->cons = 0;
+    a->het = 0;
+    a->allele = 0;
+    a->mn = INT_MAX;
+    a->mx = INT_MIN;
 }
 
 // --------------------------------------------------- warp reductions
 // Exact warp sums of per-lane integers through redux.sync on 16-bit limbs
-// (every limb sum stays far below 2^32).
-__device__ __forceinline__ long long warp_sum_i32(int v) {
-    const uint32_t lo = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)v & 0xFFFFu);
-    const int hi = __reduce_add_sync(0xFFFFFFFFu, v >> 16);
-    return (long long)hi * 65536ll + (long long)lo;
+// (every limb sum stays far below 2^32; the top limb carries the sign).
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+    const uint32_t l0 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)v & 0xFFFFu);
+    const uint32_t l1 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(v >> 16) & 0xFFFFu);
+    const uint32_t l2 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(v >> 32) & 0xFFFFu);
+    const int l3 = __reduce_add_sync(0xFFFFFFFFu, (int)(v >> 48));
+    return ((long long)l3 << 48) + ((long long)l2 << 32) + ((long long)l1 << 16) + (long long)l0;
 }
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
     unsigned long long r = 0;
@@ -246,6 +216,76 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     for (int q = 3; q >= 0; --q)
         r = (r << 16) + __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(v >> (16 * q)) & 0xFFFFu);
     return r;
+}
+__device__ __forceinline__ unsigned long long shfl_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// Close generation g of one population; run by one full warp of the block
+// that finished the population's last compaction bucket.  The statistics
+// accumulators (kAccCopies copies) are summed, the resource is updated,
+// the statistics record and the state are written, and the accumulators
+// are reset for the next generation.
+__device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g, uint32_t f_used) {
+    const uint32_t lane = threadIdx.x & 31u;
+    StatAcc mine;
+    clear_acc(&mine);
+    if (lane < (uint32_t)kAccCopies) {
+        StatAcc *src = sg.acc + lane;
+        mine.s = __ldcg(&src->s);
+        mine.sum_raw = __ldcg(&src->sum_raw);
+        mine.sum_raw_s = __ldcg(&src->sum_raw_s);
+        mine.sum_raw2 = __ldcg(&src->sum_raw2);
+        mine.cons = __ldcg(&src->cons);
+        mine.het = __ldcg(&src->het);
+        mine.allele = __ldcg(&src->allele);
+        mine.mn = __ldcg(&src->mn);
+        mine.mx = __ldcg(&src->mx);
+        clear_acc(src);
+    }
+    const unsigned long long S_new = shfl_sum_u64(mine.s);
+    const unsigned long long sum_raw = shfl_sum_u64((unsigned long long)mine.sum_raw);
+    const unsigned long long sum_raw_s = shfl_sum_u64((unsigned long long)mine.sum_raw_s);
+    const unsigned long long sum_raw2 = shfl_sum_u64(mine.sum_raw2);
+    const unsigned long long cons = shfl_sum_u64(mine.cons);
+    const unsigned long long het = shfl_sum_u64(mine.het);
+    const unsigned long long allele = shfl_sum_u64(mine.allele);
+    const int mn = __reduce_min_sync(0xFFFFFFFFu, mine.mn), mx = __reduce_max_sync(0xFFFFFFFFu, mine.mx);
+    if (lane == 0) {
+        DevState *st = sg.state;
+        spg_stats *rec = sg.ring + (g - 1) % P->stats_cap;
+        uint32_t f_next = f_used;
+        double R = 0.0;
+        if (P->has_eco) {
+            R = resource_update(ld_relaxed_f64(&st->R), P->r, P->K, cons);
+            f_next = factor_q32(R, P->R_half);
+            st->R = R;
+        }
+        const int32_t status = (S_new == 0ull) ? SPG_EXTINCT : SPG_OK;
+        rec->gen = g;
+        rec->n = sg.n;
+        rec->s = (uint32_t)S_new;
+        rec->status = (uint32_t)status;
+        rec->sum_raw = (long long)sum_raw;
+        rec->sum_raw2 = sum_raw2;
+        rec->sum_raw_surv = (long long)sum_raw_s;
+        rec->min_raw = mn;
+        rec->max_raw = mx;
+        rec->het = het;
+        rec->allele = allele;
+        rec->consumption = P->has_eco ? cons : 0ull;
+        rec->R = R;
+        rec->f = f_next;
+        rec->pad = 0;
+        if (st->status == SPG_OK) st->status = status;
+        st->f = f_next;
+        st->S = (uint32_t)S_new;
+        st->done = 0;
+        __threadfence();
+        st->gen = g;
+    }
 }
 
 // Segment (population) owning launch-wide unit `u` given each segment's
@@ -276,177 +316,334 @@ __device__ __forceinline__ PopNow read_state(const DevState *st) {
     return s;
 }
 
-// --------------------------------------------- offspring kernel (Fig. 1A-D)
-// One block per tile of kBlock*ITEMS offspring; offspring j = base +
-// it*kBlock + tid.  Writes the child records, the alive bitmap (word j/32 is
-// the ballot of the warp holding j), the tile's survivor count into its
-// compaction bucket, and the integer statistics.
+// ------------------------------------------------------- async copies
+__device__ __forceinline__ void cp_async_16(uint32_t saddr, const void *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(uint32_t saddr, const void *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared-memory staging of parent records: per stage, item, parent (0
+// mother, 1 father) and chunk q, one chunk per thread, chunks of consecutive
+// threads adjacent (conflict-free 8/16-byte accesses).  A thread only ever
+// reads the chunks it copied itself.
 template <int W, int ITEMS>
-__global__ void __launch_bounds__(kBlock) k_offspring(GenArgs a) {
-    constexpr int NW = kBlock / 32;
-    constexpr uint32_t TILE = (uint32_t)(kBlock * ITEMS);
-    __shared__ uint32_t s_planes[kMaxPlanes * W];
-    __shared__ uint32_t s_cdf[kMaxKmax];
-    __shared__ long long s_sum[2][NW];
-    __shared__ unsigned long long s_sum64[2][NW];
-    __shared__ uint32_t s_cnt[3][NW];
-    __shared__ int s_mm[2][NW];
+struct Staging {
+    static constexpr int kChunkBytes = (W == 1) ? 8 : 16;
+    static constexpr int kChunks = (W == 1) ? 1 : W / 2;  // per record
+    static constexpr uint32_t kStageBytes = (uint32_t)ITEMS * 2u * kChunks * kBlock * kChunkBytes;
+    static constexpr uint32_t kBytes = 2u * kStageBytes;
+    __device__ static __forceinline__ uint32_t offset(int stage, int it, int parent, int q, int tid) {
+        return (uint32_t)stage * kStageBytes +
+               ((((uint32_t)it * 2u + (uint32_t)parent) * kChunks + (uint32_t)q) * kBlock + (uint32_t)tid) *
+                   kChunkBytes;
+    }
+};
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t tile = blockIdx.x;
-    const Segment &sg = a.segs[find_segment(a.segs, a.nsegs, tile, [](const Segment &x) { return x.tile_begin; })];
-    const PopNow now = read_state(sg.state);
-    if (!now.active) return;
-    const PopParams *__restrict__ P = sg.prm;
-    const uint32_t t_local = tile - sg.tile_begin;
-    const uint32_t n = P->n, nplanes = P->nplanes, kmax = P->kmax, rep = P->rep;
-    const uint32_t k0 = P->key0, k1 = P->key1;
-    const int32_t e_min = P->e_min, bias = P->bias;
-    const uint32_t shift = P->shift, S = now.S, f = now.f;
-    const bool has_eco = P->has_eco != 0u;
-    const uint32_t gen = now.gen, g = gen + 1;
-    const uint32_t *__restrict__ par = sg.geno[gen & 1u];
-    uint32_t *__restrict__ chi = sg.geno[(gen + 1u) & 1u];
-    const uint32_t *__restrict__ sin = sg.surv[gen & 1u];
-    const uint32_t base = t_local * TILE;
-    uint32_t *bucket_now = sg.bucket_sum + (g & 1u) * sg.nbuckets;
-    uint32_t *bucket_next = sg.bucket_sum + ((g + 1u) & 1u) * sg.nbuckets;
-
-    for (uint32_t i = tid; i < nplanes * W; i += kBlock) s_planes[i] = P->planes[i];
-    if (tid < kMaxKmax) s_cdf[tid] = tid < kmax ? P->cdf[tid] : 0u;
-    // the bucket this tile opens is cleared for the next generation
-    if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
-    __syncthreads();
-
-    // (A) parents: Philox draws, then the survivor-list gathers
+// Parents of one tile: indices into the previous generation and the
+// survival / mutation-count draws of each item.
+template <int ITEMS>
+struct TileDraws {
     uint32_t mom[ITEMS], dad[ITEMS], u_surv[ITEMS], u_mut[ITEMS];
-#pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-        const uint32_t j = base + it * kBlock + tid;
-        mom[it] = dad[it] = u_surv[it] = u_mut[it] = 0u;
-        if (j < n) {
-            const uint4 d = philox(make_uint4(j, g, rep, kMate << 24), k0, k1);
-            mom[it] = __ldg(sin + __umulhi(d.x, S));
-            dad[it] = __ldg(sin + __umulhi(d.y, S));
-            u_surv[it] = d.z;
-            u_mut[it] = d.w;
-        }
-    }
-    uint32_t pm[ITEMS][2 * W], pf[ITEMS][2 * W];
-#pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-        const uint32_t j = base + it * kBlock + tid;
-        if (j < n) {
-            load_record<W>(par + (size_t)mom[it] * (2 * W), pm[it]);
-            load_record<W>(par + (size_t)dad[it] * (2 * W), pf[it]);
-        }
-    }
+};
 
-    int sum_raw = 0, sum_raw_s = 0, mn = INT_MAX, mx = INT_MIN;
+struct SegCtx {
+    const PopParams *P;
+    const uint32_t *par;
+    uint32_t *chi;
+    const uint32_t *sin;
+    uint32_t *alive;
+    uint32_t *bucket_now;
+    uint32_t n, S, f, g, rep, k0, k1, kmax, nplanes, shift;
+    int32_t e_min, bias;
+    bool has_eco;
+};
+
+template <int ITEMS>
+__device__ __forceinline__ void draw_parents(const SegCtx &c, uint32_t base, int tid, TileDraws<ITEMS> &d) {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t j = base + (uint32_t)(it * kBlock + tid);
+        d.mom[it] = d.dad[it] = d.u_surv[it] = d.u_mut[it] = 0u;
+        if (j < c.n) {
+            const uint4 r = philox(make_uint4(j, c.g, c.rep, kMate << 24), c.k0, c.k1);
+            d.mom[it] = __ldg(c.sin + __umulhi(r.x, c.S));
+            d.dad[it] = __ldg(c.sin + __umulhi(r.y, c.S));
+            d.u_surv[it] = r.z;
+            d.u_mut[it] = r.w;
+        }
+    }
+}
+
+template <int W, int ITEMS>
+__device__ __forceinline__ void stage_parents(const SegCtx &c, uint32_t base, int tid, const TileDraws<ITEMS> &d,
+                                              uint32_t s_base, int stage) {
+    using St = Staging<W, ITEMS>;
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t j = base + (uint32_t)(it * kBlock + tid);
+        if (j < c.n) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const uint32_t *src = c.par + (size_t)(p ? d.dad[it] : d.mom[it]) * (2 * W);
+#pragma unroll
+                for (int q = 0; q < St::kChunks; ++q) {
+                    const uint32_t sa = s_base + St::offset(stage, it, p, q, tid);
+                    if constexpr (W == 1) cp_async_8(sa, src);
+                    else cp_async_16(sa, src + 4 * q);
+                }
+            }
+        }
+    }
+    cp_async_commit();
+}
+
+template <int W, int ITEMS>
+__device__ __forceinline__ void read_parent(const unsigned char *s_dyn, int stage, int it, int p, int tid,
+                                            uint32_t (&r)[2 * W]) {
+    using St = Staging<W, ITEMS>;
+    if constexpr (W == 1) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(s_dyn + St::offset(stage, it, p, 0, tid));
+        r[0] = v.x;
+        r[1] = v.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < St::kChunks; ++q) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(s_dyn + St::offset(stage, it, p, q, tid));
+            r[4 * q + 0] = v.x;
+            r[4 * q + 1] = v.y;
+            r[4 * q + 2] = v.z;
+            r[4 * q + 3] = v.w;
+        }
+    }
+}
+
+struct ThreadStats {
+    long long sum_raw = 0, sum_raw_s = 0;
     unsigned long long sum_raw2 = 0, cons = 0;
-    uint32_t het_sum = 0, allele_sum = 0, tile_alive = 0;
+    uint32_t het = 0, allele = 0;
+    int mn = INT_MAX, mx = INT_MIN;
+};
 
+// One tile: gametes (B), phenotype (C), survival (D), bitmap (E, first half).
+template <int W, int ITEMS>
+__device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t base, int tid, int lane, int warp,
+                                                   const unsigned char *s_dyn, int stage, const uint32_t *u_surv,
+                                                   const uint32_t *u_mut, const uint32_t *s_planes,
+                                                   const uint32_t *s_cdf, ThreadStats &ts) {
+    constexpr int NW = kBlock / 32;
+    uint32_t alive_count = 0;  // meaningful in lane 0
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
-        const uint32_t j = base + it * kBlock + tid;
+        const uint32_t j = base + (uint32_t)(it * kBlock + tid);
         bool alive = false;
-        if (j < n) {
+        if (j < c.n) {
+            uint32_t pm[2 * W], pf[2 * W], ch[2 * W];
+            read_parent<W, ITEMS>(s_dyn, stage, it, 0, tid, pm);
+            read_parent<W, ITEMS>(s_dyn, stage, it, 1, tid, pf);
             // (B) gametes: stream q = 2w + parent is lane q%4 of sub q/4
-            uint32_t c[2 * W];
 #pragma unroll
             for (int q4 = 0; q4 < (2 * W + 3) / 4; ++q4) {
-                const uint4 d = philox(make_uint4(j, g, rep, (kRecomb << 24) | (uint32_t)q4), k0, k1);
+                const uint4 d = philox(make_uint4(j, c.g, c.rep, (kRecomb << 24) | (uint32_t)q4), c.k0, c.k1);
 #pragma unroll
                 for (int l = 0; l < 4; ++l) {
                     const int q = 4 * q4 + l;
                     if (q < 2 * W) {
                         const int w = q >> 1;
                         const uint32_t m = lane_of(d, l);
-                        if ((q & 1) == 0) c[w] = (pm[it][w] & ~m) | (pm[it][W + w] & m);
-                        else c[W + w] = (pf[it][w] & ~m) | (pf[it][W + w] & m);
+                        if ((q & 1) == 0) ch[w] = (pm[w] & ~m) | (pm[W + w] & m);
+                        else ch[W + w] = (pf[w] & ~m) | (pf[W + w] & m);
                     }
                 }
             }
             // (B) mutation count from the CDF, positions on the rare path
             uint32_t k = 0;
-            for (uint32_t i = 0; i < kmax; ++i) k += (u_mut[it] >= s_cdf[i]) ? 1u : 0u;
-            if (k != 0u) mutate<W>(c, k, j, g, rep, k0, k1);
-            store_record<W>(chi + (size_t)j * (2 * W), c);
+            for (uint32_t i = 0; i < c.kmax; ++i) k += (u_mut[it] >= s_cdf[i]) ? 1u : 0u;
+            if (k != 0u) mutate<W>(ch, k, j, c.g, c.rep, c.k0, c.k1);
+            store_record<W>(c.chi + (size_t)j * (2 * W), ch);
 
             // (C) phenotype, (D) survival
             uint32_t allele, hz;
-            const int32_t raw = phenotype<W>(c, s_planes, nplanes, e_min, allele, hz);
-            const long long v = (long long)raw + (long long)bias;
-            const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> shift, (long long)(kBins - 1));
-            uint32_t thr = __ldg(&P->table[bin]);
-            if (f != kCertain) thr = __umulhi(thr, f);
+            const int32_t raw = phenotype<W>(ch, s_planes, c.nplanes, c.e_min, allele, hz);
+            const long long v = (long long)raw + (long long)c.bias;
+            const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> c.shift, (long long)(kBins - 1));
+            uint32_t thr = __ldg(&c.P->table[bin]);
+            if (c.f != kCertain) thr = __umulhi(thr, c.f);
             alive = (thr == kCertain) || (u_surv[it] < thr);
 
-            sum_raw += raw;
-            sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
-            mn = min(mn, raw);
-            mx = max(mx, raw);
-            het_sum += hz;
-            allele_sum += allele;
+            ts.sum_raw += raw;
+            ts.sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
+            ts.mn = min(ts.mn, raw);
+            ts.mx = max(ts.mx, raw);
+            ts.het += hz;
+            ts.allele += allele;
             if (alive) {
-                sum_raw_s += raw;
-                if (has_eco) cons += __ldg(&P->attack[bin]);
+                ts.sum_raw_s += raw;
+                if (c.has_eco) ts.cons += __ldg(&c.P->attack[bin]);
             }
         }
-        // (E, first half) the alive bitmap: word (base + it*kBlock + 32*warp)/32
+        // (E, first half) alive bitmap word (base + it*kBlock + 32*warp)/32
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, alive);
-        if (lane == 0) sg.alive[(base >> 5) + it * NW + warp] = bal;
-        tile_alive += __popc(bal);
+        if (lane == 0) c.alive[(base >> 5) + (uint32_t)(it * NW + warp)] = bal;
+        alive_count += __popc(bal);
     }
+    return alive_count;
+}
 
-    // statistics: exact warp sums, then one atomic per field and block
-    const long long w_raw = warp_sum_i32(sum_raw), w_raw_s = warp_sum_i32(sum_raw_s);
-    const unsigned long long w_raw2 = warp_sum_u64(sum_raw2), w_cons = warp_sum_u64(cons);
-    const uint32_t w_het = __reduce_add_sync(0xFFFFFFFFu, het_sum);
-    const uint32_t w_allele = __reduce_add_sync(0xFFFFFFFFu, allele_sum);
-    const int w_mn = __reduce_min_sync(0xFFFFFFFFu, mn), w_mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-    if (lane == 0) {
-        s_sum[0][warp] = w_raw;
-        s_sum[1][warp] = w_raw_s;
-        s_sum64[0][warp] = w_raw2;
-        s_sum64[1][warp] = w_cons;
-        s_cnt[0][warp] = w_het;
-        s_cnt[1][warp] = w_allele;
-        s_cnt[2][warp] = tile_alive;
-        s_mm[0][warp] = w_mn;
-        s_mm[1][warp] = w_mx;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        long long a0 = 0, a1 = 0;
-        unsigned long long b0 = 0, b1 = 0, hz = 0, al = 0;
-        uint32_t alive_cnt = 0;
-        int m0 = INT_MAX, m1 = INT_MIN;
+// --------------------------------------------- offspring kernel (Fig. 1A-D)
+template <int W, int ITEMS>
+__global__ void __launch_bounds__(kBlock) k_offspring(GenArgs a) {
+    constexpr int NW = kBlock / 32;
+    constexpr uint32_t TILE = (uint32_t)(kBlock * ITEMS);
+    static_assert(kBucket % TILE == 0, "tiles must not straddle compaction buckets");
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ uint32_t s_planes[kMaxPlanes * W];
+    __shared__ uint32_t s_cdf[kMaxKmax];
+    __shared__ long long s_ll[2][NW];
+    __shared__ unsigned long long s_ull[2][NW];
+    __shared__ uint32_t s_u32[3][NW];
+    __shared__ int s_mm[2][NW];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(s_dyn);
+    const uint32_t T = a.total_tiles, G = gridDim.x;
+    uint32_t t = (uint32_t)(((unsigned long long)T * blockIdx.x) / G);
+    const uint32_t t_end = (uint32_t)(((unsigned long long)T * (blockIdx.x + 1)) / G);
+    if (t >= t_end) return;
+    uint32_t si = find_segment(a.segs, a.nsegs, t, [](const Segment &x) { return x.tile_begin; });
+
+    while (t < t_end) {
+        const Segment &sg = a.segs[si];
+        const uint32_t seg_end = min(t_end, sg.tile_begin + sg.ntiles);
+        const PopNow now = read_state(sg.state);
+        if (now.active) {
+            SegCtx c;
+            c.P = sg.prm;
+            c.n = sg.n;
+            c.S = now.S;
+            c.f = now.f;
+            c.g = now.gen + 1u;
+            c.par = sg.geno[now.gen & 1u];
+            c.chi = sg.geno[(now.gen + 1u) & 1u];
+            c.sin = sg.surv[now.gen & 1u];
+            c.alive = sg.alive;
+            c.bucket_now = sg.bucket_sum + (c.g & 1u) * sg.nbuckets;
+            uint32_t *bucket_next = sg.bucket_sum + ((c.g + 1u) & 1u) * sg.nbuckets;
+            c.rep = c.P->rep;
+            c.k0 = c.P->key0;
+            c.k1 = c.P->key1;
+            c.kmax = c.P->kmax;
+            c.nplanes = c.P->nplanes;
+            c.shift = c.P->shift;
+            c.e_min = c.P->e_min;
+            c.bias = c.P->bias;
+            c.has_eco = c.P->has_eco != 0u;
+
+            __syncthreads();  // the previous population's tables are no longer read
+            for (uint32_t i = tid; i < c.nplanes * W; i += kBlock) s_planes[i] = c.P->planes[i];
+            if (tid < kMaxKmax) s_cdf[tid] = (uint32_t)tid < c.kmax ? c.P->cdf[tid] : 0u;
+            __syncthreads();
+
+            const uint32_t lt0 = t - sg.tile_begin, lt1 = seg_end - sg.tile_begin;
+            ThreadStats ts;
+            uint32_t warp_alive = 0, bucket_alive = 0, bucket_cur = (lt0 * TILE) / kBucket;
+
+            // software pipeline: draws two tiles ahead, staged records one ahead
+            TileDraws<ITEMS> d1, d2;
+            draw_parents<ITEMS>(c, lt0 * TILE, tid, d1);
+            stage_parents<W, ITEMS>(c, lt0 * TILE, tid, d1, s_base, 0);
+            uint32_t cur_surv[ITEMS], cur_mut[ITEMS];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            a0 += s_sum[0][w];
-            a1 += s_sum[1][w];
-            b0 += s_sum64[0][w];
-            b1 += s_sum64[1][w];
-            hz += s_cnt[0][w];
-            al += s_cnt[1][w];
-            alive_cnt += s_cnt[2][w];
-            m0 = min(m0, s_mm[0][w]);
-            m1 = max(m1, s_mm[1][w]);
+            for (int it = 0; it < ITEMS; ++it) {
+                cur_surv[it] = d1.u_surv[it];
+                cur_mut[it] = d1.u_mut[it];
+            }
+            if (lt0 + 1 < lt1) draw_parents<ITEMS>(c, (lt0 + 1) * TILE, tid, d1);
+            for (uint32_t lt = lt0; lt < lt1; ++lt) {
+                const int stage = (int)((lt - lt0) & 1u);
+                const uint32_t base = lt * TILE;
+                if (lt + 1 < lt1) {
+                    stage_parents<W, ITEMS>(c, base + TILE, tid, d1, s_base, stage ^ 1);
+                    if (lt + 2 < lt1) draw_parents<ITEMS>(c, base + 2 * TILE, tid, d2);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
+                const uint32_t bkt = base / kBucket;
+                if (bkt != bucket_cur) {
+                    if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
+                    bucket_alive = 0;
+                    bucket_cur = bkt;
+                }
+                const uint32_t cnt = offspring_tile<W, ITEMS>(c, base, tid, lane, warp, s_dyn, stage, cur_surv,
+                                                              cur_mut, s_planes, s_cdf, ts);
+                bucket_alive += cnt;
+                warp_alive += cnt;
+#pragma unroll
+                for (int it = 0; it < ITEMS; ++it) {
+                    cur_surv[it] = d1.u_surv[it];
+                    cur_mut[it] = d1.u_mut[it];
+                }
+                d1 = d2;
+            }
+            if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
+
+            // statistics of this block's tiles: exact warp sums, one atomic
+            // per field into one of the population's accumulator copies
+            const long long w_raw = warp_sum_i64(ts.sum_raw), w_raw_s = warp_sum_i64(ts.sum_raw_s);
+            const unsigned long long w_raw2 = warp_sum_u64(ts.sum_raw2), w_cons = warp_sum_u64(ts.cons);
+            const uint32_t w_het = __reduce_add_sync(0xFFFFFFFFu, ts.het);
+            const uint32_t w_allele = __reduce_add_sync(0xFFFFFFFFu, ts.allele);
+            const int w_mn = __reduce_min_sync(0xFFFFFFFFu, ts.mn), w_mx = __reduce_max_sync(0xFFFFFFFFu, ts.mx);
+            if (lane == 0) {
+                s_ll[0][warp] = w_raw;
+                s_ll[1][warp] = w_raw_s;
+                s_ull[0][warp] = w_raw2;
+                s_ull[1][warp] = w_cons;
+                s_u32[0][warp] = w_het;
+                s_u32[1][warp] = w_allele;
+                s_u32[2][warp] = warp_alive;
+                s_mm[0][warp] = w_mn;
+                s_mm[1][warp] = w_mx;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                long long a0 = 0, a1 = 0;
+                unsigned long long b0 = 0, b1 = 0, hz = 0, al = 0, sv = 0;
+                int m0 = INT_MAX, m1 = INT_MIN;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    a0 += s_ll[0][w];
+                    a1 += s_ll[1][w];
+                    b0 += s_ull[0][w];
+                    b1 += s_ull[1][w];
+                    hz += s_u32[0][w];
+                    al += s_u32[1][w];
+                    sv += s_u32[2][w];
+                    m0 = min(m0, s_mm[0][w]);
+                    m1 = max(m1, s_mm[1][w]);
+                }
+                StatAcc *acc = sg.acc + blockIdx.x % kAccCopies;
+                atomicAdd(&acc->s, sv);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&acc->sum_raw), (unsigned long long)a0);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&acc->sum_raw_s), (unsigned long long)a1);
+                atomicAdd(&acc->sum_raw2, b0);
+                if (b1) atomicAdd(&acc->cons, b1);
+                atomicAdd(&acc->het, hz);
+                atomicAdd(&acc->allele, al);
+                atomicMin(&acc->mn, m0);
+                atomicMax(&acc->mx, m1);
+            }
         }
-        spg_stats *rec = sg.ring + (g - 1) % P->stats_cap;
-        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_raw), (unsigned long long)a0);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_raw_surv), (unsigned long long)a1);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_raw2), b0);
-        if (b1) atomicAdd(reinterpret_cast<unsigned long long *>(&rec->consumption), b1);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->het), hz);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->allele), al);
-        atomicMin(&rec->min_raw, m0);
-        atomicMax(&rec->max_raw, m1);
-        if (alive_cnt) {
-            atomicAdd(&rec->s, alive_cnt);
-            atomicAdd(&bucket_now[base / kBucket], alive_cnt);
-        }
+        t = seg_end;
+        ++si;
     }
 }
 
@@ -458,19 +655,24 @@ __global__ void __launch_bounds__(kBlock) k_offspring(GenArgs a) {
 __global__ void __launch_bounds__(kBucketWords) k_compact(GenArgs a) {
     constexpr int NW = kBucketWords / 32;
     __shared__ uint32_t s_warp[NW];
-    __shared__ uint32_t s_base;
+    __shared__ uint32_t s_prev[NW];
+    __shared__ uint32_t s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t bkt = blockIdx.x;
     const Segment &sg =
         a.segs[find_segment(a.segs, a.nsegs, bkt, [](const Segment &x) { return x.bucket_begin; })];
     const PopNow now = read_state(sg.state);
     if (!now.active) return;
-    const PopParams *__restrict__ P = sg.prm;
     const uint32_t b = bkt - sg.bucket_begin;
     const uint32_t g = now.gen + 1u;
-    const uint32_t valid_words = (P->n + 31u) >> 5;
-    const uint32_t w = b * kBucketWords + tid;
+    const uint32_t valid_words = (sg.n + 31u) >> 5;
+    const uint32_t w = b * kBucketWords + (uint32_t)tid;
     const uint32_t bits = w < valid_words ? __ldcg(sg.alive + w) : 0u;
+    // survivors of all earlier buckets, read in parallel by the whole block
+    const uint32_t *bs = sg.bucket_sum + (g & 1u) * sg.nbuckets;
+    uint32_t prev = 0;
+    for (uint32_t i = (uint32_t)tid; i < b; i += kBucketWords) prev += __ldcg(bs + i);
+    prev = __reduce_add_sync(0xFFFFFFFFu, prev);
     const uint32_t cnt = __popc(bits);
     uint32_t incl = cnt;
 #pragma unroll
@@ -479,32 +681,31 @@ __global__ void __launch_bounds__(kBucketWords) k_compact(GenArgs a) {
         if (lane >= o) incl += y;
     }
     if (lane == 31) s_warp[warp] = incl;
-    if (warp == 0) {
-        const uint32_t *bs = sg.bucket_sum + (g & 1u) * sg.nbuckets;
-        uint32_t acc = 0;
-        for (uint32_t i = lane; i < b; i += 32) acc += __ldcg(bs + i);
-        acc = __reduce_add_sync(0xFFFFFFFFu, acc);
-        if (lane == 0) s_base = acc;
-    }
+    if (lane == 0) s_prev[warp] = prev;
     __syncthreads();
-    uint32_t excl = s_base + incl - cnt;
-    for (int q = 0; q < warp; ++q) excl += s_warp[q];
+    uint32_t excl = incl - cnt;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        excl += q < warp ? s_warp[q] : 0u;
+        excl += s_prev[q];
+    }
     uint32_t *__restrict__ sout = sg.surv[(now.gen + 1u) & 1u];
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t w0 = b * kBucketWords + (uint32_t)warp * 32u;
+#pragma unroll 4
     for (int k = 0; k < 32; ++k) {
         const uint32_t word = __shfl_sync(0xFFFFFFFFu, bits, k);
         const uint32_t r0 = __shfl_sync(0xFFFFFFFFu, excl, k);
         if ((word >> lane) & 1u) sout[r0 + __popc(word & lt)] = (w0 + (uint32_t)k) * 32u + (uint32_t)lane;
     }
-    __syncthreads();
     if (tid == 0) {
         __threadfence();
-        const uint32_t d = atomicAdd(&sg.state->done, 1u);
-        if (d == sg.nbuckets - 1u) {
-            __threadfence();
-            finalize(sg.state, sg.ring, P, g, now.f);
-        }
+        s_last = (atomicAdd(&sg.state->done, 1u) == sg.nbuckets - 1u) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last && warp == 0) {
+        __threadfence();
+        finalize_warp(sg, sg.prm, g, now.f);
     }
 }
 
@@ -536,33 +737,65 @@ __global__ void k_iota(uint32_t *__restrict__ surv, uint32_t n) {
     if (i < n) surv[i] = i;
 }
 
-__global__ void k_set_state(DevState *st, spg_stats *ring, uint32_t cap, uint32_t gen, uint32_t S, uint32_t f,
-                            double R, int32_t status) {
-    st->gen = gen;
-    st->S = S;
-    st->f = f;
-    st->status = status;
-    st->R = R;
-    st->done = 0;
-    init_record(ring + gen % cap);
+__global__ void k_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R,
+                            int32_t status) {
+    if (threadIdx.x == 0) {
+        st->gen = gen;
+        st->S = S;
+        st->f = f;
+        st->status = status;
+        st->R = R;
+        st->done = 0;
+    }
+    if (threadIdx.x < (unsigned)kAccCopies) clear_acc(acc + threadIdx.x);
 }
 
 }  // namespace
 
-bool supported_items(uint32_t items) { return items == 1 || items == 2 || items == 4; }
+bool supported_items(uint32_t words, uint32_t items) {
+    if (!(items == 1 || items == 2 || items == 4)) return false;
+    return !(words == 8 && items == 4);
+}
 uint32_t tile_size(uint32_t items) { return (uint32_t)kBlock * items; }
 
 GenKernel compact_kernel() { return &k_compact; }
 
-GenKernel offspring_kernel(uint32_t words, uint32_t items) {
+namespace {
+template <int W, int I>
+OffspringKernel make_offspring() {
+    OffspringKernel k;
+    k.fn = &k_offspring<W, I>;
+    k.smem = Staging<W, I>::kBytes;
+    return k;
+}
+}  // namespace
+
+OffspringKernel offspring_kernel(uint32_t words, uint32_t items) {
 #define SPG_CASE(Wv, Iv) \
-    if (words == Wv && items == Iv) return &k_offspring<Wv, Iv>;
+    if (words == Wv && items == Iv) return make_offspring<Wv, Iv>();
     SPG_CASE(1, 1) SPG_CASE(1, 2) SPG_CASE(1, 4)
     SPG_CASE(2, 1) SPG_CASE(2, 2) SPG_CASE(2, 4)
     SPG_CASE(4, 1) SPG_CASE(4, 2) SPG_CASE(4, 4)
-    SPG_CASE(8, 1) SPG_CASE(8, 2) SPG_CASE(8, 4)
+    SPG_CASE(8, 1) SPG_CASE(8, 2)
 #undef SPG_CASE
-    return nullptr;
+    return OffspringKernel{};
+}
+
+int prepare_offspring(OffspringKernel &k) {
+    if (!k.fn) return SPG_ERR_INVALID;
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k.fn),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+    if (e != cudaSuccess) return SPG_ERR_CUDA;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k.fn), kBlock,
+                                                      k.smem);
+    if (e != cudaSuccess || per_sm <= 0) return SPG_ERR_CUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return SPG_ERR_CUDA;
+    k.resident = (uint32_t)per_sm * (uint32_t)sms;
+    return SPG_OK;
 }
 
 int launch_founders(uint32_t words, uint32_t *geno, uint32_t *surv, uint32_t n, uint32_t key0, uint32_t key1,
@@ -584,9 +817,9 @@ int launch_iota(uint32_t *surv, uint32_t n, void *stream) {
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
 }
 
-int launch_set_state(DevState *st, spg_stats *ring, uint32_t cap, uint32_t gen, uint32_t S, uint32_t f, double R,
-                     int32_t status, void *stream) {
-    k_set_state<<<1, 1, 0, (cudaStream_t)stream>>>(st, ring, cap, gen, S, f, R, status);
+int launch_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,
+                     void *stream) {
+    k_set_state<<<1, 32, 0, (cudaStream_t)stream>>>(st, acc, gen, S, f, R, status);
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
 }
 

@@ -32,15 +32,15 @@ struct Allocator {
 
 // Byte offsets of one population's buffers inside its arena.
 struct PopLayout {
-    size_t params, state, geno0, geno1, surv0, surv1, alive, buckets, ring, segment, total;
+    size_t params, state, acc, geno0, geno1, surv0, surv1, alive, buckets, ring, segment, total;
 };
 
 // The two launches of one generation for a launch group.
 struct GenLaunch {
-    GenKernel offspring = nullptr;
+    OffspringKernel offspring;
     GenKernel compact = nullptr;
     GenArgs args{};
-    uint32_t tiles = 0;    // offspring grid
+    uint32_t blocks = 0;   // offspring grid: min(tiles, resident blocks)
     uint32_t buckets = 0;  // compaction grid
 };
 
@@ -63,8 +63,8 @@ size_t align_up(size_t x, size_t a);
 int validate_desc(const spg_pop_desc *d);
 int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm);
 PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap);
-Segment segment_at(char *base, const PopLayout &L, uint32_t ntiles, uint32_t tile_begin, uint32_t nbuckets,
-                   uint32_t bucket_begin);
+Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, uint32_t tile_begin,
+                   uint32_t nbuckets, uint32_t bucket_begin);
 uint32_t bucket_count(uint32_t n);
 uint32_t default_items(uint32_t words);
 int launch_generation(const GenLaunch &gl, cudaStream_t stream);

@@ -18,6 +18,7 @@ constexpr int kBlock = 256;       // threads per block of the offspring kernel
 constexpr uint32_t kBucket = 4096;                 // offspring per compaction bucket
 constexpr uint32_t kBucketWords = kBucket / 32;    // bitmap words per bucket = compaction threads
 constexpr uint32_t kCertain = 0xFFFFFFFFu;
+constexpr int kAccCopies = 16;    // copies of the statistics accumulators (spread atomics)
 
 // Philox counter word 3 = purpose << 24 | sub
 enum Purpose : uint32_t { kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4 };
@@ -54,6 +55,15 @@ struct alignas(16) DevState {
     uint32_t pad[3];
 };
 
+// Statistics of the generation being formed, accumulated by atomics; each
+// population has kAccCopies copies on separate cache lines.
+struct alignas(128) StatAcc {
+    unsigned long long s;
+    long long sum_raw, sum_raw_s;
+    unsigned long long sum_raw2, cons, het, allele;
+    int mn, mx;
+};
+
 // One population as seen by a generation launch.
 struct alignas(16) Segment {
     const PopParams *prm;
@@ -62,11 +72,14 @@ struct alignas(16) Segment {
     uint32_t *alive;                  // alive bitmap of the generation being formed [nbuckets * kBucketWords]
     uint32_t *bucket_sum;             // survivors per bucket, by generation parity [2][nbuckets]
     DevState *state;
+    StatAcc *acc;                     // [kAccCopies]
     spg_stats *ring;                  // [stats_cap]
+    uint32_t n;                       // offspring per generation
     uint32_t tile_begin;              // first launch-wide tile of this population
     uint32_t ntiles;
     uint32_t bucket_begin;            // first launch-wide bucket of this population
     uint32_t nbuckets;
+    uint32_t pad[3];
 };
 
 struct GenArgs {
@@ -79,18 +92,27 @@ struct GenArgs {
 
 using GenKernel = void (*)(GenArgs);
 
+// The offspring kernel for (W, items): entry, dynamic shared memory, and the
+// number of blocks resident on the device (its persistent grid).
+struct OffspringKernel {
+    GenKernel fn = nullptr;
+    uint32_t smem = 0;
+    uint32_t resident = 0;
+};
+
 // Kernels of kernels.cu (host-callable handles).
-GenKernel offspring_kernel(uint32_t words, uint32_t items);
+OffspringKernel offspring_kernel(uint32_t words, uint32_t items);
+int prepare_offspring(OffspringKernel &k);  // sets the shared-memory limit, fills `resident`
 GenKernel compact_kernel();
-bool supported_items(uint32_t items);
+bool supported_items(uint32_t words, uint32_t items);
 uint32_t tile_size(uint32_t items);
 // Enqueue founders: generation-0 records by Philox draws, survivors = 0..n-1.
 int launch_founders(uint32_t words, uint32_t *geno, uint32_t *surv, uint32_t n, uint32_t key0, uint32_t key1,
                     uint32_t rep, uint32_t p0_q32, void *stream);
 // Enqueue survivors = 0..n-1 only (caller-supplied founders).
 int launch_iota(uint32_t *surv, uint32_t n, void *stream);
-// Enqueue a state reset: state fields and the ring slot of generation gen+1.
-int launch_set_state(DevState *st, spg_stats *ring, uint32_t cap, uint32_t gen, uint32_t S, uint32_t f,
-                     double R, int32_t status, void *stream);
+// Enqueue a state reset: state fields and cleared statistics accumulators.
+int launch_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,
+                     void *stream);
 
 }  // namespace spg
