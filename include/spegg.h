@@ -191,6 +191,60 @@ int spg_restore(spg_pop *pop, const void *host, size_t bytes);
 int spg_set_tiling(spg_pop *pop, uint32_t items_per_thread);
 int spg_get_tiling(spg_pop *pop, uint32_t *items_per_thread);
 
+/* ---- One generation without any device allocation -----------------------
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory: code that runs while a CUDA stream is being
+ * captured into a graph (allocation calls are not permitted there), host
+ * applications whose device memory is owned entirely by another framework's
+ * pool, and real-time or certified loops that forbid allocation after start-up
+ * because an allocation can block or fail at an arbitrary moment.
+ *
+ * It forms generation `generation` of one population from caller-owned device
+ * buffers: `parents` (N * 2W records of generation-1) and `survivors` (their S
+ * ascending survivor indices) in, `children` (N * 2W), `survivors_out`
+ * (capacity N; the first stats->s entries are written) and one statistics
+ * record `stats` out.  The draws, arithmetic and results are those of
+ * spg_step_generations for the same population at the same generation,
+ * without an ecology (the survival factor f is given; R is reported as 0).
+ * All working memory comes from one fixed array inside the library of
+ * SPG_NOALLOC_SCRATCH_BYTES on every device that loads the library, held
+ * until the process exits; it bounds N to SPG_NOALLOC_MAX_N, and larger
+ * populations are rejected with SPG_ERR_INVALID before any device work.
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture begins.
+ * Every call on a device shares the array and finds the previous call's
+ * contents in it (the call re-initialises what must start from zero), so
+ * calls whose work overlaps on the GPU -- on different streams or from
+ * different threads -- race and must be serialised by the caller.
+ * Host inputs (effects, surv_table) are read during the call; the work is
+ * enqueued on `stream` (a cudaStream_t, NULL = the legacy default stream) and
+ * the outputs are valid once it completes.  Returns SPG_OK or a negative
+ * SPG_ERR_* code (spg_last_error() explains it). */
+#define SPG_NOALLOC_MAX_N 4194304u
+#define SPG_NOALLOC_SCRATCH_BYTES 568576u
+
+typedef struct {
+    uint32_t n;                   /* N, 1 .. SPG_NOALLOC_MAX_N                  */
+    uint32_t n_loci;              /* 32, 64, 128 or 256                         */
+    uint64_t seed;
+    uint32_t replicate;
+    uint32_t generation;          /* generation being formed, >= 1              */
+    uint32_t S;                   /* survivors listed in `survivors`, 1 .. N    */
+    uint32_t f;                   /* survival factor, Q32 (0xFFFFFFFF = none)   */
+    const int16_t *effects;       /* host [L]                                   */
+    const uint32_t *surv_table;   /* host [4096]                                */
+    int32_t bin_bias;
+    uint32_t bin_shift;
+    double mu;
+    const uint32_t *parents;      /* device [N * 2W]                            */
+    const uint32_t *survivors;    /* device [S]                                 */
+    uint32_t *children;           /* device [N * 2W], written                   */
+    uint32_t *survivors_out;      /* device [N], first stats->s written         */
+    spg_stats *stats;             /* device, one record written                 */
+} spg_noalloc_generation;
+
+int spg_generation_noalloc(const spg_noalloc_generation *args, void *stream);
+
 /* Wait for all work enqueued on the population's stream. */
 int spg_synchronize(spg_pop *pop);
 

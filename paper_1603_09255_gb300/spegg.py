@@ -52,6 +52,17 @@ class spg_ecology(ctypes.Structure):
                 ("R_half", ctypes.c_double), ("attack", ctypes.c_void_p)]
 
 
+class spg_noalloc_generation(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint32), ("n_loci", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+        ("replicate", ctypes.c_uint32), ("generation", ctypes.c_uint32), ("S", ctypes.c_uint32),
+        ("f", ctypes.c_uint32), ("effects", ctypes.c_void_p), ("surv_table", ctypes.c_void_p),
+        ("bin_bias", ctypes.c_int32), ("bin_shift", ctypes.c_uint32), ("mu", ctypes.c_double),
+        ("parents", ctypes.c_void_p), ("survivors", ctypes.c_void_p), ("children", ctypes.c_void_p),
+        ("survivors_out", ctypes.c_void_p), ("stats", ctypes.c_void_p),
+    ]
+
+
 class spg_state(ctypes.Structure):
     _fields_ = [("gen", ctypes.c_uint32), ("S", ctypes.c_uint32), ("status", ctypes.c_int32),
                 ("f", ctypes.c_uint32), ("R", ctypes.c_double)]
@@ -87,6 +98,7 @@ _SIGNATURES = {
     "spg_summarize": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p], None),
     "spg_mutation_cdf": ([ctypes.c_double, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_uint32),
     "spg_set_tiling": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "spg_generation_noalloc": ([ctypes.POINTER(spg_noalloc_generation), ctypes.c_void_p], ctypes.c_int),
     "spg_get_tiling": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
 }
 
@@ -277,3 +289,9 @@ def mutation_cdf(mu: float, n_copies: int) -> np.ndarray:
     out = np.zeros(32, np.uint32)
     k = lib().spg_mutation_cdf(float(mu), int(n_copies), out.ctypes.data)
     return out[:k].copy()
+
+
+def generation_noalloc(args: spg_noalloc_generation, stream: int = 0) -> None:
+    """One generation on caller-owned device buffers, without any device
+    allocation (spg_generation_noalloc); enqueued on `stream`."""
+    check(lib().spg_generation_noalloc(ctypes.byref(args), ctypes.c_void_p(stream)), "spg_generation_noalloc")
