@@ -425,6 +425,7 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
     }
     p->gl.compact = compact_kernel();
     p->gl.args.segs = reinterpret_cast<const Segment *>(p->arena + p->L.segment);
+    p->gl.args.one = segment_at(p->arena, p->L, p->n, p->ntiles, 0, p->nbuckets, 0);
     p->gl.args.nsegs = 1;
     p->gl.args.total_tiles = p->ntiles;
     p->gl.args.total_buckets = p->nbuckets;
@@ -620,6 +621,7 @@ int spg_set_tiling(spg_pop *p, uint32_t items) {
     rc = upload_params(p);
     if (rc != SPG_OK) return rc;
     p->gl.offspring = k;
+    p->gl.args.one = seg;
     p->gl.args.total_tiles = p->ntiles;
     p->gl.blocks = std::min(p->ntiles, k.resident);
     p->chain.reset();

@@ -30,6 +30,12 @@
 
 #include "spegg_internal.h"
 
+// Minimum resident blocks per SM requested from the compiler for the
+// offspring kernel (a register cap: 65536 / (256 * SPG_MIN_BLOCKS) per thread).
+#ifndef SPG_MIN_BLOCKS
+#define SPG_MIN_BLOCKS 2
+#endif
+
 namespace spg {
 namespace {
 
@@ -57,11 +63,6 @@ __device__ __forceinline__ uint32_t lane_of(const uint4 &d, int lane) {
 }
 
 // ------------------------------------------------- relaxed gpu-scope access
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -141,6 +142,31 @@ __device__ __forceinline__ void mutate(uint32_t (&c)[2 * W], uint32_t k, uint32_
 // Additive phenotype (Fig. 1C, eq. S2-phenval) with effects in offset
 // binary: e_l = e_min + sum_b 2^b * bit_b(e_l - e_min), so
 // raw = e_min * (copies) + sum_b 2^b * popc(plane_b & copies).
+// Words of plane b (W consecutive words, 8-byte aligned for W = 2 and
+// 16-byte aligned for W >= 4) in one or two vector shared-memory loads.
+template <int W>
+__device__ __forceinline__ void plane_words(const uint32_t *s_planes, uint32_t b, uint32_t (&pl)[W]) {
+    if constexpr (W == 1) {
+        pl[0] = s_planes[b];
+    } else if constexpr (W == 2) {
+        const uint2 v = reinterpret_cast<const uint2 *>(s_planes)[b];
+        pl[0] = v.x;
+        pl[1] = v.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q) {
+            const uint4 v = reinterpret_cast<const uint4 *>(s_planes)[b * (W / 4) + q];
+            pl[4 * q + 0] = v.x;
+            pl[4 * q + 1] = v.y;
+            pl[4 * q + 2] = v.z;
+            pl[4 * q + 3] = v.w;
+        }
+    }
+}
+
+// Additive phenotype (Fig. 1C, eq. S2-phenval) with effects in offset
+// binary: e_l = e_min + sum_b 2^b * bit_b(e_l - e_min), so
+// raw = e_min * (copies) + sum_b 2^b * popc(plane_b & copies).
 template <int W>
 __device__ __forceinline__ int32_t phenotype(const uint32_t (&c)[2 * W], const uint32_t *s_planes,
                                              uint32_t nplanes, int32_t e_min, uint32_t &allele,
@@ -152,13 +178,13 @@ __device__ __forceinline__ int32_t phenotype(const uint32_t (&c)[2 * W], const u
         hz += __popc(c[w] ^ c[W + w]);
     }
     int32_t raw = e_min * (int32_t)total;
+#pragma unroll 2
     for (uint32_t b = 0; b < nplanes; ++b) {
+        uint32_t pl[W];
+        plane_words<W>(s_planes, b, pl);
         int32_t cnt = 0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const uint32_t pl = s_planes[b * W + w];
-            cnt += __popc(pl & c[w]) + __popc(pl & c[W + w]);
-        }
+        for (int w = 0; w < W; ++w) cnt += __popc(pl[w] & c[w]) + __popc(pl[w] & c[W + w]);
         raw += cnt << b;
     }
     allele = total;
@@ -283,7 +309,6 @@ __device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g,
         st->f = f_next;
         st->S = (uint32_t)S_new;
         st->done = 0;
-        __threadfence();
         st->gen = g;
     }
 }
@@ -498,12 +523,12 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
 
 // --------------------------------------------- offspring kernel (Fig. 1A-D)
 template <int W, int ITEMS>
-__global__ void __launch_bounds__(kBlock) k_offspring(GenArgs a) {
+__global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __grid_constant__ GenArgs a) {
     constexpr int NW = kBlock / 32;
     constexpr uint32_t TILE = (uint32_t)(kBlock * ITEMS);
     static_assert(kBucket % TILE == 0, "tiles must not straddle compaction buckets");
     extern __shared__ __align__(16) unsigned char s_dyn[];
-    __shared__ uint32_t s_planes[kMaxPlanes * W];
+    __shared__ __align__(16) uint32_t s_planes[kMaxPlanes * W];
     __shared__ uint32_t s_cdf[kMaxKmax];
     __shared__ long long s_ll[2][NW];
     __shared__ unsigned long long s_ull[2][NW];
@@ -516,10 +541,10 @@ __global__ void __launch_bounds__(kBlock) k_offspring(GenArgs a) {
     uint32_t t = (uint32_t)(((unsigned long long)T * blockIdx.x) / G);
     const uint32_t t_end = (uint32_t)(((unsigned long long)T * (blockIdx.x + 1)) / G);
     if (t >= t_end) return;
-    uint32_t si = find_segment(a.segs, a.nsegs, t, [](const Segment &x) { return x.tile_begin; });
+    uint32_t si = a.nsegs == 1u ? 0u : find_segment(a.segs, a.nsegs, t, [](const Segment &x) { return x.tile_begin; });
 
     while (t < t_end) {
-        const Segment &sg = a.segs[si];
+        const Segment &sg = a.nsegs == 1u ? a.one : a.segs[si];
         const uint32_t seg_end = min(t_end, sg.tile_begin + sg.ntiles);
         const PopNow now = read_state(sg.state);
         if (now.active) {
@@ -651,28 +676,27 @@ __global__ void __launch_bounds__(kBlock) k_offspring(GenArgs a) {
 // One block of kBucketWords threads per bucket of kBucket offspring: the
 // survivors' indices, in offspring order, at offset (survivors of all earlier
 // buckets) + (block scan of the bitmap words' popcounts).  The block that
-// finishes a population's last bucket closes its generation.
-__global__ void __launch_bounds__(kBucketWords) k_compact(GenArgs a) {
+// finishes a population's last bucket closes its generation.  Every load that
+// does not depend on the population state is issued together with it (both
+// parities of the bucket counts are summed; the state picks one).
+__device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
     constexpr int NW = kBucketWords / 32;
     __shared__ uint32_t s_warp[NW];
     __shared__ uint32_t s_prev[NW];
     __shared__ uint32_t s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t bkt = blockIdx.x;
-    const Segment &sg =
-        a.segs[find_segment(a.segs, a.nsegs, bkt, [](const Segment &x) { return x.bucket_begin; })];
-    const PopNow now = read_state(sg.state);
-    if (!now.active) return;
-    const uint32_t b = bkt - sg.bucket_begin;
-    const uint32_t g = now.gen + 1u;
     const uint32_t valid_words = (sg.n + 31u) >> 5;
     const uint32_t w = b * kBucketWords + (uint32_t)tid;
     const uint32_t bits = w < valid_words ? __ldcg(sg.alive + w) : 0u;
-    // survivors of all earlier buckets, read in parallel by the whole block
-    const uint32_t *bs = sg.bucket_sum + (g & 1u) * sg.nbuckets;
-    uint32_t prev = 0;
-    for (uint32_t i = (uint32_t)tid; i < b; i += kBucketWords) prev += __ldcg(bs + i);
-    prev = __reduce_add_sync(0xFFFFFFFFu, prev);
+    uint32_t prev0 = 0, prev1 = 0;
+    for (uint32_t i = (uint32_t)tid; i < b; i += kBucketWords) {
+        prev0 += __ldcg(sg.bucket_sum + i);
+        prev1 += __ldcg(sg.bucket_sum + sg.nbuckets + i);
+    }
+    const PopNow now = read_state(sg.state);
+    if (!now.active) return;
+    const uint32_t g = now.gen + 1u;
+    const uint32_t prev = __reduce_add_sync(0xFFFFFFFFu, (g & 1u) ? prev1 : prev0);
     const uint32_t cnt = __popc(bits);
     uint32_t incl = cnt;
 #pragma unroll
@@ -698,14 +722,21 @@ __global__ void __launch_bounds__(kBucketWords) k_compact(GenArgs a) {
         const uint32_t r0 = __shfl_sync(0xFFFFFFFFu, excl, k);
         if ((word >> lane) & 1u) sout[r0 + __popc(word & lt)] = (w0 + (uint32_t)k) * 32u + (uint32_t)lane;
     }
-    if (tid == 0) {
-        __threadfence();
-        s_last = (atomicAdd(&sg.state->done, 1u) == sg.nbuckets - 1u) ? 1u : 0u;
-    }
+    // every block has read the state by now (its values fed the stores
+    // above), so the last one may rewrite it
+    if (tid == 0) s_last = (atomicAdd(&sg.state->done, 1u) == sg.nbuckets - 1u) ? 1u : 0u;
     __syncthreads();
-    if (s_last && warp == 0) {
-        __threadfence();
-        finalize_warp(sg, sg.prm, g, now.f);
+    if (s_last && warp == 0) finalize_warp(sg, sg.prm, g, now.f);
+}
+
+__global__ void __launch_bounds__(kBucketWords) k_compact(const __grid_constant__ GenArgs a) {
+    const uint32_t bkt = blockIdx.x;
+    if (a.nsegs == 1u) {
+        compact_bucket(a.one, bkt);
+    } else {
+        const Segment &sg =
+            a.segs[find_segment(a.segs, a.nsegs, bkt, [](const Segment &x) { return x.bucket_begin; })];
+        compact_bucket(sg, bkt - sg.bucket_begin);
     }
 }
 

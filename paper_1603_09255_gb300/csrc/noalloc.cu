@@ -141,6 +141,7 @@ extern "C" int spg_generation_noalloc(const spg_noalloc_generation *a, void *str
     gl.compact = compact_kernel();
     gl.args.segs = reinterpret_cast<const Segment *>(scratch + kOffSegment);
     gl.args.nsegs = 1;
+    gl.args.one = seg;
     gl.args.total_tiles = ntiles;
     gl.args.total_buckets = nbuckets;
     gl.blocks = std::min(ntiles, k.resident);

@@ -83,11 +83,12 @@ struct alignas(16) Segment {
 };
 
 struct GenArgs {
-    const Segment *segs;
+    const Segment *segs;   // device array of nsegs segments (used when nsegs > 1)
     uint32_t nsegs;
     uint32_t total_tiles;
     uint32_t total_buckets;
     uint32_t pad;
+    Segment one;           // the segment itself when nsegs == 1 (read from kernel parameters)
 };
 
 using GenKernel = void (*)(GenArgs);
