@@ -191,6 +191,39 @@ int spg_restore(spg_pop *pop, const void *host, size_t bytes);
 int spg_set_tiling(spg_pop *pop, uint32_t items_per_thread);
 int spg_get_tiling(spg_pop *pop, uint32_t *items_per_thread);
 
+/* ---- Batched replicates ---------------------------------------------------
+ * Many independent populations advanced by shared launches: the flattened
+ * loop over replicates of the paper's Fig. S5 B.  Members are grouped by
+ * locus count; each generation is one offspring launch and one compaction
+ * launch per group, groups run as independent branches of one cached CUDA
+ * graph.  Every member keeps its own parameters, state, buffers and
+ * statistics ring, and its results are identical to the same population
+ * created with spg_create_population and stepped alone.  Member i is
+ * descs[i]; the descriptions are copied.  Errors as for a population;
+ * SPG_ERR_INVALID names the first invalid member. */
+typedef struct spg_batch spg_batch;
+
+int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_allocator *alloc, void *stream,
+                     spg_batch **out);
+int spg_batch_set_ecology(spg_batch *batch, uint32_t member, const spg_ecology *eco);
+/* Enqueue n_gen generations of every member (returns after enqueue). */
+int spg_batch_step(spg_batch *batch, uint32_t n_gen);
+/* Offspring per thread for the members with n_loci loci (as spg_set_tiling). */
+int spg_batch_set_tiling(spg_batch *batch, uint32_t n_loci, uint32_t items_per_thread);
+int spg_batch_get_tiling(spg_batch *batch, uint32_t n_loci, uint32_t *items_per_thread);
+/* Launch-shape autotuner: for each locus-count group, times gens_per_trial
+ * real generations with each of three tilings and keeps the fastest.  Every
+ * member advances by the same number of generations (*gens_run = 3 *
+ * gens_per_trial); results do not depend on the tilings chosen. */
+int spg_batch_autotune(spg_batch *batch, uint32_t gens_per_trial, uint32_t *gens_run);
+int spg_batch_read_stats(spg_batch *batch, uint32_t member, uint32_t first_gen, uint32_t count, spg_stats *out);
+int spg_batch_read_genotypes(spg_batch *batch, uint32_t member, uint32_t *host, size_t n_words);
+int spg_batch_read_survivors(spg_batch *batch, uint32_t member, uint32_t *host, size_t capacity, uint32_t *S);
+int spg_batch_get_state(spg_batch *batch, uint32_t member, spg_state *out);
+int spg_batch_synchronize(spg_batch *batch);
+uint32_t spg_batch_size(const spg_batch *batch);
+void spg_batch_destroy(spg_batch *batch);
+
 /* ---- One generation without any device allocation -----------------------
  * The paper has no counterpart to this call; it exists for callers that may
  * not allocate device memory: code that runs while a CUDA stream is being

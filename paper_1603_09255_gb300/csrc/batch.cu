@@ -1,0 +1,376 @@
+// Batched replicates (spg_batch): many independent populations advanced by
+// shared launches -- the flattened replicate loop of the paper's Fig. S5 B.
+//
+// Members are grouped by locus count (the offspring kernel is specialised
+// on W).  A group's members are the segments of one launch: every
+// generation is one offspring launch and one compaction launch per group,
+// the groups' chains are independent branches of one CUDA graph (so groups
+// overlap on the GPU), and the graph of kGraphChunk generations is replayed.
+// Each member keeps its own parameters, state, buffers and statistics ring,
+// and its Philox counters carry its own replicate id, so a member's results
+// are identical to the same population stepped alone.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "spegg.h"
+#include "spegg_engine.h"
+#include "spegg_internal.h"
+
+using namespace spg;
+
+namespace {
+
+struct Member {
+    PopView v;
+    std::unique_ptr<PopParams> prm;
+    uint32_t group = 0;
+};
+
+struct Group {
+    uint32_t words = 0, items = 0;
+    std::vector<uint32_t> members;
+    size_t segs_off = 0, tile_map_off = 0, bucket_map_off = 0;  // in the batch arena
+    uint32_t max_tiles = 0;                                     // tile map capacity (items = 1)
+    uint32_t total_buckets = 0;
+    GenLaunch gl;
+};
+
+// A graph of `len` generations for every group: one dependent chain of
+// (offspring, compaction) launches per group, chains independent.
+struct MultiChain {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~MultiChain() { reset(); }
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+    int build(const std::vector<Group> &groups, uint32_t len) {
+        reset();
+        cudaError_t e = cudaGraphCreate(&graph, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+        for (const Group &g : groups) {
+            if (g.members.empty() || g.gl.blocks == 0) continue;
+            GenArgs a = g.gl.args;
+            void *params[] = {&a};
+            cudaGraphNode_t prev = nullptr;
+            for (uint32_t i = 0; i < 2 * len; ++i) {
+                const bool off = (i % 2) == 0;
+                cudaKernelNodeParams kp{};
+                kp.func = reinterpret_cast<void *>(off ? g.gl.offspring.fn : g.gl.compact);
+                kp.gridDim = dim3(off ? g.gl.blocks : g.gl.buckets);
+                kp.blockDim = dim3(off ? kBlock : kBucketWords);
+                kp.sharedMemBytes = off ? g.gl.offspring.smem : 0;
+                kp.kernelParams = params;
+                cudaGraphNode_t node;
+                e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+                if (e != cudaSuccess) {
+                    reset();
+                    return cuda_fail(e, "cudaGraphAddKernelNode");
+                }
+                prev = node;
+            }
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            reset();
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        return SPG_OK;
+    }
+};
+
+uint32_t group_of_words(uint32_t words) { return words == 1 ? 0u : words == 2 ? 1u : words == 4 ? 2u : 3u; }
+
+}  // namespace
+
+struct spg_batch {
+    std::vector<Member> members;
+    std::vector<Group> groups;  // indexed by group_of_words
+    Allocator alloc;
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::map<uint32_t, std::unique_ptr<MultiChain>> chains;  // by length
+};
+
+namespace {
+
+// (Re)build a group's segment table and maps for `items` offspring per
+// thread; uploads them (synchronous).
+int configure_group(spg_batch *b, Group &g, uint32_t items) {
+    if (g.members.empty()) return SPG_OK;
+    OffspringKernel k = offspring_kernel(g.words, items);
+    int rc = prepare_offspring(k);
+    if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
+    std::vector<Segment> segs;
+    std::vector<uint32_t> tile_map, bucket_map;
+    segs.reserve(g.members.size());
+    uint32_t tiles = 0, buckets = 0;
+    for (uint32_t si = 0; si < g.members.size(); ++si) {
+        Member &m = b->members[g.members[si]];
+        const uint32_t nt = (m.v.n + tile_size(items) - 1) / tile_size(items);
+        m.prm->ntiles = nt;
+        segs.push_back(segment_at(m.v.base, m.v.L, m.v.n, nt, tiles, m.v.nbuckets, buckets));
+        tile_map.insert(tile_map.end(), nt, si);
+        bucket_map.insert(bucket_map.end(), m.v.nbuckets, si);
+        tiles += nt;
+        buckets += m.v.nbuckets;
+    }
+    cudaError_t e = cudaMemcpy(b->arena + g.segs_off, segs.data(), segs.size() * sizeof(Segment),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->arena + g.tile_map_off, tile_map.data(), tile_map.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->arena + g.bucket_map_off, bucket_map.data(), bucket_map.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload segment table");
+    g.items = items;
+    g.total_buckets = buckets;
+    g.gl.offspring = k;
+    g.gl.compact = compact_kernel();
+    g.gl.args = GenArgs{};
+    g.gl.args.segs = reinterpret_cast<const Segment *>(b->arena + g.segs_off);
+    g.gl.args.tile_seg = reinterpret_cast<const uint32_t *>(b->arena + g.tile_map_off);
+    g.gl.args.bucket_seg = reinterpret_cast<const uint32_t *>(b->arena + g.bucket_map_off);
+    g.gl.args.nsegs = (uint32_t)segs.size();
+    if (segs.size() == 1) g.gl.args.one = segs[0];
+    g.gl.args.total_tiles = tiles;
+    g.gl.args.total_buckets = buckets;
+    g.gl.blocks = std::min(tiles, k.resident);
+    g.gl.buckets = buckets;
+    b->chains.clear();
+    return SPG_OK;
+}
+
+int member_view(spg_batch *b, uint32_t member, PopView &v) {
+    if (!b) return fail(SPG_ERR_INVALID, "batch is NULL");
+    if (member >= b->members.size()) return fail(SPG_ERR_INVALID, "member %u out of range", member);
+    v = b->members[member].v;
+    return SPG_OK;
+}
+
+int run_chunk(spg_batch *b, uint32_t len) {
+    auto it = b->chains.find(len);
+    if (it == b->chains.end()) {
+        std::unique_ptr<MultiChain> c(new (std::nothrow) MultiChain());
+        if (!c) return fail(SPG_ERR_OOM, "host allocation failed");
+        const int rc = c->build(b->groups, len);
+        if (rc != SPG_OK) return rc;
+        it = b->chains.emplace(len, std::move(c)).first;
+    }
+    const cudaError_t e = cudaGraphLaunch(it->second->exec, b->stream);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+}  // namespace
+
+extern "C" {
+
+int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_allocator *alloc, void *stream,
+                     spg_batch **out) {
+    if (!out) return fail(SPG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!descs || count == 0) return fail(SPG_ERR_INVALID, "a batch needs at least one population");
+    for (uint32_t i = 0; i < count; ++i) {
+        const int rc = validate_desc(descs + i);
+        if (rc != SPG_OK) return fail(rc, "member %u: %s", i, spg_last_error());
+    }
+    std::unique_ptr<spg_batch> b(new (std::nothrow) spg_batch());
+    if (!b) return fail(SPG_ERR_OOM, "host allocation failed");
+    b->members.resize(count);
+    b->groups.resize(4);
+    for (uint32_t gi = 0; gi < 4; ++gi) b->groups[gi].words = 1u << gi;
+    size_t off = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        Member &m = b->members[i];
+        const spg_pop_desc &d = descs[i];
+        m.prm.reset(new (std::nothrow) PopParams());
+        if (!m.prm) return fail(SPG_ERR_OOM, "host allocation failed");
+        const uint32_t words = d.n_loci / 32;
+        int rc = build_params(&d, 1, *m.prm);
+        if (rc != SPG_OK) return fail(rc, "member %u: %s", i, spg_last_error());
+        m.v.n = d.n;
+        m.v.words = words;
+        m.v.cap = m.prm->stats_cap;
+        m.v.nbuckets = bucket_count(d.n);
+        m.v.L = layout_for(d.n, words, m.v.nbuckets, m.v.cap);
+        m.group = group_of_words(words);
+        b->groups[m.group].members.push_back(i);
+        m.v.base = reinterpret_cast<char *>(off);  // offset until the arena exists
+        off = align_up(off + m.v.L.total, 256);
+    }
+    for (Group &g : b->groups) {
+        if (g.members.empty()) continue;
+        uint32_t tiles = 0, buckets = 0;
+        for (uint32_t mi : g.members) {
+            tiles += (b->members[mi].v.n + tile_size(1) - 1) / tile_size(1);
+            buckets += b->members[mi].v.nbuckets;
+        }
+        g.max_tiles = tiles;
+        g.segs_off = off;
+        off = align_up(off + g.members.size() * sizeof(Segment), 256);
+        g.tile_map_off = off;
+        off = align_up(off + (size_t)tiles * 4, 256);
+        g.bucket_map_off = off;
+        off = align_up(off + (size_t)buckets * 4, 256);
+    }
+    b->arena_bytes = off;
+    if (alloc) b->alloc.hooks = *alloc;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        const cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        b->own_stream = true;
+    }
+    b->arena = static_cast<char *>(b->alloc.alloc(b->arena_bytes, b->stream));
+    if (!b->arena) {
+        spg_batch_destroy(b.release());
+        return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", b->arena_bytes);
+    }
+    for (uint32_t i = 0; i < count; ++i) {
+        Member &m = b->members[i];
+        m.v.base = b->arena + reinterpret_cast<size_t>(m.v.base);
+        m.v.stream = b->stream;
+        const int rc = view_init(m.v, *m.prm, descs[i].init_genotypes, descs[i].p0_q32);
+        if (rc != SPG_OK) {
+            spg_batch *raw = b.release();
+            spg_batch_destroy(raw);
+            return rc;
+        }
+    }
+    int rc = view_sync(b->members[0].v);  // caller arrays and host parameters have been read
+    for (Group &g : b->groups)
+        if (rc == SPG_OK) rc = configure_group(b.get(), g, default_items(g.words));
+    if (rc != SPG_OK) {
+        spg_batch_destroy(b.release());
+        return rc;
+    }
+    *out = b.release();
+    return SPG_OK;
+}
+
+int spg_batch_set_ecology(spg_batch *b, uint32_t member, const spg_ecology *eco) {
+    PopView v;
+    int rc = member_view(b, member, v);
+    if (rc != SPG_OK) return rc;
+    return view_set_ecology(v, *b->members[member].prm, eco);
+}
+
+int spg_batch_step(spg_batch *b, uint32_t n_gen) {
+    if (!b) return fail(SPG_ERR_INVALID, "batch is NULL");
+    for (uint32_t i = 0; i + kGraphChunk <= n_gen; i += kGraphChunk) {
+        const int rc = run_chunk(b, kGraphChunk);
+        if (rc != SPG_OK) return rc;
+    }
+    if (n_gen % kGraphChunk) return run_chunk(b, n_gen % kGraphChunk);
+    return SPG_OK;
+}
+
+int spg_batch_set_tiling(spg_batch *b, uint32_t n_loci, uint32_t items) {
+    if (!b) return fail(SPG_ERR_INVALID, "batch is NULL");
+    if (!(n_loci == 32 || n_loci == 64 || n_loci == 128 || n_loci == 256))
+        return fail(SPG_ERR_INVALID, "n_loci must be 32, 64, 128 or 256");
+    const uint32_t words = n_loci / 32;
+    if (!supported_items(words, items))
+        return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (1 or 2 for 256 loci); got %u", items);
+    int rc = view_sync(b->members[0].v);
+    if (rc != SPG_OK) return rc;
+    return configure_group(b, b->groups[group_of_words(words)], items);
+}
+
+int spg_batch_get_tiling(spg_batch *b, uint32_t n_loci, uint32_t *items) {
+    if (!b || !items) return fail(SPG_ERR_INVALID, "NULL argument");
+    if (!(n_loci == 32 || n_loci == 64 || n_loci == 128 || n_loci == 256))
+        return fail(SPG_ERR_INVALID, "n_loci must be 32, 64, 128 or 256");
+    *items = b->groups[group_of_words(n_loci / 32)].items;
+    return SPG_OK;
+}
+
+int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, uint32_t *gens_run) {
+    if (!b || gens_per_trial == 0) return fail(SPG_ERR_INVALID, "batch is NULL or no trial generations");
+    cudaEvent_t t0, t1;
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+        return fail(SPG_ERR_CUDA, "cudaEventCreate");
+    static const uint32_t kCandidates[3] = {1, 2, 4};
+    int rc = SPG_OK;
+    // every group runs three trials, so all members advance equally
+    for (Group &g : b->groups) {
+        if (g.members.empty()) continue;
+        float best_ms = 0.f;
+        uint32_t best = g.items;
+        for (int c = 0; c < 3 && rc == SPG_OK; ++c) {
+            uint32_t items = kCandidates[c];
+            if (!supported_items(g.words, items)) items = 2;
+            rc = configure_group(b, g, items);
+            if (rc != SPG_OK) break;
+            cudaEventRecord(t0, b->stream);
+            for (uint32_t i = 0; i < gens_per_trial && rc == SPG_OK; ++i) rc = launch_generation(g.gl, b->stream);
+            cudaEventRecord(t1, b->stream);
+            if (cudaEventSynchronize(t1) != cudaSuccess) rc = fail(SPG_ERR_CUDA, "trial timing");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (c == 0 || ms < best_ms) {
+                best_ms = ms;
+                best = items;
+            }
+        }
+        if (rc == SPG_OK) rc = configure_group(b, g, best);
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (rc == SPG_OK && gens_run) *gens_run = 3 * gens_per_trial;
+    return rc;
+}
+
+int spg_batch_read_stats(spg_batch *b, uint32_t member, uint32_t first_gen, uint32_t count, spg_stats *out) {
+    PopView v;
+    const int rc = member_view(b, member, v);
+    return rc != SPG_OK ? rc : view_read_stats(v, first_gen, count, out);
+}
+
+int spg_batch_read_genotypes(spg_batch *b, uint32_t member, uint32_t *host, size_t n_words) {
+    PopView v;
+    const int rc = member_view(b, member, v);
+    return rc != SPG_OK ? rc : view_read_genotypes(v, host, n_words);
+}
+
+int spg_batch_read_survivors(spg_batch *b, uint32_t member, uint32_t *host, size_t capacity, uint32_t *S) {
+    PopView v;
+    const int rc = member_view(b, member, v);
+    return rc != SPG_OK ? rc : view_read_survivors(v, host, capacity, S);
+}
+
+int spg_batch_get_state(spg_batch *b, uint32_t member, spg_state *out) {
+    PopView v;
+    const int rc = member_view(b, member, v);
+    return rc != SPG_OK ? rc : view_get_state(v, out);
+}
+
+int spg_batch_synchronize(spg_batch *b) {
+    if (!b) return fail(SPG_ERR_INVALID, "batch is NULL");
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
+
+uint32_t spg_batch_size(const spg_batch *b) { return b ? (uint32_t)b->members.size() : 0u; }
+
+void spg_batch_destroy(spg_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    b->chains.clear();
+    if (b->arena) b->alloc.release(b->arena, b->stream);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

@@ -262,53 +262,143 @@ int enqueue_generations(const GenLaunch &gl, uint32_t n_gen, GraphChain &chain, 
     return SPG_OK;
 }
 
-}  // namespace spg
-
-using namespace spg;
-
-struct spg_pop {
-    uint32_t n = 0, n_loci = 0, words = 0, items = 0, ntiles = 0, cap = 0;
-    uint64_t seed = 0;
-    uint32_t rep = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    Allocator alloc;
-    char *arena = nullptr;
-    PopLayout L{};
-    PopParams *host_prm = nullptr;  // host copy of the parameters
-    uint32_t nbuckets = 0;
-    GenLaunch gl;
-    GraphChain chain;
-    bool has_eco = false;
-    double R0 = 0.0;
-};
-
-namespace {
-
-int sync_stream(spg_pop *p) {
-    const cudaError_t e = cudaStreamSynchronize(p->stream);
+// ------------------------------------------------- one population's memory
+int view_sync(const PopView &v) {
+    const cudaError_t e = cudaStreamSynchronize(v.stream);
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "cudaStreamSynchronize");
 }
 
-int read_state(spg_pop *p, DevState &st) {
-    int rc = sync_stream(p);
+int view_state(const PopView &v, DevState &st) {
+    int rc = view_sync(v);
     if (rc != SPG_OK) return rc;
-    const cudaError_t e = cudaMemcpy(&st, p->arena + p->L.state, sizeof st, cudaMemcpyDeviceToHost);
+    const cudaError_t e = cudaMemcpy(&st, v.base + v.L.state, sizeof st, cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read state");
 }
 
-int upload_params(spg_pop *p) {
-    const cudaError_t e = cudaMemcpyAsync(p->arena + p->L.params, p->host_prm, sizeof(PopParams),
-                                          cudaMemcpyHostToDevice, p->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "upload parameters");
-    // the host copy must stay valid until the copy has run
-    return sync_stream(p);
+int view_set_state(const PopView &v, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status) {
+    return launch_set_state(reinterpret_cast<DevState *>(v.base + v.L.state),
+                            reinterpret_cast<StatAcc *>(v.base + v.L.acc), gen, S, f, R, status, v.stream);
 }
 
-}  // namespace
+// Enqueue the generation-0 set-up of one population: parameters, counters,
+// founders and state.  `prm` and `init_genotypes` must stay valid until the
+// stream has run the copies (callers synchronise before returning).
+int view_init(const PopView &v, const PopParams &prm, const uint32_t *init_genotypes, uint32_t p0_q32) {
+    cudaError_t e = cudaMemsetAsync(v.base + v.L.buckets, 0, (size_t)2 * v.nbuckets * 4, v.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.base + v.L.ring, 0, (size_t)v.cap * sizeof(spg_stats), v.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(v.base + v.L.params, &prm, sizeof(PopParams), cudaMemcpyHostToDevice, v.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "initialise device memory");
+    uint32_t *geno0 = reinterpret_cast<uint32_t *>(v.base + v.L.geno0);
+    uint32_t *surv0 = reinterpret_cast<uint32_t *>(v.base + v.L.surv0);
+    int rc;
+    if (init_genotypes) {
+        e = cudaMemcpyAsync(geno0, init_genotypes, (size_t)v.n * 2 * v.words * 4, cudaMemcpyHostToDevice, v.stream);
+        if (e != cudaSuccess) return cuda_fail(e, "upload founders");
+        rc = launch_iota(surv0, v.n, v.stream);
+    } else {
+        rc = launch_founders(v.words, geno0, surv0, v.n, prm.key0, prm.key1, prm.rep, p0_q32, v.stream);
+    }
+    if (rc != SPG_OK) return fail(rc, "founder launch failed");
+    rc = view_set_state(v, 0, v.n, kCertain, 0.0, SPG_OK);
+    return rc == SPG_OK ? SPG_OK : fail(rc, "state launch failed");
+}
+
+int check_ecology(const spg_ecology *eco) {
+    if (!eco) return fail(SPG_ERR_INVALID, "ecology is NULL");
+    if (!eco->attack) return fail(SPG_ERR_INVALID, "attack table is NULL");
+    if (!(eco->K > 0.0) || !(eco->R_half > 0.0) || !(eco->R0 >= 0.0) || !std::isfinite(eco->r) ||
+        !std::isfinite(eco->K) || !std::isfinite(eco->R0))
+        return fail(SPG_ERR_INVALID, "ecology needs K > 0, R_half > 0, R0 >= 0, finite r");
+    return SPG_OK;
+}
+
+// Attach an ecology: parameters (host copy updated and uploaded, then the
+// stream synchronised) and the state's R and f.
+int view_set_ecology(const PopView &v, PopParams &prm, const spg_ecology *eco) {
+    int rc = check_ecology(eco);
+    if (rc != SPG_OK) return rc;
+    DevState st;
+    rc = view_state(v, st);
+    if (rc != SPG_OK) return rc;
+    std::memcpy(prm.attack, eco->attack, sizeof prm.attack);
+    prm.has_eco = 1;
+    prm.r = eco->r;
+    prm.K = eco->K;
+    prm.R_half = eco->R_half;
+    const cudaError_t e =
+        cudaMemcpyAsync(v.base + v.L.params, &prm, sizeof(PopParams), cudaMemcpyHostToDevice, v.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload parameters");
+    rc = view_set_state(v, st.gen, st.S, factor_q32_host(eco->R0, eco->R_half), eco->R0, st.status);
+    if (rc != SPG_OK) return rc;
+    return view_sync(v);
+}
+
+int view_read_stats(const PopView &v, uint32_t first_gen, uint32_t count, spg_stats *out) {
+    if (!out && count) return fail(SPG_ERR_INVALID, "NULL argument");
+    DevState st;
+    int rc = view_state(v, st);
+    if (rc != SPG_OK) return rc;
+    if (count == 0) return SPG_OK;
+    const uint64_t last = (uint64_t)first_gen + count - 1;
+    if (first_gen == 0 || last > st.gen || (uint64_t)st.gen - first_gen >= v.cap)
+        return fail(SPG_ERR_RANGE, "generations %u..%llu not in the ring (completed %u, capacity %u)", first_gen,
+                    (unsigned long long)last, st.gen, v.cap);
+    const spg_stats *ring = reinterpret_cast<const spg_stats *>(v.base + v.L.ring);
+    for (uint32_t i = 0; i < count;) {
+        const uint32_t slot = (first_gen - 1 + i) % v.cap;
+        const uint32_t run = std::min(count - i, v.cap - slot);
+        const cudaError_t e = cudaMemcpy(out + i, ring + slot, run * sizeof(spg_stats), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read stats");
+        i += run;
+    }
+    return st.status < 0 ? fail(st.status, "device status %d", st.status) : SPG_OK;
+}
+
+int view_read_genotypes(const PopView &v, uint32_t *host, size_t n_words) {
+    if (!host) return fail(SPG_ERR_INVALID, "NULL argument");
+    const size_t need = (size_t)v.n * 2 * v.words;
+    if (n_words < need) return fail(SPG_ERR_INVALID, "buffer holds %zu words, need %zu", n_words, need);
+    DevState st;
+    int rc = view_state(v, st);
+    if (rc != SPG_OK) return rc;
+    const char *src = v.base + ((st.gen & 1u) ? v.L.geno1 : v.L.geno0);
+    const cudaError_t e = cudaMemcpy(host, src, need * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read genotypes");
+}
+
+int view_read_survivors(const PopView &v, uint32_t *host, size_t capacity, uint32_t *S) {
+    if (!S) return fail(SPG_ERR_INVALID, "NULL argument");
+    DevState st;
+    int rc = view_state(v, st);
+    if (rc != SPG_OK) return rc;
+    *S = st.S;
+    if (!host) return SPG_OK;
+    if (capacity < st.S) return fail(SPG_ERR_INVALID, "buffer holds %zu, need %u", capacity, st.S);
+    const char *src = v.base + ((st.gen & 1u) ? v.L.surv1 : v.L.surv0);
+    const cudaError_t e = cudaMemcpy(host, src, (size_t)st.S * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read survivors");
+}
+
+int view_get_state(const PopView &v, spg_state *out) {
+    if (!out) return fail(SPG_ERR_INVALID, "NULL argument");
+    DevState st;
+    const int rc = view_state(v, st);
+    if (rc != SPG_OK) return rc;
+    out->gen = st.gen;
+    out->S = st.S;
+    out->status = st.status;
+    out->f = st.f;
+    out->R = st.R;
+    return SPG_OK;
+}
+
+}  // namespace spg
+
+
+using namespace spg;
 
 extern "C" {
-
 uint32_t spg_abi_version(void) { return SPG_ABI_VERSION; }
 
 uint32_t spg_mutation_cdf(double mu, uint32_t n_copies, uint32_t cdf[32]) {
@@ -330,324 +420,6 @@ const char *spg_status_string(int code) {
         case SPG_ERR_BUDGET: return "memory budget exceeded";
         default: return "unknown status";
     }
-}
-
-int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, void *stream, spg_pop **out) {
-    if (!out) return fail(SPG_ERR_INVALID, "out is NULL");
-    *out = nullptr;
-    int rc = validate_desc(desc);
-    if (rc != SPG_OK) return rc;
-    spg_pop *p = new (std::nothrow) spg_pop();
-    if (!p) return fail(SPG_ERR_OOM, "host allocation failed");
-    p->n = desc->n;
-    p->n_loci = desc->n_loci;
-    p->words = desc->n_loci / 32;
-    p->items = default_items(p->words);
-    p->seed = desc->seed;
-    p->rep = desc->replicate;
-    p->host_prm = new (std::nothrow) PopParams();
-    if (!p->host_prm) {
-        delete p;
-        return fail(SPG_ERR_OOM, "host allocation failed");
-    }
-    rc = build_params(desc, p->items, *p->host_prm);
-    if (rc != SPG_OK) {
-        delete p->host_prm;
-        delete p;
-        return rc;
-    }
-    p->ntiles = p->host_prm->ntiles;
-    p->cap = p->host_prm->stats_cap;
-    if (alloc) p->alloc.hooks = *alloc;
-    if (stream) {
-        p->stream = (cudaStream_t)stream;
-    } else {
-        const cudaError_t e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            delete p->host_prm;
-            delete p;
-            return cuda_fail(e, "cudaStreamCreate");
-        }
-        p->own_stream = true;
-    }
-    p->nbuckets = bucket_count(p->n);
-    p->L = layout_for(p->n, p->words, p->nbuckets, p->cap);
-    p->arena = static_cast<char *>(p->alloc.alloc(p->L.total, p->stream));
-    if (!p->arena) {
-        spg_destroy(p);
-        return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", p->L.total);
-    }
-    cudaError_t e = cudaMemsetAsync(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4, p->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->arena + p->L.ring, 0, (size_t)p->cap * sizeof(spg_stats), p->stream);
-    if (e != cudaSuccess) {
-        spg_destroy(p);
-        return cuda_fail(e, "initialise device memory");
-    }
-    const Segment seg = segment_at(p->arena, p->L, p->n, p->ntiles, 0, p->nbuckets, 0);
-    e = cudaMemcpyAsync(p->arena + p->L.segment, &seg, sizeof seg, cudaMemcpyHostToDevice, p->stream);
-    if (e != cudaSuccess) {
-        spg_destroy(p);
-        return cuda_fail(e, "upload segment");
-    }
-    rc = upload_params(p);  // synchronises, so &seg above is no longer needed
-    if (rc != SPG_OK) {
-        spg_destroy(p);
-        return rc;
-    }
-    uint32_t *geno0 = reinterpret_cast<uint32_t *>(p->arena + p->L.geno0);
-    uint32_t *surv0 = reinterpret_cast<uint32_t *>(p->arena + p->L.surv0);
-    if (desc->init_genotypes) {
-        e = cudaMemcpyAsync(geno0, desc->init_genotypes, (size_t)p->n * 2 * p->words * 4, cudaMemcpyHostToDevice,
-                            p->stream);
-        if (e != cudaSuccess) {
-            spg_destroy(p);
-            return cuda_fail(e, "upload founders");
-        }
-        rc = launch_iota(surv0, p->n, p->stream);
-    } else {
-        rc = launch_founders(p->words, geno0, surv0, p->n, p->host_prm->key0, p->host_prm->key1, p->rep,
-                             desc->p0_q32, p->stream);
-    }
-    if (rc == SPG_OK)
-        rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
-                              reinterpret_cast<StatAcc *>(p->arena + p->L.acc), 0, p->n, kCertain, 0.0, SPG_OK,
-                              p->stream);
-    if (rc == SPG_OK) rc = sync_stream(p);  // caller's founder array is read before returning
-    if (rc != SPG_OK) {
-        spg_destroy(p);
-        return rc == SPG_ERR_CUDA ? rc : fail(rc, "initialise population");
-    }
-    p->gl.offspring = offspring_kernel(p->words, p->items);
-    rc = prepare_offspring(p->gl.offspring);
-    if (rc != SPG_OK) {
-        spg_destroy(p);
-        return fail(rc, "offspring kernel setup failed");
-    }
-    p->gl.compact = compact_kernel();
-    p->gl.args.segs = reinterpret_cast<const Segment *>(p->arena + p->L.segment);
-    p->gl.args.one = segment_at(p->arena, p->L, p->n, p->ntiles, 0, p->nbuckets, 0);
-    p->gl.args.nsegs = 1;
-    p->gl.args.total_tiles = p->ntiles;
-    p->gl.args.total_buckets = p->nbuckets;
-    p->gl.blocks = std::min(p->ntiles, p->gl.offspring.resident);
-    p->gl.buckets = p->nbuckets;
-    *out = p;
-    return SPG_OK;
-}
-
-int spg_set_ecology(spg_pop *p, const spg_ecology *eco) {
-    if (!p || !eco) return fail(SPG_ERR_INVALID, "NULL argument");
-    if (!eco->attack) return fail(SPG_ERR_INVALID, "attack table is NULL");
-    if (!(eco->K > 0.0) || !(eco->R_half > 0.0) || !(eco->R0 >= 0.0) || !std::isfinite(eco->r) ||
-        !std::isfinite(eco->K) || !std::isfinite(eco->R0))
-        return fail(SPG_ERR_INVALID, "ecology needs K > 0, R_half > 0, R0 >= 0, finite r");
-    DevState st;
-    int rc = read_state(p, st);
-    if (rc != SPG_OK) return rc;
-    std::memcpy(p->host_prm->attack, eco->attack, sizeof p->host_prm->attack);
-    p->host_prm->has_eco = 1;
-    p->host_prm->r = eco->r;
-    p->host_prm->K = eco->K;
-    p->host_prm->R_half = eco->R_half;
-    p->has_eco = true;
-    p->R0 = eco->R0;
-    rc = upload_params(p);
-    if (rc != SPG_OK) return rc;
-    rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
-                          reinterpret_cast<StatAcc *>(p->arena + p->L.acc), st.gen, st.S,
-                          factor_q32_host(eco->R0, eco->R_half), eco->R0, st.status, p->stream);
-    return rc;
-}
-
-int spg_step_generations(spg_pop *p, uint32_t n_gen) {
-    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
-    return enqueue_generations(p->gl, n_gen, p->chain, p->stream);
-}
-
-int spg_read_stats(spg_pop *p, uint32_t first_gen, uint32_t count, spg_stats *out) {
-    if (!p || (!out && count)) return fail(SPG_ERR_INVALID, "NULL argument");
-    DevState st;
-    int rc = read_state(p, st);
-    if (rc != SPG_OK) return rc;
-    if (count == 0) return SPG_OK;
-    const uint64_t last = (uint64_t)first_gen + count - 1;
-    if (first_gen == 0 || last > st.gen || (uint64_t)st.gen - first_gen >= p->cap)
-        return fail(SPG_ERR_RANGE, "generations %u..%llu not in the ring (completed %u, capacity %u)", first_gen,
-                    (unsigned long long)last, st.gen, p->cap);
-    const spg_stats *ring = reinterpret_cast<const spg_stats *>(p->arena + p->L.ring);
-    for (uint32_t i = 0; i < count;) {
-        const uint32_t slots = p->cap;
-        const uint32_t slot = (first_gen - 1 + i) % slots;
-        const uint32_t run = std::min(count - i, slots - slot);
-        const cudaError_t e = cudaMemcpy(out + i, ring + slot, run * sizeof(spg_stats), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(e, "read stats");
-        i += run;
-    }
-    return st.status < 0 ? fail(st.status, "device status %d", st.status) : SPG_OK;
-}
-
-int spg_read_genotypes(spg_pop *p, uint32_t *host, size_t n_words) {
-    if (!p || !host) return fail(SPG_ERR_INVALID, "NULL argument");
-    const size_t need = (size_t)p->n * 2 * p->words;
-    if (n_words < need) return fail(SPG_ERR_INVALID, "buffer holds %zu words, need %zu", n_words, need);
-    DevState st;
-    int rc = read_state(p, st);
-    if (rc != SPG_OK) return rc;
-    const char *src = p->arena + ((st.gen & 1u) ? p->L.geno1 : p->L.geno0);
-    const cudaError_t e = cudaMemcpy(host, src, need * 4, cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read genotypes");
-}
-
-int spg_read_survivors(spg_pop *p, uint32_t *host, size_t capacity, uint32_t *S) {
-    if (!p || !S) return fail(SPG_ERR_INVALID, "NULL argument");
-    DevState st;
-    int rc = read_state(p, st);
-    if (rc != SPG_OK) return rc;
-    *S = st.S;
-    if (!host) return SPG_OK;
-    if (capacity < st.S) return fail(SPG_ERR_INVALID, "buffer holds %zu, need %u", capacity, st.S);
-    const char *src = p->arena + ((st.gen & 1u) ? p->L.surv1 : p->L.surv0);
-    const cudaError_t e = cudaMemcpy(host, src, (size_t)st.S * 4, cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read survivors");
-}
-
-int spg_get_state(spg_pop *p, spg_state *out) {
-    if (!p || !out) return fail(SPG_ERR_INVALID, "NULL argument");
-    DevState st;
-    const int rc = read_state(p, st);
-    if (rc != SPG_OK) return rc;
-    out->gen = st.gen;
-    out->S = st.S;
-    out->status = st.status;
-    out->f = st.f;
-    out->R = st.R;
-    return SPG_OK;
-}
-
-int spg_checkpoint_size(spg_pop *p, size_t *bytes) {
-    if (!p || !bytes) return fail(SPG_ERR_INVALID, "NULL argument");
-    *bytes = sizeof(CheckpointHeader) + (size_t)p->n * 2 * p->words * 4 + (size_t)p->n * 4;
-    return SPG_OK;
-}
-
-int spg_checkpoint(spg_pop *p, void *host, size_t capacity) {
-    size_t need = 0;
-    int rc = spg_checkpoint_size(p, &need);
-    if (rc != SPG_OK) return rc;
-    if (!host || capacity < need) return fail(SPG_ERR_INVALID, "checkpoint buffer too small (need %zu)", need);
-    DevState st;
-    rc = read_state(p, st);
-    if (rc != SPG_OK) return rc;
-    CheckpointHeader h{};
-    h.magic = kCheckpointMagic;
-    h.version = SPG_ABI_VERSION;
-    h.n = p->n;
-    h.n_loci = p->n_loci;
-    h.gen = st.gen;
-    h.S = st.S;
-    h.status = st.status;
-    h.f = st.f;
-    h.R = st.R;
-    h.seed = p->seed;
-    h.replicate = p->rep;
-    char *dst = static_cast<char *>(host);
-    std::memcpy(dst, &h, sizeof h);
-    const size_t gbytes = (size_t)p->n * 2 * p->words * 4;
-    cudaError_t e = cudaMemcpy(dst + sizeof h, p->arena + ((st.gen & 1u) ? p->L.geno1 : p->L.geno0), gbytes,
-                               cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(dst + sizeof h + gbytes, p->arena + ((st.gen & 1u) ? p->L.surv1 : p->L.surv0),
-                       (size_t)st.S * 4, cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "checkpoint copy");
-}
-
-int spg_restore(spg_pop *p, const void *host, size_t bytes) {
-    size_t need = 0;
-    int rc = spg_checkpoint_size(p, &need);
-    if (rc != SPG_OK) return rc;
-    if (!host || bytes < sizeof(CheckpointHeader)) return fail(SPG_ERR_INVALID, "checkpoint too small");
-    CheckpointHeader h;
-    std::memcpy(&h, host, sizeof h);
-    if (h.magic != kCheckpointMagic || h.n != p->n || h.n_loci != p->n_loci || h.S > p->n || bytes < need)
-        return fail(SPG_ERR_INVALID, "checkpoint does not match this population");
-    if ((h.S == 0) != (h.status == SPG_EXTINCT) || h.status < 0)
-        return fail(SPG_ERR_INVALID, "checkpoint state is inconsistent");
-    const char *src = static_cast<const char *>(host);
-    const size_t gbytes = (size_t)p->n * 2 * p->words * 4;
-    {
-        // survivors index parent records: strictly increasing and < n
-        const uint32_t *sv = reinterpret_cast<const uint32_t *>(src + sizeof h + gbytes);
-        uint32_t prev = 0;
-        for (uint32_t i = 0; i < h.S; ++i) {
-            uint32_t v;
-            std::memcpy(&v, sv + i, 4);
-            if (v >= p->n || (i > 0 && v <= prev)) return fail(SPG_ERR_INVALID, "checkpoint survivor list is invalid");
-            prev = v;
-        }
-    }
-    rc = sync_stream(p);
-    if (rc != SPG_OK) return rc;
-    cudaError_t e = cudaMemcpy(p->arena + ((h.gen & 1u) ? p->L.geno1 : p->L.geno0), src + sizeof h, gbytes,
-                               cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(p->arena + ((h.gen & 1u) ? p->L.surv1 : p->L.surv0), src + sizeof h + gbytes,
-                       (size_t)h.S * 4, cudaMemcpyHostToDevice);
-    // per-bucket survivor counts of the replaced run must not leak into the
-    // generations about to be replayed
-    if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4);
-    if (e != cudaSuccess) return cuda_fail(e, "restore copy");
-    rc = launch_set_state(reinterpret_cast<DevState *>(p->arena + p->L.state),
-                          reinterpret_cast<StatAcc *>(p->arena + p->L.acc), h.gen, h.S, h.f, h.R, h.status,
-                          p->stream);
-    if (rc != SPG_OK) return rc;
-    return sync_stream(p);
-}
-
-int spg_set_tiling(spg_pop *p, uint32_t items) {
-    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
-    if (!supported_items(p->words, items))
-        return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (1 or 2 for 256 loci); got %u", items);
-    OffspringKernel k = offspring_kernel(p->words, items);
-    int prc = prepare_offspring(k);
-    if (prc != SPG_OK) return fail(prc, "offspring kernel setup failed");
-    int rc = sync_stream(p);
-    if (rc != SPG_OK) return rc;
-    p->items = items;
-    p->ntiles = (p->n + tile_size(items) - 1) / tile_size(items);
-    p->host_prm->ntiles = p->ntiles;
-    const Segment seg = segment_at(p->arena, p->L, p->n, p->ntiles, 0, p->nbuckets, 0);
-    const cudaError_t e = cudaMemcpy(p->arena + p->L.segment, &seg, sizeof seg, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "upload segment");
-    rc = upload_params(p);
-    if (rc != SPG_OK) return rc;
-    p->gl.offspring = k;
-    p->gl.args.one = seg;
-    p->gl.args.total_tiles = p->ntiles;
-    p->gl.blocks = std::min(p->ntiles, k.resident);
-    p->chain.reset();
-    return SPG_OK;
-}
-
-int spg_get_tiling(spg_pop *p, uint32_t *items) {
-    if (!p || !items) return fail(SPG_ERR_INVALID, "NULL argument");
-    *items = p->items;
-    return SPG_OK;
-}
-
-int spg_synchronize(spg_pop *p) {
-    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
-    return sync_stream(p);
-}
-
-void spg_destroy(spg_pop *p) {
-    if (!p) return;
-    if (p->stream) cudaStreamSynchronize(p->stream);
-    p->chain.reset();
-    if (p->arena) p->alloc.release(p->arena, p->stream);
-    if (p->stream) cudaStreamSynchronize(p->stream);
-    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
-    delete p->host_prm;
-    delete p;
 }
 
 void spg_summarize(const spg_stats *st, uint32_t n_loci, float out[5]) {

@@ -313,19 +313,6 @@ __device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g,
     }
 }
 
-// Segment (population) owning launch-wide unit `u` given each segment's
-// first unit: last segment with first <= u.
-template <typename F>
-__device__ __forceinline__ uint32_t find_segment(const Segment *segs, uint32_t nsegs, uint32_t u, F first) {
-    uint32_t lo = 0, hi = nsegs - 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (first(segs[mid]) <= u) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 struct PopNow {
     uint32_t gen, S, f;
     bool active;
@@ -541,7 +528,7 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
     uint32_t t = (uint32_t)(((unsigned long long)T * blockIdx.x) / G);
     const uint32_t t_end = (uint32_t)(((unsigned long long)T * (blockIdx.x + 1)) / G);
     if (t >= t_end) return;
-    uint32_t si = a.nsegs == 1u ? 0u : find_segment(a.segs, a.nsegs, t, [](const Segment &x) { return x.tile_begin; });
+    uint32_t si = a.nsegs == 1u ? 0u : __ldg(a.tile_seg + t);
 
     while (t < t_end) {
         const Segment &sg = a.nsegs == 1u ? a.one : a.segs[si];
@@ -734,8 +721,7 @@ __global__ void __launch_bounds__(kBucketWords) k_compact(const __grid_constant_
     if (a.nsegs == 1u) {
         compact_bucket(a.one, bkt);
     } else {
-        const Segment &sg =
-            a.segs[find_segment(a.segs, a.nsegs, bkt, [](const Segment &x) { return x.bucket_begin; })];
+        const Segment &sg = a.segs[__ldg(a.bucket_seg + bkt)];
         compact_bucket(sg, bkt - sg.bucket_begin);
     }
 }

@@ -1,0 +1,276 @@
+// C ABI of one population (spg_pop): create, ecology, stepping, reads,
+// checkpoint/restore, tiling (see include/spegg.h).
+//
+// A population owns one device arena (parameters, state, accumulators, two
+// genotype buffers, two survivor lists, bitmap, bucket counts, statistics
+// ring).  Generations are enqueued as a cached CUDA graph of kGraphChunk
+// generations (two launches each); every launch has identical arguments
+// because buffers are chosen on the device by generation parity.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "spegg.h"
+#include "spegg_engine.h"
+#include "spegg_internal.h"
+
+using namespace spg;
+
+struct spg_pop {
+    uint32_t n = 0, n_loci = 0, words = 0, items = 0, ntiles = 0, nbuckets = 0, cap = 0;
+    uint64_t seed = 0;
+    uint32_t rep = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Allocator alloc;
+    char *arena = nullptr;
+    PopLayout L{};
+    PopParams *host_prm = nullptr;  // host copy of the parameters
+    GenLaunch gl;
+    GraphChain chain;
+
+    PopView view() const {
+        PopView v;
+        v.base = arena;
+        v.L = L;
+        v.n = n;
+        v.words = words;
+        v.cap = cap;
+        v.nbuckets = nbuckets;
+        v.stream = stream;
+        return v;
+    }
+};
+
+namespace {
+
+// Point the launch at the population's single segment with `items` offspring
+// per thread (uploads the device copy of the segment; synchronous).
+int configure_launch(spg_pop *p, uint32_t items) {
+    OffspringKernel k = offspring_kernel(p->words, items);
+    int rc = prepare_offspring(k);
+    if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
+    p->items = items;
+    p->ntiles = (p->n + tile_size(items) - 1) / tile_size(items);
+    p->host_prm->ntiles = p->ntiles;
+    const Segment seg = segment_at(p->arena, p->L, p->n, p->ntiles, 0, p->nbuckets, 0);
+    cudaError_t e = cudaMemcpyAsync(p->arena + p->L.segment, &seg, sizeof seg, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->arena + p->L.params, p->host_prm, sizeof(PopParams), cudaMemcpyHostToDevice,
+                            p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload segment");
+    rc = view_sync(p->view());
+    if (rc != SPG_OK) return rc;
+    p->gl.offspring = k;
+    p->gl.compact = compact_kernel();
+    p->gl.args.segs = reinterpret_cast<const Segment *>(p->arena + p->L.segment);
+    p->gl.args.one = seg;
+    p->gl.args.nsegs = 1;
+    p->gl.args.total_tiles = p->ntiles;
+    p->gl.args.total_buckets = p->nbuckets;
+    p->gl.blocks = std::min(p->ntiles, k.resident);
+    p->gl.buckets = p->nbuckets;
+    p->chain.reset();
+    return SPG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, void *stream, spg_pop **out) {
+    if (!out) return fail(SPG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int rc = validate_desc(desc);
+    if (rc != SPG_OK) return rc;
+    spg_pop *p = new (std::nothrow) spg_pop();
+    if (!p) return fail(SPG_ERR_OOM, "host allocation failed");
+    p->n = desc->n;
+    p->n_loci = desc->n_loci;
+    p->words = desc->n_loci / 32;
+    p->seed = desc->seed;
+    p->rep = desc->replicate;
+    p->host_prm = new (std::nothrow) PopParams();
+    if (!p->host_prm) {
+        delete p;
+        return fail(SPG_ERR_OOM, "host allocation failed");
+    }
+    const uint32_t items = default_items(p->words);
+    rc = build_params(desc, items, *p->host_prm);
+    if (rc != SPG_OK) {
+        delete p->host_prm;
+        delete p;
+        return rc;
+    }
+    p->cap = p->host_prm->stats_cap;
+    p->nbuckets = bucket_count(p->n);
+    if (alloc) p->alloc.hooks = *alloc;
+    if (stream) {
+        p->stream = (cudaStream_t)stream;
+    } else {
+        const cudaError_t e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete p->host_prm;
+            delete p;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        p->own_stream = true;
+    }
+    p->L = layout_for(p->n, p->words, p->nbuckets, p->cap);
+    p->arena = static_cast<char *>(p->alloc.alloc(p->L.total, p->stream));
+    if (!p->arena) {
+        spg_destroy(p);
+        return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", p->L.total);
+    }
+    rc = view_init(p->view(), *p->host_prm, desc->init_genotypes, desc->p0_q32);
+    if (rc == SPG_OK) rc = view_sync(p->view());  // the caller's arrays are read before returning
+    if (rc == SPG_OK) rc = configure_launch(p, items);
+    if (rc != SPG_OK) {
+        spg_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return SPG_OK;
+}
+
+int spg_set_ecology(spg_pop *p, const spg_ecology *eco) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    return view_set_ecology(p->view(), *p->host_prm, eco);
+}
+
+int spg_step_generations(spg_pop *p, uint32_t n_gen) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    return enqueue_generations(p->gl, n_gen, p->chain, p->stream);
+}
+
+int spg_read_stats(spg_pop *p, uint32_t first_gen, uint32_t count, spg_stats *out) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    return view_read_stats(p->view(), first_gen, count, out);
+}
+
+int spg_read_genotypes(spg_pop *p, uint32_t *host, size_t n_words) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    return view_read_genotypes(p->view(), host, n_words);
+}
+
+int spg_read_survivors(spg_pop *p, uint32_t *host, size_t capacity, uint32_t *S) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    return view_read_survivors(p->view(), host, capacity, S);
+}
+
+int spg_get_state(spg_pop *p, spg_state *out) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    return view_get_state(p->view(), out);
+}
+
+int spg_checkpoint_size(spg_pop *p, size_t *bytes) {
+    if (!p || !bytes) return fail(SPG_ERR_INVALID, "NULL argument");
+    *bytes = sizeof(CheckpointHeader) + (size_t)p->n * 2 * p->words * 4 + (size_t)p->n * 4;
+    return SPG_OK;
+}
+
+int spg_checkpoint(spg_pop *p, void *host, size_t capacity) {
+    size_t need = 0;
+    int rc = spg_checkpoint_size(p, &need);
+    if (rc != SPG_OK) return rc;
+    if (!host || capacity < need) return fail(SPG_ERR_INVALID, "checkpoint buffer too small (need %zu)", need);
+    DevState st;
+    rc = view_state(p->view(), st);
+    if (rc != SPG_OK) return rc;
+    CheckpointHeader h{};
+    h.magic = kCheckpointMagic;
+    h.version = SPG_ABI_VERSION;
+    h.n = p->n;
+    h.n_loci = p->n_loci;
+    h.gen = st.gen;
+    h.S = st.S;
+    h.status = st.status;
+    h.f = st.f;
+    h.R = st.R;
+    h.seed = p->seed;
+    h.replicate = p->rep;
+    char *dst = static_cast<char *>(host);
+    std::memcpy(dst, &h, sizeof h);
+    const size_t gbytes = (size_t)p->n * 2 * p->words * 4;
+    cudaError_t e = cudaMemcpy(dst + sizeof h, p->arena + ((st.gen & 1u) ? p->L.geno1 : p->L.geno0), gbytes,
+                               cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dst + sizeof h + gbytes, p->arena + ((st.gen & 1u) ? p->L.surv1 : p->L.surv0),
+                       (size_t)st.S * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "checkpoint copy");
+}
+
+int spg_restore(spg_pop *p, const void *host, size_t bytes) {
+    size_t need = 0;
+    int rc = spg_checkpoint_size(p, &need);
+    if (rc != SPG_OK) return rc;
+    if (!host || bytes < sizeof(CheckpointHeader)) return fail(SPG_ERR_INVALID, "checkpoint too small");
+    CheckpointHeader h;
+    std::memcpy(&h, host, sizeof h);
+    if (h.magic != kCheckpointMagic || h.n != p->n || h.n_loci != p->n_loci || h.S > p->n || bytes < need)
+        return fail(SPG_ERR_INVALID, "checkpoint does not match this population");
+    if ((h.S == 0) != (h.status == SPG_EXTINCT) || h.status < 0)
+        return fail(SPG_ERR_INVALID, "checkpoint state is inconsistent");
+    const char *src = static_cast<const char *>(host);
+    const size_t gbytes = (size_t)p->n * 2 * p->words * 4;
+    {
+        // survivors index parent records: strictly increasing and < n
+        const uint32_t *sv = reinterpret_cast<const uint32_t *>(src + sizeof h + gbytes);
+        uint32_t prev = 0;
+        for (uint32_t i = 0; i < h.S; ++i) {
+            uint32_t v;
+            std::memcpy(&v, sv + i, 4);
+            if (v >= p->n || (i > 0 && v <= prev)) return fail(SPG_ERR_INVALID, "checkpoint survivor list is invalid");
+            prev = v;
+        }
+    }
+    rc = view_sync(p->view());
+    if (rc != SPG_OK) return rc;
+    cudaError_t e = cudaMemcpy(p->arena + ((h.gen & 1u) ? p->L.geno1 : p->L.geno0), src + sizeof h, gbytes,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->arena + ((h.gen & 1u) ? p->L.surv1 : p->L.surv0), src + sizeof h + gbytes,
+                       (size_t)h.S * 4, cudaMemcpyHostToDevice);
+    // per-bucket survivor counts of the replaced run must not leak into the
+    // generations about to be replayed
+    if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "restore copy");
+    rc = view_set_state(p->view(), h.gen, h.S, h.f, h.R, h.status);
+    if (rc != SPG_OK) return rc;
+    return view_sync(p->view());
+}
+
+int spg_set_tiling(spg_pop *p, uint32_t items) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    if (!supported_items(p->words, items))
+        return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (1 or 2 for 256 loci); got %u", items);
+    const int rc = view_sync(p->view());
+    if (rc != SPG_OK) return rc;
+    return configure_launch(p, items);
+}
+
+int spg_get_tiling(spg_pop *p, uint32_t *items) {
+    if (!p || !items) return fail(SPG_ERR_INVALID, "NULL argument");
+    *items = p->items;
+    return SPG_OK;
+}
+
+int spg_synchronize(spg_pop *p) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    return view_sync(p->view());
+}
+
+void spg_destroy(spg_pop *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    p->chain.reset();
+    if (p->arena) p->alloc.release(p->arena, p->stream);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    delete p->host_prm;
+    delete p;
+}
+
+}  // extern "C"

@@ -35,6 +35,14 @@ struct PopLayout {
     size_t params, state, acc, geno0, geno1, surv0, surv1, alive, buckets, ring, segment, total;
 };
 
+// One population's device memory: its arena, layout and sizes.
+struct PopView {
+    char *base = nullptr;
+    PopLayout L{};
+    uint32_t n = 0, words = 0, cap = 0, nbuckets = 0;
+    cudaStream_t stream = nullptr;
+};
+
 // The two launches of one generation for a launch group.
 struct GenLaunch {
     OffspringKernel offspring;
@@ -68,6 +76,16 @@ Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, 
 uint32_t bucket_count(uint32_t n);
 uint32_t default_items(uint32_t words);
 int launch_generation(const GenLaunch &gl, cudaStream_t stream);
+int view_sync(const PopView &v);
+int view_state(const PopView &v, DevState &st);
+int view_set_state(const PopView &v, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status);
+int view_init(const PopView &v, const PopParams &prm, const uint32_t *init_genotypes, uint32_t p0_q32);
+int check_ecology(const spg_ecology *eco);
+int view_set_ecology(const PopView &v, PopParams &prm, const spg_ecology *eco);
+int view_read_stats(const PopView &v, uint32_t first_gen, uint32_t count, spg_stats *out);
+int view_read_genotypes(const PopView &v, uint32_t *host, size_t n_words);
+int view_read_survivors(const PopView &v, uint32_t *host, size_t capacity, uint32_t *S);
+int view_get_state(const PopView &v, spg_state *out);
 int enqueue_generations(const GenLaunch &gl, uint32_t n_gen, GraphChain &chain, cudaStream_t stream);
 
 }  // namespace spg

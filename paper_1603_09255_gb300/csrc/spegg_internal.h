@@ -83,7 +83,9 @@ struct alignas(16) Segment {
 };
 
 struct GenArgs {
-    const Segment *segs;   // device array of nsegs segments (used when nsegs > 1)
+    const Segment *segs;         // device array of nsegs segments (used when nsegs > 1)
+    const uint32_t *tile_seg;    // segment of each launch-wide tile (nsegs > 1)
+    const uint32_t *bucket_seg;  // segment of each launch-wide bucket (nsegs > 1)
     uint32_t nsegs;
     uint32_t total_tiles;
     uint32_t total_buckets;

@@ -99,6 +99,22 @@ _SIGNATURES = {
     "spg_mutation_cdf": ([ctypes.c_double, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_uint32),
     "spg_set_tiling": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
     "spg_generation_noalloc": ([ctypes.POINTER(spg_noalloc_generation), ctypes.c_void_p], ctypes.c_int),
+    "spg_batch_create": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(spg_allocator), ctypes.c_void_p,
+                          ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "spg_batch_set_ecology": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(spg_ecology)], ctypes.c_int),
+    "spg_batch_step": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "spg_batch_set_tiling": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32], ctypes.c_int),
+    "spg_batch_get_tiling": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "spg_batch_autotune": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "spg_batch_read_stats": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p],
+                             ctypes.c_int),
+    "spg_batch_read_genotypes": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "spg_batch_read_survivors": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t,
+                                  ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "spg_batch_get_state": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(spg_state)], ctypes.c_int),
+    "spg_batch_synchronize": ([ctypes.c_void_p], ctypes.c_int),
+    "spg_batch_size": ([ctypes.c_void_p], ctypes.c_uint32),
+    "spg_batch_destroy": ([ctypes.c_void_p], None),
     "spg_get_tiling": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
 }
 
@@ -268,6 +284,97 @@ class Population:
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().spg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _desc_for(w, keep: list, stats_capacity: int = 0) -> spg_pop_desc:
+    e = np.ascontiguousarray(w.effects, dtype=np.int16)
+    t = _u32(w.surv_table)
+    g = None if w.init_genotypes is None else _u32(w.init_genotypes).reshape(-1)
+    keep.extend([e, t, g])
+    return spg_pop_desc(int(w.n), int(w.n_loci), int(w.seed), int(w.replicate), e.ctypes.data,
+                        None if g is None else g.ctypes.data, int(w.p0_q32), t.ctypes.data, int(w.bias),
+                        int(w.shift), float(w.mu), int(stats_capacity))
+
+
+class Batch:
+    """Independent populations advanced by shared launches (spg_batch_*)."""
+
+    def __init__(self, workloads, stats_capacity: int = 0, stream=None, allocator: Optional[TorchAllocator] = None):
+        L = lib()
+        keep = []
+        descs = (spg_pop_desc * len(workloads))(*[_desc_for(w, keep, stats_capacity) for w in workloads])
+        self.workloads = list(workloads)
+        self.allocator = allocator if allocator is not None else TorchAllocator()
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        check(L.spg_batch_create(descs, len(workloads), ctypes.byref(self.allocator.struct), self._stream,
+                                 ctypes.byref(h)), "spg_batch_create")
+        self._h = h
+        for i, w in enumerate(workloads):
+            if w.has_ecology:
+                a = _u32(w.attack)
+                eco = spg_ecology(float(w.eco_r), float(w.eco_K), float(w.eco_R0), float(w.eco_R_half),
+                                  a.ctypes.data)
+                check(L.spg_batch_set_ecology(self._h, i, ctypes.byref(eco)), "spg_batch_set_ecology")
+
+    def __len__(self):
+        return int(lib().spg_batch_size(self._h))
+
+    def step(self, n_gen: int) -> None:
+        check(lib().spg_batch_step(self._h, int(n_gen)), "spg_batch_step")
+
+    def set_tiling(self, n_loci: int, items: int) -> None:
+        check(lib().spg_batch_set_tiling(self._h, int(n_loci), int(items)), "spg_batch_set_tiling")
+
+    def tiling(self, n_loci: int) -> int:
+        v = ctypes.c_uint32()
+        check(lib().spg_batch_get_tiling(self._h, int(n_loci), ctypes.byref(v)), "spg_batch_get_tiling")
+        return v.value
+
+    def autotune(self, gens_per_trial: int) -> int:
+        ran = ctypes.c_uint32()
+        check(lib().spg_batch_autotune(self._h, int(gens_per_trial), ctypes.byref(ran)), "spg_batch_autotune")
+        return ran.value
+
+    def read_stats(self, member: int, first_gen: int, count: int) -> np.ndarray:
+        out = np.zeros(max(int(count), 1), STATS_DTYPE)
+        check(lib().spg_batch_read_stats(self._h, int(member), int(first_gen), int(count), out.ctypes.data),
+              "spg_batch_read_stats")
+        return out[:count]
+
+    def genotypes(self, member: int) -> np.ndarray:
+        w = self.workloads[member]
+        out = np.zeros((w.n, 2 * (w.n_loci // 32)), np.uint32)
+        check(lib().spg_batch_read_genotypes(self._h, int(member), out.ctypes.data, out.size),
+              "spg_batch_read_genotypes")
+        return out
+
+    def survivors(self, member: int) -> np.ndarray:
+        S = ctypes.c_uint32(0)
+        w = self.workloads[member]
+        out = np.zeros(max(w.n, 1), np.uint32)
+        check(lib().spg_batch_read_survivors(self._h, int(member), out.ctypes.data, out.size, ctypes.byref(S)),
+              "spg_batch_read_survivors")
+        return out[:S.value]
+
+    def state(self, member: int) -> dict:
+        s = spg_state()
+        check(lib().spg_batch_get_state(self._h, int(member), ctypes.byref(s)), "spg_batch_get_state")
+        return {"gen": s.gen, "S": s.S, "status": s.status, "R": s.R, "f": s.f}
+
+    def synchronize(self) -> None:
+        check(lib().spg_batch_synchronize(self._h), "spg_batch_synchronize")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().spg_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

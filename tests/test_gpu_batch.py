@@ -1,0 +1,108 @@
+"""Batched replicates (spg_batch_*) through the C ABI: every member equals
+the same population stepped alone (and, for a sample, the CPU oracle) bit for
+bit; the launch-shape autotuner and tilings never change results."""
+import numpy as np
+import pytest
+
+import oracle
+import spegg_synth as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_09255_gb300 import build
+    build.build()
+
+
+def sp():
+    from paper_1603_09255_gb300 import spegg
+    return spegg
+
+
+def mixed_workloads(count=24, seed=7):
+    rng = np.random.default_rng(seed)
+    out = []
+    sizes = [1, 2, 33, 255, 1000, 1025, 4096, 4097, 9001, 30000]
+    for r in range(count):
+        n = sizes[r % len(sizes)] if r < len(sizes) else int(rng.integers(100, 40000))
+        L = [32, 64, 128, 256][r % 4]
+        s = float(rng.uniform(0.0, 2.0))
+        if r % 5 == 3:
+            w = S.consumer_resource(n=n, n_loci=L, mu=1e-3, s=s, K=max(4.0 * n, 100.0), seed=11, replicate=r,
+                                    effects_seed=100 + r)
+        else:
+            w = S.single_species(n=n, n_loci=L, mu=1e-3, s=s, seed=11, replicate=r, effects_seed=100 + r)
+        if r % 7 == 2:
+            w.surv_table = S.constant_table(0)  # goes extinct in its first generation
+        out.append(w)
+    return out
+
+
+def assert_member_equals(batch, i, ref_stats, ref_geno, ref_surv, ref_state):
+    st = batch.state(i)
+    assert {k: st[k] for k in ("gen", "S", "status", "f", "R")} == \
+        {k: ref_state[k] for k in ("gen", "S", "status", "f", "R")}, i
+    got = batch.read_stats(i, 1, st["gen"]) if st["gen"] else np.zeros(0, sp().STATS_DTYPE)
+    assert got.tobytes() == ref_stats.tobytes(), i
+    assert np.array_equal(batch.genotypes(i), ref_geno), i
+    assert np.array_equal(batch.survivors(i), ref_surv), i
+
+
+def test_batch_members_equal_standalone_populations():
+    ws = mixed_workloads()
+    n_gen = 40  # one cached 32-generation graph and an 8-generation remainder
+    b = sp().Batch(ws, stats_capacity=64)
+    b.step(n_gen)
+    for i, w in enumerate(ws):
+        p = sp().Population.from_workload(w, stats_capacity=64)
+        p.step(n_gen)
+        st = p.state()
+        ref = p.read_stats(1, st["gen"]) if st["gen"] else np.zeros(0, sp().STATS_DTYPE)
+        assert_member_equals(b, i, ref, p.genotypes(), p.survivors(), st)
+        p.close()
+
+
+@pytest.mark.parametrize("member", [0, 3, 5, 8, 13])
+def test_batch_members_equal_oracle(member):
+    ws = mixed_workloads()
+    b = sp().Batch(ws, stats_capacity=16)
+    b.step(6)
+    w = ws[member]
+    orc = oracle.OraclePopulation.from_workload(w)
+    so = orc.step(6)
+    st = orc.state()
+    assert_member_equals(b, member, so, orc.genotypes(), orc.survivors(), st)
+
+
+def test_autotune_and_tiling_do_not_change_results():
+    ws = mixed_workloads(12, seed=3)
+    a = sp().Batch(ws, stats_capacity=64)
+    ran = a.autotune(2)
+    assert ran == 6
+    for L in (32, 64, 128, 256):
+        assert a.tiling(L) in ((1, 2) if L == 256 else (1, 2, 4))
+    a.step(30)
+    b = sp().Batch(ws, stats_capacity=64)
+    b.set_tiling(64, 4)
+    b.step(ran + 5)
+    b.set_tiling(64, 1)
+    b.set_tiling(128, 4)
+    b.step(25)
+    for i in range(len(ws)):
+        st = a.state(i)
+        ref = b.read_stats(i, 1, st["gen"]) if st["gen"] else np.zeros(0, sp().STATS_DTYPE)
+        assert_member_equals(a, i, ref, b.genotypes(i), b.survivors(i), b.state(i))
+
+
+def test_batch_rejects_invalid_member():
+    ws = mixed_workloads(4)
+    ws[2].n_loci = 48
+    with pytest.raises(sp().SpeggError) as e:
+        sp().Batch(ws)
+    assert "member 2" in str(e.value)
