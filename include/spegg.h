@@ -186,7 +186,7 @@ int spg_checkpoint(spg_pop *pop, void *host, size_t capacity);
 int spg_restore(spg_pop *pop, const void *host, size_t bytes);
 
 /* Offspring per thread of the generation kernel (1, 2 or 4; 1 or 2 for
- * L = 256; default 4 for L <= 64, else 2).  A launch-shape choice only: every
+ * L = 256; default 1).  A launch-shape choice only: every
  * setting gives identical results.  Waits for the stream. */
 int spg_set_tiling(spg_pop *pop, uint32_t items_per_thread);
 int spg_get_tiling(spg_pop *pop, uint32_t *items_per_thread);

@@ -191,7 +191,7 @@ Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, 
     return s;
 }
 
-uint32_t default_items(uint32_t words) { return words >= 4 ? 2u : 4u; }
+uint32_t default_items(uint32_t words) { (void)words; return 1u; }
 
 GraphChain::~GraphChain() { reset(); }
 

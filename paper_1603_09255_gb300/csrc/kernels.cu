@@ -341,20 +341,28 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Shared-memory staging of parent records: per stage, item, parent (0
-// mother, 1 father) and chunk q, one chunk per thread, chunks of consecutive
-// threads adjacent (conflict-free 8/16-byte accesses).  A thread only ever
-// reads the chunks it copied itself.
+// Shared-memory staging of parent records: a ring of kStages stages; per
+// stage, item, parent (0 mother, 1 father) and chunk q one chunk per thread,
+// chunks of consecutive threads adjacent (conflict-free 8/16-byte accesses),
+// followed by each item's survival and mutation-count draws.  A thread only
+// ever reads the slots it wrote itself, so the ring needs no block barrier.
 template <int W, int ITEMS>
 struct Staging {
     static constexpr int kChunkBytes = (W == 1) ? 8 : 16;
     static constexpr int kChunks = (W == 1) ? 1 : W / 2;  // per record
-    static constexpr uint32_t kStageBytes = (uint32_t)ITEMS * 2u * kChunks * kBlock * kChunkBytes;
-    static constexpr uint32_t kBytes = 2u * kStageBytes;
+    static constexpr uint32_t kRecBytes = (uint32_t)ITEMS * 2u * kChunks * kBlock * kChunkBytes;
+    static constexpr uint32_t kDrawBytes = (uint32_t)ITEMS * kBlock * 8u;
+    static constexpr uint32_t kStageBytes = kRecBytes + kDrawBytes;
+    // as many stages (2..4) as fit in ~110 KB, so two blocks share an SM
+    static constexpr int kStages = (4u * kStageBytes <= 112640u) ? 4 : (3u * kStageBytes <= 112640u) ? 3 : 2;
+    static constexpr uint32_t kBytes = (uint32_t)kStages * kStageBytes;
     __device__ static __forceinline__ uint32_t offset(int stage, int it, int parent, int q, int tid) {
         return (uint32_t)stage * kStageBytes +
                ((((uint32_t)it * 2u + (uint32_t)parent) * kChunks + (uint32_t)q) * kBlock + (uint32_t)tid) *
                    kChunkBytes;
+    }
+    __device__ static __forceinline__ uint32_t draw_offset(int stage, int it, int tid) {
+        return (uint32_t)stage * kStageBytes + kRecBytes + ((uint32_t)it * kBlock + (uint32_t)tid) * 8u;
     }
 };
 
@@ -395,7 +403,7 @@ __device__ __forceinline__ void draw_parents(const SegCtx &c, uint32_t base, int
 
 template <int W, int ITEMS>
 __device__ __forceinline__ void stage_parents(const SegCtx &c, uint32_t base, int tid, const TileDraws<ITEMS> &d,
-                                              uint32_t s_base, int stage) {
+                                              unsigned char *s_dyn, uint32_t s_base, int stage) {
     using St = Staging<W, ITEMS>;
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
@@ -411,9 +419,10 @@ __device__ __forceinline__ void stage_parents(const SegCtx &c, uint32_t base, in
                     else cp_async_16(sa, src + 4 * q);
                 }
             }
+            *reinterpret_cast<uint2 *>(s_dyn + St::draw_offset(stage, it, tid)) =
+                make_uint2(d.u_surv[it], d.u_mut[it]);
         }
     }
-    cp_async_commit();
 }
 
 template <int W, int ITEMS>
@@ -446,16 +455,17 @@ struct ThreadStats {
 // One tile: gametes (B), phenotype (C), survival (D), bitmap (E, first half).
 template <int W, int ITEMS>
 __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t base, int tid, int lane, int warp,
-                                                   const unsigned char *s_dyn, int stage, const uint32_t *u_surv,
-                                                   const uint32_t *u_mut, const uint32_t *s_planes,
+                                                   const unsigned char *s_dyn, int stage, const uint32_t *s_planes,
                                                    const uint32_t *s_cdf, ThreadStats &ts) {
     constexpr int NW = kBlock / 32;
-    uint32_t alive_count = 0;  // meaningful in lane 0
+    using St = Staging<W, ITEMS>;
+    uint32_t alive_count = 0;  // the warp's survivors (same in every lane)
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
         const uint32_t j = base + (uint32_t)(it * kBlock + tid);
         bool alive = false;
         if (j < c.n) {
+            const uint2 u = *reinterpret_cast<const uint2 *>(s_dyn + St::draw_offset(stage, it, tid));
             uint32_t pm[2 * W], pf[2 * W], ch[2 * W];
             read_parent<W, ITEMS>(s_dyn, stage, it, 0, tid, pm);
             read_parent<W, ITEMS>(s_dyn, stage, it, 1, tid, pf);
@@ -476,7 +486,7 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
             }
             // (B) mutation count from the CDF, positions on the rare path
             uint32_t k = 0;
-            for (uint32_t i = 0; i < c.kmax; ++i) k += (u_mut[it] >= s_cdf[i]) ? 1u : 0u;
+            for (uint32_t i = 0; i < c.kmax; ++i) k += (u.y >= s_cdf[i]) ? 1u : 0u;
             if (k != 0u) mutate<W>(ch, k, j, c.g, c.rep, c.k0, c.k1);
             store_record<W>(c.chi + (size_t)j * (2 * W), ch);
 
@@ -487,7 +497,7 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
             const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> c.shift, (long long)(kBins - 1));
             uint32_t thr = __ldg(&c.P->table[bin]);
             if (c.f != kCertain) thr = __umulhi(thr, c.f);
-            alive = (thr == kCertain) || (u_surv[it] < thr);
+            alive = (thr == kCertain) || (u.x < thr);
 
             ts.sum_raw += raw;
             ts.sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
@@ -566,27 +576,33 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
             ThreadStats ts;
             uint32_t warp_alive = 0, bucket_alive = 0, bucket_cur = (lt0 * TILE) / kBucket;
 
-            // software pipeline: draws two tiles ahead, staged records one ahead
-            TileDraws<ITEMS> d1, d2;
-            draw_parents<ITEMS>(c, lt0 * TILE, tid, d1);
-            stage_parents<W, ITEMS>(c, lt0 * TILE, tid, d1, s_base, 0);
-            uint32_t cur_surv[ITEMS], cur_mut[ITEMS];
-#pragma unroll
-            for (int it = 0; it < ITEMS; ++it) {
-                cur_surv[it] = d1.u_surv[it];
-                cur_mut[it] = d1.u_mut[it];
-            }
-            if (lt0 + 1 < lt1) draw_parents<ITEMS>(c, (lt0 + 1) * TILE, tid, d1);
-            for (uint32_t lt = lt0; lt < lt1; ++lt) {
-                const int stage = (int)((lt - lt0) & 1u);
-                const uint32_t base = lt * TILE;
-                if (lt + 1 < lt1) {
-                    stage_parents<W, ITEMS>(c, base + TILE, tid, d1, s_base, stage ^ 1);
-                    if (lt + 2 < lt1) draw_parents<ITEMS>(c, base + 2 * TILE, tid, d2);
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
+            // software pipeline over the block's tiles: parent records (and
+            // each item's draws) are staged kStages-1 tiles ahead; survivor
+            // indices are fetched two iterations before they are staged.
+            // Every iteration commits one cp.async group (empty near the end),
+            // so waiting for all but the newest R groups completes tile lt's.
+            using St = Staging<W, ITEMS>;
+            constexpr int R = St::kStages - 1;
+            TileDraws<ITEMS> dA, dB;
+            for (int k = 0; k < R; ++k) {
+                const uint32_t tk = lt0 + (uint32_t)k;
+                if (tk < lt1) {
+                    draw_parents<ITEMS>(c, tk * TILE, tid, dA);
+                    stage_parents<W, ITEMS>(c, tk * TILE, tid, dA, s_dyn, s_base, k);
                 }
+                cp_async_commit();
+            }
+            if (lt0 + R < lt1) draw_parents<ITEMS>(c, (lt0 + R) * TILE, tid, dA);
+            if (lt0 + R + 1 < lt1) draw_parents<ITEMS>(c, (lt0 + R + 1) * TILE, tid, dB);
+            int stage = 0;
+            for (uint32_t lt = lt0; lt < lt1; ++lt) {
+                const uint32_t base = lt * TILE;
+                const int ahead = stage == 0 ? R : stage - 1;  // (stage + R) % kStages
+                if (lt + R < lt1) stage_parents<W, ITEMS>(c, base + R * TILE, tid, dA, s_dyn, s_base, ahead);
+                cp_async_commit();
+                dA = dB;
+                if (lt + R + 2 < lt1) draw_parents<ITEMS>(c, base + (R + 2) * TILE, tid, dB);
+                cp_async_wait<R>();
                 if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
                 const uint32_t bkt = base / kBucket;
                 if (bkt != bucket_cur) {
@@ -594,17 +610,13 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
                     bucket_alive = 0;
                     bucket_cur = bkt;
                 }
-                const uint32_t cnt = offspring_tile<W, ITEMS>(c, base, tid, lane, warp, s_dyn, stage, cur_surv,
-                                                              cur_mut, s_planes, s_cdf, ts);
+                const uint32_t cnt =
+                    offspring_tile<W, ITEMS>(c, base, tid, lane, warp, s_dyn, stage, s_planes, s_cdf, ts);
                 bucket_alive += cnt;
                 warp_alive += cnt;
-#pragma unroll
-                for (int it = 0; it < ITEMS; ++it) {
-                    cur_surv[it] = d1.u_surv[it];
-                    cur_mut[it] = d1.u_mut[it];
-                }
-                d1 = d2;
+                stage = stage + 1 == St::kStages ? 0 : stage + 1;
             }
+            cp_async_wait<0>();
             if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
 
             // statistics of this block's tiles: exact warp sums, one atomic
