@@ -155,6 +155,52 @@ def bench_config(w, l2):
             "n": w.n, "n_loci": w.n_loci, "generations_per_step": GENERATIONS, "l2": l2}
 
 
+def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, plain_gens: int = 32):
+    """Batched-replicates workload: 4,096 independent single-species runs (N
+    log-uniform in [1e3, 2e5], L in {32, 64, 128}, s in [0, 0.5]) advanced by
+    shared, graph-captured launches with autotuned tilings, against the plain
+    path (one population at a time) timed on the first `plain_members`."""
+    ws = S.batch_replicates(count=4096, n_gen=gens)
+    stream = torch.cuda.Stream()
+    batch = spegg.Batch(ws, stats_capacity=gens + 64, stream=stream)
+    ran = batch.autotune(2)
+    batch.step(32)
+    batch.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+    batch.step(gens)
+    with torch.cuda.stream(stream):
+        b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b)
+    sum_n = sum(w.n for w in ws)
+    tilings = {str(L): batch.tiling(L) for L in (32, 64, 128)}
+    batch.close()
+    pops = [spegg.Population.from_workload(ws[i], stats_capacity=64, stream=stream) for i in range(plain_members)]
+    for p in pops:
+        p.step(1)
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+    for p in pops:
+        p.step(plain_gens)
+    with torch.cuda.stream(stream):
+        b.record(stream)
+    stream.synchronize()
+    ms_plain = a.elapsed_time(b)
+    plain = sum(ws[i].n for i in range(plain_members)) * plain_gens / (ms_plain / 1e3)
+    for p in pops:
+        p.close()
+    value = sum_n * gens / (ms / 1e3)
+    return {"workload": f"4096 replicates, N log-uniform [1e3, 2e5] (sum {sum_n}), L in {{32, 64, 128}}, "
+                        f"s in [0, 0.5], {gens} generations timed after {ran + 32}",
+            "value": value, "unit": "individual-generations/s", "ms": ms, "tilings": tilings,
+            "plain_value": plain, "plain_sample": f"first {plain_members} replicates, {plain_gens} generations, "
+                                                  "one population stepped at a time",
+            "speedup_vs_plain": value / plain}
+
+
 def cpu_baseline(workload, target_seconds=12.0):
     import oracle
     pop = oracle.OraclePopulation.from_workload(workload)
@@ -175,7 +221,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="omit the CPU oracle baseline measurement")
+    ap.add_argument("--no-batched", action="store_true", help="omit the batched-replicates measurement")
     args = ap.parse_args()
     workload = S.consumer_resource()
     if args.impl == "reference":
@@ -230,7 +277,8 @@ def main():
     ind_gen = workload.n * GENERATIONS * args.steps
     value = ind_gen * ws / (total_ms / 1000.0)
 
-    # dominant kernel: the fused generation kernel, one launch per generation
+    # each generation is one offspring launch and one compaction launch; the
+    # offspring kernel dominates, the pair is timed together
     launches = GENERATIONS * args.steps
     avg_launch_s = total_ms / 1000.0 / launches
     peak, peak_kind = load_peaks()
@@ -266,6 +314,7 @@ def main():
     e2e_value = workload.n * GENERATIONS * ws / (sum(e2e_times) / len(e2e_times))
     assert len(stats) == GENERATIONS
 
+    batched = None if args.no_batched else batched_replicates(spegg, torch)
     if rank != 0:
         return
     line = {
@@ -276,14 +325,16 @@ def main():
         "config": bench_config(workload, "flushed before every step (256 MB write)"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": f"k_generation<W={workload.words}> (fused generation)",
+                     "kernel": f"k_offspring<W={workload.words}> + k_compact (one generation)",
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6,
                      "isolated_launch_us": kernel_ms * 1000.0},
         "e2e": {"value": e2e_value, "unit": "individual-generations/s", "h2d_bytes_per_step": len(blob),
                 "d2h_bytes_per_step": int(stats.nbytes)},
-        "gpu_launches": launches,
+        "gpu_launches": 2 * launches,
         "clocks": clocks.summary(),
     }
+    if batched is not None:
+        line["batched"] = batched
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload)
     print(json.dumps(line))
