@@ -224,6 +224,66 @@ int spg_batch_synchronize(spg_batch *batch);
 uint32_t spg_batch_size(const spg_batch *batch);
 void spg_batch_destroy(spg_batch *batch);
 
+/* ---- Served jobs (continuous batching) -------------------------------------
+ * Jobs -- one population each, with its own generation count -- arrive over
+ * time.  Each scheduling tick retires the resident jobs that reached their
+ * generation count (their statistics are kept in host memory, their device
+ * memory is freed), admits queued jobs in arrival order while a resident slot
+ * is free and the job's device footprint fits the memory budget, and advances
+ * every resident job by up to gens_per_tick generations in shared launches
+ * (jobs of different lengths and locus counts run together; each stops at its
+ * own count).  A job's results are identical to the same population run
+ * alone.  Times are seconds on the server's clock (spg_server_clock). */
+#define SPG_JOB_QUEUED 0u
+#define SPG_JOB_RESIDENT 1u
+#define SPG_JOB_FINISHED 2u
+
+typedef struct spg_server spg_server;
+
+typedef struct {
+    size_t memory_budget;     /* device bytes for resident jobs (0: 80% of free memory) */
+    uint32_t max_resident;    /* resident job slots (0: 1024)                          */
+    uint32_t gens_per_tick;   /* generations advanced per tick (0: 16)                 */
+} spg_server_config;
+
+typedef struct {
+    uint64_t job;
+    uint32_t state;           /* SPG_JOB_QUEUED / RESIDENT / FINISHED */
+    uint32_t gen;             /* generations completed (enqueued while resident) */
+    int32_t status;           /* SPG_OK or SPG_EXTINCT once finished */
+    uint32_t n_gen;           /* requested generations */
+    double t_arrival, t_admit, t_finish;   /* -1 until reached */
+    size_t footprint;         /* device bytes while resident */
+} spg_job_info;
+
+typedef struct {
+    uint64_t submitted, queued, resident, peak_resident;
+    size_t memory_budget, memory_used, peak_memory_used;
+} spg_server_counters;
+
+int spg_server_create(const spg_server_config *cfg, const spg_allocator *alloc, void *stream, spg_server **out);
+/* Queue a job (the description, founders and ecology are copied).  t_arrival
+ * is recorded for latency.  SPG_ERR_BUDGET if the job alone exceeds the budget. */
+int spg_server_submit(spg_server *server, const spg_pop_desc *desc, const spg_ecology *eco, uint32_t n_gen,
+                      double t_arrival, uint64_t *job);
+/* One scheduling tick (waits for its generations); reports resident and queued jobs. */
+int spg_server_tick(spg_server *server, uint32_t *resident, uint32_t *queued);
+/* Tick until every submitted job has finished. */
+int spg_server_drain(spg_server *server);
+/* Replay an arrival trace: job i is submitted once arrivals[i] seconds have
+ * passed since the call started (ecos[i] applies where has_eco[i] != 0; both
+ * may be NULL), ticking in between, until every job has finished; jobs[i]
+ * receives job i's id. */
+int spg_server_run_trace(spg_server *server, const spg_pop_desc *descs, const spg_ecology *ecos,
+                         const uint8_t *has_eco, const uint32_t *n_gen, const double *arrivals, uint32_t count,
+                         uint64_t *jobs);
+int spg_server_job_info(spg_server *server, uint64_t job, spg_job_info *out);
+/* Statistics of a finished job (generations first_gen .. first_gen+count-1). */
+int spg_server_job_stats(spg_server *server, uint64_t job, uint32_t first_gen, uint32_t count, spg_stats *out);
+int spg_server_stats(spg_server *server, spg_server_counters *out);
+double spg_server_clock(spg_server *server);
+void spg_server_destroy(spg_server *server);
+
 /* ---- One generation without any device allocation -----------------------
  * The paper has no counterpart to this call; it exists for callers that may
  * not allocate device memory: code that runs while a CUDA stream is being

@@ -34,9 +34,7 @@ struct Member {
 struct Group {
     uint32_t words = 0, items = 0;
     std::vector<uint32_t> members;
-    size_t segs_off = 0, tile_map_off = 0, bucket_map_off = 0;  // in the batch arena
-    uint32_t max_tiles = 0;                                     // tile map capacity (items = 1)
-    uint32_t total_buckets = 0;
+    size_t table_off = 0, table_bytes = 0;  // launch table in the batch arena (sized for items = 1)
     GenLaunch gl;
 };
 
@@ -104,48 +102,16 @@ struct spg_batch {
 
 namespace {
 
-// (Re)build a group's segment table and maps for `items` offspring per
-// thread; uploads them (synchronous).
+// (Re)build a group's launch table for `items` offspring per thread
+// (synchronous upload).
 int configure_group(spg_batch *b, Group &g, uint32_t items) {
     if (g.members.empty()) return SPG_OK;
-    OffspringKernel k = offspring_kernel(g.words, items);
-    int rc = prepare_offspring(k);
-    if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
-    std::vector<Segment> segs;
-    std::vector<uint32_t> tile_map, bucket_map;
-    segs.reserve(g.members.size());
-    uint32_t tiles = 0, buckets = 0;
-    for (uint32_t si = 0; si < g.members.size(); ++si) {
-        Member &m = b->members[g.members[si]];
-        const uint32_t nt = (m.v.n + tile_size(items) - 1) / tile_size(items);
-        m.prm->ntiles = nt;
-        segs.push_back(segment_at(m.v.base, m.v.L, m.v.n, nt, tiles, m.v.nbuckets, buckets));
-        tile_map.insert(tile_map.end(), nt, si);
-        bucket_map.insert(bucket_map.end(), m.v.nbuckets, si);
-        tiles += nt;
-        buckets += m.v.nbuckets;
-    }
-    cudaError_t e = cudaMemcpy(b->arena + g.segs_off, segs.data(), segs.size() * sizeof(Segment),
-                               cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->arena + g.tile_map_off, tile_map.data(), tile_map.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->arena + g.bucket_map_off, bucket_map.data(), bucket_map.size() * 4, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "upload segment table");
+    std::vector<const PopView *> views;
+    views.reserve(g.members.size());
+    for (uint32_t mi : g.members) views.push_back(&b->members[mi].v);
+    const int rc = build_group_launch(views, g.words, items, b->arena + g.table_off, g.table_bytes, g.gl);
+    if (rc != SPG_OK) return rc;
     g.items = items;
-    g.total_buckets = buckets;
-    g.gl.offspring = k;
-    g.gl.compact = compact_kernel();
-    g.gl.args = GenArgs{};
-    g.gl.args.segs = reinterpret_cast<const Segment *>(b->arena + g.segs_off);
-    g.gl.args.tile_seg = reinterpret_cast<const uint32_t *>(b->arena + g.tile_map_off);
-    g.gl.args.bucket_seg = reinterpret_cast<const uint32_t *>(b->arena + g.bucket_map_off);
-    g.gl.args.nsegs = (uint32_t)segs.size();
-    if (segs.size() == 1) g.gl.args.one = segs[0];
-    g.gl.args.total_tiles = tiles;
-    g.gl.args.total_buckets = buckets;
-    g.gl.blocks = std::min(tiles, k.resident);
-    g.gl.buckets = buckets;
     b->chains.clear();
     return SPG_OK;
 }
@@ -211,16 +177,12 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
         if (g.members.empty()) continue;
         uint32_t tiles = 0, buckets = 0;
         for (uint32_t mi : g.members) {
-            tiles += (b->members[mi].v.n + tile_size(1) - 1) / tile_size(1);
+            tiles += tiles_for(b->members[mi].v.n, 1);
             buckets += b->members[mi].v.nbuckets;
         }
-        g.max_tiles = tiles;
-        g.segs_off = off;
-        off = align_up(off + g.members.size() * sizeof(Segment), 256);
-        g.tile_map_off = off;
-        off = align_up(off + (size_t)tiles * 4, 256);
-        g.bucket_map_off = off;
-        off = align_up(off + (size_t)buckets * 4, 256);
+        g.table_off = off;
+        g.table_bytes = group_table_bytes((uint32_t)g.members.size(), tiles, buckets);
+        off = align_up(off + g.table_bytes, 256);
     }
     b->arena_bytes = off;
     if (alloc) b->alloc.hooks = *alloc;

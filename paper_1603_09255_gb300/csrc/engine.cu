@@ -262,6 +262,60 @@ int enqueue_generations(const GenLaunch &gl, uint32_t n_gen, GraphChain &chain, 
     return SPG_OK;
 }
 
+// ------------------------------------------------- launch groups
+size_t group_table_bytes(uint32_t members, uint32_t tiles, uint32_t buckets) {
+    return align_up((size_t)members * sizeof(Segment), 256) + align_up((size_t)tiles * 4, 256) +
+           align_up((size_t)buckets * 4, 256);
+}
+
+uint32_t tiles_for(uint32_t n, uint32_t items) { return (n + tile_size(items) - 1) / tile_size(items); }
+
+int build_group_launch(const std::vector<const PopView *> &members, uint32_t words, uint32_t items, char *table,
+                       size_t table_capacity, GenLaunch &gl) {
+    if (members.empty()) {
+        gl = GenLaunch{};
+        return SPG_OK;
+    }
+    OffspringKernel k = offspring_kernel(words, items);
+    int rc = prepare_offspring(k);
+    if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
+    std::vector<Segment> segs;
+    std::vector<uint32_t> tile_map, bucket_map;
+    segs.reserve(members.size());
+    uint32_t tiles = 0, buckets = 0;
+    for (uint32_t si = 0; si < members.size(); ++si) {
+        const PopView &v = *members[si];
+        const uint32_t nt = tiles_for(v.n, items);
+        segs.push_back(segment_at(v.base, v.L, v.n, nt, tiles, v.nbuckets, buckets));
+        tile_map.insert(tile_map.end(), nt, si);
+        bucket_map.insert(bucket_map.end(), v.nbuckets, si);
+        tiles += nt;
+        buckets += v.nbuckets;
+    }
+    if (group_table_bytes((uint32_t)segs.size(), tiles, buckets) > table_capacity)
+        return fail(SPG_ERR_INVALID, "launch table does not fit its buffer");
+    const size_t off_tiles = align_up(segs.size() * sizeof(Segment), 256);
+    const size_t off_buckets = off_tiles + align_up((size_t)tiles * 4, 256);
+    cudaError_t e = cudaMemcpy(table, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(table + off_tiles, tile_map.data(), tile_map.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(table + off_buckets, bucket_map.data(), bucket_map.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload launch table");
+    gl = GenLaunch{};
+    gl.offspring = k;
+    gl.compact = compact_kernel();
+    gl.args.segs = reinterpret_cast<const Segment *>(table);
+    gl.args.tile_seg = reinterpret_cast<const uint32_t *>(table + off_tiles);
+    gl.args.bucket_seg = reinterpret_cast<const uint32_t *>(table + off_buckets);
+    gl.args.nsegs = (uint32_t)segs.size();
+    if (segs.size() == 1) gl.args.one = segs[0];
+    gl.args.total_tiles = tiles;
+    gl.args.total_buckets = buckets;
+    gl.blocks = std::min(tiles, k.resident);
+    gl.buckets = buckets;
+    return SPG_OK;
+}
+
 // ------------------------------------------------- one population's memory
 int view_sync(const PopView &v) {
     const cudaError_t e = cudaStreamSynchronize(v.stream);
@@ -275,9 +329,10 @@ int view_state(const PopView &v, DevState &st) {
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read state");
 }
 
-int view_set_state(const PopView &v, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status) {
+int view_set_state(const PopView &v, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,
+                   uint32_t target) {
     return launch_set_state(reinterpret_cast<DevState *>(v.base + v.L.state),
-                            reinterpret_cast<StatAcc *>(v.base + v.L.acc), gen, S, f, R, status, v.stream);
+                            reinterpret_cast<StatAcc *>(v.base + v.L.acc), gen, S, f, R, status, target, v.stream);
 }
 
 // Enqueue the generation-0 set-up of one population: parameters, counters,
@@ -300,7 +355,7 @@ int view_init(const PopView &v, const PopParams &prm, const uint32_t *init_genot
         rc = launch_founders(v.words, geno0, surv0, v.n, prm.key0, prm.key1, prm.rep, p0_q32, v.stream);
     }
     if (rc != SPG_OK) return fail(rc, "founder launch failed");
-    rc = view_set_state(v, 0, v.n, kCertain, 0.0, SPG_OK);
+    rc = view_set_state(v, 0, v.n, kCertain, 0.0, SPG_OK, 0xFFFFFFFFu);
     return rc == SPG_OK ? SPG_OK : fail(rc, "state launch failed");
 }
 
@@ -329,7 +384,7 @@ int view_set_ecology(const PopView &v, PopParams &prm, const spg_ecology *eco) {
     const cudaError_t e =
         cudaMemcpyAsync(v.base + v.L.params, &prm, sizeof(PopParams), cudaMemcpyHostToDevice, v.stream);
     if (e != cudaSuccess) return cuda_fail(e, "upload parameters");
-    rc = view_set_state(v, st.gen, st.S, factor_q32_host(eco->R0, eco->R_half), eco->R0, st.status);
+    rc = view_set_state(v, st.gen, st.S, factor_q32_host(eco->R0, eco->R_half), eco->R0, st.status, st.target);
     if (rc != SPG_OK) return rc;
     return view_sync(v);
 }

@@ -324,7 +324,8 @@ __device__ __forceinline__ PopNow read_state(const DevState *st) {
     s.S = ld_relaxed_u32(&st->S);
     s.f = ld_relaxed_u32(&st->f);
     const int32_t status = (int32_t)ld_relaxed_u32(reinterpret_cast<const uint32_t *>(&st->status));
-    s.active = s.S > 0u && status == SPG_OK;
+    const uint32_t target = ld_relaxed_u32(&st->target);
+    s.active = s.S > 0u && status == SPG_OK && s.gen < target;
     return s;
 }
 
@@ -767,8 +768,9 @@ __global__ void k_iota(uint32_t *__restrict__ surv, uint32_t n) {
 }
 
 __global__ void k_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R,
-                            int32_t status) {
+                            int32_t status, uint32_t target) {
     if (threadIdx.x == 0) {
+        st->target = target;
         st->gen = gen;
         st->S = S;
         st->f = f;
@@ -847,8 +849,8 @@ int launch_iota(uint32_t *surv, uint32_t n, void *stream) {
 }
 
 int launch_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,
-                     void *stream) {
-    k_set_state<<<1, 32, 0, (cudaStream_t)stream>>>(st, acc, gen, S, f, R, status);
+                     uint32_t target, void *stream) {
+    k_set_state<<<1, 32, 0, (cudaStream_t)stream>>>(st, acc, gen, S, f, R, status, target);
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
 }
 

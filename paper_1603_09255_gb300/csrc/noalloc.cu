@@ -133,7 +133,8 @@ extern "C" int spg_generation_noalloc(const spg_noalloc_generation *a, void *str
     if (e == cudaSuccess) e = cudaMemsetAsync(scratch + kOffBuckets, 0, (size_t)2 * nbuckets * 4, s);
     if (e != cudaSuccess) return cuda_fail(e, "stage allocation-free generation");
     rc = launch_set_state(reinterpret_cast<DevState *>(scratch + kOffState),
-                          reinterpret_cast<StatAcc *>(scratch + kOffAcc), g - 1u, a->S, a->f, 0.0, SPG_OK, s);
+                          reinterpret_cast<StatAcc *>(scratch + kOffAcc), g - 1u, a->S, a->f, 0.0, SPG_OK,
+                          0xFFFFFFFFu, s);
     if (rc != SPG_OK) return fail(rc, "reset allocation-free state");
 
     GenLaunch gl;

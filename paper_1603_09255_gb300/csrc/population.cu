@@ -237,7 +237,7 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
     // generations about to be replayed
     if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4);
     if (e != cudaSuccess) return cuda_fail(e, "restore copy");
-    rc = view_set_state(p->view(), h.gen, h.S, h.f, h.R, h.status);
+    rc = view_set_state(p->view(), h.gen, h.S, h.f, h.R, h.status, 0xFFFFFFFFu);
     if (rc != SPG_OK) return rc;
     return view_sync(p->view());
 }

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "spegg.h"
 #include "spegg_internal.h"
@@ -76,9 +77,16 @@ Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, 
 uint32_t bucket_count(uint32_t n);
 uint32_t default_items(uint32_t words);
 int launch_generation(const GenLaunch &gl, cudaStream_t stream);
+size_t group_table_bytes(uint32_t members, uint32_t tiles, uint32_t buckets);
+uint32_t tiles_for(uint32_t n, uint32_t items);
+// Segment table and tile/bucket maps of one launch group, uploaded into
+// `table` (device memory; synchronous), and the group's launch description.
+int build_group_launch(const std::vector<const PopView *> &members, uint32_t words, uint32_t items, char *table,
+                       size_t table_capacity, GenLaunch &gl);
 int view_sync(const PopView &v);
 int view_state(const PopView &v, DevState &st);
-int view_set_state(const PopView &v, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status);
+int view_set_state(const PopView &v, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,
+                   uint32_t target);
 int view_init(const PopView &v, const PopParams &prm, const uint32_t *init_genotypes, uint32_t p0_q32);
 int check_ecology(const spg_ecology *eco);
 int view_set_ecology(const PopView &v, PopParams &prm, const spg_ecology *eco);

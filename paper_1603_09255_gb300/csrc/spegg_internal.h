@@ -52,7 +52,8 @@ struct alignas(16) DevState {
     int32_t status;   // SPG_OK or SPG_EXTINCT
     double R;         // resource density
     uint32_t done;    // compaction buckets of the running generation that have finished
-    uint32_t pad[3];
+    uint32_t target;  // generations stop once gen reaches target (0xFFFFFFFF: never)
+    uint32_t pad[2];
 };
 
 // Statistics of the generation being formed, accumulated by atomics; each
@@ -116,6 +117,6 @@ int launch_founders(uint32_t words, uint32_t *geno, uint32_t *surv, uint32_t n, 
 int launch_iota(uint32_t *surv, uint32_t n, void *stream);
 // Enqueue a state reset: state fields and cleared statistics accumulators.
 int launch_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,
-                     void *stream);
+                     uint32_t target, void *stream);
 
 }  // namespace spg

@@ -63,6 +63,23 @@ class spg_noalloc_generation(ctypes.Structure):
     ]
 
 
+class spg_server_config(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_size_t), ("max_resident", ctypes.c_uint32),
+                ("gens_per_tick", ctypes.c_uint32)]
+
+
+class spg_job_info(ctypes.Structure):
+    _fields_ = [("job", ctypes.c_uint64), ("state", ctypes.c_uint32), ("gen", ctypes.c_uint32),
+                ("status", ctypes.c_int32), ("n_gen", ctypes.c_uint32), ("t_arrival", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_finish", ctypes.c_double), ("footprint", ctypes.c_size_t)]
+
+
+class spg_server_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("resident", ctypes.c_uint64),
+                ("peak_resident", ctypes.c_uint64), ("memory_budget", ctypes.c_size_t),
+                ("memory_used", ctypes.c_size_t), ("peak_memory_used", ctypes.c_size_t)]
+
+
 class spg_state(ctypes.Structure):
     _fields_ = [("gen", ctypes.c_uint32), ("S", ctypes.c_uint32), ("status", ctypes.c_int32),
                 ("f", ctypes.c_uint32), ("R", ctypes.c_double)]
@@ -115,6 +132,21 @@ _SIGNATURES = {
     "spg_batch_synchronize": ([ctypes.c_void_p], ctypes.c_int),
     "spg_batch_size": ([ctypes.c_void_p], ctypes.c_uint32),
     "spg_batch_destroy": ([ctypes.c_void_p], None),
+    "spg_server_create": ([ctypes.POINTER(spg_server_config), ctypes.POINTER(spg_allocator), ctypes.c_void_p,
+                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "spg_server_submit": ([ctypes.c_void_p, ctypes.POINTER(spg_pop_desc), ctypes.POINTER(spg_ecology), ctypes.c_uint32,
+                           ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "spg_server_tick": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)],
+                        ctypes.c_int),
+    "spg_server_drain": ([ctypes.c_void_p], ctypes.c_int),
+    "spg_server_run_trace": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
+    "spg_server_job_info": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(spg_job_info)], ctypes.c_int),
+    "spg_server_job_stats": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p],
+                             ctypes.c_int),
+    "spg_server_stats": ([ctypes.c_void_p, ctypes.POINTER(spg_server_counters)], ctypes.c_int),
+    "spg_server_clock": ([ctypes.c_void_p], ctypes.c_double),
+    "spg_server_destroy": ([ctypes.c_void_p], None),
     "spg_get_tiling": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
 }
 
@@ -375,6 +407,95 @@ class Batch:
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().spg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _eco_for(w, keep: list):
+    if not w.has_ecology:
+        return None
+    a = _u32(w.attack)
+    keep.append(a)
+    return spg_ecology(float(w.eco_r), float(w.eco_K), float(w.eco_R0), float(w.eco_R_half), a.ctypes.data)
+
+
+class Server:
+    """Continuous batching of jobs (spg_server_*): jobs are admitted by device
+    footprint as they arrive and advanced together in shared launches."""
+
+    def __init__(self, memory_budget: int = 0, max_resident: int = 0, gens_per_tick: int = 0, stream=None,
+                 allocator: Optional[TorchAllocator] = None):
+        cfg = spg_server_config(int(memory_budget), int(max_resident), int(gens_per_tick))
+        self.allocator = allocator if allocator is not None else TorchAllocator()
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        check(lib().spg_server_create(ctypes.byref(cfg), ctypes.byref(self.allocator.struct), self._stream,
+                                      ctypes.byref(h)), "spg_server_create")
+        self._h = h
+
+    def submit(self, w, n_gen: int, t_arrival: Optional[float] = None) -> int:
+        keep = []
+        d = _desc_for(w, keep)
+        eco = _eco_for(w, keep)
+        job = ctypes.c_uint64()
+        t = self.clock() if t_arrival is None else float(t_arrival)
+        check(lib().spg_server_submit(self._h, ctypes.byref(d), ctypes.byref(eco) if eco is not None else None,
+                                      int(n_gen), t, ctypes.byref(job)), "spg_server_submit")
+        return job.value
+
+    def tick(self):
+        r, q = ctypes.c_uint32(), ctypes.c_uint32()
+        check(lib().spg_server_tick(self._h, ctypes.byref(r), ctypes.byref(q)), "spg_server_tick")
+        return r.value, q.value
+
+    def drain(self) -> None:
+        check(lib().spg_server_drain(self._h), "spg_server_drain")
+
+    def run_trace(self, workloads, n_gens, arrivals):
+        keep = []
+        count = len(workloads)
+        descs = (spg_pop_desc * count)(*[_desc_for(w, keep) for w in workloads])
+        ecos = (spg_ecology * count)()
+        has = np.zeros(count, np.uint8)
+        for i, w in enumerate(workloads):
+            e = _eco_for(w, keep)
+            if e is not None:
+                ecos[i] = e
+                has[i] = 1
+        ng = _u32(n_gens)
+        arr = np.ascontiguousarray(arrivals, dtype=np.float64)
+        jobs = np.zeros(count, np.uint64)
+        check(lib().spg_server_run_trace(self._h, descs, ecos, has.ctypes.data, ng.ctypes.data, arr.ctypes.data,
+                                         count, jobs.ctypes.data), "spg_server_run_trace")
+        return jobs
+
+    def job_info(self, job: int) -> dict:
+        i = spg_job_info()
+        check(lib().spg_server_job_info(self._h, int(job), ctypes.byref(i)), "spg_server_job_info")
+        return {k: getattr(i, k) for k, _ in spg_job_info._fields_}
+
+    def job_stats(self, job: int, first_gen: int, count: int) -> np.ndarray:
+        out = np.zeros(max(int(count), 1), STATS_DTYPE)
+        check(lib().spg_server_job_stats(self._h, int(job), int(first_gen), int(count), out.ctypes.data),
+              "spg_server_job_stats")
+        return out[:count]
+
+    def counters(self) -> dict:
+        c = spg_server_counters()
+        check(lib().spg_server_stats(self._h, ctypes.byref(c)), "spg_server_stats")
+        return {k: getattr(c, k) for k, _ in spg_server_counters._fields_}
+
+    def clock(self) -> float:
+        return float(lib().spg_server_clock(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().spg_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -221,3 +221,25 @@ def batch_replicates(count: int = 4096, n_gen: int = 500, n_min: int = 1_000, n_
         out.append(single_species(n, L, n_gen, mu, s, seed, r, effects_seed=1000 + r,
                                   name=f"replicate-{r}"))
     return out
+
+
+def served_trace(count: int = 200, rate: float = 200.0, n_min: int = 1_000, n_max: int = 2_000_000,
+                 loci_choices=(64, 256), gen_min: int = 100, gen_max: int = 2000, mu: float = 1e-5,
+                 s_max: float = 0.5, seed: int = 0, trace_seed: int = 2024):
+    """Parameter-sweep jobs arriving as a Poisson stream: returns (workloads,
+    generation counts, arrival times in seconds).  N log-uniform in
+    [n_min, n_max], L uniform over loci_choices, generations uniform in
+    [gen_min, gen_max], selection strength uniform in [0, s_max]; job i uses
+    replicate id i."""
+    rng = np.random.default_rng(trace_seed)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    ws, gens = [], []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        L = int(rng.choice(loci_choices))
+        g = int(rng.integers(gen_min, gen_max + 1))
+        s = float(rng.uniform(0.0, s_max))
+        ws.append(single_species(n, L, g, mu, s, seed, i, effects_seed=5000 + i, name=f"job-{i}"))
+        gens.append(g)
+    return ws, gens, arrivals
