@@ -204,6 +204,32 @@ def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, p
             "speedup_vs_plain": value / plain}
 
 
+def served_sweep(spegg, torch, count: int = 48, rate: float = 200.0):
+    """Served parameter sweep: a seeded Poisson stream (rate jobs/s) of jobs
+    with N log-uniform in [1e3, 2e6], L in {64, 256}, 100-2000 generations,
+    admitted by device footprint and run by continuous batching; latency is
+    arrival -> finish on the server's clock."""
+    ws, gens, arrivals = S.served_trace(count=count, rate=rate)
+    srv = spegg.Server(gens_per_tick=16)
+    t0 = time.perf_counter()
+    jobs = srv.run_trace(ws, gens, arrivals)
+    wall = time.perf_counter() - t0
+    infos = [srv.job_info(int(j)) for j in jobs]
+    lat = np.array([i["t_finish"] - i["t_arrival"] for i in infos])
+    work = sum(w.n * i["gen"] for w, i in zip(ws, infos))
+    makespan = max(i["t_finish"] for i in infos) - min(i["t_arrival"] for i in infos)
+    c = srv.counters()
+    srv.close()
+    value = work / makespan
+    mean_job = work / count
+    return {"workload": f"{count} jobs, Poisson {rate:g}/s, N log-uniform [1e3, 2e6], L in {{64, 256}}, "
+                        "100-2000 generations, continuous batching",
+            "value": value, "unit": "individual-generations/s", "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "makespan_s": makespan, "wall_s": wall,
+            "offered_load": rate * mean_job / value, "peak_resident": c["peak_resident"],
+            "peak_memory_gb": c["peak_memory_used"] / 1e9}
+
+
 def cpu_baseline(workload, target_seconds=12.0):
     import oracle
     pop = oracle.OraclePopulation.from_workload(workload)
@@ -226,6 +252,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true", help="omit the CPU oracle baseline measurement")
     ap.add_argument("--no-batched", action="store_true", help="omit the batched-replicates measurement")
+    ap.add_argument("--no-served", action="store_true", help="omit the served-sweep measurement")
     args = ap.parse_args()
     workload = S.consumer_resource()
     if args.impl == "reference":
@@ -318,6 +345,7 @@ def main():
     assert len(stats) == GENERATIONS
 
     batched = None if args.no_batched else batched_replicates(spegg, torch)
+    served = None if args.no_served else served_sweep(spegg, torch)
     if rank != 0:
         return
     line = {
@@ -338,6 +366,8 @@ def main():
     }
     if batched is not None:
         line["batched"] = batched
+    if served is not None:
+        line["served"] = served
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload)
     print(json.dumps(line))
