@@ -170,3 +170,104 @@ class OraclePopulation:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- spatial
+SP_STATS_DTYPE = np.dtype([
+    ("t", "<u4"), ("species", "<u4"), ("n_before", "<u4"), ("adults_before", "<u4"), ("births", "<u4"),
+    ("survivors", "<u4"), ("movers", "<u4"), ("n_after", "<u4"), ("adults_after", "<u4"), ("pad", "<u4"),
+    ("sum_raw_surv", "<i8"), ("het_newborn", "<u8"), ("allele_newborn", "<u8"),
+])
+
+
+class _SpeciesDesc(ctypes.Structure):
+    _fields_ = [("effects", ctypes.c_void_p), ("tables", ctypes.c_void_p), ("bin_bias", ctypes.c_int32),
+                ("bin_shift", ctypes.c_uint32), ("mu", ctypes.c_double), ("n0", ctypes.c_uint32),
+                ("p0_q32", ctypes.c_uint32), ("D", ctypes.c_uint32), ("A", ctypes.c_uint32 * 4),
+                ("G", ctypes.c_uint32), ("P", ctypes.c_uint32 * 4), ("E", ctypes.c_uint32),
+                ("C", ctypes.c_uint32 * 4), ("beta_q16", ctypes.c_uint32), ("bmax", ctypes.c_uint32)]
+
+
+def _splib():
+    L = lib()
+    if not getattr(L, "_sp_ready", False):
+        L.orc_space_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]
+        L.orc_space_create.restype = ctypes.c_void_p
+        L.orc_space_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_space_destroy.restype = None
+        L.orc_space_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_space_step.restype = ctypes.c_int
+        L.orc_space_deme_size.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]
+        L.orc_space_deme_size.restype = ctypes.c_uint32
+        L.orc_space_read_deme.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                          ctypes.c_void_p]
+        L.orc_space_read_deme.restype = ctypes.c_int
+        L.orc_space_set_deme.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_uint32]
+        L.orc_space_set_deme.restype = ctypes.c_int
+        L.orc_sp_stats_size.restype = ctypes.c_uint32
+        L.orc_species_desc_size.restype = ctypes.c_uint32
+        assert L.orc_sp_stats_size() == SP_STATS_DTYPE.itemsize
+        assert L.orc_species_desc_size() == ctypes.sizeof(_SpeciesDesc)
+        L._sp_ready = True
+    return L
+
+
+class OracleSpace:
+    """The spatial community advanced step by step on the CPU."""
+
+    def __init__(self, community):
+        L = _splib()
+        self.c = community
+        self.ns = len(community.species)
+        self.words = community.n_loci // 32
+        self._keep = []
+        descs = (_SpeciesDesc * self.ns)()
+        for i, sp in enumerate(community.species):
+            e = np.ascontiguousarray(sp.effects, dtype=np.int16)
+            t = np.ascontiguousarray(sp.tables, dtype=np.uint32).reshape(3, 4096)
+            self._keep += [e, t]
+            pad = lambda v: (ctypes.c_uint32 * 4)(*(list(v) + [0] * (4 - len(v))))
+            descs[i] = _SpeciesDesc(e.ctypes.data, t.ctypes.data, int(sp.bias), int(sp.shift), float(sp.mu),
+                                    int(sp.n0), int(sp.p0_q32), int(sp.D), pad(sp.A), int(sp.G), pad(sp.P),
+                                    int(sp.E), pad(sp.C), int(sp.beta_q16), int(sp.bmax))
+        self._h = L.orc_space_create(community.X, community.Y, self.ns, community.n_loci, community.seed,
+                                     community.disp_q32, ctypes.cast(descs, ctypes.c_void_p))
+        if not self._h:
+            raise ValueError("oracle rejected the community description")
+
+    def step(self, n: int = 1) -> np.ndarray:
+        out = np.zeros((n, self.ns), SP_STATS_DTYPE)
+        for i in range(n):
+            if _splib().orc_space_step(self._h, out[i].ctypes.data) != 0:
+                raise RuntimeError("oracle step failed")
+        return out
+
+    def deme(self, species: int, patch: int):
+        k = _splib().orc_space_deme_size(self._h, species, patch)
+        rec = np.zeros((max(k, 1), 2 * self.words), np.uint32)
+        age = np.zeros(max(k, 1), np.uint8)
+        _splib().orc_space_read_deme(self._h, species, patch, rec.ctypes.data, age.ctypes.data)
+        return rec[:k], age[:k]
+
+    def set_deme(self, species: int, patch: int, rec, age) -> None:
+        r = np.ascontiguousarray(rec, dtype=np.uint32).reshape(-1, 2 * self.words)
+        a = np.ascontiguousarray(age, dtype=np.uint8)
+        if _splib().orc_space_set_deme(self._h, species, patch, r.ctypes.data, a.ctypes.data, len(a)) != 0:
+            raise ValueError("invalid deme contents")
+
+    def sizes(self) -> np.ndarray:
+        return np.array([[_splib().orc_space_deme_size(self._h, s, p) for p in range(self.c.patches)]
+                         for s in range(self.ns)], dtype=np.int64)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _splib().orc_space_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

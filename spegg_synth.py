@@ -243,3 +243,73 @@ def served_trace(count: int = 200, rate: float = 200.0, n_min: int = 1_000, n_ma
         ws.append(single_species(n, L, g, mu, s, seed, i, effects_seed=5000 + i, name=f"job-{i}"))
         gens.append(g)
     return ws, gens, arrivals
+
+
+# --------------------------------------------------------------------------
+# spatial community (species on a torus of patches, age classes 0/1/2)
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Species:
+    """One species of a spatial community.  tables: uint32[3, 4096] viability
+    by age class; D, A: survival interaction; G, P, E, C, beta_q16, bmax:
+    recruitment (see the library header for the integer formulas)."""
+    effects: np.ndarray
+    bias: int
+    shift: int
+    tables: np.ndarray
+    mu: float
+    n0: int
+    p0_q32: int
+    D: int
+    A: List[int]
+    G: int
+    P: List[int]
+    E: int
+    C: List[int]
+    beta_q16: int
+    bmax: int
+
+
+@dataclasses.dataclass
+class Community:
+    X: int
+    Y: int
+    n_loci: int
+    seed: int
+    disp_q32: int
+    species: List[Species]
+    n_gen: int = 200
+
+    @property
+    def patches(self) -> int:
+        return self.X * self.Y
+
+
+def spatial_community(X: int = 64, Y: int = 64, n0: int = 814, n_loci: int = 256, n_gen: int = 200,
+                      disp: float = 0.05, mu: float = 1e-5, s: float = 0.3, seed: int = 0,
+                      effects_seed: int = 77) -> Community:
+    """Three species (prey, competitor, predator) on an X x Y torus, n0 founders
+    per species and patch (10^7 individuals at the defaults), L loci, dispersal
+    probability `disp` to one of the four neighbours.  Viabilities are Gaussian
+    stabilising in the trait, scaled per age class (newborn, juvenile, adult);
+    prey and competitor recruitment falls with local crowding, the predator's
+    rises with local prey; predators depress prey survival."""
+    rng_seeds = [effects_seed + k for k in range(3)]
+    age_scale = [[0.80, 0.90, 0.82], [0.80, 0.90, 0.82], [0.85, 0.92, 0.85]]
+    inter_A = [[1, 1, 3], [1, 1, 3], [0, 0, 1]]
+    D = [20000, 20000, 30000]
+    G = [2000, 2000, 0]
+    P = [[0, 0, 0], [0, 0, 0], [1, 1, 0]]
+    E = [0, 0, 500]
+    C = [[2, 1, 0], [1, 2, 0], [0, 0, 2]]
+    beta = [int(0.9 * 65536), int(0.9 * 65536), int(0.9 * 65536)]
+    out = []
+    for k in range(3):
+        e = effects_q8(n_loci, 0.1, rng_seeds[k])
+        bias, shift = bin_map(e)
+        w = stabilizing_table(bias, shift, s).astype(np.float64)
+        tabs = np.stack([np.minimum(np.floor(w * a), 4294967294.0) for a in age_scale[k]]).astype(np.uint32)
+        out.append(Species(effects=e, bias=bias, shift=shift, tables=tabs, mu=mu, n0=n0, p0_q32=0x80000000,
+                           D=D[k], A=list(inter_A[k]), G=G[k], P=list(P[k]), E=E[k], C=list(C[k]),
+                           beta_q16=beta[k], bmax=2 * n0))
+    return Community(X=X, Y=Y, n_loci=n_loci, seed=seed, disp_q32=p0_threshold(disp), species=out, n_gen=n_gen)
