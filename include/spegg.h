@@ -284,6 +284,87 @@ int spg_server_stats(spg_server *server, spg_server_counters *out);
 double spg_server_clock(spg_server *server);
 void spg_server_destroy(spg_server *server);
 
+/* ---- Spatial, age-structured multi-species community ----------------------
+ * Species on an X x Y torus of patches (migration among patches, Main text
+ * and S3), individuals of age class 0, 1, 2 (overlapping generations), all
+ * updated in parallel per deme (species s in patch p, d = s*P + p; Fig. S5 B).
+ * A deme stores adults (age 2) first, then age 1, then age 0.  One step,
+ * with counts n_k (all ages) of every species in the patch and m (adults) of
+ * the deme at its start:
+ *   survival factor  f = 0xFFFFFFFF if sum_k A[k] n_k == 0, else
+ *                    min(floor(2^32 D / (D + sum_k A[k] n_k)), 0xFFFFFFFE);
+ *   births           num = G + sum_k P[k] n_k, den = num + E + sum_k C[k] n_k,
+ *                    g = den ? floor(2^32 num / den) : 0,
+ *                    B = min(bmax, floor(m * beta_q16 * g / 2^48));
+ *   member of rank r and age a: Philox (r, t, d, 5<<24) lanes (u, v, w):
+ *                    survives iff table[a][bin] scaled by f (as in a population)
+ *                    exceeds u; survivors age to min(a+1, 2) and move iff
+ *                    v < disp_q32, to neighbour 1 + floor(4 w / 2^32) (1 N:
+ *                    y-1, 2 S: y+1, 3 E: x+1, 4 W: x-1, wrapping);
+ *   newborn k (age 0, no survival draw this step): Philox (k, t, d, 2<<24)
+ *                    lanes (mother rank and father rank among the m adults,
+ *                    move draw, mutation count); gametes (purpose 3) and
+ *                    mutation positions (purpose 4) as in a population;
+ *                    direction from lane 0 of Philox (k, t, d, 6<<24);
+ *   new deme (s, q): for age 2, 1, 0: movers into q from q itself, then from
+ *                    its north, south, east and west neighbours, each in
+ *                    source order (members by rank, then newborns).
+ * Founders: n0 per deme, allele copy q of rank r is 1 iff lane q%4 of
+ * Philox (r, 0, d, 1<<24 | q/4) < p0_q32; ranks below n0/2 are adults, the
+ * next n0/4 age 1, the rest age 0.  Exceeding `capacity` individuals or
+ * `staging_capacity` newborns in a step stops the community with
+ * SPG_ERR_RANGE (the last complete layout is kept). */
+typedef struct {
+    const int16_t *effects;     /* [L] allelic effects, Q8 */
+    const uint32_t *tables;     /* [3][4096] viability by age class 0, 1, 2 */
+    int32_t bin_bias;
+    uint32_t bin_shift;
+    double mu;                  /* per-locus mutation probability */
+    uint32_t n0;                /* founders per patch */
+    uint32_t p0_q32;
+    uint32_t D, A[4];           /* survival interaction */
+    uint32_t G, P[4], E, C[4];  /* recruitment */
+    uint32_t beta_q16, bmax;    /* births per adult (Q16), cap per deme and step */
+} spg_species;
+
+typedef struct {
+    uint32_t X, Y;              /* torus; X * Y <= 2^20 patches */
+    uint32_t n_species;         /* 1 .. 4 */
+    uint32_t n_loci;            /* 32, 64, 128 or 256 (all species) */
+    uint64_t seed;
+    uint32_t disp_q32;          /* dispersal probability, Q32 */
+    uint32_t capacity;          /* individuals (0: twice the founders) */
+    uint32_t staging_capacity;  /* newborns per step (0: capacity / 2) */
+    uint32_t stats_capacity;    /* steps kept in the statistics ring (0: 1024) */
+    const spg_species *species; /* [n_species], copied */
+} spg_space_desc;
+
+typedef struct {
+    uint32_t t, species;
+    uint32_t n_before, adults_before, births, survivors, movers, n_after, adults_after;
+    uint32_t pad;
+    int64_t sum_raw_surv;       /* raw phenotype over surviving members */
+    uint64_t het_newborn;       /* heterozygous loci over newborns */
+    uint64_t allele_newborn;    /* allele-1 copies over newborns */
+} spg_space_stats;
+
+typedef struct spg_space spg_space;
+
+int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, void *stream, spg_space **out);
+/* Enqueue n_steps steps (returns after enqueue). */
+int spg_space_step(spg_space *space, uint32_t n_steps);
+/* Statistics of steps first_step .. first_step+count-1: count * n_species
+ * records, species-major within a step.  Waits for the stream. */
+int spg_space_read_stats(spg_space *space, uint32_t first_step, uint32_t count, spg_space_stats *out);
+/* Individuals per deme (n_species * X * Y entries, deme d = s*P + p). */
+int spg_space_sizes(spg_space *space, uint32_t *sizes, size_t count);
+/* One deme's records ([n][2W]) and ages ([n]); either may be NULL to query n. */
+int spg_space_read_deme(spg_space *space, uint32_t species, uint32_t patch, uint32_t *rec, uint8_t *age,
+                        size_t capacity, uint32_t *n);
+int spg_space_get_state(spg_space *space, uint32_t *t, int32_t *status, uint32_t *total);
+int spg_space_synchronize(spg_space *space);
+void spg_space_destroy(spg_space *space);
+
 /* ---- One generation without any device allocation -----------------------
  * The paper has no counterpart to this call; it exists for callers that may
  * not allocate device memory: code that runs while a CUDA stream is being

@@ -80,6 +80,28 @@ class spg_server_counters(ctypes.Structure):
                 ("memory_used", ctypes.c_size_t), ("peak_memory_used", ctypes.c_size_t)]
 
 
+class spg_species(ctypes.Structure):
+    _fields_ = [("effects", ctypes.c_void_p), ("tables", ctypes.c_void_p), ("bin_bias", ctypes.c_int32),
+                ("bin_shift", ctypes.c_uint32), ("mu", ctypes.c_double), ("n0", ctypes.c_uint32),
+                ("p0_q32", ctypes.c_uint32), ("D", ctypes.c_uint32), ("A", ctypes.c_uint32 * 4),
+                ("G", ctypes.c_uint32), ("P", ctypes.c_uint32 * 4), ("E", ctypes.c_uint32),
+                ("C", ctypes.c_uint32 * 4), ("beta_q16", ctypes.c_uint32), ("bmax", ctypes.c_uint32)]
+
+
+class spg_space_desc(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_uint32), ("Y", ctypes.c_uint32), ("n_species", ctypes.c_uint32),
+                ("n_loci", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("disp_q32", ctypes.c_uint32),
+                ("capacity", ctypes.c_uint32), ("staging_capacity", ctypes.c_uint32),
+                ("stats_capacity", ctypes.c_uint32), ("species", ctypes.c_void_p)]
+
+
+SPACE_STATS_DTYPE = np.dtype([
+    ("t", "<u4"), ("species", "<u4"), ("n_before", "<u4"), ("adults_before", "<u4"), ("births", "<u4"),
+    ("survivors", "<u4"), ("movers", "<u4"), ("n_after", "<u4"), ("adults_after", "<u4"), ("pad", "<u4"),
+    ("sum_raw_surv", "<i8"), ("het_newborn", "<u8"), ("allele_newborn", "<u8"),
+])
+
+
 class spg_state(ctypes.Structure):
     _fields_ = [("gen", ctypes.c_uint32), ("S", ctypes.c_uint32), ("status", ctypes.c_int32),
                 ("f", ctypes.c_uint32), ("R", ctypes.c_double)]
@@ -147,6 +169,17 @@ _SIGNATURES = {
     "spg_server_stats": ([ctypes.c_void_p, ctypes.POINTER(spg_server_counters)], ctypes.c_int),
     "spg_server_clock": ([ctypes.c_void_p], ctypes.c_double),
     "spg_server_destroy": ([ctypes.c_void_p], None),
+    "spg_space_create": ([ctypes.POINTER(spg_space_desc), ctypes.POINTER(spg_allocator), ctypes.c_void_p,
+                          ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "spg_space_step": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "spg_space_read_stats": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
+    "spg_space_sizes": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "spg_space_read_deme": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "spg_space_get_state": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "spg_space_synchronize": ([ctypes.c_void_p], ctypes.c_int),
+    "spg_space_destroy": ([ctypes.c_void_p], None),
     "spg_get_tiling": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
 }
 
@@ -496,6 +529,79 @@ class Server:
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().spg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Space:
+    """Spatial, age-structured multi-species community (spg_space_*)."""
+
+    def __init__(self, community, capacity: int = 0, staging_capacity: int = 0, stats_capacity: int = 0,
+                 stream=None, allocator: Optional[TorchAllocator] = None):
+        L = lib()
+        self.c = community
+        self.ns = len(community.species)
+        self.words = community.n_loci // 32
+        keep = []
+        arr = (spg_species * self.ns)()
+        for i, sp in enumerate(community.species):
+            e = np.ascontiguousarray(sp.effects, dtype=np.int16)
+            t = np.ascontiguousarray(sp.tables, dtype=np.uint32).reshape(3, 4096)
+            keep += [e, t]
+            pad = lambda v: (ctypes.c_uint32 * 4)(*(list(v) + [0] * (4 - len(v))))
+            arr[i] = spg_species(e.ctypes.data, t.ctypes.data, int(sp.bias), int(sp.shift), float(sp.mu), int(sp.n0),
+                                 int(sp.p0_q32), int(sp.D), pad(sp.A), int(sp.G), pad(sp.P), int(sp.E), pad(sp.C),
+                                 int(sp.beta_q16), int(sp.bmax))
+        d = spg_space_desc(community.X, community.Y, self.ns, community.n_loci, community.seed, community.disp_q32,
+                           int(capacity), int(staging_capacity), int(stats_capacity),
+                           ctypes.cast(arr, ctypes.c_void_p))
+        self.allocator = allocator if allocator is not None else TorchAllocator()
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        check(L.spg_space_create(ctypes.byref(d), ctypes.byref(self.allocator.struct), self._stream,
+                                 ctypes.byref(h)), "spg_space_create")
+        self._h = h
+
+    def step(self, n: int = 1) -> None:
+        check(lib().spg_space_step(self._h, int(n)), "spg_space_step")
+
+    def read_stats(self, first: int, count: int) -> np.ndarray:
+        out = np.zeros((max(count, 1), self.ns), SPACE_STATS_DTYPE)
+        check(lib().spg_space_read_stats(self._h, int(first), int(count), out.ctypes.data), "spg_space_read_stats")
+        return out[:count]
+
+    def sizes(self) -> np.ndarray:
+        out = np.zeros(self.ns * self.c.patches, np.uint32)
+        check(lib().spg_space_sizes(self._h, out.ctypes.data, out.size), "spg_space_sizes")
+        return out.reshape(self.ns, self.c.patches).astype(np.int64)
+
+    def deme(self, species: int, patch: int):
+        n = ctypes.c_uint32()
+        check(lib().spg_space_read_deme(self._h, int(species), int(patch), None, None, 0, ctypes.byref(n)),
+              "spg_space_read_deme")
+        rec = np.zeros((max(n.value, 1), 2 * self.words), np.uint32)
+        age = np.zeros(max(n.value, 1), np.uint8)
+        check(lib().spg_space_read_deme(self._h, int(species), int(patch), rec.ctypes.data, age.ctypes.data,
+                                        max(n.value, 1), ctypes.byref(n)), "spg_space_read_deme")
+        return rec[:n.value], age[:n.value]
+
+    def state(self) -> dict:
+        t, st, tot = ctypes.c_uint32(), ctypes.c_int32(), ctypes.c_uint32()
+        check(lib().spg_space_get_state(self._h, ctypes.byref(t), ctypes.byref(st), ctypes.byref(tot)),
+              "spg_space_get_state")
+        return {"t": t.value, "status": st.value, "total": tot.value}
+
+    def synchronize(self) -> None:
+        check(lib().spg_space_synchronize(self._h), "spg_space_synchronize")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().spg_space_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,81 @@
+"""Spatial community on the GPU (spg_space_*) against the CPU oracle: every
+deme's records and ages, and every statistics record, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import spegg_synth as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_09255_gb300 import build
+    build.build()
+
+
+def sp():
+    from paper_1603_09255_gb300 import spegg
+    return spegg
+
+
+def assert_same(gpu, orc, steps):
+    so = orc.step(steps)
+    sg = gpu.read_stats(1, steps)
+    for name in so.dtype.names:
+        assert np.array_equal(so[name], sg[name]), name
+    assert np.array_equal(gpu.sizes(), orc.sizes())
+    for s in range(gpu.ns):
+        for p in range(gpu.c.patches):
+            rg, ag = gpu.deme(s, p)
+            ro, ao = orc.deme(s, p)
+            assert np.array_equal(ag, ao), (s, p)
+            assert np.array_equal(rg, ro), (s, p)
+
+
+@pytest.mark.parametrize("X,Y,n0,L,steps,disp", [
+    (4, 4, 120, 64, 8, 0.05),
+    (3, 5, 60, 256, 6, 0.3),
+    (1, 1, 500, 32, 10, 0.5),
+    (2, 1, 80, 128, 8, 0.9),     # neighbours coincide on a 2 x 1 torus
+    (1, 3, 50, 32, 8, 1.0),
+])
+def test_space_matches_oracle(X, Y, n0, L, steps, disp):
+    c = S.spatial_community(X=X, Y=Y, n0=n0, n_loci=L, mu=1e-3, disp=disp if disp < 1 else 0.999999, seed=3)
+    gpu = sp().Space(c, stats_capacity=64)
+    orc = oracle.OracleSpace(c)
+    gpu.step(steps)
+    assert_same(gpu, orc, steps)
+    assert gpu.state()["t"] == steps and gpu.state()["status"] == 0
+
+
+def test_space_founders_match_and_stepwise_calls():
+    c = S.spatial_community(X=5, Y=4, n0=90, n_loci=128, mu=1e-2, seed=9)
+    gpu = sp().Space(c, stats_capacity=32)
+    orc = oracle.OracleSpace(c)
+    for s in range(3):
+        for p in range(20):
+            rg, ag = gpu.deme(s, p)
+            ro, ao = orc.deme(s, p)
+            assert np.array_equal(rg, ro) and np.array_equal(ag, ao)
+    for k in (1, 2, 3):
+        gpu.step(k)
+        assert_same(gpu, orc, k)
+
+
+def test_space_capacity_overflow_is_reported():
+    c = S.spatial_community(X=2, Y=2, n0=100, n_loci=32, seed=1)
+    for spc in c.species:
+        spc.beta_q16 = 8 * 65536
+        spc.bmax = 10_000
+        spc.G, spc.E, spc.C = 1000, 0, [0, 0, 0]
+    gpu = sp().Space(c, capacity=1500)
+    gpu.step(5)
+    st = gpu.state()
+    assert st["status"] == sp().ERR_RANGE and st["t"] < 5
+    assert gpu.sizes().sum() <= 1500
