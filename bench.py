@@ -230,6 +230,39 @@ def served_sweep(spegg, torch, count: int = 48, rate: float = 200.0):
             "peak_memory_gb": c["peak_memory_used"] / 1e9}
 
 
+def spatial_community(spegg, torch, steps: int = 200):
+    """Three-species community on a 64 x 64 torus, 814 founders per species
+    and patch (1.0e7 individuals), L = 256, age classes 0/1/2, dispersal 0.05,
+    200 steps; throughput in individual-steps per second."""
+    c = S.spatial_community()
+    stream = torch.cuda.Stream()
+    g = spegg.Space(c, stream=stream, stats_capacity=steps + 8)
+    g.step(3)
+    g.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+    g.step(steps)
+    with torch.cuda.stream(stream):
+        b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b)
+    st = g.read_stats(4, steps)
+    ind = int(st["n_before"].sum())
+    births = int(st["births"].sum())
+    words = c.n_loci // 32
+    # every member's record is read and rewritten; every newborn reads two
+    # parent records and is written to staging and read back
+    algo = ind * 2 * 8 * words + births * 4 * 8 * words
+    out = {"workload": f"3 species on a 64 x 64 torus, {c.species[0].n0} founders per species and patch, "
+                       f"L={c.n_loci}, dispersal 0.05, {steps} steps after 3",
+           "value": ind / (ms / 1e3), "unit": "individual-steps/s", "ms_per_step": ms / steps,
+           "individuals_first_step": int(st[0]["n_before"].sum()), "individuals_last_step": int(st[-1]["n_after"].sum()),
+           "births": births, "algorithmic_GBs": algo / (ms / 1e3) / 1e9}
+    g.close()
+    return out
+
+
 def cpu_baseline(workload, target_seconds=12.0):
     import oracle
     pop = oracle.OraclePopulation.from_workload(workload)
@@ -253,6 +286,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="omit the CPU oracle baseline measurement")
     ap.add_argument("--no-batched", action="store_true", help="omit the batched-replicates measurement")
     ap.add_argument("--no-served", action="store_true", help="omit the served-sweep measurement")
+    ap.add_argument("--no-spatial", action="store_true", help="omit the spatial-community measurement")
     args = ap.parse_args()
     workload = S.consumer_resource()
     if args.impl == "reference":
@@ -346,6 +380,7 @@ def main():
 
     batched = None if args.no_batched else batched_replicates(spegg, torch)
     served = None if args.no_served else served_sweep(spegg, torch)
+    spatial = None if args.no_spatial else spatial_community(spegg, torch)
     if rank != 0:
         return
     line = {
@@ -368,6 +403,8 @@ def main():
         line["batched"] = batched
     if served is not None:
         line["served"] = served
+    if spatial is not None:
+        line["spatial"] = spatial
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload)
     print(json.dumps(line))

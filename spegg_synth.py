@@ -292,17 +292,18 @@ def spatial_community(X: int = 64, Y: int = 64, n0: int = 814, n_loci: int = 256
     per species and patch (10^7 individuals at the defaults), L loci, dispersal
     probability `disp` to one of the four neighbours.  Viabilities are Gaussian
     stabilising in the trait, scaled per age class (newborn, juvenile, adult);
-    prey and competitor recruitment falls with local crowding, the predator's
-    rises with local prey; predators depress prey survival."""
+    recruitment falls with the species' own local density, the predator's
+    rises with local prey; all three depress the prey's and competitor's
+    survival, the predator only its own."""
     rng_seeds = [effects_seed + k for k in range(3)]
     age_scale = [[0.80, 0.90, 0.82], [0.80, 0.90, 0.82], [0.85, 0.92, 0.85]]
     inter_A = [[1, 1, 3], [1, 1, 3], [0, 0, 1]]
-    D = [20000, 20000, 30000]
-    G = [2000, 2000, 0]
+    D = [400000, 400000, 400000]
+    G = [1500, 1500, 0]
     P = [[0, 0, 0], [0, 0, 0], [1, 1, 0]]
     E = [0, 0, 500]
-    C = [[2, 1, 0], [1, 2, 0], [0, 0, 2]]
-    beta = [int(0.9 * 65536), int(0.9 * 65536), int(0.9 * 65536)]
+    C = [[2, 0, 0], [0, 2, 0], [0, 0, 2]]
+    beta = [int(0.7 * 65536), int(0.7 * 65536), int(0.45 * 65536)]
     out = []
     for k in range(3):
         e = effects_q8(n_loci, 0.1, rng_seeds[k])
