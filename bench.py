@@ -251,14 +251,19 @@ def spatial_community(spegg, torch, steps: int = 200):
     ind = int(st["n_before"].sum())
     births = int(st["births"].sum())
     words = c.n_loci // 32
-    # every member's record is read and rewritten; every newborn reads two
-    # parent records and is written to staging and read back
-    algo = ind * 2 * 8 * words + births * 4 * 8 * words
+    # algorithmic bytes: every member's record (8W B) and age read once and
+    # written once at its new place; every newborn reads two parent records
+    # and is written once with its age
+    algo = ind * (16 * words + 2) + births * (24 * words + 1)
+    peak, source = load_peaks()
+    achieved = algo / (ms / 1e3) / 1e9
     out = {"workload": f"3 species on a 64 x 64 torus, {c.species[0].n0} founders per species and patch, "
                        f"L={c.n_loci}, dispersal 0.05, {steps} steps after 3",
            "value": ind / (ms / 1e3), "unit": "individual-steps/s", "ms_per_step": ms / steps,
            "individuals_first_step": int(st[0]["n_before"].sum()), "individuals_last_step": int(st[-1]["n_after"].sum()),
-           "births": births, "algorithmic_GBs": algo / (ms / 1e3) / 1e9}
+           "births": births,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "note": f"whole step (7 launches), of {source}"}}
     g.close()
     return out
 

@@ -291,7 +291,8 @@ def spatial_community(X: int = 64, Y: int = 64, n0: int = 814, n_loci: int = 256
     """Three species (prey, competitor, predator) on an X x Y torus, n0 founders
     per species and patch (10^7 individuals at the defaults), L loci, dispersal
     probability `disp` to one of the four neighbours.  Viabilities are Gaussian
-    stabilising in the trait, scaled per age class (newborn, juvenile, adult);
+    stabilising in the trait around the founders' mean, scaled per age class
+    (newborn, juvenile, adult);
     recruitment falls with the species' own local density, the predator's
     rises with local prey; all three depress the prey's and competitor's
     survival, the predator only its own."""
@@ -303,12 +304,14 @@ def spatial_community(X: int = 64, Y: int = 64, n0: int = 814, n_loci: int = 256
     P = [[0, 0, 0], [0, 0, 0], [1, 1, 0]]
     E = [0, 0, 500]
     C = [[2, 0, 0], [0, 2, 0], [0, 0, 2]]
-    beta = [int(0.7 * 65536), int(0.7 * 65536), int(0.45 * 65536)]
+    beta = [int(0.7 * 65536), int(0.7 * 65536), int(0.65 * 65536)]
     out = []
     for k in range(3):
         e = effects_q8(n_loci, 0.1, rng_seeds[k])
         bias, shift = bin_map(e)
-        w = stabilizing_table(bias, shift, s).astype(np.float64)
+        # optimum at the founders' mean trait (allele frequency 1/2: raw = sum e)
+        theta = float(e.astype(np.float64).sum()) / 512.0
+        w = stabilizing_table(bias, shift, s, theta).astype(np.float64)
         tabs = np.stack([np.minimum(np.floor(w * a), 4294967294.0) for a in age_scale[k]]).astype(np.uint32)
         out.append(Species(effects=e, bias=bias, shift=shift, tables=tabs, mu=mu, n0=n0, p0_q32=0x80000000,
                            D=D[k], A=list(inter_A[k]), G=G[k], P=list(P[k]), E=E[k], C=list(C[k]),
