@@ -256,6 +256,10 @@ __device__ __forceinline__ unsigned long long shfl_sum_u64(unsigned long long v)
 // are reset for the next generation.
 __device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g, uint32_t f_used) {
     const uint32_t lane = threadIdx.x & 31u;
+    DevState *st = sg.state;
+    // state loads issued together with the accumulator loads
+    const double R_prev = ld_relaxed_f64(&st->R);
+    const int32_t status_prev = (int32_t)ld_relaxed_u32(reinterpret_cast<const uint32_t *>(&st->status));
     StatAcc mine;
     clear_acc(&mine);
     if (lane < (uint32_t)kAccCopies) {
@@ -280,12 +284,11 @@ __device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g,
     const unsigned long long allele = shfl_sum_u64(mine.allele);
     const int mn = __reduce_min_sync(0xFFFFFFFFu, mine.mn), mx = __reduce_max_sync(0xFFFFFFFFu, mine.mx);
     if (lane == 0) {
-        DevState *st = sg.state;
         spg_stats *rec = sg.ring + (g - 1) % P->stats_cap;
         uint32_t f_next = f_used;
         double R = 0.0;
         if (P->has_eco) {
-            R = resource_update(ld_relaxed_f64(&st->R), P->r, P->K, cons);
+            R = resource_update(R_prev, P->r, P->K, cons);
             f_next = factor_q32(R, P->R_half);
             st->R = R;
         }
@@ -305,7 +308,7 @@ __device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g,
         rec->R = R;
         rec->f = f_next;
         rec->pad = 0;
-        if (st->status == SPG_OK) st->status = status;
+        if (status_prev == SPG_OK) st->status = status;
         st->f = f_next;
         st->S = (uint32_t)S_new;
         st->done = 0;
@@ -394,8 +397,10 @@ __device__ __forceinline__ void draw_parents(const SegCtx &c, uint32_t base, int
         d.mom[it] = d.dad[it] = d.u_surv[it] = d.u_mut[it] = 0u;
         if (j < c.n) {
             const uint4 r = philox(make_uint4(j, c.g, c.rep, kMate << 24), c.k0, c.k1);
-            d.mom[it] = __ldg(c.sin + __umulhi(r.x, c.S));
-            d.dad[it] = __ldg(c.sin + __umulhi(r.y, c.S));
+            // survivor indices through L2 only: random 4-byte reads would
+            // evict the threshold table from L1
+            d.mom[it] = __ldcg(c.sin + __umulhi(r.x, c.S));
+            d.dad[it] = __ldcg(c.sin + __umulhi(r.y, c.S));
             d.u_surv[it] = r.z;
             d.u_mut[it] = r.w;
         }
@@ -485,10 +490,13 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
                     }
                 }
             }
-            // (B) mutation count from the CDF, positions on the rare path
-            uint32_t k = 0;
-            for (uint32_t i = 0; i < c.kmax; ++i) k += (u.y >= s_cdf[i]) ? 1u : 0u;
-            if (k != 0u) mutate<W>(ch, k, j, c.g, c.rep, c.k0, c.k1);
+            // (B) mutation count from the CDF (none below its first entry,
+            // the common case), positions on the rare path
+            if (c.kmax != 0u && u.y >= s_cdf[0]) {
+                uint32_t k = 0;
+                for (uint32_t i = 0; i < c.kmax; ++i) k += (u.y >= s_cdf[i]) ? 1u : 0u;
+                mutate<W>(ch, k, j, c.g, c.rep, c.k0, c.k1);
+            }
             store_record<W>(c.chi + (size_t)j * (2 * W), ch);
 
             // (C) phenotype, (D) survival
