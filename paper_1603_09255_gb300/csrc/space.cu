@@ -124,8 +124,45 @@ __device__ __forceinline__ void sp_slot_source(const SpaceArgs &a, uint32_t q, u
     dir = moved[slot];
 }
 
+// One record (2W words; 8W bytes, 16-byte aligned for W >= 2) in vector accesses.
 template <int W>
-__device__ __forceinline__ int32_t sp_phenotype(const uint32_t (&c)[2 * W], const SpeciesParams *sp) {
+__device__ __forceinline__ void sp_load_rec(const uint32_t *p, uint32_t (&r)[2 * W]) {
+    if constexpr (W == 1) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        r[0] = v.x;
+        r[1] = v.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < W / 2; ++q) {
+            const uint4 v = reinterpret_cast<const uint4 *>(p)[q];
+            r[4 * q] = v.x;
+            r[4 * q + 1] = v.y;
+            r[4 * q + 2] = v.z;
+            r[4 * q + 3] = v.w;
+        }
+    }
+}
+template <int W>
+__device__ __forceinline__ void sp_store_rec(uint32_t *p, const uint32_t (&r)[2 * W]) {
+    if constexpr (W == 1) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(r[0], r[1]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < W / 2; ++q)
+            reinterpret_cast<uint4 *>(p)[q] = make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    }
+}
+
+// Effect planes of one species staged in shared memory (plane b, word w at
+// [b * W + w]) by the whole block.
+template <int W>
+__device__ __forceinline__ void sp_stage_planes(const SpeciesParams *sp, uint32_t *s_planes) {
+    for (uint32_t i = threadIdx.x; i < kMaxPlanes * W; i += blockDim.x) s_planes[i] = sp->planes[i];
+}
+
+template <int W>
+__device__ __forceinline__ int32_t sp_phenotype(const uint32_t (&c)[2 * W], const SpeciesParams *sp,
+                                                const uint32_t *s_planes) {
     uint32_t total = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) total += __popc(c[w]) + __popc(c[W + w]);
@@ -134,7 +171,7 @@ __device__ __forceinline__ int32_t sp_phenotype(const uint32_t (&c)[2 * W], cons
         int32_t cnt = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            const uint32_t pl = __ldg(&sp->planes[b * W + w]);
+            const uint32_t pl = s_planes[b * W + w];
             cnt += __popc(pl & c[w]) + __popc(pl & c[W + w]);
         }
         raw += cnt << b;
@@ -303,10 +340,12 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
     __shared__ uint32_t s_run[16];
     __shared__ uint32_t s_w[kSpBlock / 32][16];
     __shared__ uint32_t s_tot[16];
+    __shared__ __align__(16) uint32_t s_planes[kMaxPlanes * W];
     if (a.state->status != SPG_OK) return;
     const uint32_t d = blockIdx.x, s = d / a.P, p = d % a.P, tid = threadIdx.x;
     const uint32_t t = a.state->t + 1u, par = a.state->t & 1u;
     const SpeciesParams *sp = a.sp + s;
+    sp_stage_planes<W>(sp, s_planes);
     const uint32_t *geno = a.geno[par];
     const uint8_t *age = a.age[par];
     const uint32_t base = a.off[par][d], n = a.off[par][d + 1] - base, m = a.adults[par][d];
@@ -322,11 +361,10 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
         uint32_t cls = kDead;
         if (r < n) {
             uint32_t rec[2 * W];
-#pragma unroll
-            for (int w = 0; w < 2 * W; ++w) rec[w] = __ldg(geno + (size_t)(base + r) * 2 * W + w);
+            sp_load_rec<W>(geno + (size_t)(base + r) * 2 * W, rec);
             const uint32_t ag = age[base + r];
             const uint4 u = sp_philox(make_uint4(r, t, d, kSpSurv << 24), a.key0, a.key1);
-            const int32_t raw = sp_phenotype<W>(rec, sp);
+            const int32_t raw = sp_phenotype<W>(rec, sp, s_planes);
             uint32_t thr = __ldg(&sp->table[ag][sp_bin(sp, raw)]);
             if (f != kCertain) thr = __umulhi(thr, f);
             if (thr == kCertain || u.x < thr) {
@@ -351,9 +389,9 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
         const bool fits = nb0 + k < a.staging_cap;
         if (k < B && fits) {
             const uint4 u = sp_philox(make_uint4(k, t, d, kSpMate << 24), a.key0, a.key1);
-            const uint32_t *mo = geno + (size_t)(base + __umulhi(u.x, m)) * 2 * W;
-            const uint32_t *fa = geno + (size_t)(base + __umulhi(u.y, m)) * 2 * W;
-            uint32_t ch[2 * W];
+            uint32_t mo[2 * W], fa[2 * W], ch[2 * W];
+            sp_load_rec<W>(geno + (size_t)(base + __umulhi(u.x, m)) * 2 * W, mo);
+            sp_load_rec<W>(geno + (size_t)(base + __umulhi(u.y, m)) * 2 * W, fa);
 #pragma unroll
             for (int q4 = 0; q4 < (2 * W + 3) / 4; ++q4) {
                 const uint4 dm = sp_philox(make_uint4(k, t, d, (kSpRecomb << 24) | (uint32_t)q4), a.key0, a.key1);
@@ -363,13 +401,14 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
                     if (q < 2 * W) {
                         const int w = q >> 1;
                         const uint32_t mk = sp_lane(dm, l);
-                        if ((q & 1) == 0) ch[w] = (__ldg(mo + w) & ~mk) | (__ldg(mo + W + w) & mk);
-                        else ch[W + w] = (__ldg(fa + w) & ~mk) | (__ldg(fa + W + w) & mk);
+                        if ((q & 1) == 0) ch[w] = (mo[w] & ~mk) | (mo[W + w] & mk);
+                        else ch[W + w] = (fa[w] & ~mk) | (fa[W + w] & mk);
                     }
                 }
             }
-            uint32_t kmut = 0;
-            for (uint32_t i = 0; i < sp->kmax; ++i) kmut += u.w >= __ldg(&sp->cdf[i]) ? 1u : 0u;
+            uint32_t kmut = 0;  // none below the CDF's first entry (the common case)
+            if (sp->kmax != 0u && u.w >= __ldg(&sp->cdf[0]))
+                for (uint32_t i = 0; i < sp->kmax; ++i) kmut += u.w >= __ldg(&sp->cdf[i]) ? 1u : 0u;
             if (kmut) {
                 uint32_t seen[2 * W];
 #pragma unroll
@@ -397,8 +436,7 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
                     }
                 }
             }
-#pragma unroll
-            for (int w = 0; w < 2 * W; ++w) a.staging[(size_t)(nb0 + k) * 2 * W + w] = ch[w];
+            sp_store_rec<W>(a.staging + (size_t)(nb0 + k) * 2 * W, ch);
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 het += __popc(ch[w] ^ ch[W + w]);
@@ -501,8 +539,9 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_scatter(SpaceArgs a) {
         const uint32_t q = s * a.P + sp_dest(a, p, dir);
         const uint32_t pos = noff[q] + a.slotoff[(size_t)q * 15 + ci * 5 + sp_slot(dir)] + rk;
         if (pos >= a.cap) continue;
-#pragma unroll
-        for (int w = 0; w < 2 * W; ++w) ngeno[(size_t)pos * 2 * W + w] = i < n ? __ldg(src + w) : src[w];
+        uint32_t rec[2 * W];
+        sp_load_rec<W>(src, rec);
+        sp_store_rec<W>(ngeno + (size_t)pos * 2 * W, rec);
         nage[pos] = (uint8_t)(2u - ci);
     }
 }
