@@ -64,7 +64,7 @@ struct MultiChain {
                 cudaKernelNodeParams kp{};
                 kp.func = reinterpret_cast<void *>(off ? g.gl.offspring.fn : g.gl.compact);
                 kp.gridDim = dim3(off ? g.gl.blocks : g.gl.buckets);
-                kp.blockDim = dim3(off ? kBlock : kBucketWords);
+                kp.blockDim = dim3(off ? kBlock : kCompactThreads);
                 kp.sharedMemBytes = off ? g.gl.offspring.smem : 0;
                 kp.kernelParams = params;
                 cudaGraphNode_t node;

@@ -216,7 +216,7 @@ int GraphChain::build(const GenLaunch &gl, uint32_t len) {
         cudaKernelNodeParams kp{};
         kp.func = reinterpret_cast<void *>(off ? gl.offspring.fn : gl.compact);
         kp.gridDim = dim3(off ? gl.blocks : gl.buckets);
-        kp.blockDim = dim3(off ? kBlock : kBucketWords);
+        kp.blockDim = dim3(off ? kBlock : kCompactThreads);
         kp.sharedMemBytes = off ? gl.offspring.smem : 0;
         kp.kernelParams = params;
         cudaGraphNode_t node;
@@ -238,7 +238,7 @@ int GraphChain::build(const GenLaunch &gl, uint32_t len) {
 
 int launch_generation(const GenLaunch &gl, cudaStream_t stream) {
     gl.offspring.fn<<<gl.blocks, kBlock, gl.offspring.smem, stream>>>(gl.args);
-    gl.compact<<<gl.buckets, kBucketWords, 0, stream>>>(gl.args);
+    gl.compact<<<gl.buckets, kCompactThreads, 0, stream>>>(gl.args);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "generation launch");
 }

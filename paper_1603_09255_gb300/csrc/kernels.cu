@@ -249,17 +249,18 @@ __device__ __forceinline__ unsigned long long shfl_sum_u64(unsigned long long v)
     return v;
 }
 
-// Close generation g of one population; run by one full warp of the block
-// that finished the population's last compaction bucket.  The statistics
-// accumulators (kAccCopies copies) are summed, the resource is updated,
-// the statistics record and the state are written, and the accumulators
-// are reset for the next generation.
+// Close generation g of one population (run by one full warp while the
+// population's survivors are being compacted; everything it reads was final
+// when the offspring launch ended).  The statistics accumulators (kAccCopies
+// copies) are summed, the resource is updated, the statistics record is
+// written, the accumulators are reset for the next generation, and the new
+// survivor count, factor, resource and status are left in the state's next_*
+// fields for commit_state.
 __device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g, uint32_t f_used) {
     const uint32_t lane = threadIdx.x & 31u;
     DevState *st = sg.state;
     // state loads issued together with the accumulator loads
     const double R_prev = ld_relaxed_f64(&st->R);
-    const int32_t status_prev = (int32_t)ld_relaxed_u32(reinterpret_cast<const uint32_t *>(&st->status));
     StatAcc mine;
     clear_acc(&mine);
     if (lane < (uint32_t)kAccCopies) {
@@ -290,7 +291,6 @@ __device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g,
         if (P->has_eco) {
             R = resource_update(R_prev, P->r, P->K, cons);
             f_next = factor_q32(R, P->R_half);
-            st->R = R;
         }
         const int32_t status = (S_new == 0ull) ? SPG_EXTINCT : SPG_OK;
         rec->gen = g;
@@ -308,12 +308,26 @@ __device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g,
         rec->R = R;
         rec->f = f_next;
         rec->pad = 0;
-        if (status_prev == SPG_OK) st->status = status;
-        st->f = f_next;
-        st->S = (uint32_t)S_new;
-        st->done = 0;
-        st->gen = g;
+        st->next_S = (uint32_t)S_new;
+        st->next_f = f_next;
+        st->next_R = P->has_eco ? R : R_prev;
+        st->next_status = status;
     }
+}
+
+// Make generation g the population's current one (one thread of the block
+// that finished the last compaction bucket, after every block has read the
+// state and the closing warp's next_* values are visible).
+__device__ void commit_state(DevState *st, uint32_t g) {
+    const uint32_t S = ld_relaxed_u32(&st->next_S), f = ld_relaxed_u32(&st->next_f);
+    const int32_t status = (int32_t)ld_relaxed_u32(reinterpret_cast<const uint32_t *>(&st->next_status));
+    const double R = ld_relaxed_f64(&st->next_R);
+    if (st->status == SPG_OK) st->status = status;
+    st->f = f;
+    st->S = S;
+    st->R = R;
+    st->done = 0;
+    st->gen = g;
 }
 
 struct PopNow {
@@ -681,29 +695,40 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
 }
 
 // ---------------------------------------- compaction kernel (Fig. 1E, 1F)
-// One block of kBucketWords threads per bucket of kBucket offspring: the
-// survivors' indices, in offspring order, at offset (survivors of all earlier
-// buckets) + (block scan of the bitmap words' popcounts).  The block that
-// finishes a population's last bucket closes its generation.  Every load that
-// does not depend on the population state is issued together with it (both
-// parities of the bucket counts are summed; the state picks one).
+// One block of kCompactThreads threads per bucket of kBucket offspring: its
+// first kBucketWords threads write the survivors' indices, in offspring order,
+// at offset (survivors of all earlier buckets) + (block scan of the bitmap
+// words' popcounts); in a population's first bucket the extra warp closes the
+// generation meanwhile (finalize_warp).  The block that finishes the last
+// bucket commits the new state.  Every load that does not depend on the
+// population state is issued together with it (both parities of the bucket
+// counts are summed; the state picks one).
+__device__ __forceinline__ void compaction_barrier() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kBucketWords) : "memory");  // the kBucketWords compaction threads
+}
+
 __device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
     constexpr int NW = kBucketWords / 32;
     __shared__ uint32_t s_warp[NW];
     __shared__ uint32_t s_prev[NW];
     __shared__ uint32_t s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool closer = tid >= (int)kBucketWords;  // the generation-closing warp
     const uint32_t valid_words = (sg.n + 31u) >> 5;
     const uint32_t w = b * kBucketWords + (uint32_t)tid;
-    const uint32_t bits = w < valid_words ? __ldcg(sg.alive + w) : 0u;
+    const uint32_t bits = (!closer && w < valid_words) ? __ldcg(sg.alive + w) : 0u;
     uint32_t prev0 = 0, prev1 = 0;
-    for (uint32_t i = (uint32_t)tid; i < b; i += kBucketWords) {
+    for (uint32_t i = (uint32_t)tid; !closer && i < b; i += kBucketWords) {
         prev0 += __ldcg(sg.bucket_sum + i);
         prev1 += __ldcg(sg.bucket_sum + sg.nbuckets + i);
     }
     const PopNow now = read_state(sg.state);
     if (!now.active) return;
     const uint32_t g = now.gen + 1u;
+    if (closer) {
+        if (b == 0u) finalize_warp(sg, sg.prm, g, now.f);
+        __threadfence();
+    } else {
     const uint32_t prev = __reduce_add_sync(0xFFFFFFFFu, (g & 1u) ? prev1 : prev0);
     const uint32_t cnt = __popc(bits);
     uint32_t incl = cnt;
@@ -714,7 +739,7 @@ __device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
     }
     if (lane == 31) s_warp[warp] = incl;
     if (lane == 0) s_prev[warp] = prev;
-    __syncthreads();
+    compaction_barrier();
     uint32_t excl = incl - cnt;
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
@@ -730,14 +755,19 @@ __device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
         const uint32_t r0 = __shfl_sync(0xFFFFFFFFu, excl, k);
         if ((word >> lane) & 1u) sout[r0 + __popc(word & lt)] = (w0 + (uint32_t)k) * 32u + (uint32_t)lane;
     }
+    }
     // every block has read the state by now (its values fed the stores
-    // above), so the last one may rewrite it
+    // above), and the closing warp of bucket 0 has published the next state
+    __syncthreads();
     if (tid == 0) s_last = (atomicAdd(&sg.state->done, 1u) == sg.nbuckets - 1u) ? 1u : 0u;
     __syncthreads();
-    if (s_last && warp == 0) finalize_warp(sg, sg.prm, g, now.f);
+    if (s_last && tid == 0) {
+        __threadfence();
+        commit_state(sg.state, g);
+    }
 }
 
-__global__ void __launch_bounds__(kBucketWords) k_compact(const __grid_constant__ GenArgs a) {
+__global__ void __launch_bounds__(kCompactThreads) k_compact(const __grid_constant__ GenArgs a) {
     const uint32_t bkt = blockIdx.x;
     if (a.nsegs == 1u) {
         compact_bucket(a.one, bkt);

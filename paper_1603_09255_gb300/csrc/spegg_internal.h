@@ -17,6 +17,7 @@ constexpr int kMaxWords = 8;      // W = L/32 <= 8
 constexpr int kBlock = 256;       // threads per block of the offspring kernel
 constexpr uint32_t kBucket = 4096;                 // offspring per compaction bucket
 constexpr uint32_t kBucketWords = kBucket / 32;    // bitmap words per bucket = compaction threads
+constexpr uint32_t kCompactThreads = kBucketWords + 32;  // + one warp that closes the generation
 constexpr uint32_t kCertain = 0xFFFFFFFFu;
 constexpr int kAccCopies = 16;    // copies of the statistics accumulators (spread atomics)
 
@@ -53,7 +54,12 @@ struct alignas(16) DevState {
     double R;         // resource density
     uint32_t done;    // compaction buckets of the running generation that have finished
     uint32_t target;  // generations stop once gen reaches target (0xFFFFFFFF: never)
-    uint32_t pad[2];
+    // the generation being closed: computed while its survivors are being
+    // compacted, committed by the block that finishes the last bucket
+    uint32_t next_S, next_f;
+    int32_t next_status;
+    uint32_t pad;
+    double next_R;
 };
 
 // Statistics of the generation being formed, accumulated by atomics; each
