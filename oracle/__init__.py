@@ -48,6 +48,8 @@ def lib():
         L.orc_set_ecology.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
         L.orc_set_ecology.restype = ctypes.c_int
+        L.orc_set_linkage.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_set_linkage.restype = ctypes.c_int
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
         L.orc_step.restype = ctypes.c_int
         L.orc_read_genotypes.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
@@ -125,6 +127,8 @@ class OraclePopulation:
                 w.init_genotypes, w.p0_q32)
         if w.has_ecology:
             p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack)
+        if getattr(w, "map_morgans", None) is not None:
+            p.set_linkage(w.map_morgans)
         return p
 
     def set_ecology(self, r, K, R0, R_half, attack):
@@ -132,6 +136,14 @@ class OraclePopulation:
         rc = lib().orc_set_ecology(self._h, float(r), float(K), float(R0), float(R_half), a.ctypes.data)
         if rc != 0:
             raise ValueError("oracle rejected the ecology description")
+
+    def set_linkage(self, map_morgans):
+        """Linkage map: map_morgans[l] = distance (Morgans) between loci l-1
+        and l, negative where locus l starts a new chromosome."""
+        m = np.ascontiguousarray(map_morgans, dtype=np.float64)
+        assert m.shape == (self.n_loci,)
+        if lib().orc_set_linkage(self._h, m.ctypes.data) != 0:
+            raise ValueError("oracle rejected the linkage map")
 
     def step(self, n_gen: int) -> np.ndarray:
         out = np.zeros(max(int(n_gen), 1), STATS_DTYPE)

@@ -29,7 +29,16 @@
  *     (0xFFFFFFFF = certain), optionally scaled by a Q32 resource factor;
  *   - every random number is one lane of Philox4x32-10 (Salmon et al., SC'11,
  *     "Parallel random numbers: as easy as 1, 2, 3") at a counter that names
- *     (individual, generation, replicate, purpose, sub-index).
+ *     (individual, generation, replicate, purpose, sub-index);
+ *   - linkage maps (the "variable linkage maps" / "arbitrary linkage
+ *     patterns" of the Main text; optional, free recombination otherwise):
+ *     loci lie on chromosomes in record order; between adjacent loci of one
+ *     chromosome the map gives a distance d_l in Morgans; crossovers follow
+ *     Haldane's no-interference model, realised as K ~ Binomial(2^16, D/2^16)
+ *     crossovers per gamete (D = total map length) each falling in interval l
+ *     with probability d_l / D; a locus takes the haplotype given by its
+ *     chromosome's fair coin, flipped once per crossover in the intervals from
+ *     the chromosome's first locus up to it.
  *
  * Genotypes are kept UNPACKED here (one byte per allele copy) so that the
  * per-locus statement of the model is visible; packing is done only when
@@ -45,7 +54,12 @@
 #define ORC_MUT_DRAWS 64
 #define ORC_CERTAIN 0xFFFFFFFFu
 
-enum { ORC_INIT = 1, ORC_MATE = 2, ORC_RECOMB = 3, ORC_MUTPOS = 4 };
+#define ORC_MAX_LOCI 256
+#define ORC_MAX_CHROM 96
+#define ORC_LINK_SITES 65536u /* crossover opportunities per gamete */
+#define ORC_MAX_MAP 16.0      /* Morgans, total map length */
+
+enum { ORC_INIT = 1, ORC_MATE = 2, ORC_RECOMB = 3, ORC_MUTPOS = 4, ORC_LINK = 5 };
 enum { ORC_OK = 0, ORC_EXTINCT = 1, ORC_ERR_INVALID = -1, ORC_ERR_OOM = -2 };
 
 /* One record per generation; same field order as the library's statistics
@@ -75,6 +89,12 @@ typedef struct {
     double mu;
     uint32_t cdf[ORC_MAX_KMAX];
     uint32_t kmax;
+    /* linkage map (linked == 0: free recombination) */
+    int linked;
+    uint32_t link_cdf[ORC_MAX_KMAX], link_kmax; /* crossovers per gamete */
+    uint32_t link_cum[ORC_MAX_LOCI];            /* crossover interval CDF */
+    uint32_t chrom_of[ORC_MAX_LOCI];            /* chromosome of each locus */
+    uint32_t nchrom;
     /* ecology */
     int has_eco;
     double r, K, R, R_half;
@@ -270,6 +290,89 @@ int orc_set_ecology(orc_pop *p, double r, double K, double R0, double R_half, co
     return ORC_OK;
 }
 
+/* Linkage map: map_morgans[l] (l >= 1) is the distance in Morgans between
+ * loci l-1 and l, or negative where locus l starts a new chromosome
+ * (map_morgans[0] is ignored: locus 0 starts chromosome 0).  Tables, in a
+ * fixed order of IEEE-double basic operations:
+ *   w_l = map_morgans[l] for linked intervals, else 0;  D = sum of w_l;
+ *   crossover count: the Binomial(2^16, D / 2^16) CDF built like the
+ *     mutation CDF;
+ *   interval CDF: s = s + w_l, cum_l = floor(2^32 * (s / D)), saturated at
+ *     0xFFFFFFFF (all zero when D = 0).
+ * A crossover with uniform u lies in interval I = #{l <= L-2 : cum_l <= u}. */
+int orc_set_linkage(orc_pop *p, const double *map_morgans)
+{
+    if (!p || !map_morgans || p->L > ORC_MAX_LOCI) return ORC_ERR_INVALID;
+    const uint32_t L = p->L;
+    double w[ORC_MAX_LOCI];
+    double D = 0.0;
+    uint32_t c = 0;
+    p->chrom_of[0] = 0;
+    w[0] = 0.0;
+    for (uint32_t l = 1; l < L; ++l) {
+        double m = map_morgans[l];
+        if (m != m) return ORC_ERR_INVALID;
+        if (m < 0.0) {
+            c++;
+            w[l] = 0.0;
+        } else {
+            w[l] = m;
+        }
+        p->chrom_of[l] = c;
+        D = D + w[l];
+    }
+    if (c + 1 > ORC_MAX_CHROM || !(D <= ORC_MAX_MAP)) return ORC_ERR_INVALID;
+    p->nchrom = c + 1;
+    p->link_kmax = orc_mutation_cdf(D / (double)ORC_LINK_SITES, ORC_LINK_SITES, p->link_cdf);
+    double run = 0.0;
+    for (uint32_t l = 0; l < L; ++l) {
+        if (D > 0.0) {
+            run = run + w[l];
+            double x = (run / D) * 4294967296.0;
+            p->link_cum[l] = x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)x;
+        } else {
+            p->link_cum[l] = 0;
+        }
+    }
+    p->linked = 1;
+    return ORC_OK;
+}
+
+/* One gamete of a parent (haplotypes h0, h1) under the linkage map; pi = 0
+ * mother, 1 father.  Draws: Philox(j, g, rep, LINK<<24 | pi<<8 | sub):
+ * sub 0 lane 0 = crossover-count uniform, lanes 1..3 = the coins of
+ * chromosomes 0..31, 32..63, 64..95 (bit c % 32); crossover a uses lane a % 4
+ * of sub 1 + a / 4. */
+static void linked_gamete(const orc_pop *p, uint32_t j, uint32_t g, uint32_t pi, const uint8_t *h0,
+                          const uint8_t *h1, uint8_t *out)
+{
+    const uint32_t L = p->L;
+    uint32_t d0[4];
+    draw4(p, j, g, ORC_LINK, (pi << 8) | 0u, d0);
+    uint32_t K = 0;
+    for (uint32_t i = 0; i < p->link_kmax; ++i)
+        if (d0[0] >= p->link_cdf[i]) K++;
+    uint8_t flips[ORC_MAX_LOCI];
+    memset(flips, 0, sizeof flips);
+    for (uint32_t a = 0; a < K; ++a) {
+        uint32_t da[4];
+        draw4(p, j, g, ORC_LINK, (pi << 8) | (1u + a / 4), da);
+        uint32_t u = da[a % 4], I = 0;
+        for (uint32_t l = 0; l + 1 < L; ++l)
+            if (p->link_cum[l] <= u) I++;
+        flips[I] ^= 1u; /* crossovers in one interval cancel in pairs */
+    }
+    uint8_t origin = 0;
+    for (uint32_t l = 0; l < L; ++l) {
+        if (l == 0 || p->chrom_of[l] != p->chrom_of[l - 1]) {
+            uint32_t c = p->chrom_of[l];
+            origin = (uint8_t)((d0[1 + c / 32] >> (c % 32)) & 1u);
+        }
+        origin ^= flips[l];
+        out[l] = origin ? h1[l] : h0[l];
+    }
+}
+
 /* Logistic update with consumption C (attack units in Q16):
  *   R' = (R + (r*R) * (1 - R/K)) - C * 2^-16, clamped at 0. */
 static double resource_update(double R, double r, double K, uint64_t C)
@@ -317,7 +420,11 @@ static void one_generation(orc_pop *p, orc_stats *st)
         const uint8_t *m1 = p->par + ((size_t)mother * 2 + 1) * L;
         const uint8_t *f0 = p->par + ((size_t)father * 2 + 0) * L;
         const uint8_t *f1 = p->par + ((size_t)father * 2 + 1) * L;
-        for (uint32_t w = 0; w < W; ++w) {
+        if (p->linked) {
+            linked_gamete(p, j, g, 0, m0, m1, c0); /* maternal gamete -> haplotype 0 */
+            linked_gamete(p, j, g, 1, f0, f1, c1); /* paternal gamete -> haplotype 1 */
+        }
+        for (uint32_t w = 0; w < W && !p->linked; ++w) {
             uint32_t qm = 2 * w + 0, qf = 2 * w + 1, dm[4], df[4];
             draw4(p, j, g, ORC_RECOMB, qm / 4, dm);
             draw4(p, j, g, ORC_RECOMB, qf / 4, df);

@@ -169,6 +169,9 @@ class Workload:
     eco_R_half: Optional[float] = None
     attack: Optional[np.ndarray] = None
     s: float = 0.0
+    # linkage map (None: free recombination): distance in Morgans between loci
+    # l-1 and l, negative where locus l starts a new chromosome
+    map_morgans: Optional[np.ndarray] = None
 
     @property
     def words(self) -> int:
@@ -177,6 +180,27 @@ class Workload:
     @property
     def has_ecology(self) -> bool:
         return self.attack is not None
+
+
+def linkage_map(n_loci: int, chromosomes: int, morgans: float) -> np.ndarray:
+    """Evenly spaced map: the loci split into `chromosomes` runs of equal
+    length (in record order), each `morgans` long with equal intervals
+    between adjacent loci; -1 marks each chromosome's first locus."""
+    per = n_loci // chromosomes
+    assert per * chromosomes == n_loci and per >= 1
+    m = np.empty(n_loci, np.float64)
+    for c in range(chromosomes):
+        m[c * per] = -1.0
+        if per > 1:
+            m[c * per + 1:(c + 1) * per] = morgans / (per - 1)
+    return m
+
+
+def with_linkage(w: "Workload", chromosomes: int = 4, morgans: float = 1.0) -> "Workload":
+    """The same workload with an evenly spaced linkage map."""
+    import dataclasses
+    return dataclasses.replace(w, map_morgans=linkage_map(w.n_loci, chromosomes, morgans),
+                               name=w.name + f"+map{chromosomes}x{morgans:g}M")
 
 
 def single_species(n: int = 10_000, n_loci: int = 32, n_gen: int = 100, mu: float = 1e-4,
