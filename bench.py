@@ -227,6 +227,37 @@ def served_sweep(spegg, torch, count: int = 48, rate: float = 200.0):
             "peak_memory_gb": c["peak_memory_used"] / 1e9}
 
 
+def linked_population(spegg, torch, gens: int = 256):
+    """The consumer-resource population (N = 10^6, L = 128) with a linkage map
+    of 4 chromosomes of 1 Morgan each (Haldane crossovers instead of free
+    recombination), `gens` generations after 64, CUDA events on its stream."""
+    w = S.with_linkage(S.consumer_resource(), 4, 1.0)
+    stream = torch.cuda.Stream()
+    pop = spegg.Population.from_workload(w, stats_capacity=gens + 128, stream=stream)
+    pop.step(64)
+    pop.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        flush.fill_(7)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+    pop.step(gens)
+    with torch.cuda.stream(stream):
+        b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b)
+    peak, source = load_peaks()
+    achieved = w.n * (12 + 24 * w.words) * gens / (ms / 1e3) / 1e9
+    out = {"workload": f"consumer-resource N={w.n} L={w.n_loci}, linkage map 4 chromosomes x 1 Morgan, "
+                       f"{gens} generations after 64 (L2 flushed before)",
+           "value": w.n * gens / (ms / 1e3), "unit": "individual-generations/s", "us_per_generation": ms * 1e3 / gens,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "note": f"(12 + 24W) B per offspring, of {source}"}}
+    pop.close()
+    return out
+
+
 def spatial_community(spegg, torch, steps: int = 200):
     """Three-species community on a 64 x 64 torus, 814 founders per species
     and patch (1.0e7 individuals), L = 256, age classes 0/1/2, dispersal 0.05,
@@ -289,6 +320,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="omit the batched-replicates measurement")
     ap.add_argument("--no-served", action="store_true", help="omit the served-sweep measurement")
     ap.add_argument("--no-spatial", action="store_true", help="omit the spatial-community measurement")
+    ap.add_argument("--no-linked", action="store_true", help="omit the linkage-map measurement")
     args = ap.parse_args()
     workload = S.consumer_resource()
     if args.impl == "reference":
@@ -383,6 +415,7 @@ def main():
     batched = None if args.no_batched else batched_replicates(spegg, torch)
     served = None if args.no_served else served_sweep(spegg, torch)
     spatial = None if args.no_spatial else spatial_community(spegg, torch)
+    linked = None if args.no_linked else linked_population(spegg, torch)
     if rank != 0:
         return
     line = {
@@ -407,6 +440,8 @@ def main():
         line["served"] = served
     if spatial is not None:
         line["spatial"] = spatial
+    if linked is not None:
+        line["linked"] = linked
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload)
     print(json.dumps(line))

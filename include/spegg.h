@@ -37,7 +37,25 @@
  *             q%4 of sub q/4; bit b set -> locus 32w+b comes from haplotype 1;
  *   mutations purpose 4: draw a is lane a%4 of sub a/4, position
  *             floor(u * 2L / 2^32) (p < L: haplotype 0 locus p, else
- *             haplotype 1 locus p-L); draws a = 0..63 until k distinct.
+ *             haplotype 1 locus p-L); draws a = 0..63 until k distinct;
+ *   linkage   purpose 5 (populations with a linkage map, replacing the
+ *             gamete draws of purpose 3): for parent pi (0 mother, 1
+ *             father), sub pi<<8 | 0: lane 0 -> crossover count K = number
+ *             of crossover-CDF entries <= u, lanes 1..3 -> the coins of
+ *             chromosomes 0..31, 32..63, 64..95 (bit c%32); crossover a uses
+ *             lane a%4 of sub pi<<8 | (1 + a/4) and lies in interval
+ *             I = number of interval-CDF entries cum[0..L-2] <= u.
+ * Linkage map (the paper's variable linkage maps, read as Haldane's
+ * no-interference model): map_morgans[l] (l >= 1) is the distance in Morgans
+ * between loci l-1 and l, or negative where locus l starts a new chromosome;
+ * w_l = that distance for linked intervals, else 0; D = sum of w_l (at most
+ * 16 Morgans; at most 96 chromosomes).  The crossover count is
+ * Binomial(65536, D/65536) (tabulated exactly like the mutation CDF below
+ * with mu = D/65536 over 65536 copies); the interval CDF is s = s + w_l,
+ * cum[l] = floor(2^32 * (s / D)) saturated at 0xFFFFFFFF (all 0 when D = 0).
+ * A gamete locus takes haplotype 1 iff its chromosome's coin XOR the parity
+ * of the crossovers in the intervals from the chromosome's first locus up to
+ * it is 1.
  * The Binomial CDF is tabulated in Q32 from mu with IEEE-double basic
  * operations in a fixed order: P0 = (1-mu)^(2L) by repeated multiplication,
  * P(k+1) = ((P(k) * (2L-k)) / (k+1)) * mu / (1-mu), cdf[k] = floor(2^32 *
@@ -62,7 +80,7 @@
 extern "C" {
 #endif
 
-#define SPG_ABI_VERSION 1u
+#define SPG_ABI_VERSION 2u
 #define SPG_N_BINS 4096u
 #define SPG_CERTAIN 0xFFFFFFFFu
 #define SPG_MAX_LOCI 256u
@@ -104,6 +122,9 @@ typedef struct {
     uint32_t bin_shift;             /* 0 .. 31                                          */
     double mu;                      /* per-locus mutation probability, 0 <= mu < 1      */
     uint32_t stats_capacity;        /* most recent generations kept readable (0: 1024)  */
+    const double *map_morgans;      /* [L] linkage map (see above), copied; NULL: free  */
+                                    /* recombination.  Single populations only: batch   */
+                                    /* and server calls reject a map (SPG_ERR_INVALID). */
 } spg_pop_desc;
 
 /* Consumer-resource ecology (Fig. 1F; S2 "Resource Consumption"): after the

@@ -141,6 +141,59 @@ int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
     prm.has_eco = 0;
     prm.ntiles = (d->n + tile_size(items) - 1) / tile_size(items);
     prm.stats_cap = d->stats_capacity ? d->stats_capacity : 1024u;
+    prm.linked = d->map_morgans ? 1u : 0u;
+    prm.link = nullptr;  // set once the population's memory exists
+    return SPG_OK;
+}
+
+// Linkage map (Haldane, no interference): w_l = map distance of the linked
+// interval between loci l-1 and l (0 where locus l starts a chromosome),
+// D = sum w_l; crossover count CDF = Binomial(kLinkSites, D / kLinkSites);
+// interval CDF cum[l] = floor(2^32 * (s / D)) with s the running sum of w.
+int build_link(const double *map, uint32_t n_loci, LinkParams &lp) {
+    std::memset(&lp, 0, sizeof lp);
+    double w[kMaxLoci];
+    double D = 0.0;
+    uint32_t chrom = 0;
+    lp.first[0] = 0;
+    w[0] = 0.0;
+    for (uint32_t l = 1; l < n_loci; ++l) {
+        const double m = map[l];
+        if (!(m == m) || std::isinf(m)) return fail(SPG_ERR_INVALID, "map_morgans[%u] is not finite", l);
+        if (m < 0.0) {
+            lp.clast[chrom] = (uint16_t)(l - 1);
+            if (++chrom >= (uint32_t)kMaxChrom)
+                return fail(SPG_ERR_INVALID, "a linkage map holds at most %d chromosomes", kMaxChrom);
+            lp.first[chrom] = (uint16_t)l;
+            w[l] = 0.0;
+        } else {
+            w[l] = m;
+        }
+        D = D + w[l];
+    }
+    lp.clast[chrom] = (uint16_t)(n_loci - 1);
+    lp.nchrom = chrom + 1;
+    if (!(D <= kMaxMapMorgans)) return fail(SPG_ERR_INVALID, "the linkage map is longer than 16 Morgans");
+    for (uint32_t c = 0; c < lp.nchrom; ++c)
+        for (uint32_t l = lp.first[c]; l <= lp.clast[c]; ++l) lp.last[l] = lp.clast[c];
+    lp.kmax = mutation_cdf(D / (double)kLinkSites, kLinkSites, lp.cdf);
+    double run = 0.0;
+    for (uint32_t l = 0; l < n_loci; ++l) {
+        if (D > 0.0) {
+            run = run + w[l];
+            const double x = (run / D) * 4294967296.0;
+            lp.cum[l] = x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)x;
+        } else {
+            lp.cum[l] = 0;
+        }
+    }
+    // guide[h] = interval of u = h * 2^22: the search for u starts there
+    for (uint32_t h = 0; h < (uint32_t)kLinkGuide; ++h) {
+        const uint32_t u = h << 22;
+        uint32_t I = 0;
+        while (I + 1 < n_loci && lp.cum[I] <= u) ++I;
+        lp.guide[h] = (uint8_t)I;
+    }
     return SPG_OK;
 }
 
@@ -166,6 +219,7 @@ PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap
     L.buckets = take((size_t)2 * nbuckets * 4);
     L.ring = take((size_t)cap * sizeof(spg_stats));
     L.segment = take(sizeof(Segment));
+    L.link = take(sizeof(LinkParams));
     L.total = off;
     return L;
 }

@@ -139,6 +139,70 @@ __device__ __forceinline__ void mutate(uint32_t (&c)[2 * W], uint32_t k, uint32_
     }
 }
 
+// Linkage map in shared memory (see LinkParams) for one population.
+struct LinkSmem {
+    const uint32_t *cdf, *cum;
+    const uint16_t *last, *first, *clast;
+    const uint8_t *guide;
+    uint32_t kmax, nchrom;
+};
+
+template <int W>
+__device__ __forceinline__ void toggle_bit(uint32_t (&t)[W], uint32_t pos) {
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        if ((uint32_t)w == (pos >> 5)) t[w] ^= 1u << (pos & 31u);
+}
+
+// Origin mask of one gamete under the linkage map (bit set: the locus comes
+// from the parent's haplotype 1): every chromosome whose coin is 1 and every
+// crossover flips the loci from its start to the chromosome's end.  Each
+// flip is two toggles (at the first flipped locus and one past the last);
+// a prefix XOR over the L bits turns the toggles into the mask.
+template <int W>
+__device__ __forceinline__ void linked_mask(const LinkSmem &lk, uint32_t j, uint32_t g, uint32_t rep, uint32_t pi,
+                                            uint32_t k0, uint32_t k1, uint32_t (&m)[W]) {
+    constexpr uint32_t L = 32u * W;
+    const uint4 d0 = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8)), k0, k1);
+    uint32_t t[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) t[w] = 0u;
+    for (uint32_t c = 0; c < lk.nchrom; ++c) {
+        const uint32_t coins = c < 32u ? d0.y : c < 64u ? d0.z : d0.w;
+        if ((coins >> (c & 31u)) & 1u) {
+            toggle_bit<W>(t, lk.first[c]);
+            if (lk.clast[c] + 1u < L) toggle_bit<W>(t, lk.clast[c] + 1u);
+        }
+    }
+    uint32_t K = 0;
+    if (lk.kmax != 0u && d0.x >= lk.cdf[0])
+        for (uint32_t i = 0; i < lk.kmax; ++i) K += d0.x >= lk.cdf[i] ? 1u : 0u;
+    uint4 d = d0;
+    for (uint32_t a = 0; a < K; ++a) {
+        if ((a & 3u) == 0u) d = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8) | (1u + a / 4u)), k0, k1);
+        const uint32_t u = lane_of(d, (int)(a & 3u));
+        // interval = #{l <= L-2 : cum[l] <= u}: from the guide entry of u's
+        // top 10 bits, forward over the (few) entries inside that range
+        uint32_t I = lk.guide[u >> 22];
+        while (I + 1u < L && lk.cum[I] <= u) ++I;
+        toggle_bit<W>(t, I);
+        if (lk.last[I] + 1u < L) toggle_bit<W>(t, lk.last[I] + 1u);
+    }
+    uint32_t carry = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint32_t x = t[w];
+        x ^= x << 1;
+        x ^= x << 2;
+        x ^= x << 4;
+        x ^= x << 8;
+        x ^= x << 16;
+        x ^= 0u - carry;
+        m[w] = x;
+        carry = x >> 31;
+    }
+}
+
 // Additive phenotype (Fig. 1C, eq. S2-phenval) with effects in offset
 // binary: e_l = e_min + sum_b 2^b * bit_b(e_l - e_min), so
 // raw = e_min * (copies) + sum_b 2^b * popc(plane_b & copies).
@@ -473,10 +537,10 @@ struct ThreadStats {
 };
 
 // One tile: gametes (B), phenotype (C), survival (D), bitmap (E, first half).
-template <int W, int ITEMS>
+template <int W, int ITEMS, bool LINKED>
 __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t base, int tid, int lane, int warp,
                                                    const unsigned char *s_dyn, int stage, const uint32_t *s_planes,
-                                                   const uint32_t *s_cdf, ThreadStats &ts) {
+                                                   const uint32_t *s_cdf, ThreadStats &ts, const LinkSmem &lk) {
     constexpr int NW = kBlock / 32;
     using St = Staging<W, ITEMS>;
     uint32_t alive_count = 0;  // the warp's survivors (same in every lane)
@@ -489,6 +553,17 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
             uint32_t pm[2 * W], pf[2 * W], ch[2 * W];
             read_parent<W, ITEMS>(s_dyn, stage, it, 0, tid, pm);
             read_parent<W, ITEMS>(s_dyn, stage, it, 1, tid, pf);
+            if constexpr (LINKED) {
+                // (B) gametes under the linkage map
+                uint32_t mm[W], mf[W];
+                linked_mask<W>(lk, j, c.g, c.rep, 0u, c.k0, c.k1, mm);
+                linked_mask<W>(lk, j, c.g, c.rep, 1u, c.k0, c.k1, mf);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    ch[w] = (pm[w] & ~mm[w]) | (pm[W + w] & mm[w]);
+                    ch[W + w] = (pf[w] & ~mf[w]) | (pf[W + w] & mf[w]);
+                }
+            } else {
             // (B) gametes: stream q = 2w + parent is lane q%4 of sub q/4
 #pragma unroll
             for (int q4 = 0; q4 < (2 * W + 3) / 4; ++q4) {
@@ -503,6 +578,7 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
                         else ch[W + w] = (pf[w] & ~m) | (pf[W + w] & m);
                     }
                 }
+            }
             }
             // (B) mutation count from the CDF (none below its first entry,
             // the common case), positions on the rare path
@@ -542,7 +618,7 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
 }
 
 // --------------------------------------------- offspring kernel (Fig. 1A-D)
-template <int W, int ITEMS>
+template <int W, int ITEMS, bool LINKED>
 __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __grid_constant__ GenArgs a) {
     constexpr int NW = kBlock / 32;
     constexpr uint32_t TILE = (uint32_t)(kBlock * ITEMS);
@@ -554,6 +630,11 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
     __shared__ unsigned long long s_ull[2][NW];
     __shared__ uint32_t s_u32[3][NW];
     __shared__ int s_mm[2][NW];
+    constexpr int LK = LINKED ? 1 : 0;  // linkage-map tables only in the linked variant
+    __shared__ uint32_t s_lcdf[LK * kMaxKmax + 1], s_lcum[LK * kMaxLoci + 1];
+    __shared__ uint16_t s_llast[LK * kMaxLoci + 1], s_lfirst[LK * kMaxChrom + 1], s_lclast[LK * kMaxChrom + 1];
+    __shared__ uint8_t s_lguide[LK * kLinkGuide + 1];
+    LinkSmem lk{s_lcdf, s_lcum, s_llast, s_lfirst, s_lclast, s_lguide, 0u, 0u};
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(s_dyn);
@@ -593,6 +674,21 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
             __syncthreads();  // the previous population's tables are no longer read
             for (uint32_t i = tid; i < c.nplanes * W; i += kBlock) s_planes[i] = c.P->planes[i];
             if (tid < kMaxKmax) s_cdf[tid] = (uint32_t)tid < c.kmax ? c.P->cdf[tid] : 0u;
+            if constexpr (LINKED) {
+                const LinkParams *lp = c.P->link;
+                lk.kmax = lp->kmax;
+                lk.nchrom = lp->nchrom;
+                for (uint32_t i = tid; i < 32u * W; i += kBlock) {
+                    s_lcum[i] = lp->cum[i];
+                    s_llast[i] = lp->last[i];
+                }
+                if (tid < kMaxKmax) s_lcdf[tid] = lp->cdf[tid];
+                for (uint32_t i = tid; i < (uint32_t)kLinkGuide; i += kBlock) s_lguide[i] = lp->guide[i];
+                if (tid < kMaxChrom) {
+                    s_lfirst[tid] = lp->first[tid];
+                    s_lclast[tid] = lp->clast[tid];
+                }
+            }
             __syncthreads();
 
             const uint32_t lt0 = t - sg.tile_begin, lt1 = seg_end - sg.tile_begin;
@@ -634,7 +730,7 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
                     bucket_cur = bkt;
                 }
                 const uint32_t cnt =
-                    offspring_tile<W, ITEMS>(c, base, tid, lane, warp, s_dyn, stage, s_planes, s_cdf, ts);
+                    offspring_tile<W, ITEMS, LINKED>(c, base, tid, lane, warp, s_dyn, stage, s_planes, s_cdf, ts, lk);
                 bucket_alive += cnt;
                 warp_alive += cnt;
                 stage = stage + 1 == St::kStages ? 0 : stage + 1;
@@ -830,16 +926,26 @@ uint32_t tile_size(uint32_t items) { return (uint32_t)kBlock * items; }
 GenKernel compact_kernel() { return &k_compact; }
 
 namespace {
-template <int W, int I>
+template <int W, int I, bool LINKED = false>
 OffspringKernel make_offspring() {
     OffspringKernel k;
-    k.fn = &k_offspring<W, I>;
+    k.fn = &k_offspring<W, I, LINKED>;
     k.smem = Staging<W, I>::kBytes;
     return k;
 }
 }  // namespace
 
-OffspringKernel offspring_kernel(uint32_t words, uint32_t items) {
+OffspringKernel offspring_kernel(uint32_t words, uint32_t items, bool linked) {
+    if (linked) {  // linkage maps: one offspring per thread
+        if (items != 1u) return OffspringKernel{};
+        switch (words) {
+            case 1: return make_offspring<1, 1, true>();
+            case 2: return make_offspring<2, 1, true>();
+            case 4: return make_offspring<4, 1, true>();
+            case 8: return make_offspring<8, 1, true>();
+            default: return OffspringKernel{};
+        }
+    }
 #define SPG_CASE(Wv, Iv) \
     if (words == Wv && items == Iv) return make_offspring<Wv, Iv>();
     SPG_CASE(1, 1) SPG_CASE(1, 2) SPG_CASE(1, 4)

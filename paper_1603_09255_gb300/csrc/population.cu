@@ -28,6 +28,7 @@ struct spg_pop {
     char *arena = nullptr;
     PopLayout L{};
     PopParams *host_prm = nullptr;  // host copy of the parameters
+    LinkParams link{};              // linkage-map tables (when host_prm->linked)
     GenLaunch gl;
     GraphChain chain;
 
@@ -49,7 +50,7 @@ namespace {
 // Point the launch at the population's single segment with `items` offspring
 // per thread (uploads the device copy of the segment; synchronous).
 int configure_launch(spg_pop *p, uint32_t items) {
-    OffspringKernel k = offspring_kernel(p->words, items);
+    OffspringKernel k = offspring_kernel(p->words, items, p->host_prm->linked != 0u);
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
     p->items = items;
@@ -104,6 +105,14 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         delete p;
         return rc;
     }
+    if (desc->map_morgans) {
+        rc = build_link(desc->map_morgans, p->n_loci, p->link);
+        if (rc != SPG_OK) {
+            delete p->host_prm;
+            delete p;
+            return rc;
+        }
+    }
     p->cap = p->host_prm->stats_cap;
     p->nbuckets = bucket_count(p->n);
     if (alloc) p->alloc.hooks = *alloc;
@@ -123,6 +132,15 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
     if (!p->arena) {
         spg_destroy(p);
         return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", p->L.total);
+    }
+    if (p->host_prm->linked) {
+        p->host_prm->link = reinterpret_cast<const LinkParams *>(p->arena + p->L.link);
+        const cudaError_t e =
+            cudaMemcpyAsync(p->arena + p->L.link, &p->link, sizeof(LinkParams), cudaMemcpyHostToDevice, p->stream);
+        if (e != cudaSuccess) {
+            spg_destroy(p);
+            return cuda_fail(e, "upload linkage map");
+        }
     }
     rc = view_init(p->view(), *p->host_prm, desc->init_genotypes, desc->p0_q32);
     if (rc == SPG_OK) rc = view_sync(p->view());  // the caller's arrays are read before returning
@@ -246,6 +264,8 @@ int spg_set_tiling(spg_pop *p, uint32_t items) {
     if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
     if (!supported_items(p->words, items))
         return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (1 or 2 for 256 loci); got %u", items);
+    if (p->host_prm->linked && items != 1u)
+        return fail(SPG_ERR_INVALID, "a population with a linkage map runs one offspring per thread");
     const int rc = view_sync(p->view());
     if (rc != SPG_OK) return rc;
     return configure_launch(p, items);

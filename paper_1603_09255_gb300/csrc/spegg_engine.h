@@ -33,7 +33,7 @@ struct Allocator {
 
 // Byte offsets of one population's buffers inside its arena.
 struct PopLayout {
-    size_t params, state, acc, geno0, geno1, surv0, surv1, alive, buckets, ring, segment, total;
+    size_t params, state, acc, geno0, geno1, surv0, surv1, alive, buckets, ring, segment, link, total;
 };
 
 // One population's device memory: its arena, layout and sizes.
@@ -71,6 +71,8 @@ uint32_t factor_q32_host(double R, double R_half);
 size_t align_up(size_t x, size_t a);
 int validate_desc(const spg_pop_desc *d);
 int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm);
+// Linkage-map tables from map_morgans[L] (validated; see spegg.h).
+int build_link(const double *map_morgans, uint32_t n_loci, LinkParams &lp);
 PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap);
 Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, uint32_t tile_begin,
                    uint32_t nbuckets, uint32_t bucket_begin);

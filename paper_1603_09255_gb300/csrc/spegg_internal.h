@@ -21,8 +21,26 @@ constexpr uint32_t kCompactThreads = kBucketWords + 32;  // + one warp that clos
 constexpr uint32_t kCertain = 0xFFFFFFFFu;
 constexpr int kAccCopies = 16;    // copies of the statistics accumulators (spread atomics)
 
+constexpr int kMaxLoci = 256;
+constexpr int kMaxChrom = 96;            // chromosomes of a linkage map
+constexpr uint32_t kLinkSites = 65536;   // crossover opportunities per gamete
+constexpr double kMaxMapMorgans = 16.0;  // total length of a linkage map
+constexpr int kLinkGuide = 1024;         // guide-table entries of the crossover interval search
+
 // Philox counter word 3 = purpose << 24 | sub
-enum Purpose : uint32_t { kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4 };
+enum Purpose : uint32_t { kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4, kLink = 5 };
+
+// Tables of a linkage map (device global memory, one per linked population).
+struct alignas(16) LinkParams {
+    uint32_t cdf[kMaxKmax];      // crossover count per gamete, Binomial(kLinkSites, D / kLinkSites) CDF, Q32
+    uint32_t cum[kMaxLoci];      // interval CDF, Q32: crossover interval = #{l <= L-2 : cum[l] <= u}
+    uint8_t guide[kLinkGuide];   // interval of u = h << 22 (search starts there for u >> 22 == h)
+    uint16_t last[kMaxLoci];     // last locus of the chromosome holding each locus
+    uint16_t first[kMaxChrom];   // first locus of each chromosome
+    uint16_t clast[kMaxChrom];   // last locus of each chromosome
+    uint32_t kmax;               // entries of cdf
+    uint32_t nchrom;
+};
 
 // Read-only parameters of one population (device global memory).
 struct alignas(16) PopParams {
@@ -43,6 +61,9 @@ struct alignas(16) PopParams {
     double r, K, R_half;
     uint32_t ntiles;
     uint32_t stats_cap;
+    const LinkParams *link;      // linkage map tables, or null (free recombination)
+    uint32_t linked;
+    uint32_t pad_link;
 };
 
 // Mutable per-population state (device global memory).
@@ -111,7 +132,7 @@ struct OffspringKernel {
 };
 
 // Kernels of kernels.cu (host-callable handles).
-OffspringKernel offspring_kernel(uint32_t words, uint32_t items);
+OffspringKernel offspring_kernel(uint32_t words, uint32_t items, bool linked = false);
 int prepare_offspring(OffspringKernel &k);  // sets the shared-memory limit, fills `resident`
 GenKernel compact_kernel();
 bool supported_items(uint32_t words, uint32_t items);

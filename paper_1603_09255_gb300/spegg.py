@@ -44,6 +44,7 @@ class spg_pop_desc(ctypes.Structure):
         ("replicate", ctypes.c_uint32), ("effects", ctypes.c_void_p), ("init_genotypes", ctypes.c_void_p),
         ("p0_q32", ctypes.c_uint32), ("surv_table", ctypes.c_void_p), ("bin_bias", ctypes.c_int32),
         ("bin_shift", ctypes.c_uint32), ("mu", ctypes.c_double), ("stats_capacity", ctypes.c_uint32),
+        ("map_morgans", ctypes.c_void_p),
     ]
 
 
@@ -260,7 +261,8 @@ class Population:
 
     def __init__(self, n: int, n_loci: int, seed: int, replicate: int, effects, surv_table, bin_bias: int,
                  bin_shift: int, mu: float, init_genotypes=None, p0_q32: int = 0x80000000,
-                 stats_capacity: int = 0, stream=None, allocator: Optional[TorchAllocator] = None):
+                 stats_capacity: int = 0, stream=None, allocator: Optional[TorchAllocator] = None,
+                 map_morgans=None):
         L = lib()
         self.n, self.n_loci, self.words = int(n), int(n_loci), int(n_loci) // 32
         e = np.ascontiguousarray(effects, dtype=np.int16)
@@ -268,9 +270,12 @@ class Population:
         if t.shape != (N_BINS,) or e.shape != (self.n_loci,):
             raise ValueError("surv_table must have 4096 entries and effects n_loci entries")
         g = None if init_genotypes is None else _u32(init_genotypes).reshape(-1)
+        m = None if map_morgans is None else np.ascontiguousarray(map_morgans, dtype=np.float64)
+        if m is not None and m.shape != (self.n_loci,):
+            raise ValueError("map_morgans must have n_loci entries")
         d = spg_pop_desc(self.n, self.n_loci, int(seed), int(replicate), e.ctypes.data,
                          None if g is None else g.ctypes.data, int(p0_q32), t.ctypes.data, int(bin_bias),
-                         int(bin_shift), float(mu), int(stats_capacity))
+                         int(bin_shift), float(mu), int(stats_capacity), None if m is None else m.ctypes.data)
         self.allocator = allocator if allocator is not None else TorchAllocator()
         self._stream = _stream_handle(stream)
         h = ctypes.c_void_p()
@@ -280,6 +285,7 @@ class Population:
 
     @classmethod
     def from_workload(cls, w, **kw) -> "Population":
+        kw.setdefault("map_morgans", getattr(w, "map_morgans", None))
         p = cls(w.n, w.n_loci, w.seed, w.replicate, w.effects, w.surv_table, w.bias, w.shift, w.mu,
                 w.init_genotypes, w.p0_q32, **kw)
         if w.has_ecology:
@@ -362,10 +368,12 @@ def _desc_for(w, keep: list, stats_capacity: int = 0) -> spg_pop_desc:
     e = np.ascontiguousarray(w.effects, dtype=np.int16)
     t = _u32(w.surv_table)
     g = None if w.init_genotypes is None else _u32(w.init_genotypes).reshape(-1)
-    keep.extend([e, t, g])
+    mm = getattr(w, "map_morgans", None)
+    m = None if mm is None else np.ascontiguousarray(mm, dtype=np.float64)
+    keep.extend([e, t, g, m])
     return spg_pop_desc(int(w.n), int(w.n_loci), int(w.seed), int(w.replicate), e.ctypes.data,
                         None if g is None else g.ctypes.data, int(w.p0_q32), t.ctypes.data, int(w.bias),
-                        int(w.shift), float(w.mu), int(stats_capacity))
+                        int(w.shift), float(w.mu), int(stats_capacity), None if m is None else m.ctypes.data)
 
 
 class Batch:
