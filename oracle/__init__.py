@@ -50,6 +50,8 @@ def lib():
         L.orc_set_ecology.restype = ctypes.c_int
         L.orc_set_linkage.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.orc_set_linkage.restype = ctypes.c_int
+        L.orc_set_weights.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_set_weights.restype = ctypes.c_int
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
         L.orc_step.restype = ctypes.c_int
         L.orc_read_genotypes.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
@@ -129,6 +131,8 @@ class OraclePopulation:
             p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack)
         if getattr(w, "map_morgans", None) is not None:
             p.set_linkage(w.map_morgans)
+        if getattr(w, "mother_weights", None) is not None or getattr(w, "father_weights", None) is not None:
+            p.set_weights(w.mother_weights, w.father_weights)
         return p
 
     def set_ecology(self, r, K, R0, R_half, attack):
@@ -144,6 +148,18 @@ class OraclePopulation:
         assert m.shape == (self.n_loci,)
         if lib().orc_set_linkage(self._h, m.ctypes.data) != 0:
             raise ValueError("oracle rejected the linkage map")
+
+    def set_weights(self, mother_weights, father_weights):
+        """Weighted parents: uint32 weights over the 4096 phenotype bins for
+        mothers and for fathers (None: uniform for that role)."""
+        m = None if mother_weights is None else _u32(mother_weights)
+        f = None if father_weights is None else _u32(father_weights)
+        for t in (m, f):
+            assert t is None or t.shape == (4096,)
+        rc = lib().orc_set_weights(self._h, None if m is None else m.ctypes.data,
+                                   None if f is None else f.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle rejected the weight tables")
 
     def step(self, n_gen: int) -> np.ndarray:
         out = np.zeros(max(int(n_gen), 1), STATS_DTYPE)

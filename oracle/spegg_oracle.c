@@ -38,7 +38,14 @@
  *     crossovers per gamete (D = total map length) each falling in interval l
  *     with probability d_l / D; a locus takes the haplotype given by its
  *     chromosome's fair coin, flipped once per crossover in the intervals from
- *     the chromosome's first locus up to it.
+ *     the chromosome's first locus up to it;
+ *   - weighted parents (S2 "Reproduction": the chance that an individual
+ *     parents an egg grows with its size relative to the others; optional,
+ *     uniform otherwise): caller weight tables over the phenotype bins, one
+ *     for mothers and one for fathers, applied to each survivor's bin at
+ *     birth; each parent is drawn by bounded rejection sampling: a uniform
+ *     survivor r is proposed and accepted with probability w(bin_r) / w_max,
+ *     at most 64 proposals, the last one taken if all are rejected.
  *
  * Genotypes are kept UNPACKED here (one byte per allele copy) so that the
  * per-locus statement of the model is visible; packing is done only when
@@ -59,7 +66,9 @@
 #define ORC_LINK_SITES 65536u /* crossover opportunities per gamete */
 #define ORC_MAX_MAP 16.0      /* Morgans, total map length */
 
-enum { ORC_INIT = 1, ORC_MATE = 2, ORC_RECOMB = 3, ORC_MUTPOS = 4, ORC_LINK = 5 };
+#define ORC_MATE_ATTEMPTS 64
+
+enum { ORC_INIT = 1, ORC_MATE = 2, ORC_RECOMB = 3, ORC_MUTPOS = 4, ORC_LINK = 5, ORC_MATEW = 6 };
 enum { ORC_OK = 0, ORC_EXTINCT = 1, ORC_ERR_INVALID = -1, ORC_ERR_OOM = -2 };
 
 /* One record per generation; same field order as the library's statistics
@@ -95,6 +104,10 @@ typedef struct {
     uint32_t link_cum[ORC_MAX_LOCI];            /* crossover interval CDF */
     uint32_t chrom_of[ORC_MAX_LOCI];            /* chromosome of each locus */
     uint32_t nchrom;
+    /* weighted parents (weighted == 0: uniform) */
+    int weighted;
+    uint32_t acc_mother[ORC_BINS], acc_father[ORC_BINS]; /* acceptance thresholds, Q32 */
+    uint16_t *bin_par, *bin_chi;                       /* phenotype bin of each individual at birth */
     /* ecology */
     int has_eco;
     double r, K, R, R_half;
@@ -107,6 +120,10 @@ typedef struct {
     uint8_t *chi; /* [n][2][L] offspring being formed                      */
     uint32_t *surv, *surv_next;
 } orc_pop;
+
+static int32_t phenotype_unpacked(const int16_t *effects, uint32_t L, const uint8_t *hap0,
+                                  const uint8_t *hap1);
+static uint32_t bin_of(const orc_pop *p, int32_t raw);
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, from its published definition: 10 rounds of
@@ -217,6 +234,8 @@ void orc_destroy(orc_pop *p)
 {
     if (!p) return;
     free(p->effects); free(p->par); free(p->chi); free(p->surv); free(p->surv_next);
+    free(p->bin_par);
+    free(p->bin_chi);
     free(p);
 }
 
@@ -237,7 +256,12 @@ orc_pop *orc_create(uint32_t n, uint32_t L, uint64_t seed, uint32_t replicate,
     p->chi = (uint8_t *)malloc((size_t)n * 2 * L);
     p->surv = (uint32_t *)malloc(sizeof(uint32_t) * n);
     p->surv_next = (uint32_t *)malloc(sizeof(uint32_t) * n);
-    if (!p->effects || !p->par || !p->chi || !p->surv || !p->surv_next) { orc_destroy(p); return NULL; }
+    p->bin_par = (uint16_t *)malloc(sizeof(uint16_t) * n);
+    p->bin_chi = (uint16_t *)malloc(sizeof(uint16_t) * n);
+    if (!p->effects || !p->par || !p->chi || !p->surv || !p->surv_next || !p->bin_par || !p->bin_chi) {
+        orc_destroy(p);
+        return NULL;
+    }
     memcpy(p->effects, effects, sizeof(int16_t) * L);
     memcpy(p->table, surv_table, sizeof(uint32_t) * ORC_BINS);
     p->bias = bias; p->shift = shift; p->mu = mu;
@@ -262,6 +286,8 @@ orc_pop *orc_create(uint32_t n, uint32_t L, uint64_t seed, uint32_t replicate,
             }
         }
         p->surv[i] = i; /* every founder is a potential parent */
+        const uint8_t *h = p->par + (size_t)i * 2 * L;
+        p->bin_par[i] = (uint16_t)bin_of(p, phenotype_unpacked(p->effects, L, h, h + L));
     }
     p->S = n;
     return p;
@@ -373,6 +399,48 @@ static void linked_gamete(const orc_pop *p, uint32_t j, uint32_t g, uint32_t pi,
     }
 }
 
+/* Weighted parents: acceptance threshold of bin b = floor(2^32 * w[b] / w_max)
+ * in integer arithmetic, 0xFFFFFFFF where w[b] == w_max (always accepted);
+ * a NULL table means uniform (every threshold 0xFFFFFFFF). */
+static int weight_thresholds(const uint32_t *w, uint32_t *acc)
+{
+    if (!w) {
+        for (uint32_t b = 0; b < ORC_BINS; ++b) acc[b] = ORC_CERTAIN;
+        return ORC_OK;
+    }
+    uint32_t mx = 0;
+    for (uint32_t b = 0; b < ORC_BINS; ++b) if (w[b] > mx) mx = w[b];
+    if (mx == 0) return ORC_ERR_INVALID;
+    for (uint32_t b = 0; b < ORC_BINS; ++b)
+        acc[b] = w[b] == mx ? ORC_CERTAIN : (uint32_t)(((uint64_t)w[b] << 32) / mx);
+    return ORC_OK;
+}
+
+int orc_set_weights(orc_pop *p, const uint32_t *mother_w, const uint32_t *father_w)
+{
+    if (!p || (!mother_w && !father_w)) return ORC_ERR_INVALID;
+    if (weight_thresholds(mother_w, p->acc_mother) != ORC_OK) return ORC_ERR_INVALID;
+    if (weight_thresholds(father_w, p->acc_father) != ORC_OK) return ORC_ERR_INVALID;
+    p->weighted = 1;
+    return ORC_OK;
+}
+
+/* One weighted parent of offspring j (pi = 0 mother, 1 father): proposal k
+ * (k = 0..63) uses lanes 2(k%2) (survivor rank, floor(u S / 2^32)) and
+ * 2(k%2)+1 (acceptance) of Philox(j, g, rep, MATEW<<24 | pi<<8 | k/2). */
+static uint32_t weighted_parent(const orc_pop *p, uint32_t j, uint32_t g, uint32_t pi, const uint32_t *acc)
+{
+    uint32_t r = 0;
+    for (uint32_t k = 0; k < ORC_MATE_ATTEMPTS; ++k) {
+        uint32_t d[4];
+        draw4(p, j, g, ORC_MATEW, (pi << 8) | (k / 2), d);
+        r = scaled_index(d[2 * (k % 2)], p->S);
+        uint32_t a = acc[p->bin_par[p->surv[r]]];
+        if (a == ORC_CERTAIN || d[2 * (k % 2) + 1] < a) break;
+    }
+    return p->surv[r];
+}
+
 /* Logistic update with consumption C (attack units in Q16):
  *   R' = (R + (r*R) * (1 - R/K)) - C * 2^-16, clamped at 0. */
 static double resource_update(double R, double r, double K, uint64_t C)
@@ -407,8 +475,14 @@ static void one_generation(orc_pop *p, orc_stats *st)
         /* (A) parents: two uniform draws over the previous survivors */
         uint32_t d[4];
         draw4(p, j, g, ORC_MATE, 0, d);
-        uint32_t mother = p->surv[scaled_index(d[0], S)];
-        uint32_t father = p->surv[scaled_index(d[1], S)];
+        uint32_t mother, father;
+        if (p->weighted) {
+            mother = weighted_parent(p, j, g, 0, p->acc_mother);
+            father = weighted_parent(p, j, g, 1, p->acc_father);
+        } else {
+            mother = p->surv[scaled_index(d[0], S)];
+            father = p->surv[scaled_index(d[1], S)];
+        }
         uint32_t u_surv = d[2];
         uint32_t u_mut = d[3];
 
@@ -464,6 +538,7 @@ static void one_generation(orc_pop *p, orc_stats *st)
 
         /* (D) survival against the selective environment */
         uint32_t b = bin_of(p, raw);
+        p->bin_chi[j] = (uint16_t)b;
         uint32_t thr = p->table[b];
         if (p->f != ORC_CERTAIN) thr = (uint32_t)(((uint64_t)thr * (uint64_t)p->f) >> 32);
         int alive = (thr == ORC_CERTAIN) || (u_surv < thr);
@@ -500,6 +575,7 @@ static void one_generation(orc_pop *p, orc_stats *st)
     /* the offspring become the next generation's parents */
     uint8_t *t8 = p->par; p->par = p->chi; p->chi = t8;
     uint32_t *t32 = p->surv; p->surv = p->surv_next; p->surv_next = t32;
+    uint16_t *t16 = p->bin_par; p->bin_par = p->bin_chi; p->bin_chi = t16;
     p->S = survivors;
     p->gen = g;
     if (survivors == 0) p->status = ORC_EXTINCT;

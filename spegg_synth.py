@@ -172,6 +172,9 @@ class Workload:
     # linkage map (None: free recombination): distance in Morgans between loci
     # l-1 and l, negative where locus l starts a new chromosome
     map_morgans: Optional[np.ndarray] = None
+    # weighted parents (None: uniform): uint32 weights over the phenotype bins
+    mother_weights: Optional[np.ndarray] = None
+    father_weights: Optional[np.ndarray] = None
 
     @property
     def words(self) -> int:
@@ -201,6 +204,23 @@ def with_linkage(w: "Workload", chromosomes: int = 4, morgans: float = 1.0) -> "
     import dataclasses
     return dataclasses.replace(w, map_morgans=linkage_map(w.n_loci, chromosomes, morgans),
                                name=w.name + f"+map{chromosomes}x{morgans:g}M")
+
+
+def fecundity_weights(bias: int, shift: int, slope: float = 1.0, theta: float = 0.0) -> np.ndarray:
+    """Parent weights rising with the trait: w(z) = 2^16 (1 + tanh(slope (z -
+    theta))) + 1 at each bin centre (always positive), as uint32."""
+    z = bin_centre_trait(bias, shift)
+    w = np.floor(65536.0 * (1.0 + np.tanh(slope * (z - theta)))) + 1.0
+    return w.astype(np.uint32)
+
+
+def with_weights(w: "Workload", slope: float = 1.0) -> "Workload":
+    """The same workload with trait-dependent mother and father weights
+    (fathers twice as steep, as for size-dependent male success)."""
+    import dataclasses
+    return dataclasses.replace(w, mother_weights=fecundity_weights(w.bias, w.shift, slope),
+                               father_weights=fecundity_weights(w.bias, w.shift, 2.0 * slope),
+                               name=w.name + f"+weights{slope:g}")
 
 
 def single_species(n: int = 10_000, n_loci: int = 32, n_gen: int = 100, mu: float = 1e-4,
