@@ -227,11 +227,9 @@ def served_sweep(spegg, torch, count: int = 48, rate: float = 200.0):
             "peak_memory_gb": c["peak_memory_used"] / 1e9}
 
 
-def linked_population(spegg, torch, gens: int = 256):
-    """The consumer-resource population (N = 10^6, L = 128) with a linkage map
-    of 4 chromosomes of 1 Morgan each (Haldane crossovers instead of free
-    recombination), `gens` generations after 64, CUDA events on its stream."""
-    w = S.with_linkage(S.consumer_resource(), 4, 1.0)
+def variant_population(spegg, torch, w, label: str, gens: int = 256):
+    """One variant of the consumer-resource population (N = 10^6, L = 128),
+    `gens` generations after 64, L2 flushed before, CUDA events on its stream."""
     stream = torch.cuda.Stream()
     pop = spegg.Population.from_workload(w, stats_capacity=gens + 128, stream=stream)
     pop.step(64)
@@ -249,7 +247,7 @@ def linked_population(spegg, torch, gens: int = 256):
     ms = a.elapsed_time(b)
     peak, source = load_peaks()
     achieved = w.n * (12 + 24 * w.words) * gens / (ms / 1e3) / 1e9
-    out = {"workload": f"consumer-resource N={w.n} L={w.n_loci}, linkage map 4 chromosomes x 1 Morgan, "
+    out = {"workload": f"consumer-resource N={w.n} L={w.n_loci}, {label}, "
                        f"{gens} generations after 64 (L2 flushed before)",
            "value": w.n * gens / (ms / 1e3), "unit": "individual-generations/s", "us_per_generation": ms * 1e3 / gens,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -321,6 +319,7 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="omit the served-sweep measurement")
     ap.add_argument("--no-spatial", action="store_true", help="omit the spatial-community measurement")
     ap.add_argument("--no-linked", action="store_true", help="omit the linkage-map measurement")
+    ap.add_argument("--no-weighted", action="store_true", help="omit the weighted-parents measurement")
     args = ap.parse_args()
     workload = S.consumer_resource()
     if args.impl == "reference":
@@ -415,7 +414,10 @@ def main():
     batched = None if args.no_batched else batched_replicates(spegg, torch)
     served = None if args.no_served else served_sweep(spegg, torch)
     spatial = None if args.no_spatial else spatial_community(spegg, torch)
-    linked = None if args.no_linked else linked_population(spegg, torch)
+    linked = None if args.no_linked else variant_population(
+        spegg, torch, S.with_linkage(S.consumer_resource(), 4, 1.0), "linkage map 4 chromosomes x 1 Morgan")
+    weighted = None if args.no_weighted else variant_population(
+        spegg, torch, S.with_weights(S.consumer_resource()), "parents weighted by trait (1 + tanh z; fathers 2z)")
     if rank != 0:
         return
     line = {
@@ -442,6 +444,8 @@ def main():
         line["spatial"] = spatial
     if linked is not None:
         line["linked"] = linked
+    if weighted is not None:
+        line["weighted"] = weighted
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload)
     print(json.dumps(line))

@@ -44,7 +44,20 @@
  *             of crossover-CDF entries <= u, lanes 1..3 -> the coins of
  *             chromosomes 0..31, 32..63, 64..95 (bit c%32); crossover a uses
  *             lane a%4 of sub pi<<8 | (1 + a/4) and lies in interval
- *             I = number of interval-CDF entries cum[0..L-2] <= u.
+ *             I = number of interval-CDF entries cum[0..L-2] <= u;
+ *   weighted  purpose 6 (populations with parent weights, replacing lanes 0
+ *   parents   and 1 of purpose 2): proposal k = 0..63 for parent pi uses lanes
+ *             2(k%2) (survivor rank floor(u * S / 2^32)) and 2(k%2)+1
+ *             (acceptance v) of sub pi<<8 | k/2; the proposal is taken iff
+ *             the threshold t of the survivor's bin is 0xFFFFFFFF or v < t,
+ *             the last proposal if all 64 are rejected.
+ * Parent weights (S2 "Reproduction": the chance to parent an egg grows with
+ * the parent's size relative to the others'): uint32 weights over the 4096
+ * phenotype bins, one table for mothers and one for fathers, applied to each
+ * survivor's bin at birth; threshold t[b] = floor(2^32 * w[b] / max w) in
+ * integer arithmetic, 0xFFFFFFFF where w[b] is the maximum (bounded
+ * rejection sampling: each parent is drawn with probability proportional to
+ * its weight, up to the 64-proposal bound).
  * Linkage map (the paper's variable linkage maps, read as Haldane's
  * no-interference model): map_morgans[l] (l >= 1) is the distance in Morgans
  * between loci l-1 and l, or negative where locus l starts a new chromosome;
@@ -125,6 +138,10 @@ typedef struct {
     const double *map_morgans;      /* [L] linkage map (see above), copied; NULL: free  */
                                     /* recombination.  Single populations only: batch   */
                                     /* and server calls reject a map (SPG_ERR_INVALID). */
+    const uint32_t *mother_weights; /* [4096] parent weights by bin (see above), copied;*/
+    const uint32_t *father_weights; /* NULL: uniform for that role.  Single populations */
+                                    /* only, like map_morgans; a table whose weights   */
+                                    /* are all 0 is SPG_ERR_INVALID.                    */
 } spg_pop_desc;
 
 /* Consumer-resource ecology (Fig. 1F; S2 "Resource Consumption"): after the

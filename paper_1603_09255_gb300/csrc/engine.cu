@@ -143,6 +143,8 @@ int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
     prm.stats_cap = d->stats_capacity ? d->stats_capacity : 1024u;
     prm.linked = d->map_morgans ? 1u : 0u;
     prm.link = nullptr;  // set once the population's memory exists
+    prm.weighted = (d->mother_weights || d->father_weights) ? 1u : 0u;
+    prm.weights = nullptr;
     return SPG_OK;
 }
 
@@ -197,10 +199,31 @@ int build_link(const double *map, uint32_t n_loci, LinkParams &lp) {
     return SPG_OK;
 }
 
+// Weighted parents: t[b] = floor(2^32 * w[b] / max w) (integer arithmetic),
+// 0xFFFFFFFF where w[b] is the maximum; a NULL table is uniform.
+static int weight_thresholds(const uint32_t *w, uint32_t *acc, const char *role) {
+    if (!w) {
+        for (int b = 0; b < kBins; ++b) acc[b] = kCertain;
+        return SPG_OK;
+    }
+    uint32_t mx = 0;
+    for (int b = 0; b < kBins; ++b) mx = std::max(mx, w[b]);
+    if (mx == 0) return fail(SPG_ERR_INVALID, "%s weights are all zero", role);
+    for (int b = 0; b < kBins; ++b)
+        acc[b] = w[b] == mx ? kCertain : (uint32_t)(((uint64_t)w[b] << 32) / mx);
+    return SPG_OK;
+}
+
+int build_weights(const uint32_t *mother_w, const uint32_t *father_w, WeightParams &wp) {
+    int rc = weight_thresholds(mother_w, wp.acc[0], "mother");
+    if (rc == SPG_OK) rc = weight_thresholds(father_w, wp.acc[1], "father");
+    return rc;
+}
+
 // ------------------------------------------------------------ population
 uint32_t bucket_count(uint32_t n) { return (n + kBucket - 1) / kBucket; }
 
-PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap) {
+PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap, bool weighted) {
     PopLayout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -220,6 +243,12 @@ PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap
     L.ring = take((size_t)cap * sizeof(spg_stats));
     L.segment = take(sizeof(Segment));
     L.link = take(sizeof(LinkParams));
+    L.weighted = weighted;
+    if (weighted) {
+        L.weights = take(sizeof(WeightParams));
+        L.obin = take((size_t)n * 2);
+        L.survw = take((size_t)n * 8);
+    }
     L.total = off;
     return L;
 }
@@ -237,6 +266,10 @@ Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, 
     s.alive = reinterpret_cast<uint32_t *>(base + L.alive);
     s.bucket_sum = reinterpret_cast<uint32_t *>(base + L.buckets);
     s.state = reinterpret_cast<DevState *>(base + L.state);
+    if (L.weighted) {
+        s.obin = reinterpret_cast<uint16_t *>(base + L.obin);
+        s.survw = reinterpret_cast<unsigned long long *>(base + L.survw);
+    }
     s.ring = reinterpret_cast<spg_stats *>(base + L.ring);
     s.tile_begin = tile_begin;
     s.ntiles = ntiles;
@@ -409,6 +442,11 @@ int view_init(const PopView &v, const PopParams &prm, const uint32_t *init_genot
         rc = launch_founders(v.words, geno0, surv0, v.n, prm.key0, prm.key1, prm.rep, p0_q32, v.stream);
     }
     if (rc != SPG_OK) return fail(rc, "founder launch failed");
+    if (v.L.weighted) {  // every founder is a potential parent, in index order
+        rc = launch_survivor_bins(reinterpret_cast<const PopParams *>(v.base + v.L.params), v.words, geno0, nullptr,
+                                  v.n, reinterpret_cast<unsigned long long *>(v.base + v.L.survw), v.stream);
+        if (rc != SPG_OK) return fail(rc, "survivor-bin launch failed");
+    }
     rc = view_set_state(v, 0, v.n, kCertain, 0.0, SPG_OK, 0xFFFFFFFFu);
     return rc == SPG_OK ? SPG_OK : fail(rc, "state launch failed");
 }

@@ -462,12 +462,34 @@ struct SegCtx {
     const uint32_t *sin;
     uint32_t *alive;
     uint32_t *bucket_now;
+    const unsigned long long *survw;   // weighted parents: survivor index | bin << 32
+    const WeightParams *wt;            // weighted parents: acceptance thresholds
+    uint16_t *obin;                    // weighted parents: bins of the offspring formed
     uint32_t n, S, f, g, rep, k0, k1, kmax, nplanes, shift;
     int32_t e_min, bias;
     bool has_eco;
 };
 
-template <int ITEMS>
+// One weighted parent (pi = 0 mother, 1 father) by bounded rejection
+// sampling: proposal k draws a uniform survivor rank and an acceptance value
+// (lanes 2(k%2), 2(k%2)+1 of Philox sub pi<<8 | k/2) and is taken when the
+// survivor's bin threshold is certain or above the value; the last proposal
+// stands if all kMateAttempts are rejected.
+__device__ __forceinline__ uint32_t weighted_parent(const SegCtx &c, uint32_t j, uint32_t pi) {
+    const uint32_t *acc = c.wt->acc[pi];
+    unsigned long long e = 0;
+    uint4 d = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t k = 0; k < kMateAttempts; ++k) {
+        if ((k & 1u) == 0u) d = philox(make_uint4(j, c.g, c.rep, (kMateW << 24) | (pi << 8) | (k >> 1)), c.k0, c.k1);
+        const uint32_t u = (k & 1u) ? d.z : d.x, v = (k & 1u) ? d.w : d.y;
+        e = __ldcg(c.survw + __umulhi(u, c.S));
+        const uint32_t t = __ldg(acc + (uint32_t)(e >> 32));
+        if (t == kCertain || v < t) break;
+    }
+    return (uint32_t)e;
+}
+
+template <int ITEMS, bool WEIGHTED = false>
 __device__ __forceinline__ void draw_parents(const SegCtx &c, uint32_t base, int tid, TileDraws<ITEMS> &d) {
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
@@ -477,8 +499,13 @@ __device__ __forceinline__ void draw_parents(const SegCtx &c, uint32_t base, int
             const uint4 r = philox(make_uint4(j, c.g, c.rep, kMate << 24), c.k0, c.k1);
             // survivor indices through L2 only: random 4-byte reads would
             // evict the threshold table from L1
-            d.mom[it] = __ldcg(c.sin + __umulhi(r.x, c.S));
-            d.dad[it] = __ldcg(c.sin + __umulhi(r.y, c.S));
+            if constexpr (WEIGHTED) {
+                d.mom[it] = weighted_parent(c, j, 0u);
+                d.dad[it] = weighted_parent(c, j, 1u);
+            } else {
+                d.mom[it] = __ldcg(c.sin + __umulhi(r.x, c.S));
+                d.dad[it] = __ldcg(c.sin + __umulhi(r.y, c.S));
+            }
             d.u_surv[it] = r.z;
             d.u_mut[it] = r.w;
         }
@@ -537,7 +564,7 @@ struct ThreadStats {
 };
 
 // One tile: gametes (B), phenotype (C), survival (D), bitmap (E, first half).
-template <int W, int ITEMS, bool LINKED>
+template <int W, int ITEMS, bool LINKED, bool WEIGHTED>
 __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t base, int tid, int lane, int warp,
                                                    const unsigned char *s_dyn, int stage, const uint32_t *s_planes,
                                                    const uint32_t *s_cdf, ThreadStats &ts, const LinkSmem &lk) {
@@ -594,6 +621,7 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
             const int32_t raw = phenotype<W>(ch, s_planes, c.nplanes, c.e_min, allele, hz);
             const long long v = (long long)raw + (long long)c.bias;
             const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> c.shift, (long long)(kBins - 1));
+            if constexpr (WEIGHTED) c.obin[j] = (uint16_t)bin;
             uint32_t thr = __ldg(&c.P->table[bin]);
             if (c.f != kCertain) thr = __umulhi(thr, c.f);
             alive = (thr == kCertain) || (u.x < thr);
@@ -618,7 +646,7 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
 }
 
 // --------------------------------------------- offspring kernel (Fig. 1A-D)
-template <int W, int ITEMS, bool LINKED>
+template <int W, int ITEMS, bool LINKED, bool WEIGHTED>
 __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __grid_constant__ GenArgs a) {
     constexpr int NW = kBlock / 32;
     constexpr uint32_t TILE = (uint32_t)(kBlock * ITEMS);
@@ -659,6 +687,9 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
             c.chi = sg.geno[(now.gen + 1u) & 1u];
             c.sin = sg.surv[now.gen & 1u];
             c.alive = sg.alive;
+            c.survw = sg.survw;
+            c.obin = sg.obin;
+            c.wt = sg.prm->weights;
             c.bucket_now = sg.bucket_sum + (c.g & 1u) * sg.nbuckets;
             uint32_t *bucket_next = sg.bucket_sum + ((c.g + 1u) & 1u) * sg.nbuckets;
             c.rep = c.P->rep;
@@ -706,13 +737,13 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
             for (int k = 0; k < R; ++k) {
                 const uint32_t tk = lt0 + (uint32_t)k;
                 if (tk < lt1) {
-                    draw_parents<ITEMS>(c, tk * TILE, tid, dA);
+                    draw_parents<ITEMS, WEIGHTED>(c, tk * TILE, tid, dA);
                     stage_parents<W, ITEMS>(c, tk * TILE, tid, dA, s_dyn, s_base, k);
                 }
                 cp_async_commit();
             }
-            if (lt0 + R < lt1) draw_parents<ITEMS>(c, (lt0 + R) * TILE, tid, dA);
-            if (lt0 + R + 1 < lt1) draw_parents<ITEMS>(c, (lt0 + R + 1) * TILE, tid, dB);
+            if (lt0 + R < lt1) draw_parents<ITEMS, WEIGHTED>(c, (lt0 + R) * TILE, tid, dA);
+            if (lt0 + R + 1 < lt1) draw_parents<ITEMS, WEIGHTED>(c, (lt0 + R + 1) * TILE, tid, dB);
             int stage = 0;
             for (uint32_t lt = lt0; lt < lt1; ++lt) {
                 const uint32_t base = lt * TILE;
@@ -720,7 +751,7 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
                 if (lt + R < lt1) stage_parents<W, ITEMS>(c, base + R * TILE, tid, dA, s_dyn, s_base, ahead);
                 cp_async_commit();
                 dA = dB;
-                if (lt + R + 2 < lt1) draw_parents<ITEMS>(c, base + (R + 2) * TILE, tid, dB);
+                if (lt + R + 2 < lt1) draw_parents<ITEMS, WEIGHTED>(c, base + (R + 2) * TILE, tid, dB);
                 cp_async_wait<R>();
                 if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
                 const uint32_t bkt = base / kBucket;
@@ -730,7 +761,8 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
                     bucket_cur = bkt;
                 }
                 const uint32_t cnt =
-                    offspring_tile<W, ITEMS, LINKED>(c, base, tid, lane, warp, s_dyn, stage, s_planes, s_cdf, ts, lk);
+                    offspring_tile<W, ITEMS, LINKED, WEIGHTED>(c, base, tid, lane, warp, s_dyn, stage, s_planes, s_cdf,
+                                                               ts, lk);
                 bucket_alive += cnt;
                 warp_alive += cnt;
                 stage = stage + 1 == St::kStages ? 0 : stage + 1;
@@ -849,7 +881,11 @@ __device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
     for (int k = 0; k < 32; ++k) {
         const uint32_t word = __shfl_sync(0xFFFFFFFFu, bits, k);
         const uint32_t r0 = __shfl_sync(0xFFFFFFFFu, excl, k);
-        if ((word >> lane) & 1u) sout[r0 + __popc(word & lt)] = (w0 + (uint32_t)k) * 32u + (uint32_t)lane;
+        if ((word >> lane) & 1u) {
+            const uint32_t rank = r0 + __popc(word & lt), idx = (w0 + (uint32_t)k) * 32u + (uint32_t)lane;
+            sout[rank] = idx;
+            if (sg.survw) sg.survw[rank] = (unsigned long long)idx | ((unsigned long long)__ldcg(sg.obin + idx) << 32);
+        }
     }
     }
     // every block has read the state by now (its values fed the stores
@@ -901,6 +937,34 @@ __global__ void k_iota(uint32_t *__restrict__ surv, uint32_t n) {
     if (i < n) surv[i] = i;
 }
 
+// survw[r] = surv[r] | bin << 32 for the current survivors, each bin from
+// its record's additive phenotype (planes read from the parameters).
+template <int W>
+__global__ void k_survivor_bins(const PopParams *__restrict__ P, const uint32_t *__restrict__ geno,
+                                const uint32_t *__restrict__ surv, uint32_t S, unsigned long long *__restrict__ survw) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= S) return;
+    const uint32_t idx = surv ? surv[r] : r;
+    uint32_t rec[2 * W];
+    load_record<W>(geno + (size_t)idx * (2 * W), rec);
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) total += __popc(rec[w]) + __popc(rec[W + w]);
+    int32_t raw = P->e_min * (int32_t)total;
+    for (uint32_t b = 0; b < P->nplanes; ++b) {
+        int32_t cnt = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint32_t pl = P->planes[b * W + w];
+            cnt += __popc(pl & rec[w]) + __popc(pl & rec[W + w]);
+        }
+        raw += cnt << b;
+    }
+    const long long v = (long long)raw + (long long)P->bias;
+    const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> P->shift, (long long)(kBins - 1));
+    survw[r] = (unsigned long long)idx | ((unsigned long long)bin << 32);
+}
+
 __global__ void k_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R,
                             int32_t status, uint32_t target) {
     if (threadIdx.x == 0) {
@@ -926,25 +990,31 @@ uint32_t tile_size(uint32_t items) { return (uint32_t)kBlock * items; }
 GenKernel compact_kernel() { return &k_compact; }
 
 namespace {
-template <int W, int I, bool LINKED = false>
+template <int W, int I, bool LINKED = false, bool WEIGHTED = false>
 OffspringKernel make_offspring() {
     OffspringKernel k;
-    k.fn = &k_offspring<W, I, LINKED>;
+    k.fn = &k_offspring<W, I, LINKED, WEIGHTED>;
     k.smem = Staging<W, I>::kBytes;
     return k;
 }
+
+template <bool LINKED, bool WEIGHTED>
+OffspringKernel variant_kernel(uint32_t words) {
+    switch (words) {
+        case 1: return make_offspring<1, 1, LINKED, WEIGHTED>();
+        case 2: return make_offspring<2, 1, LINKED, WEIGHTED>();
+        case 4: return make_offspring<4, 1, LINKED, WEIGHTED>();
+        case 8: return make_offspring<8, 1, LINKED, WEIGHTED>();
+        default: return OffspringKernel{};
+    }
+}
 }  // namespace
 
-OffspringKernel offspring_kernel(uint32_t words, uint32_t items, bool linked) {
-    if (linked) {  // linkage maps: one offspring per thread
+OffspringKernel offspring_kernel(uint32_t words, uint32_t items, bool linked, bool weighted) {
+    if (linked || weighted) {  // linkage maps and weighted parents: one offspring per thread
         if (items != 1u) return OffspringKernel{};
-        switch (words) {
-            case 1: return make_offspring<1, 1, true>();
-            case 2: return make_offspring<2, 1, true>();
-            case 4: return make_offspring<4, 1, true>();
-            case 8: return make_offspring<8, 1, true>();
-            default: return OffspringKernel{};
-        }
+        if (linked && weighted) return variant_kernel<true, true>(words);
+        return linked ? variant_kernel<true, false>(words) : variant_kernel<false, true>(words);
     }
 #define SPG_CASE(Wv, Iv) \
     if (words == Wv && items == Iv) return make_offspring<Wv, Iv>();
@@ -989,6 +1059,21 @@ int launch_founders(uint32_t words, uint32_t *geno, uint32_t *surv, uint32_t n, 
 
 int launch_iota(uint32_t *surv, uint32_t n, void *stream) {
     k_iota<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(surv, n);
+    return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
+}
+
+int launch_survivor_bins(const PopParams *prm, uint32_t words, const uint32_t *geno, const uint32_t *surv,
+                         uint32_t S, unsigned long long *survw, void *stream) {
+    if (S == 0) return SPG_OK;
+    const dim3 grid((S + 255) / 256), block(256);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (words) {
+        case 1: k_survivor_bins<1><<<grid, block, 0, s>>>(prm, geno, surv, S, survw); break;
+        case 2: k_survivor_bins<2><<<grid, block, 0, s>>>(prm, geno, surv, S, survw); break;
+        case 4: k_survivor_bins<4><<<grid, block, 0, s>>>(prm, geno, surv, S, survw); break;
+        case 8: k_survivor_bins<8><<<grid, block, 0, s>>>(prm, geno, surv, S, survw); break;
+        default: return SPG_ERR_INVALID;
+    }
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
 }
 

@@ -29,6 +29,7 @@ struct spg_pop {
     PopLayout L{};
     PopParams *host_prm = nullptr;  // host copy of the parameters
     LinkParams link{};              // linkage-map tables (when host_prm->linked)
+    WeightParams *weights = nullptr;  // parent acceptance thresholds (when host_prm->weighted)
     GenLaunch gl;
     GraphChain chain;
 
@@ -50,7 +51,7 @@ namespace {
 // Point the launch at the population's single segment with `items` offspring
 // per thread (uploads the device copy of the segment; synchronous).
 int configure_launch(spg_pop *p, uint32_t items) {
-    OffspringKernel k = offspring_kernel(p->words, items, p->host_prm->linked != 0u);
+    OffspringKernel k = offspring_kernel(p->words, items, p->host_prm->linked != 0u, p->host_prm->weighted != 0u);
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
     p->items = items;
@@ -105,13 +106,17 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         delete p;
         return rc;
     }
-    if (desc->map_morgans) {
-        rc = build_link(desc->map_morgans, p->n_loci, p->link);
-        if (rc != SPG_OK) {
-            delete p->host_prm;
-            delete p;
-            return rc;
-        }
+    if (desc->map_morgans) rc = build_link(desc->map_morgans, p->n_loci, p->link);
+    if (rc == SPG_OK && p->host_prm->weighted) {
+        p->weights = new (std::nothrow) WeightParams();
+        rc = p->weights ? build_weights(desc->mother_weights, desc->father_weights, *p->weights)
+                        : fail(SPG_ERR_OOM, "host allocation failed");
+    }
+    if (rc != SPG_OK) {
+        delete p->weights;
+        delete p->host_prm;
+        delete p;
+        return rc;
     }
     p->cap = p->host_prm->stats_cap;
     p->nbuckets = bucket_count(p->n);
@@ -127,7 +132,7 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         }
         p->own_stream = true;
     }
-    p->L = layout_for(p->n, p->words, p->nbuckets, p->cap);
+    p->L = layout_for(p->n, p->words, p->nbuckets, p->cap, p->host_prm->weighted != 0u);
     p->arena = static_cast<char *>(p->alloc.alloc(p->L.total, p->stream));
     if (!p->arena) {
         spg_destroy(p);
@@ -140,6 +145,15 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         if (e != cudaSuccess) {
             spg_destroy(p);
             return cuda_fail(e, "upload linkage map");
+        }
+    }
+    if (p->host_prm->weighted) {
+        p->host_prm->weights = reinterpret_cast<const WeightParams *>(p->arena + p->L.weights);
+        const cudaError_t e = cudaMemcpyAsync(p->arena + p->L.weights, p->weights, sizeof(WeightParams),
+                                              cudaMemcpyHostToDevice, p->stream);
+        if (e != cudaSuccess) {
+            spg_destroy(p);
+            return cuda_fail(e, "upload parent weights");
         }
     }
     rc = view_init(p->view(), *p->host_prm, desc->init_genotypes, desc->p0_q32);
@@ -255,6 +269,14 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
     // generations about to be replayed
     if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4);
     if (e != cudaSuccess) return cuda_fail(e, "restore copy");
+    if (p->host_prm->weighted) {  // the restored survivors' bins, from their records
+        const uint32_t par = h.gen & 1u;
+        rc = launch_survivor_bins(reinterpret_cast<const PopParams *>(p->arena + p->L.params), p->words,
+                                  reinterpret_cast<const uint32_t *>(p->arena + (par ? p->L.geno1 : p->L.geno0)),
+                                  reinterpret_cast<const uint32_t *>(p->arena + (par ? p->L.surv1 : p->L.surv0)), h.S,
+                                  reinterpret_cast<unsigned long long *>(p->arena + p->L.survw), p->stream);
+        if (rc != SPG_OK) return fail(rc, "survivor-bin launch failed");
+    }
     rc = view_set_state(p->view(), h.gen, h.S, h.f, h.R, h.status, 0xFFFFFFFFu);
     if (rc != SPG_OK) return rc;
     return view_sync(p->view());
@@ -264,8 +286,8 @@ int spg_set_tiling(spg_pop *p, uint32_t items) {
     if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
     if (!supported_items(p->words, items))
         return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (1 or 2 for 256 loci); got %u", items);
-    if (p->host_prm->linked && items != 1u)
-        return fail(SPG_ERR_INVALID, "a population with a linkage map runs one offspring per thread");
+    if ((p->host_prm->linked || p->host_prm->weighted) && items != 1u)
+        return fail(SPG_ERR_INVALID, "a population with a linkage map or parent weights runs one offspring per thread");
     const int rc = view_sync(p->view());
     if (rc != SPG_OK) return rc;
     return configure_launch(p, items);
@@ -289,6 +311,7 @@ void spg_destroy(spg_pop *p) {
     if (p->arena) p->alloc.release(p->arena, p->stream);
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    delete p->weights;
     delete p->host_prm;
     delete p;
 }

@@ -33,7 +33,10 @@ struct Allocator {
 
 // Byte offsets of one population's buffers inside its arena.
 struct PopLayout {
-    size_t params, state, acc, geno0, geno1, surv0, surv1, alive, buckets, ring, segment, link, total;
+    size_t params, state, acc, geno0, geno1, surv0, surv1, alive, buckets, ring, segment, link;
+    size_t weights, obin, survw;  // weighted parents only (0 otherwise)
+    bool weighted;
+    size_t total;
 };
 
 // One population's device memory: its arena, layout and sizes.
@@ -73,7 +76,9 @@ int validate_desc(const spg_pop_desc *d);
 int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm);
 // Linkage-map tables from map_morgans[L] (validated; see spegg.h).
 int build_link(const double *map_morgans, uint32_t n_loci, LinkParams &lp);
-PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap);
+// Acceptance thresholds from the mother and father weight tables (NULL: uniform).
+int build_weights(const uint32_t *mother_w, const uint32_t *father_w, WeightParams &wp);
+PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap, bool weighted = false);
 Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, uint32_t tile_begin,
                    uint32_t nbuckets, uint32_t bucket_begin);
 uint32_t bucket_count(uint32_t n);

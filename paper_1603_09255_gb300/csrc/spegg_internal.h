@@ -28,7 +28,14 @@ constexpr double kMaxMapMorgans = 16.0;  // total length of a linkage map
 constexpr int kLinkGuide = 1024;         // guide-table entries of the crossover interval search
 
 // Philox counter word 3 = purpose << 24 | sub
-enum Purpose : uint32_t { kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4, kLink = 5 };
+enum Purpose : uint32_t { kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4, kLink = 5, kMateW = 6 };
+constexpr uint32_t kMateAttempts = 64;   // proposals per weighted parent
+
+// Acceptance thresholds of weighted parents (device global memory): acc[0]
+// mothers, acc[1] fathers, by phenotype bin (Q32, 0xFFFFFFFF = always).
+struct alignas(16) WeightParams {
+    uint32_t acc[2][kBins];
+};
 
 // Tables of a linkage map (device global memory, one per linked population).
 struct alignas(16) LinkParams {
@@ -63,7 +70,8 @@ struct alignas(16) PopParams {
     uint32_t stats_cap;
     const LinkParams *link;      // linkage map tables, or null (free recombination)
     uint32_t linked;
-    uint32_t pad_link;
+    uint32_t weighted;           // parents drawn by weight (weights != null)
+    const WeightParams *weights;
 };
 
 // Mutable per-population state (device global memory).
@@ -99,6 +107,8 @@ struct alignas(16) Segment {
     uint32_t *surv[2];                // ping-pong survivor lists [N]
     uint32_t *alive;                  // alive bitmap of the generation being formed [nbuckets * kBucketWords]
     uint32_t *bucket_sum;             // survivors per bucket, by generation parity [2][nbuckets]
+    uint16_t *obin;                   // weighted parents: phenotype bin of each offspring [N]
+    unsigned long long *survw;        // weighted parents: survivor index | bin << 32, by rank [N]
     DevState *state;
     StatAcc *acc;                     // [kAccCopies]
     spg_stats *ring;                  // [stats_cap]
@@ -132,7 +142,7 @@ struct OffspringKernel {
 };
 
 // Kernels of kernels.cu (host-callable handles).
-OffspringKernel offspring_kernel(uint32_t words, uint32_t items, bool linked = false);
+OffspringKernel offspring_kernel(uint32_t words, uint32_t items, bool linked = false, bool weighted = false);
 int prepare_offspring(OffspringKernel &k);  // sets the shared-memory limit, fills `resident`
 GenKernel compact_kernel();
 bool supported_items(uint32_t words, uint32_t items);
@@ -142,6 +152,10 @@ int launch_founders(uint32_t words, uint32_t *geno, uint32_t *surv, uint32_t n, 
                     uint32_t rep, uint32_t p0_q32, void *stream);
 // Enqueue survivors = 0..n-1 only (caller-supplied founders).
 int launch_iota(uint32_t *surv, uint32_t n, void *stream);
+// Enqueue survw[r] = surv[r] | bin << 32 for the S current survivors (surv
+// NULL: survivor r is record r), the bin computed from the record.
+int launch_survivor_bins(const PopParams *prm, uint32_t words, const uint32_t *geno, const uint32_t *surv,
+                         uint32_t S, unsigned long long *survw, void *stream);
 // Enqueue a state reset: state fields and cleared statistics accumulators.
 int launch_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,
                      uint32_t target, void *stream);

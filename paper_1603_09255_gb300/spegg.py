@@ -44,7 +44,7 @@ class spg_pop_desc(ctypes.Structure):
         ("replicate", ctypes.c_uint32), ("effects", ctypes.c_void_p), ("init_genotypes", ctypes.c_void_p),
         ("p0_q32", ctypes.c_uint32), ("surv_table", ctypes.c_void_p), ("bin_bias", ctypes.c_int32),
         ("bin_shift", ctypes.c_uint32), ("mu", ctypes.c_double), ("stats_capacity", ctypes.c_uint32),
-        ("map_morgans", ctypes.c_void_p),
+        ("map_morgans", ctypes.c_void_p), ("mother_weights", ctypes.c_void_p), ("father_weights", ctypes.c_void_p),
     ]
 
 
@@ -262,7 +262,7 @@ class Population:
     def __init__(self, n: int, n_loci: int, seed: int, replicate: int, effects, surv_table, bin_bias: int,
                  bin_shift: int, mu: float, init_genotypes=None, p0_q32: int = 0x80000000,
                  stats_capacity: int = 0, stream=None, allocator: Optional[TorchAllocator] = None,
-                 map_morgans=None):
+                 map_morgans=None, mother_weights=None, father_weights=None):
         L = lib()
         self.n, self.n_loci, self.words = int(n), int(n_loci), int(n_loci) // 32
         e = np.ascontiguousarray(effects, dtype=np.int16)
@@ -273,9 +273,15 @@ class Population:
         m = None if map_morgans is None else np.ascontiguousarray(map_morgans, dtype=np.float64)
         if m is not None and m.shape != (self.n_loci,):
             raise ValueError("map_morgans must have n_loci entries")
+        mw = None if mother_weights is None else _u32(mother_weights)
+        fw = None if father_weights is None else _u32(father_weights)
+        for x in (mw, fw):
+            if x is not None and x.shape != (N_BINS,):
+                raise ValueError("weight tables must have 4096 entries")
         d = spg_pop_desc(self.n, self.n_loci, int(seed), int(replicate), e.ctypes.data,
                          None if g is None else g.ctypes.data, int(p0_q32), t.ctypes.data, int(bin_bias),
-                         int(bin_shift), float(mu), int(stats_capacity), None if m is None else m.ctypes.data)
+                         int(bin_shift), float(mu), int(stats_capacity), None if m is None else m.ctypes.data,
+                         None if mw is None else mw.ctypes.data, None if fw is None else fw.ctypes.data)
         self.allocator = allocator if allocator is not None else TorchAllocator()
         self._stream = _stream_handle(stream)
         h = ctypes.c_void_p()
@@ -286,6 +292,8 @@ class Population:
     @classmethod
     def from_workload(cls, w, **kw) -> "Population":
         kw.setdefault("map_morgans", getattr(w, "map_morgans", None))
+        kw.setdefault("mother_weights", getattr(w, "mother_weights", None))
+        kw.setdefault("father_weights", getattr(w, "father_weights", None))
         p = cls(w.n, w.n_loci, w.seed, w.replicate, w.effects, w.surv_table, w.bias, w.shift, w.mu,
                 w.init_genotypes, w.p0_q32, **kw)
         if w.has_ecology:
@@ -370,10 +378,13 @@ def _desc_for(w, keep: list, stats_capacity: int = 0) -> spg_pop_desc:
     g = None if w.init_genotypes is None else _u32(w.init_genotypes).reshape(-1)
     mm = getattr(w, "map_morgans", None)
     m = None if mm is None else np.ascontiguousarray(mm, dtype=np.float64)
-    keep.extend([e, t, g, m])
+    mw = None if getattr(w, "mother_weights", None) is None else _u32(w.mother_weights)
+    fw = None if getattr(w, "father_weights", None) is None else _u32(w.father_weights)
+    keep.extend([e, t, g, m, mw, fw])
     return spg_pop_desc(int(w.n), int(w.n_loci), int(w.seed), int(w.replicate), e.ctypes.data,
                         None if g is None else g.ctypes.data, int(w.p0_q32), t.ctypes.data, int(w.bias),
-                        int(w.shift), float(w.mu), int(stats_capacity), None if m is None else m.ctypes.data)
+                        int(w.shift), float(w.mu), int(stats_capacity), None if m is None else m.ctypes.data,
+                        None if mw is None else mw.ctypes.data, None if fw is None else fw.ctypes.data)
 
 
 class Batch:
