@@ -52,6 +52,8 @@ def lib():
         L.orc_set_linkage.restype = ctypes.c_int
         L.orc_set_weights.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_set_weights.restype = ctypes.c_int
+        L.orc_set_dominance.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_set_dominance.restype = ctypes.c_int
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
         L.orc_step.restype = ctypes.c_int
         L.orc_read_genotypes.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
@@ -129,6 +131,8 @@ class OraclePopulation:
                 w.init_genotypes, w.p0_q32)
         if w.has_ecology:
             p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack)
+        if getattr(w, "dominance", None) is not None:
+            p.set_dominance(w.dominance)
         if getattr(w, "map_morgans", None) is not None:
             p.set_linkage(w.map_morgans)
         if getattr(w, "mother_weights", None) is not None or getattr(w, "father_weights", None) is not None:
@@ -148,6 +152,13 @@ class OraclePopulation:
         assert m.shape == (self.n_loci,)
         if lib().orc_set_linkage(self._h, m.ctypes.data) != 0:
             raise ValueError("oracle rejected the linkage map")
+
+    def set_dominance(self, dominance):
+        """Dominance deviations (int16 Q8, one per locus) of heterozygous loci."""
+        d = np.ascontiguousarray(dominance, dtype=np.int16)
+        assert d.shape == (self.n_loci,)
+        if lib().orc_set_dominance(self._h, d.ctypes.data) != 0:
+            raise ValueError("oracle rejected the dominance deviations")
 
     def set_weights(self, mother_weights, father_weights):
         """Weighted parents: uint32 weights over the 4096 phenotype bins for

@@ -45,7 +45,11 @@
  *     for mothers and one for fathers, applied to each survivor's bin at
  *     birth; each parent is drawn by bounded rejection sampling: a uniform
  *     survivor r is proposed and accepted with probability w(bin_r) / w_max,
- *     at most 64 proposals, the last one taken if all are rejected.
+ *     at most 64 proposals, the last one taken if all are rejected;
+ *   - dominance (the non-additive genotype-phenotype maps of the Main text;
+ *     optional): a heterozygous locus l adds its dominance deviation d_l
+ *     (Q8 int16) to the genetic value, raw = sum_l e_l (a0 + a1) + sum_l d_l
+ *     [a0 != a1].
  *
  * Genotypes are kept UNPACKED here (one byte per allele copy) so that the
  * per-locus statement of the model is visible; packing is done only when
@@ -108,6 +112,7 @@ typedef struct {
     int weighted;
     uint32_t acc_mother[ORC_BINS], acc_father[ORC_BINS]; /* acceptance thresholds, Q32 */
     uint16_t *bin_par, *bin_chi;                       /* phenotype bin of each individual at birth */
+    int16_t *dominance;                                /* [L] dominance deviations, or NULL */
     /* ecology */
     int has_eco;
     double r, K, R, R_half;
@@ -123,6 +128,7 @@ typedef struct {
 
 static int32_t phenotype_unpacked(const int16_t *effects, uint32_t L, const uint8_t *hap0,
                                   const uint8_t *hap1);
+static int32_t genetic_value(const orc_pop *p, const uint8_t *hap0, const uint8_t *hap1);
 static uint32_t bin_of(const orc_pop *p, int32_t raw);
 
 /* ------------------------------------------------------------------------ */
@@ -206,6 +212,17 @@ static int32_t phenotype_unpacked(const int16_t *effects, uint32_t L, const uint
     return raw;
 }
 
+/* Genetic value of one individual: additive part plus, with dominance, the
+ * deviation of every heterozygous locus. */
+static int32_t genetic_value(const orc_pop *p, const uint8_t *hap0, const uint8_t *hap1)
+{
+    int32_t raw = phenotype_unpacked(p->effects, p->L, hap0, hap1);
+    if (p->dominance)
+        for (uint32_t l = 0; l < p->L; ++l)
+            if (hap0[l] != hap1[l]) raw += (int32_t)p->dominance[l];
+    return raw;
+}
+
 static uint32_t bin_of(const orc_pop *p, int32_t raw)
 {
     int64_t v = (int64_t)raw + (int64_t)p->bias;
@@ -236,6 +253,7 @@ void orc_destroy(orc_pop *p)
     free(p->effects); free(p->par); free(p->chi); free(p->surv); free(p->surv_next);
     free(p->bin_par);
     free(p->bin_chi);
+    free(p->dominance);
     free(p);
 }
 
@@ -287,7 +305,7 @@ orc_pop *orc_create(uint32_t n, uint32_t L, uint64_t seed, uint32_t replicate,
         }
         p->surv[i] = i; /* every founder is a potential parent */
         const uint8_t *h = p->par + (size_t)i * 2 * L;
-        p->bin_par[i] = (uint16_t)bin_of(p, phenotype_unpacked(p->effects, L, h, h + L));
+        p->bin_par[i] = (uint16_t)bin_of(p, genetic_value(p, h, h + L));
     }
     p->S = n;
     return p;
@@ -397,6 +415,20 @@ static void linked_gamete(const orc_pop *p, uint32_t j, uint32_t g, uint32_t pi,
         origin ^= flips[l];
         out[l] = origin ? h1[l] : h0[l];
     }
+}
+
+/* Dominance deviations d[L] (Q8); the current parents' bins are recomputed. */
+int orc_set_dominance(orc_pop *p, const int16_t *d)
+{
+    if (!p || !d) return ORC_ERR_INVALID;
+    if (!p->dominance) p->dominance = (int16_t *)malloc(sizeof(int16_t) * p->L);
+    if (!p->dominance) return ORC_ERR_OOM;
+    memcpy(p->dominance, d, sizeof(int16_t) * p->L);
+    for (uint32_t i = 0; i < p->n; ++i) {
+        const uint8_t *h = p->par + (size_t)i * 2 * p->L;
+        p->bin_par[i] = (uint16_t)bin_of(p, genetic_value(p, h, h + p->L));
+    }
+    return ORC_OK;
 }
 
 /* Weighted parents: acceptance threshold of bin b = floor(2^32 * w[b] / w_max)
@@ -534,7 +566,7 @@ static void one_generation(orc_pop *p, orc_stats *st)
         }
 
         /* (C) additive phenotype */
-        int32_t raw = phenotype_unpacked(p->effects, L, c0, c1);
+        int32_t raw = genetic_value(p, c0, c1);
 
         /* (D) survival against the selective environment */
         uint32_t b = bin_of(p, raw);

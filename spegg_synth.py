@@ -175,6 +175,9 @@ class Workload:
     # weighted parents (None: uniform): uint32 weights over the phenotype bins
     mother_weights: Optional[np.ndarray] = None
     father_weights: Optional[np.ndarray] = None
+    # dominance deviations (None: additive): int16 Q8 per locus, added at
+    # heterozygous loci; bias/shift then cover the widened phenotype range
+    dominance: Optional[np.ndarray] = None
 
     @property
     def words(self) -> int:
@@ -204,6 +207,27 @@ def with_linkage(w: "Workload", chromosomes: int = 4, morgans: float = 1.0) -> "
     import dataclasses
     return dataclasses.replace(w, map_morgans=linkage_map(w.n_loci, chromosomes, morgans),
                                name=w.name + f"+map{chromosomes}x{morgans:g}M")
+
+
+def with_dominance(w: "Workload", sd: float = 0.1, seed: int = 99) -> "Workload":
+    """The same workload with dominance deviations d_l = Q8(N(0, sd)) and the
+    bin map and viability table rebuilt over the widened phenotype range
+    (raw = sum e_l (a0 + a1) + sum d_l [a0 != a1])."""
+    import dataclasses
+    d = effects_q8(w.n_loci, sd, seed)
+    e = w.effects.astype(np.int64)
+    # per locus the genotype values are 0, e + d, 2e: bounds over them
+    vals = np.stack([np.zeros_like(e), e + d.astype(np.int64), 2 * e])
+    raw_min, raw_max = int(vals.min(axis=0).sum()), int(vals.max(axis=0).sum())
+    bias = -raw_min
+    shift = 0
+    while ((raw_max - raw_min) >> shift) >= N_BINS:
+        shift += 1
+    table = stabilizing_table(bias, shift, w.s if w.s else 0.5)
+    out = dataclasses.replace(w, dominance=d, bias=bias, shift=shift, surv_table=table, name=w.name + "+dominance")
+    if w.attack is not None:
+        out.attack = attack_table(bias, shift)
+    return out
 
 
 def fecundity_weights(bias: int, shift: int, slope: float = 1.0, theta: float = 0.0) -> np.ndarray:
