@@ -320,6 +320,7 @@ def main():
     ap.add_argument("--no-spatial", action="store_true", help="omit the spatial-community measurement")
     ap.add_argument("--no-linked", action="store_true", help="omit the linkage-map measurement")
     ap.add_argument("--no-weighted", action="store_true", help="omit the weighted-parents measurement")
+    ap.add_argument("--no-dominance", action="store_true", help="omit the dominance measurement")
     args = ap.parse_args()
     workload = S.consumer_resource()
     if args.impl == "reference":
@@ -418,6 +419,8 @@ def main():
         spegg, torch, S.with_linkage(S.consumer_resource(), 4, 1.0), "linkage map 4 chromosomes x 1 Morgan")
     weighted = None if args.no_weighted else variant_population(
         spegg, torch, S.with_weights(S.consumer_resource()), "parents weighted by trait (1 + tanh z; fathers 2z)")
+    dominance = None if args.no_dominance else variant_population(
+        spegg, torch, S.with_dominance(S.consumer_resource()), "dominance deviations N(0, 0.1) at every locus")
     if rank != 0:
         return
     line = {
@@ -446,6 +449,8 @@ def main():
         line["linked"] = linked
     if weighted is not None:
         line["weighted"] = weighted
+    if dominance is not None:
+        line["dominance"] = dominance
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload)
     print(json.dumps(line))

@@ -11,7 +11,9 @@
  *       two haplotypes by an independent fair bit (free recombination, S2
  *       "Genetics"), then each allele copy mutates (flips) with probability mu;
  *   (C) phenotype: raw = sum over loci of effect[l] * (copies of allele 1)
- *       (additive map, eq. S2-phenval; the trait is z = raw / 512);
+ *       (additive map, eq. S2-phenval; the trait is z = raw / 512), plus,
+ *       with dominance (the Main text's non-additive maps), dominance[l] at
+ *       every heterozygous locus;
  *   (D) survival: bin = clamp((raw + bin_bias) >> bin_shift, 0, 4095); the
  *       offspring survives with probability table[bin] / 2^32 (0xFFFFFFFF =
  *       certain), scaled by the resource factor f when an ecology is set;
@@ -142,6 +144,10 @@ typedef struct {
     const uint32_t *father_weights; /* NULL: uniform for that role.  Single populations */
                                     /* only, like map_morgans; a table whose weights   */
                                     /* are all 0 is SPG_ERR_INVALID.                    */
+    const int16_t *dominance;       /* [L] dominance deviations (Q8) of heterozygous    */
+                                    /* loci, copied; NULL: additive.  Every population, */
+                                    /* batch member and job; bin_bias / bin_shift must  */
+                                    /* cover the widened phenotype range.               */
 } spg_pop_desc;
 
 /* Consumer-resource ecology (Fig. 1F; S2 "Resource Consumption"): after the
@@ -433,7 +439,7 @@ void spg_space_destroy(spg_space *space);
  * the outputs are valid once it completes.  Returns SPG_OK or a negative
  * SPG_ERR_* code (spg_last_error() explains it). */
 #define SPG_NOALLOC_MAX_N 4194304u
-#define SPG_NOALLOC_SCRATCH_BYTES 568576u
+#define SPG_NOALLOC_SCRATCH_BYTES 569088u
 
 typedef struct {
     uint32_t n;                   /* N, 1 .. SPG_NOALLOC_MAX_N                  */

@@ -59,26 +59,31 @@ uint32_t mutation_cdf(double mu, uint32_t n_copies, uint32_t *cdf) {
     return entries;
 }
 
-// Effects in offset binary: e_l - e_min split into bit planes, plane b word w
-// holding bit b of the offsets of loci 32w .. 32w+31.
-void effect_planes(const int16_t *effects, uint32_t n_loci, PopParams &prm) {
+// Per-locus values in offset binary: v_l - v_min split into bit planes, plane
+// b word w holding bit b of the offsets of loci 32w .. 32w+31.
+static void offset_planes(const int16_t *v, uint32_t n_loci, uint32_t *planes, int32_t &v_min, uint32_t &nplanes) {
     const uint32_t W = n_loci / 32;
-    int32_t e_min = effects[0], e_max = effects[0];
+    int32_t lo = v[0], hi = v[0];
     for (uint32_t l = 1; l < n_loci; ++l) {
-        e_min = std::min<int32_t>(e_min, effects[l]);
-        e_max = std::max<int32_t>(e_max, effects[l]);
+        lo = std::min<int32_t>(lo, v[l]);
+        hi = std::max<int32_t>(hi, v[l]);
     }
-    const uint32_t span = (uint32_t)(e_max - e_min);
-    uint32_t nplanes = 0;
-    while (nplanes < 32 && (span >> nplanes) != 0u) ++nplanes;
-    std::memset(prm.planes, 0, sizeof prm.planes);
+    const uint32_t span = (uint32_t)(hi - lo);
+    uint32_t np = 0;
+    while (np < 32 && (span >> np) != 0u) ++np;
+    std::memset(planes, 0, sizeof(uint32_t) * kMaxPlanes * kMaxWords);
     for (uint32_t l = 0; l < n_loci; ++l) {
-        const uint32_t off = (uint32_t)((int32_t)effects[l] - e_min);
-        for (uint32_t b = 0; b < nplanes; ++b)
-            if ((off >> b) & 1u) prm.planes[b * W + l / 32] |= 1u << (l % 32);
+        const uint32_t off = (uint32_t)((int32_t)v[l] - lo);
+        for (uint32_t b = 0; b < np && b < (uint32_t)kMaxPlanes; ++b)
+            if ((off >> b) & 1u) planes[b * W + l / 32] |= 1u << (l % 32);
     }
-    prm.e_min = e_min;
-    prm.nplanes = nplanes;
+    v_min = lo;
+    nplanes = np;
+}
+
+// Effects in offset binary (the additive genetic value's bit planes).
+void effect_planes(const int16_t *effects, uint32_t n_loci, PopParams &prm) {
+    offset_planes(effects, n_loci, prm.planes, prm.e_min, prm.nplanes);
 }
 
 // Resource factor of the ecology, same arithmetic as the device finalizer.
@@ -129,6 +134,11 @@ int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
     std::memcpy(prm.table, d->surv_table, sizeof prm.table);
     effect_planes(d->effects, d->n_loci, prm);
     if (prm.nplanes > (uint32_t)kMaxPlanes) return fail(SPG_ERR_INVALID, "effects span more than 16 bits");
+    if (d->dominance) {
+        offset_planes(d->dominance, d->n_loci, prm.dplanes, prm.d_min, prm.ndplanes);
+        if (prm.ndplanes > (uint32_t)kMaxPlanes)
+            return fail(SPG_ERR_INVALID, "dominance deviations span more than 16 bits");
+    }
     prm.kmax = mutation_cdf(d->mu, 2 * d->n_loci, prm.cdf);
     prm.bias = d->bin_bias;
     prm.shift = d->bin_shift;

@@ -256,6 +256,24 @@ __device__ __forceinline__ int32_t phenotype(const uint32_t (&c)[2 * W], const u
     return raw;
 }
 
+// Dominance part of the genetic value: heterozygous loci x = h0 ^ h1 add
+// their deviations, d_min * popc(x) + sum_b 2^b * popc(dplane_b & x)
+// (zero when the population has no dominance: d_min = 0, no planes).
+template <int W>
+__device__ __forceinline__ int32_t dominance_part(const uint32_t (&c)[2 * W], const uint32_t *s_dplanes,
+                                                  uint32_t ndplanes, int32_t d_min, uint32_t het) {
+    int32_t raw = d_min * (int32_t)het;
+    for (uint32_t b = 0; b < ndplanes; ++b) {
+        uint32_t pl[W];
+        plane_words<W>(s_dplanes, b, pl);
+        int32_t cnt = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) cnt += __popc(pl[w] & (c[w] ^ c[W + w]));
+        raw += cnt << b;
+    }
+    return raw;
+}
+
 // ------------------------------------------------------ ecology (Fig. 1F)
 __device__ double resource_update(double R, double r, double K, unsigned long long C) {
     const double ratio = __ddiv_rn(R, K);
@@ -465,8 +483,8 @@ struct SegCtx {
     const unsigned long long *survw;   // weighted parents: survivor index | bin << 32
     const WeightParams *wt;            // weighted parents: acceptance thresholds
     uint16_t *obin;                    // weighted parents: bins of the offspring formed
-    uint32_t n, S, f, g, rep, k0, k1, kmax, nplanes, shift;
-    int32_t e_min, bias;
+    uint32_t n, S, f, g, rep, k0, k1, kmax, nplanes, shift, ndplanes;
+    int32_t e_min, bias, d_min;
     bool has_eco;
 };
 
@@ -567,7 +585,8 @@ struct ThreadStats {
 template <int W, int ITEMS, bool LINKED, bool WEIGHTED>
 __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t base, int tid, int lane, int warp,
                                                    const unsigned char *s_dyn, int stage, const uint32_t *s_planes,
-                                                   const uint32_t *s_cdf, ThreadStats &ts, const LinkSmem &lk) {
+                                                   const uint32_t *s_cdf, ThreadStats &ts, const LinkSmem &lk,
+                                                   const uint32_t *s_dplanes) {
     constexpr int NW = kBlock / 32;
     using St = Staging<W, ITEMS>;
     uint32_t alive_count = 0;  // the warp's survivors (same in every lane)
@@ -618,7 +637,8 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
 
             // (C) phenotype, (D) survival
             uint32_t allele, hz;
-            const int32_t raw = phenotype<W>(ch, s_planes, c.nplanes, c.e_min, allele, hz);
+            const int32_t raw = phenotype<W>(ch, s_planes, c.nplanes, c.e_min, allele, hz) +
+                                dominance_part<W>(ch, s_dplanes, c.ndplanes, c.d_min, hz);
             const long long v = (long long)raw + (long long)c.bias;
             const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> c.shift, (long long)(kBins - 1));
             if constexpr (WEIGHTED) c.obin[j] = (uint16_t)bin;
@@ -653,6 +673,7 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
     static_assert(kBucket % TILE == 0, "tiles must not straddle compaction buckets");
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ __align__(16) uint32_t s_planes[kMaxPlanes * W];
+    __shared__ __align__(16) uint32_t s_dplanes[kMaxPlanes * W];
     __shared__ uint32_t s_cdf[kMaxKmax];
     __shared__ long long s_ll[2][NW];
     __shared__ unsigned long long s_ull[2][NW];
@@ -699,11 +720,14 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
             c.nplanes = c.P->nplanes;
             c.shift = c.P->shift;
             c.e_min = c.P->e_min;
+            c.d_min = c.P->d_min;
+            c.ndplanes = c.P->ndplanes;
             c.bias = c.P->bias;
             c.has_eco = c.P->has_eco != 0u;
 
             __syncthreads();  // the previous population's tables are no longer read
             for (uint32_t i = tid; i < c.nplanes * W; i += kBlock) s_planes[i] = c.P->planes[i];
+            for (uint32_t i = tid; i < c.ndplanes * W; i += kBlock) s_dplanes[i] = c.P->dplanes[i];
             if (tid < kMaxKmax) s_cdf[tid] = (uint32_t)tid < c.kmax ? c.P->cdf[tid] : 0u;
             if constexpr (LINKED) {
                 const LinkParams *lp = c.P->link;
@@ -762,7 +786,7 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
                 }
                 const uint32_t cnt =
                     offspring_tile<W, ITEMS, LINKED, WEIGHTED>(c, base, tid, lane, warp, s_dyn, stage, s_planes, s_cdf,
-                                                               ts, lk);
+                                                               ts, lk, s_dplanes);
                 bucket_alive += cnt;
                 warp_alive += cnt;
                 stage = stage + 1 == St::kStages ? 0 : stage + 1;
@@ -947,10 +971,13 @@ __global__ void k_survivor_bins(const PopParams *__restrict__ P, const uint32_t 
     const uint32_t idx = surv ? surv[r] : r;
     uint32_t rec[2 * W];
     load_record<W>(geno + (size_t)idx * (2 * W), rec);
-    uint32_t total = 0;
+    uint32_t total = 0, het = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) total += __popc(rec[w]) + __popc(rec[W + w]);
-    int32_t raw = P->e_min * (int32_t)total;
+    for (int w = 0; w < W; ++w) {
+        total += __popc(rec[w]) + __popc(rec[W + w]);
+        het += __popc(rec[w] ^ rec[W + w]);
+    }
+    int32_t raw = P->e_min * (int32_t)total + P->d_min * (int32_t)het;
     for (uint32_t b = 0; b < P->nplanes; ++b) {
         int32_t cnt = 0;
 #pragma unroll
@@ -958,6 +985,12 @@ __global__ void k_survivor_bins(const PopParams *__restrict__ P, const uint32_t 
             const uint32_t pl = P->planes[b * W + w];
             cnt += __popc(pl & rec[w]) + __popc(pl & rec[W + w]);
         }
+        raw += cnt << b;
+    }
+    for (uint32_t b = 0; b < P->ndplanes; ++b) {
+        int32_t cnt = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) cnt += __popc(P->dplanes[b * W + w] & (rec[w] ^ rec[W + w]));
         raw += cnt << b;
     }
     const long long v = (long long)raw + (long long)P->bias;

@@ -35,7 +35,7 @@ constexpr int kGroups = 4;  // W = 1, 2, 4, 8
 
 struct Job {
     spg_pop_desc desc{};
-    std::vector<int16_t> effects;
+    std::vector<int16_t> effects, dominance;
     std::vector<uint32_t> table, founders, attack;
     bool has_eco = false;
     spg_ecology eco{};
@@ -248,6 +248,10 @@ int spg_server_submit(spg_server *s, const spg_pop_desc *desc, const spg_ecology
     if (desc->init_genotypes)
         j->founders.assign(desc->init_genotypes, desc->init_genotypes + (size_t)desc->n * 2 * (desc->n_loci / 32));
     j->desc.effects = j->effects.data();
+    if (desc->dominance) {
+        j->dominance.assign(desc->dominance, desc->dominance + desc->n_loci);
+        j->desc.dominance = j->dominance.data();
+    }
     j->desc.surv_table = j->table.data();
     j->desc.init_genotypes = nullptr;
     j->desc.stats_capacity = n_gen;  // every generation's statistics stay readable

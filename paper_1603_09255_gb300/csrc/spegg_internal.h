@@ -54,6 +54,9 @@ struct alignas(16) PopParams {
     uint32_t table[kBins];                  // viability thresholds per bin
     uint32_t attack[kBins];                 // Q16 attack rate per bin (ecology)
     uint32_t planes[kMaxPlanes * kMaxWords];// plane b, word w at [b * W + w]
+    uint32_t dplanes[kMaxPlanes * kMaxWords];// dominance deviations, offset binary like planes
+    int32_t d_min;                          // dominance = d_min + sum_b 2^b * dplane_b
+    uint32_t ndplanes;                      // 0: additive genetic value
     uint32_t cdf[kMaxKmax];                 // Binomial(2L, mu) CDF, Q32
     int32_t e_min;                          // effects = e_min + sum_b 2^b * plane_b
     uint32_t nplanes;

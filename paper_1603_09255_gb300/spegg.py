@@ -45,6 +45,7 @@ class spg_pop_desc(ctypes.Structure):
         ("p0_q32", ctypes.c_uint32), ("surv_table", ctypes.c_void_p), ("bin_bias", ctypes.c_int32),
         ("bin_shift", ctypes.c_uint32), ("mu", ctypes.c_double), ("stats_capacity", ctypes.c_uint32),
         ("map_morgans", ctypes.c_void_p), ("mother_weights", ctypes.c_void_p), ("father_weights", ctypes.c_void_p),
+        ("dominance", ctypes.c_void_p),
     ]
 
 
@@ -262,7 +263,7 @@ class Population:
     def __init__(self, n: int, n_loci: int, seed: int, replicate: int, effects, surv_table, bin_bias: int,
                  bin_shift: int, mu: float, init_genotypes=None, p0_q32: int = 0x80000000,
                  stats_capacity: int = 0, stream=None, allocator: Optional[TorchAllocator] = None,
-                 map_morgans=None, mother_weights=None, father_weights=None):
+                 map_morgans=None, mother_weights=None, father_weights=None, dominance=None):
         L = lib()
         self.n, self.n_loci, self.words = int(n), int(n_loci), int(n_loci) // 32
         e = np.ascontiguousarray(effects, dtype=np.int16)
@@ -278,10 +279,15 @@ class Population:
         for x in (mw, fw):
             if x is not None and x.shape != (N_BINS,):
                 raise ValueError("weight tables must have 4096 entries")
+        dm = None if dominance is None else np.ascontiguousarray(dominance, dtype=np.int16)
+        if dm is not None and dm.shape != (self.n_loci,):
+            raise ValueError("dominance must have n_loci entries")
+        self._keep = (e, t, g, m, mw, fw, dm)
         d = spg_pop_desc(self.n, self.n_loci, int(seed), int(replicate), e.ctypes.data,
                          None if g is None else g.ctypes.data, int(p0_q32), t.ctypes.data, int(bin_bias),
                          int(bin_shift), float(mu), int(stats_capacity), None if m is None else m.ctypes.data,
-                         None if mw is None else mw.ctypes.data, None if fw is None else fw.ctypes.data)
+                         None if mw is None else mw.ctypes.data, None if fw is None else fw.ctypes.data,
+                         None if dm is None else dm.ctypes.data)
         self.allocator = allocator if allocator is not None else TorchAllocator()
         self._stream = _stream_handle(stream)
         h = ctypes.c_void_p()
@@ -294,6 +300,7 @@ class Population:
         kw.setdefault("map_morgans", getattr(w, "map_morgans", None))
         kw.setdefault("mother_weights", getattr(w, "mother_weights", None))
         kw.setdefault("father_weights", getattr(w, "father_weights", None))
+        kw.setdefault("dominance", getattr(w, "dominance", None))
         p = cls(w.n, w.n_loci, w.seed, w.replicate, w.effects, w.surv_table, w.bias, w.shift, w.mu,
                 w.init_genotypes, w.p0_q32, **kw)
         if w.has_ecology:
@@ -380,11 +387,13 @@ def _desc_for(w, keep: list, stats_capacity: int = 0) -> spg_pop_desc:
     m = None if mm is None else np.ascontiguousarray(mm, dtype=np.float64)
     mw = None if getattr(w, "mother_weights", None) is None else _u32(w.mother_weights)
     fw = None if getattr(w, "father_weights", None) is None else _u32(w.father_weights)
-    keep.extend([e, t, g, m, mw, fw])
+    dm = None if getattr(w, "dominance", None) is None else np.ascontiguousarray(w.dominance, dtype=np.int16)
+    keep.extend([e, t, g, m, mw, fw, dm])
     return spg_pop_desc(int(w.n), int(w.n_loci), int(w.seed), int(w.replicate), e.ctypes.data,
                         None if g is None else g.ctypes.data, int(w.p0_q32), t.ctypes.data, int(w.bias),
                         int(w.shift), float(w.mu), int(stats_capacity), None if m is None else m.ctypes.data,
-                        None if mw is None else mw.ctypes.data, None if fw is None else fw.ctypes.data)
+                        None if mw is None else mw.ctypes.data, None if fw is None else fw.ctypes.data,
+                        None if dm is None else dm.ctypes.data)
 
 
 class Batch:
