@@ -52,6 +52,8 @@ def lib():
         L.orc_set_linkage.restype = ctypes.c_int
         L.orc_set_weights.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_set_weights.restype = ctypes.c_int
+        L.orc_set_resource_model.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
+        L.orc_set_resource_model.restype = ctypes.c_int
         L.orc_set_dominance.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.orc_set_dominance.restype = ctypes.c_int
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
@@ -130,7 +132,8 @@ class OraclePopulation:
         p = cls(w.n, w.n_loci, w.seed, w.replicate, w.effects, w.surv_table, w.bias, w.shift, w.mu,
                 w.init_genotypes, w.p0_q32)
         if w.has_ecology:
-            p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack)
+            p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack,
+                          getattr(w, "eco_model", 0), getattr(w, "eco_r_sd", 0.0))
         if getattr(w, "dominance", None) is not None:
             p.set_dominance(w.dominance)
         if getattr(w, "map_morgans", None) is not None:
@@ -139,9 +142,13 @@ class OraclePopulation:
             p.set_weights(w.mother_weights, w.father_weights)
         return p
 
-    def set_ecology(self, r, K, R0, R_half, attack):
+    def set_ecology(self, r, K, R0, R_half, attack, model: int = 0, r_sd: float = 0.0):
+        """Resource: model 0 logistic, 1 Beverton-Holt with growth rate r +
+        r_sd z per generation."""
         a = _u32(attack)
         rc = lib().orc_set_ecology(self._h, float(r), float(K), float(R0), float(R_half), a.ctypes.data)
+        if rc == 0 and (model or r_sd):
+            rc = lib().orc_set_resource_model(self._h, int(model), float(r_sd))
         if rc != 0:
             raise ValueError("oracle rejected the ecology description")
 

@@ -49,7 +49,13 @@
  *   - dominance (the non-additive genotype-phenotype maps of the Main text;
  *     optional): a heterozygous locus l adds its dominance deviation d_l
  *     (Q8 int16) to the genetic value, raw = sum_l e_l (a0 + a1) + sum_l d_l
- *     [a0 != a1].
+ *     [a0 != a1];
+ *   - Beverton-Holt resource (S2 "Resource Consumption", optional instead of
+ *     the logistic): R' = r' R / (1 + R/K) - C 2^-16, clamped at 0, with the
+ *     growth rate r' = r + r_sd z drawn every generation; the paper draws it
+ *     from a normal distribution, read here as the Irwin-Hall(12) normal
+ *     z = (u_1 + ... + u_12) 2^-32 - 6 (mean 0, variance 1, tails cut at
+ *     6), whose integer sum keeps both implementations exact.
  *
  * Genotypes are kept UNPACKED here (one byte per allele copy) so that the
  * per-locus statement of the model is visible; packing is done only when
@@ -72,7 +78,7 @@
 
 #define ORC_MATE_ATTEMPTS 64
 
-enum { ORC_INIT = 1, ORC_MATE = 2, ORC_RECOMB = 3, ORC_MUTPOS = 4, ORC_LINK = 5, ORC_MATEW = 6 };
+enum { ORC_INIT = 1, ORC_MATE = 2, ORC_RECOMB = 3, ORC_MUTPOS = 4, ORC_LINK = 5, ORC_MATEW = 6, ORC_GROWTH = 7 };
 enum { ORC_OK = 0, ORC_EXTINCT = 1, ORC_ERR_INVALID = -1, ORC_ERR_OOM = -2 };
 
 /* One record per generation; same field order as the library's statistics
@@ -116,6 +122,8 @@ typedef struct {
     /* ecology */
     int has_eco;
     double r, K, R, R_half;
+    int eco_model;   /* 0 logistic, 1 Beverton-Holt */
+    double r_sd;     /* Beverton-Holt: standard deviation of the growth rate */
     uint32_t attack[ORC_BINS];
     uint32_t f;
     /* state */
@@ -328,6 +336,8 @@ int orc_set_ecology(orc_pop *p, double r, double K, double R0, double R_half, co
 {
     if (!p || !attack || !(K > 0.0) || !(R_half > 0.0) || !(R0 >= 0.0)) return ORC_ERR_INVALID;
     p->has_eco = 1;
+    p->eco_model = 0;
+    p->r_sd = 0.0;
     p->r = r; p->K = K; p->R = R0; p->R_half = R_half;
     memcpy(p->attack, attack, sizeof(uint32_t) * ORC_BINS);
     p->f = factor_q32(R0, R_half);
@@ -473,6 +483,49 @@ static uint32_t weighted_parent(const orc_pop *p, uint32_t j, uint32_t g, uint32
     return p->surv[r];
 }
 
+/* Beverton-Holt resource with a growth rate drawn every generation (model 1);
+ * r_sd = 0 keeps r' = r. */
+int orc_set_resource_model(orc_pop *p, int model, double r_sd)
+{
+    if (!p || !p->has_eco || (model != 0 && model != 1) || !(r_sd >= 0.0) || (model == 0 && r_sd != 0.0))
+        return ORC_ERR_INVALID;
+    p->eco_model = model;
+    p->r_sd = r_sd;
+    return ORC_OK;
+}
+
+/* Growth rate of generation g: r' = r + r_sd * z with the Irwin-Hall(12)
+ * normal z = (u_1 + ... + u_12) 2^-32 - 6, u_k = lane k%4 of
+ * Philox(0, g, rep, GROWTH<<24 | k/4). */
+static double growth_rate(const orc_pop *p, uint32_t g)
+{
+    if (p->r_sd == 0.0) return p->r;
+    uint64_t sum = 0;
+    for (uint32_t k = 0; k < 12; ++k) {
+        uint32_t d[4];
+        draw4(p, 0, g, ORC_GROWTH, k / 4, d);
+        sum += d[k % 4];
+    }
+    double u = (double)sum * (1.0 / 4294967296.0);
+    double z = u - 6.0;
+    double dev = p->r_sd * z;
+    return p->r + dev;
+}
+
+/* Beverton-Holt update with consumption C (Q16): R' = (r' R) / (1 + R/K) -
+ * C 2^-16, clamped at 0. */
+static double resource_update_bh(double R, double rg, double K, uint64_t C)
+{
+    double grown_num = rg * R;
+    double ratio = R / K;
+    double den = 1.0 + ratio;
+    double grown = grown_num / den;
+    double eaten = (double)C * (1.0 / 65536.0);
+    double next = grown - eaten;
+    if (!(next > 0.0)) next = 0.0;
+    return next;
+}
+
 /* Logistic update with consumption C (attack units in Q16):
  *   R' = (R + (r*R) * (1 - R/K)) - C * 2^-16, clamped at 0. */
 static double resource_update(double R, double r, double K, uint64_t C)
@@ -596,7 +649,8 @@ static void one_generation(orc_pop *p, orc_stats *st)
 
     /* (F) environment update from the survivors */
     if (p->has_eco) {
-        p->R = resource_update(p->R, p->r, p->K, st->consumption);
+        if (p->eco_model == 1) p->R = resource_update_bh(p->R, growth_rate(p, g), p->K, st->consumption);
+        else p->R = resource_update(p->R, p->r, p->K, st->consumption);
         p->f = factor_q32(p->R, p->R_half);
         st->R = p->R;
     } else {

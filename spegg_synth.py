@@ -168,6 +168,8 @@ class Workload:
     eco_R0: Optional[float] = None
     eco_R_half: Optional[float] = None
     attack: Optional[np.ndarray] = None
+    eco_model: int = 0      # 0 logistic resource, 1 Beverton-Holt
+    eco_r_sd: float = 0.0   # Beverton-Holt: standard deviation of the growth rate
     s: float = 0.0
     # linkage map (None: free recombination): distance in Morgans between loci
     # l-1 and l, negative where locus l starts a new chromosome
@@ -236,6 +238,14 @@ def fecundity_weights(bias: int, shift: int, slope: float = 1.0, theta: float = 
     z = bin_centre_trait(bias, shift)
     w = np.floor(65536.0 * (1.0 + np.tanh(slope * (z - theta)))) + 1.0
     return w.astype(np.uint32)
+
+
+def with_beverton_holt(w: "Workload", r: float = 2.0, r_sd: float = 0.2) -> "Workload":
+    """The same consumer-resource workload with a Beverton-Holt resource whose
+    growth rate is r + r_sd z each generation (z: Irwin-Hall(12) normal)."""
+    import dataclasses
+    assert w.has_ecology
+    return dataclasses.replace(w, eco_model=1, eco_r=r, eco_r_sd=r_sd, name=w.name + f"+BH{r:g}sd{r_sd:g}")
 
 
 def with_weights(w: "Workload", slope: float = 1.0) -> "Workload":
