@@ -153,12 +153,20 @@ typedef struct {
 /* Consumer-resource ecology (Fig. 1F; S2 "Resource Consumption"): after the
  * survivors of generation g are known,
  *   C  = sum over survivors of attack[bin]            (Q16 units)
- *   R' = (R + (r*R) * (1 - R/K)) - C * 2^-16, clamped at 0
+ *   R' = (R + (r*R) * (1 - R/K)) - C * 2^-16, clamped at 0          (model 0)
+ *   R' = (r'*R) / (1 + R/K) - C * 2^-16, clamped at 0, Beverton-Holt (model 1)
  *   f  = floor(2^32 * R' / (R' + R_half)), capped at 0xFFFFFFFE
- * and generation g+1 survives with threshold floor(table[bin] * f / 2^32). */
+ * and generation g+1 survives with threshold floor(table[bin] * f / 2^32).
+ * Beverton-Holt growth rate of generation g: r' = r + r_sd * z with the
+ * Irwin-Hall(12) normal z = (u_1 + ... + u_12) * 2^-32 - 6, u_k = lane k%4 of
+ * Philox counter (0, g, replicate, 7<<24 | k/4) (the paper's normally drawn
+ * r'; the integer sum keeps every implementation exact); r_sd = 0: r' = r.
+ * Every operation is one IEEE-double operation in the order written. */
 typedef struct {
     double r, K, R0, R_half;   /* growth rate, carrying capacity, initial R, half-saturation */
     const uint32_t *attack;    /* [4096] attack rate per phenotype bin, Q16 */
+    uint32_t model;            /* 0 logistic, 1 Beverton-Holt                */
+    double r_sd;               /* Beverton-Holt: sd of r' per generation (>= 0; 0 for model 0) */
 } spg_ecology;
 
 /* Exact per-generation statistics (integer sums over the N offspring unless

@@ -467,6 +467,9 @@ int check_ecology(const spg_ecology *eco) {
     if (!(eco->K > 0.0) || !(eco->R_half > 0.0) || !(eco->R0 >= 0.0) || !std::isfinite(eco->r) ||
         !std::isfinite(eco->K) || !std::isfinite(eco->R0))
         return fail(SPG_ERR_INVALID, "ecology needs K > 0, R_half > 0, R0 >= 0, finite r");
+    if (eco->model > 1u) return fail(SPG_ERR_INVALID, "ecology model must be 0 (logistic) or 1 (Beverton-Holt)");
+    if (!(eco->r_sd >= 0.0) || !std::isfinite(eco->r_sd) || (eco->model == 0u && eco->r_sd != 0.0))
+        return fail(SPG_ERR_INVALID, "r_sd must be finite, >= 0, and 0 for the logistic resource");
     return SPG_OK;
 }
 
@@ -480,6 +483,8 @@ int view_set_ecology(const PopView &v, PopParams &prm, const spg_ecology *eco) {
     if (rc != SPG_OK) return rc;
     std::memcpy(prm.attack, eco->attack, sizeof prm.attack);
     prm.has_eco = 1;
+    prm.eco_model = eco->model;
+    prm.r_sd = eco->r_sd;
     prm.r = eco->r;
     prm.K = eco->K;
     prm.R_half = eco->R_half;

@@ -287,6 +287,33 @@ __device__ double resource_update(double R, double r, double K, unsigned long lo
     return next;
 }
 
+// Beverton-Holt variant: R' = (r' R) / (1 + R/K) - C 2^-16, clamped at 0.
+__device__ double resource_update_bh(double R, double rg, double K, unsigned long long C) {
+    const double grown_num = __dmul_rn(rg, R);
+    const double ratio = __ddiv_rn(R, K);
+    const double den = __dadd_rn(1.0, ratio);
+    const double grown = __ddiv_rn(grown_num, den);
+    const double eaten = __dmul_rn(__ull2double_rn(C), 1.0 / 65536.0);
+    double next = __dsub_rn(grown, eaten);
+    if (!(next > 0.0)) next = 0.0;
+    return next;
+}
+
+// Growth rate of generation g: r + r_sd * z, z the Irwin-Hall(12) normal
+// (sum of twelve Philox lanes of counter (0, g, rep, 7<<24 | k/4)) * 2^-32 - 6.
+__device__ double growth_rate(const PopParams *P, uint32_t g) {
+    if (P->r_sd == 0.0) return P->r;
+    unsigned long long sum = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < 3; ++k) {
+        const uint4 d = philox(make_uint4(0u, g, P->rep, (kGrowth << 24) | k), P->key0, P->key1);
+        sum += (unsigned long long)d.x + d.y + d.z + d.w;
+    }
+    const double u = __dmul_rn(__ull2double_rn(sum), 1.0 / 4294967296.0);
+    const double z = __dsub_rn(u, 6.0);
+    return __dadd_rn(P->r, __dmul_rn(P->r_sd, z));
+}
+
 __device__ uint32_t factor_q32(double R, double R_half) {
     const double den = __dadd_rn(R, R_half);
     const double q = __ddiv_rn(R, den);
@@ -371,7 +398,8 @@ __device__ void finalize_warp(const Segment &sg, const PopParams *P, uint32_t g,
         uint32_t f_next = f_used;
         double R = 0.0;
         if (P->has_eco) {
-            R = resource_update(R_prev, P->r, P->K, cons);
+            R = P->eco_model == 1u ? resource_update_bh(R_prev, growth_rate(P, g), P->K, cons)
+                                   : resource_update(R_prev, P->r, P->K, cons);
             f_next = factor_q32(R, P->R_half);
         }
         const int32_t status = (S_new == 0ull) ? SPG_EXTINCT : SPG_OK;

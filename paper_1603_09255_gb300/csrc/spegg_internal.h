@@ -28,7 +28,7 @@ constexpr double kMaxMapMorgans = 16.0;  // total length of a linkage map
 constexpr int kLinkGuide = 1024;         // guide-table entries of the crossover interval search
 
 // Philox counter word 3 = purpose << 24 | sub
-enum Purpose : uint32_t { kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4, kLink = 5, kMateW = 6 };
+enum Purpose : uint32_t { kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4, kLink = 5, kMateW = 6, kGrowth = 7 };
 constexpr uint32_t kMateAttempts = 64;   // proposals per weighted parent
 
 // Acceptance thresholds of weighted parents (device global memory): acc[0]
@@ -69,6 +69,9 @@ struct alignas(16) PopParams {
     uint32_t key0, key1, rep;
     uint32_t has_eco;
     double r, K, R_half;
+    double r_sd;                 // Beverton-Holt: sd of the growth rate
+    uint32_t eco_model;          // 0 logistic, 1 Beverton-Holt
+    uint32_t pad_eco;
     uint32_t ntiles;
     uint32_t stats_cap;
     const LinkParams *link;      // linkage map tables, or null (free recombination)

@@ -51,7 +51,8 @@ class spg_pop_desc(ctypes.Structure):
 
 class spg_ecology(ctypes.Structure):
     _fields_ = [("r", ctypes.c_double), ("K", ctypes.c_double), ("R0", ctypes.c_double),
-                ("R_half", ctypes.c_double), ("attack", ctypes.c_void_p)]
+                ("R_half", ctypes.c_double), ("attack", ctypes.c_void_p), ("model", ctypes.c_uint32),
+                ("r_sd", ctypes.c_double)]
 
 
 class spg_noalloc_generation(ctypes.Structure):
@@ -304,16 +305,18 @@ class Population:
         p = cls(w.n, w.n_loci, w.seed, w.replicate, w.effects, w.surv_table, w.bias, w.shift, w.mu,
                 w.init_genotypes, w.p0_q32, **kw)
         if w.has_ecology:
-            p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack)
+            p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack, getattr(w, "eco_model", 0),
+                          getattr(w, "eco_r_sd", 0.0))
         return p
 
     @property
     def handle(self):
         return self._h
 
-    def set_ecology(self, r, K, R0, R_half, attack):
+    def set_ecology(self, r, K, R0, R_half, attack, model: int = 0, r_sd: float = 0.0):
+        """Resource: model 0 logistic, 1 Beverton-Holt with growth rate r + r_sd z."""
         a = _u32(attack)
-        eco = spg_ecology(float(r), float(K), float(R0), float(R_half), a.ctypes.data)
+        eco = spg_ecology(float(r), float(K), float(R0), float(R_half), a.ctypes.data, int(model), float(r_sd))
         check(lib().spg_set_ecology(self._h, ctypes.byref(eco)), "spg_set_ecology")
 
     def step(self, n_gen: int) -> None:
@@ -414,7 +417,7 @@ class Batch:
             if w.has_ecology:
                 a = _u32(w.attack)
                 eco = spg_ecology(float(w.eco_r), float(w.eco_K), float(w.eco_R0), float(w.eco_R_half),
-                                  a.ctypes.data)
+                                  a.ctypes.data, int(getattr(w, "eco_model", 0)), float(getattr(w, "eco_r_sd", 0.0)))
                 check(L.spg_batch_set_ecology(self._h, i, ctypes.byref(eco)), "spg_batch_set_ecology")
 
     def __len__(self):
@@ -482,7 +485,8 @@ def _eco_for(w, keep: list):
         return None
     a = _u32(w.attack)
     keep.append(a)
-    return spg_ecology(float(w.eco_r), float(w.eco_K), float(w.eco_R0), float(w.eco_R_half), a.ctypes.data)
+    return spg_ecology(float(w.eco_r), float(w.eco_K), float(w.eco_R0), float(w.eco_R_half), a.ctypes.data,
+                       int(getattr(w, "eco_model", 0)), float(getattr(w, "eco_r_sd", 0.0)))
 
 
 class Server:
