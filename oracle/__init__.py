@@ -54,6 +54,8 @@ def lib():
         L.orc_set_weights.restype = ctypes.c_int
         L.orc_set_resource_model.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_set_resource_model.restype = ctypes.c_int
+        L.orc_set_continuous.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
+        L.orc_set_continuous.restype = ctypes.c_int
         L.orc_set_dominance.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.orc_set_dominance.restype = ctypes.c_int
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
@@ -115,6 +117,7 @@ class OraclePopulation:
                  p0_q32: int = 0x80000000):
         self.n, self.n_loci = int(n), int(n_loci)
         self.words = self.n_loci // 32
+        self.continuous = False
         e = np.ascontiguousarray(effects, dtype=np.int16)
         t = _u32(surv_table)
         assert t.shape == (4096,) and e.shape == (self.n_loci,)
@@ -134,6 +137,8 @@ class OraclePopulation:
         if w.has_ecology:
             p.set_ecology(w.eco_r, w.eco_K, w.eco_R0, w.eco_R_half, w.attack,
                           getattr(w, "eco_model", 0), getattr(w, "eco_r_sd", 0.0))
+        if getattr(w, "allele_model", 0) == 1:
+            p.set_continuous(w.mut_sd, w.env_sd, getattr(w, "init_values", None))
         if getattr(w, "dominance", None) is not None:
             p.set_dominance(w.dominance)
         if getattr(w, "map_morgans", None) is not None:
@@ -159,6 +164,22 @@ class OraclePopulation:
         assert m.shape == (self.n_loci,)
         if lib().orc_set_linkage(self._h, m.ctypes.data) != 0:
             raise ValueError("oracle rejected the linkage map")
+
+    def set_continuous(self, mut_sd: float, env_sd: float, init_values=None):
+        """Continuous allelic values (int16 Q8 per allele copy): Gaussian
+        (Irwin-Hall) mutation steps of sd mut_sd and environmental phenotype
+        deviations of sd env_sd, both in trait units."""
+        v = None if init_values is None else np.ascontiguousarray(init_values, dtype=np.int16)
+        assert v is None or v.size == self.n * 2 * self.n_loci
+        rc = lib().orc_set_continuous(self._h, float(mut_sd), float(env_sd), None if v is None else v.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle rejected the continuous-allele description")
+        self.continuous = True
+
+    def values(self) -> np.ndarray:
+        """Allelic values [n, 2, L] (int16 Q8) of a continuous population."""
+        assert self.continuous
+        return self.genotypes().view(np.int16).reshape(self.n, 2, self.n_loci)
 
     def set_dominance(self, dominance):
         """Dominance deviations (int16 Q8, one per locus) of heterozygous loci."""
@@ -187,7 +208,7 @@ class OraclePopulation:
         return out[:done]
 
     def genotypes(self) -> np.ndarray:
-        out = np.zeros((self.n, 2 * self.words), np.uint32)
+        out = np.zeros((self.n, self.n_loci if self.continuous else 2 * self.words), np.uint32)
         lib().orc_read_genotypes(self._h, out.ctypes.data)
         return out
 

@@ -55,7 +55,15 @@
  *     growth rate r' = r + r_sd z drawn every generation; the paper draws it
  *     from a normal distribution, read here as the Irwin-Hall(12) normal
  *     z = (u_1 + ... + u_12) 2^-32 - 6 (mean 0, variance 1, tails cut at
- *     6), whose integer sum keeps both implementations exact.
+ *     6), whose integer sum keeps both implementations exact;
+ *   - continuous allelic values (S2 "Genetics": allelic values vary
+ *     continuously, a mutation redraws the value from a normal centred on the
+ *     old one, the phenotype is normal around the genetic value; optional):
+ *     every allele copy holds an int16 value in Q8 (the biallelic model's
+ *     effect scale), raw = sum_l (v0_l + v1_l) plus an environmental
+ *     deviation; a mutated copy adds floor(z * s) and an offspring's phenotype
+ *     adds floor(z * s_env), z the Irwin-Hall(12) normal in exact integer
+ *     arithmetic (see irwin_hall_step), values clamped to the int16 range.
  *
  * Genotypes are kept UNPACKED here (one byte per allele copy) so that the
  * per-locus statement of the model is visible; packing is done only when
@@ -78,7 +86,8 @@
 
 #define ORC_MATE_ATTEMPTS 64
 
-enum { ORC_INIT = 1, ORC_MATE = 2, ORC_RECOMB = 3, ORC_MUTPOS = 4, ORC_LINK = 5, ORC_MATEW = 6, ORC_GROWTH = 7 };
+enum { ORC_INIT = 1, ORC_MATE = 2, ORC_RECOMB = 3, ORC_MUTPOS = 4, ORC_LINK = 5, ORC_MATEW = 6, ORC_GROWTH = 7,
+       ORC_MUTSIZE = 8, ORC_ENV = 9 };
 enum { ORC_OK = 0, ORC_EXTINCT = 1, ORC_ERR_INVALID = -1, ORC_ERR_OOM = -2 };
 
 /* One record per generation; same field order as the library's statistics
@@ -119,6 +128,10 @@ typedef struct {
     uint32_t acc_mother[ORC_BINS], acc_father[ORC_BINS]; /* acceptance thresholds, Q32 */
     uint16_t *bin_par, *bin_chi;                       /* phenotype bin of each individual at birth */
     int16_t *dominance;                                /* [L] dominance deviations, or NULL */
+    /* continuous allelic values (continuous == 0: biallelic) */
+    int continuous;
+    int16_t *vpar, *vchi;  /* [n][2][L] allelic values, Q8 */
+    int64_t s_mut, s_env;  /* Irwin-Hall scales, Q16 (raw units per standard deviation) */
     /* ecology */
     int has_eco;
     double r, K, R, R_half;
@@ -262,6 +275,8 @@ void orc_destroy(orc_pop *p)
     free(p->bin_par);
     free(p->bin_chi);
     free(p->dominance);
+    free(p->vpar);
+    free(p->vchi);
     free(p);
 }
 
@@ -441,6 +456,97 @@ int orc_set_dominance(orc_pop *p, const int16_t *d)
     return ORC_OK;
 }
 
+/* Normal step in raw units from twelve Philox lanes (Irwin-Hall(12)):
+ * sum = u_1 + ... + u_12 (lane k%4 of sub sub0 + k/4), t = sum - 6 * 2^32,
+ * step = floor(floor(t / 2^8) * s / 2^40) for a Q16 scale s, i.e. about
+ * z * s / 2^16 with z = t / 2^32 (arithmetic shifts are floors). */
+static int32_t irwin_hall_step(const orc_pop *p, uint32_t j, uint32_t g, uint32_t purpose, uint32_t sub0, int64_t s)
+{
+    uint64_t sum = 0;
+    for (uint32_t k = 0; k < 12; ++k) {
+        uint32_t d[4];
+        draw4(p, j, g, purpose, sub0 + k / 4, d);
+        sum += d[k % 4];
+    }
+    int64_t t = (int64_t)sum - (int64_t)6 * 4294967296LL;
+    return (int32_t)(((t >> 8) * s) >> 40);
+}
+
+static int16_t clamp16(int32_t v)
+{
+    return (int16_t)(v < -32768 ? -32768 : v > 32767 ? 32767 : v);
+}
+
+/* Continuous allelic values: Q16 scales from standard deviations in trait
+ * units (mutation: per allele copy, 256 raw units per trait unit; phenotype:
+ * 512 raw units per trait unit), s = floor(sd * units * 2^16 + 1/2); the
+ * current generation's values are init_values ([n][2][L]) or the biallelic
+ * founders mapped to effect[l] * allele. */
+int orc_set_continuous(orc_pop *p, double mut_sd, double env_sd, const int16_t *init_values)
+{
+    if (!p || !(mut_sd >= 0.0 && mut_sd < 64.0) || !(env_sd >= 0.0 && env_sd < 64.0) || p->linked || p->weighted ||
+        p->dominance || p->gen != 0)
+        return ORC_ERR_INVALID;
+    const size_t cells = (size_t)p->n * 2 * p->L;
+    p->vpar = (int16_t *)malloc(sizeof(int16_t) * cells);
+    p->vchi = (int16_t *)malloc(sizeof(int16_t) * cells);
+    if (!p->vpar || !p->vchi) return ORC_ERR_OOM;
+    if (init_values) {
+        memcpy(p->vpar, init_values, sizeof(int16_t) * cells);
+    } else {
+        for (size_t c = 0; c < cells; ++c) p->vpar[c] = (int16_t)(p->par[c] ? p->effects[c % p->L] : 0);
+    }
+    p->s_mut = (int64_t)floor(mut_sd * 256.0 * 65536.0 + 0.5);
+    p->s_env = (int64_t)floor(env_sd * 512.0 * 65536.0 + 0.5);
+    p->continuous = 1;
+    return ORC_OK;
+}
+
+/* One offspring j of generation g under continuous allelic values: gametes
+ * by the free-recombination bits of the biallelic model, mutations at the
+ * same K distinct positions, each adding an Irwin-Hall step (mutation t uses
+ * subs 3t..3t+2 of purpose MUTSIZE), then the phenotype with its
+ * environmental step (subs 0..2 of purpose ENV).  Returns raw. */
+static int32_t continuous_offspring(orc_pop *p, uint32_t j, uint32_t g, uint32_t mother, uint32_t father,
+                                    uint32_t u_mut, int16_t *c0, int16_t *c1)
+{
+    const uint32_t L = p->L, W = L / 32;
+    const int16_t *m0 = p->vpar + ((size_t)mother * 2 + 0) * L, *m1 = m0 + L;
+    const int16_t *f0 = p->vpar + ((size_t)father * 2 + 0) * L, *f1 = f0 + L;
+    for (uint32_t w = 0; w < W; ++w) {
+        uint32_t qm = 2 * w + 0, qf = 2 * w + 1, dm[4], df[4];
+        draw4(p, j, g, ORC_RECOMB, qm / 4, dm);
+        draw4(p, j, g, ORC_RECOMB, qf / 4, df);
+        for (uint32_t bit = 0; bit < 32; ++bit) {
+            uint32_t l = 32 * w + bit;
+            c0[l] = ((dm[qm % 4] >> bit) & 1u) ? m1[l] : m0[l];
+            c1[l] = ((df[qf % 4] >> bit) & 1u) ? f1[l] : f0[l];
+        }
+    }
+    uint32_t k = 0;
+    for (uint32_t i = 0; i < p->kmax; ++i)
+        if (u_mut >= p->cdf[i]) k++;
+    uint32_t chosen[ORC_MAX_KMAX];
+    uint32_t n_chosen = 0;
+    for (uint32_t a = 0; a < ORC_MUT_DRAWS && n_chosen < k; ++a) {
+        uint32_t dp[4];
+        draw4(p, j, g, ORC_MUTPOS, a / 4, dp);
+        uint32_t pos = scaled_index(dp[a % 4], 2 * L);
+        int dup = 0;
+        for (uint32_t t = 0; t < n_chosen; ++t)
+            if (chosen[t] == pos) dup = 1;
+        if (!dup) chosen[n_chosen++] = pos;
+    }
+    for (uint32_t t = 0; t < n_chosen; ++t) {
+        int16_t *v = chosen[t] < L ? &c0[chosen[t]] : &c1[chosen[t] - L];
+        *v = clamp16((int32_t)*v + irwin_hall_step(p, j, g, ORC_MUTSIZE, 3 * t, p->s_mut));
+    }
+    int32_t raw = 0;
+    for (uint32_t l = 0; l < L; ++l) raw += (int32_t)c0[l] + (int32_t)c1[l];
+    if (p->s_env) raw += irwin_hall_step(p, j, g, ORC_ENV, 0, p->s_env);
+    return raw;
+}
+
 /* Weighted parents: acceptance threshold of bin b = floor(2^32 * w[b] / w_max)
  * in integer arithmetic, 0xFFFFFFFF where w[b] == w_max (always accepted);
  * a NULL table means uniform (every threshold 0xFFFFFFFF). */
@@ -579,6 +685,28 @@ static void one_generation(orc_pop *p, orc_stats *st)
         const uint8_t *m1 = p->par + ((size_t)mother * 2 + 1) * L;
         const uint8_t *f0 = p->par + ((size_t)father * 2 + 0) * L;
         const uint8_t *f1 = p->par + ((size_t)father * 2 + 1) * L;
+        if (p->continuous) {
+            int16_t *v0 = p->vchi + ((size_t)j * 2 + 0) * L, *v1 = v0 + L;
+            int32_t raw = continuous_offspring(p, j, g, mother, father, u_mut, v0, v1);
+            uint32_t b = bin_of(p, raw);
+            uint32_t thr = p->table[b];
+            if (p->f != ORC_CERTAIN) thr = (uint32_t)(((uint64_t)thr * (uint64_t)p->f) >> 32);
+            int alive = (thr == ORC_CERTAIN) || (u_surv < thr);
+            if (alive) {
+                p->surv_next[survivors++] = j;
+                st->sum_raw_surv += raw;
+                if (p->has_eco) st->consumption += p->attack[b];
+            }
+            st->sum_raw += raw;
+            st->sum_raw2 += (uint64_t)((int64_t)raw * (int64_t)raw);
+            if (raw < st->min_raw) st->min_raw = raw;
+            if (raw > st->max_raw) st->max_raw = raw;
+            for (uint32_t l = 0; l < L; ++l) {
+                st->het += (uint64_t)(v0[l] != v1[l]);
+                st->allele += (uint64_t)((int64_t)v0[l] * v0[l] + (int64_t)v1[l] * v1[l]);
+            }
+            continue;
+        }
         if (p->linked) {
             linked_gamete(p, j, g, 0, m0, m1, c0); /* maternal gamete -> haplotype 0 */
             linked_gamete(p, j, g, 1, f0, f1, c1); /* paternal gamete -> haplotype 1 */
@@ -662,6 +790,7 @@ static void one_generation(orc_pop *p, orc_stats *st)
     uint8_t *t8 = p->par; p->par = p->chi; p->chi = t8;
     uint32_t *t32 = p->surv; p->surv = p->surv_next; p->surv_next = t32;
     uint16_t *t16 = p->bin_par; p->bin_par = p->bin_chi; p->bin_chi = t16;
+    int16_t *tv = p->vpar; p->vpar = p->vchi; p->vchi = tv;
     p->S = survivors;
     p->gen = g;
     if (survivors == 0) p->status = ORC_EXTINCT;
@@ -689,6 +818,10 @@ int orc_step(orc_pop *p, uint32_t n_gen, orc_stats *out)
 int orc_read_genotypes(const orc_pop *p, uint32_t *out)
 {
     if (!p || !out) return ORC_ERR_INVALID;
+    if (p->continuous) { /* records of 2L int16 values (L words) */
+        memcpy(out, p->vpar, sizeof(int16_t) * (size_t)p->n * 2 * p->L);
+        return ORC_OK;
+    }
     uint32_t W = p->L / 32;
     memset(out, 0, sizeof(uint32_t) * (size_t)p->n * 2 * W);
     for (uint32_t i = 0; i < p->n; ++i)

@@ -180,6 +180,13 @@ class Workload:
     # dominance deviations (None: additive): int16 Q8 per locus, added at
     # heterozygous loci; bias/shift then cover the widened phenotype range
     dominance: Optional[np.ndarray] = None
+    # continuous allelic values (allele_model 1): int16 Q8 per allele copy,
+    # Gaussian mutation steps (sd mut_sd) and environmental deviations (sd
+    # env_sd), trait units; founders = biallelic draws mapped to effect * allele
+    allele_model: int = 0
+    mut_sd: float = 0.0
+    env_sd: float = 0.0
+    init_values: Optional[np.ndarray] = None
 
     @property
     def words(self) -> int:
@@ -209,6 +216,26 @@ def with_linkage(w: "Workload", chromosomes: int = 4, morgans: float = 1.0) -> "
     import dataclasses
     return dataclasses.replace(w, map_morgans=linkage_map(w.n_loci, chromosomes, morgans),
                                name=w.name + f"+map{chromosomes}x{morgans:g}M")
+
+
+def continuous_trait(n: int = 10_000, n_loci: int = 64, n_gen: int = 100, mu: float = 1e-3,
+                     mut_sd: float = 0.05, env_sd: float = 0.2, s: float = 0.5, seed: int = 0,
+                     replicate: int = 0, effects_seed: int = 0, name: str = "continuous") -> "Workload":
+    """The paper's continuous genetic model (S2 "Genetics"): allelic values
+    start at effect * allele of biallelic founders (p0 = 1/2), mutate by
+    Gaussian steps of sd `mut_sd` and the phenotype carries an environmental
+    deviation of sd `env_sd` (trait units); Gaussian stabilising viability
+    exp(-s z^2) over a bin map wide enough for the drift of the values."""
+    import dataclasses
+    w = single_species(n=n, n_loci=n_loci, n_gen=n_gen, mu=mu, s=s, seed=seed, replicate=replicate,
+                       effects_seed=effects_seed, name=name)
+    span = 2 * int(np.abs(w.effects.astype(np.int64)).sum()) + 4096 * 4
+    shift = 0
+    while ((2 * span) >> shift) >= N_BINS:
+        shift += 1
+    bias = span
+    return dataclasses.replace(w, allele_model=1, mut_sd=mut_sd, env_sd=env_sd, bias=bias, shift=shift,
+                               surv_table=stabilizing_table(bias, shift, s))
 
 
 def with_dominance(w: "Workload", sd: float = 0.1, seed: int = 99) -> "Workload":
