@@ -227,7 +227,7 @@ def served_sweep(spegg, torch, count: int = 48, rate: float = 200.0):
             "peak_memory_gb": c["peak_memory_used"] / 1e9}
 
 
-def variant_population(spegg, torch, w, label: str, gens: int = 256):
+def variant_population(spegg, torch, w, label: str, gens: int = 256, bytes_per_offspring=None):
     """One variant of the consumer-resource population (N = 10^6, L = 128),
     `gens` generations after 64, L2 flushed before, CUDA events on its stream."""
     stream = torch.cuda.Stream()
@@ -246,12 +246,13 @@ def variant_population(spegg, torch, w, label: str, gens: int = 256):
     stream.synchronize()
     ms = a.elapsed_time(b)
     peak, source = load_peaks()
-    achieved = w.n * (12 + 24 * w.words) * gens / (ms / 1e3) / 1e9
-    out = {"workload": f"consumer-resource N={w.n} L={w.n_loci}, {label}, "
+    per = bytes_per_offspring if bytes_per_offspring is not None else 12 + 24 * w.words
+    achieved = w.n * per * gens / (ms / 1e3) / 1e9
+    out = {"workload": f"{w.name.split('+')[0]} N={w.n} L={w.n_loci}, {label}, "
                        f"{gens} generations after 64 (L2 flushed before)",
            "value": w.n * gens / (ms / 1e3), "unit": "individual-generations/s", "us_per_generation": ms * 1e3 / gens,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "note": f"(12 + 24W) B per offspring, of {source}"}}
+                        "note": f"{per} B per offspring (algorithmic), of {source}"}}
     pop.close()
     return out
 
@@ -321,6 +322,7 @@ def main():
     ap.add_argument("--no-linked", action="store_true", help="omit the linkage-map measurement")
     ap.add_argument("--no-weighted", action="store_true", help="omit the weighted-parents measurement")
     ap.add_argument("--no-dominance", action="store_true", help="omit the dominance measurement")
+    ap.add_argument("--no-continuous", action="store_true", help="omit the continuous-allele measurement")
     args = ap.parse_args()
     workload = S.consumer_resource()
     if args.impl == "reference":
@@ -421,6 +423,10 @@ def main():
         spegg, torch, S.with_weights(S.consumer_resource()), "parents weighted by trait (1 + tanh z; fathers 2z)")
     dominance = None if args.no_dominance else variant_population(
         spegg, torch, S.with_dominance(S.consumer_resource()), "dominance deviations N(0, 0.1) at every locus")
+    continuous = None if args.no_continuous else variant_population(
+        spegg, torch, S.continuous_trait(n=1_000_000, n_loci=128, mu=1e-3, mut_sd=0.05, env_sd=0.2),
+        "continuous allelic values (int16 Q8), mu 1e-3, mutation sd 0.05, environmental sd 0.2, no resource",
+        gens=64, bytes_per_offspring=12 + 12 * 128)
     if rank != 0:
         return
     line = {
@@ -451,6 +457,8 @@ def main():
         line["weighted"] = weighted
     if dominance is not None:
         line["dominance"] = dominance
+    if continuous is not None:
+        line["continuous"] = continuous
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload)
     print(json.dumps(line))

@@ -60,6 +60,21 @@
  * integer arithmetic, 0xFFFFFFFF where w[b] is the maximum (bounded
  * rejection sampling: each parent is drawn with probability proportional to
  * its weight, up to the 64-proposal bound).
+ * Continuous allelic values (allele_model 1; S2 "Genetics": values vary
+ * continuously, a mutation moves a value by a normal step, the phenotype is
+ * normal around the genetic value): a record holds 2L int16 values in Q8
+ * (haplotype 0 loci 0..L-1, then haplotype 1; L uint32 words, little-endian
+ * pairs), raw = sum of all 2L values plus an environmental step.  Gametes use
+ * the purpose-3 bits of the biallelic model, mutations its purpose-2/4 count
+ * and distinct positions; mutation t (in the order its position was drawn)
+ * adds the step of purpose 8 subs 3t..3t+2, the phenotype the step of purpose
+ * 9 subs 0..2, and a mutated value is clamped to [-32768, 32767].  A step
+ * with scale s: sum = the twelve lanes of the three subs, t = sum - 6 * 2^32,
+ * step = ((t >> 8) * s) >> 40 (arithmetic shifts), with s = floor(sd * 256 *
+ * 2^16 + 1/2) for mutations and floor(sd * 512 * 2^16 + 1/2) for the
+ * phenotype (sd in trait units; the Irwin-Hall(12) normal, exact in integer
+ * arithmetic).  Founders: init_values, or the biallelic founder draws mapped
+ * to value = effect[l] * allele.
  * Linkage map (the paper's variable linkage maps, read as Haldane's
  * no-interference model): map_morgans[l] (l >= 1) is the distance in Morgans
  * between loci l-1 and l, or negative where locus l starts a new chromosome;
@@ -148,6 +163,12 @@ typedef struct {
                                     /* loci, copied; NULL: additive.  Every population, */
                                     /* batch member and job; bin_bias / bin_shift must  */
                                     /* cover the widened phenotype range.               */
+    uint32_t allele_model;          /* 0 biallelic bits, 1 continuous int16 values      */
+    double mut_sd;                  /* continuous: sd of a mutation step (trait units)  */
+    double env_sd;                  /* continuous: sd of the environmental step         */
+    const int16_t *init_values;     /* continuous: [N * 2L] generation-0 values or NULL */
+                                    /* Continuous populations: single populations only, */
+                                    /* no linkage map, weights or dominance, 0 <= sd < 64.*/
 } spg_pop_desc;
 
 /* Consumer-resource ecology (Fig. 1F; S2 "Resource Consumption"): after the
@@ -447,7 +468,7 @@ void spg_space_destroy(spg_space *space);
  * the outputs are valid once it completes.  Returns SPG_OK or a negative
  * SPG_ERR_* code (spg_last_error() explains it). */
 #define SPG_NOALLOC_MAX_N 4194304u
-#define SPG_NOALLOC_SCRATCH_BYTES 569088u
+#define SPG_NOALLOC_SCRATCH_BYTES 569344u
 
 typedef struct {
     uint32_t n;                   /* N, 1 .. SPG_NOALLOC_MAX_N                  */

@@ -148,7 +148,7 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
     for (uint32_t i = 0; i < count; ++i) {
         const int rc = validate_desc(descs + i);
         if (rc != SPG_OK) return fail(rc, "member %u: %s", i, spg_last_error());
-        if (descs[i].map_morgans || descs[i].mother_weights || descs[i].father_weights)
+        if (descs[i].map_morgans || descs[i].mother_weights || descs[i].father_weights || descs[i].allele_model)
             return fail(SPG_ERR_INVALID,
                         "member %u: linkage maps and parent weights are supported for single populations", i);
     }

@@ -126,6 +126,14 @@ int validate_desc(const spg_pop_desc *d) {
     if (d->bin_shift > 31) return fail(SPG_ERR_INVALID, "bin_shift must be <= 31");
     if (!(d->mu >= 0.0 && d->mu < 1.0)) return fail(SPG_ERR_INVALID, "mu must be in [0, 1)");
     if (d->stats_capacity > (1u << 24)) return fail(SPG_ERR_INVALID, "stats_capacity must be <= 2^24");
+    if (d->allele_model > 1u) return fail(SPG_ERR_INVALID, "allele_model must be 0 (biallelic) or 1 (continuous)");
+    if (d->allele_model == 1u) {
+        if (d->map_morgans || d->mother_weights || d->father_weights || d->dominance || d->init_genotypes)
+            return fail(SPG_ERR_INVALID, "continuous allelic values take no linkage map, weights, dominance or "
+                                         "init_genotypes (use init_values)");
+        if (!(d->mut_sd >= 0.0 && d->mut_sd < 64.0) || !(d->env_sd >= 0.0 && d->env_sd < 64.0))
+            return fail(SPG_ERR_INVALID, "mut_sd and env_sd must be in [0, 64)");
+    }
     return SPG_OK;
 }
 
@@ -155,6 +163,9 @@ int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
     prm.link = nullptr;  // set once the population's memory exists
     prm.weighted = (d->mother_weights || d->father_weights) ? 1u : 0u;
     prm.weights = nullptr;
+    prm.continuous = d->allele_model == 1u ? 1u : 0u;
+    prm.s_mut = prm.continuous ? (long long)std::floor(d->mut_sd * 256.0 * 65536.0 + 0.5) : 0;
+    prm.s_env = prm.continuous ? (long long)std::floor(d->env_sd * 512.0 * 65536.0 + 0.5) : 0;
     return SPG_OK;
 }
 
@@ -448,6 +459,9 @@ int view_init(const PopView &v, const PopParams &prm, const uint32_t *init_genot
         e = cudaMemcpyAsync(geno0, init_genotypes, (size_t)v.n * 2 * v.words * 4, cudaMemcpyHostToDevice, v.stream);
         if (e != cudaSuccess) return cuda_fail(e, "upload founders");
         rc = launch_iota(surv0, v.n, v.stream);
+    } else if (prm.continuous) {
+        rc = launch_founders_cont(reinterpret_cast<const PopParams *>(v.base + v.L.params), prm.n_loci, geno0, surv0,
+                                  v.n, p0_q32, v.stream);
     } else {
         rc = launch_founders(v.words, geno0, surv0, v.n, prm.key0, prm.key1, prm.rep, p0_q32, v.stream);
     }

@@ -874,6 +874,273 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
     }
 }
 
+// ------------------------------------------------ continuous allelic values
+// A normal step in raw units from twelve Philox lanes (Irwin-Hall(12)): the
+// lanes of subs sub0..sub0+2 summed, t = sum - 6 * 2^32, step =
+// ((t >> 8) * s) >> 40 for a Q16 scale s (see spegg.h).
+__device__ __forceinline__ int32_t irwin_hall_step(uint32_t j, uint32_t g, uint32_t rep, uint32_t purpose,
+                                                   uint32_t sub0, long long s, uint32_t k0, uint32_t k1) {
+    unsigned long long sum = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < 3; ++q) {
+        const uint4 d = philox(make_uint4(j, g, rep, (purpose << 24) | (sub0 + q)), k0, k1);
+        sum += (unsigned long long)d.x + d.y + d.z + d.w;
+    }
+    const long long t = (long long)sum - 6LL * 4294967296LL;
+    return (int32_t)(((t >> 8) * s) >> 40);
+}
+
+// C consecutive int16 values (2C bytes, aligned to 2C) in one access.
+template <int C>
+__device__ __forceinline__ void load_vals(const int16_t *p, int32_t (&v)[C]) {
+    if constexpr (C == 1) {
+        v[0] = __ldg(p);
+    } else {
+        uint32_t w[C / 2];
+        if constexpr (C == 2) {
+            w[0] = __ldg(reinterpret_cast<const uint32_t *>(p));
+        } else if constexpr (C == 4) {
+            const uint2 x = __ldg(reinterpret_cast<const uint2 *>(p));
+            w[0] = x.x;
+            w[1] = x.y;
+        } else {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
+            w[0] = x.x;
+            w[1] = x.y;
+            w[2] = x.z;
+            w[3] = x.w;
+        }
+#pragma unroll
+        for (int k = 0; k < C / 2; ++k) {
+            v[2 * k] = (int32_t)(int16_t)(w[k] & 0xFFFFu);
+            v[2 * k + 1] = (int32_t)(int16_t)(w[k] >> 16);
+        }
+    }
+}
+template <int C>
+__device__ __forceinline__ void store_vals(int16_t *p, const int32_t (&v)[C]) {
+    if constexpr (C == 1) {
+        *p = (int16_t)v[0];
+    } else {
+        uint32_t w[C / 2];
+#pragma unroll
+        for (int k = 0; k < C / 2; ++k) w[k] = ((uint32_t)v[2 * k] & 0xFFFFu) | ((uint32_t)v[2 * k + 1] << 16);
+        if constexpr (C == 2) *reinterpret_cast<uint32_t *>(p) = w[0];
+        else if constexpr (C == 4) *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+        else *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Generation kernel of a continuous-allele population (S2 "Genetics"): each
+// warp forms 32 consecutive offspring one at a time, lane i owning loci
+// i*C .. i*C+C-1 of both haplotypes (L = 32 C), so parent and child records
+// (2L int16) move in coalesced accesses.  Parents, gamete bits, mutation
+// counts and positions follow the biallelic model's draws; mutated values
+// take Irwin-Hall steps; the phenotype is the warp sum of the values plus the
+// environmental step.  Survivors, statistics and the bitmap feed the same
+// compaction kernel as the biallelic model.
+template <int C>
+__global__ void __launch_bounds__(kBlock) k_offspring_cont(const __grid_constant__ GenArgs a) {
+    constexpr uint32_t L = 32u * C;
+    constexpr int NW = kBlock / 32;
+    __shared__ uint32_t s_cdf[kMaxKmax];
+    __shared__ uint32_t s_mpos[NW][kMaxKmax];
+    __shared__ long long s_ll[2][NW];
+    __shared__ unsigned long long s_ull[4][NW];
+    __shared__ uint32_t s_u32[2][NW];
+    __shared__ int s_mm[2][NW];
+    const Segment &sg = a.one;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const PopNow now = read_state(sg.state);
+    if (!now.active) return;
+    const PopParams *P = sg.prm;
+    const uint32_t n = sg.n, S = now.S, g = now.gen + 1u, f = now.f;
+    const uint32_t rep = P->rep, k0 = P->key0, k1 = P->key1, kmax = P->kmax, shift_bin = P->shift;
+    const int32_t bias = P->bias;
+    const long long s_mut = P->s_mut, s_env = P->s_env;
+    const bool has_eco = P->has_eco != 0u;
+    const uint32_t *par = sg.geno[now.gen & 1u];
+    uint32_t *chi = sg.geno[g & 1u];
+    const uint32_t *sin = sg.surv[now.gen & 1u];
+    uint32_t *bucket_now = sg.bucket_sum + (g & 1u) * sg.nbuckets;
+    uint32_t *bucket_next = sg.bucket_sum + ((g + 1u) & 1u) * sg.nbuckets;
+    if (tid < kMaxKmax) s_cdf[tid] = (uint32_t)tid < kmax ? P->cdf[tid] : 0u;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * (uint32_t)kBlock;
+    if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
+    const uint32_t wbase = base + (uint32_t)warp * 32u;
+    const uint32_t wv = ((uint32_t)lane * C) >> 5, sh = ((uint32_t)lane * C) & 31u;  // this lane's mask word and bit
+
+    long long sum_raw = 0, sum_raw_s = 0;
+    unsigned long long sum_raw2 = 0, cons = 0, lane_allele = 0;
+    uint32_t lane_het = 0, alive_bits = 0, nsurv = 0;
+    int mn = INT_MAX, mx = INT_MIN;
+    for (uint32_t i = 0; i < 32u; ++i) {
+        const uint32_t j = wbase + i;
+        if (j >= n) break;  // the same for every lane
+        // (A) parents
+        const uint4 r = philox(make_uint4(j, g, rep, kMate << 24), k0, k1);
+        const uint32_t mom = __ldcg(sin + __umulhi(r.x, S)), dad = __ldcg(sin + __umulhi(r.y, S));
+        // (B) gametes: mask word wv of the mother (stream 2wv) and father (2wv + 1)
+        const uint4 dm = philox(make_uint4(j, g, rep, (kRecomb << 24) | (wv >> 1)), k0, k1);
+        const uint32_t mm = (wv & 1u) ? dm.z : dm.x, mf = (wv & 1u) ? dm.w : dm.y;
+        const int16_t *pm = reinterpret_cast<const int16_t *>(par + (size_t)mom * L);
+        const int16_t *pf = reinterpret_cast<const int16_t *>(par + (size_t)dad * L);
+        int32_t m0[C], m1[C], f0[C], f1[C], c0[C], c1[C];
+        load_vals<C>(pm + lane * C, m0);
+        load_vals<C>(pm + L + lane * C, m1);
+        load_vals<C>(pf + lane * C, f0);
+        load_vals<C>(pf + L + lane * C, f1);
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            c0[k] = ((mm >> (sh + k)) & 1u) ? m1[k] : m0[k];
+            c1[k] = ((mf >> (sh + k)) & 1u) ? f1[k] : f0[k];
+        }
+        // the child's values, and this lane's part of the phenotype sum, its
+        // heterozygous loci and its sum of squares
+        int16_t *pc = reinterpret_cast<int16_t *>(chi + (size_t)j * L);
+        store_vals<C>(pc + lane * C, c0);
+        store_vals<C>(pc + L + lane * C, c1);
+        int32_t part = 0;
+        uint32_t het = 0;
+        unsigned long long sq = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            part += c0[k] + c1[k];
+            het += c0[k] != c1[k] ? 1u : 0u;
+            sq += (unsigned long long)((long long)c0[k] * c0[k] + (long long)c1[k] * c1[k]);
+        }
+        // (B) mutation: the biallelic count and distinct positions, each
+        // mutated value moved by an Irwin-Hall step; rare, so the owner lane
+        // updates the stored value in place and corrects its sums
+        const uint32_t u_mut = r.w;
+        if (kmax != 0u && u_mut >= s_cdf[0]) {
+            uint32_t K = 0;
+            for (uint32_t q = 0; q < kmax; ++q) K += u_mut >= s_cdf[q] ? 1u : 0u;
+            uint32_t chosen = 0;
+            uint4 dp = make_uint4(0u, 0u, 0u, 0u);
+            for (uint32_t t = 0; t < (uint32_t)kMutDraws && chosen < K; ++t) {
+                if ((t & 3u) == 0u) dp = philox(make_uint4(j, g, rep, (kMutPos << 24) | (t >> 2)), k0, k1);
+                const uint32_t pos = __umulhi(lane_of(dp, (int)(t & 3u)), 2u * L);
+                bool dup = false;
+                for (uint32_t q = 0; q < chosen; ++q) dup |= s_mpos[warp][q] == pos;
+                if (!dup) {
+                    if (lane == 0) s_mpos[warp][chosen] = pos;
+                    __syncwarp();
+                    ++chosen;
+                }
+            }
+            __threadfence_block();  // the vector stores above precede the in-place updates
+            for (uint32_t t = 0; t < chosen; ++t) {
+                const uint32_t pos = s_mpos[warp][t];
+                const int32_t step = irwin_hall_step(j, g, rep, kMutSize, 3u * t, s_mut, k0, k1);
+                const uint32_t locus = pos >= L ? pos - L : pos;
+                if (locus / C == (uint32_t)lane) {
+                    int16_t *cell = pc + pos, *other = pc + (pos >= L ? locus : locus + L);
+                    const int32_t old = *cell, nv = min(max(old + step, -32768), 32767), o = *other;
+                    *cell = (int16_t)nv;
+                    part += nv - old;
+                    het += (nv != o ? 1u : 0u) - (old != o ? 1u : 0u);
+                    sq += (unsigned long long)((long long)nv * nv - (long long)old * old);
+                }
+            }
+            __syncwarp();  // positions are rewritten by the next offspring
+        }
+        lane_het += het;
+        lane_allele += sq;
+        // (C) phenotype: the sum of all values, plus the environmental step
+        int32_t raw = __reduce_add_sync(0xFFFFFFFFu, part);
+        if (s_env != 0) raw += irwin_hall_step(j, g, rep, kEnv, 0u, s_env, k0, k1);
+        // (D) survival
+        const long long v = (long long)raw + (long long)bias;
+        const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> shift_bin, (long long)(kBins - 1));
+        uint32_t thr = __ldg(&P->table[bin]);
+        if (f != kCertain) thr = __umulhi(thr, f);
+        const bool alive = (thr == kCertain) || (r.z < thr);
+        sum_raw += raw;
+        sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
+        mn = min(mn, raw);
+        mx = max(mx, raw);
+        if (alive) {
+            alive_bits |= 1u << i;
+            ++nsurv;
+            sum_raw_s += raw;
+            if (has_eco) cons += __ldg(&P->attack[bin]);
+        }
+    }
+    if (lane == 0 && wbase < n) {
+        sg.alive[wbase >> 5] = alive_bits;
+        if (nsurv) atomicAdd(&bucket_now[wbase / kBucket], nsurv);
+    }
+    // statistics: the per-offspring sums are the same in every lane; the
+    // per-lane het and allele sums are reduced over the warp
+    const uint32_t w_het = __reduce_add_sync(0xFFFFFFFFu, lane_het);
+    const unsigned long long w_allele = warp_sum_u64(lane_allele);
+    if (lane == 0) {
+        s_ll[0][warp] = sum_raw;
+        s_ll[1][warp] = sum_raw_s;
+        s_ull[0][warp] = sum_raw2;
+        s_ull[1][warp] = cons;
+        s_ull[2][warp] = w_allele;
+        s_ull[3][warp] = nsurv;
+        s_u32[0][warp] = w_het;
+        s_mm[0][warp] = mn;
+        s_mm[1][warp] = mx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long a0 = 0, a1 = 0;
+        unsigned long long b0 = 0, b1 = 0, al = 0, sv = 0, hz = 0;
+        int m0 = INT_MAX, m1 = INT_MIN;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            a0 += s_ll[0][w];
+            a1 += s_ll[1][w];
+            b0 += s_ull[0][w];
+            b1 += s_ull[1][w];
+            al += s_ull[2][w];
+            sv += s_ull[3][w];
+            hz += s_u32[0][w];
+            m0 = min(m0, s_mm[0][w]);
+            m1 = max(m1, s_mm[1][w]);
+        }
+        if (sv | hz | (unsigned long long)(m1 != INT_MIN)) {
+            StatAcc *acc = sg.acc + blockIdx.x % kAccCopies;
+            atomicAdd(&acc->s, sv);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&acc->sum_raw), (unsigned long long)a0);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&acc->sum_raw_s), (unsigned long long)a1);
+            atomicAdd(&acc->sum_raw2, b0);
+            if (b1) atomicAdd(&acc->cons, b1);
+            atomicAdd(&acc->het, hz);
+            atomicAdd(&acc->allele, al);
+            atomicMin(&acc->mn, m0);
+            atomicMax(&acc->mx, m1);
+        }
+    }
+}
+
+// Continuous founders: value of copy q = h*L + l is effect[l] (decoded from the
+// offset-binary planes) when the biallelic founder draw of q is below p0.
+template <int C>
+__global__ void k_founders_cont(const PopParams *__restrict__ P, uint32_t *__restrict__ geno,
+                                uint32_t *__restrict__ surv, uint32_t n, uint32_t p0) {
+    constexpr uint32_t L = 32u * C, W = C;  // W = L / 32 words of the planes
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int16_t *rec = reinterpret_cast<int16_t *>(geno + (size_t)i * L);
+    for (uint32_t q4 = 0; q4 < 2u * L / 4u; ++q4) {
+        const uint4 d = philox(make_uint4(i, 0u, P->rep, (kFounder << 24) | q4), P->key0, P->key1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t q = 4u * q4 + (uint32_t)c, l = q % L;
+            int32_t e = P->e_min;
+            for (uint32_t b = 0; b < P->nplanes; ++b) e += (int32_t)((P->planes[b * W + l / 32u] >> (l % 32u)) & 1u) << b;
+            rec[q] = (int16_t)(lane_of(d, c) < p0 ? e : 0);
+        }
+    }
+    surv[i] = i;
+}
+
 // ---------------------------------------- compaction kernel (Fig. 1E, 1F)
 // One block of kCompactThreads threads per bucket of kBucket offspring: its
 // first kBucketWords threads write the survivors' indices, in offspring order,
@@ -1049,6 +1316,34 @@ bool supported_items(uint32_t words, uint32_t items) {
 uint32_t tile_size(uint32_t items) { return (uint32_t)kBlock * items; }
 
 GenKernel compact_kernel() { return &k_compact; }
+
+OffspringKernel continuous_kernel(uint32_t n_loci) {
+    OffspringKernel k;
+    switch (n_loci) {
+        case 32: k.fn = &k_offspring_cont<1>; break;
+        case 64: k.fn = &k_offspring_cont<2>; break;
+        case 128: k.fn = &k_offspring_cont<4>; break;
+        case 256: k.fn = &k_offspring_cont<8>; break;
+        default: return OffspringKernel{};
+    }
+    k.smem = 0;
+    k.resident = 0;  // not persistent: one block per 256 offspring
+    return k;
+}
+
+int launch_founders_cont(const PopParams *prm, uint32_t n_loci, uint32_t *geno, uint32_t *surv, uint32_t n,
+                         uint32_t p0_q32, void *stream) {
+    const dim3 grid((n + 127) / 128), block(128);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (n_loci) {
+        case 32: k_founders_cont<1><<<grid, block, 0, s>>>(prm, geno, surv, n, p0_q32); break;
+        case 64: k_founders_cont<2><<<grid, block, 0, s>>>(prm, geno, surv, n, p0_q32); break;
+        case 128: k_founders_cont<4><<<grid, block, 0, s>>>(prm, geno, surv, n, p0_q32); break;
+        case 256: k_founders_cont<8><<<grid, block, 0, s>>>(prm, geno, surv, n, p0_q32); break;
+        default: return SPG_ERR_INVALID;
+    }
+    return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
+}
 
 namespace {
 template <int W, int I, bool LINKED = false, bool WEIGHTED = false>

@@ -51,7 +51,11 @@ namespace {
 // Point the launch at the population's single segment with `items` offspring
 // per thread (uploads the device copy of the segment; synchronous).
 int configure_launch(spg_pop *p, uint32_t items) {
-    OffspringKernel k = offspring_kernel(p->words, items, p->host_prm->linked != 0u, p->host_prm->weighted != 0u);
+    const bool continuous = p->host_prm->continuous != 0u;
+    OffspringKernel k = continuous ? continuous_kernel(p->n_loci)
+                                   : offspring_kernel(p->words, items, p->host_prm->linked != 0u,
+                                                      p->host_prm->weighted != 0u);
+    if (continuous && items != 1u) return fail(SPG_ERR_INVALID, "continuous allelic values run one offspring per thread");
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
     p->items = items;
@@ -72,7 +76,7 @@ int configure_launch(spg_pop *p, uint32_t items) {
     p->gl.args.nsegs = 1;
     p->gl.args.total_tiles = p->ntiles;
     p->gl.args.total_buckets = p->nbuckets;
-    p->gl.blocks = std::min(p->ntiles, k.resident);
+    p->gl.blocks = continuous ? p->ntiles : std::min(p->ntiles, k.resident);  // continuous: not persistent
     p->gl.buckets = p->nbuckets;
     p->chain.reset();
     return SPG_OK;
@@ -91,7 +95,8 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
     if (!p) return fail(SPG_ERR_OOM, "host allocation failed");
     p->n = desc->n;
     p->n_loci = desc->n_loci;
-    p->words = desc->n_loci / 32;
+    // record = 2 * words uint32: bit-packed haplotypes, or 2L int16 values
+    p->words = desc->allele_model == 1u ? desc->n_loci / 2 : desc->n_loci / 32;
     p->seed = desc->seed;
     p->rep = desc->replicate;
     p->host_prm = new (std::nothrow) PopParams();
@@ -156,7 +161,10 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
             return cuda_fail(e, "upload parent weights");
         }
     }
-    rc = view_init(p->view(), *p->host_prm, desc->init_genotypes, desc->p0_q32);
+    rc = view_init(p->view(), *p->host_prm,
+                   desc->allele_model == 1u ? reinterpret_cast<const uint32_t *>(desc->init_values)
+                                            : desc->init_genotypes,
+                   desc->p0_q32);
     if (rc == SPG_OK) rc = view_sync(p->view());  // the caller's arrays are read before returning
     if (rc == SPG_OK) rc = configure_launch(p, items);
     if (rc != SPG_OK) {
@@ -286,7 +294,7 @@ int spg_set_tiling(spg_pop *p, uint32_t items) {
     if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
     if (!supported_items(p->words, items))
         return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (1 or 2 for 256 loci); got %u", items);
-    if ((p->host_prm->linked || p->host_prm->weighted) && items != 1u)
+    if ((p->host_prm->linked || p->host_prm->weighted || p->host_prm->continuous) && items != 1u)
         return fail(SPG_ERR_INVALID, "a population with a linkage map or parent weights runs one offspring per thread");
     const int rc = view_sync(p->view());
     if (rc != SPG_OK) return rc;

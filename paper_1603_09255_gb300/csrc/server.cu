@@ -238,7 +238,7 @@ int spg_server_submit(spg_server *s, const spg_pop_desc *desc, const spg_ecology
     if (rc != SPG_OK) return rc;
     if (eco && (rc = check_ecology(eco)) != SPG_OK) return rc;
     if (n_gen == 0) return fail(SPG_ERR_INVALID, "a job needs at least one generation");
-    if (desc->map_morgans || desc->mother_weights || desc->father_weights)
+    if (desc->map_morgans || desc->mother_weights || desc->father_weights || desc->allele_model)
         return fail(SPG_ERR_INVALID, "linkage maps and parent weights are supported for single populations");
     std::unique_ptr<Job> j(new (std::nothrow) Job());
     if (!j) return fail(SPG_ERR_OOM, "host allocation failed");

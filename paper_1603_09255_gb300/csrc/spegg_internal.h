@@ -28,7 +28,9 @@ constexpr double kMaxMapMorgans = 16.0;  // total length of a linkage map
 constexpr int kLinkGuide = 1024;         // guide-table entries of the crossover interval search
 
 // Philox counter word 3 = purpose << 24 | sub
-enum Purpose : uint32_t { kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4, kLink = 5, kMateW = 6, kGrowth = 7 };
+enum Purpose : uint32_t {
+    kFounder = 1, kMate = 2, kRecomb = 3, kMutPos = 4, kLink = 5, kMateW = 6, kGrowth = 7, kMutSize = 8, kEnv = 9
+};
 constexpr uint32_t kMateAttempts = 64;   // proposals per weighted parent
 
 // Acceptance thresholds of weighted parents (device global memory): acc[0]
@@ -71,7 +73,8 @@ struct alignas(16) PopParams {
     double r, K, R_half;
     double r_sd;                 // Beverton-Holt: sd of the growth rate
     uint32_t eco_model;          // 0 logistic, 1 Beverton-Holt
-    uint32_t pad_eco;
+    uint32_t continuous;         // allelic values are int16 Q8 (records of L words)
+    long long s_mut, s_env;      // continuous: Irwin-Hall step scales, Q16
     uint32_t ntiles;
     uint32_t stats_cap;
     const LinkParams *link;      // linkage map tables, or null (free recombination)
@@ -158,6 +161,13 @@ int launch_founders(uint32_t words, uint32_t *geno, uint32_t *surv, uint32_t n, 
                     uint32_t rep, uint32_t p0_q32, void *stream);
 // Enqueue survivors = 0..n-1 only (caller-supplied founders).
 int launch_iota(uint32_t *surv, uint32_t n, void *stream);
+// The generation kernel of a continuous-allele population (one warp per
+// offspring at a time, 256 offspring per block, no persistent grid).
+OffspringKernel continuous_kernel(uint32_t n_loci);
+// Enqueue continuous founders: value = effect[l] * allele of the biallelic
+// founder draws (records of 2L int16), survivors = 0..n-1.
+int launch_founders_cont(const PopParams *prm, uint32_t n_loci, uint32_t *geno, uint32_t *surv, uint32_t n,
+                         uint32_t p0_q32, void *stream);
 // Enqueue survw[r] = surv[r] | bin << 32 for the S current survivors (surv
 // NULL: survivor r is record r), the bin computed from the record.
 int launch_survivor_bins(const PopParams *prm, uint32_t words, const uint32_t *geno, const uint32_t *surv,

@@ -45,7 +45,8 @@ class spg_pop_desc(ctypes.Structure):
         ("p0_q32", ctypes.c_uint32), ("surv_table", ctypes.c_void_p), ("bin_bias", ctypes.c_int32),
         ("bin_shift", ctypes.c_uint32), ("mu", ctypes.c_double), ("stats_capacity", ctypes.c_uint32),
         ("map_morgans", ctypes.c_void_p), ("mother_weights", ctypes.c_void_p), ("father_weights", ctypes.c_void_p),
-        ("dominance", ctypes.c_void_p),
+        ("dominance", ctypes.c_void_p), ("allele_model", ctypes.c_uint32), ("mut_sd", ctypes.c_double),
+        ("env_sd", ctypes.c_double), ("init_values", ctypes.c_void_p),
     ]
 
 
@@ -264,9 +265,13 @@ class Population:
     def __init__(self, n: int, n_loci: int, seed: int, replicate: int, effects, surv_table, bin_bias: int,
                  bin_shift: int, mu: float, init_genotypes=None, p0_q32: int = 0x80000000,
                  stats_capacity: int = 0, stream=None, allocator: Optional[TorchAllocator] = None,
-                 map_morgans=None, mother_weights=None, father_weights=None, dominance=None):
+                 map_morgans=None, mother_weights=None, father_weights=None, dominance=None,
+                 allele_model: int = 0, mut_sd: float = 0.0, env_sd: float = 0.0, init_values=None):
         L = lib()
-        self.n, self.n_loci, self.words = int(n), int(n_loci), int(n_loci) // 32
+        self.n, self.n_loci = int(n), int(n_loci)
+        self.continuous = int(allele_model) == 1
+        # a record is 2 * words uint32: bit-packed haplotypes or 2L int16 values
+        self.words = self.n_loci // 2 if self.continuous else self.n_loci // 32
         e = np.ascontiguousarray(effects, dtype=np.int16)
         t = _u32(surv_table)
         if t.shape != (N_BINS,) or e.shape != (self.n_loci,):
@@ -283,12 +288,16 @@ class Population:
         dm = None if dominance is None else np.ascontiguousarray(dominance, dtype=np.int16)
         if dm is not None and dm.shape != (self.n_loci,):
             raise ValueError("dominance must have n_loci entries")
-        self._keep = (e, t, g, m, mw, fw, dm)
+        iv = None if init_values is None else np.ascontiguousarray(init_values, dtype=np.int16).reshape(-1)
+        if iv is not None and iv.size != self.n * 2 * self.n_loci:
+            raise ValueError("init_values must have n * 2 * n_loci entries")
+        self._keep = (e, t, g, m, mw, fw, dm, iv)
         d = spg_pop_desc(self.n, self.n_loci, int(seed), int(replicate), e.ctypes.data,
                          None if g is None else g.ctypes.data, int(p0_q32), t.ctypes.data, int(bin_bias),
                          int(bin_shift), float(mu), int(stats_capacity), None if m is None else m.ctypes.data,
                          None if mw is None else mw.ctypes.data, None if fw is None else fw.ctypes.data,
-                         None if dm is None else dm.ctypes.data)
+                         None if dm is None else dm.ctypes.data, int(allele_model), float(mut_sd), float(env_sd),
+                         None if iv is None else iv.ctypes.data)
         self.allocator = allocator if allocator is not None else TorchAllocator()
         self._stream = _stream_handle(stream)
         h = ctypes.c_void_p()
@@ -302,6 +311,10 @@ class Population:
         kw.setdefault("mother_weights", getattr(w, "mother_weights", None))
         kw.setdefault("father_weights", getattr(w, "father_weights", None))
         kw.setdefault("dominance", getattr(w, "dominance", None))
+        kw.setdefault("allele_model", getattr(w, "allele_model", 0))
+        kw.setdefault("mut_sd", getattr(w, "mut_sd", 0.0))
+        kw.setdefault("env_sd", getattr(w, "env_sd", 0.0))
+        kw.setdefault("init_values", getattr(w, "init_values", None))
         p = cls(w.n, w.n_loci, w.seed, w.replicate, w.effects, w.surv_table, w.bias, w.shift, w.mu,
                 w.init_genotypes, w.p0_q32, **kw)
         if w.has_ecology:
@@ -336,6 +349,12 @@ class Population:
         out = np.zeros((self.n, 2 * self.words), np.uint32)
         check(lib().spg_read_genotypes(self._h, out.ctypes.data, out.size), "spg_read_genotypes")
         return out
+
+    def values(self) -> np.ndarray:
+        """Allelic values [n, 2, L] (int16 Q8) of a continuous population."""
+        if not self.continuous:
+            raise ValueError("not a continuous-allele population")
+        return self.genotypes().view(np.int16).reshape(self.n, 2, self.n_loci)
 
     def survivors(self) -> np.ndarray:
         S = ctypes.c_uint32(0)
@@ -396,7 +415,8 @@ def _desc_for(w, keep: list, stats_capacity: int = 0) -> spg_pop_desc:
                         None if g is None else g.ctypes.data, int(w.p0_q32), t.ctypes.data, int(w.bias),
                         int(w.shift), float(w.mu), int(stats_capacity), None if m is None else m.ctypes.data,
                         None if mw is None else mw.ctypes.data, None if fw is None else fw.ctypes.data,
-                        None if dm is None else dm.ctypes.data)
+                        None if dm is None else dm.ctypes.data, int(getattr(w, "allele_model", 0)),
+                        float(getattr(w, "mut_sd", 0.0)), float(getattr(w, "env_sd", 0.0)), None)
 
 
 class Batch:
