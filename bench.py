@@ -117,6 +117,25 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
 
 
+def replica_workload(workload, rank: int):
+    """Replicas only: rank r runs the same population with replicate id r
+    (independent Philox streams, no exchange between ranks)."""
+    workload.replicate = rank
+    return workload
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value over all ranks (timings: the slowest rank sets the
+    whole job's time); the value itself without an initialised group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def reference_arm(args, workload):
     """The CPU oracle timed on a bounded sample: each step is one generation of
     the full-size population, single-threaded."""
@@ -339,7 +358,7 @@ def main():
     pkg_build.build()
     from paper_1603_09255_gb300 import spegg
 
-    workload.replicate = rank
+    workload = replica_workload(workload, rank)
     stream = torch.cuda.Stream()
     pop = spegg.Population.from_workload(workload, stats_capacity=GENERATIONS + 8, stream=stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -368,10 +387,7 @@ def main():
         barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, device="cuda")
     st = pop.state()
     assert st["status"] == 0, f"population status {st['status']}"
     ind_gen = workload.n * GENERATIONS * args.steps
