@@ -890,61 +890,55 @@ __device__ __forceinline__ int32_t irwin_hall_step(uint32_t j, uint32_t g, uint3
     return (int32_t)(((t >> 8) * s) >> 40);
 }
 
-// C consecutive int16 values (2C bytes, aligned to 2C) in one access.
-template <int C>
-__device__ __forceinline__ void load_vals(const int16_t *p, int32_t (&v)[C]) {
-    if constexpr (C == 1) {
-        v[0] = __ldg(p);
-    } else {
-        uint32_t w[C / 2];
-        if constexpr (C == 2) {
-            w[0] = __ldg(reinterpret_cast<const uint32_t *>(p));
-        } else if constexpr (C == 4) {
-            const uint2 x = __ldg(reinterpret_cast<const uint2 *>(p));
-            w[0] = x.x;
-            w[1] = x.y;
-        } else {
-            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
-            w[0] = x.x;
-            w[1] = x.y;
-            w[2] = x.z;
-            w[3] = x.w;
-        }
-#pragma unroll
-        for (int k = 0; k < C / 2; ++k) {
-            v[2 * k] = (int32_t)(int16_t)(w[k] & 0xFFFFu);
-            v[2 * k + 1] = (int32_t)(int16_t)(w[k] >> 16);
-        }
-    }
+// Eight packed int16 values (one 16-byte access) per lane and haplotype.
+// val16: value `half` (0 low, 1 high) of a packed word, sign-extended.
+__device__ __forceinline__ int32_t val16(uint32_t w, uint32_t half) {
+    return half ? (int32_t)w >> 16 : (int32_t)(int16_t)(w & 0xFFFFu);
 }
-template <int C>
-__device__ __forceinline__ void store_vals(int16_t *p, const int32_t (&v)[C]) {
-    if constexpr (C == 1) {
-        *p = (int16_t)v[0];
-    } else {
-        uint32_t w[C / 2];
-#pragma unroll
-        for (int k = 0; k < C / 2; ++k) w[k] = ((uint32_t)v[2 * k] & 0xFFFFu) | ((uint32_t)v[2 * k + 1] << 16);
-        if constexpr (C == 2) *reinterpret_cast<uint32_t *>(p) = w[0];
-        else if constexpr (C == 4) *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
-        else *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
+__device__ __forceinline__ uint32_t word_of(const uint4 &c, uint32_t q) {
+    return q == 0u ? c.x : q == 1u ? c.y : q == 2u ? c.z : c.w;
+}
+__device__ __forceinline__ void set_word(uint4 &c, uint32_t q, uint32_t v) {
+    if (q == 0u) c.x = v;
+    else if (q == 1u) c.y = v;
+    else if (q == 2u) c.z = v;
+    else c.w = v;
+}
+// the values of b where bit k (k = 0..7, value k of the eight) of `bits` is set, of a elsewhere
+__device__ __forceinline__ uint4 pick8(const uint4 &a, const uint4 &b, uint32_t bits) {
+    auto sel = [](uint32_t x, uint32_t y, uint32_t two) {
+        const uint32_t m = ((two & 1u) ? 0x0000FFFFu : 0u) | ((two & 2u) ? 0xFFFF0000u : 0u);
+        return (x & ~m) | (y & m);
+    };
+    return make_uint4(sel(a.x, b.x, bits), sel(a.y, b.y, bits >> 2), sel(a.z, b.z, bits >> 4),
+                      sel(a.w, b.w, bits >> 6));
+}
+// value k of the eight moved by `step`, clamped to the int16 range
+__device__ __forceinline__ void add_step(uint4 &c, uint32_t k, int32_t step) {
+    const uint32_t q = k >> 1, half = k & 1u, w = word_of(c, q);
+    const int32_t nv = min(max(val16(w, half) + step, -32768), 32767);
+    set_word(c, q, half ? (w & 0xFFFFu) | ((uint32_t)nv << 16) : (w & 0xFFFF0000u) | ((uint32_t)nv & 0xFFFFu));
 }
 
-// Generation kernel of a continuous-allele population (S2 "Genetics"): each
-// warp forms 32 consecutive offspring one at a time, lane i owning loci
-// i*C .. i*C+C-1 of both haplotypes (L = 32 C), so parent and child records
-// (2L int16) move in coalesced accesses.  Parents, gamete bits, mutation
-// counts and positions follow the biallelic model's draws; mutated values
-// take Irwin-Hall steps; the phenotype is the warp sum of the values plus the
-// environmental step.  Survivors, statistics and the bitmap feed the same
-// compaction kernel as the biallelic model.
-template <int C>
-__global__ void __launch_bounds__(kBlock) k_offspring_cont(const __grid_constant__ GenArgs a) {
-    constexpr uint32_t L = 32u * C;
-    constexpr int NW = kBlock / 32;
+// Generation kernel of a continuous-allele population (S2 "Genetics").  A
+// group of G = L/8 lanes forms one offspring, lane li owning loci
+// 8li .. 8li+7 of both haplotypes, so parent and child records (2L int16)
+// move in coalesced 16-byte accesses; a warp holds 32/G groups and each
+// group U offspring at a time, all their parent loads issued before any is
+// used.  Parents, gamete bits, mutation counts and positions follow the
+// biallelic model's draws; mutated values take Irwin-Hall steps; the
+// phenotype is the group sum of the values plus the environmental step.
+// Survivors, statistics and the bitmap feed the same compaction kernel as
+// the biallelic model.
+constexpr int kContInFlight = 2;  // offspring a group of lanes forms at a time
+
+template <int G, int U>
+__global__ void __launch_bounds__(kBlock, 3) k_offspring_cont(const __grid_constant__ GenArgs a) {
+    constexpr uint32_t L = 8u * G;
+    constexpr int NW = kBlock / 32, NO = 32 / G;
+    static_assert(G >= 4 && G <= 32 && (G & (G - 1)) == 0 && G % U == 0, "group of 4..32 lanes");
     __shared__ uint32_t s_cdf[kMaxKmax];
-    __shared__ uint32_t s_mpos[NW][kMaxKmax];
+    __shared__ uint32_t s_mpos[NW * NO][kMaxKmax];
     __shared__ long long s_ll[2][NW];
     __shared__ unsigned long long s_ull[4][NW];
     __shared__ uint32_t s_u32[2][NW];
@@ -959,8 +953,8 @@ __global__ void __launch_bounds__(kBlock) k_offspring_cont(const __grid_constant
     const int32_t bias = P->bias;
     const long long s_mut = P->s_mut, s_env = P->s_env;
     const bool has_eco = P->has_eco != 0u;
-    const uint32_t *par = sg.geno[now.gen & 1u];
-    uint32_t *chi = sg.geno[g & 1u];
+    const uint4 *par = reinterpret_cast<const uint4 *>(sg.geno[now.gen & 1u]);
+    uint4 *chi = reinterpret_cast<uint4 *>(sg.geno[g & 1u]);
     const uint32_t *sin = sg.surv[now.gen & 1u];
     uint32_t *bucket_now = sg.bucket_sum + (g & 1u) * sg.nbuckets;
     uint32_t *bucket_next = sg.bucket_sum + ((g + 1u) & 1u) * sg.nbuckets;
@@ -969,123 +963,142 @@ __global__ void __launch_bounds__(kBlock) k_offspring_cont(const __grid_constant
     const uint32_t base = blockIdx.x * (uint32_t)kBlock;
     if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
     const uint32_t wbase = base + (uint32_t)warp * 32u;
-    const uint32_t wv = ((uint32_t)lane * C) >> 5, sh = ((uint32_t)lane * C) & 31u;  // this lane's mask word and bit
+    const uint32_t grp = (uint32_t)lane / G, li = (uint32_t)lane % G;
+    const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u) << (grp * G);
+    const uint32_t wv = li >> 2, sh = (li & 3u) * 8u;  // this lane's mask word and first bit
+    uint32_t *mpos = s_mpos[warp * NO + grp];
+    constexpr uint32_t R4 = L / 4;  // 16-byte units per record
 
     long long sum_raw = 0, sum_raw_s = 0;
     unsigned long long sum_raw2 = 0, cons = 0, lane_allele = 0;
     uint32_t lane_het = 0, alive_bits = 0, nsurv = 0;
     int mn = INT_MAX, mx = INT_MIN;
-    for (uint32_t i = 0; i < 32u; ++i) {
-        const uint32_t j = wbase + i;
-        if (j >= n) break;  // the same for every lane
-        // (A) parents
-        const uint4 r = philox(make_uint4(j, g, rep, kMate << 24), k0, k1);
-        const uint32_t mom = __ldcg(sin + __umulhi(r.x, S)), dad = __ldcg(sin + __umulhi(r.y, S));
-        // (B) gametes: mask word wv of the mother (stream 2wv) and father (2wv + 1)
-        const uint4 dm = philox(make_uint4(j, g, rep, (kRecomb << 24) | (wv >> 1)), k0, k1);
-        const uint32_t mm = (wv & 1u) ? dm.z : dm.x, mf = (wv & 1u) ? dm.w : dm.y;
-        const int16_t *pm = reinterpret_cast<const int16_t *>(par + (size_t)mom * L);
-        const int16_t *pf = reinterpret_cast<const int16_t *>(par + (size_t)dad * L);
-        int32_t m0[C], m1[C], f0[C], f1[C], c0[C], c1[C];
-        load_vals<C>(pm + lane * C, m0);
-        load_vals<C>(pm + L + lane * C, m1);
-        load_vals<C>(pf + lane * C, f0);
-        load_vals<C>(pf + L + lane * C, f1);
+    for (uint32_t it = 0; it < (uint32_t)(G / U); ++it) {
+        uint32_t jj[U], mom[U], dad[U];
+        uint4 r[U], m0[U], m1[U], f0[U], f1[U];
+        // (A) parents of the group's U offspring; then all their records
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            c0[k] = ((mm >> (sh + k)) & 1u) ? m1[k] : m0[k];
-            c1[k] = ((mf >> (sh + k)) & 1u) ? f1[k] : f0[k];
+        for (int u = 0; u < U; ++u) {
+            jj[u] = wbase + (it * U + (uint32_t)u) * NO + grp;
+            r[u] = philox(make_uint4(jj[u], g, rep, kMate << 24), k0, k1);
+            mom[u] = jj[u] < n ? __ldcg(sin + __umulhi(r[u].x, S)) : 0u;
+            dad[u] = jj[u] < n ? __ldcg(sin + __umulhi(r[u].y, S)) : 0u;
         }
-        // the child's values, and this lane's part of the phenotype sum, its
-        // heterozygous loci and its sum of squares
-        int16_t *pc = reinterpret_cast<int16_t *>(chi + (size_t)j * L);
-        store_vals<C>(pc + lane * C, c0);
-        store_vals<C>(pc + L + lane * C, c1);
-        int32_t part = 0;
-        uint32_t het = 0;
-        unsigned long long sq = 0;
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            part += c0[k] + c1[k];
-            het += c0[k] != c1[k] ? 1u : 0u;
-            sq += (unsigned long long)((long long)c0[k] * c0[k] + (long long)c1[k] * c1[k]);
+        for (int u = 0; u < U; ++u) {
+            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+            const bool ok = jj[u] < n;
+            const uint4 *pm = par + (size_t)mom[u] * R4, *pf = par + (size_t)dad[u] * R4;
+            m0[u] = ok ? __ldg(pm + li) : z;
+            m1[u] = ok ? __ldg(pm + G + li) : z;
+            f0[u] = ok ? __ldg(pf + li) : z;
+            f1[u] = ok ? __ldg(pf + G + li) : z;
         }
-        // (B) mutation: the biallelic count and distinct positions, each
-        // mutated value moved by an Irwin-Hall step; rare, so the owner lane
-        // updates the stored value in place and corrects its sums
-        const uint32_t u_mut = r.w;
-        if (kmax != 0u && u_mut >= s_cdf[0]) {
-            uint32_t K = 0;
-            for (uint32_t q = 0; q < kmax; ++q) K += u_mut >= s_cdf[q] ? 1u : 0u;
-            uint32_t chosen = 0;
-            uint4 dp = make_uint4(0u, 0u, 0u, 0u);
-            for (uint32_t t = 0; t < (uint32_t)kMutDraws && chosen < K; ++t) {
-                if ((t & 3u) == 0u) dp = philox(make_uint4(j, g, rep, (kMutPos << 24) | (t >> 2)), k0, k1);
-                const uint32_t pos = __umulhi(lane_of(dp, (int)(t & 3u)), 2u * L);
-                bool dup = false;
-                for (uint32_t q = 0; q < chosen; ++q) dup |= s_mpos[warp][q] == pos;
-                if (!dup) {
-                    if (lane == 0) s_mpos[warp][chosen] = pos;
-                    __syncwarp();
-                    ++chosen;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t j = jj[u], bit = (it * U + (uint32_t)u) * NO + grp;
+            const bool ok = j < n;
+            // (B) gametes: mask word wv of the mother (stream 2wv) and father (2wv + 1)
+            const uint4 dm = philox(make_uint4(j, g, rep, (kRecomb << 24) | (wv >> 1)), k0, k1);
+            const uint32_t mm = (wv & 1u) ? dm.z : dm.x, mf = (wv & 1u) ? dm.w : dm.y;
+            uint4 c0 = pick8(m0[u], m1[u], (mm >> sh) & 0xFFu), c1 = pick8(f0[u], f1[u], (mf >> sh) & 0xFFu);
+            // (B) mutation: the biallelic count and distinct positions, each
+            // mutated value moved by an Irwin-Hall step by the lane owning it
+            const uint32_t u_mut = r[u].w;
+            if (ok && kmax != 0u && u_mut >= s_cdf[0]) {  // the same in the whole group
+                uint32_t K = 0;
+                for (uint32_t q = 0; q < kmax; ++q) K += u_mut >= s_cdf[q] ? 1u : 0u;
+                uint32_t chosen = 0;
+                uint4 dp = make_uint4(0u, 0u, 0u, 0u);
+                for (uint32_t t = 0; t < (uint32_t)kMutDraws && chosen < K; ++t) {
+                    if ((t & 3u) == 0u) dp = philox(make_uint4(j, g, rep, (kMutPos << 24) | (t >> 2)), k0, k1);
+                    const uint32_t pos = __umulhi(lane_of(dp, (int)(t & 3u)), 2u * L);
+                    bool dup = false;
+                    for (uint32_t q = 0; q < chosen; ++q) dup |= mpos[q] == pos;
+                    if (!dup) {
+                        if (li == 0u) mpos[chosen] = pos;
+                        __syncwarp(gmask);
+                        ++chosen;
+                    }
+                }
+                for (uint32_t t = 0; t < chosen; ++t) {
+                    const uint32_t pos = mpos[t], locus = pos >= L ? pos - L : pos;
+                    if ((locus >> 3) == li) {
+                        const int32_t step = irwin_hall_step(j, g, rep, kMutSize, 3u * t, s_mut, k0, k1);
+                        if (pos >= L) add_step(c1, locus & 7u, step);
+                        else add_step(c0, locus & 7u, step);
+                    }
+                }
+                __syncwarp(gmask);  // positions are rewritten by the group's next offspring
+            }
+            if (ok) {
+                chi[(size_t)j * R4 + li] = c0;
+                chi[(size_t)j * R4 + G + li] = c1;
+            }
+            // this lane's part of the phenotype sum, its heterozygous loci and squares
+            int32_t part = 0;
+            uint32_t het = 0;
+            unsigned long long sq = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < 8u; ++k) {
+                const int32_t x = val16(word_of(c0, k >> 1), k & 1u), y = val16(word_of(c1, k >> 1), k & 1u);
+                part += x + y;
+                het += x != y ? 1u : 0u;
+                sq += (uint32_t)(x * x) + (uint32_t)(y * y);
+            }
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+            // (C) phenotype: the sum of all values, plus the environmental step
+            int32_t raw = part;
+            if (s_env != 0) raw += irwin_hall_step(j, g, rep, kEnv, 0u, s_env, k0, k1);
+            // (D) survival
+            const long long v = (long long)raw + (long long)bias;
+            const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> shift_bin, (long long)(kBins - 1));
+            uint32_t thr = __ldg(&P->table[bin]);
+            if (f != kCertain) thr = __umulhi(thr, f);
+            const bool alive = (thr == kCertain) || (r[u].z < thr);
+            if (ok) {
+                lane_het += het;
+                lane_allele += sq;
+                mn = min(mn, raw);
+                mx = max(mx, raw);
+                if (alive) alive_bits |= 1u << bit;
+                if (li == 0u) {  // per-offspring sums once per group
+                    sum_raw += raw;
+                    sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
+                    if (alive) {
+                        ++nsurv;
+                        sum_raw_s += raw;
+                        if (has_eco) cons += __ldg(&P->attack[bin]);
+                    }
                 }
             }
-            __threadfence_block();  // the vector stores above precede the in-place updates
-            for (uint32_t t = 0; t < chosen; ++t) {
-                const uint32_t pos = s_mpos[warp][t];
-                const int32_t step = irwin_hall_step(j, g, rep, kMutSize, 3u * t, s_mut, k0, k1);
-                const uint32_t locus = pos >= L ? pos - L : pos;
-                if (locus / C == (uint32_t)lane) {
-                    int16_t *cell = pc + pos, *other = pc + (pos >= L ? locus : locus + L);
-                    const int32_t old = *cell, nv = min(max(old + step, -32768), 32767), o = *other;
-                    *cell = (int16_t)nv;
-                    part += nv - old;
-                    het += (nv != o ? 1u : 0u) - (old != o ? 1u : 0u);
-                    sq += (unsigned long long)((long long)nv * nv - (long long)old * old);
-                }
-            }
-            __syncwarp();  // positions are rewritten by the next offspring
-        }
-        lane_het += het;
-        lane_allele += sq;
-        // (C) phenotype: the sum of all values, plus the environmental step
-        int32_t raw = __reduce_add_sync(0xFFFFFFFFu, part);
-        if (s_env != 0) raw += irwin_hall_step(j, g, rep, kEnv, 0u, s_env, k0, k1);
-        // (D) survival
-        const long long v = (long long)raw + (long long)bias;
-        const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> shift_bin, (long long)(kBins - 1));
-        uint32_t thr = __ldg(&P->table[bin]);
-        if (f != kCertain) thr = __umulhi(thr, f);
-        const bool alive = (thr == kCertain) || (r.z < thr);
-        sum_raw += raw;
-        sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
-        mn = min(mn, raw);
-        mx = max(mx, raw);
-        if (alive) {
-            alive_bits |= 1u << i;
-            ++nsurv;
-            sum_raw_s += raw;
-            if (has_eco) cons += __ldg(&P->attack[bin]);
         }
     }
+    alive_bits = __reduce_or_sync(0xFFFFFFFFu, alive_bits);
+    const uint32_t w_surv = __reduce_add_sync(0xFFFFFFFFu, nsurv);
     if (lane == 0 && wbase < n) {
         sg.alive[wbase >> 5] = alive_bits;
-        if (nsurv) atomicAdd(&bucket_now[wbase / kBucket], nsurv);
+        if (w_surv) atomicAdd(&bucket_now[wbase / kBucket], w_surv);
     }
-    // statistics: the per-offspring sums are the same in every lane; the
-    // per-lane het and allele sums are reduced over the warp
+    // statistics over the warp: the per-offspring sums sit in the group
+    // leaders, the het and allele sums in every lane
     const uint32_t w_het = __reduce_add_sync(0xFFFFFFFFu, lane_het);
     const unsigned long long w_allele = warp_sum_u64(lane_allele);
+    const long long w_raw = (long long)warp_sum_u64((unsigned long long)sum_raw);
+    const long long w_raw_s = (long long)warp_sum_u64((unsigned long long)sum_raw_s);
+    const unsigned long long w_raw2 = warp_sum_u64(sum_raw2), w_cons = warp_sum_u64(cons);
+    const int w_mn = __reduce_min_sync(0xFFFFFFFFu, mn), w_mx = __reduce_max_sync(0xFFFFFFFFu, mx);
     if (lane == 0) {
-        s_ll[0][warp] = sum_raw;
-        s_ll[1][warp] = sum_raw_s;
-        s_ull[0][warp] = sum_raw2;
-        s_ull[1][warp] = cons;
+        s_ll[0][warp] = w_raw;
+        s_ll[1][warp] = w_raw_s;
+        s_ull[0][warp] = w_raw2;
+        s_ull[1][warp] = w_cons;
         s_ull[2][warp] = w_allele;
-        s_ull[3][warp] = nsurv;
+        s_ull[3][warp] = w_surv;
         s_u32[0][warp] = w_het;
-        s_mm[0][warp] = mn;
-        s_mm[1][warp] = mx;
+        s_mm[0][warp] = w_mn;
+        s_mm[1][warp] = w_mx;
     }
     __syncthreads();
     if (tid == 0) {
@@ -1320,10 +1333,10 @@ GenKernel compact_kernel() { return &k_compact; }
 OffspringKernel continuous_kernel(uint32_t n_loci) {
     OffspringKernel k;
     switch (n_loci) {
-        case 32: k.fn = &k_offspring_cont<1>; break;
-        case 64: k.fn = &k_offspring_cont<2>; break;
-        case 128: k.fn = &k_offspring_cont<4>; break;
-        case 256: k.fn = &k_offspring_cont<8>; break;
+        case 32: k.fn = &k_offspring_cont<4, kContInFlight>; break;
+        case 64: k.fn = &k_offspring_cont<8, kContInFlight>; break;
+        case 128: k.fn = &k_offspring_cont<16, kContInFlight>; break;
+        case 256: k.fn = &k_offspring_cont<32, kContInFlight>; break;
         default: return OffspringKernel{};
     }
     k.smem = 0;

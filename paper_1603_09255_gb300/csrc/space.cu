@@ -72,10 +72,12 @@ struct SpaceArgs {
     uint32_t cap, staging_cap, ring_cap;
     uint32_t *geno[2];   // [cap][2W] by step parity
     uint8_t *age[2];     // [cap]
+    int32_t *raw[2];     // [cap] additive phenotype of each record, set at birth
     uint32_t *off[2];    // [nd + 1]
     uint32_t *adults[2]; // [nd]
     uint32_t *f, *births, *nb_off;   // [nd], [nd], [nd + 1]
     uint32_t *staging;               // [staging_cap][2W] newborn records
+    int32_t *nb_raw;                 // [staging_cap] their phenotypes
     uint8_t *cls, *nb_cls;           // [cap], [staging_cap]
     uint32_t *rank, *nb_rank;        // [cap], [staging_cap]
     uint32_t *cnt;                   // [nd][15] per source deme and (age class, direction)
@@ -209,6 +211,7 @@ __global__ void k_sp_founders(SpaceArgs a, const uint32_t *n0, const uint32_t *p
     }
 #pragma unroll
     for (int hw = 0; hw < 2 * W; ++hw) a.geno[0][(size_t)i * 2 * W + hw] = rec[hw];
+    a.raw[0][i] = sp_phenotype<W>(rec, a.sp + s, a.sp[s].planes);
     const uint32_t half = n0[s] / 2, quarter = n0[s] / 4;
     a.age[0][i] = r < half ? 2 : (r < half + quarter ? 1 : 0);
 }
@@ -348,6 +351,7 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
     sp_stage_planes<W>(sp, s_planes);
     const uint32_t *geno = a.geno[par];
     const uint8_t *age = a.age[par];
+    const int32_t *rawp = a.raw[par];
     const uint32_t base = a.off[par][d], n = a.off[par][d + 1] - base, m = a.adults[par][d];
     const uint32_t f = a.f[d], B = a.births[d], nb0 = a.nb_off[d];
     if (tid < 16) s_run[tid] = 0;
@@ -360,11 +364,10 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
         const uint32_t r = c0 + tid;
         uint32_t cls = kDead;
         if (r < n) {
-            uint32_t rec[2 * W];
-            sp_load_rec<W>(geno + (size_t)(base + r) * 2 * W, rec);
+            // a genotype is fixed for life, so its phenotype was computed once at birth
             const uint32_t ag = age[base + r];
+            const int32_t raw = rawp[base + r];
             const uint4 u = sp_philox(make_uint4(r, t, d, kSpSurv << 24), a.key0, a.key1);
-            const int32_t raw = sp_phenotype<W>(rec, sp, s_planes);
             uint32_t thr = __ldg(&sp->table[ag][sp_bin(sp, raw)]);
             if (f != kCertain) thr = __umulhi(thr, f);
             if (thr == kCertain || u.x < thr) {
@@ -437,6 +440,7 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
                 }
             }
             sp_store_rec<W>(a.staging + (size_t)(nb0 + k) * 2 * W, ch);
+            a.nb_raw[nb0 + k] = sp_phenotype<W>(ch, sp, s_planes);
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 het += __popc(ch[w] ^ ch[W + w]);
@@ -517,22 +521,26 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_scatter(SpaceArgs a) {
     const uint8_t *age = a.age[par];
     uint32_t *ngeno = a.geno[npar];
     uint8_t *nage = a.age[npar];
+    int32_t *nraw = a.raw[npar];
     const uint32_t *noff = a.off[npar];
     const uint32_t base = a.off[par][d], n = a.off[par][d + 1] - base;
     const uint32_t B = a.births[d], nb0 = a.nb_off[d];
     for (uint32_t i = tid; i < n + B; i += kSpBlock) {
         uint32_t cls, rk;
         const uint32_t *src;
+        const int32_t *src_raw;
         if (i < n) {
             cls = a.cls[base + i];
             rk = a.rank[base + i];
             src = geno + (size_t)(base + i) * 2 * W;
+            src_raw = a.raw[par] + base + i;
         } else {
             const uint32_t k = i - n;
             if (nb0 + k >= a.staging_cap) continue;
             cls = a.nb_cls[nb0 + k];
             rk = a.nb_rank[nb0 + k];
             src = a.staging + (size_t)(nb0 + k) * 2 * W;
+            src_raw = a.nb_raw + nb0 + k;
         }
         if (cls >= kDead) continue;
         const uint32_t ci = cls / 5u, dir = cls % 5u;
@@ -543,6 +551,7 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_scatter(SpaceArgs a) {
         sp_load_rec<W>(src, rec);
         sp_store_rec<W>(ngeno + (size_t)pos * 2 * W, rec);
         nage[pos] = (uint8_t)(2u - ci);
+        nraw[pos] = *src_raw;
     }
 }
 
@@ -701,6 +710,7 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
     const size_t o_sp = take(sizeof(SpeciesParams) * c->ns);
     const size_t o_g0 = take((size_t)c->cap * 2 * c->W * 4), o_g1 = take((size_t)c->cap * 2 * c->W * 4);
     const size_t o_a0 = take(c->cap), o_a1 = take(c->cap);
+    const size_t o_r0 = take((size_t)c->cap * 4), o_r1 = take((size_t)c->cap * 4), o_nr = take((size_t)c->staging_cap * 4);
     const size_t o_off0 = take((size_t)(c->nd + 1) * 4), o_off1 = take((size_t)(c->nd + 1) * 4);
     const size_t o_ad0 = take((size_t)c->nd * 4), o_ad1 = take((size_t)c->nd * 4);
     const size_t o_f = take((size_t)c->nd * 4), o_b = take((size_t)c->nd * 4), o_nbo = take((size_t)(c->nd + 1) * 4);
@@ -743,6 +753,9 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
     a.geno[1] = reinterpret_cast<uint32_t *>(b + o_g1);
     a.age[0] = reinterpret_cast<uint8_t *>(b + o_a0);
     a.age[1] = reinterpret_cast<uint8_t *>(b + o_a1);
+    a.raw[0] = reinterpret_cast<int32_t *>(b + o_r0);
+    a.raw[1] = reinterpret_cast<int32_t *>(b + o_r1);
+    a.nb_raw = reinterpret_cast<int32_t *>(b + o_nr);
     a.off[0] = reinterpret_cast<uint32_t *>(b + o_off0);
     a.off[1] = reinterpret_cast<uint32_t *>(b + o_off1);
     a.adults[0] = reinterpret_cast<uint32_t *>(b + o_ad0);
