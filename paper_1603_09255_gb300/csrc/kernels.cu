@@ -923,19 +923,24 @@ __device__ __forceinline__ void add_step(uint4 &c, uint32_t k, int32_t step) {
 // Generation kernel of a continuous-allele population (S2 "Genetics").  A
 // group of G = L/8 lanes forms one offspring, lane li owning loci
 // 8li .. 8li+7 of both haplotypes, so parent and child records (2L int16)
-// move in coalesced 16-byte accesses; a warp holds 32/G groups and each
-// group U offspring at a time, all their parent loads issued before any is
-// used.  Parents, gamete bits, mutation counts and positions follow the
-// biallelic model's draws; mutated values take Irwin-Hall steps; the
-// phenotype is the group sum of the values plus the environmental step.
-// Survivors, statistics and the bitmap feed the same compaction kernel as
-// the biallelic model.
-constexpr int kContInFlight = 2;  // offspring a group of lanes forms at a time
+// move in coalesced 16-byte accesses; a warp holds 32/G groups, each forming
+// U offspring at a time with all their parent loads issued before any is
+// used.  The per-offspring draws (parents, survival and mutation uniforms,
+// environmental step, gamete-mask streams) are made once per warp, one
+// offspring per lane, and handed to the groups by shuffles.  Parents, gamete
+// bits, mutation counts and positions follow the biallelic model's draws;
+// mutated values take Irwin-Hall steps; the phenotype is the group sum of the
+// values plus the environmental step.  Survivors, statistics and the bitmap
+// feed the same compaction kernel as the biallelic model.
+constexpr int kContInFlight = 1;  // offspring a group of lanes forms at a time (four blocks per SM)
 
 template <int G, int U>
-__global__ void __launch_bounds__(kBlock, 3) k_offspring_cont(const __grid_constant__ GenArgs a) {
+__global__ void __launch_bounds__(kBlock, 4) k_offspring_cont(const __grid_constant__ GenArgs a) {
     constexpr uint32_t L = 8u * G;
     constexpr int NW = kBlock / 32, NO = 32 / G;
+    constexpr int NST = G >= 8 ? G / 8 : 1;  // gamete-mask streams per offspring (2 words per parent each)
+    constexpr int PER_T = NO * NST;          // (offspring, stream) pairs one step of the warp uses
+    constexpr int T_PER_SLOT = 32 / PER_T;   // steps served by one register slot of those pairs
     static_assert(G >= 4 && G <= 32 && (G & (G - 1)) == 0 && G % U == 0, "group of 4..32 lanes");
     __shared__ uint32_t s_cdf[kMaxKmax];
     __shared__ uint32_t s_mpos[NW * NO][kMaxKmax];
@@ -969,26 +974,40 @@ __global__ void __launch_bounds__(kBlock, 3) k_offspring_cont(const __grid_const
     uint32_t *mpos = s_mpos[warp * NO + grp];
     constexpr uint32_t R4 = L / 4;  // 16-byte units per record
 
+    // (A) the draws of offspring wbase + lane and its parents' indices
+    const uint32_t jl = wbase + (uint32_t)lane;
+    const uint4 rl = philox(make_uint4(jl, g, rep, kMate << 24), k0, k1);
+    const uint32_t mom_l = jl < n ? __ldcg(sin + __umulhi(rl.x, S)) : 0u;
+    const uint32_t dad_l = jl < n ? __ldcg(sin + __umulhi(rl.y, S)) : 0u;
+    const int32_t env_l = s_env != 0 ? irwin_hall_step(jl, g, rep, kEnv, 0u, s_env, k0, k1) : 0;
+    // (B) gamete-mask streams: slot q of lane k holds pair 32q + k, i.e. step
+    // (32q + k) / PER_T, group ((32q + k) % PER_T) / NST, stream (32q + k) % NST
+    uint4 dml[NST];
+#pragma unroll
+    for (int q = 0; q < NST; ++q) {
+        const uint32_t pr = 32u * (uint32_t)q + (uint32_t)lane, t = pr / PER_T, rem = pr % PER_T;
+        dml[q] = philox(make_uint4(wbase + t * NO + rem / NST, g, rep, (kRecomb << 24) | (rem % NST)), k0, k1);
+    }
+
     long long sum_raw = 0, sum_raw_s = 0;
     unsigned long long sum_raw2 = 0, cons = 0, lane_allele = 0;
     uint32_t lane_het = 0, alive_bits = 0, nsurv = 0;
     int mn = INT_MAX, mx = INT_MIN;
     for (uint32_t it = 0; it < (uint32_t)(G / U); ++it) {
-        uint32_t jj[U], mom[U], dad[U];
-        uint4 r[U], m0[U], m1[U], f0[U], f1[U];
-        // (A) parents of the group's U offspring; then all their records
+        uint32_t bit[U], rz[U], rw[U];
+        int32_t env[U];
+        uint4 m0[U], m1[U], f0[U], f1[U];
+        // the group's U offspring: parents and draws from their lanes, then all the records
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            jj[u] = wbase + (it * U + (uint32_t)u) * NO + grp;
-            r[u] = philox(make_uint4(jj[u], g, rep, kMate << 24), k0, k1);
-            mom[u] = jj[u] < n ? __ldcg(sin + __umulhi(r[u].x, S)) : 0u;
-            dad[u] = jj[u] < n ? __ldcg(sin + __umulhi(r[u].y, S)) : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
+            bit[u] = (it * U + (uint32_t)u) * NO + grp;
+            const uint32_t mom = __shfl_sync(0xFFFFFFFFu, mom_l, bit[u]), dad = __shfl_sync(0xFFFFFFFFu, dad_l, bit[u]);
+            rz[u] = __shfl_sync(0xFFFFFFFFu, rl.z, bit[u]);
+            rw[u] = __shfl_sync(0xFFFFFFFFu, rl.w, bit[u]);
+            env[u] = __shfl_sync(0xFFFFFFFFu, env_l, bit[u]);
             const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-            const bool ok = jj[u] < n;
-            const uint4 *pm = par + (size_t)mom[u] * R4, *pf = par + (size_t)dad[u] * R4;
+            const bool ok = wbase + bit[u] < n;
+            const uint4 *pm = par + (size_t)mom * R4, *pf = par + (size_t)dad * R4;
             m0[u] = ok ? __ldg(pm + li) : z;
             m1[u] = ok ? __ldg(pm + G + li) : z;
             f0[u] = ok ? __ldg(pf + li) : z;
@@ -996,35 +1015,42 @@ __global__ void __launch_bounds__(kBlock, 3) k_offspring_cont(const __grid_const
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const uint32_t j = jj[u], bit = (it * U + (uint32_t)u) * NO + grp;
+            const uint32_t j = wbase + bit[u], t = it * U + (uint32_t)u;
             const bool ok = j < n;
             // (B) gametes: mask word wv of the mother (stream 2wv) and father (2wv + 1)
-            const uint4 dm = philox(make_uint4(j, g, rep, (kRecomb << 24) | (wv >> 1)), k0, k1);
-            const uint32_t mm = (wv & 1u) ? dm.z : dm.x, mf = (wv & 1u) ? dm.w : dm.y;
+            const uint32_t q = t / T_PER_SLOT;
+            uint4 dsrc = dml[0];
+#pragma unroll
+            for (int qq = 1; qq < NST; ++qq)
+                if (q == (uint32_t)qq) dsrc = dml[qq];
+            const uint32_t src = (t % T_PER_SLOT) * PER_T + grp * NST + (wv >> 1);
+            const uint32_t dx = __shfl_sync(0xFFFFFFFFu, dsrc.x, src), dy = __shfl_sync(0xFFFFFFFFu, dsrc.y, src);
+            const uint32_t dz = __shfl_sync(0xFFFFFFFFu, dsrc.z, src), dw = __shfl_sync(0xFFFFFFFFu, dsrc.w, src);
+            const uint32_t mm = (wv & 1u) ? dz : dx, mf = (wv & 1u) ? dw : dy;
             uint4 c0 = pick8(m0[u], m1[u], (mm >> sh) & 0xFFu), c1 = pick8(f0[u], f1[u], (mf >> sh) & 0xFFu);
             // (B) mutation: the biallelic count and distinct positions, each
             // mutated value moved by an Irwin-Hall step by the lane owning it
-            const uint32_t u_mut = r[u].w;
+            const uint32_t u_mut = rw[u];
             if (ok && kmax != 0u && u_mut >= s_cdf[0]) {  // the same in the whole group
                 uint32_t K = 0;
-                for (uint32_t q = 0; q < kmax; ++q) K += u_mut >= s_cdf[q] ? 1u : 0u;
+                for (uint32_t qk = 0; qk < kmax; ++qk) K += u_mut >= s_cdf[qk] ? 1u : 0u;
                 uint32_t chosen = 0;
                 uint4 dp = make_uint4(0u, 0u, 0u, 0u);
-                for (uint32_t t = 0; t < (uint32_t)kMutDraws && chosen < K; ++t) {
-                    if ((t & 3u) == 0u) dp = philox(make_uint4(j, g, rep, (kMutPos << 24) | (t >> 2)), k0, k1);
-                    const uint32_t pos = __umulhi(lane_of(dp, (int)(t & 3u)), 2u * L);
+                for (uint32_t d = 0; d < (uint32_t)kMutDraws && chosen < K; ++d) {
+                    if ((d & 3u) == 0u) dp = philox(make_uint4(j, g, rep, (kMutPos << 24) | (d >> 2)), k0, k1);
+                    const uint32_t pos = __umulhi(lane_of(dp, (int)(d & 3u)), 2u * L);
                     bool dup = false;
-                    for (uint32_t q = 0; q < chosen; ++q) dup |= mpos[q] == pos;
+                    for (uint32_t qk = 0; qk < chosen; ++qk) dup |= mpos[qk] == pos;
                     if (!dup) {
                         if (li == 0u) mpos[chosen] = pos;
                         __syncwarp(gmask);
                         ++chosen;
                     }
                 }
-                for (uint32_t t = 0; t < chosen; ++t) {
-                    const uint32_t pos = mpos[t], locus = pos >= L ? pos - L : pos;
+                for (uint32_t m = 0; m < chosen; ++m) {
+                    const uint32_t pos = mpos[m], locus = pos >= L ? pos - L : pos;
                     if ((locus >> 3) == li) {
-                        const int32_t step = irwin_hall_step(j, g, rep, kMutSize, 3u * t, s_mut, k0, k1);
+                        const int32_t step = irwin_hall_step(j, g, rep, kMutSize, 3u * m, s_mut, k0, k1);
                         if (pos >= L) add_step(c1, locus & 7u, step);
                         else add_step(c0, locus & 7u, step);
                     }
@@ -1049,20 +1075,19 @@ __global__ void __launch_bounds__(kBlock, 3) k_offspring_cont(const __grid_const
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
             // (C) phenotype: the sum of all values, plus the environmental step
-            int32_t raw = part;
-            if (s_env != 0) raw += irwin_hall_step(j, g, rep, kEnv, 0u, s_env, k0, k1);
+            const int32_t raw = part + env[u];
             // (D) survival
             const long long v = (long long)raw + (long long)bias;
             const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> shift_bin, (long long)(kBins - 1));
             uint32_t thr = __ldg(&P->table[bin]);
             if (f != kCertain) thr = __umulhi(thr, f);
-            const bool alive = (thr == kCertain) || (r[u].z < thr);
+            const bool alive = (thr == kCertain) || (rz[u] < thr);
             if (ok) {
                 lane_het += het;
                 lane_allele += sq;
                 mn = min(mn, raw);
                 mx = max(mx, raw);
-                if (alive) alive_bits |= 1u << bit;
+                if (alive) alive_bits |= 1u << bit[u];
                 if (li == 0u) {  // per-offspring sums once per group
                     sum_raw += raw;
                     sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
