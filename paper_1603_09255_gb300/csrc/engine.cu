@@ -210,12 +210,20 @@ int build_link(const double *map, uint32_t n_loci, LinkParams &lp) {
             lp.cum[l] = 0;
         }
     }
-    // guide[h] = interval of u = h * 2^22: the search for u starts there
-    for (uint32_t h = 0; h < (uint32_t)kLinkGuide; ++h) {
-        const uint32_t u = h << 22;
+    // guide[h]: the interval of the bucket's first uniform, the chromosome ends
+    // for it and the next interval, and the interval boundaries inside the
+    // bucket (none for most buckets: the guide entry is the answer)
+    constexpr uint32_t shift = 32u - (uint32_t)kLinkGuideBits;
+    auto interval = [&](uint32_t u) {
         uint32_t I = 0;
         while (I + 1 < n_loci && lp.cum[I] <= u) ++I;
-        lp.guide[h] = (uint8_t)I;
+        return I;
+    };
+    for (uint32_t h = 0; h < (uint32_t)kLinkGuide; ++h) {
+        const uint32_t lo = h << shift, hi = lo | ((1u << shift) - 1u);
+        const uint32_t I0 = interval(lo), nb = std::min<uint32_t>(interval(hi) - I0, 2u);
+        const uint32_t e0 = lp.last[I0] + 1u, e1 = nb != 0u ? lp.last[I0 + 1u] + 1u : 0u;
+        lp.guide[h] = I0 | (e0 << 8) | (e1 << 17) | (nb << 26);
     }
     return SPG_OK;
 }

@@ -143,7 +143,7 @@ __device__ __forceinline__ void mutate(uint32_t (&c)[2 * W], uint32_t k, uint32_
 struct LinkSmem {
     const uint32_t *cdf, *cum;
     const uint16_t *last, *first, *clast;
-    const uint8_t *guide;
+    const uint32_t *guide;
     uint32_t kmax, nchrom;
 };
 
@@ -181,12 +181,22 @@ __device__ __forceinline__ void linked_mask(const LinkSmem &lk, uint32_t j, uint
     for (uint32_t a = 0; a < K; ++a) {
         if ((a & 3u) == 0u) d = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8) | (1u + a / 4u)), k0, k1);
         const uint32_t u = lane_of(d, (int)(a & 3u));
-        // interval = #{l <= L-2 : cum[l] <= u}: from the guide entry of u's
-        // top 10 bits, forward over the (few) entries inside that range
-        uint32_t I = lk.guide[u >> 22];
-        while (I + 1u < L && lk.cum[I] <= u) ++I;
+        // interval I = #{l <= L-2 : cum[l] <= u} and its chromosome's end + 1:
+        // the guide entry of u's top bits when no boundary lies inside that
+        // bucket, one comparison when one does, a forward search otherwise
+        const uint32_t ge = lk.guide[u >> (32 - kLinkGuideBits)], nb = ge >> 26;
+        uint32_t I = ge & 0xFFu, e = (ge >> 8) & 0x1FFu;
+        if (nb == 1u) {
+            if (lk.cum[I] <= u) {
+                ++I;
+                e = (ge >> 17) & 0x1FFu;
+            }
+        } else if (nb > 1u) {
+            while (I + 1u < L && lk.cum[I] <= u) ++I;
+            e = lk.last[I] + 1u;
+        }
         toggle_bit<W>(t, I);
-        if (lk.last[I] + 1u < L) toggle_bit<W>(t, lk.last[I] + 1u);
+        if (e < L) toggle_bit<W>(t, e);
     }
     uint32_t carry = 0;
 #pragma unroll
@@ -710,7 +720,7 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
     constexpr int LK = LINKED ? 1 : 0;  // linkage-map tables only in the linked variant
     __shared__ uint32_t s_lcdf[LK * kMaxKmax + 1], s_lcum[LK * kMaxLoci + 1];
     __shared__ uint16_t s_llast[LK * kMaxLoci + 1], s_lfirst[LK * kMaxChrom + 1], s_lclast[LK * kMaxChrom + 1];
-    __shared__ uint8_t s_lguide[LK * kLinkGuide + 1];
+    __shared__ uint32_t s_lguide[LK * kLinkGuide + 1];
     LinkSmem lk{s_lcdf, s_lcum, s_llast, s_lfirst, s_lclast, s_lguide, 0u, 0u};
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

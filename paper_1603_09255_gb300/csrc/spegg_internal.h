@@ -25,7 +25,8 @@ constexpr int kMaxLoci = 256;
 constexpr int kMaxChrom = 96;            // chromosomes of a linkage map
 constexpr uint32_t kLinkSites = 65536;   // crossover opportunities per gamete
 constexpr double kMaxMapMorgans = 16.0;  // total length of a linkage map
-constexpr int kLinkGuide = 1024;         // guide-table entries of the crossover interval search
+constexpr int kLinkGuideBits = 12;       // the crossover uniform's top bits that index the guide table
+constexpr int kLinkGuide = 1 << kLinkGuideBits;
 
 // Philox counter word 3 = purpose << 24 | sub
 enum Purpose : uint32_t {
@@ -43,7 +44,11 @@ struct alignas(16) WeightParams {
 struct alignas(16) LinkParams {
     uint32_t cdf[kMaxKmax];      // crossover count per gamete, Binomial(kLinkSites, D / kLinkSites) CDF, Q32
     uint32_t cum[kMaxLoci];      // interval CDF, Q32: crossover interval = #{l <= L-2 : cum[l] <= u}
-    uint8_t guide[kLinkGuide];   // interval of u = h << 22 (search starts there for u >> 22 == h)
+    // bucket h of crossover uniforms (u >> 20 == h): interval I0 of u = h << 20
+    // (bits 0-7), last[I0] + 1 (bits 8-16), last[I0 + 1] + 1 (bits 17-25), and
+    // how many cum[l] (l <= L-2) lie inside the bucket (bits 26-27: 0, 1, or
+    // 2 = two or more)
+    uint32_t guide[kLinkGuide];
     uint16_t last[kMaxLoci];     // last locus of the chromosome holding each locus
     uint16_t first[kMaxChrom];   // first locus of each chromosome
     uint16_t clast[kMaxChrom];   // last locus of each chromosome
