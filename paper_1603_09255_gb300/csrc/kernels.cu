@@ -526,23 +526,45 @@ struct SegCtx {
     bool has_eco;
 };
 
-// One weighted parent (pi = 0 mother, 1 father) by bounded rejection
-// sampling: proposal k draws a uniform survivor rank and an acceptance value
-// (lanes 2(k%2), 2(k%2)+1 of Philox sub pi<<8 | k/2) and is taken when the
+// Weighted parents (pi = 0 mother, 1 father) by bounded rejection sampling:
+// proposal k draws a uniform survivor rank and an acceptance value (lanes
+// 2(k%2), 2(k%2)+1 of Philox sub pi<<8 | k/2) and is taken when the
 // survivor's bin threshold is certain or above the value; the last proposal
-// stands if all kMateAttempts are rejected.
-__device__ __forceinline__ uint32_t weighted_parent(const SegCtx &c, uint32_t j, uint32_t pi) {
-    const uint32_t *acc = c.wt->acc[pi];
-    unsigned long long e = 0;
-    uint4 d = make_uint4(0u, 0u, 0u, 0u);
-    for (uint32_t k = 0; k < kMateAttempts; ++k) {
-        if ((k & 1u) == 0u) d = philox(make_uint4(j, c.g, c.rep, (kMateW << 24) | (pi << 8) | (k >> 1)), c.k0, c.k1);
-        const uint32_t u = (k & 1u) ? d.z : d.x, v = (k & 1u) ? d.w : d.y;
-        e = __ldcg(c.survw + __umulhi(u, c.S));
-        const uint32_t t = __ldg(acc + (uint32_t)(e >> 32));
-        if (t == kCertain || v < t) break;
+// stands if all kMateAttempts are rejected.  Proposals go in pairs (one
+// Philox block), both roles together, so four gathers are in flight at once;
+// the first accepted proposal in order is the parent, as if they were tried
+// one at a time.
+static_assert(kMateAttempts % 2 == 0, "whole Philox blocks of proposals");
+
+// Proposals k and k+1 of one role: whether one was taken, and the parent (the
+// first taken, else proposal k+1).
+__device__ __forceinline__ bool weighted_pair(const uint32_t *acc, const uint4 &d, unsigned long long e0,
+                                              unsigned long long e1, uint32_t &parent) {
+    const uint32_t t0 = __ldg(acc + (uint32_t)(e0 >> 32)), t1 = __ldg(acc + (uint32_t)(e1 >> 32));
+    const bool a0 = t0 == kCertain || d.y < t0, a1 = t1 == kCertain || d.w < t1;
+    parent = a0 ? (uint32_t)e0 : (uint32_t)e1;
+    return a0 || a1;
+}
+
+__device__ __forceinline__ void weighted_parents(const SegCtx &c, uint32_t j, uint32_t &mom, uint32_t &dad) {
+    bool open_m = true, open_f = true;
+    for (uint32_t k = 0; k < kMateAttempts && (open_m || open_f); k += 2) {
+        const uint32_t sub = (kMateW << 24) | (k >> 1);
+        uint4 dm = make_uint4(0u, 0u, 0u, 0u), df = dm;
+        unsigned long long em0 = 0, em1 = 0, ef0 = 0, ef1 = 0;
+        if (open_m) {
+            dm = philox(make_uint4(j, c.g, c.rep, sub), c.k0, c.k1);
+            em0 = __ldcg(c.survw + __umulhi(dm.x, c.S));
+            em1 = __ldcg(c.survw + __umulhi(dm.z, c.S));
+        }
+        if (open_f) {
+            df = philox(make_uint4(j, c.g, c.rep, sub | (1u << 8)), c.k0, c.k1);
+            ef0 = __ldcg(c.survw + __umulhi(df.x, c.S));
+            ef1 = __ldcg(c.survw + __umulhi(df.z, c.S));
+        }
+        if (open_m) open_m = !weighted_pair(c.wt->acc[0], dm, em0, em1, mom);
+        if (open_f) open_f = !weighted_pair(c.wt->acc[1], df, ef0, ef1, dad);
     }
-    return (uint32_t)e;
 }
 
 template <int ITEMS, bool WEIGHTED = false>
@@ -556,8 +578,7 @@ __device__ __forceinline__ void draw_parents(const SegCtx &c, uint32_t base, int
             // survivor indices through L2 only: random 4-byte reads would
             // evict the threshold table from L1
             if constexpr (WEIGHTED) {
-                d.mom[it] = weighted_parent(c, j, 0u);
-                d.dad[it] = weighted_parent(c, j, 1u);
+                weighted_parents(c, j, d.mom[it], d.dad[it]);
             } else {
                 d.mom[it] = __ldcg(c.sin + __umulhi(r.x, c.S));
                 d.dad[it] = __ldcg(c.sin + __umulhi(r.y, c.S));
