@@ -309,7 +309,7 @@ def spatial_community(spegg, torch, steps: int = 200):
            "individuals_first_step": int(st[0]["n_before"].sum()), "individuals_last_step": int(st[-1]["n_after"].sum()),
            "births": births,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "note": f"whole step (7 launches), of {source}"}}
+                        "frac": achieved / peak, "note": f"whole step (8 launches), of {source}"}}
     g.close()
     return out
 

@@ -6,19 +6,21 @@
 // per deme, Fig. S5 B flattening over demes).
 //
 // Layout: all demes d = s*P + p concatenated; a deme stores adults first
-// (age 2, then 1, then 0).  One step is seven launches, none of which waits
+// (age 2, then 1, then 0).  One step is eight launches, none of which waits
 // on another block:
 //   k_sp_plan      one thread per deme: interaction factor f, births B;
 //   k_sp_scan      (x2) one block: exclusive scans of births (newborn
 //                  staging offsets) and of the new deme sizes;
 //   k_sp_classify  one block per deme: survival, ageing and direction of
-//                  every member, newborns formed into staging, and each
+//                  every member, direction of every newborn, and each
 //                  item's stable rank within its (age class, direction)
 //                  class via match/ballot scans;
+//   k_sp_births    grid-stride over all newborns: records formed into
+//                  staging with their phenotypes;
 //   k_sp_totals    one thread per destination deme: offsets of the five
 //                  source slots (stay, from N, S, E, W) per age class;
-//   k_sp_scatter   one block per deme: records and ages to their final
-//                  positions;
+//   k_sp_scatter   one block per deme: records, ages and phenotypes to
+//                  their final positions;
 //   k_sp_finish    one thread: statistics record, step counter.
 #include <cuda_runtime.h>
 
@@ -78,6 +80,7 @@ struct SpaceArgs {
     uint32_t *f, *births, *nb_off;   // [nd], [nd], [nd + 1]
     uint32_t *staging;               // [staging_cap][2W] newborn records
     int32_t *nb_raw;                 // [staging_cap] their phenotypes
+    uint32_t *nb_deme;               // [staging_cap] their demes
     uint8_t *cls, *nb_cls;           // [cap], [staging_cap]
     uint32_t *rank, *nb_rank;        // [cap], [staging_cap]
     uint32_t *cnt;                   // [nd][15] per source deme and (age class, direction)
@@ -308,172 +311,260 @@ __global__ void k_sp_scan(SpaceArgs a, int which) {
     }
 }
 
-// Stable rank of each thread's class within the block's running counters:
-// rank = items of the same class in earlier chunks + in earlier warps of this
-// chunk + in earlier lanes of this warp.
-__device__ __forceinline__ uint32_t block_rank(uint32_t cls, uint32_t *s_run, uint32_t (*s_w)[16], uint32_t *s_tot) {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = kSpBlock / 32;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, cls);
-    const uint32_t in_warp = __popc(peers & ((1u << lane) - 1u));
-    if (threadIdx.x < NW * 16) s_w[threadIdx.x / 16][threadIdx.x % 16] = 0;
-    __syncthreads();
-    if (in_warp == 0) s_w[warp][cls] = __popc(peers);
-    __syncthreads();
-    if (threadIdx.x < 16) {
-        uint32_t run = 0;
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t c = s_w[w][threadIdx.x];
-            s_w[w][threadIdx.x] = run;
-            run += c;
+// Stable ranks of one pass of items, thread t holding items IPT t ..
+// IPT t + IPT - 1 of the pass: rank = items of the same class in earlier
+// passes (s_carry) + in earlier threads of this pass + earlier items of this
+// thread.  The thread's own counts sit in 3-bit fields of one word; the scans
+// over threads use 16-bit fields, two classes per word (classes 2Q0 ..
+// 2Q1-1; a pass holds at most kSpBlock * IPT <= 65535 items); kDead is not
+// counted.
+template <int IPT, int Q0, int Q1>
+__device__ __forceinline__ void class_ranks(const uint32_t (&cls)[IPT], uint32_t (&rk)[IPT], uint32_t *s_carry,
+                                            uint32_t (*s_wt)[8]) {
+    constexpr int NQ = Q1 - Q0, NW = kSpBlock / 32;
+    constexpr uint32_t C0 = 2u * Q0;
+    static_assert(kSpBlock * IPT <= 65535 && Q1 <= 8 && IPT <= 7 && NQ <= 5, "field widths");
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t mine = 0, before[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t c = cls[i], sh = 3u * (c - C0);
+        const bool counted = c < kDead && c >= C0;
+        before[i] = counted ? (mine >> sh) & 7u : 0u;
+        if (counted) mine += 1u << sh;
+    }
+    uint32_t own[NQ], x[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        own[q] = ((mine >> (6 * q)) & 7u) | (((mine >> (6 * q + 3)) & 7u) << 16);
+        x[q] = own[q];
+    }
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int o = 1 << step;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x[q], o);
+            if ((int)lane >= o) x[q] += y;
         }
-        s_tot[threadIdx.x] = run;
+    }
+    if (lane == 31u)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) s_wt[warp][q] = x[q];
+    __syncthreads();
+    // earlier warps' totals: lane q of each warp sums word q, then shares it
+    uint32_t wp = 0;
+    if (lane < (uint32_t)NQ)
+        for (uint32_t v = 0; v < warp; ++v) wp += s_wt[v][lane];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) x[q] += __shfl_sync(0xFFFFFFFFu, wp, q) - own[q];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t c = cls[i];
+        rk[i] = 0;
+        if (c < kDead && c >= C0) {
+            uint32_t sel = x[0];
+#pragma unroll
+            for (int q = 1; q < NQ; ++q)
+                if ((c >> 1) == (uint32_t)(Q0 + q)) sel = x[q];
+            rk[i] = s_carry[c] + ((sel >> ((c & 1u) * 16u)) & 0xFFFFu) + before[i];
+        }
+    }
+    __syncthreads();  // s_carry and s_wt read by every thread
+    if (threadIdx.x < 2u * NQ) {
+        const uint32_t c = C0 + threadIdx.x, q = threadIdx.x >> 1;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) tot += (s_wt[w][q] >> ((c & 1u) * 16u)) & 0xFFFFu;
+        s_carry[c] += tot;
     }
     __syncthreads();
-    const uint32_t r = s_run[cls] + s_w[warp][cls] + in_warp;
-    __syncthreads();
-    if (threadIdx.x < 16) s_run[threadIdx.x] += s_tot[threadIdx.x];
-    __syncthreads();
-    return r;
 }
 
 // ----------------------------------------------- survival and births (A-E)
-template <int W>
+// One block per deme: survival, ageing and direction of every member, the
+// direction of every newborn (its mate and dispersal draws), and each item's
+// stable rank within its (age class, direction) class.  Members (classes
+// 0-9) go kSpIPT consecutive ones per thread, so all their loads are in
+// flight together; newborns (classes 10-14) one per thread.  The newborns'
+// records are formed by k_sp_births.
+constexpr int kSpIPT = 4;
+
 __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
-    __shared__ uint32_t s_run[16];
-    __shared__ uint32_t s_w[kSpBlock / 32][16];
-    __shared__ uint32_t s_tot[16];
-    __shared__ __align__(16) uint32_t s_planes[kMaxPlanes * W];
+    __shared__ uint32_t s_carry[16];
+    __shared__ uint32_t s_wt[kSpBlock / 32][8];
     if (a.state->status != SPG_OK) return;
-    const uint32_t d = blockIdx.x, s = d / a.P, p = d % a.P, tid = threadIdx.x;
+    const uint32_t d = blockIdx.x, s = d / a.P, tid = threadIdx.x;
     const uint32_t t = a.state->t + 1u, par = a.state->t & 1u;
     const SpeciesParams *sp = a.sp + s;
-    sp_stage_planes<W>(sp, s_planes);
-    const uint32_t *geno = a.geno[par];
     const uint8_t *age = a.age[par];
     const int32_t *rawp = a.raw[par];
-    const uint32_t base = a.off[par][d], n = a.off[par][d + 1] - base, m = a.adults[par][d];
+    const uint32_t base = a.off[par][d], n = a.off[par][d + 1] - base;
     const uint32_t f = a.f[d], B = a.births[d], nb0 = a.nb_off[d];
-    if (tid < 16) s_run[tid] = 0;
+    if (tid < 16) s_carry[tid] = 0;
     __syncthreads();
     long long sum_raw = 0;
     uint32_t surv = 0, moved = 0;
-    unsigned long long het = 0, allele = 0;
     // pre-existing members, in rank order
-    for (uint32_t c0 = 0; c0 < n; c0 += kSpBlock) {
-        const uint32_t r = c0 + tid;
-        uint32_t cls = kDead;
-        if (r < n) {
-            // a genotype is fixed for life, so its phenotype was computed once at birth
-            const uint32_t ag = age[base + r];
-            const int32_t raw = rawp[base + r];
-            const uint4 u = sp_philox(make_uint4(r, t, d, kSpSurv << 24), a.key0, a.key1);
-            uint32_t thr = __ldg(&sp->table[ag][sp_bin(sp, raw)]);
-            if (f != kCertain) thr = __umulhi(thr, f);
-            if (thr == kCertain || u.x < thr) {
-                const uint32_t na = ag + 1 > 2 ? 2u : ag + 1;
-                const uint32_t dir = u.y < a.disp_q32 ? 1u + __umulhi(u.z, 4u) : 0u;
-                cls = (2u - na) * 5u + dir;
-                ++surv;
-                sum_raw += raw;
-                moved += dir != 0;
+    for (uint32_t p0 = 0; p0 < n; p0 += kSpBlock * kSpIPT) {
+        const uint32_t r0 = p0 + tid * kSpIPT;
+        uint32_t ag[kSpIPT], cls[kSpIPT], rk[kSpIPT];
+        int32_t raw[kSpIPT];
+        // a genotype is fixed for life, so its phenotype was computed once at birth
+#pragma unroll
+        for (int i = 0; i < kSpIPT; ++i) {
+            ag[i] = r0 + i < n ? age[base + r0 + i] : 0u;
+            raw[i] = r0 + i < n ? rawp[base + r0 + i] : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kSpIPT; ++i) {
+            const uint32_t r = r0 + (uint32_t)i;
+            cls[i] = kDead;
+            if (r < n) {
+                const uint4 u = sp_philox(make_uint4(r, t, d, kSpSurv << 24), a.key0, a.key1);
+                uint32_t thr = __ldg(&sp->table[ag[i]][sp_bin(sp, raw[i])]);
+                if (f != kCertain) thr = __umulhi(thr, f);
+                if (thr == kCertain || u.x < thr) {
+                    const uint32_t na = ag[i] + 1 > 2 ? 2u : ag[i] + 1;
+                    const uint32_t dir = u.y < a.disp_q32 ? 1u + __umulhi(u.z, 4u) : 0u;
+                    cls[i] = (2u - na) * 5u + dir;
+                    ++surv;
+                    sum_raw += raw[i];
+                    moved += dir != 0;
+                }
             }
         }
-        const uint32_t rk = block_rank(cls, s_run, s_w, s_tot);
-        if (r < n) {
-            a.cls[base + r] = (uint8_t)cls;
-            a.rank[base + r] = rk;
-        }
+        class_ranks<kSpIPT, 0, 5>(cls, rk, s_carry, s_wt);
+#pragma unroll
+        for (int i = 0; i < kSpIPT; ++i)
+            if (r0 + i < n) {
+                a.cls[base + r0 + i] = (uint8_t)cls[i];
+                a.rank[base + r0 + i] = rk[i];
+            }
     }
-    // newborns, in birth order (parents among the deme's m adults)
+    // newborns, in birth order: dispersal from the mate draw's third lane,
+    // direction from the dispersal draw
     for (uint32_t c0 = 0; c0 < B; c0 += kSpBlock) {
         const uint32_t k = c0 + tid;
-        uint32_t cls = kDead;
+        uint32_t cls[1] = {kDead}, rk[1];
         const bool fits = nb0 + k < a.staging_cap;
         if (k < B && fits) {
             const uint4 u = sp_philox(make_uint4(k, t, d, kSpMate << 24), a.key0, a.key1);
-            uint32_t mo[2 * W], fa[2 * W], ch[2 * W];
-            sp_load_rec<W>(geno + (size_t)(base + __umulhi(u.x, m)) * 2 * W, mo);
-            sp_load_rec<W>(geno + (size_t)(base + __umulhi(u.y, m)) * 2 * W, fa);
-#pragma unroll
-            for (int q4 = 0; q4 < (2 * W + 3) / 4; ++q4) {
-                const uint4 dm = sp_philox(make_uint4(k, t, d, (kSpRecomb << 24) | (uint32_t)q4), a.key0, a.key1);
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    const int q = 4 * q4 + l;
-                    if (q < 2 * W) {
-                        const int w = q >> 1;
-                        const uint32_t mk = sp_lane(dm, l);
-                        if ((q & 1) == 0) ch[w] = (mo[w] & ~mk) | (mo[W + w] & mk);
-                        else ch[W + w] = (fa[w] & ~mk) | (fa[W + w] & mk);
-                    }
-                }
-            }
-            uint32_t kmut = 0;  // none below the CDF's first entry (the common case)
-            if (sp->kmax != 0u && u.w >= __ldg(&sp->cdf[0]))
-                for (uint32_t i = 0; i < sp->kmax; ++i) kmut += u.w >= __ldg(&sp->cdf[i]) ? 1u : 0u;
-            if (kmut) {
-                uint32_t seen[2 * W];
-#pragma unroll
-                for (int w = 0; w < 2 * W; ++w) seen[w] = 0;
-                uint32_t chosen = 0;
-                for (uint32_t a4 = 0; a4 < kMutDraws / 4 && chosen < kmut; ++a4) {
-                    const uint4 dp = sp_philox(make_uint4(k, t, d, (kSpMutPos << 24) | a4), a.key0, a.key1);
-                    for (int l = 0; l < 4; ++l) {
-                        if (chosen >= kmut) break;
-                        const uint32_t pos = __umulhi(sp_lane(dp, l), 64u * W);
-                        const uint32_t wi = pos >> 5, bit = 1u << (pos & 31u);
-                        bool dup = false;
-#pragma unroll
-                        for (int w = 0; w < 2 * W; ++w)
-                            if ((uint32_t)w == wi) dup = (seen[w] & bit) != 0u;
-                        if (!dup) {
-#pragma unroll
-                            for (int w = 0; w < 2 * W; ++w)
-                                if ((uint32_t)w == wi) {
-                                    seen[w] |= bit;
-                                    ch[w] ^= bit;
-                                }
-                            ++chosen;
-                        }
-                    }
-                }
-            }
-            sp_store_rec<W>(a.staging + (size_t)(nb0 + k) * 2 * W, ch);
-            a.nb_raw[nb0 + k] = sp_phenotype<W>(ch, sp, s_planes);
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                het += __popc(ch[w] ^ ch[W + w]);
-                allele += __popc(ch[w]) + __popc(ch[W + w]);
-            }
-            const uint4 dd = sp_philox(make_uint4(k, t, d, kSpDisp << 24), a.key0, a.key1);
-            const uint32_t dir = u.z < a.disp_q32 ? 1u + __umulhi(dd.x, 4u) : 0u;
-            cls = 2u * 5u + dir;
+            uint32_t dir = 0;
+            if (u.z < a.disp_q32) dir = 1u + __umulhi(sp_philox(make_uint4(k, t, d, kSpDisp << 24), a.key0, a.key1).x, 4u);
+            cls[0] = 2u * 5u + dir;
             moved += dir != 0;
         }
-        const uint32_t rk = block_rank(cls, s_run, s_w, s_tot);
+        class_ranks<1, 5, 8>(cls, rk, s_carry, s_wt);
         if (k < B && fits) {
-            a.nb_cls[nb0 + k] = (uint8_t)cls;
-            a.nb_rank[nb0 + k] = rk;
+            a.nb_cls[nb0 + k] = (uint8_t)cls[0];
+            a.nb_rank[nb0 + k] = rk[0];
+            a.nb_deme[nb0 + k] = d;
         }
     }
-    if (tid < 15) a.cnt[(size_t)d * 15 + tid] = s_run[tid];
+    if (tid < 15) a.cnt[(size_t)d * 15 + tid] = s_carry[tid];
     // statistics
     const uint32_t w_s = __reduce_add_sync(0xFFFFFFFFu, surv), w_m = __reduce_add_sync(0xFFFFFFFFu, moved);
-    unsigned long long w_het = het, w_al = allele;
     long long w_raw = sum_raw;
-    for (int o = 16; o > 0; o >>= 1) {
-        w_het += __shfl_xor_sync(0xFFFFFFFFu, w_het, o);
-        w_al += __shfl_xor_sync(0xFFFFFFFFu, w_al, o);
-        w_raw += __shfl_xor_sync(0xFFFFFFFFu, w_raw, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) w_raw += __shfl_xor_sync(0xFFFFFFFFu, w_raw, o);
     if ((tid & 31) == 0) {
         SpAcc *ac = a.acc + s;
         if (w_s) atomicAdd(&ac->survivors, (unsigned long long)w_s);
         if (w_m) atomicAdd(&ac->movers, (unsigned long long)w_m);
         if (w_raw) atomicAdd(reinterpret_cast<unsigned long long *>(&ac->sum_raw_surv), (unsigned long long)w_raw);
-        if (w_het) atomicAdd(&ac->het_newborn, w_het);
-        if (w_al) atomicAdd(&ac->allele_newborn, w_al);
+    }
+}
+
+// Newborn records (A-C), one thread per newborn over all demes: parents
+// among the deme's m adults, free recombination, mutation, into staging
+// with their phenotypes; heterozygosity and allele counts per species.
+template <int W>
+__global__ void __launch_bounds__(kSpBlock) k_sp_births(SpaceArgs a) {
+    __shared__ __align__(16) uint32_t s_planes[kMaxSpecies][kMaxPlanes * W];
+    if (a.state->status != SPG_OK) return;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t t = a.state->t + 1u, par = a.state->t & 1u;
+    const uint32_t total = min(a.state->births, a.staging_cap);
+    for (uint32_t k = 0; k < a.ns; ++k) sp_stage_planes<W>(a.sp + k, s_planes[k]);
+    __syncthreads();
+    uint32_t het_s[kMaxSpecies] = {0u, 0u, 0u, 0u}, allele_s[kMaxSpecies] = {0u, 0u, 0u, 0u};
+    const uint32_t *geno = a.geno[par];
+    for (uint32_t i = blockIdx.x * kSpBlock + tid; i < total; i += gridDim.x * kSpBlock) {
+        const uint32_t d = a.nb_deme[i], s = d / a.P, k = i - a.nb_off[d];
+        const SpeciesParams *sp = a.sp + s;
+        const uint32_t base = a.off[par][d], m = a.adults[par][d];
+        const uint4 u = sp_philox(make_uint4(k, t, d, kSpMate << 24), a.key0, a.key1);
+        uint32_t mo[2 * W], fa[2 * W], ch[2 * W];
+        sp_load_rec<W>(geno + (size_t)(base + __umulhi(u.x, m)) * 2 * W, mo);
+        sp_load_rec<W>(geno + (size_t)(base + __umulhi(u.y, m)) * 2 * W, fa);
+#pragma unroll
+        for (int q4 = 0; q4 < (2 * W + 3) / 4; ++q4) {
+            const uint4 dm = sp_philox(make_uint4(k, t, d, (kSpRecomb << 24) | (uint32_t)q4), a.key0, a.key1);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int q = 4 * q4 + l;
+                if (q < 2 * W) {
+                    const int w = q >> 1;
+                    const uint32_t mk = sp_lane(dm, l);
+                    if ((q & 1) == 0) ch[w] = (mo[w] & ~mk) | (mo[W + w] & mk);
+                    else ch[W + w] = (fa[w] & ~mk) | (fa[W + w] & mk);
+                }
+            }
+        }
+        uint32_t kmut = 0;  // none below the CDF's first entry (the common case)
+        if (sp->kmax != 0u && u.w >= __ldg(&sp->cdf[0]))
+            for (uint32_t q = 0; q < sp->kmax; ++q) kmut += u.w >= __ldg(&sp->cdf[q]) ? 1u : 0u;
+        if (kmut) {
+            uint32_t seen[2 * W];
+#pragma unroll
+            for (int w = 0; w < 2 * W; ++w) seen[w] = 0;
+            uint32_t chosen = 0;
+            for (uint32_t a4 = 0; a4 < kMutDraws / 4 && chosen < kmut; ++a4) {
+                const uint4 dp = sp_philox(make_uint4(k, t, d, (kSpMutPos << 24) | a4), a.key0, a.key1);
+                for (int l = 0; l < 4; ++l) {
+                    if (chosen >= kmut) break;
+                    const uint32_t pos = __umulhi(sp_lane(dp, l), 64u * W);
+                    const uint32_t wi = pos >> 5, bit = 1u << (pos & 31u);
+                    bool dup = false;
+#pragma unroll
+                    for (int w = 0; w < 2 * W; ++w)
+                        if ((uint32_t)w == wi) dup = (seen[w] & bit) != 0u;
+                    if (!dup) {
+#pragma unroll
+                        for (int w = 0; w < 2 * W; ++w)
+                            if ((uint32_t)w == wi) {
+                                seen[w] |= bit;
+                                ch[w] ^= bit;
+                            }
+                        ++chosen;
+                    }
+                }
+            }
+        }
+        sp_store_rec<W>(a.staging + (size_t)i * 2 * W, ch);
+        a.nb_raw[i] = sp_phenotype<W>(ch, sp, s_planes[s]);
+        uint32_t het = 0, allele = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            het += __popc(ch[w] ^ ch[W + w]);
+            allele += __popc(ch[w]) + __popc(ch[W + w]);
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < kMaxSpecies; ++q)
+            if (q == s) {
+                het_s[q] += het;
+                allele_s[q] += allele;
+            }
+    }
+    // a thread's sums stay below 2^32: at most 2L <= 512 per newborn, and a
+    // thread forms at most staging_cap / (resident threads) < 2^23 newborns
+#pragma unroll
+    for (uint32_t q = 0; q < kMaxSpecies; ++q) {
+        const uint32_t h = __reduce_add_sync(0xFFFFFFFFu, het_s[q]), al = __reduce_add_sync(0xFFFFFFFFu, allele_s[q]);
+        if ((tid & 31) == 0 && (h | al)) {
+            atomicAdd(&a.acc[q].het_newborn, (unsigned long long)h);
+            atomicAdd(&a.acc[q].allele_newborn, (unsigned long long)al);
+        }
     }
 }
 
@@ -518,7 +609,6 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_scatter(SpaceArgs a) {
     const uint32_t d = blockIdx.x, s = d / a.P, p = d % a.P, tid = threadIdx.x;
     const uint32_t par = a.state->t & 1u, npar = par ^ 1u;
     const uint32_t *geno = a.geno[par];
-    const uint8_t *age = a.age[par];
     uint32_t *ngeno = a.geno[npar];
     uint8_t *nage = a.age[npar];
     int32_t *nraw = a.raw[npar];
@@ -596,6 +686,7 @@ using namespace spg;
 
 struct spg_space {
     uint32_t X = 0, Y = 0, P = 0, ns = 0, L = 0, W = 0, nd = 0, cap = 0, staging_cap = 0, ring_cap = 0;
+    uint32_t births_grid = 0;  // resident blocks of k_sp_births
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -619,6 +710,18 @@ int space_state(spg_space *c, SpState &st) {
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "read state");
 }
 
+// Resident blocks of k_sp_births on this device (a grid-stride kernel).
+template <int W>
+int births_grid_for(uint32_t &grid) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sp_births<W>, kSpBlock, 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "newborn kernel occupancy");
+    grid = (uint32_t)std::max(per_sm, 1) * (uint32_t)std::max(sms, 1);
+    return SPG_OK;
+}
+
 template <int W>
 int launch_step(spg_space *c) {
     const SpaceArgs &a = c->args;
@@ -626,7 +729,8 @@ int launch_step(spg_space *c) {
     const uint32_t g = (a.nd + 255) / 256;
     k_sp_plan<<<g, 256, 0, s>>>(a);
     k_sp_scan<<<1, 1024, 0, s>>>(a, 0);
-    k_sp_classify<W><<<a.nd, kSpBlock, 0, s>>>(a);
+    k_sp_classify<<<a.nd, kSpBlock, 0, s>>>(a);
+    k_sp_births<W><<<c->births_grid, kSpBlock, 0, s>>>(a);
     k_sp_totals<<<g, 256, 0, s>>>(a);
     k_sp_scan<<<1, 1024, 0, s>>>(a, 1);
     k_sp_scatter<W><<<a.nd, kSpBlock, 0, s>>>(a);
@@ -711,6 +815,7 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
     const size_t o_g0 = take((size_t)c->cap * 2 * c->W * 4), o_g1 = take((size_t)c->cap * 2 * c->W * 4);
     const size_t o_a0 = take(c->cap), o_a1 = take(c->cap);
     const size_t o_r0 = take((size_t)c->cap * 4), o_r1 = take((size_t)c->cap * 4), o_nr = take((size_t)c->staging_cap * 4);
+    const size_t o_nd = take((size_t)c->staging_cap * 4);
     const size_t o_off0 = take((size_t)(c->nd + 1) * 4), o_off1 = take((size_t)(c->nd + 1) * 4);
     const size_t o_ad0 = take((size_t)c->nd * 4), o_ad1 = take((size_t)c->nd * 4);
     const size_t o_f = take((size_t)c->nd * 4), o_b = take((size_t)c->nd * 4), o_nbo = take((size_t)(c->nd + 1) * 4);
@@ -756,6 +861,7 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
     a.raw[0] = reinterpret_cast<int32_t *>(b + o_r0);
     a.raw[1] = reinterpret_cast<int32_t *>(b + o_r1);
     a.nb_raw = reinterpret_cast<int32_t *>(b + o_nr);
+    a.nb_deme = reinterpret_cast<uint32_t *>(b + o_nd);
     a.off[0] = reinterpret_cast<uint32_t *>(b + o_off0);
     a.off[1] = reinterpret_cast<uint32_t *>(b + o_off1);
     a.adults[0] = reinterpret_cast<uint32_t *>(b + o_ad0);
@@ -795,6 +901,17 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
     if (e != cudaSuccess) {
         spg_space_destroy(c.release());
         return cuda_fail(e, "initialise community");
+    }
+    int rc0;
+    switch (c->W) {
+        case 1: rc0 = births_grid_for<1>(c->births_grid); break;
+        case 2: rc0 = births_grid_for<2>(c->births_grid); break;
+        case 4: rc0 = births_grid_for<4>(c->births_grid); break;
+        default: rc0 = births_grid_for<8>(c->births_grid); break;
+    }
+    if (rc0 != SPG_OK) {
+        spg_space_destroy(c.release());
+        return rc0;
     }
     const uint32_t grid = (run + 127) / 128;
     const uint32_t *dn0 = reinterpret_cast<const uint32_t *>(b + o_n0), *dp0 = reinterpret_cast<const uint32_t *>(b + o_p0);

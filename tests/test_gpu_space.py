@@ -45,6 +45,7 @@ def assert_same(gpu, orc, steps):
     (1, 1, 500, 32, 10, 0.5),
     (2, 1, 80, 128, 8, 0.9),     # neighbours coincide on a 2 x 1 torus
     (1, 3, 50, 32, 8, 1.0),
+    (1, 2, 2600, 64, 5, 0.2),    # demes above 1024 members and 256 births: several scan passes
 ])
 def test_space_matches_oracle(X, Y, n0, L, steps, disp):
     c = S.spatial_community(X=X, Y=Y, n0=n0, n_loci=L, mu=1e-3, disp=disp if disp < 1 else 0.999999, seed=3)
