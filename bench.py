@@ -195,6 +195,18 @@ def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, p
     ms = a.elapsed_time(b)
     sum_n = sum(w.n for w in ws)
     tilings = {str(L): batch.tiling(L) for L in (32, 64, 128)}
+    # per-generation latency of the whole batch: single generations bracketed
+    # by events, after 3 untimed ones
+    batch.step(3)
+    g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(32)]
+    for ga, gb in g_ev:
+        with torch.cuda.stream(stream):
+            ga.record(stream)
+        batch.step(1)
+        with torch.cuda.stream(stream):
+            gb.record(stream)
+    stream.synchronize()
+    gen_ms = [ga.elapsed_time(gb) for ga, gb in g_ev]
     batch.close()
     pops = [spegg.Population.from_workload(ws[i], stats_capacity=64, stream=stream) for i in range(plain_members)]
     for p in pops:
@@ -217,7 +229,9 @@ def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, p
             "value": value, "unit": "individual-generations/s", "ms": ms, "tilings": tilings,
             "plain_value": plain, "plain_sample": f"first {plain_members} replicates, {plain_gens} generations, "
                                                   "one population stepped at a time",
-            "speedup_vs_plain": value / plain}
+            "speedup_vs_plain": value / plain,
+            "per_generation": {"p50_ms": float(np.percentile(gen_ms, 50)), "p99_ms": float(np.percentile(gen_ms, 99)),
+                               "repeats": len(gen_ms), "warmup": 3}}
 
 
 def served_sweep(spegg, torch, count: int = 48, rate: float = 200.0):
@@ -402,7 +416,9 @@ def main():
     achieved = bytes_per_launch / avg_launch_s / 1e9
     traffic = MEASURED_TRAFFIC.get(kernel_source_hash())
 
-    # kernel-only duration: direct launches bracketed by events (untimed pass)
+    # kernel-only duration and per-generation latency: single generations
+    # (direct launches) bracketed by events, after 3 untimed ones
+    pop.step(3)
     k_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
     for a, b in k_ev:
         with torch.cuda.stream(stream):
@@ -411,7 +427,8 @@ def main():
         with torch.cuda.stream(stream):
             b.record(stream)
     stream.synchronize()
-    kernel_ms = statistics.median([a.elapsed_time(b) for a, b in k_ev])
+    gen_us = [a.elapsed_time(b) * 1000.0 for a, b in k_ev]
+    kernel_ms = statistics.median(gen_us) / 1000.0
 
     # end to end through the C ABI with host buffers: restore the population
     # from pinned host memory, run the generations, read the statistics back
@@ -460,6 +477,9 @@ def main():
                 "d2h_bytes_per_step": int(stats.nbytes)},
         "gpu_launches": 2 * launches,
         "clocks": clocks.summary(),
+        "per_generation": {"p50_us": float(np.percentile(gen_us, 50)), "p99_us": float(np.percentile(gen_us, 99)),
+                           "repeats": len(gen_us), "warmup": 3,
+                           "note": "one generation (two launches, no graph) bracketed by CUDA events"},
     }
     if batched is not None:
         line["batched"] = batched

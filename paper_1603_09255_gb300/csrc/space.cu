@@ -9,18 +9,19 @@
 // (age 2, then 1, then 0).  One step is eight launches, none of which waits
 // on another block:
 //   k_sp_plan      one thread per deme: interaction factor f, births B;
-//   k_sp_scan      (x2) one block: exclusive scans of births (newborn
-//                  staging offsets) and of the new deme sizes;
+//   k_sp_scan      (x2) one block: exclusive scans of births (offsets of
+//                  each deme's newborns in the step's newborn arrays) and of
+//                  the new deme sizes;
 //   k_sp_classify  one block per deme: survival, ageing and direction of
 //                  every member, direction of every newborn, and each
 //                  item's stable rank within its (age class, direction)
-//                  class via match/ballot scans;
-//   k_sp_births    grid-stride over all newborns: records formed into
-//                  staging with their phenotypes;
+//                  class by block scans of per-class counts;
 //   k_sp_totals    one thread per destination deme: offsets of the five
 //                  source slots (stay, from N, S, E, W) per age class;
-//   k_sp_scatter   one block per deme: records, ages and phenotypes to
-//                  their final positions;
+//   k_sp_births    grid-stride over all newborns: records formed and
+//                  written with age and phenotype to their final positions;
+//   k_sp_scatter   one block per deme: surviving members' records, ages and
+//                  phenotypes to their final positions;
 //   k_sp_finish    one thread: statistics record, step counter.
 #include <cuda_runtime.h>
 
@@ -78,9 +79,7 @@ struct SpaceArgs {
     uint32_t *off[2];    // [nd + 1]
     uint32_t *adults[2]; // [nd]
     uint32_t *f, *births, *nb_off;   // [nd], [nd], [nd + 1]
-    uint32_t *staging;               // [staging_cap][2W] newborn records
-    int32_t *nb_raw;                 // [staging_cap] their phenotypes
-    uint32_t *nb_deme;               // [staging_cap] their demes
+    uint32_t *nb_deme;               // [staging_cap] demes of the step's newborns
     uint8_t *cls, *nb_cls;           // [cap], [staging_cap]
     uint32_t *rank, *nb_rank;        // [cap], [staging_cap]
     uint32_t *cnt;                   // [nd][15] per source deme and (age class, direction)
@@ -329,7 +328,7 @@ __device__ __forceinline__ void class_ranks(const uint32_t (&cls)[IPT], uint32_t
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         const uint32_t c = cls[i], sh = 3u * (c - C0);
-        const bool counted = c < kDead && c >= C0;
+        const bool counted = c < kDead && c - C0 < 2u * NQ;
         before[i] = counted ? (mine >> sh) & 7u : 0u;
         if (counted) mine += 1u << sh;
     }
@@ -362,7 +361,7 @@ __device__ __forceinline__ void class_ranks(const uint32_t (&cls)[IPT], uint32_t
     for (int i = 0; i < IPT; ++i) {
         const uint32_t c = cls[i];
         rk[i] = 0;
-        if (c < kDead && c >= C0) {
+        if (c < kDead && c - C0 < 2u * NQ) {
             uint32_t sel = x[0];
 #pragma unroll
             for (int q = 1; q < NQ; ++q)
@@ -476,8 +475,10 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
 }
 
 // Newborn records (A-C), one thread per newborn over all demes: parents
-// among the deme's m adults, free recombination, mutation, into staging
-// with their phenotypes; heterozygosity and allele counts per species.
+// among the deme's m adults, free recombination, mutation, written with
+// their age and phenotype straight to their places in the new layout (after
+// k_sp_totals and the second scan); heterozygosity and allele counts per
+// species.
 template <int W>
 __global__ void __launch_bounds__(kSpBlock) k_sp_births(SpaceArgs a) {
     __shared__ __align__(16) uint32_t s_planes[kMaxSpecies][kMaxPlanes * W];
@@ -489,8 +490,11 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_births(SpaceArgs a) {
     __syncthreads();
     uint32_t het_s[kMaxSpecies] = {0u, 0u, 0u, 0u}, allele_s[kMaxSpecies] = {0u, 0u, 0u, 0u};
     const uint32_t *geno = a.geno[par];
+    uint32_t *ngeno = a.geno[par ^ 1u];
+    const uint32_t *noff = a.off[par ^ 1u];
     for (uint32_t i = blockIdx.x * kSpBlock + tid; i < total; i += gridDim.x * kSpBlock) {
         const uint32_t d = a.nb_deme[i], s = d / a.P, k = i - a.nb_off[d];
+        const uint32_t dir = a.nb_cls[i] % 5u, rk = a.nb_rank[i];  // class 10 + dir: age 0
         const SpeciesParams *sp = a.sp + s;
         const uint32_t base = a.off[par][d], m = a.adults[par][d];
         const uint4 u = sp_philox(make_uint4(k, t, d, kSpMate << 24), a.key0, a.key1);
@@ -541,8 +545,13 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_births(SpaceArgs a) {
                 }
             }
         }
-        sp_store_rec<W>(a.staging + (size_t)i * 2 * W, ch);
-        a.nb_raw[i] = sp_phenotype<W>(ch, sp, s_planes[s]);
+        const uint32_t q = s * a.P + sp_dest(a, d % a.P, dir);
+        const uint32_t pos = noff[q] + a.slotoff[(size_t)q * 15 + 2u * 5u + sp_slot(dir)] + rk;
+        if (pos < a.cap) {
+            sp_store_rec<W>(ngeno + (size_t)pos * 2 * W, ch);
+            a.age[par ^ 1u][pos] = 0;
+            a.raw[par ^ 1u][pos] = sp_phenotype<W>(ch, sp, s_planes[s]);
+        }
         uint32_t het = 0, allele = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -614,24 +623,10 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_scatter(SpaceArgs a) {
     int32_t *nraw = a.raw[npar];
     const uint32_t *noff = a.off[npar];
     const uint32_t base = a.off[par][d], n = a.off[par][d + 1] - base;
-    const uint32_t B = a.births[d], nb0 = a.nb_off[d];
-    for (uint32_t i = tid; i < n + B; i += kSpBlock) {
-        uint32_t cls, rk;
-        const uint32_t *src;
-        const int32_t *src_raw;
-        if (i < n) {
-            cls = a.cls[base + i];
-            rk = a.rank[base + i];
-            src = geno + (size_t)(base + i) * 2 * W;
-            src_raw = a.raw[par] + base + i;
-        } else {
-            const uint32_t k = i - n;
-            if (nb0 + k >= a.staging_cap) continue;
-            cls = a.nb_cls[nb0 + k];
-            rk = a.nb_rank[nb0 + k];
-            src = a.staging + (size_t)(nb0 + k) * 2 * W;
-            src_raw = a.nb_raw + nb0 + k;
-        }
+    for (uint32_t i = tid; i < n; i += kSpBlock) {
+        const uint32_t cls = a.cls[base + i], rk = a.rank[base + i];
+        const uint32_t *src = geno + (size_t)(base + i) * 2 * W;
+        const int32_t *src_raw = a.raw[par] + base + i;
         if (cls >= kDead) continue;
         const uint32_t ci = cls / 5u, dir = cls % 5u;
         const uint32_t q = s * a.P + sp_dest(a, p, dir);
@@ -730,9 +725,9 @@ int launch_step(spg_space *c) {
     k_sp_plan<<<g, 256, 0, s>>>(a);
     k_sp_scan<<<1, 1024, 0, s>>>(a, 0);
     k_sp_classify<<<a.nd, kSpBlock, 0, s>>>(a);
-    k_sp_births<W><<<c->births_grid, kSpBlock, 0, s>>>(a);
     k_sp_totals<<<g, 256, 0, s>>>(a);
     k_sp_scan<<<1, 1024, 0, s>>>(a, 1);
+    k_sp_births<W><<<c->births_grid, kSpBlock, 0, s>>>(a);
     k_sp_scatter<W><<<a.nd, kSpBlock, 0, s>>>(a);
     k_sp_finish<<<1, 32, 0, s>>>(a);
     const cudaError_t e = cudaGetLastError();
@@ -814,12 +809,11 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
     const size_t o_sp = take(sizeof(SpeciesParams) * c->ns);
     const size_t o_g0 = take((size_t)c->cap * 2 * c->W * 4), o_g1 = take((size_t)c->cap * 2 * c->W * 4);
     const size_t o_a0 = take(c->cap), o_a1 = take(c->cap);
-    const size_t o_r0 = take((size_t)c->cap * 4), o_r1 = take((size_t)c->cap * 4), o_nr = take((size_t)c->staging_cap * 4);
+    const size_t o_r0 = take((size_t)c->cap * 4), o_r1 = take((size_t)c->cap * 4);
     const size_t o_nd = take((size_t)c->staging_cap * 4);
     const size_t o_off0 = take((size_t)(c->nd + 1) * 4), o_off1 = take((size_t)(c->nd + 1) * 4);
     const size_t o_ad0 = take((size_t)c->nd * 4), o_ad1 = take((size_t)c->nd * 4);
     const size_t o_f = take((size_t)c->nd * 4), o_b = take((size_t)c->nd * 4), o_nbo = take((size_t)(c->nd + 1) * 4);
-    const size_t o_stg = take((size_t)c->staging_cap * 2 * c->W * 4);
     const size_t o_cls = take(c->cap), o_ncls = take(c->staging_cap);
     const size_t o_rk = take((size_t)c->cap * 4), o_nrk = take((size_t)c->staging_cap * 4);
     const size_t o_cnt = take((size_t)c->nd * 15 * 4), o_so = take((size_t)c->nd * 15 * 4), o_nn = take((size_t)c->nd * 4);
@@ -860,7 +854,6 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
     a.age[1] = reinterpret_cast<uint8_t *>(b + o_a1);
     a.raw[0] = reinterpret_cast<int32_t *>(b + o_r0);
     a.raw[1] = reinterpret_cast<int32_t *>(b + o_r1);
-    a.nb_raw = reinterpret_cast<int32_t *>(b + o_nr);
     a.nb_deme = reinterpret_cast<uint32_t *>(b + o_nd);
     a.off[0] = reinterpret_cast<uint32_t *>(b + o_off0);
     a.off[1] = reinterpret_cast<uint32_t *>(b + o_off1);
@@ -869,7 +862,6 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
     a.f = reinterpret_cast<uint32_t *>(b + o_f);
     a.births = reinterpret_cast<uint32_t *>(b + o_b);
     a.nb_off = reinterpret_cast<uint32_t *>(b + o_nbo);
-    a.staging = reinterpret_cast<uint32_t *>(b + o_stg);
     a.cls = reinterpret_cast<uint8_t *>(b + o_cls);
     a.nb_cls = reinterpret_cast<uint8_t *>(b + o_ncls);
     a.rank = reinterpret_cast<uint32_t *>(b + o_rk);
