@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -67,7 +68,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"spegg_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -224,12 +225,18 @@ def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, p
     for p in pops:
         p.close()
     value = sum_n * gens / (ms / 1e3)
+    # algorithmic bytes of one generation of every replicate: sum of N (12 + 24W)
+    algo = sum(w.n * algorithmic_bytes(w.words) for w in ws) * gens
+    peak, source = load_peaks()
+    achieved = algo / (ms / 1e3) / 1e9
     return {"workload": f"4096 replicates, N log-uniform [1e3, 2e5] (sum {sum_n}), L in {{32, 64, 128}}, "
                         f"s in [0, 0.5], {gens} generations timed after {ran + 32}",
             "value": value, "unit": "individual-generations/s", "ms": ms, "tilings": tilings,
             "plain_value": plain, "plain_sample": f"first {plain_members} replicates, {plain_gens} generations, "
                                                   "one population stepped at a time",
             "speedup_vs_plain": value / plain,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "note": f"sum of N (12 + 24W) B per generation, of {source}"},
             "per_generation": {"p50_ms": float(np.percentile(gen_ms, 50)), "p99_ms": float(np.percentile(gen_ms, 99)),
                                "repeats": len(gen_ms), "warmup": 3}}
 
