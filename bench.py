@@ -183,7 +183,7 @@ def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, p
     ws = S.batch_replicates(count=4096, n_gen=gens)
     stream = torch.cuda.Stream()
     batch = spegg.Batch(ws, stats_capacity=gens + 64, stream=stream)
-    ran = batch.autotune(2)
+    ran = batch.autotune(4)
     batch.step(32)
     batch.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

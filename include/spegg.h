@@ -284,10 +284,11 @@ int spg_batch_step(spg_batch *batch, uint32_t n_gen);
 /* Offspring per thread for the members with n_loci loci (as spg_set_tiling). */
 int spg_batch_set_tiling(spg_batch *batch, uint32_t n_loci, uint32_t items_per_thread);
 int spg_batch_get_tiling(spg_batch *batch, uint32_t n_loci, uint32_t *items_per_thread);
-/* Launch-shape autotuner: for each locus-count group, times gens_per_trial
- * real generations with each of three tilings and keeps the fastest.  Every
- * member advances by the same number of generations (*gens_run = 3 *
- * gens_per_trial); results do not depend on the tilings chosen. */
+/* Launch-shape autotuner: for each locus-count group, runs one untimed
+ * generation and then times gens_per_trial real generations with each of
+ * three tilings, and keeps the fastest.  Every member advances by the same
+ * number of generations (*gens_run = 3 * (gens_per_trial + 1)); results do
+ * not depend on the tilings chosen. */
 int spg_batch_autotune(spg_batch *batch, uint32_t gens_per_trial, uint32_t *gens_run);
 int spg_batch_read_stats(spg_batch *batch, uint32_t member, uint32_t first_gen, uint32_t count, spg_stats *out);
 int spg_batch_read_genotypes(spg_batch *batch, uint32_t member, uint32_t *host, size_t n_words);

@@ -267,7 +267,9 @@ int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, uint32_t *gens_run
         return fail(SPG_ERR_CUDA, "cudaEventCreate");
     static const uint32_t kCandidates[3] = {1, 2, 4};
     int rc = SPG_OK;
-    // every group runs three trials, so all members advance equally
+    // every group runs three trials, each one untimed generation (the new
+    // tiling's first launches) then gens_per_trial timed ones, so all members
+    // advance equally
     for (Group &g : b->groups) {
         if (g.members.empty()) continue;
         float best_ms = 0.f;
@@ -276,6 +278,7 @@ int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, uint32_t *gens_run
             uint32_t items = kCandidates[c];
             if (!supported_items(g.words, items)) items = 2;
             rc = configure_group(b, g, items);
+            if (rc == SPG_OK) rc = launch_generation(g.gl, b->stream);
             if (rc != SPG_OK) break;
             cudaEventRecord(t0, b->stream);
             for (uint32_t i = 0; i < gens_per_trial && rc == SPG_OK; ++i) rc = launch_generation(g.gl, b->stream);
@@ -292,7 +295,7 @@ int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, uint32_t *gens_run
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    if (rc == SPG_OK && gens_run) *gens_run = 3 * gens_per_trial;
+    if (rc == SPG_OK && gens_run) *gens_run = 3 * (gens_per_trial + 1);
     return rc;
 }
 
