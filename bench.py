@@ -175,7 +175,8 @@ def bench_config(w, l2):
             "n": w.n, "n_loci": w.n_loci, "generations_per_step": GENERATIONS, "l2": l2}
 
 
-def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, plain_gens: int = 32):
+def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, plain_gens: int = 32,
+                       oracle_cpu: bool = False):
     """Batched-replicates workload: 4,096 independent single-species runs (N
     log-uniform in [1e3, 2e5], L in {32, 64, 128}, s in [0, 0.5]) advanced by
     shared, graph-captured launches with autotuned tilings, against the plain
@@ -238,7 +239,8 @@ def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, p
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "note": f"sum of N (12 + 24W) B per generation, of {source}"},
             "per_generation": {"p50_ms": float(np.percentile(gen_ms, 50)), "p99_ms": float(np.percentile(gen_ms, 99)),
-                               "repeats": len(gen_ms), "warmup": 3}}
+                               "repeats": len(gen_ms), "warmup": 3},
+            "cpu_baseline": oracle_batched_baseline(ws) if oracle_cpu else None}
 
 
 def served_sweep(spegg, torch, count: int = 48, rate: float = 200.0):
@@ -297,7 +299,7 @@ def variant_population(spegg, torch, w, label: str, gens: int = 256, bytes_per_o
     return out
 
 
-def spatial_community(spegg, torch, steps: int = 200):
+def spatial_community(spegg, torch, steps: int = 200, oracle_cpu: bool = False):
     """Three-species community on a 64 x 64 torus, 814 founders per species
     and patch (1.0e7 individuals), L = 256, age classes 0/1/2, dispersal 0.05,
     200 steps; throughput in individual-steps per second."""
@@ -330,9 +332,54 @@ def spatial_community(spegg, torch, steps: int = 200):
            "individuals_first_step": int(st[0]["n_before"].sum()), "individuals_last_step": int(st[-1]["n_after"].sum()),
            "births": births,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "note": f"whole step (8 launches), of {source}"}}
+                        "frac": achieved / peak, "note": f"whole step (8 launches), of {source}"},
+           "cpu_baseline": oracle_spatial_baseline() if oracle_cpu else None}
     g.close()
     return out
+
+
+def _oracle_generations(job):
+    """Pool worker: one workload on the oracle; (individual-generations, seconds
+    of its generation steps)."""
+    w, gens = job
+    import oracle
+    pop = oracle.OraclePopulation.from_workload(w)
+    t0 = time.perf_counter()
+    pop.step(gens)
+    return w.n * gens, time.perf_counter() - t0
+
+
+def oracle_batched_baseline(ws, members: int = 64, gens: int = 2):
+    """The oracle on the first `members` replicates, one process per core
+    (spawned: safe after CUDA initialisation); the value is the summed
+    per-process step rate."""
+    import multiprocessing as mp
+    sample = ws[:members]
+    cores = max(1, min(len(sample), os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_generations, [(w, gens) for w in sample], chunksize=1)
+    ind = sum(r[0] for r in res)
+    busy = sum(r[1] for r in res)
+    return {"value": ind / busy * cores, "unit": "individual-generations/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {members} replicates ({sum(w.n for w in sample)} individuals), {gens} generations "
+                      f"each, {cores} processes; value = individual-generations / step seconds x processes"}
+
+
+def oracle_spatial_baseline(X: int = 8, Y: int = 8, steps: int = 4):
+    """The oracle on an X x Y torus with the measured community's per-patch
+    density, single thread."""
+    import oracle
+    c = S.spatial_community(X=X, Y=Y)
+    sp = oracle.OracleSpace(c)
+    sp.step(1)
+    t0 = time.perf_counter()
+    st = sp.step(steps)
+    dt = time.perf_counter() - t0
+    ind = int(st["n_before"].sum())
+    sp.close()
+    return {"value": ind / dt, "unit": "individual-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{X} x {Y} torus, same species and per-patch density ({ind // steps} individuals), "
+                      f"{steps} steps after 1, single thread, {dt:.1f} s"}
 
 
 def cpu_baseline(workload, target_seconds=12.0):
@@ -454,9 +501,10 @@ def main():
     e2e_value = workload.n * GENERATIONS * ws / (sum(e2e_times) / len(e2e_times))
     assert len(stats) == GENERATIONS
 
-    batched = None if args.no_batched else batched_replicates(spegg, torch)
+    oracle_cpu = rank == 0 and not args.no_cpu_baseline
+    batched = None if args.no_batched else batched_replicates(spegg, torch, oracle_cpu=oracle_cpu)
     served = None if args.no_served else served_sweep(spegg, torch)
-    spatial = None if args.no_spatial else spatial_community(spegg, torch)
+    spatial = None if args.no_spatial else spatial_community(spegg, torch, oracle_cpu=oracle_cpu)
     linked = None if args.no_linked else variant_population(
         spegg, torch, S.with_linkage(S.consumer_resource(), 4, 1.0), "linkage map 4 chromosomes x 1 Morgan")
     weighted = None if args.no_weighted else variant_population(
