@@ -252,7 +252,7 @@ __device__ __forceinline__ int32_t phenotype(const uint32_t (&c)[2 * W], const u
         hz += __popc(c[w] ^ c[W + w]);
     }
     int32_t raw = e_min * (int32_t)total;
-#pragma unroll 2
+#pragma unroll 4
     for (uint32_t b = 0; b < nplanes; ++b) {
         uint32_t pl[W];
         plane_words<W>(s_planes, b, pl);
