@@ -198,7 +198,7 @@ int build_link(const double *map, uint32_t n_loci, LinkParams &lp) {
     lp.nchrom = chrom + 1;
     if (!(D <= kMaxMapMorgans)) return fail(SPG_ERR_INVALID, "the linkage map is longer than 16 Morgans");
     for (uint32_t c = 0; c < lp.nchrom; ++c)
-        for (uint32_t l = lp.first[c]; l <= lp.clast[c]; ++l) lp.last[l] = lp.clast[c];
+        for (uint32_t l = lp.first[c]; l <= lp.clast[c]; ++l) lp.chrom[l] = (uint8_t)c;
     lp.kmax = mutation_cdf(D / (double)kLinkSites, kLinkSites, lp.cdf);
     double run = 0.0;
     for (uint32_t l = 0; l < n_loci; ++l) {
@@ -210,8 +210,8 @@ int build_link(const double *map, uint32_t n_loci, LinkParams &lp) {
             lp.cum[l] = 0;
         }
     }
-    // guide[h]: the interval of the bucket's first uniform, the chromosome ends
-    // for it and the next interval, and the interval boundaries inside the
+    // guide[h]: the interval of the bucket's first uniform, the chromosomes of
+    // it and of the next interval, and the interval boundaries inside the
     // bucket (none for most buckets: the guide entry is the answer)
     constexpr uint32_t shift = 32u - (uint32_t)kLinkGuideBits;
     auto interval = [&](uint32_t u) {
@@ -222,8 +222,8 @@ int build_link(const double *map, uint32_t n_loci, LinkParams &lp) {
     for (uint32_t h = 0; h < (uint32_t)kLinkGuide; ++h) {
         const uint32_t lo = h << shift, hi = lo | ((1u << shift) - 1u);
         const uint32_t I0 = interval(lo), nb = std::min<uint32_t>(interval(hi) - I0, 2u);
-        const uint32_t e0 = lp.last[I0] + 1u, e1 = nb != 0u ? lp.last[I0 + 1u] + 1u : 0u;
-        lp.guide[h] = I0 | (e0 << 8) | (e1 << 17) | (nb << 26);
+        const uint32_t c0 = lp.chrom[I0], c1 = nb != 0u ? lp.chrom[I0 + 1u] : 0u;
+        lp.guide[h] = I0 | (c0 << 8) | (c1 << 15) | (nb << 26);
     }
     return SPG_OK;
 }

@@ -142,7 +142,8 @@ __device__ __forceinline__ void mutate(uint32_t (&c)[2 * W], uint32_t k, uint32_
 // Linkage map in shared memory (see LinkParams) for one population.
 struct LinkSmem {
     const uint32_t *cdf, *cum;
-    const uint16_t *last, *first, *clast;
+    const uint8_t *chrom;
+    const uint16_t *first, *clast;
     const uint32_t *guide;
     uint32_t kmax, nchrom;
 };
@@ -157,8 +158,11 @@ __device__ __forceinline__ void toggle_bit(uint32_t (&t)[W], uint32_t pos) {
 // Origin mask of one gamete under the linkage map (bit set: the locus comes
 // from the parent's haplotype 1): every chromosome whose coin is 1 and every
 // crossover flips the loci from its start to the chromosome's end.  Each
-// flip is two toggles (at the first flipped locus and one past the last);
-// a prefix XOR over the L bits turns the toggles into the mask.
+// flip is two toggles (at the first flipped locus and one past the last); a
+// crossover toggles its start and flips its chromosome's parity bit, and the
+// end toggles, which cancel in pairs, are applied once per chromosome whose
+// coin and parity differ.  A prefix XOR over the L bits turns the toggles
+// into the mask.
 template <int W>
 __device__ __forceinline__ void linked_mask(const LinkSmem &lk, uint32_t j, uint32_t g, uint32_t rep, uint32_t pi,
                                             uint32_t k0, uint32_t k1, uint32_t (&m)[W]) {
@@ -167,13 +171,7 @@ __device__ __forceinline__ void linked_mask(const LinkSmem &lk, uint32_t j, uint
     uint32_t t[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) t[w] = 0u;
-    for (uint32_t c = 0; c < lk.nchrom; ++c) {
-        const uint32_t coins = c < 32u ? d0.y : c < 64u ? d0.z : d0.w;
-        if ((coins >> (c & 31u)) & 1u) {
-            toggle_bit<W>(t, lk.first[c]);
-            if (lk.clast[c] + 1u < L) toggle_bit<W>(t, lk.clast[c] + 1u);
-        }
-    }
+    uint32_t par0 = 0, par1 = 0, par2 = 0;  // crossovers per chromosome, mod 2 (chromosomes 0-31, 32-63, 64-95)
     uint32_t K = 0;
     if (lk.kmax != 0u && d0.x >= lk.cdf[0])
         for (uint32_t i = 0; i < lk.kmax; ++i) K += d0.x >= lk.cdf[i] ? 1u : 0u;
@@ -181,22 +179,31 @@ __device__ __forceinline__ void linked_mask(const LinkSmem &lk, uint32_t j, uint
     for (uint32_t a = 0; a < K; ++a) {
         if ((a & 3u) == 0u) d = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8) | (1u + a / 4u)), k0, k1);
         const uint32_t u = lane_of(d, (int)(a & 3u));
-        // interval I = #{l <= L-2 : cum[l] <= u} and its chromosome's end + 1:
-        // the guide entry of u's top bits when no boundary lies inside that
-        // bucket, one comparison when one does, a forward search otherwise
+        // interval I = #{l <= L-2 : cum[l] <= u} and its chromosome: the guide
+        // entry of u's top bits when no boundary lies inside that bucket, one
+        // comparison when one does, a forward search otherwise
         const uint32_t ge = lk.guide[u >> (32 - kLinkGuideBits)], nb = ge >> 26;
-        uint32_t I = ge & 0xFFu, e = (ge >> 8) & 0x1FFu;
+        uint32_t I = ge & 0xFFu, ch = (ge >> 8) & 0x7Fu;
         if (nb == 1u) {
             if (lk.cum[I] <= u) {
                 ++I;
-                e = (ge >> 17) & 0x1FFu;
+                ch = (ge >> 15) & 0x7Fu;
             }
         } else if (nb > 1u) {
             while (I + 1u < L && lk.cum[I] <= u) ++I;
-            e = lk.last[I] + 1u;
+            ch = lk.chrom[I];
         }
         toggle_bit<W>(t, I);
-        if (e < L) toggle_bit<W>(t, e);
+        const uint32_t cb = 1u << (ch & 31u);
+        par0 ^= ch < 32u ? cb : 0u;
+        par1 ^= (ch >= 32u && ch < 64u) ? cb : 0u;
+        par2 ^= ch >= 64u ? cb : 0u;
+    }
+    for (uint32_t c = 0; c < lk.nchrom; ++c) {
+        const uint32_t coin = ((c < 32u ? d0.y : c < 64u ? d0.z : d0.w) >> (c & 31u)) & 1u;
+        const uint32_t par = ((c < 32u ? par0 : c < 64u ? par1 : par2) >> (c & 31u)) & 1u;
+        if (coin) toggle_bit<W>(t, lk.first[c]);
+        if ((coin ^ par) && lk.clast[c] + 1u < L) toggle_bit<W>(t, lk.clast[c] + 1u);
     }
     uint32_t carry = 0;
 #pragma unroll
@@ -696,8 +703,8 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
 
             // (C) phenotype, (D) survival
             uint32_t allele, hz;
-            const int32_t raw = phenotype<W>(ch, s_planes, c.nplanes, c.e_min, allele, hz) +
-                                dominance_part<W>(ch, s_dplanes, c.ndplanes, c.d_min, hz);
+            int32_t raw = phenotype<W>(ch, s_planes, c.nplanes, c.e_min, allele, hz);
+            raw += dominance_part<W>(ch, s_dplanes, c.ndplanes, c.d_min, hz);  // hz is set by the line above
             const long long v = (long long)raw + (long long)c.bias;
             const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> c.shift, (long long)(kBins - 1));
             if constexpr (WEIGHTED) c.obin[j] = (uint16_t)bin;
@@ -740,9 +747,10 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
     __shared__ int s_mm[2][NW];
     constexpr int LK = LINKED ? 1 : 0;  // linkage-map tables only in the linked variant
     __shared__ uint32_t s_lcdf[LK * kMaxKmax + 1], s_lcum[LK * kMaxLoci + 1];
-    __shared__ uint16_t s_llast[LK * kMaxLoci + 1], s_lfirst[LK * kMaxChrom + 1], s_lclast[LK * kMaxChrom + 1];
+    __shared__ uint8_t s_lchrom[LK * kMaxLoci + 1];
+    __shared__ uint16_t s_lfirst[LK * kMaxChrom + 1], s_lclast[LK * kMaxChrom + 1];
     __shared__ uint32_t s_lguide[LK * kLinkGuide + 1];
-    LinkSmem lk{s_lcdf, s_lcum, s_llast, s_lfirst, s_lclast, s_lguide, 0u, 0u};
+    LinkSmem lk{s_lcdf, s_lcum, s_lchrom, s_lfirst, s_lclast, s_lguide, 0u, 0u};
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(s_dyn);
@@ -794,7 +802,7 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
                 lk.nchrom = lp->nchrom;
                 for (uint32_t i = tid; i < 32u * W; i += kBlock) {
                     s_lcum[i] = lp->cum[i];
-                    s_llast[i] = lp->last[i];
+                    s_lchrom[i] = lp->chrom[i];
                 }
                 if (tid < kMaxKmax) s_lcdf[tid] = lp->cdf[tid];
                 for (uint32_t i = tid; i < (uint32_t)kLinkGuide; i += kBlock) s_lguide[i] = lp->guide[i];

@@ -45,11 +45,11 @@ struct alignas(16) LinkParams {
     uint32_t cdf[kMaxKmax];      // crossover count per gamete, Binomial(kLinkSites, D / kLinkSites) CDF, Q32
     uint32_t cum[kMaxLoci];      // interval CDF, Q32: crossover interval = #{l <= L-2 : cum[l] <= u}
     // bucket h of crossover uniforms (u >> 20 == h): interval I0 of u = h << 20
-    // (bits 0-7), last[I0] + 1 (bits 8-16), last[I0 + 1] + 1 (bits 17-25), and
-    // how many cum[l] (l <= L-2) lie inside the bucket (bits 26-27: 0, 1, or
-    // 2 = two or more)
+    // (bits 0-7), chrom[I0] (bits 8-14), chrom[I0 + 1] (bits 15-21), and how
+    // many cum[l] (l <= L-2) lie inside the bucket (bits 26-27: 0, 1, or 2 =
+    // two or more)
     uint32_t guide[kLinkGuide];
-    uint16_t last[kMaxLoci];     // last locus of the chromosome holding each locus
+    uint8_t chrom[kMaxLoci];     // chromosome holding each locus
     uint16_t first[kMaxChrom];   // first locus of each chromosome
     uint16_t clast[kMaxChrom];   // last locus of each chromosome
     uint32_t kmax;               // entries of cdf
