@@ -173,8 +173,12 @@ __device__ __forceinline__ void linked_mask(const LinkSmem &lk, uint32_t j, uint
     for (int w = 0; w < W; ++w) t[w] = 0u;
     uint32_t par0 = 0, par1 = 0, par2 = 0;  // crossovers per chromosome, mod 2 (chromosomes 0-31, 32-63, 64-95)
     uint32_t K = 0;
-    if (lk.kmax != 0u && d0.x >= lk.cdf[0])
-        for (uint32_t i = 0; i < lk.kmax; ++i) K += d0.x >= lk.cdf[i] ? 1u : 0u;
+    if (lk.kmax != 0u && d0.x >= lk.cdf[0]) {  // K = #{i < kmax : cdf[i] <= u} by bisection (the CDF is non-decreasing)
+        K = 1u;
+#pragma unroll
+        for (uint32_t step = 16u; step > 0u; step >>= 1)
+            if (K + step <= lk.kmax && lk.cdf[K + step - 1u] <= d0.x) K += step;
+    }
     uint4 d = d0;
     for (uint32_t a = 0; a < K; ++a) {
         if ((a & 3u) == 0u) d = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8) | (1u + a / 4u)), k0, k1);
