@@ -104,3 +104,11 @@ def test_continuous_validation_through_the_abi():
         sp.Population.from_workload(dataclasses.replace(w, mut_sd=100.0))
     with pytest.raises(sp.SpeggError):
         sp.Batch([w])
+
+
+def test_continuous_full_size_two_generations():
+    """The measured continuous-allele configuration (N = 10^6, L = 128,
+    mu 1e-3, mutation sd 0.05, environmental sd 0.2) for two generations."""
+    w = S.continuous_trait(n=1_000_000, n_loci=128, mu=1e-3, mut_sd=0.05, env_sd=0.2)
+    orc, gpu, so, sg = run_both(w, 2)
+    assert_identical(orc, gpu, so, sg)

@@ -96,3 +96,11 @@ def test_dominance_in_a_batch():
         for name in so.dtype.names:
             assert np.array_equal(so[name], sg[name]), (i, name)
         assert np.array_equal(orc.genotypes(), batch.genotypes(i))
+
+
+def test_dominance_full_size_two_generations():
+    """The measured dominance configuration (consumer-resource population,
+    N = 10^6, L = 128, deviations Q8(N(0, 0.1))) for two generations."""
+    w = S.with_dominance(S.consumer_resource())
+    orc, gpu, so, sg = run_both(w, 2)
+    assert_identical(orc, gpu, so, sg)

@@ -81,3 +81,45 @@ def test_space_capacity_overflow_is_reported():
     st = gpu.state()
     assert st["status"] == sp().ERR_RANGE and st["t"] < 5
     assert gpu.sizes().sum() <= 1500
+
+
+def _popcount(words: np.ndarray) -> int:
+    return int(np.unpackbits(np.ascontiguousarray(words).view(np.uint8)).sum())
+
+
+def test_space_full_size_counts_and_newborns():
+    """The measured community (64 x 64 torus, 3 species, 814 founders per
+    species and patch, L = 256) after three steps, checked on every deme
+    against properties that hold at any size: counts are conserved from step
+    to step, every deme stores adults first, and the last step's newborns --
+    exactly the age-0 individuals -- agree with its birth, adult,
+    heterozygosity and allele-count statistics."""
+    c = S.spatial_community()
+    g = sp().Space(c, stats_capacity=16)
+    g.step(3)
+    state = g.state()
+    assert state["status"] == 0 and state["t"] == 3
+    st = g.read_stats(1, 3)
+    assert np.array_equal(st["n_after"], st["survivors"] + st["births"])
+    assert np.array_equal(st["n_before"][1:], st["n_after"][:-1])
+    sizes = g.sizes()
+    assert np.array_equal(sizes.sum(axis=1), st["n_after"][-1])
+    assert sizes.sum() == state["total"]
+    W = c.n_loci // 32
+    for s in range(g.ns):
+        young = het = allele = adults = 0
+        for p in range(c.patches):
+            rec, age = g.deme(s, p)
+            assert len(age) == sizes[s, p]
+            assert np.all(np.diff(age.astype(np.int64)) <= 0), (s, p)
+            new = rec[age == 0]
+            young += len(new)
+            adults += int((age == 2).sum())
+            het += _popcount(new[:, :W] ^ new[:, W:])
+            allele += _popcount(new)
+        last = st[-1][s]
+        assert young == last["births"], s
+        assert adults == last["adults_after"], s
+        assert het == last["het_newborn"], s
+        assert allele == last["allele_newborn"], s
+    g.close()
