@@ -106,3 +106,18 @@ def test_batch_rejects_invalid_member():
     with pytest.raises(sp().SpeggError) as e:
         sp().Batch(ws)
     assert "member 2" in str(e.value)
+
+
+def test_batch_full_size_sampled_members_equal_oracle():
+    """The measured batch (4,096 replicates, N log-uniform [1e3, 2e5], L in
+    {32, 64, 128}) for three generations; a seeded sample of members, each
+    recomputed alone by the oracle, bit for bit."""
+    ws = S.batch_replicates(count=4096, n_gen=64)
+    b = sp().Batch(ws, stats_capacity=8)
+    b.step(3)
+    rng = np.random.default_rng(5)
+    for i in sorted(int(x) for x in rng.choice(len(ws), 8, replace=False)):
+        orc = oracle.OraclePopulation.from_workload(ws[i])
+        so = orc.step(3)
+        assert_member_equals(b, i, so, orc.genotypes(), orc.survivors(), orc.state())
+    b.close()
