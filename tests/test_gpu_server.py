@@ -90,3 +90,22 @@ def test_oversized_job_is_rejected():
         srv.submit(w, 100)
     assert e.value.code == sp().ERR_BUDGET
     srv.close()
+
+
+def test_measured_trace_jobs_equal_jobs_run_alone():
+    """The measured served trace (48 jobs from a Poisson stream at 200 jobs/s,
+    N log-uniform [1e3, 2e6], L in {64, 256}, 100-2000 generations), served
+    as the benchmark serves it; a seeded sample of jobs, each re-run alone on
+    the GPU, bit for bit."""
+    ws, gens, arrivals = S.served_trace(count=48, rate=200.0)
+    srv = sp().Server(gens_per_tick=16)
+    jobs = srv.run_trace(ws, gens, arrivals)
+    assert srv.counters()["queued"] == 0
+    rng = np.random.default_rng(11)
+    for i in sorted(int(x) for x in rng.choice(len(ws), 6, replace=False)):
+        info = srv.job_info(int(jobs[i]))
+        ref, st = alone(ws[i], gens[i])
+        assert info["state"] == 2 and info["gen"] == st["gen"] and info["status"] == st["status"]
+        got = srv.job_stats(int(jobs[i]), 1, info["gen"]) if info["gen"] else ref
+        assert got.tobytes() == ref.tobytes(), f"job {i} differs from the same population run alone"
+    srv.close()
