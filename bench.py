@@ -175,7 +175,7 @@ def bench_config(w, l2):
             "n": w.n, "n_loci": w.n_loci, "generations_per_step": GENERATIONS, "l2": l2}
 
 
-def batched_replicates(spegg, torch, gens: int = 64, plain_members: int = 256, plain_gens: int = 32,
+def batched_replicates(spegg, torch, gens: int = 500, plain_members: int = 256, plain_gens: int = 32,
                        oracle_cpu: bool = False):
     """Batched-replicates workload: 4,096 independent single-species runs (N
     log-uniform in [1e3, 2e5], L in {32, 64, 128}, s in [0, 0.5]) advanced by
