@@ -276,7 +276,7 @@ PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap
     if (weighted) {
         L.weights = take(sizeof(WeightParams));
         L.obin = take((size_t)n * 2);
-        L.survw = take((size_t)n * 8);
+        L.survw = take((size_t)n * 16);
     }
     L.total = off;
     return L;
@@ -476,7 +476,7 @@ int view_init(const PopView &v, const PopParams &prm, const uint32_t *init_genot
     if (rc != SPG_OK) return fail(rc, "founder launch failed");
     if (v.L.weighted) {  // every founder is a potential parent, in index order
         rc = launch_survivor_bins(reinterpret_cast<const PopParams *>(v.base + v.L.params), v.words, geno0, nullptr,
-                                  v.n, reinterpret_cast<unsigned long long *>(v.base + v.L.survw), v.stream);
+                                  v.n, v.n, reinterpret_cast<unsigned long long *>(v.base + v.L.survw), v.stream);
         if (rc != SPG_OK) return fail(rc, "survivor-bin launch failed");
     }
     rc = view_set_state(v, 0, v.n, kCertain, 0.0, SPG_OK, 0xFFFFFFFFu);

@@ -529,8 +529,7 @@ struct SegCtx {
     const uint32_t *sin;
     uint32_t *alive;
     uint32_t *bucket_now;
-    const unsigned long long *survw;   // weighted parents: survivor index | bin << 32
-    const WeightParams *wt;            // weighted parents: acceptance thresholds
+    const unsigned long long *survw;   // weighted parents: [2][n] survivor index | role threshold << 32
     uint16_t *obin;                    // weighted parents: bins of the offspring formed
     uint32_t n, S, f, g, rep, k0, k1, kmax, nplanes, shift, ndplanes;
     int32_t e_min, bias, d_min;
@@ -544,14 +543,16 @@ struct SegCtx {
 // stands if all kMateAttempts are rejected.  Proposals go in pairs (one
 // Philox block), both roles together, so four gathers are in flight at once;
 // the first accepted proposal in order is the parent, as if they were tried
-// one at a time.
+// one at a time.  A gathered word carries the survivor's threshold for the
+// role (looked up once per survivor by the compaction), so a proposal is one
+// 8-byte read and a comparison.
 static_assert(kMateAttempts % 2 == 0, "whole Philox blocks of proposals");
 
 // Proposals k and k+1 of one role: whether one was taken, and the parent (the
 // first taken, else proposal k+1).
-__device__ __forceinline__ bool weighted_pair(const uint32_t *acc, const uint4 &d, unsigned long long e0,
-                                              unsigned long long e1, uint32_t &parent) {
-    const uint32_t t0 = __ldg(acc + (uint32_t)(e0 >> 32)), t1 = __ldg(acc + (uint32_t)(e1 >> 32));
+__device__ __forceinline__ bool weighted_pair(const uint4 &d, unsigned long long e0, unsigned long long e1,
+                                              uint32_t &parent) {
+    const uint32_t t0 = (uint32_t)(e0 >> 32), t1 = (uint32_t)(e1 >> 32);
     const bool a0 = t0 == kCertain || d.y < t0, a1 = t1 == kCertain || d.w < t1;
     parent = a0 ? (uint32_t)e0 : (uint32_t)e1;
     return a0 || a1;
@@ -570,11 +571,11 @@ __device__ __forceinline__ void weighted_parents(const SegCtx &c, uint32_t j, ui
         }
         if (open_f) {
             df = philox(make_uint4(j, c.g, c.rep, sub | (1u << 8)), c.k0, c.k1);
-            ef0 = __ldcg(c.survw + __umulhi(df.x, c.S));
-            ef1 = __ldcg(c.survw + __umulhi(df.z, c.S));
+            ef0 = __ldcg(c.survw + c.n + __umulhi(df.x, c.S));
+            ef1 = __ldcg(c.survw + c.n + __umulhi(df.z, c.S));
         }
-        if (open_m) open_m = !weighted_pair(c.wt->acc[0], dm, em0, em1, mom);
-        if (open_f) open_f = !weighted_pair(c.wt->acc[1], df, ef0, ef1, dad);
+        if (open_m) open_m = !weighted_pair(dm, em0, em1, mom);
+        if (open_f) open_f = !weighted_pair(df, ef0, ef1, dad);
     }
 }
 
@@ -781,7 +782,6 @@ __global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __gr
             c.alive = sg.alive;
             c.survw = sg.survw;
             c.obin = sg.obin;
-            c.wt = sg.prm->weights;
             c.bucket_now = sg.bucket_sum + (c.g & 1u) * sg.nbuckets;
             uint32_t *bucket_next = sg.bucket_sum + ((c.g + 1u) & 1u) * sg.nbuckets;
             c.rep = c.P->rep;
@@ -1284,7 +1284,12 @@ __device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
         if ((word >> lane) & 1u) {
             const uint32_t rank = r0 + __popc(word & lt), idx = (w0 + (uint32_t)k) * 32u + (uint32_t)lane;
             sout[rank] = idx;
-            if (sg.survw) sg.survw[rank] = (unsigned long long)idx | ((unsigned long long)__ldcg(sg.obin + idx) << 32);
+            if (sg.survw) {  // the survivor's acceptance thresholds as mother and as father
+                const uint32_t bin = __ldcg(sg.obin + idx);
+                const WeightParams *wt = sg.prm->weights;
+                sg.survw[rank] = (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[0][bin]) << 32);
+                sg.survw[sg.n + rank] = (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[1][bin]) << 32);
+            }
         }
     }
     }
@@ -1337,11 +1342,13 @@ __global__ void k_iota(uint32_t *__restrict__ surv, uint32_t n) {
     if (i < n) surv[i] = i;
 }
 
-// survw[r] = surv[r] | bin << 32 for the current survivors, each bin from
-// its record's additive phenotype (planes read from the parameters).
+// survw[pi * n + r] = surv[r] | (role pi's threshold for the survivor's bin)
+// << 32 for the current survivors, each bin from its record's genetic value
+// (planes read from the parameters).
 template <int W>
 __global__ void k_survivor_bins(const PopParams *__restrict__ P, const uint32_t *__restrict__ geno,
-                                const uint32_t *__restrict__ surv, uint32_t S, unsigned long long *__restrict__ survw) {
+                                const uint32_t *__restrict__ surv, uint32_t S, uint32_t n,
+                                unsigned long long *__restrict__ survw) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= S) return;
     const uint32_t idx = surv ? surv[r] : r;
@@ -1371,7 +1378,8 @@ __global__ void k_survivor_bins(const PopParams *__restrict__ P, const uint32_t 
     }
     const long long v = (long long)raw + (long long)P->bias;
     const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> P->shift, (long long)(kBins - 1));
-    survw[r] = (unsigned long long)idx | ((unsigned long long)bin << 32);
+    survw[r] = (unsigned long long)idx | ((unsigned long long)P->weights->acc[0][bin] << 32);
+    survw[(size_t)n + r] = (unsigned long long)idx | ((unsigned long long)P->weights->acc[1][bin] << 32);
 }
 
 __global__ void k_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R,
@@ -1500,15 +1508,15 @@ int launch_iota(uint32_t *surv, uint32_t n, void *stream) {
 }
 
 int launch_survivor_bins(const PopParams *prm, uint32_t words, const uint32_t *geno, const uint32_t *surv,
-                         uint32_t S, unsigned long long *survw, void *stream) {
+                         uint32_t S, uint32_t n, unsigned long long *survw, void *stream) {
     if (S == 0) return SPG_OK;
     const dim3 grid((S + 255) / 256), block(256);
     cudaStream_t s = (cudaStream_t)stream;
     switch (words) {
-        case 1: k_survivor_bins<1><<<grid, block, 0, s>>>(prm, geno, surv, S, survw); break;
-        case 2: k_survivor_bins<2><<<grid, block, 0, s>>>(prm, geno, surv, S, survw); break;
-        case 4: k_survivor_bins<4><<<grid, block, 0, s>>>(prm, geno, surv, S, survw); break;
-        case 8: k_survivor_bins<8><<<grid, block, 0, s>>>(prm, geno, surv, S, survw); break;
+        case 1: k_survivor_bins<1><<<grid, block, 0, s>>>(prm, geno, surv, S, n, survw); break;
+        case 2: k_survivor_bins<2><<<grid, block, 0, s>>>(prm, geno, surv, S, n, survw); break;
+        case 4: k_survivor_bins<4><<<grid, block, 0, s>>>(prm, geno, surv, S, n, survw); break;
+        case 8: k_survivor_bins<8><<<grid, block, 0, s>>>(prm, geno, surv, S, n, survw); break;
         default: return SPG_ERR_INVALID;
     }
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;

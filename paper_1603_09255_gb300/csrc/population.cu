@@ -282,7 +282,7 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
         rc = launch_survivor_bins(reinterpret_cast<const PopParams *>(p->arena + p->L.params), p->words,
                                   reinterpret_cast<const uint32_t *>(p->arena + (par ? p->L.geno1 : p->L.geno0)),
                                   reinterpret_cast<const uint32_t *>(p->arena + (par ? p->L.surv1 : p->L.surv0)), h.S,
-                                  reinterpret_cast<unsigned long long *>(p->arena + p->L.survw), p->stream);
+                                  p->n, reinterpret_cast<unsigned long long *>(p->arena + p->L.survw), p->stream);
         if (rc != SPG_OK) return fail(rc, "survivor-bin launch failed");
     }
     rc = view_set_state(p->view(), h.gen, h.S, h.f, h.R, h.status, 0xFFFFFFFFu);

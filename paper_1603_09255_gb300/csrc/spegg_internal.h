@@ -122,7 +122,8 @@ struct alignas(16) Segment {
     uint32_t *alive;                  // alive bitmap of the generation being formed [nbuckets * kBucketWords]
     uint32_t *bucket_sum;             // survivors per bucket, by generation parity [2][nbuckets]
     uint16_t *obin;                   // weighted parents: phenotype bin of each offspring [N]
-    unsigned long long *survw;        // weighted parents: survivor index | bin << 32, by rank [N]
+    unsigned long long *survw;        // weighted parents: [2][N], role pi and rank r -> survivor index | its
+                                      // acceptance threshold for role pi << 32
     DevState *state;
     StatAcc *acc;                     // [kAccCopies]
     spg_stats *ring;                  // [stats_cap]
@@ -173,10 +174,11 @@ OffspringKernel continuous_kernel(uint32_t n_loci);
 // founder draws (records of 2L int16), survivors = 0..n-1.
 int launch_founders_cont(const PopParams *prm, uint32_t n_loci, uint32_t *geno, uint32_t *surv, uint32_t n,
                          uint32_t p0_q32, void *stream);
-// Enqueue survw[r] = surv[r] | bin << 32 for the S current survivors (surv
-// NULL: survivor r is record r), the bin computed from the record.
+// Enqueue the weighted-parent words of the S current survivors (surv
+// NULL: survivor r is record r), the bin computed from the record; the
+// father words start n words after the mother words.
 int launch_survivor_bins(const PopParams *prm, uint32_t words, const uint32_t *geno, const uint32_t *surv,
-                         uint32_t S, unsigned long long *survw, void *stream);
+                         uint32_t S, uint32_t n, unsigned long long *survw, void *stream);
 // Enqueue a state reset: state fields and cleared statistics accumulators.
 int launch_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,
                      uint32_t target, void *stream);
