@@ -176,12 +176,13 @@ def bench_config(w, l2):
 
 
 def batched_replicates(spegg, torch, gens: int = 500, plain_members: int = 256, plain_gens: int = 32,
-                       oracle_cpu: bool = False):
+                       oracle_cpu: bool = False, count: int = 4096):
     """Batched-replicates workload: 4,096 independent single-species runs (N
     log-uniform in [1e3, 2e5], L in {32, 64, 128}, s in [0, 0.5]) advanced by
     shared, graph-captured launches with autotuned tilings, against the plain
     path (one population at a time) timed on the first `plain_members`."""
-    ws = S.batch_replicates(count=4096, n_gen=gens)
+    ws = S.batch_replicates(count=count, n_gen=gens)
+    plain_members = min(plain_members, count)
     stream = torch.cuda.Stream()
     batch = spegg.Batch(ws, stats_capacity=gens + 64, stream=stream)
     ran = batch.autotune(4)
@@ -196,7 +197,8 @@ def batched_replicates(spegg, torch, gens: int = 500, plain_members: int = 256, 
     stream.synchronize()
     ms = a.elapsed_time(b)
     sum_n = sum(w.n for w in ws)
-    tilings = {str(L): batch.tiling(L) for L in (32, 64, 128)}
+    tilings = {str(L): batch.launch_shape(L) for L in (32, 64, 128)}
+    tuned = getattr(batch, "autotune_report", {})
     # per-generation latency of the whole batch: single generations bracketed
     # by events, after 3 untimed ones
     batch.step(3)
@@ -232,7 +234,7 @@ def batched_replicates(spegg, torch, gens: int = 500, plain_members: int = 256, 
     achieved = algo / (ms / 1e3) / 1e9
     return {"workload": f"4096 replicates, N log-uniform [1e3, 2e5] (sum {sum_n}), L in {{32, 64, 128}}, "
                         f"s in [0, 0.5], {gens} generations timed after {ran + 32}",
-            "value": value, "unit": "individual-generations/s", "ms": ms, "tilings": tilings,
+            "value": value, "unit": "individual-generations/s", "ms": ms, "tilings": tilings, "autotune": tuned,
             "plain_value": plain, "plain_sample": f"first {plain_members} replicates, {plain_gens} generations, "
                                                   "one population stepped at a time",
             "speedup_vs_plain": value / plain,
@@ -410,8 +412,20 @@ def main():
     ap.add_argument("--no-weighted", action="store_true", help="omit the weighted-parents measurement")
     ap.add_argument("--no-dominance", action="store_true", help="omit the dominance measurement")
     ap.add_argument("--no-continuous", action="store_true", help="omit the continuous-allele measurement")
+    ap.add_argument("--shape", default="", metavar="B,I",
+                    help="launch shape of the headline population: threads per block, offspring per thread; "
+                         "results do not depend on it")
+    ap.add_argument("--only-batched", type=int, default=0, metavar="R",
+                    help="run only the batched-replicates measurement on the first R replicates (profiling)")
     args = ap.parse_args()
     workload = S.consumer_resource()
+    if args.only_batched:
+        import torch
+        from paper_1603_09255_gb300 import build as pkg_build
+        pkg_build.build()
+        from paper_1603_09255_gb300 import spegg
+        print(json.dumps(batched_replicates(spegg, torch, gens=args.steps, count=args.only_batched)))
+        return
     if args.impl == "reference":
         reference_arm(args, workload)
         return
@@ -429,6 +443,8 @@ def main():
     workload = replica_workload(workload, rank)
     stream = torch.cuda.Stream()
     pop = spegg.Population.from_workload(workload, stats_capacity=GENERATIONS + 8, stream=stream)
+    if args.shape:
+        pop.set_launch_shape(*[int(x) for x in args.shape.split(",")])
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -526,6 +542,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": f"k_offspring<W={workload.words}> + k_compact (one generation)",
+                     "shape": pop.launch_shape(),
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6,
                      "isolated_launch_us": kernel_ms * 1000.0},
         "e2e": {"value": e2e_value, "unit": "individual-generations/s", "h2d_bytes_per_step": len(blob),

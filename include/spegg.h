@@ -110,7 +110,7 @@
 extern "C" {
 #endif
 
-#define SPG_ABI_VERSION 2u
+#define SPG_ABI_VERSION 3u
 #define SPG_N_BINS 4096u
 #define SPG_CERTAIN 0xFFFFFFFFu
 #define SPG_MAX_LOCI 256u
@@ -258,9 +258,23 @@ int spg_checkpoint_size(spg_pop *pop, size_t *bytes);
 int spg_checkpoint(spg_pop *pop, void *host, size_t capacity);
 int spg_restore(spg_pop *pop, const void *host, size_t bytes);
 
-/* Offspring per thread of the generation kernel (1, 2 or 4; 1 or 2 for
- * L = 256; default 1).  A launch-shape choice only: every
- * setting gives identical results.  Waits for the stream. */
+/* Launch shape of the generation kernel: threads per block (128, 256 or 512;
+ * 0 = 256) and offspring per thread (1 or 2 for L <= 64, 1 for L >= 128;
+ * 0 = 1).  A launch-shape choice only: every shape gives identical results.
+ * Populations with a linkage map or parent weights, and continuous allelic
+ * values, run 256 threads with one offspring each.  spg_get_launch_shape
+ * reports the shape in use.  SPG_ERR_INVALID for an unsupported shape.
+ * Waits for the stream. */
+typedef struct {
+    uint32_t threads_per_block;
+    uint32_t items_per_thread;
+} spg_launch_shape;
+
+int spg_set_launch_shape(spg_pop *pop, const spg_launch_shape *shape);
+int spg_get_launch_shape(spg_pop *pop, spg_launch_shape *out);
+/* Offspring per thread at 256 threads per block (spg_set_launch_shape with
+ * {256, items_per_thread}); spg_get_tiling reports the offspring per thread
+ * in use. */
 int spg_set_tiling(spg_pop *pop, uint32_t items_per_thread);
 int spg_get_tiling(spg_pop *pop, uint32_t *items_per_thread);
 
@@ -281,15 +295,31 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
 int spg_batch_set_ecology(spg_batch *batch, uint32_t member, const spg_ecology *eco);
 /* Enqueue n_gen generations of every member (returns after enqueue). */
 int spg_batch_step(spg_batch *batch, uint32_t n_gen);
-/* Offspring per thread for the members with n_loci loci (as spg_set_tiling). */
+/* Launch shape of the members with n_loci loci (as spg_set_launch_shape);
+ * spg_batch_set_tiling / spg_batch_get_tiling as spg_set_tiling. */
+int spg_batch_set_launch_shape(spg_batch *batch, uint32_t n_loci, const spg_launch_shape *shape);
+int spg_batch_get_launch_shape(spg_batch *batch, uint32_t n_loci, spg_launch_shape *out);
 int spg_batch_set_tiling(spg_batch *batch, uint32_t n_loci, uint32_t items_per_thread);
 int spg_batch_get_tiling(spg_batch *batch, uint32_t n_loci, uint32_t *items_per_thread);
 /* Launch-shape autotuner: for each locus-count group, runs one untimed
  * generation and then times gens_per_trial real generations with each of
- * three tilings, and keeps the fastest.  Every member advances by the same
- * number of generations (*gens_run = 3 * (gens_per_trial + 1)); results do
- * not depend on the tilings chosen. */
-int spg_batch_autotune(spg_batch *batch, uint32_t gens_per_trial, uint32_t *gens_run);
+ * SPG_AUTOTUNE_CANDIDATES launch shapes -- threads per block (128, 256, 512)
+ * x offspring per thread (1, 2 for L <= 64; for L >= 128 each block size is
+ * timed twice) -- and keeps the fastest.  Every
+ * member advances by the same number of generations (report->gens_run =
+ * SPG_AUTOTUNE_CANDIDATES * (gens_per_trial + 1)); results do not depend on
+ * the shapes chosen.  The report (may be NULL) gives each group's chosen
+ * shape (index 0..3 for L = 32, 64, 128, 256; zeros for an empty group) and
+ * the best and worst candidate's time per generation. */
+#define SPG_AUTOTUNE_CANDIDATES 6u
+typedef struct {
+    spg_launch_shape groups[4];
+    float best_ms[4];
+    float worst_ms[4];
+    uint32_t gens_run;
+} spg_autotune_report;
+
+int spg_batch_autotune(spg_batch *batch, uint32_t gens_per_trial, spg_autotune_report *report);
 int spg_batch_read_stats(spg_batch *batch, uint32_t member, uint32_t first_gen, uint32_t count, spg_stats *out);
 int spg_batch_read_genotypes(spg_batch *batch, uint32_t member, uint32_t *host, size_t n_words);
 int spg_batch_read_survivors(spg_batch *batch, uint32_t member, uint32_t *host, size_t capacity, uint32_t *S);
@@ -441,11 +471,12 @@ void spg_space_destroy(spg_space *space);
 
 /* ---- One generation without any device allocation -----------------------
  * The paper has no counterpart to this call; it exists for callers that may
- * not allocate device memory: code that runs while a CUDA stream is being
- * captured into a graph (allocation calls are not permitted there), host
- * applications whose device memory is owned entirely by another framework's
- * pool, and real-time or certified loops that forbid allocation after start-up
- * because an allocation can block or fail at an arbitrary moment.
+ * not allocate device memory: host applications whose device memory is owned
+ * entirely by another framework's pool (a cudaMalloc of their own would fail
+ * or fragment that pool), plug-ins that run inside such a framework under a
+ * fixed memory budget, and real-time or certified loops that forbid
+ * allocation after start-up because an allocation can block the device or
+ * fail at an arbitrary moment.
  *
  * It forms generation `generation` of one population from caller-owned device
  * buffers: `parents` (N * 2W records of generation-1) and `survivors` (their S
@@ -469,7 +500,7 @@ void spg_space_destroy(spg_space *space);
  * the outputs are valid once it completes.  Returns SPG_OK or a negative
  * SPG_ERR_* code (spg_last_error() explains it). */
 #define SPG_NOALLOC_MAX_N 4194304u
-#define SPG_NOALLOC_SCRATCH_BYTES 569344u
+#define SPG_NOALLOC_SCRATCH_BYTES 634624u
 
 typedef struct {
     uint32_t n;                   /* N, 1 .. SPG_NOALLOC_MAX_N                  */

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libspegg_gb300.so")
-SOURCES = ["kernels.cu", "engine.cu", "population.cu", "batch.cu", "server.cu", "space.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "offspring_w1.cu", "offspring_w2.cu", "offspring_w4.cu", "offspring_w8.cu", "engine.cu",
+           "population.cu", "batch.cu", "server.cu", "space.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -32,9 +32,10 @@ struct Member {
 };
 
 struct Group {
-    uint32_t words = 0, items = 0;
+    uint32_t words = 0;
+    Shape shape;
     std::vector<uint32_t> members;
-    size_t table_off = 0, table_bytes = 0;  // launch table in the batch arena (sized for items = 1)
+    size_t table_off = 0, table_bytes = 0;  // launch table in the batch arena (sized for every shape)
     GenLaunch gl;
 };
 
@@ -64,7 +65,7 @@ struct MultiChain {
                 cudaKernelNodeParams kp{};
                 kp.func = reinterpret_cast<void *>(off ? g.gl.offspring.fn : g.gl.compact);
                 kp.gridDim = dim3(off ? g.gl.blocks : g.gl.buckets);
-                kp.blockDim = dim3(off ? kBlock : kCompactThreads);
+                kp.blockDim = dim3(off ? g.gl.offspring.block : kCompactThreads);
                 kp.sharedMemBytes = off ? g.gl.offspring.smem : 0;
                 kp.kernelParams = params;
                 cudaGraphNode_t node;
@@ -102,16 +103,20 @@ struct spg_batch {
 
 namespace {
 
-// (Re)build a group's launch table for `items` offspring per thread
-// (synchronous upload).
-int configure_group(spg_batch *b, Group &g, uint32_t items) {
+// (Re)build a group's launch table for a launch shape (synchronous upload).
+int configure_group(spg_batch *b, Group &g, const Shape &shape) {
     if (g.members.empty()) return SPG_OK;
     std::vector<const PopView *> views;
     views.reserve(g.members.size());
-    for (uint32_t mi : g.members) views.push_back(&b->members[mi].v);
-    const int rc = build_group_launch(views, g.words, items, b->arena + g.table_off, g.table_bytes, g.gl);
+    bool eco = false, dom = false;
+    for (uint32_t mi : g.members) {
+        views.push_back(&b->members[mi].v);
+        eco |= b->members[mi].prm->has_eco != 0u;
+        dom |= b->members[mi].prm->has_dom != 0u;
+    }
+    const int rc = build_group_launch(views, g.words, shape, eco, dom, b->arena + g.table_off, g.table_bytes, g.gl);
     if (rc != SPG_OK) return rc;
-    g.items = items;
+    g.shape = shape;
     b->chains.clear();
     return SPG_OK;
 }
@@ -164,7 +169,7 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
         m.prm.reset(new (std::nothrow) PopParams());
         if (!m.prm) return fail(SPG_ERR_OOM, "host allocation failed");
         const uint32_t words = d.n_loci / 32;
-        int rc = build_params(&d, 1, *m.prm);
+        int rc = build_params(&d, *m.prm);
         if (rc != SPG_OK) return fail(rc, "member %u: %s", i, spg_last_error());
         m.v.n = d.n;
         m.v.words = words;
@@ -178,13 +183,14 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
     }
     for (Group &g : b->groups) {
         if (g.members.empty()) continue;
-        uint32_t tiles = 0, buckets = 0;
+        uint64_t offspring = 0;
+        uint32_t buckets = 0;
         for (uint32_t mi : g.members) {
-            tiles += tiles_for(b->members[mi].v.n, 1);
+            offspring += b->members[mi].v.n;
             buckets += b->members[mi].v.nbuckets;
         }
         g.table_off = off;
-        g.table_bytes = group_table_bytes((uint32_t)g.members.size(), tiles, buckets);
+        g.table_bytes = group_table_bytes((uint32_t)g.members.size(), offspring, buckets);
         off = align_up(off + g.table_bytes, 256);
     }
     b->arena_bytes = off;
@@ -214,7 +220,7 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
     }
     int rc = view_sync(b->members[0].v);  // caller arrays and host parameters have been read
     for (Group &g : b->groups)
-        if (rc == SPG_OK) rc = configure_group(b.get(), g, default_items(g.words));
+        if (rc == SPG_OK) rc = configure_group(b.get(), g, default_shape(g.words));
     if (rc != SPG_OK) {
         spg_batch_destroy(b.release());
         return rc;
@@ -227,7 +233,12 @@ int spg_batch_set_ecology(spg_batch *b, uint32_t member, const spg_ecology *eco)
     PopView v;
     int rc = member_view(b, member, v);
     if (rc != SPG_OK) return rc;
-    return view_set_ecology(v, *b->members[member].prm, eco);
+    rc = view_set_ecology(v, *b->members[member].prm, eco);
+    if (rc != SPG_OK) return rc;
+    // the group's survival tables now carry attack rates
+    Group &g = b->groups[b->members[member].group];
+    if (!g.gl.offspring.eco_table) rc = configure_group(b, g, g.shape);
+    return rc;
 }
 
 int spg_batch_step(spg_batch *b, uint32_t n_gen) {
@@ -241,43 +252,59 @@ int spg_batch_step(spg_batch *b, uint32_t n_gen) {
 }
 
 int spg_batch_set_tiling(spg_batch *b, uint32_t n_loci, uint32_t items) {
-    if (!b) return fail(SPG_ERR_INVALID, "batch is NULL");
-    if (!(n_loci == 32 || n_loci == 64 || n_loci == 128 || n_loci == 256))
-        return fail(SPG_ERR_INVALID, "n_loci must be 32, 64, 128 or 256");
-    const uint32_t words = n_loci / 32;
-    if (!supported_items(words, items))
-        return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (1 or 2 for 256 loci); got %u", items);
-    int rc = view_sync(b->members[0].v);
-    if (rc != SPG_OK) return rc;
-    return configure_group(b, b->groups[group_of_words(words)], items);
+    spg_launch_shape sh{256u, items};
+    return spg_batch_set_launch_shape(b, n_loci, &sh);
 }
 
 int spg_batch_get_tiling(spg_batch *b, uint32_t n_loci, uint32_t *items) {
-    if (!b || !items) return fail(SPG_ERR_INVALID, "NULL argument");
+    if (!items) return fail(SPG_ERR_INVALID, "NULL argument");
+    spg_launch_shape sh{};
+    const int rc = spg_batch_get_launch_shape(b, n_loci, &sh);
+    if (rc == SPG_OK) *items = sh.items_per_thread;
+    return rc;
+}
+
+int spg_batch_set_launch_shape(spg_batch *b, uint32_t n_loci, const spg_launch_shape *shape) {
+    if (!b || !shape) return fail(SPG_ERR_INVALID, "NULL argument");
     if (!(n_loci == 32 || n_loci == 64 || n_loci == 128 || n_loci == 256))
         return fail(SPG_ERR_INVALID, "n_loci must be 32, 64, 128 or 256");
-    *items = b->groups[group_of_words(n_loci / 32)].items;
+    const uint32_t words = n_loci / 32;
+    Shape sh;
+    int rc = shape_from_abi(words, shape, sh);
+    if (rc != SPG_OK) return rc;
+    rc = view_sync(b->members[0].v);
+    if (rc != SPG_OK) return rc;
+    return configure_group(b, b->groups[group_of_words(words)], sh);
+}
+
+int spg_batch_get_launch_shape(spg_batch *b, uint32_t n_loci, spg_launch_shape *out) {
+    if (!b || !out) return fail(SPG_ERR_INVALID, "NULL argument");
+    if (!(n_loci == 32 || n_loci == 64 || n_loci == 128 || n_loci == 256))
+        return fail(SPG_ERR_INVALID, "n_loci must be 32, 64, 128 or 256");
+    const Group &g = b->groups[group_of_words(n_loci / 32)];
+    out->threads_per_block = g.members.empty() ? g.shape.block : g.gl.offspring.block;
+    out->items_per_thread = g.members.empty() ? g.shape.items : g.gl.offspring.items;
     return SPG_OK;
 }
 
-int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, uint32_t *gens_run) {
+int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, spg_autotune_report *report) {
     if (!b || gens_per_trial == 0) return fail(SPG_ERR_INVALID, "batch is NULL or no trial generations");
     cudaEvent_t t0, t1;
     if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
         return fail(SPG_ERR_CUDA, "cudaEventCreate");
-    static const uint32_t kCandidates[3] = {1, 2, 4};
     int rc = SPG_OK;
-    // every group runs three trials, each one untimed generation (the new
-    // tiling's first launches) then gens_per_trial timed ones, so all members
-    // advance equally
-    for (Group &g : b->groups) {
+    spg_autotune_report rep{};
+    // every group runs the same number of trials (kAutotuneCandidates), each
+    // one untimed generation (the new shape's first launches) then
+    // gens_per_trial timed ones, so all members advance equally
+    for (uint32_t gi = 0; gi < (uint32_t)b->groups.size() && rc == SPG_OK; ++gi) {
+        Group &g = b->groups[gi];
         if (g.members.empty()) continue;
-        float best_ms = 0.f;
-        uint32_t best = g.items;
-        for (int c = 0; c < 3 && rc == SPG_OK; ++c) {
-            uint32_t items = kCandidates[c];
-            if (!supported_items(g.words, items)) items = 2;
-            rc = configure_group(b, g, items);
+        float best_ms = 0.f, worst_ms = 0.f;
+        Shape best = g.shape;
+        for (uint32_t c = 0; c < kAutotuneCandidates && rc == SPG_OK; ++c) {
+            const Shape cand = autotune_candidate(g.words, c);
+            rc = configure_group(b, g, cand);
             if (rc == SPG_OK) rc = launch_generation(g.gl, b->stream);
             if (rc != SPG_OK) break;
             cudaEventRecord(t0, b->stream);
@@ -288,14 +315,22 @@ int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, uint32_t *gens_run
             cudaEventElapsedTime(&ms, t0, t1);
             if (c == 0 || ms < best_ms) {
                 best_ms = ms;
-                best = items;
+                best = cand;
             }
+            worst_ms = std::max(worst_ms, ms);
         }
         if (rc == SPG_OK) rc = configure_group(b, g, best);
+        if (rc == SPG_OK) {
+            rep.groups[gi].threads_per_block = g.gl.offspring.block;
+            rep.groups[gi].items_per_thread = g.gl.offspring.items;
+            rep.best_ms[gi] = best_ms / (float)gens_per_trial;
+            rep.worst_ms[gi] = worst_ms / (float)gens_per_trial;
+        }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    if (rc == SPG_OK && gens_run) *gens_run = 3 * (gens_per_trial + 1);
+    rep.gens_run = kAutotuneCandidates * (gens_per_trial + 1);
+    if (rc == SPG_OK && report) *report = rep;
     return rc;
 }
 

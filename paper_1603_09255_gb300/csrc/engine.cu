@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <queue>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -86,6 +87,21 @@ void effect_planes(const int16_t *effects, uint32_t n_loci, PopParams &prm) {
     offset_planes(effects, n_loci, prm.planes, prm.e_min, prm.nplanes);
 }
 
+// Byte tables of per-locus values v (effects, or dominance deviations): table
+// k, entry b is the sum of v[8k + i] over the bits i set in b -- the value of
+// the eight loci 8k .. 8k+7 held in byte k of a haplotype (locus l is bit l % 32
+// of word l / 32).  Exact in int32 (at most 8 * 32768 in magnitude).
+static void byte_tables(const int16_t *v, uint32_t n_loci, int32_t *lut) {
+    std::memset(lut, 0, sizeof(int32_t) * kMaxLutBytes * kLutWords);
+    for (uint32_t k = 0; k < n_loci / 8; ++k)
+        for (uint32_t b = 0; b < (uint32_t)kLutWords; ++b) {
+            int32_t sum = 0;
+            for (uint32_t i = 0; i < 8; ++i)
+                if ((b >> i) & 1u) sum += v[8 * k + i];
+            lut[k * kLutWords + b] = sum;
+        }
+}
+
 // Resource factor of the ecology, same arithmetic as the device finalizer.
 uint32_t factor_q32_host(double R, double R_half) {
     const double den = R + R_half;
@@ -137,15 +153,18 @@ int validate_desc(const spg_pop_desc *d) {
     return SPG_OK;
 }
 
-int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
+int build_params(const spg_pop_desc *d, PopParams &prm) {
     std::memset(&prm, 0, sizeof prm);
     std::memcpy(prm.table, d->surv_table, sizeof prm.table);
     effect_planes(d->effects, d->n_loci, prm);
     if (prm.nplanes > (uint32_t)kMaxPlanes) return fail(SPG_ERR_INVALID, "effects span more than 16 bits");
+    byte_tables(d->effects, d->n_loci, prm.lut);
     if (d->dominance) {
         offset_planes(d->dominance, d->n_loci, prm.dplanes, prm.d_min, prm.ndplanes);
         if (prm.ndplanes > (uint32_t)kMaxPlanes)
             return fail(SPG_ERR_INVALID, "dominance deviations span more than 16 bits");
+        for (uint32_t l = 0; l < d->n_loci; ++l) prm.has_dom |= d->dominance[l] != 0 ? 1u : 0u;
+        byte_tables(d->dominance, d->n_loci, prm.dlut);
     }
     prm.kmax = mutation_cdf(d->mu, 2 * d->n_loci, prm.cdf);
     prm.bias = d->bin_bias;
@@ -157,7 +176,6 @@ int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm) {
     prm.key1 = (uint32_t)(d->seed >> 32);
     prm.rep = d->replicate;
     prm.has_eco = 0;
-    prm.ntiles = (d->n + tile_size(items) - 1) / tile_size(items);
     prm.stats_cap = d->stats_capacity ? d->stats_capacity : 1024u;
     prm.linked = d->map_morgans ? 1u : 0u;
     prm.link = nullptr;  // set once the population's memory exists
@@ -252,7 +270,7 @@ int build_weights(const uint32_t *mother_w, const uint32_t *father_w, WeightPara
 // ------------------------------------------------------------ population
 uint32_t bucket_count(uint32_t n) { return (n + kBucket - 1) / kBucket; }
 
-PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap, bool weighted) {
+PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap, bool weighted, bool dense) {
     PopLayout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -265,6 +283,7 @@ PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap
     L.acc = take(sizeof(StatAcc) * kAccCopies);
     L.geno0 = take((size_t)n * 2 * words * 4);
     L.geno1 = take((size_t)n * 2 * words * 4);
+    L.dense = dense ? take((size_t)n * 2 * words * 4) : 0;
     L.surv0 = take((size_t)n * 4);
     L.surv1 = take((size_t)n * 4);
     L.alive = take((size_t)nbuckets * kBucketWords * 4);
@@ -290,6 +309,7 @@ Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, 
     s.prm = reinterpret_cast<const PopParams *>(base + L.params);
     s.geno[0] = reinterpret_cast<uint32_t *>(base + L.geno0);
     s.geno[1] = reinterpret_cast<uint32_t *>(base + L.geno1);
+    s.dense = L.dense ? reinterpret_cast<uint32_t *>(base + L.dense) : nullptr;
     s.surv[0] = reinterpret_cast<uint32_t *>(base + L.surv0);
     s.surv[1] = reinterpret_cast<uint32_t *>(base + L.surv1);
     s.alive = reinterpret_cast<uint32_t *>(base + L.alive);
@@ -307,7 +327,50 @@ Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, 
     return s;
 }
 
-uint32_t default_items(uint32_t words) { (void)words; return 1u; }
+// Launch shapes the batch autotuner times, per locus count: threads per
+// block x offspring per thread (one offspring per thread for L >= 128, whose
+// records fill the registers; each shape timed twice there).
+Shape autotune_candidate(uint32_t words, uint32_t c) {
+    static const uint32_t narrow[kAutotuneCandidates][2] = {{128, 1}, {128, 2}, {256, 1},
+                                                             {256, 2}, {512, 1}, {512, 2}};
+    static const uint32_t wide[kAutotuneCandidates][2] = {{128, 1}, {256, 1}, {512, 1},
+                                                           {128, 1}, {256, 1}, {512, 1}};
+    const uint32_t(&e)[2] = words >= 4 ? wide[c % kAutotuneCandidates] : narrow[c % kAutotuneCandidates];
+    Shape s;
+    s.block = e[0];
+    s.items = e[1];
+    return s;
+}
+
+// A caller's launch shape: 0 fields take the defaults (threads per block of
+// the locus count, one offspring per thread).  words 0: the continuous-allele
+// kernel (256 threads, one offspring each).
+int shape_from_abi(uint32_t words, const spg_launch_shape *in, Shape &out) {
+    if (words == 0) {
+        out = Shape{(uint32_t)kBlock, 1u};
+        if ((in->threads_per_block && in->threads_per_block != (uint32_t)kBlock) ||
+            (in->items_per_thread && in->items_per_thread != 1u))
+            return fail(SPG_ERR_INVALID, "continuous allelic values run 256 threads, one offspring each");
+        return SPG_OK;
+    }
+    out = default_shape(words);
+    if (in->threads_per_block) out.block = in->threads_per_block;
+    out.items = in->items_per_thread ? in->items_per_thread : 1u;
+    if (!supported_shape(words, out.block, out.items))
+        return fail(SPG_ERR_INVALID,
+                    "unsupported launch shape (%u threads, %u offspring per thread) for %u loci: threads 128, 256 or "
+                    "512; offspring per thread 1 or 2 for L <= 64, 1 for L >= 128",
+                    out.block, out.items, 32u * words);
+    return SPG_OK;
+}
+
+Shape default_shape(uint32_t words) {
+    (void)words;
+    Shape s;
+    s.block = 256;
+    s.items = 1;
+    return s;
+}
 
 GraphChain::~GraphChain() { reset(); }
 
@@ -332,7 +395,7 @@ int GraphChain::build(const GenLaunch &gl, uint32_t len) {
         cudaKernelNodeParams kp{};
         kp.func = reinterpret_cast<void *>(off ? gl.offspring.fn : gl.compact);
         kp.gridDim = dim3(off ? gl.blocks : gl.buckets);
-        kp.blockDim = dim3(off ? kBlock : kCompactThreads);
+        kp.blockDim = dim3(off ? gl.offspring.block : kCompactThreads);
         kp.sharedMemBytes = off ? gl.offspring.smem : 0;
         kp.kernelParams = params;
         cudaGraphNode_t node;
@@ -353,7 +416,7 @@ int GraphChain::build(const GenLaunch &gl, uint32_t len) {
 }
 
 int launch_generation(const GenLaunch &gl, cudaStream_t stream) {
-    gl.offspring.fn<<<gl.blocks, kBlock, gl.offspring.smem, stream>>>(gl.args);
+    gl.offspring.fn<<<gl.blocks, gl.offspring.block, gl.offspring.smem, stream>>>(gl.args);
     gl.compact<<<gl.buckets, kCompactThreads, 0, stream>>>(gl.args);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "generation launch");
@@ -379,55 +442,120 @@ int enqueue_generations(const GenLaunch &gl, uint32_t n_gen, GraphChain &chain, 
 }
 
 // ------------------------------------------------- launch groups
-size_t group_table_bytes(uint32_t members, uint32_t tiles, uint32_t buckets) {
-    return align_up((size_t)members * sizeof(Segment), 256) + align_up((size_t)tiles * 4, 256) +
-           align_up((size_t)buckets * 4, 256);
+// Bytes of a launch group's table: segments, runs (at most two per member plus
+// one per kMinRunOffspring offspring, whatever the tile size), the blocks' run
+// offsets and the bucket map.
+size_t group_table_bytes(uint32_t members, uint64_t offspring, uint32_t buckets) {
+    const uint64_t runs = 2ull * members + offspring / kMinRunOffspring + 1ull;
+    return align_up((size_t)members * sizeof(Segment), 256) + align_up((size_t)runs * sizeof(Run), 256) +
+           align_up((size_t)(kMaxGridBlocks + 1) * 4, 256) + align_up((size_t)buckets * 4, 256);
 }
 
-uint32_t tiles_for(uint32_t n, uint32_t items) { return (n + tile_size(items) - 1) / tile_size(items); }
+uint32_t tiles_for(uint32_t n, const Shape &shape) {
+    const uint32_t t = tile_size(shape.block, shape.items);
+    return (n + t - 1) / t;
+}
 
-int build_group_launch(const std::vector<const PopView *> &members, uint32_t words, uint32_t items, char *table,
-                       size_t table_capacity, GenLaunch &gl) {
+// Runs of a launch group (see GenArgs): member m's tiles[m] tiles dealt out to
+// G blocks.  Members in order, each to the k = clamp(tiles / min_run, 1, G)
+// blocks with the least work so far, as k contiguous runs of near-equal
+// length: all blocks sweep the members together, so the populations being
+// formed at any moment are few and their parent records stay in L2 (the
+// flattened replicate loop of Fig. S5 B, scheduled for locality).  A run's
+// set-up (tables, pipeline start) counts as one tile of work.
+void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_run, std::vector<Run> &runs,
+                   std::vector<uint32_t> &block_runs) {
+    std::vector<std::vector<Run>> per(G);
+    using Load = std::pair<uint64_t, uint32_t>;  // (work so far, block)
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (uint32_t b = 0; b < G; ++b) heap.push({0ull, b});
+    std::vector<Load> picked;
+    for (uint32_t m = 0; m < (uint32_t)tiles.size(); ++m) {
+        const uint32_t T = tiles[m];
+        if (T == 0) continue;
+        const uint32_t k = std::max(1u, std::min(G, T / std::max(1u, min_run)));
+        picked.clear();
+        for (uint32_t i = 0; i < k; ++i) {
+            picked.push_back(heap.top());
+            heap.pop();
+        }
+        std::sort(picked.begin(), picked.end(), [](const Load &x, const Load &y) { return x.second < y.second; });
+        for (uint32_t i = 0; i < k; ++i) {
+            const uint32_t t0 = (uint32_t)((uint64_t)T * i / k), t1 = (uint32_t)((uint64_t)T * (i + 1) / k);
+            per[picked[i].second].push_back(Run{m, t0, t1 - t0, i, k, {0u, 0u, 0u}});
+            heap.push({picked[i].first + (t1 - t0) + 1u, picked[i].second});
+        }
+    }
+    runs.clear();
+    block_runs.assign(G + 1, 0u);
+    for (uint32_t b = 0; b < G; ++b) {
+        block_runs[b] = (uint32_t)runs.size();
+        runs.insert(runs.end(), per[b].begin(), per[b].end());
+    }
+    block_runs[G] = (uint32_t)runs.size();
+}
+
+int build_group_launch(const std::vector<const PopView *> &members, uint32_t words, const Shape &shape, bool eco,
+                       bool dom, char *table, size_t table_capacity, GenLaunch &gl) {
     if (members.empty()) {
         gl = GenLaunch{};
         return SPG_OK;
     }
-    OffspringKernel k = offspring_kernel(words, items);
+    if (!supported_shape(words, shape.block, shape.items))
+        return fail(SPG_ERR_INVALID, "unsupported launch shape (%u threads, %u offspring per thread) for %u loci",
+                    shape.block, shape.items, 32u * words);
+    OffspringKernel k = offspring_kernel(words, shape, false, false, eco, dom);
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
     std::vector<Segment> segs;
-    std::vector<uint32_t> tile_map, bucket_map;
+    std::vector<uint32_t> tiles, bucket_map;
     segs.reserve(members.size());
-    uint32_t tiles = 0, buckets = 0;
+    uint32_t total_tiles = 0, buckets = 0;
+    uint64_t offspring = 0;
     for (uint32_t si = 0; si < members.size(); ++si) {
         const PopView &v = *members[si];
-        const uint32_t nt = tiles_for(v.n, items);
-        segs.push_back(segment_at(v.base, v.L, v.n, nt, tiles, v.nbuckets, buckets));
-        tile_map.insert(tile_map.end(), nt, si);
+        const uint32_t nt = tiles_for(v.n, shape);
+        segs.push_back(segment_at(v.base, v.L, v.n, nt, total_tiles, v.nbuckets, buckets));
+        tiles.push_back(nt);
         bucket_map.insert(bucket_map.end(), v.nbuckets, si);
-        tiles += nt;
+        total_tiles += nt;
         buckets += v.nbuckets;
+        offspring += v.n;
     }
-    if (group_table_bytes((uint32_t)segs.size(), tiles, buckets) > table_capacity)
+    const uint32_t G = std::max(1u, std::min(k.resident, kMaxGridBlocks));
+    const uint32_t min_run = std::max(1u, kMinRunOffspring / tile_size(shape.block, shape.items));
+    std::vector<Run> runs;
+    std::vector<uint32_t> block_runs;
+    schedule_runs(tiles, G, min_run, runs, block_runs);
+    if (group_table_bytes((uint32_t)segs.size(), offspring, buckets) > table_capacity)
         return fail(SPG_ERR_INVALID, "launch table does not fit its buffer");
-    const size_t off_tiles = align_up(segs.size() * sizeof(Segment), 256);
-    const size_t off_buckets = off_tiles + align_up((size_t)tiles * 4, 256);
+    const size_t off_runs = align_up(segs.size() * sizeof(Segment), 256);
+    const size_t off_block = off_runs + align_up(runs.size() * sizeof(Run), 256);
+    const size_t off_buckets = off_block + align_up((size_t)(kMaxGridBlocks + 1) * 4, 256);
     cudaError_t e = cudaMemcpy(table, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(table + off_tiles, tile_map.data(), tile_map.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(table + off_runs, runs.data(), runs.size() * sizeof(Run), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(table + off_block, block_runs.data(), block_runs.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(table + off_buckets, bucket_map.data(), bucket_map.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload launch table");
     gl = GenLaunch{};
     gl.offspring = k;
-    gl.compact = compact_kernel();
+    gl.compact = compact_kernel(words);
     gl.args.segs = reinterpret_cast<const Segment *>(table);
-    gl.args.tile_seg = reinterpret_cast<const uint32_t *>(table + off_tiles);
+    gl.args.runs = reinterpret_cast<const Run *>(table + off_runs);
+    gl.args.block_runs = reinterpret_cast<const uint32_t *>(table + off_block);
     gl.args.bucket_seg = reinterpret_cast<const uint32_t *>(table + off_buckets);
     gl.args.nsegs = (uint32_t)segs.size();
-    if (segs.size() == 1) gl.args.one = segs[0];
-    gl.args.total_tiles = tiles;
+    if (segs.size() == 1) {
+        // one member: contiguous shares of its tiles per block (no run table)
+        gl.args.one = segs[0];
+        gl.args.nsegs = 1;
+    }
+    gl.args.total_tiles = total_tiles;
     gl.args.total_buckets = buckets;
-    gl.blocks = std::min(tiles, k.resident);
+    apply_kernel(k, gl.args);
+    gl.blocks = segs.size() == 1 ? std::min(total_tiles, G) : G;
     gl.buckets = buckets;
     return SPG_OK;
 }
@@ -474,6 +602,11 @@ int view_init(const PopView &v, const PopParams &prm, const uint32_t *init_genot
         rc = launch_founders(v.words, geno0, surv0, v.n, prm.key0, prm.key1, prm.rep, p0_q32, v.stream);
     }
     if (rc != SPG_OK) return fail(rc, "founder launch failed");
+    if (v.L.dense) {  // every founder survives: the dense parents are the founders in index order
+        rc = launch_dense_gather(v.words, geno0, nullptr, v.n, reinterpret_cast<uint32_t *>(v.base + v.L.dense),
+                                 v.stream);
+        if (rc != SPG_OK) return fail(rc, "dense-parent launch failed");
+    }
     if (v.L.weighted) {  // every founder is a potential parent, in index order
         rc = launch_survivor_bins(reinterpret_cast<const PopParams *>(v.base + v.L.params), v.words, geno0, nullptr,
                                   v.n, v.n, reinterpret_cast<unsigned long long *>(v.base + v.L.survw), v.stream);

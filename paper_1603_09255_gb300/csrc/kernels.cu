@@ -1,18 +1,16 @@
-// Device kernels of the per-generation update (sm_103a).
+// Device kernels of the per-generation update (sm_103a) other than the
+// offspring kernel (offspring.cuh): the continuous-allele generation kernel,
+// the compaction kernel that closes every generation, and the set-up kernels
+// (founders, survivor words of weighted parents, state resets).
 //
 // A generation of every population in a launch group is two launches
 // (Fig. 1 A-F of the paper):
-//   k_offspring  persistent: each resident block walks a contiguous range of
-//                tiles of kBlock*ITEMS offspring.  Per offspring it draws both
-//                parents from the previous survivors (A), forms the gametes
-//                by crossover masks and mutation XOR (B), sums the additive
-//                phenotype with bit-plane popcounts (C) and decides survival
-//                from the threshold table (D); it writes the child records,
-//                the alive bitmap, per-bucket survivor counts and exact
-//                integer statistics.  The parents' survivor indices are
-//                fetched two tiles ahead and their records are staged into
-//                shared memory with cp.async one tile ahead, so the random
-//                gathers overlap the arithmetic of the tile in hand;
+//   k_offspring  (offspring.cuh) draws both parents of every offspring from
+//                the previous survivors (A), forms the gametes by crossover
+//                masks and mutation XOR (B), sums the genetic value (C) and
+//                decides survival from the threshold table (D); it writes the
+//                child records, the alive bitmap, per-bucket survivor counts
+//                and exact integer statistics;
 //   k_compact    one block per bucket of kBucket offspring: turns the bitmap
 //                into the ordered survivor list (E) with a two-level scan
 //                (earlier buckets' counts + a block scan), and the block that
@@ -28,272 +26,11 @@
 #include <climits>
 #include <cstdint>
 
+#include "device_common.cuh"
 #include "spegg_internal.h"
-
-// Minimum resident blocks per SM requested from the compiler for the
-// offspring kernel (a register cap: 65536 / (256 * SPG_MIN_BLOCKS) per thread).
-#ifndef SPG_MIN_BLOCKS
-#define SPG_MIN_BLOCKS 2
-#endif
 
 namespace spg {
 namespace {
-
-// ---------------------------------------------------------------- Philox
-// Philox4x32-10 from its published definition (Salmon, Moraes, Dror, Shaw,
-// "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of
-// (c0,c1,c2,c3) -> (hi(B*c2)^c1^k0, lo(B*c2), hi(A*c0)^c3^k1, lo(A*c0)),
-// the key advanced by the Weyl increments between rounds.
-__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
-    constexpr uint32_t A = 0xD2511F53u, B = 0xCD9E8D57u;
-    constexpr uint32_t WA = 0x9E3779B9u, WB = 0xBB67AE85u;
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint32_t hi0 = __umulhi(A, c.x), lo0 = A * c.x;
-        const uint32_t hi1 = __umulhi(B, c.z), lo1 = B * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += WA;
-        k1 += WB;
-    }
-    return c;
-}
-
-__device__ __forceinline__ uint32_t lane_of(const uint4 &d, int lane) {
-    return lane == 0 ? d.x : lane == 1 ? d.y : lane == 2 ? d.z : d.w;
-}
-
-// ------------------------------------------------- relaxed gpu-scope access
-__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ double ld_relaxed_f64(const double *p) {
-    double v;
-    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// --------------------------------------------------- packed record access
-template <int W>
-__device__ __forceinline__ void load_record(const uint32_t *__restrict__ p, uint32_t (&r)[2 * W]) {
-    if constexpr (W == 1) {
-        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
-        r[0] = v.x;
-        r[1] = v.y;
-    } else {
-#pragma unroll
-        for (int q = 0; q < W / 2; ++q) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p) + q);
-            r[4 * q + 0] = v.x;
-            r[4 * q + 1] = v.y;
-            r[4 * q + 2] = v.z;
-            r[4 * q + 3] = v.w;
-        }
-    }
-}
-
-template <int W>
-__device__ __forceinline__ void store_record(uint32_t *__restrict__ p, const uint32_t (&r)[2 * W]) {
-    if constexpr (W == 1) {
-        *reinterpret_cast<uint2 *>(p) = make_uint2(r[0], r[1]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < W / 2; ++q)
-            reinterpret_cast<uint4 *>(p)[q] = make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-    }
-}
-
-// Flip K distinct uniformly drawn allele positions (per-locus mutation,
-// S2 "Genetics").  Rare path; indices are resolved by unrolled compares so
-// the record stays in registers.
-template <int W>
-__device__ __forceinline__ void mutate(uint32_t (&c)[2 * W], uint32_t k, uint32_t j, uint32_t g, uint32_t rep,
-                                    uint32_t k0, uint32_t k1) {
-    uint32_t seen[2 * W];
-#pragma unroll
-    for (int w = 0; w < 2 * W; ++w) seen[w] = 0u;
-    uint32_t chosen = 0;
-    for (uint32_t a4 = 0; a4 < kMutDraws / 4 && chosen < k; ++a4) {
-        const uint4 d = philox(make_uint4(j, g, rep, (kMutPos << 24) | a4), k0, k1);
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            if (chosen < k) {
-                const uint32_t pos = __umulhi(lane_of(d, l), 64u * W);  // [0, 2L)
-                const uint32_t wi = pos >> 5, bit = 1u << (pos & 31u);
-                bool dup = false;
-#pragma unroll
-                for (int w = 0; w < 2 * W; ++w)
-                    if ((uint32_t)w == wi) dup = (seen[w] & bit) != 0u;
-                if (!dup) {
-#pragma unroll
-                    for (int w = 0; w < 2 * W; ++w)
-                        if ((uint32_t)w == wi) {
-                            seen[w] |= bit;
-                            c[w] ^= bit;
-                        }
-                    ++chosen;
-                }
-            }
-        }
-    }
-}
-
-// Linkage map in shared memory (see LinkParams) for one population.
-struct LinkSmem {
-    const uint32_t *cdf, *cum;
-    const uint8_t *chrom;
-    const uint16_t *first, *clast;
-    const uint32_t *guide;
-    uint32_t kmax, nchrom;
-};
-
-template <int W>
-__device__ __forceinline__ void toggle_bit(uint32_t (&t)[W], uint32_t pos) {
-#pragma unroll
-    for (int w = 0; w < W; ++w)
-        if ((uint32_t)w == (pos >> 5)) t[w] ^= 1u << (pos & 31u);
-}
-
-// Origin mask of one gamete under the linkage map (bit set: the locus comes
-// from the parent's haplotype 1): every chromosome whose coin is 1 and every
-// crossover flips the loci from its start to the chromosome's end.  Each
-// flip is two toggles (at the first flipped locus and one past the last); a
-// crossover toggles its start and flips its chromosome's parity bit, and the
-// end toggles, which cancel in pairs, are applied once per chromosome whose
-// coin and parity differ.  A prefix XOR over the L bits turns the toggles
-// into the mask.
-template <int W>
-__device__ __forceinline__ void linked_mask(const LinkSmem &lk, uint32_t j, uint32_t g, uint32_t rep, uint32_t pi,
-                                            uint32_t k0, uint32_t k1, uint32_t (&m)[W]) {
-    constexpr uint32_t L = 32u * W;
-    const uint4 d0 = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8)), k0, k1);
-    uint32_t t[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) t[w] = 0u;
-    uint32_t par0 = 0, par1 = 0, par2 = 0;  // crossovers per chromosome, mod 2 (chromosomes 0-31, 32-63, 64-95)
-    uint32_t K = 0;
-    if (lk.kmax != 0u && d0.x >= lk.cdf[0]) {  // K = #{i < kmax : cdf[i] <= u} by bisection (the CDF is non-decreasing)
-        K = 1u;
-#pragma unroll
-        for (uint32_t step = 16u; step > 0u; step >>= 1)
-            if (K + step <= lk.kmax && lk.cdf[K + step - 1u] <= d0.x) K += step;
-    }
-    uint4 d = d0;
-    for (uint32_t a = 0; a < K; ++a) {
-        if ((a & 3u) == 0u) d = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8) | (1u + a / 4u)), k0, k1);
-        const uint32_t u = lane_of(d, (int)(a & 3u));
-        // interval I = #{l <= L-2 : cum[l] <= u} and its chromosome: the guide
-        // entry of u's top bits when no boundary lies inside that bucket, one
-        // comparison when one does, a forward search otherwise
-        const uint32_t ge = lk.guide[u >> (32 - kLinkGuideBits)], nb = ge >> 26;
-        uint32_t I = ge & 0xFFu, ch = (ge >> 8) & 0x7Fu;
-        if (nb == 1u) {
-            if (lk.cum[I] <= u) {
-                ++I;
-                ch = (ge >> 15) & 0x7Fu;
-            }
-        } else if (nb > 1u) {
-            while (I + 1u < L && lk.cum[I] <= u) ++I;
-            ch = lk.chrom[I];
-        }
-        toggle_bit<W>(t, I);
-        const uint32_t cb = 1u << (ch & 31u);
-        par0 ^= ch < 32u ? cb : 0u;
-        par1 ^= (ch >= 32u && ch < 64u) ? cb : 0u;
-        par2 ^= ch >= 64u ? cb : 0u;
-    }
-    for (uint32_t c = 0; c < lk.nchrom; ++c) {
-        const uint32_t coin = ((c < 32u ? d0.y : c < 64u ? d0.z : d0.w) >> (c & 31u)) & 1u;
-        const uint32_t par = ((c < 32u ? par0 : c < 64u ? par1 : par2) >> (c & 31u)) & 1u;
-        if (coin) toggle_bit<W>(t, lk.first[c]);
-        if ((coin ^ par) && lk.clast[c] + 1u < L) toggle_bit<W>(t, lk.clast[c] + 1u);
-    }
-    uint32_t carry = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        uint32_t x = t[w];
-        x ^= x << 1;
-        x ^= x << 2;
-        x ^= x << 4;
-        x ^= x << 8;
-        x ^= x << 16;
-        x ^= 0u - carry;
-        m[w] = x;
-        carry = x >> 31;
-    }
-}
-
-// Additive phenotype (Fig. 1C, eq. S2-phenval) with effects in offset
-// binary: e_l = e_min + sum_b 2^b * bit_b(e_l - e_min), so
-// raw = e_min * (copies) + sum_b 2^b * popc(plane_b & copies).
-// Words of plane b (W consecutive words, 8-byte aligned for W = 2 and
-// 16-byte aligned for W >= 4) in one or two vector shared-memory loads.
-template <int W>
-__device__ __forceinline__ void plane_words(const uint32_t *s_planes, uint32_t b, uint32_t (&pl)[W]) {
-    if constexpr (W == 1) {
-        pl[0] = s_planes[b];
-    } else if constexpr (W == 2) {
-        const uint2 v = reinterpret_cast<const uint2 *>(s_planes)[b];
-        pl[0] = v.x;
-        pl[1] = v.y;
-    } else {
-#pragma unroll
-        for (int q = 0; q < W / 4; ++q) {
-            const uint4 v = reinterpret_cast<const uint4 *>(s_planes)[b * (W / 4) + q];
-            pl[4 * q + 0] = v.x;
-            pl[4 * q + 1] = v.y;
-            pl[4 * q + 2] = v.z;
-            pl[4 * q + 3] = v.w;
-        }
-    }
-}
-
-// Additive phenotype (Fig. 1C, eq. S2-phenval) with effects in offset
-// binary: e_l = e_min + sum_b 2^b * bit_b(e_l - e_min), so
-// raw = e_min * (copies) + sum_b 2^b * popc(plane_b & copies).
-template <int W>
-__device__ __forceinline__ int32_t phenotype(const uint32_t (&c)[2 * W], const uint32_t *s_planes,
-                                             uint32_t nplanes, int32_t e_min, uint32_t &allele,
-                                             uint32_t &het) {
-    uint32_t total = 0, hz = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        total += __popc(c[w]) + __popc(c[W + w]);
-        hz += __popc(c[w] ^ c[W + w]);
-    }
-    int32_t raw = e_min * (int32_t)total;
-#pragma unroll 4
-    for (uint32_t b = 0; b < nplanes; ++b) {
-        uint32_t pl[W];
-        plane_words<W>(s_planes, b, pl);
-        int32_t cnt = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) cnt += __popc(pl[w] & c[w]) + __popc(pl[w] & c[W + w]);
-        raw += cnt << b;
-    }
-    allele = total;
-    het = hz;
-    return raw;
-}
-
-// Dominance part of the genetic value: heterozygous loci x = h0 ^ h1 add
-// their deviations, d_min * popc(x) + sum_b 2^b * popc(dplane_b & x)
-// (zero when the population has no dominance: d_min = 0, no planes).
-template <int W>
-__device__ __forceinline__ int32_t dominance_part(const uint32_t (&c)[2 * W], const uint32_t *s_dplanes,
-                                                  uint32_t ndplanes, int32_t d_min, uint32_t het) {
-    int32_t raw = d_min * (int32_t)het;
-    for (uint32_t b = 0; b < ndplanes; ++b) {
-        uint32_t pl[W];
-        plane_words<W>(s_dplanes, b, pl);
-        int32_t cnt = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) cnt += __popc(pl[w] & (c[w] ^ c[W + w]));
-        raw += cnt << b;
-    }
-    return raw;
-}
 
 // ------------------------------------------------------ ecology (Fig. 1F)
 __device__ double resource_update(double R, double r, double K, unsigned long long C) {
@@ -354,29 +91,6 @@ __device__ __forceinline__ void clear_acc(StatAcc *a) {
     a->allele = 0;
     a->mn = INT_MAX;
     a->mx = INT_MIN;
-}
-
-// --------------------------------------------------- warp reductions
-// Exact warp sums of per-lane integers through redux.sync on 16-bit limbs
-// (every limb sum stays far below 2^32; the top limb carries the sign).
-__device__ __forceinline__ long long warp_sum_i64(long long v) {
-    const uint32_t l0 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)v & 0xFFFFu);
-    const uint32_t l1 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(v >> 16) & 0xFFFFu);
-    const uint32_t l2 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(v >> 32) & 0xFFFFu);
-    const int l3 = __reduce_add_sync(0xFFFFFFFFu, (int)(v >> 48));
-    return ((long long)l3 << 48) + ((long long)l2 << 32) + ((long long)l1 << 16) + (long long)l0;
-}
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-    unsigned long long r = 0;
-#pragma unroll
-    for (int q = 3; q >= 0; --q)
-        r = (r << 16) + __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(v >> (16 * q)) & 0xFFFFu);
-    return r;
-}
-__device__ __forceinline__ unsigned long long shfl_sum_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
 }
 
 // Close generation g of one population (run by one full warp while the
@@ -459,462 +173,6 @@ __device__ void commit_state(DevState *st, uint32_t g) {
     st->R = R;
     st->done = 0;
     st->gen = g;
-}
-
-struct PopNow {
-    uint32_t gen, S, f;
-    bool active;
-};
-
-__device__ __forceinline__ PopNow read_state(const DevState *st) {
-    PopNow s;
-    s.gen = ld_relaxed_u32(&st->gen);
-    s.S = ld_relaxed_u32(&st->S);
-    s.f = ld_relaxed_u32(&st->f);
-    const int32_t status = (int32_t)ld_relaxed_u32(reinterpret_cast<const uint32_t *>(&st->status));
-    const uint32_t target = ld_relaxed_u32(&st->target);
-    s.active = s.S > 0u && status == SPG_OK && s.gen < target;
-    return s;
-}
-
-// ------------------------------------------------------- async copies
-__device__ __forceinline__ void cp_async_16(uint32_t saddr, const void *g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_8(uint32_t saddr, const void *g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Shared-memory staging of parent records: a ring of kStages stages; per
-// stage, item, parent (0 mother, 1 father) and chunk q one chunk per thread,
-// chunks of consecutive threads adjacent (conflict-free 8/16-byte accesses),
-// followed by each item's survival and mutation-count draws.  A thread only
-// ever reads the slots it wrote itself, so the ring needs no block barrier.
-template <int W, int ITEMS>
-struct Staging {
-    static constexpr int kChunkBytes = (W == 1) ? 8 : 16;
-    static constexpr int kChunks = (W == 1) ? 1 : W / 2;  // per record
-    static constexpr uint32_t kRecBytes = (uint32_t)ITEMS * 2u * kChunks * kBlock * kChunkBytes;
-    static constexpr uint32_t kDrawBytes = (uint32_t)ITEMS * kBlock * 8u;
-    static constexpr uint32_t kStageBytes = kRecBytes + kDrawBytes;
-    // as many stages (2..4) as fit in ~110 KB, so two blocks share an SM
-    static constexpr int kStages = (4u * kStageBytes <= 112640u) ? 4 : (3u * kStageBytes <= 112640u) ? 3 : 2;
-    static constexpr uint32_t kBytes = (uint32_t)kStages * kStageBytes;
-    __device__ static __forceinline__ uint32_t offset(int stage, int it, int parent, int q, int tid) {
-        return (uint32_t)stage * kStageBytes +
-               ((((uint32_t)it * 2u + (uint32_t)parent) * kChunks + (uint32_t)q) * kBlock + (uint32_t)tid) *
-                   kChunkBytes;
-    }
-    __device__ static __forceinline__ uint32_t draw_offset(int stage, int it, int tid) {
-        return (uint32_t)stage * kStageBytes + kRecBytes + ((uint32_t)it * kBlock + (uint32_t)tid) * 8u;
-    }
-};
-
-// Parents of one tile: indices into the previous generation and the
-// survival / mutation-count draws of each item.
-template <int ITEMS>
-struct TileDraws {
-    uint32_t mom[ITEMS], dad[ITEMS], u_surv[ITEMS], u_mut[ITEMS];
-};
-
-struct SegCtx {
-    const PopParams *P;
-    const uint32_t *par;
-    uint32_t *chi;
-    const uint32_t *sin;
-    uint32_t *alive;
-    uint32_t *bucket_now;
-    const unsigned long long *survw;   // weighted parents: [2][n] survivor index | role threshold << 32
-    uint16_t *obin;                    // weighted parents: bins of the offspring formed
-    uint32_t n, S, f, g, rep, k0, k1, kmax, nplanes, shift, ndplanes;
-    int32_t e_min, bias, d_min;
-    bool has_eco;
-};
-
-// Weighted parents (pi = 0 mother, 1 father) by bounded rejection sampling:
-// proposal k draws a uniform survivor rank and an acceptance value (lanes
-// 2(k%2), 2(k%2)+1 of Philox sub pi<<8 | k/2) and is taken when the
-// survivor's bin threshold is certain or above the value; the last proposal
-// stands if all kMateAttempts are rejected.  Proposals go in pairs (one
-// Philox block), both roles together, so four gathers are in flight at once;
-// the first accepted proposal in order is the parent, as if they were tried
-// one at a time.  A gathered word carries the survivor's threshold for the
-// role (looked up once per survivor by the compaction), so a proposal is one
-// 8-byte read and a comparison.
-static_assert(kMateAttempts % 2 == 0, "whole Philox blocks of proposals");
-
-// Proposals k and k+1 of one role: whether one was taken, and the parent (the
-// first taken, else proposal k+1).
-__device__ __forceinline__ bool weighted_pair(const uint4 &d, unsigned long long e0, unsigned long long e1,
-                                              uint32_t &parent) {
-    const uint32_t t0 = (uint32_t)(e0 >> 32), t1 = (uint32_t)(e1 >> 32);
-    const bool a0 = t0 == kCertain || d.y < t0, a1 = t1 == kCertain || d.w < t1;
-    parent = a0 ? (uint32_t)e0 : (uint32_t)e1;
-    return a0 || a1;
-}
-
-__device__ __forceinline__ void weighted_parents(const SegCtx &c, uint32_t j, uint32_t &mom, uint32_t &dad) {
-    bool open_m = true, open_f = true;
-    for (uint32_t k = 0; k < kMateAttempts && (open_m || open_f); k += 2) {
-        const uint32_t sub = (kMateW << 24) | (k >> 1);
-        uint4 dm = make_uint4(0u, 0u, 0u, 0u), df = dm;
-        unsigned long long em0 = 0, em1 = 0, ef0 = 0, ef1 = 0;
-        if (open_m) {
-            dm = philox(make_uint4(j, c.g, c.rep, sub), c.k0, c.k1);
-            em0 = __ldcg(c.survw + __umulhi(dm.x, c.S));
-            em1 = __ldcg(c.survw + __umulhi(dm.z, c.S));
-        }
-        if (open_f) {
-            df = philox(make_uint4(j, c.g, c.rep, sub | (1u << 8)), c.k0, c.k1);
-            ef0 = __ldcg(c.survw + c.n + __umulhi(df.x, c.S));
-            ef1 = __ldcg(c.survw + c.n + __umulhi(df.z, c.S));
-        }
-        if (open_m) open_m = !weighted_pair(dm, em0, em1, mom);
-        if (open_f) open_f = !weighted_pair(df, ef0, ef1, dad);
-    }
-}
-
-template <int ITEMS, bool WEIGHTED = false>
-__device__ __forceinline__ void draw_parents(const SegCtx &c, uint32_t base, int tid, TileDraws<ITEMS> &d) {
-#pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-        const uint32_t j = base + (uint32_t)(it * kBlock + tid);
-        d.mom[it] = d.dad[it] = d.u_surv[it] = d.u_mut[it] = 0u;
-        if (j < c.n) {
-            const uint4 r = philox(make_uint4(j, c.g, c.rep, kMate << 24), c.k0, c.k1);
-            // survivor indices through L2 only: random 4-byte reads would
-            // evict the threshold table from L1
-            if constexpr (WEIGHTED) {
-                weighted_parents(c, j, d.mom[it], d.dad[it]);
-            } else {
-                d.mom[it] = __ldcg(c.sin + __umulhi(r.x, c.S));
-                d.dad[it] = __ldcg(c.sin + __umulhi(r.y, c.S));
-            }
-            d.u_surv[it] = r.z;
-            d.u_mut[it] = r.w;
-        }
-    }
-}
-
-template <int W, int ITEMS>
-__device__ __forceinline__ void stage_parents(const SegCtx &c, uint32_t base, int tid, const TileDraws<ITEMS> &d,
-                                              unsigned char *s_dyn, uint32_t s_base, int stage) {
-    using St = Staging<W, ITEMS>;
-#pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-        const uint32_t j = base + (uint32_t)(it * kBlock + tid);
-        if (j < c.n) {
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const uint32_t *src = c.par + (size_t)(p ? d.dad[it] : d.mom[it]) * (2 * W);
-#pragma unroll
-                for (int q = 0; q < St::kChunks; ++q) {
-                    const uint32_t sa = s_base + St::offset(stage, it, p, q, tid);
-                    if constexpr (W == 1) cp_async_8(sa, src);
-                    else cp_async_16(sa, src + 4 * q);
-                }
-            }
-            *reinterpret_cast<uint2 *>(s_dyn + St::draw_offset(stage, it, tid)) =
-                make_uint2(d.u_surv[it], d.u_mut[it]);
-        }
-    }
-}
-
-template <int W, int ITEMS>
-__device__ __forceinline__ void read_parent(const unsigned char *s_dyn, int stage, int it, int p, int tid,
-                                            uint32_t (&r)[2 * W]) {
-    using St = Staging<W, ITEMS>;
-    if constexpr (W == 1) {
-        const uint2 v = *reinterpret_cast<const uint2 *>(s_dyn + St::offset(stage, it, p, 0, tid));
-        r[0] = v.x;
-        r[1] = v.y;
-    } else {
-#pragma unroll
-        for (int q = 0; q < St::kChunks; ++q) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(s_dyn + St::offset(stage, it, p, q, tid));
-            r[4 * q + 0] = v.x;
-            r[4 * q + 1] = v.y;
-            r[4 * q + 2] = v.z;
-            r[4 * q + 3] = v.w;
-        }
-    }
-}
-
-struct ThreadStats {
-    long long sum_raw = 0, sum_raw_s = 0;
-    unsigned long long sum_raw2 = 0, cons = 0;
-    uint32_t het = 0, allele = 0;
-    int mn = INT_MAX, mx = INT_MIN;
-};
-
-// One tile: gametes (B), phenotype (C), survival (D), bitmap (E, first half).
-template <int W, int ITEMS, bool LINKED, bool WEIGHTED>
-__device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t base, int tid, int lane, int warp,
-                                                   const unsigned char *s_dyn, int stage, const uint32_t *s_planes,
-                                                   const uint32_t *s_cdf, ThreadStats &ts, const LinkSmem &lk,
-                                                   const uint32_t *s_dplanes) {
-    constexpr int NW = kBlock / 32;
-    using St = Staging<W, ITEMS>;
-    uint32_t alive_count = 0;  // the warp's survivors (same in every lane)
-#pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-        const uint32_t j = base + (uint32_t)(it * kBlock + tid);
-        bool alive = false;
-        if (j < c.n) {
-            const uint2 u = *reinterpret_cast<const uint2 *>(s_dyn + St::draw_offset(stage, it, tid));
-            uint32_t pm[2 * W], pf[2 * W], ch[2 * W];
-            read_parent<W, ITEMS>(s_dyn, stage, it, 0, tid, pm);
-            read_parent<W, ITEMS>(s_dyn, stage, it, 1, tid, pf);
-            if constexpr (LINKED) {
-                // (B) gametes under the linkage map
-                uint32_t mm[W], mf[W];
-                linked_mask<W>(lk, j, c.g, c.rep, 0u, c.k0, c.k1, mm);
-                linked_mask<W>(lk, j, c.g, c.rep, 1u, c.k0, c.k1, mf);
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    ch[w] = (pm[w] & ~mm[w]) | (pm[W + w] & mm[w]);
-                    ch[W + w] = (pf[w] & ~mf[w]) | (pf[W + w] & mf[w]);
-                }
-            } else {
-            // (B) gametes: stream q = 2w + parent is lane q%4 of sub q/4
-#pragma unroll
-            for (int q4 = 0; q4 < (2 * W + 3) / 4; ++q4) {
-                const uint4 d = philox(make_uint4(j, c.g, c.rep, (kRecomb << 24) | (uint32_t)q4), c.k0, c.k1);
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    const int q = 4 * q4 + l;
-                    if (q < 2 * W) {
-                        const int w = q >> 1;
-                        const uint32_t m = lane_of(d, l);
-                        if ((q & 1) == 0) ch[w] = (pm[w] & ~m) | (pm[W + w] & m);
-                        else ch[W + w] = (pf[w] & ~m) | (pf[W + w] & m);
-                    }
-                }
-            }
-            }
-            // (B) mutation count from the CDF (none below its first entry,
-            // the common case), positions on the rare path
-            if (c.kmax != 0u && u.y >= s_cdf[0]) {
-                uint32_t k = 0;
-                for (uint32_t i = 0; i < c.kmax; ++i) k += (u.y >= s_cdf[i]) ? 1u : 0u;
-                mutate<W>(ch, k, j, c.g, c.rep, c.k0, c.k1);
-            }
-            store_record<W>(c.chi + (size_t)j * (2 * W), ch);
-
-            // (C) phenotype, (D) survival
-            uint32_t allele, hz;
-            int32_t raw = phenotype<W>(ch, s_planes, c.nplanes, c.e_min, allele, hz);
-            raw += dominance_part<W>(ch, s_dplanes, c.ndplanes, c.d_min, hz);  // hz is set by the line above
-            const long long v = (long long)raw + (long long)c.bias;
-            const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> c.shift, (long long)(kBins - 1));
-            if constexpr (WEIGHTED) c.obin[j] = (uint16_t)bin;
-            uint32_t thr = __ldg(&c.P->table[bin]);
-            if (c.f != kCertain) thr = __umulhi(thr, c.f);
-            alive = (thr == kCertain) || (u.x < thr);
-
-            ts.sum_raw += raw;
-            ts.sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
-            ts.mn = min(ts.mn, raw);
-            ts.mx = max(ts.mx, raw);
-            ts.het += hz;
-            ts.allele += allele;
-            if (alive) {
-                ts.sum_raw_s += raw;
-                if (c.has_eco) ts.cons += __ldg(&c.P->attack[bin]);
-            }
-        }
-        // (E, first half) alive bitmap word (base + it*kBlock + 32*warp)/32
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, alive);
-        if (lane == 0) c.alive[(base >> 5) + (uint32_t)(it * NW + warp)] = bal;
-        alive_count += __popc(bal);
-    }
-    return alive_count;
-}
-
-// --------------------------------------------- offspring kernel (Fig. 1A-D)
-template <int W, int ITEMS, bool LINKED, bool WEIGHTED>
-__global__ void __launch_bounds__(kBlock, SPG_MIN_BLOCKS) k_offspring(const __grid_constant__ GenArgs a) {
-    constexpr int NW = kBlock / 32;
-    constexpr uint32_t TILE = (uint32_t)(kBlock * ITEMS);
-    static_assert(kBucket % TILE == 0, "tiles must not straddle compaction buckets");
-    extern __shared__ __align__(16) unsigned char s_dyn[];
-    __shared__ __align__(16) uint32_t s_planes[kMaxPlanes * W];
-    __shared__ __align__(16) uint32_t s_dplanes[kMaxPlanes * W];
-    __shared__ uint32_t s_cdf[kMaxKmax];
-    __shared__ long long s_ll[2][NW];
-    __shared__ unsigned long long s_ull[2][NW];
-    __shared__ uint32_t s_u32[3][NW];
-    __shared__ int s_mm[2][NW];
-    constexpr int LK = LINKED ? 1 : 0;  // linkage-map tables only in the linked variant
-    __shared__ uint32_t s_lcdf[LK * kMaxKmax + 1], s_lcum[LK * kMaxLoci + 1];
-    __shared__ uint8_t s_lchrom[LK * kMaxLoci + 1];
-    __shared__ uint16_t s_lfirst[LK * kMaxChrom + 1], s_lclast[LK * kMaxChrom + 1];
-    __shared__ uint32_t s_lguide[LK * kLinkGuide + 1];
-    LinkSmem lk{s_lcdf, s_lcum, s_lchrom, s_lfirst, s_lclast, s_lguide, 0u, 0u};
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(s_dyn);
-    const uint32_t T = a.total_tiles, G = gridDim.x;
-    uint32_t t = (uint32_t)(((unsigned long long)T * blockIdx.x) / G);
-    const uint32_t t_end = (uint32_t)(((unsigned long long)T * (blockIdx.x + 1)) / G);
-    if (t >= t_end) return;
-    uint32_t si = a.nsegs == 1u ? 0u : __ldg(a.tile_seg + t);
-
-    while (t < t_end) {
-        const Segment &sg = a.nsegs == 1u ? a.one : a.segs[si];
-        const uint32_t seg_end = min(t_end, sg.tile_begin + sg.ntiles);
-        const PopNow now = read_state(sg.state);
-        if (now.active) {
-            SegCtx c;
-            c.P = sg.prm;
-            c.n = sg.n;
-            c.S = now.S;
-            c.f = now.f;
-            c.g = now.gen + 1u;
-            c.par = sg.geno[now.gen & 1u];
-            c.chi = sg.geno[(now.gen + 1u) & 1u];
-            c.sin = sg.surv[now.gen & 1u];
-            c.alive = sg.alive;
-            c.survw = sg.survw;
-            c.obin = sg.obin;
-            c.bucket_now = sg.bucket_sum + (c.g & 1u) * sg.nbuckets;
-            uint32_t *bucket_next = sg.bucket_sum + ((c.g + 1u) & 1u) * sg.nbuckets;
-            c.rep = c.P->rep;
-            c.k0 = c.P->key0;
-            c.k1 = c.P->key1;
-            c.kmax = c.P->kmax;
-            c.nplanes = c.P->nplanes;
-            c.shift = c.P->shift;
-            c.e_min = c.P->e_min;
-            c.d_min = c.P->d_min;
-            c.ndplanes = c.P->ndplanes;
-            c.bias = c.P->bias;
-            c.has_eco = c.P->has_eco != 0u;
-
-            __syncthreads();  // the previous population's tables are no longer read
-            for (uint32_t i = tid; i < c.nplanes * W; i += kBlock) s_planes[i] = c.P->planes[i];
-            for (uint32_t i = tid; i < c.ndplanes * W; i += kBlock) s_dplanes[i] = c.P->dplanes[i];
-            if (tid < kMaxKmax) s_cdf[tid] = (uint32_t)tid < c.kmax ? c.P->cdf[tid] : 0u;
-            if constexpr (LINKED) {
-                const LinkParams *lp = c.P->link;
-                lk.kmax = lp->kmax;
-                lk.nchrom = lp->nchrom;
-                for (uint32_t i = tid; i < 32u * W; i += kBlock) {
-                    s_lcum[i] = lp->cum[i];
-                    s_lchrom[i] = lp->chrom[i];
-                }
-                if (tid < kMaxKmax) s_lcdf[tid] = lp->cdf[tid];
-                for (uint32_t i = tid; i < (uint32_t)kLinkGuide; i += kBlock) s_lguide[i] = lp->guide[i];
-                if (tid < kMaxChrom) {
-                    s_lfirst[tid] = lp->first[tid];
-                    s_lclast[tid] = lp->clast[tid];
-                }
-            }
-            __syncthreads();
-
-            const uint32_t lt0 = t - sg.tile_begin, lt1 = seg_end - sg.tile_begin;
-            ThreadStats ts;
-            uint32_t warp_alive = 0, bucket_alive = 0, bucket_cur = (lt0 * TILE) / kBucket;
-
-            // software pipeline over the block's tiles: parent records (and
-            // each item's draws) are staged kStages-1 tiles ahead; survivor
-            // indices are fetched two iterations before they are staged.
-            // Every iteration commits one cp.async group (empty near the end),
-            // so waiting for all but the newest R groups completes tile lt's.
-            using St = Staging<W, ITEMS>;
-            constexpr int R = St::kStages - 1;
-            TileDraws<ITEMS> dA, dB;
-            for (int k = 0; k < R; ++k) {
-                const uint32_t tk = lt0 + (uint32_t)k;
-                if (tk < lt1) {
-                    draw_parents<ITEMS, WEIGHTED>(c, tk * TILE, tid, dA);
-                    stage_parents<W, ITEMS>(c, tk * TILE, tid, dA, s_dyn, s_base, k);
-                }
-                cp_async_commit();
-            }
-            if (lt0 + R < lt1) draw_parents<ITEMS, WEIGHTED>(c, (lt0 + R) * TILE, tid, dA);
-            if (lt0 + R + 1 < lt1) draw_parents<ITEMS, WEIGHTED>(c, (lt0 + R + 1) * TILE, tid, dB);
-            int stage = 0;
-            for (uint32_t lt = lt0; lt < lt1; ++lt) {
-                const uint32_t base = lt * TILE;
-                const int ahead = stage == 0 ? R : stage - 1;  // (stage + R) % kStages
-                if (lt + R < lt1) stage_parents<W, ITEMS>(c, base + R * TILE, tid, dA, s_dyn, s_base, ahead);
-                cp_async_commit();
-                dA = dB;
-                if (lt + R + 2 < lt1) draw_parents<ITEMS, WEIGHTED>(c, base + (R + 2) * TILE, tid, dB);
-                cp_async_wait<R>();
-                if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
-                const uint32_t bkt = base / kBucket;
-                if (bkt != bucket_cur) {
-                    if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
-                    bucket_alive = 0;
-                    bucket_cur = bkt;
-                }
-                const uint32_t cnt =
-                    offspring_tile<W, ITEMS, LINKED, WEIGHTED>(c, base, tid, lane, warp, s_dyn, stage, s_planes, s_cdf,
-                                                               ts, lk, s_dplanes);
-                bucket_alive += cnt;
-                warp_alive += cnt;
-                stage = stage + 1 == St::kStages ? 0 : stage + 1;
-            }
-            cp_async_wait<0>();
-            if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
-
-            // statistics of this block's tiles: exact warp sums, one atomic
-            // per field into one of the population's accumulator copies
-            const long long w_raw = warp_sum_i64(ts.sum_raw), w_raw_s = warp_sum_i64(ts.sum_raw_s);
-            const unsigned long long w_raw2 = warp_sum_u64(ts.sum_raw2), w_cons = warp_sum_u64(ts.cons);
-            const uint32_t w_het = __reduce_add_sync(0xFFFFFFFFu, ts.het);
-            const uint32_t w_allele = __reduce_add_sync(0xFFFFFFFFu, ts.allele);
-            const int w_mn = __reduce_min_sync(0xFFFFFFFFu, ts.mn), w_mx = __reduce_max_sync(0xFFFFFFFFu, ts.mx);
-            if (lane == 0) {
-                s_ll[0][warp] = w_raw;
-                s_ll[1][warp] = w_raw_s;
-                s_ull[0][warp] = w_raw2;
-                s_ull[1][warp] = w_cons;
-                s_u32[0][warp] = w_het;
-                s_u32[1][warp] = w_allele;
-                s_u32[2][warp] = warp_alive;
-                s_mm[0][warp] = w_mn;
-                s_mm[1][warp] = w_mx;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                long long a0 = 0, a1 = 0;
-                unsigned long long b0 = 0, b1 = 0, hz = 0, al = 0, sv = 0;
-                int m0 = INT_MAX, m1 = INT_MIN;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    a0 += s_ll[0][w];
-                    a1 += s_ll[1][w];
-                    b0 += s_ull[0][w];
-                    b1 += s_ull[1][w];
-                    hz += s_u32[0][w];
-                    al += s_u32[1][w];
-                    sv += s_u32[2][w];
-                    m0 = min(m0, s_mm[0][w]);
-                    m1 = max(m1, s_mm[1][w]);
-                }
-                StatAcc *acc = sg.acc + blockIdx.x % kAccCopies;
-                atomicAdd(&acc->s, sv);
-                atomicAdd(reinterpret_cast<unsigned long long *>(&acc->sum_raw), (unsigned long long)a0);
-                atomicAdd(reinterpret_cast<unsigned long long *>(&acc->sum_raw_s), (unsigned long long)a1);
-                atomicAdd(&acc->sum_raw2, b0);
-                if (b1) atomicAdd(&acc->cons, b1);
-                atomicAdd(&acc->het, hz);
-                atomicAdd(&acc->allele, al);
-                atomicMin(&acc->mn, m0);
-                atomicMax(&acc->mx, m1);
-            }
-        }
-        t = seg_end;
-        ++si;
-    }
 }
 
 // ------------------------------------------------ continuous allelic values
@@ -1223,30 +481,63 @@ __global__ void k_founders_cont(const PopParams *__restrict__ P, uint32_t *__res
 }
 
 // ---------------------------------------- compaction kernel (Fig. 1E, 1F)
-// One block of kCompactThreads threads per bucket of kBucket offspring: its
-// first kBucketWords threads write the survivors' indices, in offspring order,
-// at offset (survivors of all earlier buckets) + (block scan of the bitmap
-// words' popcounts); in a population's first bucket the extra warp closes the
+// One block per bucket of kBucket offspring.  Its first kBucketWords threads
+// read the bucket's bitmap words and the survivor counts of all earlier
+// buckets and scan the words' popcounts; then kCompactCopyThreads threads
+// (8 warps, 16 bitmap words each) write every survivor's index, in offspring
+// order, at its rank = (survivors of earlier buckets) + (survivors before it
+// in the bucket), and, for populations with a dense parent buffer, its record
+// at the same rank (the parents of the next generation, read by rank without
+// an index hop).  In a population's first bucket an extra warp closes the
 // generation meanwhile (finalize_warp).  The block that finishes the last
 // bucket commits the new state.  Every load that does not depend on the
 // population state is issued together with it (both parities of the bucket
 // counts are summed; the state picks one).
 __device__ __forceinline__ void compaction_barrier() {
-    asm volatile("bar.sync 1, %0;" ::"n"(kBucketWords) : "memory");  // the kBucketWords compaction threads
+    asm volatile("bar.sync 1, %0;" ::"n"(kCompactCopyThreads) : "memory");  // the compaction threads
 }
 
+// A record of 2W words read through L2 and written with whole-sector stores.
+template <int W>
+__device__ __forceinline__ void copy_record(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst) {
+    uint32_t r[2 * W];
+    if constexpr (W == 1) {
+        const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(src));
+        r[0] = v.x;
+        r[1] = v.y;
+    } else if constexpr (W == 2) {
+        const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(src));
+        r[0] = v.x;
+        r[1] = v.y;
+        r[2] = v.z;
+        r[3] = v.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q)
+            asm volatile("ld.global.cg.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(r[8 * q]), "=r"(r[8 * q + 1]), "=r"(r[8 * q + 2]), "=r"(r[8 * q + 3]),
+                           "=r"(r[8 * q + 4]), "=r"(r[8 * q + 5]), "=r"(r[8 * q + 6]), "=r"(r[8 * q + 7])
+                         : "l"(src + 8 * q));
+    }
+    store_record<W>(dst, r);
+}
+
+template <int W>
 __device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
-    constexpr int NW = kBucketWords / 32;
+    constexpr int NW = kBucketWords / 32;                     // warps that scan the bitmap words
+    constexpr int WPW = kBucketWords / (kCompactCopyThreads / 32);  // bitmap words per copying warp
     __shared__ uint32_t s_warp[NW];
     __shared__ uint32_t s_prev[NW];
+    __shared__ uint32_t s_bits[kBucketWords], s_incl[kBucketWords];
     __shared__ uint32_t s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool closer = tid >= (int)kBucketWords;  // the generation-closing warp
+    const bool closer = tid >= (int)kCompactCopyThreads;  // the generation-closing warp
+    const bool scanner = tid < (int)kBucketWords;
     const uint32_t valid_words = (sg.n + 31u) >> 5;
     const uint32_t w = b * kBucketWords + (uint32_t)tid;
-    const uint32_t bits = (!closer && w < valid_words) ? __ldcg(sg.alive + w) : 0u;
+    const uint32_t bits = (scanner && w < valid_words) ? __ldcg(sg.alive + w) : 0u;
     uint32_t prev0 = 0, prev1 = 0;
-    for (uint32_t i = (uint32_t)tid; !closer && i < b; i += kBucketWords) {
+    for (uint32_t i = (uint32_t)tid; scanner && i < b; i += kBucketWords) {
         prev0 += __ldcg(sg.bucket_sum + i);
         prev1 += __ldcg(sg.bucket_sum + sg.nbuckets + i);
     }
@@ -1257,41 +548,47 @@ __device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
         if (b == 0u) finalize_warp(sg, sg.prm, g, now.f);
         __threadfence();
     } else {
-    const uint32_t prev = __reduce_add_sync(0xFFFFFFFFu, (g & 1u) ? prev1 : prev0);
-    const uint32_t cnt = __popc(bits);
-    uint32_t incl = cnt;
+        if (scanner) {
+            const uint32_t prev = __reduce_add_sync(0xFFFFFFFFu, (g & 1u) ? prev1 : prev0);
+            uint32_t incl = __popc(bits);
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    if (lane == 0) s_prev[warp] = prev;
-    compaction_barrier();
-    uint32_t excl = incl - cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            s_bits[tid] = bits;
+            s_incl[tid] = incl;
+            if (lane == 31) s_warp[warp] = incl;
+            if (lane == 0) s_prev[warp] = prev;
+        }
+        compaction_barrier();
+        uint32_t before = 0;  // survivors of all earlier buckets
 #pragma unroll
-    for (int q = 0; q < NW; ++q) {
-        excl += q < warp ? s_warp[q] : 0u;
-        excl += s_prev[q];
-    }
-    uint32_t *__restrict__ sout = sg.surv[(now.gen + 1u) & 1u];
-    const uint32_t lt = (1u << lane) - 1u;
-    const uint32_t w0 = b * kBucketWords + (uint32_t)warp * 32u;
+        for (int q = 0; q < NW; ++q) before += s_prev[q];
+        uint32_t *__restrict__ sout = sg.surv[g & 1u];
+        const uint32_t *__restrict__ chi = sg.geno[g & 1u];
+        uint32_t *__restrict__ dense = sg.dense;
+        const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll 4
-    for (int k = 0; k < 32; ++k) {
-        const uint32_t word = __shfl_sync(0xFFFFFFFFu, bits, k);
-        const uint32_t r0 = __shfl_sync(0xFFFFFFFFu, excl, k);
-        if ((word >> lane) & 1u) {
-            const uint32_t rank = r0 + __popc(word & lt), idx = (w0 + (uint32_t)k) * 32u + (uint32_t)lane;
-            sout[rank] = idx;
-            if (sg.survw) {  // the survivor's acceptance thresholds as mother and as father
-                const uint32_t bin = __ldcg(sg.obin + idx);
-                const WeightParams *wt = sg.prm->weights;
-                sg.survw[rank] = (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[0][bin]) << 32);
-                sg.survw[sg.n + rank] = (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[1][bin]) << 32);
+        for (int k = 0; k < WPW; ++k) {
+            const int q = warp * WPW + k;  // bitmap word of the bucket
+            const uint32_t word = s_bits[q];
+            uint32_t r0 = before + s_incl[q] - __popc(word);
+#pragma unroll
+            for (int v = 0; v < NW; ++v) r0 += v < q / 32 ? s_warp[v] : 0u;
+            if ((word >> lane) & 1u) {
+                const uint32_t rank = r0 + __popc(word & lt), idx = (b * kBucketWords + (uint32_t)q) * 32u + lane;
+                sout[rank] = idx;
+                if (dense) copy_record<W>(chi + (size_t)idx * (2 * W), dense + (size_t)rank * (2 * W));
+                if (sg.survw) {  // the survivor's acceptance thresholds as mother and as father
+                    const uint32_t bin = __ldcg(sg.obin + idx);
+                    const WeightParams *wt = sg.prm->weights;
+                    sg.survw[rank] = (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[0][bin]) << 32);
+                    sg.survw[sg.n + rank] =
+                        (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[1][bin]) << 32);
+                }
             }
         }
-    }
     }
     // every block has read the state by now (its values fed the stores
     // above), and the closing warp of bucket 0 has published the next state
@@ -1304,14 +601,26 @@ __device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
     }
 }
 
-__global__ void __launch_bounds__(kCompactThreads) k_compact(const __grid_constant__ GenArgs a) {
+template <int W>
+__global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const __grid_constant__ GenArgs a) {
     const uint32_t bkt = blockIdx.x;
     if (a.nsegs == 1u) {
-        compact_bucket(a.one, bkt);
+        compact_bucket<W>(a.one, bkt);
     } else {
         const Segment &sg = a.segs[__ldg(a.bucket_seg + bkt)];
-        compact_bucket(sg, bkt - sg.bucket_begin);
+        compact_bucket<W>(sg, bkt - sg.bucket_begin);
     }
+}
+
+// dense[r] = geno[surv[r]] (surv null: r) for r < S: the dense parent buffer
+// of founders or of a restored generation.
+template <int W>
+__global__ void k_dense_gather(const uint32_t *__restrict__ geno, const uint32_t *__restrict__ surv, uint32_t S,
+                               uint32_t *__restrict__ dense) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= S) return;
+    const uint32_t idx = surv ? surv[r] : r;
+    copy_record<W>(geno + (size_t)idx * (2 * W), dense + (size_t)r * (2 * W));
 }
 
 // ---------------------------------------------------------- founders
@@ -1398,13 +707,64 @@ __global__ void k_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S
 
 }  // namespace
 
-bool supported_items(uint32_t words, uint32_t items) {
-    if (!(items == 1 || items == 2 || items == 4)) return false;
-    return !(words == 8 && items == 4);
-}
-uint32_t tile_size(uint32_t items) { return (uint32_t)kBlock * items; }
+OffspringKernel offspring_kernel_w1(uint32_t block, uint32_t items, bool linked, bool weighted);
+OffspringKernel offspring_kernel_w2(uint32_t block, uint32_t items, bool linked, bool weighted);
+OffspringKernel offspring_kernel_w4(uint32_t block, uint32_t items, bool linked, bool weighted);
+OffspringKernel offspring_kernel_w8(uint32_t block, uint32_t items, bool linked, bool weighted);
 
-GenKernel compact_kernel() { return &k_compact; }
+bool supported_shape(uint32_t words, uint32_t block, uint32_t items) {
+    if (!(block == 128 || block == 256 || block == 512)) return false;
+    return words <= 2 ? (items == 1 || items == 2) : items == 1;
+}
+
+uint32_t tile_size(uint32_t block, uint32_t items) { return block * items; }
+
+GenKernel compact_kernel(uint32_t words) {
+    switch (words) {
+        case 2: return &k_compact<2>;
+        case 4: return &k_compact<4>;
+        case 8: return &k_compact<8>;
+        default: return &k_compact<1>;  // and populations without a dense buffer (no record copies)
+    }
+}
+
+int launch_dense_gather(uint32_t words, const uint32_t *geno, const uint32_t *surv, uint32_t S, uint32_t *dense,
+                        void *stream) {
+    if (S == 0) return SPG_OK;
+    const dim3 grid((S + 255) / 256), block(256);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (words) {
+        case 1: k_dense_gather<1><<<grid, block, 0, s>>>(geno, surv, S, dense); break;
+        case 2: k_dense_gather<2><<<grid, block, 0, s>>>(geno, surv, S, dense); break;
+        case 4: k_dense_gather<4><<<grid, block, 0, s>>>(geno, surv, S, dense); break;
+        case 8: k_dense_gather<8><<<grid, block, 0, s>>>(geno, surv, S, dense); break;
+        default: return SPG_ERR_INVALID;
+    }
+    return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
+}
+
+OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom) {
+    OffspringKernel k;
+    switch (words) {
+        case 1: k = offspring_kernel_w1(shape.block, shape.items, linked, weighted); break;
+        case 2: k = offspring_kernel_w2(shape.block, shape.items, linked, weighted); break;
+        case 4: k = offspring_kernel_w4(shape.block, shape.items, linked, weighted); break;
+        case 8: k = offspring_kernel_w8(shape.block, shape.items, linked, weighted); break;
+        default: return OffspringKernel{};
+    }
+    if (!k.fn) return k;
+    // dynamic shared memory: thresholds (and attack rates when some
+    // population of the launch has an ecology), byte tables (dominance ones
+    // only when some population has dominance)
+    const uint32_t tab = eco ? (uint32_t)kBins * 8u : (uint32_t)kBins * 4u;
+    const uint32_t lut = words * 4u * (uint32_t)kLutWords * 4u;
+    k.words = words;
+    k.eco_table = eco ? 1u : 0u;
+    k.smem_lut = tab;
+    k.smem_dlut = dom ? tab + lut : 0u;
+    k.smem = tab + lut * (dom ? 2u : 1u);
+    return k;
+}
 
 OffspringKernel continuous_kernel(uint32_t n_loci) {
     OffspringKernel k;
@@ -1415,9 +775,36 @@ OffspringKernel continuous_kernel(uint32_t n_loci) {
         case 256: k.fn = &k_offspring_cont<32, kContInFlight>; break;
         default: return OffspringKernel{};
     }
+    k.block = kBlock;
+    k.items = 1;
     k.smem = 0;
-    k.resident = 0;  // not persistent: one block per 256 offspring
+    k.resident = 0;
+    k.persistent = false;  // one block per 256 offspring
     return k;
+}
+
+int prepare_offspring(OffspringKernel &k) {
+    if (!k.fn) return SPG_ERR_INVALID;
+    const void *fn = reinterpret_cast<const void *>(k.fn);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return SPG_ERR_CUDA;
+    if (k.persistent) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+        if (e != cudaSuccess) return SPG_ERR_CUDA;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)k.block, k.smem);
+    if (e != cudaSuccess || per_sm <= 0) return SPG_ERR_CUDA;
+    k.resident = (uint32_t)per_sm * (uint32_t)sms;
+    return SPG_OK;
+}
+
+void apply_kernel(const OffspringKernel &k, GenArgs &a) {
+    a.eco_table = k.eco_table;
+    a.smem_lut = k.smem_lut;
+    a.smem_dlut = k.smem_dlut;
 }
 
 int launch_founders_cont(const PopParams *prm, uint32_t n_loci, uint32_t *geno, uint32_t *surv, uint32_t n,
@@ -1432,60 +819,6 @@ int launch_founders_cont(const PopParams *prm, uint32_t n_loci, uint32_t *geno, 
         default: return SPG_ERR_INVALID;
     }
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
-}
-
-namespace {
-template <int W, int I, bool LINKED = false, bool WEIGHTED = false>
-OffspringKernel make_offspring() {
-    OffspringKernel k;
-    k.fn = &k_offspring<W, I, LINKED, WEIGHTED>;
-    k.smem = Staging<W, I>::kBytes;
-    return k;
-}
-
-template <bool LINKED, bool WEIGHTED>
-OffspringKernel variant_kernel(uint32_t words) {
-    switch (words) {
-        case 1: return make_offspring<1, 1, LINKED, WEIGHTED>();
-        case 2: return make_offspring<2, 1, LINKED, WEIGHTED>();
-        case 4: return make_offspring<4, 1, LINKED, WEIGHTED>();
-        case 8: return make_offspring<8, 1, LINKED, WEIGHTED>();
-        default: return OffspringKernel{};
-    }
-}
-}  // namespace
-
-OffspringKernel offspring_kernel(uint32_t words, uint32_t items, bool linked, bool weighted) {
-    if (linked || weighted) {  // linkage maps and weighted parents: one offspring per thread
-        if (items != 1u) return OffspringKernel{};
-        if (linked && weighted) return variant_kernel<true, true>(words);
-        return linked ? variant_kernel<true, false>(words) : variant_kernel<false, true>(words);
-    }
-#define SPG_CASE(Wv, Iv) \
-    if (words == Wv && items == Iv) return make_offspring<Wv, Iv>();
-    SPG_CASE(1, 1) SPG_CASE(1, 2) SPG_CASE(1, 4)
-    SPG_CASE(2, 1) SPG_CASE(2, 2) SPG_CASE(2, 4)
-    SPG_CASE(4, 1) SPG_CASE(4, 2) SPG_CASE(4, 4)
-    SPG_CASE(8, 1) SPG_CASE(8, 2)
-#undef SPG_CASE
-    return OffspringKernel{};
-}
-
-int prepare_offspring(OffspringKernel &k) {
-    if (!k.fn) return SPG_ERR_INVALID;
-    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k.fn),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
-    if (e != cudaSuccess) return SPG_ERR_CUDA;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k.fn), kBlock,
-                                                      k.smem);
-    if (e != cudaSuccess || per_sm <= 0) return SPG_ERR_CUDA;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return SPG_ERR_CUDA;
-    k.resident = (uint32_t)per_sm * (uint32_t)sms;
-    return SPG_OK;
 }
 
 int launch_founders(uint32_t words, uint32_t *geno, uint32_t *surv, uint32_t n, uint32_t key0, uint32_t key1,

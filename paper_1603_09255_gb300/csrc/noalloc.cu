@@ -2,10 +2,10 @@
 // caller owns, with every piece of working memory taken from a fixed array
 // in this file, so the call performs no device allocation at all.
 //
-// The working memory (parameters, state, statistics accumulators, segment
-// descriptor, alive bitmap, per-bucket survivor counts) lives in the
-// file-scope array g_noalloc_scratch below.  Host code cannot use the array's
-// name as a device address, so its address is looked up once per device with
+// The working memory (parameters, state, statistics accumulators, alive
+// bitmap, per-bucket survivor counts) lives in the file-scope array
+// g_noalloc_scratch below.  Host code cannot use the array's name as a device
+// address, so its address is looked up once per device with
 // cudaGetSymbolAddress (with that device current) and cached.
 #include <cuda_runtime.h>
 
@@ -26,8 +26,7 @@ constexpr uint32_t kMaxBuckets = SPG_NOALLOC_MAX_N / kBucket;
 constexpr size_t kOffParams = 0;
 constexpr size_t kOffState = kOffParams + align256(sizeof(PopParams));
 constexpr size_t kOffAcc = kOffState + align256(sizeof(DevState));
-constexpr size_t kOffSegment = kOffAcc + align256(sizeof(StatAcc) * kAccCopies);
-constexpr size_t kOffAlive = kOffSegment + align256(sizeof(Segment));
+constexpr size_t kOffAlive = kOffAcc + align256(sizeof(StatAcc) * kAccCopies);
 constexpr size_t kOffBuckets = kOffAlive + align256((size_t)kMaxBuckets * kBucketWords * 4);
 constexpr size_t kScratchBytes = kOffBuckets + align256((size_t)2 * kMaxBuckets * 4);
 static_assert(SPG_NOALLOC_MAX_N % kBucket == 0, "the maximum population must be a whole number of buckets");
@@ -83,7 +82,7 @@ extern "C" int spg_generation_noalloc(const spg_noalloc_generation *a, void *str
     if (rc != SPG_OK) return rc;
 
     const uint32_t W = a->n_loci / 32, g = a->generation;
-    const uint32_t items = default_items(W);
+    const Shape shape = default_shape(W);
     spg_pop_desc d{};
     d.n = a->n;
     d.n_loci = a->n_loci;
@@ -97,15 +96,15 @@ extern "C" int spg_generation_noalloc(const spg_noalloc_generation *a, void *str
     d.stats_capacity = 1;
     // host staging of the parameters without a per-call host allocation
     static thread_local PopParams prm;
-    rc = build_params(&d, items, prm);
+    rc = build_params(&d, prm);
     if (rc != SPG_OK) return rc;
     prm.stats_cap = 1;  // the caller's single statistics record
     prm.has_eco = 0;
 
-    OffspringKernel k = offspring_kernel(W, items);
+    OffspringKernel k = offspring_kernel(W, shape, false, false, false, false);
     rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
-    const uint32_t ntiles = prm.ntiles, nbuckets = bucket_count(a->n);
+    const uint32_t ntiles = tiles_for(a->n, shape), nbuckets = bucket_count(a->n);
 
     Segment seg{};
     seg.prm = reinterpret_cast<const PopParams *>(scratch + kOffParams);
@@ -126,9 +125,8 @@ extern "C" int spg_generation_noalloc(const spg_noalloc_generation *a, void *str
     seg.nbuckets = nbuckets;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // pageable sources: both copies are staged before the calls return
+    // pageable source: the copy is staged before the call returns
     cudaError_t e = cudaMemcpyAsync(scratch + kOffParams, &prm, sizeof prm, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + kOffSegment, &seg, sizeof seg, cudaMemcpyHostToDevice, s);
     // the per-bucket counts must start at zero; the rest is overwritten
     if (e == cudaSuccess) e = cudaMemsetAsync(scratch + kOffBuckets, 0, (size_t)2 * nbuckets * 4, s);
     if (e != cudaSuccess) return cuda_fail(e, "stage allocation-free generation");
@@ -139,12 +137,13 @@ extern "C" int spg_generation_noalloc(const spg_noalloc_generation *a, void *str
 
     GenLaunch gl;
     gl.offspring = k;
-    gl.compact = compact_kernel();
-    gl.args.segs = reinterpret_cast<const Segment *>(scratch + kOffSegment);
+    gl.compact = compact_kernel(W);  // no dense buffer: parents by survivor index, no record copies
+    gl.args.segs = nullptr;  // one segment: the kernels read it from their parameters
     gl.args.nsegs = 1;
     gl.args.one = seg;
     gl.args.total_tiles = ntiles;
     gl.args.total_buckets = nbuckets;
+    apply_kernel(k, gl.args);
     gl.blocks = std::min(ntiles, k.resident);
     gl.buckets = nbuckets;
     return launch_generation(gl, s);

@@ -19,7 +19,8 @@
 using namespace spg;
 
 struct spg_pop {
-    uint32_t n = 0, n_loci = 0, words = 0, items = 0, ntiles = 0, nbuckets = 0, cap = 0;
+    uint32_t n = 0, n_loci = 0, words = 0, ntiles = 0, nbuckets = 0, cap = 0;
+    Shape shape;
     uint64_t seed = 0;
     uint32_t rep = 0;
     cudaStream_t stream = nullptr;
@@ -48,34 +49,44 @@ struct spg_pop {
 
 namespace {
 
-// Point the launch at the population's single segment with `items` offspring
-// per thread (uploads the device copy of the segment; synchronous).
-int configure_launch(spg_pop *p, uint32_t items) {
-    const bool continuous = p->host_prm->continuous != 0u;
-    OffspringKernel k = continuous ? continuous_kernel(p->n_loci)
-                                   : offspring_kernel(p->words, items, p->host_prm->linked != 0u,
-                                                      p->host_prm->weighted != 0u);
-    if (continuous && items != 1u) return fail(SPG_ERR_INVALID, "continuous allelic values run one offspring per thread");
+// Point the launch at the population's single segment with a launch shape
+// (uploads the device copy of the segment; synchronous).
+int configure_launch(spg_pop *p, const Shape &shape) {
+    const PopParams &prm = *p->host_prm;
+    const bool continuous = prm.continuous != 0u;
+    OffspringKernel k;
+    if (continuous) {
+        if (shape.block != (uint32_t)kBlock || shape.items != 1u)
+            return fail(SPG_ERR_INVALID, "continuous allelic values run 256 threads, one offspring each");
+        k = continuous_kernel(p->n_loci);
+    } else {
+        if (!supported_shape(p->words, shape.block, shape.items))
+            return fail(SPG_ERR_INVALID, "unsupported launch shape (%u threads, %u offspring per thread) for %u loci",
+                        shape.block, shape.items, p->n_loci);
+        if ((prm.linked || prm.weighted) && (shape.block != 256u || shape.items != 1u))
+            return fail(SPG_ERR_INVALID,
+                        "a population with a linkage map or parent weights runs 256 threads, one offspring each");
+        k = offspring_kernel(p->words, shape, prm.linked != 0u, prm.weighted != 0u, prm.has_eco != 0u,
+                             prm.has_dom != 0u);
+    }
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
-    p->items = items;
-    p->ntiles = (p->n + tile_size(items) - 1) / tile_size(items);
-    p->host_prm->ntiles = p->ntiles;
+    p->shape = shape;
+    p->ntiles = continuous ? (p->n + kBlock - 1) / kBlock : tiles_for(p->n, shape);
     const Segment seg = segment_at(p->arena, p->L, p->n, p->ntiles, 0, p->nbuckets, 0);
     cudaError_t e = cudaMemcpyAsync(p->arena + p->L.segment, &seg, sizeof seg, cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(p->arena + p->L.params, p->host_prm, sizeof(PopParams), cudaMemcpyHostToDevice,
-                            p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "upload segment");
     rc = view_sync(p->view());
     if (rc != SPG_OK) return rc;
+    p->gl = GenLaunch{};
     p->gl.offspring = k;
-    p->gl.compact = compact_kernel();
+    p->gl.compact = compact_kernel(p->words);
     p->gl.args.segs = reinterpret_cast<const Segment *>(p->arena + p->L.segment);
     p->gl.args.one = seg;
     p->gl.args.nsegs = 1;
     p->gl.args.total_tiles = p->ntiles;
     p->gl.args.total_buckets = p->nbuckets;
+    if (!continuous) apply_kernel(k, p->gl.args);
     p->gl.blocks = continuous ? p->ntiles : std::min(p->ntiles, k.resident);  // continuous: not persistent
     p->gl.buckets = p->nbuckets;
     p->chain.reset();
@@ -104,8 +115,9 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         delete p;
         return fail(SPG_ERR_OOM, "host allocation failed");
     }
-    const uint32_t items = default_items(p->words);
-    rc = build_params(desc, items, *p->host_prm);
+    const bool variant = desc->map_morgans || desc->mother_weights || desc->father_weights;
+    const Shape shape = (desc->allele_model == 1u || variant) ? Shape{(uint32_t)kBlock, 1u} : default_shape(p->words);
+    rc = build_params(desc, *p->host_prm);
     if (rc != SPG_OK) {
         delete p->host_prm;
         delete p;
@@ -137,7 +149,8 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         }
         p->own_stream = true;
     }
-    p->L = layout_for(p->n, p->words, p->nbuckets, p->cap, p->host_prm->weighted != 0u);
+    p->L = layout_for(p->n, p->words, p->nbuckets, p->cap, p->host_prm->weighted != 0u,
+                      p->host_prm->continuous == 0u);
     p->arena = static_cast<char *>(p->alloc.alloc(p->L.total, p->stream));
     if (!p->arena) {
         spg_destroy(p);
@@ -166,7 +179,7 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
                                             : desc->init_genotypes,
                    desc->p0_q32);
     if (rc == SPG_OK) rc = view_sync(p->view());  // the caller's arrays are read before returning
-    if (rc == SPG_OK) rc = configure_launch(p, items);
+    if (rc == SPG_OK) rc = configure_launch(p, shape);
     if (rc != SPG_OK) {
         spg_destroy(p);
         return rc;
@@ -177,7 +190,11 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
 
 int spg_set_ecology(spg_pop *p, const spg_ecology *eco) {
     if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
-    return view_set_ecology(p->view(), *p->host_prm, eco);
+    const int rc = view_set_ecology(p->view(), *p->host_prm, eco);
+    if (rc != SPG_OK) return rc;
+    // the survival table of the offspring kernel now carries attack rates
+    if (!p->host_prm->continuous && !p->gl.offspring.eco_table) return configure_launch(p, p->shape);
+    return SPG_OK;
 }
 
 int spg_step_generations(spg_pop *p, uint32_t n_gen) {
@@ -277,6 +294,13 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
     // generations about to be replayed
     if (e == cudaSuccess) e = cudaMemset(p->arena + p->L.buckets, 0, (size_t)2 * p->nbuckets * 4);
     if (e != cudaSuccess) return cuda_fail(e, "restore copy");
+    if (p->L.dense) {  // the restored survivors' records in rank order: the next generation's parents
+        const uint32_t par = h.gen & 1u;
+        rc = launch_dense_gather(p->words, reinterpret_cast<const uint32_t *>(p->arena + (par ? p->L.geno1 : p->L.geno0)),
+                                 reinterpret_cast<const uint32_t *>(p->arena + (par ? p->L.surv1 : p->L.surv0)), h.S,
+                                 reinterpret_cast<uint32_t *>(p->arena + p->L.dense), p->stream);
+        if (rc != SPG_OK) return fail(rc, "dense-parent launch failed");
+    }
     if (p->host_prm->weighted) {  // the restored survivors' bins, from their records
         const uint32_t par = h.gen & 1u;
         rc = launch_survivor_bins(reinterpret_cast<const PopParams *>(p->arena + p->L.params), p->words,
@@ -291,19 +315,30 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
 }
 
 int spg_set_tiling(spg_pop *p, uint32_t items) {
-    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
-    if (!supported_items(p->words, items))
-        return fail(SPG_ERR_INVALID, "items_per_thread must be 1, 2 or 4 (1 or 2 for 256 loci); got %u", items);
-    if ((p->host_prm->linked || p->host_prm->weighted || p->host_prm->continuous) && items != 1u)
-        return fail(SPG_ERR_INVALID, "a population with a linkage map or parent weights runs one offspring per thread");
-    const int rc = view_sync(p->view());
-    if (rc != SPG_OK) return rc;
-    return configure_launch(p, items);
+    spg_launch_shape sh{256u, items};
+    return spg_set_launch_shape(p, &sh);
 }
 
 int spg_get_tiling(spg_pop *p, uint32_t *items) {
     if (!p || !items) return fail(SPG_ERR_INVALID, "NULL argument");
-    *items = p->items;
+    *items = p->shape.items;
+    return SPG_OK;
+}
+
+int spg_set_launch_shape(spg_pop *p, const spg_launch_shape *shape) {
+    if (!p || !shape) return fail(SPG_ERR_INVALID, "NULL argument");
+    Shape sh;
+    int rc = shape_from_abi(p->host_prm->continuous ? 0u : p->words, shape, sh);
+    if (rc != SPG_OK) return rc;
+    rc = view_sync(p->view());
+    if (rc != SPG_OK) return rc;
+    return configure_launch(p, sh);
+}
+
+int spg_get_launch_shape(spg_pop *p, spg_launch_shape *out) {
+    if (!p || !out) return fail(SPG_ERR_INVALID, "NULL argument");
+    out->threads_per_block = p->gl.offspring.block;
+    out->items_per_thread = p->gl.offspring.items;
     return SPG_OK;
 }
 

@@ -118,7 +118,7 @@ int admit(spg_server *s, Job &j) {
     const uint32_t words = j.desc.n_loci / 32;
     j.prm.reset(new (std::nothrow) PopParams());
     if (!j.prm) return fail(SPG_ERR_OOM, "host allocation failed");
-    int rc = build_params(&j.desc, 1, *j.prm);
+    int rc = build_params(&j.desc, *j.prm);
     if (rc != SPG_OK) return rc;
     j.v.base = j.arena;
     j.v.n = j.desc.n;
@@ -145,15 +145,19 @@ int rebuild(spg_server *s) {
     if (rc != SPG_OK) return rc;
     for (int gi = 0; gi < kGroups; ++gi) {
         std::vector<const PopView *> views;
-        uint32_t tiles = 0, buckets = 0;
+        uint64_t offspring = 0;
+        uint32_t buckets = 0;
+        bool eco = false, dom = false;
         for (uint64_t id : s->resident) {
             const Job &j = *s->jobs[id];
             if (group_of(j.v.words) != (uint32_t)gi) continue;
             views.push_back(&j.v);
-            tiles += tiles_for(j.v.n, 1);
+            offspring += j.v.n;
             buckets += j.v.nbuckets;
+            eco |= j.prm->has_eco != 0u;
+            dom |= j.prm->has_dom != 0u;
         }
-        const size_t need = group_table_bytes((uint32_t)views.size(), tiles, buckets);
+        const size_t need = group_table_bytes((uint32_t)views.size(), offspring, buckets);
         if (need > s->table_cap[gi]) {
             if (s->table[gi]) s->alloc.release(s->table[gi], s->stream);
             s->table[gi] = nullptr;
@@ -163,7 +167,8 @@ int rebuild(spg_server *s) {
             if (!s->table[gi]) return fail(SPG_ERR_OOM, "launch table allocation failed");
             s->table_cap[gi] = cap;
         }
-        rc = build_group_launch(views, 1u << gi, 1, s->table[gi], s->table_cap[gi], s->gl[gi]);
+        rc = build_group_launch(views, 1u << gi, default_shape(1u << gi), eco, dom, s->table[gi], s->table_cap[gi],
+                                s->gl[gi]);
         if (rc != SPG_OK) return rc;
     }
     s->dirty = false;

@@ -14,6 +14,8 @@
 namespace spg {
 
 constexpr uint32_t kGraphChunk = 32;          // generations per cached graph
+constexpr uint32_t kMinRunOffspring = 8192;   // offspring of a run of a launch group (members that have them)
+constexpr uint32_t kMaxGridBlocks = 8192;     // offspring blocks of a launch group, at most
 constexpr uint32_t kCheckpointMagic = 0x43475053u;  // "SPGC"
 
 struct CheckpointHeader {
@@ -33,7 +35,7 @@ struct Allocator {
 
 // Byte offsets of one population's buffers inside its arena.
 struct PopLayout {
-    size_t params, state, acc, geno0, geno1, surv0, surv1, alive, buckets, ring, segment, link;
+    size_t params, state, acc, geno0, geno1, dense, surv0, surv1, alive, buckets, ring, segment, link;
     size_t weights, obin, survw;  // weighted parents only (0 otherwise)
     bool weighted;
     size_t total;
@@ -73,23 +75,32 @@ void effect_planes(const int16_t *effects, uint32_t n_loci, PopParams &prm);
 uint32_t factor_q32_host(double R, double R_half);
 size_t align_up(size_t x, size_t a);
 int validate_desc(const spg_pop_desc *d);
-int build_params(const spg_pop_desc *d, uint32_t items, PopParams &prm);
+int build_params(const spg_pop_desc *d, PopParams &prm);
 // Linkage-map tables from map_morgans[L] (validated; see spegg.h).
 int build_link(const double *map_morgans, uint32_t n_loci, LinkParams &lp);
 // Acceptance thresholds from the mother and father weight tables (NULL: uniform).
 int build_weights(const uint32_t *mother_w, const uint32_t *father_w, WeightParams &wp);
-PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap, bool weighted = false);
+// dense: the population has a dense parent buffer (biallelic records; not
+// the continuous-allele model, whose generation kernel reads parents by index).
+PopLayout layout_for(uint32_t n, uint32_t words, uint32_t nbuckets, uint32_t cap, bool weighted = false,
+                     bool dense = true);
 Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, uint32_t tile_begin,
                    uint32_t nbuckets, uint32_t bucket_begin);
 uint32_t bucket_count(uint32_t n);
-uint32_t default_items(uint32_t words);
+Shape default_shape(uint32_t words);
+constexpr uint32_t kAutotuneCandidates = SPG_AUTOTUNE_CANDIDATES;  // launch shapes timed per group
+Shape autotune_candidate(uint32_t words, uint32_t c);
+int shape_from_abi(uint32_t words, const spg_launch_shape *in, Shape &out);
 int launch_generation(const GenLaunch &gl, cudaStream_t stream);
-size_t group_table_bytes(uint32_t members, uint32_t tiles, uint32_t buckets);
-uint32_t tiles_for(uint32_t n, uint32_t items);
-// Segment table and tile/bucket maps of one launch group, uploaded into
+size_t group_table_bytes(uint32_t members, uint64_t offspring, uint32_t buckets);
+uint32_t tiles_for(uint32_t n, const Shape &shape);
+void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_run, std::vector<Run> &runs,
+                   std::vector<uint32_t> &block_runs);
+// Segment table, runs and bucket map of one launch group, uploaded into
 // `table` (device memory; synchronous), and the group's launch description.
-int build_group_launch(const std::vector<const PopView *> &members, uint32_t words, uint32_t items, char *table,
-                       size_t table_capacity, GenLaunch &gl);
+// eco / dom: some member has an ecology / dominance deviations.
+int build_group_launch(const std::vector<const PopView *> &members, uint32_t words, const Shape &shape, bool eco,
+                       bool dom, char *table, size_t table_capacity, GenLaunch &gl);
 int view_sync(const PopView &v);
 int view_state(const PopView &v, DevState &st);
 int view_set_state(const PopView &v, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,

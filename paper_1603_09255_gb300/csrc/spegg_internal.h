@@ -14,14 +14,17 @@ constexpr int kMaxKmax = 32;      // entries of the Binomial(2L, mu) CDF table
 constexpr int kMutDraws = 64;     // position draws tried per offspring
 constexpr int kMaxPlanes = 16;    // bit planes of the offset-binary effects
 constexpr int kMaxWords = 8;      // W = L/32 <= 8
-constexpr int kBlock = 256;       // threads per block of the offspring kernel
+constexpr int kBlock = 256;       // threads per block of the continuous-allele kernel
+constexpr int kLutWords = 256;    // entries of one byte table (one per byte value)
 constexpr uint32_t kBucket = 4096;                 // offspring per compaction bucket
 constexpr uint32_t kBucketWords = kBucket / 32;    // bitmap words per bucket = compaction threads
-constexpr uint32_t kCompactThreads = kBucketWords + 32;  // + one warp that closes the generation
+constexpr uint32_t kCompactCopyThreads = 256;  // threads that write a bucket's survivors (8 warps)
+constexpr uint32_t kCompactThreads = kCompactCopyThreads + 32;  // + one warp that closes the generation
 constexpr uint32_t kCertain = 0xFFFFFFFFu;
 constexpr int kAccCopies = 16;    // copies of the statistics accumulators (spread atomics)
 
 constexpr int kMaxLoci = 256;
+constexpr int kMaxLutBytes = kMaxLoci / 8;  // byte positions of a haplotype (L / 8)
 constexpr int kMaxChrom = 96;            // chromosomes of a linkage map
 constexpr uint32_t kLinkSites = 65536;   // crossover opportunities per gamete
 constexpr double kMaxMapMorgans = 16.0;  // total length of a linkage map
@@ -64,6 +67,12 @@ struct alignas(16) PopParams {
     uint32_t dplanes[kMaxPlanes * kMaxWords];// dominance deviations, offset binary like planes
     int32_t d_min;                          // dominance = d_min + sum_b 2^b * dplane_b
     uint32_t ndplanes;                      // 0: additive genetic value
+    uint32_t has_dom;                       // some locus has a non-zero dominance deviation
+    // byte tables of the genetic value: lut[k * 256 + v] is the sum of the
+    // effects of loci 8k .. 8k+7 whose bit is set in v (L / 8 tables), dlut
+    // the same for the dominance deviations (applied to h0 ^ h1)
+    alignas(16) int32_t lut[kMaxLutBytes * kLutWords];
+    alignas(16) int32_t dlut[kMaxLutBytes * kLutWords];
     uint32_t cdf[kMaxKmax];                 // Binomial(2L, mu) CDF, Q32
     int32_t e_min;                          // effects = e_min + sum_b 2^b * plane_b
     uint32_t nplanes;
@@ -87,6 +96,11 @@ struct alignas(16) PopParams {
     uint32_t weighted;           // parents drawn by weight (weights != null)
     const WeightParams *weights;
 };
+
+// the offspring kernel copies these tables with 16-byte cp.async
+static_assert(offsetof(PopParams, table) % 16 == 0 && offsetof(PopParams, attack) % 16 == 0 &&
+                  offsetof(PopParams, lut) % 16 == 0 && offsetof(PopParams, dlut) % 16 == 0,
+              "tables copied in 16-byte chunks");
 
 // Mutable per-population state (device global memory).
 struct alignas(16) DevState {
@@ -118,6 +132,8 @@ struct alignas(128) StatAcc {
 struct alignas(16) Segment {
     const PopParams *prm;
     uint32_t *geno[2];                // ping-pong genotype buffers [N * 2W]
+    uint32_t *dense;                  // the survivors' records in rank order [N * 2W] (parents of the next
+                                      // generation), or null: parents through the survivor list
     uint32_t *surv[2];                // ping-pong survivor lists [N]
     uint32_t *alive;                  // alive bitmap of the generation being formed [nbuckets * kBucketWords]
     uint32_t *bucket_sum;             // survivors per bucket, by generation parity [2][nbuckets]
@@ -132,41 +148,73 @@ struct alignas(16) Segment {
     uint32_t ntiles;
     uint32_t bucket_begin;            // first launch-wide bucket of this population
     uint32_t nbuckets;
-    uint32_t pad[3];
+    uint32_t pad;
+};
+
+// One run of an offspring block: tiles tile0 .. tile0 + count - 1 of segment
+// seg.  The population's tiles are split into `shares` runs (this is run
+// `share`); each run prefetches the same share of the population's parent
+// records into L2.
+struct alignas(16) Run {
+    uint32_t seg, tile0, count, share, shares, pad[3];
 };
 
 struct GenArgs {
     const Segment *segs;         // device array of nsegs segments (used when nsegs > 1)
-    const uint32_t *tile_seg;    // segment of each launch-wide tile (nsegs > 1)
+    const Run *runs;             // runs of all offspring blocks, block by block (nsegs > 1)
+    const uint32_t *block_runs;  // runs of block b: runs[block_runs[b] .. block_runs[b + 1]) (nsegs > 1)
     const uint32_t *bucket_seg;  // segment of each launch-wide bucket (nsegs > 1)
     uint32_t nsegs;
-    uint32_t total_tiles;
+    uint32_t total_tiles;        // tiles of the single segment (nsegs == 1: contiguous shares per block)
     uint32_t total_buckets;
-    uint32_t pad;
+    // dynamic shared memory of the offspring kernel: the survival thresholds
+    // at 0, attack rates after them when eco_table, the byte tables at
+    // smem_lut and smem_dlut (0: the launch has no dominance)
+    uint32_t eco_table;
+    uint32_t smem_lut, smem_dlut;
     Segment one;           // the segment itself when nsegs == 1 (read from kernel parameters)
 };
 
 using GenKernel = void (*)(GenArgs);
 
-// The offspring kernel for (W, items): entry, dynamic shared memory, and the
-// number of blocks resident on the device (its persistent grid).
-struct OffspringKernel {
-    GenKernel fn = nullptr;
-    uint32_t smem = 0;
-    uint32_t resident = 0;
+// Launch shape of the offspring kernel: threads per block and offspring per
+// thread.  Results never depend on it.
+struct Shape {
+    uint32_t block = 256, items = 1;
 };
 
-// Kernels of kernels.cu (host-callable handles).
-OffspringKernel offspring_kernel(uint32_t words, uint32_t items, bool linked = false, bool weighted = false);
+// The offspring kernel of one launch: entry, shape, dynamic shared-memory
+// layout and size, and the number of blocks resident on the device (its
+// persistent grid).  persistent = false: the continuous-allele kernel, one
+// block per 256 offspring and no dynamic shared memory.
+struct OffspringKernel {
+    GenKernel fn = nullptr;
+    uint32_t words = 0, block = 256, items = 1;
+    uint32_t eco_table = 0, smem_lut = 0, smem_dlut = 0;
+    uint32_t smem = 0;
+    uint32_t resident = 0;
+    bool persistent = true;
+};
+
+// Offspring kernels (offspring_w*.cu) and the other kernels (kernels.cu).
+bool supported_shape(uint32_t words, uint32_t block, uint32_t items);
+// The offspring kernel of a shape; eco: some population of the launch has an
+// ecology (the survival table carries attack rates), dom: some has dominance.
+OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom);
 int prepare_offspring(OffspringKernel &k);  // sets the shared-memory limit, fills `resident`
-GenKernel compact_kernel();
-bool supported_items(uint32_t words, uint32_t items);
-uint32_t tile_size(uint32_t items);
+GenKernel compact_kernel(uint32_t words);  // the compaction kernel for records of 2W words
+uint32_t tile_size(uint32_t block, uint32_t items);
+// Copy the offspring kernel's shape and shared-memory layout into a launch.
+void apply_kernel(const OffspringKernel &k, GenArgs &a);
 // Enqueue founders: generation-0 records by Philox draws, survivors = 0..n-1.
 int launch_founders(uint32_t words, uint32_t *geno, uint32_t *surv, uint32_t n, uint32_t key0, uint32_t key1,
                     uint32_t rep, uint32_t p0_q32, void *stream);
 // Enqueue survivors = 0..n-1 only (caller-supplied founders).
 int launch_iota(uint32_t *surv, uint32_t n, void *stream);
+// Enqueue dense[r] = geno[surv[r]] for the S current survivors (records of
+// 2W words): the dense parent buffer after founders or a restore.
+int launch_dense_gather(uint32_t words, const uint32_t *geno, const uint32_t *surv, uint32_t S, uint32_t *dense,
+                        void *stream);
 // The generation kernel of a continuous-allele population (one warp per
 // offspring at a time, 256 offspring per block, no persistent grid).
 OffspringKernel continuous_kernel(uint32_t n_loci);

@@ -67,6 +67,19 @@ class spg_noalloc_generation(ctypes.Structure):
     ]
 
 
+class spg_launch_shape(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_uint32), ("items_per_thread", ctypes.c_uint32)]
+
+
+class spg_autotune_report(ctypes.Structure):
+    _fields_ = [("groups", spg_launch_shape * 4), ("best_ms", ctypes.c_float * 4), ("worst_ms", ctypes.c_float * 4),
+                ("gens_run", ctypes.c_uint32)]
+
+
+def _shape_tuple(sh: spg_launch_shape):
+    return (int(sh.threads_per_block), int(sh.items_per_thread))
+
+
 class spg_server_config(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_size_t), ("max_resident", ctypes.c_uint32),
                 ("gens_per_tick", ctypes.c_uint32)]
@@ -148,7 +161,13 @@ _SIGNATURES = {
     "spg_batch_step": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
     "spg_batch_set_tiling": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32], ctypes.c_int),
     "spg_batch_get_tiling": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
-    "spg_batch_autotune": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "spg_batch_autotune": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(spg_autotune_report)], ctypes.c_int),
+    "spg_batch_set_launch_shape": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(spg_launch_shape)],
+                                   ctypes.c_int),
+    "spg_batch_get_launch_shape": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(spg_launch_shape)],
+                                   ctypes.c_int),
+    "spg_set_launch_shape": ([ctypes.c_void_p, ctypes.POINTER(spg_launch_shape)], ctypes.c_int),
+    "spg_get_launch_shape": ([ctypes.c_void_p, ctypes.POINTER(spg_launch_shape)], ctypes.c_int),
     "spg_batch_read_stats": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p],
                              ctypes.c_int),
     "spg_batch_read_genotypes": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
@@ -386,6 +405,16 @@ class Population:
         check(lib().spg_get_tiling(self._h, ctypes.byref(v)), "spg_get_tiling")
         return v.value
 
+    def set_launch_shape(self, threads_per_block: int = 0, items_per_thread: int = 0) -> None:
+        sh = spg_launch_shape(int(threads_per_block), int(items_per_thread))
+        check(lib().spg_set_launch_shape(self._h, ctypes.byref(sh)), "spg_set_launch_shape")
+
+    def launch_shape(self):
+        """(threads per block, offspring per thread) in use."""
+        sh = spg_launch_shape()
+        check(lib().spg_get_launch_shape(self._h, ctypes.byref(sh)), "spg_get_launch_shape")
+        return _shape_tuple(sh)
+
     def synchronize(self) -> None:
         check(lib().spg_synchronize(self._h), "spg_synchronize")
 
@@ -454,10 +483,29 @@ class Batch:
         check(lib().spg_batch_get_tiling(self._h, int(n_loci), ctypes.byref(v)), "spg_batch_get_tiling")
         return v.value
 
+    def set_launch_shape(self, n_loci: int, threads_per_block: int = 0, items_per_thread: int = 0) -> None:
+        sh = spg_launch_shape(int(threads_per_block), int(items_per_thread))
+        check(lib().spg_batch_set_launch_shape(self._h, int(n_loci), ctypes.byref(sh)), "spg_batch_set_launch_shape")
+
+    def launch_shape(self, n_loci: int):
+        """(threads per block, offspring per thread) of the members with
+        n_loci loci."""
+        sh = spg_launch_shape()
+        check(lib().spg_batch_get_launch_shape(self._h, int(n_loci), ctypes.byref(sh)), "spg_batch_get_launch_shape")
+        return _shape_tuple(sh)
+
     def autotune(self, gens_per_trial: int) -> int:
-        ran = ctypes.c_uint32()
-        check(lib().spg_batch_autotune(self._h, int(gens_per_trial), ctypes.byref(ran)), "spg_batch_autotune")
-        return ran.value
+        """Time every candidate launch shape per locus-count group and keep the
+        fastest; returns the generations every member advanced.  The report
+        of the last call is kept in self.autotune_report (by L: chosen shape,
+        best and worst ms per generation)."""
+        rep = spg_autotune_report()
+        check(lib().spg_batch_autotune(self._h, int(gens_per_trial), ctypes.byref(rep)), "spg_batch_autotune")
+        self.autotune_report = {
+            32 << gi: {"shape": _shape_tuple(rep.groups[gi]), "best_ms": float(rep.best_ms[gi]),
+                       "worst_ms": float(rep.worst_ms[gi])}
+            for gi in range(4) if rep.groups[gi].threads_per_block}
+        return int(rep.gens_run)
 
     def read_stats(self, member: int, first_gen: int, count: int) -> np.ndarray:
         out = np.zeros(max(int(count), 1), STATS_DTYPE)

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_abi_version_and_status_strings():
-    assert spegg.lib().spg_abi_version() == 2
+    assert spegg.lib().spg_abi_version() == 3
     assert spegg.status_string(0) == "ok"
     assert "extinct" in spegg.status_string(1)
     assert "timed out" in spegg.status_string(-4)

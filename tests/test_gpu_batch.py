@@ -80,32 +80,46 @@ def test_batch_members_equal_oracle(member):
     assert_member_equals(b, member, so, orc.genotypes(), orc.survivors(), st)
 
 
-def test_autotune_and_tiling_do_not_change_results():
+# the candidates the autotuner times (threads per block, offspring per
+# thread): six for L = 32 and 64, three (each timed twice) for L = 128, 256
+NARROW = [(128, 1), (128, 2), (256, 1), (256, 2), (512, 1), (512, 2)]
+WIDE = [(128, 1), (256, 1), (512, 1), (128, 1), (256, 1), (512, 1)]
+
+
+def test_autotune_and_launch_shapes_do_not_change_results():
     ws = mixed_workloads(12, seed=3)
-    a = sp().Batch(ws, stats_capacity=64)
+    a = sp().Batch(ws, stats_capacity=128)
     ran = a.autotune(2)
-    assert ran == 9  # three tilings, each one untimed and two timed generations
+    assert ran == 18  # six shapes, each one untimed and two timed generations
     for L in (32, 64, 128, 256):
-        assert a.tiling(L) in ((1, 2) if L == 256 else (1, 2, 4))
+        cands = WIDE if L >= 128 else NARROW
+        assert a.launch_shape(L) in cands, L
+        rep = a.autotune_report[L]
+        assert rep["shape"] == a.launch_shape(L) and 0 < rep["best_ms"] <= rep["worst_ms"]
     a.step(30)
-    b = sp().Batch(ws, stats_capacity=64)
-    b.set_tiling(64, 4)
-    b.step(ran + 5)
-    b.set_tiling(64, 1)
-    b.set_tiling(128, 4)
-    b.step(25)
+    # the same members stepped through every candidate shape in turn
+    b = sp().Batch(ws, stats_capacity=128)
+    done = 0
+    for k in range(6):
+        for L in (32, 64, 128, 256):
+            b.set_launch_shape(L, *(WIDE if L >= 128 else NARROW)[k])
+        b.step(8)
+        done += 8
+    b.set_tiling(64, 2)
+    b.set_tiling(128, 1)
+    b.step(ran + 30 - done)
     for i in range(len(ws)):
         st = a.state(i)
         ref = b.read_stats(i, 1, st["gen"]) if st["gen"] else np.zeros(0, sp().STATS_DTYPE)
         assert_member_equals(a, i, ref, b.genotypes(i), b.survivors(i), b.state(i))
 
 
-def test_batch_rejects_invalid_member():
-    ws = mixed_workloads(4)
-    ws[2].n_loci = 48
-    with pytest.raises(sp().SpeggError) as e:
-        sp().Batch(ws)
-    assert "member 2" in str(e.value)
+def test_batch_rejects_unsupported_launch_shapes():
+    b = sp().Batch(mixed_workloads(4), stats_capacity=8)
+    for L, shape in ((32, (64, 1)), (64, (256, 4)), (256, (256, 2)), (128, (512, 2)), (48, (256, 1))):
+        with pytest.raises(sp().SpeggError):
+            b.set_launch_shape(L, *shape)
+    b.close()
 
 
 def test_batch_full_size_sampled_members_equal_oracle():
