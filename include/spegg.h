@@ -259,22 +259,25 @@ int spg_checkpoint(spg_pop *pop, void *host, size_t capacity);
 int spg_restore(spg_pop *pop, const void *host, size_t bytes);
 
 /* Launch shape of the generation kernel: threads per block (128, 256 or 512;
- * 0 = 256) and offspring per thread (1 or 2 for L <= 64, 1 for L >= 128;
- * 0 = 1).  A launch-shape choice only: every shape gives identical results.
- * Populations with a linkage map or parent weights, and continuous allelic
- * values, run 256 threads with one offspring each.  spg_get_launch_shape
- * reports the shape in use.  SPG_ERR_INVALID for an unsupported shape.
- * Waits for the stream. */
+ * 0 = 256), offspring per thread (1 or 2 for L <= 64, 1 for L >= 128; 0 = 1)
+ * and lanes per offspring (1, or 2 for L >= 128: one lane per parent, each
+ * loading that parent's record and forming the gamete it passes on; 0 = the
+ * default, 2 for L = 256 and 1 otherwise).  A launch-shape choice only: every
+ * shape gives identical results.  Populations with a linkage map or parent
+ * weights, and continuous allelic values, run 256 threads with one offspring
+ * per thread.  spg_get_launch_shape reports the shape in use.
+ * SPG_ERR_INVALID for an unsupported shape.  Waits for the stream. */
 typedef struct {
     uint32_t threads_per_block;
     uint32_t items_per_thread;
+    uint32_t lanes_per_offspring;
 } spg_launch_shape;
 
 int spg_set_launch_shape(spg_pop *pop, const spg_launch_shape *shape);
 int spg_get_launch_shape(spg_pop *pop, spg_launch_shape *out);
-/* Offspring per thread at 256 threads per block (spg_set_launch_shape with
- * {256, items_per_thread}); spg_get_tiling reports the offspring per thread
- * in use. */
+/* Offspring per thread at 256 threads per block and one lane per offspring
+ * (spg_set_launch_shape with {256, items_per_thread, 1}); spg_get_tiling
+ * reports the offspring per thread in use. */
 int spg_set_tiling(spg_pop *pop, uint32_t items_per_thread);
 int spg_get_tiling(spg_pop *pop, uint32_t *items_per_thread);
 
@@ -304,8 +307,8 @@ int spg_batch_get_tiling(spg_batch *batch, uint32_t n_loci, uint32_t *items_per_
 /* Launch-shape autotuner: for each locus-count group, runs one untimed
  * generation and then times gens_per_trial real generations with each of
  * SPG_AUTOTUNE_CANDIDATES launch shapes -- threads per block (128, 256, 512)
- * x offspring per thread (1, 2 for L <= 64; for L >= 128 each block size is
- * timed twice) -- and keeps the fastest.  Every
+ * x offspring per thread (1, 2) for L <= 64, x lanes per offspring (1, 2) for
+ * L >= 128 -- and keeps the fastest.  Every
  * member advances by the same number of generations (report->gens_run =
  * SPG_AUTOTUNE_CANDIDATES * (gens_per_trial + 1)); results do not depend on
  * the shapes chosen.  The report (may be NULL) gives each group's chosen

@@ -252,7 +252,7 @@ int spg_batch_step(spg_batch *b, uint32_t n_gen) {
 }
 
 int spg_batch_set_tiling(spg_batch *b, uint32_t n_loci, uint32_t items) {
-    spg_launch_shape sh{256u, items};
+    spg_launch_shape sh{256u, items, 1u};
     return spg_batch_set_launch_shape(b, n_loci, &sh);
 }
 
@@ -284,6 +284,7 @@ int spg_batch_get_launch_shape(spg_batch *b, uint32_t n_loci, spg_launch_shape *
     const Group &g = b->groups[group_of_words(n_loci / 32)];
     out->threads_per_block = g.members.empty() ? g.shape.block : g.gl.offspring.block;
     out->items_per_thread = g.members.empty() ? g.shape.items : g.gl.offspring.items;
+    out->lanes_per_offspring = g.members.empty() ? g.shape.lanes : g.gl.offspring.lanes;
     return SPG_OK;
 }
 
@@ -323,6 +324,7 @@ int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, spg_autotune_repor
         if (rc == SPG_OK) {
             rep.groups[gi].threads_per_block = g.gl.offspring.block;
             rep.groups[gi].items_per_thread = g.gl.offspring.items;
+            rep.groups[gi].lanes_per_offspring = g.gl.offspring.lanes;
             rep.best_ms[gi] = best_ms / (float)gens_per_trial;
             rep.worst_ms[gi] = worst_ms / (float)gens_per_trial;
         }

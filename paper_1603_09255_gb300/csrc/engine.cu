@@ -328,47 +328,50 @@ Segment segment_at(char *base, const PopLayout &L, uint32_t n, uint32_t ntiles, 
 }
 
 // Launch shapes the batch autotuner times, per locus count: threads per
-// block x offspring per thread (one offspring per thread for L >= 128, whose
-// records fill the registers; each shape timed twice there).
+// block x offspring per thread for L <= 64, threads per block x lanes per
+// offspring for L >= 128.
 Shape autotune_candidate(uint32_t words, uint32_t c) {
-    static const uint32_t narrow[kAutotuneCandidates][2] = {{128, 1}, {128, 2}, {256, 1},
-                                                             {256, 2}, {512, 1}, {512, 2}};
-    static const uint32_t wide[kAutotuneCandidates][2] = {{128, 1}, {256, 1}, {512, 1},
-                                                           {128, 1}, {256, 1}, {512, 1}};
-    const uint32_t(&e)[2] = words >= 4 ? wide[c % kAutotuneCandidates] : narrow[c % kAutotuneCandidates];
+    static const uint32_t narrow[kAutotuneCandidates][3] = {{128, 1, 1}, {128, 2, 1}, {256, 1, 1},
+                                                             {256, 2, 1}, {512, 1, 1}, {512, 2, 1}};
+    static const uint32_t wide[kAutotuneCandidates][3] = {{128, 1, 1}, {256, 1, 1}, {512, 1, 1},
+                                                           {128, 1, 2}, {256, 1, 2}, {512, 1, 2}};
+    const uint32_t(&e)[3] = words >= 4 ? wide[c % kAutotuneCandidates] : narrow[c % kAutotuneCandidates];
     Shape s;
     s.block = e[0];
     s.items = e[1];
+    s.lanes = e[2];
     return s;
 }
 
-// A caller's launch shape: 0 fields take the defaults (threads per block of
-// the locus count, one offspring per thread).  words 0: the continuous-allele
-// kernel (256 threads, one offspring each).
+// A caller's launch shape: 0 fields take the defaults of the locus count.
+// words 0: the continuous-allele kernel (256 threads, one offspring each).
 int shape_from_abi(uint32_t words, const spg_launch_shape *in, Shape &out) {
     if (words == 0) {
-        out = Shape{(uint32_t)kBlock, 1u};
+        out = Shape{(uint32_t)kBlock, 1u, 1u};
         if ((in->threads_per_block && in->threads_per_block != (uint32_t)kBlock) ||
-            (in->items_per_thread && in->items_per_thread != 1u))
+            (in->items_per_thread && in->items_per_thread != 1u) ||
+            (in->lanes_per_offspring && in->lanes_per_offspring != 1u))
             return fail(SPG_ERR_INVALID, "continuous allelic values run 256 threads, one offspring each");
         return SPG_OK;
     }
     out = default_shape(words);
     if (in->threads_per_block) out.block = in->threads_per_block;
+    if (in->lanes_per_offspring) out.lanes = in->lanes_per_offspring;
     out.items = in->items_per_thread ? in->items_per_thread : 1u;
-    if (!supported_shape(words, out.block, out.items))
+    if (!supported_shape(words, out))
         return fail(SPG_ERR_INVALID,
-                    "unsupported launch shape (%u threads, %u offspring per thread) for %u loci: threads 128, 256 or "
-                    "512; offspring per thread 1 or 2 for L <= 64, 1 for L >= 128",
-                    out.block, out.items, 32u * words);
+                    "unsupported launch shape (%u threads, %u offspring per thread, %u lanes per offspring) for %u "
+                    "loci: threads 128, 256 or 512; L <= 64: 1 lane, 1 or 2 offspring per thread; L >= 128: 1 or 2 "
+                    "lanes, 1 offspring",
+                    out.block, out.items, out.lanes, 32u * words);
     return SPG_OK;
 }
 
 Shape default_shape(uint32_t words) {
-    (void)words;
     Shape s;
     s.block = 256;
     s.items = 1;
+    s.lanes = words == 8 ? 2u : 1u;  // L = 256: a lane per parent record (two records do not fit a thread)
     return s;
 }
 
@@ -452,7 +455,7 @@ size_t group_table_bytes(uint32_t members, uint64_t offspring, uint32_t buckets)
 }
 
 uint32_t tiles_for(uint32_t n, const Shape &shape) {
-    const uint32_t t = tile_size(shape.block, shape.items);
+    const uint32_t t = tile_size(shape);
     return (n + t - 1) / t;
 }
 
@@ -501,9 +504,10 @@ int build_group_launch(const std::vector<const PopView *> &members, uint32_t wor
         gl = GenLaunch{};
         return SPG_OK;
     }
-    if (!supported_shape(words, shape.block, shape.items))
-        return fail(SPG_ERR_INVALID, "unsupported launch shape (%u threads, %u offspring per thread) for %u loci",
-                    shape.block, shape.items, 32u * words);
+    if (!supported_shape(words, shape))
+        return fail(SPG_ERR_INVALID,
+                    "unsupported launch shape (%u threads, %u offspring per thread, %u lanes per offspring) for %u loci",
+                    shape.block, shape.items, shape.lanes, 32u * words);
     OffspringKernel k = offspring_kernel(words, shape, false, false, eco, dom);
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
@@ -523,7 +527,7 @@ int build_group_launch(const std::vector<const PopView *> &members, uint32_t wor
         offspring += v.n;
     }
     const uint32_t G = std::max(1u, std::min(k.resident, kMaxGridBlocks));
-    const uint32_t min_run = std::max(1u, kMinRunOffspring / tile_size(shape.block, shape.items));
+    const uint32_t min_run = std::max(1u, kMinRunOffspring / tile_size(shape));
     std::vector<Run> runs;
     std::vector<uint32_t> block_runs;
     schedule_runs(tiles, G, min_run, runs, block_runs);

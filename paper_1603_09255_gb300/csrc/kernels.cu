@@ -707,17 +707,19 @@ __global__ void k_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S
 
 }  // namespace
 
-OffspringKernel offspring_kernel_w1(uint32_t block, uint32_t items, bool linked, bool weighted);
-OffspringKernel offspring_kernel_w2(uint32_t block, uint32_t items, bool linked, bool weighted);
-OffspringKernel offspring_kernel_w4(uint32_t block, uint32_t items, bool linked, bool weighted);
-OffspringKernel offspring_kernel_w8(uint32_t block, uint32_t items, bool linked, bool weighted);
+OffspringKernel offspring_kernel_w1(const Shape &shape, bool linked, bool weighted);
+OffspringKernel offspring_kernel_w2(const Shape &shape, bool linked, bool weighted);
+OffspringKernel offspring_kernel_w4(const Shape &shape, bool linked, bool weighted);
+OffspringKernel offspring_kernel_w8(const Shape &shape, bool linked, bool weighted);
 
-bool supported_shape(uint32_t words, uint32_t block, uint32_t items) {
-    if (!(block == 128 || block == 256 || block == 512)) return false;
-    return words <= 2 ? (items == 1 || items == 2) : items == 1;
+bool supported_shape(uint32_t words, const Shape &s) {
+    if (!(s.block == 128 || s.block == 256 || s.block == 512)) return false;
+    if (s.lanes == 2) return words >= 4 && s.items == 1;
+    if (s.lanes != 1) return false;
+    return words <= 2 ? (s.items == 1 || s.items == 2) : s.items == 1;
 }
 
-uint32_t tile_size(uint32_t block, uint32_t items) { return block * items; }
+uint32_t tile_size(const Shape &s) { return s.block * s.items / s.lanes; }
 
 GenKernel compact_kernel(uint32_t words) {
     switch (words) {
@@ -746,23 +748,22 @@ int launch_dense_gather(uint32_t words, const uint32_t *geno, const uint32_t *su
 OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom) {
     OffspringKernel k;
     switch (words) {
-        case 1: k = offspring_kernel_w1(shape.block, shape.items, linked, weighted); break;
-        case 2: k = offspring_kernel_w2(shape.block, shape.items, linked, weighted); break;
-        case 4: k = offspring_kernel_w4(shape.block, shape.items, linked, weighted); break;
-        case 8: k = offspring_kernel_w8(shape.block, shape.items, linked, weighted); break;
+        case 1: k = offspring_kernel_w1(shape, linked, weighted); break;
+        case 2: k = offspring_kernel_w2(shape, linked, weighted); break;
+        case 4: k = offspring_kernel_w4(shape, linked, weighted); break;
+        case 8: k = offspring_kernel_w8(shape, linked, weighted); break;
         default: return OffspringKernel{};
     }
     if (!k.fn) return k;
-    // dynamic shared memory: thresholds (and attack rates when some
-    // population of the launch has an ecology), byte tables (dominance ones
-    // only when some population has dominance)
-    const uint32_t tab = eco ? (uint32_t)kBins * 8u : (uint32_t)kBins * 4u;
+    // dynamic shared memory: byte tables, thresholds (and attack rates when
+    // some population of the launch has an ecology), dominance byte tables
+    // (only when some population has dominance)
     const uint32_t lut = words * 4u * (uint32_t)kLutWords * 4u;
+    const uint32_t tab = eco ? (uint32_t)kBins * 8u : (uint32_t)kBins * 4u;
     k.words = words;
     k.eco_table = eco ? 1u : 0u;
-    k.smem_lut = tab;
-    k.smem_dlut = dom ? tab + lut : 0u;
-    k.smem = tab + lut * (dom ? 2u : 1u);
+    k.smem_dlut = dom ? lut + tab : 0u;
+    k.smem = lut + tab + (dom ? lut : 0u);
     return k;
 }
 
@@ -803,7 +804,6 @@ int prepare_offspring(OffspringKernel &k) {
 
 void apply_kernel(const OffspringKernel &k, GenArgs &a) {
     a.eco_table = k.eco_table;
-    a.smem_lut = k.smem_lut;
     a.smem_dlut = k.smem_dlut;
 }
 

@@ -67,16 +67,22 @@ struct SegCtx {
     uint32_t *bucket_now;
     const unsigned long long *survw;   // weighted parents: [2][n] survivor index | role threshold << 32
     uint16_t *obin;                    // weighted parents: bins of the offspring formed
-    uint32_t lut, dlut;                // byte offsets of the byte tables in the dynamic shared memory (dlut 0: none)
+    uint32_t dlut;                     // byte offset of the dominance byte tables (0: none)
     uint32_t n, S, f, g, rep, k0, k1, kmax, shift;
     int32_t bias;
     bool eco;
 };
 
-// The dynamic shared memory of the offspring kernel: survival thresholds at 0,
-// attack rates at kBins * 4 (eco launches), byte tables at the offsets the
-// launch gives.
+// The dynamic shared memory of the offspring kernel: the byte tables of the
+// additive value at 0 (so a lookup's address is its byte value times 4 plus a
+// constant), the survival thresholds after them, the attack rates after those
+// (eco launches), the dominance byte tables at the offset the launch gives.
 extern __shared__ __align__(16) unsigned char s_dyn[];
+template <int W>
+struct SmemLayout {
+    static constexpr uint32_t kThr = 4096u * W;       // 4W byte tables of 256 int32
+    static constexpr uint32_t kAtt = kThr + kBins * 4u;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(uint32_t byte_off) {
     return *reinterpret_cast<const uint32_t *>(s_dyn + byte_off);
@@ -208,14 +214,15 @@ __device__ __forceinline__ void prefetch_parents(const uint32_t *par, uint32_t r
     }
 }
 
-// Sum of the byte-table entries of one word (four loci bytes of word w):
-// part of a haplotype's genetic value (eq. S2-phenval, per locus e_l *
-// allele), exact in int32.  lut: byte offset of the tables.
-template <int w>
-__device__ __forceinline__ int32_t byte_table_word(uint32_t lut, uint32_t x) {
+// Sum of the byte-table entries of one word x holding loci 32w .. 32w+31 (its
+// four bytes): part of a haplotype's genetic value (eq. S2-phenval, per locus
+// e_l * allele), exact in int32.  lut: byte offset of the tables (0 for the
+// additive ones, a compile-time constant then).
+__device__ __forceinline__ int32_t byte_table_word(uint32_t lut, uint32_t w, uint32_t x) {
     constexpr uint32_t T = (uint32_t)kLutWords * 4u;  // bytes per table
-    return smem_i32(lut + (4 * w + 0) * T + ((x << 2) & 0x3FCu)) + smem_i32(lut + (4 * w + 1) * T + ((x >> 6) & 0x3FCu)) +
-           smem_i32(lut + (4 * w + 2) * T + ((x >> 14) & 0x3FCu)) + smem_i32(lut + (4 * w + 3) * T + ((x >> 22) & 0x3FCu));
+    const uint32_t t = lut + 4u * w * T;
+    return smem_i32(t + ((x << 2) & 0x3FCu)) + smem_i32(t + T + ((x >> 6) & 0x3FCu)) +
+           smem_i32(t + 2u * T + ((x >> 14) & 0x3FCu)) + smem_i32(t + 3u * T + ((x >> 22) & 0x3FCu));
 }
 
 // Genetic value (Fig. 1C) of a record from the byte tables: both
@@ -223,15 +230,15 @@ __device__ __forceinline__ int32_t byte_table_word(uint32_t lut, uint32_t x) {
 // heterozygous loci (h0 ^ h1) when dlut is set; allele and heterozygosity
 // counts for the statistics.
 template <int W, int w = 0>
-__device__ __forceinline__ void genetic_value(const uint32_t (&ch)[2 * W], uint32_t lut, uint32_t dlut, int32_t &raw,
-                                              uint32_t &allele, uint32_t &hz) {
+__device__ __forceinline__ void genetic_value(const uint32_t (&ch)[2 * W], uint32_t dlut, int32_t &raw, uint32_t &allele,
+                                              uint32_t &hz) {
     if constexpr (w < W) {
         const uint32_t x = ch[w] ^ ch[W + w];
-        raw += byte_table_word<w>(lut, ch[w]) + byte_table_word<w>(lut, ch[W + w]);
-        if (dlut) raw += byte_table_word<w>(dlut, x);
+        raw += byte_table_word(0u, (uint32_t)w, ch[w]) + byte_table_word(0u, (uint32_t)w, ch[W + w]);
+        if (dlut) raw += byte_table_word(dlut, (uint32_t)w, x);
         allele += __popc(ch[w]) + __popc(ch[W + w]);
         hz += __popc(x);
-        genetic_value<W, w + 1>(ch, lut, dlut, raw, allele, hz);
+        genetic_value<W, w + 1>(ch, dlut, raw, allele, hz);
     }
 }
 
@@ -297,12 +304,12 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
             // (C) genetic value from the byte tables
             int32_t raw = 0;
             uint32_t allele = 0, hz = 0;
-            genetic_value<W>(ch, c.lut, c.dlut, raw, allele, hz);
+            genetic_value<W>(ch, c.dlut, raw, allele, hz);
             // (D) survival: the bin's threshold scaled by the resource factor
             const long long v = (long long)raw + (long long)c.bias;
             const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> c.shift, (long long)(kBins - 1));
             if constexpr (WEIGHTED) c.obin[j] = (uint16_t)bin;
-            uint32_t thr = smem_u32(bin * 4u);
+            uint32_t thr = smem_u32(SmemLayout<W>::kThr + bin * 4u);
             if (c.f != kCertain) thr = __umulhi(thr, c.f);
             alive = (thr == kCertain) || (dr.u_surv[it] < thr);
 
@@ -314,7 +321,7 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
             ts.allele += allele;
             if (alive) {
                 ts.sum_raw_s += raw;
-                if (c.eco) ts.cons += smem_u32((uint32_t)kBins * 4u + bin * 4u);
+                if (c.eco) ts.cons += smem_u32(SmemLayout<W>::kAtt + bin * 4u);
             }
         }
         // (E, first half) alive bitmap word (base + it*BLOCK + 32*warp)/32
@@ -330,8 +337,10 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
 // launch has an attack-rate table (zeros for a population without ecology);
 // dlut: the population's dominance tables are needed.
 template <int W, int BLOCK>
-__device__ __forceinline__ void copy_tables(const PopParams *P, bool eco, bool has_eco, uint32_t s_thr, uint32_t s_att,
-                                            uint32_t s_lut, uint32_t s_dlut, bool dlut, int tid) {
+__device__ __forceinline__ void copy_tables(const PopParams *P, bool eco, bool has_eco, uint32_t dyn, uint32_t dlut_off,
+                                            bool dlut, int tid) {
+    const uint32_t s_lut = dyn, s_thr = dyn + SmemLayout<W>::kThr, s_att = dyn + SmemLayout<W>::kAtt,
+                   s_dlut = dyn + dlut_off;
     constexpr uint32_t kTab16 = (uint32_t)kBins * 4u / 16u;         // 16-byte chunks of a bin table
     constexpr uint32_t kLut16 = (uint32_t)W * 4u * kLutWords / 4u;  // of the 4W byte tables
     for (uint32_t i = (uint32_t)tid; i < kTab16; i += BLOCK) cp_async_16(s_thr + 16u * i, P->table + 4u * i);
@@ -391,10 +400,250 @@ __device__ __forceinline__ void offspring_run(const SegCtx &c, uint32_t lt0, uin
     if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
 }
 
-template <int W, int ITEMS, int BLOCK, bool LINKED, bool WEIGHTED>
-__global__ void __launch_bounds__(BLOCK, offspring_min_blocks(BLOCK)) k_offspring(const __grid_constant__ GenArgs a) {
+// ----------------------------------------------------------- lane pairs
+// The second launch shape for L = 128 and 256 ("words per thread"): two lanes
+// per offspring.  Lane h of a pair (h = 0 mother, 1 father) draws that
+// parent, loads its record (one request per sector) and forms the gamete that
+// becomes the child's haplotype h; the pair shares the gamete-mask draws (each
+// lane computes half the Philox blocks and hands the other lane its lanes of
+// them), the genetic value (each lane sums its gamete's byte tables, and the
+// dominance tables over half the heterozygous words) and the survival
+// decision.  A lane holds one parent record instead of two, so twice as many
+// records can be in flight per register file; the two gametes of a child are
+// written by adjacent lanes as one coalesced record.
+constexpr int pair_min_blocks(int block) { return block >= 512 ? 1 : 512 / block; }
+
+template <int ITEMS>
+struct PairDraws {
+    uint32_t par[ITEMS], u_surv[ITEMS], u_mut[ITEMS];  // this lane's parent, the offspring's uniforms
+};
+
+template <int W, int ITEMS>
+struct PairRecs {
+    uint32_t r[ITEMS][2 * W];  // this lane's parent record
+};
+
+template <int ITEMS, int BLOCK>
+__device__ __forceinline__ void pair_draw(const SegCtx &c, uint32_t base, int tid, uint32_t h, PairDraws<ITEMS> &d) {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t j = base + (uint32_t)(it * (BLOCK / 2) + (tid >> 1));
+        d.par[it] = d.u_surv[it] = d.u_mut[it] = 0u;
+        if (j < c.n) {
+            const uint4 r = philox(make_uint4(j, c.g, c.rep, kMate << 24), c.k0, c.k1);
+            uint32_t p = __umulhi(h ? r.y : r.x, c.S);
+            if (c.sin) p = __ldcg(c.sin + p);
+            d.par[it] = p;
+            d.u_surv[it] = r.z;
+            d.u_mut[it] = r.w;
+        }
+    }
+}
+
+template <int W, int ITEMS, int BLOCK>
+__device__ __forceinline__ void pair_load(const SegCtx &c, uint32_t base, int tid, const PairDraws<ITEMS> &d,
+                                          PairRecs<W, ITEMS> &rec) {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t j = base + (uint32_t)(it * (BLOCK / 2) + (tid >> 1));
+        if (j < c.n) load_parent<W>(c.par + (size_t)d.par[it] * (2 * W), rec.r[it]);
+    }
+}
+
+// The gamete-mask words of lane h's parent: the gamete stream q = 2w + h is
+// lane q % 4 of Philox sub q / 4 (sub s covers words 2s and 2s+1: lanes x, y
+// mother and father of word 2s, z, w of word 2s+1).  Of each pair of subs
+// (2t, 2t+1) lane h computes sub 2t + h and receives its lanes of the other
+// from the partner lane.  All lanes of the warp take part (shuffles).
+template <int W>
+__device__ __forceinline__ void pair_masks(const SegCtx &c, uint32_t j, uint32_t h, uint32_t (&m)[W]) {
+    static_assert(W % 4 == 0, "lane pairs serve records of 4 or 8 words per haplotype");
+#pragma unroll
+    for (int t = 0; t < W / 4; ++t) {
+        const uint4 d = philox(make_uint4(j, c.g, c.rep, (kRecomb << 24) | (uint32_t)(2 * t) + h), c.k0, c.k1);
+        const uint32_t a = __shfl_xor_sync(0xFFFFFFFFu, h ? d.x : d.y, 1);
+        const uint32_t b = __shfl_xor_sync(0xFFFFFFFFu, h ? d.z : d.w, 1);
+        m[4 * t + 0] = h ? a : d.x;  // word 4t:   sub 2t, lane x (mother) / y (father)
+        m[4 * t + 1] = h ? b : d.z;  // word 4t+1: sub 2t, lane z / w
+        m[4 * t + 2] = h ? d.y : a;  // word 4t+2: sub 2t+1, lane x / y
+        m[4 * t + 3] = h ? d.w : b;  // word 4t+3: sub 2t+1, lane z / w
+    }
+}
+
+// Per-locus mutation of a pair's child (the draws of mutate(), made by both
+// lanes alike): each position belongs to one haplotype, whose lane checks it
+// against the positions already chosen there and flips it; the pair agrees
+// on every duplicate through a shuffle, so both count the same K distinct
+// positions.
+template <int W>
+__device__ __forceinline__ void pair_mutate(uint32_t (&g)[W], uint32_t k, uint32_t j, uint32_t gen, uint32_t rep,
+                                            uint32_t k0, uint32_t k1, uint32_t h, uint32_t pair_mask) {
+    constexpr uint32_t L = 32u * W;
+    uint32_t seen[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) seen[w] = 0u;
+    uint32_t chosen = 0;
+    for (uint32_t a4 = 0; a4 < kMutDraws / 4 && chosen < k; ++a4) {
+        const uint4 d = philox(make_uint4(j, gen, rep, (kMutPos << 24) | a4), k0, k1);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if (chosen < k) {
+                const uint32_t pos = __umulhi(lane_of(d, l), 2u * L);  // [0, 2L)
+                const uint32_t owner = pos >= L ? 1u : 0u, loc = pos - owner * L;
+                const uint32_t wi = loc >> 5, bit = 1u << (loc & 31u);
+                bool mine_dup = false;
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    if ((uint32_t)w == wi) mine_dup = (seen[w] & bit) != 0u;
+                const bool other_dup = __shfl_xor_sync(pair_mask, mine_dup, 1);
+                const bool dup = owner == h ? mine_dup : other_dup;
+                if (!dup) {
+                    if (owner == h) {
+#pragma unroll
+                        for (int w = 0; w < W; ++w)
+                            if ((uint32_t)w == wi) {
+                                seen[w] |= bit;
+                                g[w] ^= bit;
+                            }
+                    }
+                    ++chosen;
+                }
+            }
+        }
+    }
+}
+
+// W words of a gamete at p (16-byte aligned for W = 4, 32-byte for W = 8).
+template <int W>
+__device__ __forceinline__ void store_gamete(uint32_t *__restrict__ p, const uint32_t (&g)[W]) {
+    if constexpr (W == 4) {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(g[0], g[1], g[2], g[3]);
+    } else {
+        asm volatile("st.global.v8.u32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(g[0]), "r"(g[1]),
+                     "r"(g[2]), "r"(g[3]), "r"(g[4]), "r"(g[5]), "r"(g[6]), "r"(g[7]));
+    }
+}
+
+// One tile of a pair kernel (BLOCK / 2 * ITEMS offspring).
+template <int W, int ITEMS, int BLOCK>
+__device__ __forceinline__ uint32_t pair_tile(const SegCtx &c, uint32_t base, int tid, int lane, int warp,
+                                              const PairRecs<W, ITEMS> &rec, const PairDraws<ITEMS> &dr,
+                                              const uint32_t *s_cdf, ThreadStats &ts) {
+    const uint32_t h = (uint32_t)lane & 1u, pair_mask = 3u << (lane & ~1);
+    uint32_t alive_count = 0;  // the warp's survivors (same in every lane)
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t j = base + (uint32_t)(it * (BLOCK / 2) + (tid >> 1));
+        const bool live = j < c.n;
+        // (B) this lane's gamete from its parent: crossover masks, mutation
+        uint32_t m[W], g[W];
+        pair_masks<W>(c, j, h, m);
+        const uint32_t(&pr)[2 * W] = rec.r[it];
+#pragma unroll
+        for (int w = 0; w < W; ++w) g[w] = (pr[w] & ~m[w]) | (pr[W + w] & m[w]);
+        const uint32_t u_mut = dr.u_mut[it];
+        if (live && c.kmax != 0u && u_mut >= s_cdf[0]) {  // the same in both lanes of the pair
+            uint32_t k = 0;
+            for (uint32_t i = 0; i < c.kmax; ++i) k += (u_mut >= s_cdf[i]) ? 1u : 0u;
+            pair_mutate<W>(g, k, j, c.g, c.rep, c.k0, c.k1, h, pair_mask);
+        }
+        if (live) store_gamete<W>(c.chi + (size_t)j * (2 * W) + h * W, g);
+        // (C) genetic value: this gamete's additive value; the dominance
+        // deviations and heterozygosity of half of the words
+        int32_t part = 0;
+        uint32_t allele = 0, hz = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            part += byte_table_word(0u, (uint32_t)w, g[w]);
+            allele += __popc(g[w]);
+        }
+#pragma unroll
+        for (int i = 0; i < W / 2; ++i) {
+            const uint32_t mine = h ? g[W / 2 + i] : g[i];  // words h * W/2 + i
+            const uint32_t other = __shfl_xor_sync(0xFFFFFFFFu, h ? g[i] : g[W / 2 + i], 1);
+            const uint32_t x = mine ^ other;
+            hz += __popc(x);
+            if (c.dlut) part += byte_table_word(c.dlut, h * (W / 2) + (uint32_t)i, x);
+        }
+        const int32_t raw = part + __shfl_xor_sync(0xFFFFFFFFu, part, 1);
+        // (D) survival: the bin's threshold scaled by the resource factor
+        bool alive = false;
+        if (live) {
+            const long long v = (long long)raw + (long long)c.bias;
+            const uint32_t bin = v < 0 ? 0u : (uint32_t)min(v >> c.shift, (long long)(kBins - 1));
+            uint32_t thr = smem_u32(SmemLayout<W>::kThr + bin * 4u);
+            if (c.f != kCertain) thr = __umulhi(thr, c.f);
+            alive = (thr == kCertain) || (dr.u_surv[it] < thr);
+            ts.het += hz;
+            ts.allele += allele;
+            if (h == 0u) {  // the offspring's sums once per pair
+                ts.sum_raw += raw;
+                ts.sum_raw2 += (unsigned long long)((long long)raw * (long long)raw);
+                ts.mn = min(ts.mn, raw);
+                ts.mx = max(ts.mx, raw);
+                if (alive) {
+                    ts.sum_raw_s += raw;
+                    if (c.eco) ts.cons += smem_u32(SmemLayout<W>::kAtt + bin * 4u);
+                }
+            }
+        }
+        // (E, first half) the warp's 16 offspring: bit p of the half word is
+        // pair p's decision (the even lanes of the ballot)
+        uint32_t bal = __ballot_sync(0xFFFFFFFFu, alive) & 0x55555555u;
+        bal = (bal | (bal >> 1)) & 0x33333333u;
+        bal = (bal | (bal >> 2)) & 0x0F0F0F0Fu;
+        bal = (bal | (bal >> 4)) & 0x00FF00FFu;
+        bal = (bal | (bal >> 8)) & 0x0000FFFFu;
+        const uint32_t j0 = base + (uint32_t)(it * (BLOCK / 2) + warp * 16);
+        if (lane == 0) reinterpret_cast<uint16_t *>(c.alive)[j0 >> 4] = (uint16_t)bal;
+        alive_count += __popc(bal);
+    }
+    return alive_count;
+}
+
+template <int W, int ITEMS, int BLOCK>
+__device__ __forceinline__ void pair_run(const SegCtx &c, uint32_t lt0, uint32_t lt1, uint32_t *bucket_next, int tid,
+                                         int lane, int warp, const uint32_t *s_cdf, ThreadStats &ts,
+                                         uint32_t &warp_alive) {
+    constexpr uint32_t TILE = (uint32_t)(BLOCK / 2 * ITEMS);
+    const uint32_t h = (uint32_t)lane & 1u;
+    PairDraws<ITEMS> d0, d1;
+    PairRecs<W, ITEMS> ra, rb;
+    pair_draw<ITEMS, BLOCK>(c, lt0 * TILE, tid, h, d0);
+    if (lt0 + 1 < lt1) pair_draw<ITEMS, BLOCK>(c, (lt0 + 1) * TILE, tid, h, d1);
+    pair_load<W, ITEMS, BLOCK>(c, lt0 * TILE, tid, d0, ra);
+    cp_async_wait<0>();
+    __syncthreads();  // the run's tables (and cdf) are visible to every thread
+
+    uint32_t bucket_alive = 0, bucket_cur = (lt0 * TILE) / kBucket;
+    auto step = [&](uint32_t lt, const PairRecs<W, ITEMS> &cur, PairRecs<W, ITEMS> &nxt) {
+        const uint32_t base = lt * TILE;
+        if (lt + 1 < lt1) pair_load<W, ITEMS, BLOCK>(c, base + TILE, tid, d1, nxt);
+        if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
+        const uint32_t bkt = base / kBucket;
+        if (bkt != bucket_cur) {
+            if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
+            bucket_alive = 0;
+            bucket_cur = bkt;
+        }
+        const uint32_t cnt = pair_tile<W, ITEMS, BLOCK>(c, base, tid, lane, warp, cur, d0, s_cdf, ts);
+        bucket_alive += cnt;
+        warp_alive += cnt;
+        d0 = d1;
+        if (lt + 2 < lt1) pair_draw<ITEMS, BLOCK>(c, base + 2 * TILE, tid, h, d1);
+    };
+    for (uint32_t lt = lt0; lt < lt1; lt += 2) {
+        step(lt, ra, rb);
+        if (lt + 1 < lt1) step(lt + 1, rb, ra);
+    }
+    if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
+}
+
+template <int W, int ITEMS, int BLOCK, bool LINKED, bool WEIGHTED, bool PAIR>
+__global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspring_min_blocks(BLOCK))
+    k_offspring(const __grid_constant__ GenArgs a) {
     constexpr int NW = BLOCK / 32;
-    constexpr uint32_t TILE = (uint32_t)(BLOCK * ITEMS);
+    constexpr uint32_t TILE = (uint32_t)(BLOCK * ITEMS) / (PAIR ? 2u : 1u);
     static_assert(kBucket % TILE == 0, "tiles must not straddle compaction buckets");
     __shared__ uint32_t s_cdf[kMaxKmax];
     __shared__ long long s_ll[2][NW];
@@ -470,12 +719,10 @@ __global__ void __launch_bounds__(BLOCK, offspring_min_blocks(BLOCK)) k_offsprin
         c.shift = c.P->shift;
         c.bias = c.P->bias;
         c.eco = a.eco_table != 0u;
-        c.lut = a.smem_lut;
         c.dlut = c.P->has_dom ? a.smem_dlut : 0u;  // 0 also when the launch has no dominance tables
 
         __syncthreads();  // the previous run's tables and statistics scratch are no longer read
-        copy_tables<W, BLOCK>(c.P, c.eco, c.P->has_eco != 0u, dyn_addr, dyn_addr + kBins * 4, dyn_addr + a.smem_lut,
-                              dyn_addr + a.smem_dlut, c.dlut != 0u, tid);
+        copy_tables<W, BLOCK>(c.P, c.eco, c.P->has_eco != 0u, dyn_addr, a.smem_dlut, c.dlut != 0u, tid);
         if (tid < kMaxKmax) s_cdf[tid] = (uint32_t)tid < c.kmax ? c.P->cdf[tid] : 0u;
         if constexpr (LINKED) {
             const LinkParams *lp = c.P->link;
@@ -495,8 +742,11 @@ __global__ void __launch_bounds__(BLOCK, offspring_min_blocks(BLOCK)) k_offsprin
 
         ThreadStats ts;
         uint32_t warp_alive = 0;
-        offspring_run<W, ITEMS, BLOCK, LINKED, WEIGHTED>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, lk,
-                                                         warp_alive);
+        if constexpr (PAIR)
+            pair_run<W, ITEMS, BLOCK>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, warp_alive);
+        else
+            offspring_run<W, ITEMS, BLOCK, LINKED, WEIGHTED>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, lk,
+                                                             warp_alive);
 
         // statistics of this run: exact warp sums, one atomic per field into
         // one of the population's accumulator copies
@@ -548,12 +798,13 @@ __global__ void __launch_bounds__(BLOCK, offspring_min_blocks(BLOCK)) k_offsprin
 }
 
 // Host-side description of one instance: entry and shape.
-template <int W, int ITEMS, int BLOCK, bool LINKED = false, bool WEIGHTED = false>
+template <int W, int ITEMS, int BLOCK, bool LINKED = false, bool WEIGHTED = false, bool PAIR = false>
 OffspringKernel offspring_instance() {
     OffspringKernel k;
-    k.fn = &k_offspring<W, ITEMS, BLOCK, LINKED, WEIGHTED>;
+    k.fn = &k_offspring<W, ITEMS, BLOCK, LINKED, WEIGHTED, PAIR>;
     k.block = BLOCK;
     k.items = ITEMS;
+    k.lanes = PAIR ? 2u : 1u;
     return k;
 }
 

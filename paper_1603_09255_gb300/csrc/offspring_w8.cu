@@ -5,15 +5,18 @@
 
 namespace spg {
 
-OffspringKernel offspring_kernel_w8(uint32_t block, uint32_t items, bool linked, bool weighted) {
+OffspringKernel offspring_kernel_w8(const Shape &s, bool linked, bool weighted) {
     if (linked || weighted) {
-        if (block != 256 || items != 1) return OffspringKernel{};
+        if (s.block != 256 || s.items != 1 || s.lanes != 1) return OffspringKernel{};
         if (linked && weighted) return offspring_instance<8, 1, 256, true, true>();
         return linked ? offspring_instance<8, 1, 256, true, false>() : offspring_instance<8, 1, 256, false, true>();
     }
-    if (block == 128 && items == 1) return offspring_instance<8, 1, 128>();
-    if (block == 256 && items == 1) return offspring_instance<8, 1, 256>();
-    if (block == 512 && items == 1) return offspring_instance<8, 1, 512>();
+    if (s.block == 128 && s.items == 1 && s.lanes == 1) return offspring_instance<8, 1, 128, false, false, false>();
+    if (s.block == 256 && s.items == 1 && s.lanes == 1) return offspring_instance<8, 1, 256, false, false, false>();
+    if (s.block == 512 && s.items == 1 && s.lanes == 1) return offspring_instance<8, 1, 512, false, false, false>();
+    if (s.block == 128 && s.items == 1 && s.lanes == 2) return offspring_instance<8, 1, 128, false, false, true>();
+    if (s.block == 256 && s.items == 1 && s.lanes == 2) return offspring_instance<8, 1, 256, false, false, true>();
+    if (s.block == 512 && s.items == 1 && s.lanes == 2) return offspring_instance<8, 1, 512, false, false, true>();
     return OffspringKernel{};
 }
 

@@ -60,10 +60,11 @@ int configure_launch(spg_pop *p, const Shape &shape) {
             return fail(SPG_ERR_INVALID, "continuous allelic values run 256 threads, one offspring each");
         k = continuous_kernel(p->n_loci);
     } else {
-        if (!supported_shape(p->words, shape.block, shape.items))
-            return fail(SPG_ERR_INVALID, "unsupported launch shape (%u threads, %u offspring per thread) for %u loci",
-                        shape.block, shape.items, p->n_loci);
-        if ((prm.linked || prm.weighted) && (shape.block != 256u || shape.items != 1u))
+        if (!supported_shape(p->words, shape))
+            return fail(SPG_ERR_INVALID,
+                        "unsupported launch shape (%u threads, %u offspring per thread, %u lanes per offspring) for %u loci",
+                        shape.block, shape.items, shape.lanes, p->n_loci);
+        if ((prm.linked || prm.weighted) && (shape.block != 256u || shape.items != 1u || shape.lanes != 1u))
             return fail(SPG_ERR_INVALID,
                         "a population with a linkage map or parent weights runs 256 threads, one offspring each");
         k = offspring_kernel(p->words, shape, prm.linked != 0u, prm.weighted != 0u, prm.has_eco != 0u,
@@ -116,7 +117,8 @@ int spg_create_population(const spg_pop_desc *desc, const spg_allocator *alloc, 
         return fail(SPG_ERR_OOM, "host allocation failed");
     }
     const bool variant = desc->map_morgans || desc->mother_weights || desc->father_weights;
-    const Shape shape = (desc->allele_model == 1u || variant) ? Shape{(uint32_t)kBlock, 1u} : default_shape(p->words);
+    const Shape shape =
+        (desc->allele_model == 1u || variant) ? Shape{(uint32_t)kBlock, 1u, 1u} : default_shape(p->words);
     rc = build_params(desc, *p->host_prm);
     if (rc != SPG_OK) {
         delete p->host_prm;
@@ -315,7 +317,7 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
 }
 
 int spg_set_tiling(spg_pop *p, uint32_t items) {
-    spg_launch_shape sh{256u, items};
+    spg_launch_shape sh{256u, items, 1u};
     return spg_set_launch_shape(p, &sh);
 }
 
@@ -339,6 +341,7 @@ int spg_get_launch_shape(spg_pop *p, spg_launch_shape *out) {
     if (!p || !out) return fail(SPG_ERR_INVALID, "NULL argument");
     out->threads_per_block = p->gl.offspring.block;
     out->items_per_thread = p->gl.offspring.items;
+    out->lanes_per_offspring = p->gl.offspring.lanes;
     return SPG_OK;
 }
 

@@ -167,20 +167,21 @@ struct GenArgs {
     uint32_t nsegs;
     uint32_t total_tiles;        // tiles of the single segment (nsegs == 1: contiguous shares per block)
     uint32_t total_buckets;
-    // dynamic shared memory of the offspring kernel: the survival thresholds
-    // at 0, attack rates after them when eco_table, the byte tables at
-    // smem_lut and smem_dlut (0: the launch has no dominance)
+    // dynamic shared memory of the offspring kernel: the byte tables at 0,
+    // the survival thresholds after them, attack rates after those when
+    // eco_table, the dominance byte tables at smem_dlut (0: none)
     uint32_t eco_table;
-    uint32_t smem_lut, smem_dlut;
+    uint32_t smem_dlut;
     Segment one;           // the segment itself when nsegs == 1 (read from kernel parameters)
 };
 
 using GenKernel = void (*)(GenArgs);
 
-// Launch shape of the offspring kernel: threads per block and offspring per
-// thread.  Results never depend on it.
+// Launch shape of the offspring kernel: threads per block, offspring per
+// thread (per lane pair when lanes = 2) and lanes per offspring (1, or 2 for
+// L >= 128: one lane per parent and gamete).  Results never depend on it.
 struct Shape {
-    uint32_t block = 256, items = 1;
+    uint32_t block = 256, items = 1, lanes = 1;
 };
 
 // The offspring kernel of one launch: entry, shape, dynamic shared-memory
@@ -189,21 +190,21 @@ struct Shape {
 // block per 256 offspring and no dynamic shared memory.
 struct OffspringKernel {
     GenKernel fn = nullptr;
-    uint32_t words = 0, block = 256, items = 1;
-    uint32_t eco_table = 0, smem_lut = 0, smem_dlut = 0;
+    uint32_t words = 0, block = 256, items = 1, lanes = 1;
+    uint32_t eco_table = 0, smem_dlut = 0;
     uint32_t smem = 0;
     uint32_t resident = 0;
     bool persistent = true;
 };
 
 // Offspring kernels (offspring_w*.cu) and the other kernels (kernels.cu).
-bool supported_shape(uint32_t words, uint32_t block, uint32_t items);
+bool supported_shape(uint32_t words, const Shape &shape);
 // The offspring kernel of a shape; eco: some population of the launch has an
 // ecology (the survival table carries attack rates), dom: some has dominance.
 OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom);
 int prepare_offspring(OffspringKernel &k);  // sets the shared-memory limit, fills `resident`
 GenKernel compact_kernel(uint32_t words);  // the compaction kernel for records of 2W words
-uint32_t tile_size(uint32_t block, uint32_t items);
+uint32_t tile_size(const Shape &shape);  // offspring per tile: block * items / lanes
 // Copy the offspring kernel's shape and shared-memory layout into a launch.
 void apply_kernel(const OffspringKernel &k, GenArgs &a);
 // Enqueue founders: generation-0 records by Philox draws, survivors = 0..n-1.

@@ -68,7 +68,8 @@ class spg_noalloc_generation(ctypes.Structure):
 
 
 class spg_launch_shape(ctypes.Structure):
-    _fields_ = [("threads_per_block", ctypes.c_uint32), ("items_per_thread", ctypes.c_uint32)]
+    _fields_ = [("threads_per_block", ctypes.c_uint32), ("items_per_thread", ctypes.c_uint32),
+                ("lanes_per_offspring", ctypes.c_uint32)]
 
 
 class spg_autotune_report(ctypes.Structure):
@@ -77,7 +78,7 @@ class spg_autotune_report(ctypes.Structure):
 
 
 def _shape_tuple(sh: spg_launch_shape):
-    return (int(sh.threads_per_block), int(sh.items_per_thread))
+    return (int(sh.threads_per_block), int(sh.items_per_thread), int(sh.lanes_per_offspring))
 
 
 class spg_server_config(ctypes.Structure):
@@ -405,12 +406,13 @@ class Population:
         check(lib().spg_get_tiling(self._h, ctypes.byref(v)), "spg_get_tiling")
         return v.value
 
-    def set_launch_shape(self, threads_per_block: int = 0, items_per_thread: int = 0) -> None:
-        sh = spg_launch_shape(int(threads_per_block), int(items_per_thread))
+    def set_launch_shape(self, threads_per_block: int = 0, items_per_thread: int = 0,
+                         lanes_per_offspring: int = 0) -> None:
+        sh = spg_launch_shape(int(threads_per_block), int(items_per_thread), int(lanes_per_offspring))
         check(lib().spg_set_launch_shape(self._h, ctypes.byref(sh)), "spg_set_launch_shape")
 
     def launch_shape(self):
-        """(threads per block, offspring per thread) in use."""
+        """(threads per block, offspring per thread, lanes per offspring) in use."""
         sh = spg_launch_shape()
         check(lib().spg_get_launch_shape(self._h, ctypes.byref(sh)), "spg_get_launch_shape")
         return _shape_tuple(sh)
@@ -483,13 +485,14 @@ class Batch:
         check(lib().spg_batch_get_tiling(self._h, int(n_loci), ctypes.byref(v)), "spg_batch_get_tiling")
         return v.value
 
-    def set_launch_shape(self, n_loci: int, threads_per_block: int = 0, items_per_thread: int = 0) -> None:
-        sh = spg_launch_shape(int(threads_per_block), int(items_per_thread))
+    def set_launch_shape(self, n_loci: int, threads_per_block: int = 0, items_per_thread: int = 0,
+                         lanes_per_offspring: int = 0) -> None:
+        sh = spg_launch_shape(int(threads_per_block), int(items_per_thread), int(lanes_per_offspring))
         check(lib().spg_batch_set_launch_shape(self._h, int(n_loci), ctypes.byref(sh)), "spg_batch_set_launch_shape")
 
     def launch_shape(self, n_loci: int):
-        """(threads per block, offspring per thread) of the members with
-        n_loci loci."""
+        """(threads per block, offspring per thread, lanes per offspring) of
+        the members with n_loci loci."""
         sh = spg_launch_shape()
         check(lib().spg_batch_get_launch_shape(self._h, int(n_loci), ctypes.byref(sh)), "spg_batch_get_launch_shape")
         return _shape_tuple(sh)

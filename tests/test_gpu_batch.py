@@ -81,9 +81,9 @@ def test_batch_members_equal_oracle(member):
 
 
 # the candidates the autotuner times (threads per block, offspring per
-# thread): six for L = 32 and 64, three (each timed twice) for L = 128, 256
-NARROW = [(128, 1), (128, 2), (256, 1), (256, 2), (512, 1), (512, 2)]
-WIDE = [(128, 1), (256, 1), (512, 1), (128, 1), (256, 1), (512, 1)]
+# thread, lanes per offspring)
+NARROW = [(128, 1, 1), (128, 2, 1), (256, 1, 1), (256, 2, 1), (512, 1, 1), (512, 2, 1)]
+WIDE = [(128, 1, 1), (256, 1, 1), (512, 1, 1), (128, 1, 2), (256, 1, 2), (512, 1, 2)]
 
 
 def test_autotune_and_launch_shapes_do_not_change_results():
@@ -116,7 +116,8 @@ def test_autotune_and_launch_shapes_do_not_change_results():
 
 def test_batch_rejects_unsupported_launch_shapes():
     b = sp().Batch(mixed_workloads(4), stats_capacity=8)
-    for L, shape in ((32, (64, 1)), (64, (256, 4)), (256, (256, 2)), (128, (512, 2)), (48, (256, 1))):
+    for L, shape in ((32, (64, 1, 1)), (64, (256, 4, 1)), (256, (256, 2, 1)), (128, (512, 2, 1)), (64, (256, 1, 2)),
+                     (128, (256, 1, 3)), (48, (256, 1, 1))):
         with pytest.raises(sp().SpeggError):
             b.set_launch_shape(L, *shape)
     b.close()

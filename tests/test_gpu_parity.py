@@ -110,26 +110,28 @@ def test_every_tiling_gives_identical_results(items, n_loci):
     assert_identical(orc, gpu, orc.step(6), gpu.read_stats(1, 6))
 
 
-SHAPES = [(128, 1), (128, 2), (256, 1), (256, 2), (512, 1), (512, 2)]
+SHAPES = [(128, 1, 1), (128, 2, 1), (256, 1, 1), (256, 2, 1), (512, 1, 1), (512, 2, 1), (128, 1, 2), (256, 1, 2),
+          (512, 1, 2)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("n_loci", [32, 64, 128, 256])
 def test_every_launch_shape_gives_identical_results(shape, n_loci):
-    """Threads per block and offspring per thread change only how the work is
-    laid out: oracle-equal for a population whose tiles end mid-bucket,
+    """Threads per block, offspring per thread and lanes per offspring change
+    only how the work is laid out: oracle-equal for a population whose tiles
+    end mid-bucket, with a high mutation rate (the lane-pair mutation path),
     switched shape half way."""
     sp = spegg()
-    block, items = shape
-    w = S.consumer_resource(n=20_011, n_loci=n_loci, n_gen=6, mu=1e-3, s=1.0, K=4e5, seed=7)
+    block, items, lanes = shape
+    w = S.consumer_resource(n=20_011, n_loci=n_loci, n_gen=6, mu=2e-3, s=1.0, K=4e5, seed=7)
     orc = oracle.OraclePopulation.from_workload(w)
     gpu = sp.Population.from_workload(w, stats_capacity=16)
-    if n_loci >= 128 and items != 1:
+    if (n_loci >= 128 and items != 1) or (n_loci <= 64 and lanes != 1):
         with pytest.raises(sp.SpeggError):
-            gpu.set_launch_shape(block, items)
+            gpu.set_launch_shape(block, items, lanes)
         return
-    gpu.set_launch_shape(block, items)
-    assert gpu.launch_shape() == (block, items)
+    gpu.set_launch_shape(block, items, lanes)
+    assert gpu.launch_shape() == (block, items, lanes)
     gpu.step(3)
     gpu.set_launch_shape()  # the default shape
     gpu.step(3)
