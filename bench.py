@@ -170,108 +170,132 @@ def reference_arm(args, workload):
 
 
 def bench_config(w, l2):
-    return {"workload": f"consumer-resource N={w.n} L={w.n_loci} mu={w.mu:g} s={w.s} r={w.eco_r} K={w.eco_K:g}, "
-                        f"{GENERATIONS} generations per step",
-            "n": w.n, "n_loci": w.n_loci, "generations_per_step": GENERATIONS, "l2": l2}
+    return {"workload": "consumer-resource", "n": w.n, "n_loci": w.n_loci, "generations_per_step": GENERATIONS,
+            "l2": l2}
+
+
+def timed_on(stream, torch, fn):
+    """Milliseconds of fn() on `stream`, CUDA events on the stream."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+    fn()
+    with torch.cuda.stream(stream):
+        b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b)
+
+
+def per_generation_ms(stream, torch, step_one, repeats=32, warmup=3):
+    """p50/p99 of single generations (direct launches) bracketed by events."""
+    for _ in range(warmup):
+        step_one()
+    stream.synchronize()
+    t = [timed_on(stream, torch, step_one) for _ in range(repeats)]
+    return float(np.percentile(t, 50)), float(np.percentile(t, 99))
+
+
+def single_species(spegg, torch, oracle_cpu: bool):
+    """The single-species workload (N = 10^4, L = 32, 100 generations): through
+    the cached graph (one step call), by direct launches (100 single-generation
+    calls), and the oracle single-threaded on the full run."""
+    w = S.single_species()
+    stream = torch.cuda.Stream()
+    ind = w.n * w.n_gen
+    times = {}
+    for mode in ("graph", "direct"):
+        ms = []
+        for _ in range(4):  # the first of four runs is a warm-up
+            pop = spegg.Population.from_workload(w, stats_capacity=w.n_gen + 8, stream=stream)
+            pop.synchronize()
+            if mode == "graph":
+                ms.append(timed_on(stream, torch, lambda: pop.step(w.n_gen)))
+            else:
+                ms.append(timed_on(stream, torch, lambda: [pop.step(1) for _ in range(w.n_gen)]))
+            pop.close()
+        times[mode] = min(ms[1:])
+    out = {"value": ind / (times["graph"] / 1e3), "nograph": ind / (times["direct"] / 1e3)}
+    if oracle_cpu:
+        import oracle
+        orc = oracle.OraclePopulation.from_workload(w)
+        t0 = time.perf_counter()
+        orc.step(w.n_gen)
+        out["cpu"] = ind / (time.perf_counter() - t0)
+        orc.close()
+    return out
 
 
 def batched_replicates(spegg, torch, gens: int = 500, plain_members: int = 256, plain_gens: int = 32,
                        oracle_cpu: bool = False, count: int = 4096):
-    """Batched-replicates workload: 4,096 independent single-species runs (N
+    """Batched-replicates workload: `count` independent single-species runs (N
     log-uniform in [1e3, 2e5], L in {32, 64, 128}, s in [0, 0.5]) advanced by
-    shared, graph-captured launches with autotuned tilings, against the plain
-    path (one population at a time) timed on the first `plain_members`."""
+    shared, graph-captured launches with autotuned launch shapes, against the
+    plain path (one population at a time) timed on the first `plain_members`."""
     ws = S.batch_replicates(count=count, n_gen=gens)
     plain_members = min(plain_members, count)
     stream = torch.cuda.Stream()
     batch = spegg.Batch(ws, stats_capacity=gens + 64, stream=stream)
-    ran = batch.autotune(4)
+    batch.autotune(4)
     batch.step(32)
     batch.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        a.record(stream)
-    batch.step(gens)
-    with torch.cuda.stream(stream):
-        b.record(stream)
-    stream.synchronize()
-    ms = a.elapsed_time(b)
+    ms = timed_on(stream, torch, lambda: batch.step(gens))
     sum_n = sum(w.n for w in ws)
-    tilings = {str(L): batch.launch_shape(L) for L in (32, 64, 128)}
     tuned = getattr(batch, "autotune_report", {})
-    # per-generation latency of the whole batch: single generations bracketed
-    # by events, after 3 untimed ones
-    batch.step(3)
-    g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(32)]
-    for ga, gb in g_ev:
-        with torch.cuda.stream(stream):
-            ga.record(stream)
-        batch.step(1)
-        with torch.cuda.stream(stream):
-            gb.record(stream)
-    stream.synchronize()
-    gen_ms = [ga.elapsed_time(gb) for ga, gb in g_ev]
+    p50, p99 = per_generation_ms(stream, torch, lambda: batch.step(1))
     batch.close()
     pops = [spegg.Population.from_workload(ws[i], stats_capacity=64, stream=stream) for i in range(plain_members)]
     for p in pops:
         p.step(1)
     stream.synchronize()
-    with torch.cuda.stream(stream):
-        a.record(stream)
-    for p in pops:
-        p.step(plain_gens)
-    with torch.cuda.stream(stream):
-        b.record(stream)
-    stream.synchronize()
-    ms_plain = a.elapsed_time(b)
+    ms_plain = timed_on(stream, torch, lambda: [p.step(plain_gens) for p in pops])
     plain = sum(ws[i].n for i in range(plain_members)) * plain_gens / (ms_plain / 1e3)
     for p in pops:
         p.close()
     value = sum_n * gens / (ms / 1e3)
     # algorithmic bytes of one generation of every replicate: sum of N (12 + 24W)
     algo = sum(w.n * algorithmic_bytes(w.words) for w in ws) * gens
-    peak, source = load_peaks()
-    achieved = algo / (ms / 1e3) / 1e9
-    return {"workload": f"4096 replicates, N log-uniform [1e3, 2e5] (sum {sum_n}), L in {{32, 64, 128}}, "
-                        f"s in [0, 0.5], {gens} generations timed after {ran + 32}",
-            "value": value, "unit": "individual-generations/s", "ms": ms, "tilings": tilings, "autotune": tuned,
-            "plain_value": plain, "plain_sample": f"first {plain_members} replicates, {plain_gens} generations, "
-                                                  "one population stepped at a time",
-            "speedup_vs_plain": value / plain,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "note": f"sum of N (12 + 24W) B per generation, of {source}"},
-            "per_generation": {"p50_ms": float(np.percentile(gen_ms, 50)), "p99_ms": float(np.percentile(gen_ms, 99)),
-                               "repeats": len(gen_ms), "warmup": 3},
-            "cpu_baseline": oracle_batched_baseline(ws) if oracle_cpu else None}
+    peak, _ = load_peaks()
+    out = {"value": value, "vs_plain": value / plain, "frac": algo / (ms / 1e3) / 1e9 / peak,
+           "p50_ms": p50, "p99_ms": p99,
+           "shapes": {str(L): list(r["shape"]) for L, r in tuned.items()},
+           "spread": {str(L): round(r["worst_ms"] / r["best_ms"], 3) for L, r in tuned.items() if r["best_ms"] > 0}}
+    if oracle_cpu:
+        out["cpu"] = oracle_batched_baseline(ws)["value"]
+    return out
 
 
-def served_sweep(spegg, torch, count: int = 48, rate: float = 200.0):
-    """Served parameter sweep: a seeded Poisson stream (rate jobs/s) of jobs
-    with N log-uniform in [1e3, 2e6], L in {64, 256}, 100-2000 generations,
+def served_sweep(spegg, torch, count: int = 1000, rate: float = 200.0):
+    """Served parameter sweep: a seeded Poisson stream (rate jobs/s) of `count`
+    jobs (N log-uniform in [1e3, 2e6], L in {64, 256}, 100-2000 generations)
     admitted by device footprint and run by continuous batching; latency is
-    arrival -> finish on the server's clock."""
+    arrival -> finish on the server's clock.  The same jobs are then run one at
+    a time (the plain path) for the same-mix comparison."""
     ws, gens, arrivals = S.served_trace(count=count, rate=rate)
     srv = spegg.Server(gens_per_tick=16)
-    t0 = time.perf_counter()
     jobs = srv.run_trace(ws, gens, arrivals)
-    wall = time.perf_counter() - t0
     infos = [srv.job_info(int(j)) for j in jobs]
+    c = srv.counters()
+    srv.close()
     lat = np.array([i["t_finish"] - i["t_arrival"] for i in infos])
     work = sum(w.n * i["gen"] for w, i in zip(ws, infos))
     makespan = max(i["t_finish"] for i in infos) - min(i["t_arrival"] for i in infos)
-    c = srv.counters()
-    srv.close()
     value = work / makespan
-    mean_job = work / count
-    return {"workload": f"{count} jobs, Poisson {rate:g}/s, N log-uniform [1e3, 2e6], L in {{64, 256}}, "
-                        "100-2000 generations, continuous batching",
-            "value": value, "unit": "individual-generations/s", "p50_latency_s": float(np.percentile(lat, 50)),
-            "p99_latency_s": float(np.percentile(lat, 99)), "makespan_s": makespan, "wall_s": wall,
-            "offered_load": rate * mean_job / value, "peak_resident": c["peak_resident"],
-            "peak_memory_gb": c["peak_memory_used"] / 1e9}
+    # the plain path on the same mix: each job created, stepped and read alone
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for w, g in zip(ws, gens):
+        p = spegg.Population.from_workload(w, stats_capacity=g, stream=stream)
+        p.step(g)
+        p.read_stats(1, g)
+        p.close()
+    plain = work / (time.perf_counter() - t0)
+    return {"value": value, "vs_plain": value / plain, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "jobs": count, "load": rate * (work / count) / value,
+            "resident": c["peak_resident"]}
 
 
-def variant_population(spegg, torch, w, label: str, gens: int = 256, bytes_per_offspring=None):
+def variant_population(spegg, torch, w, gens: int = 256, bytes_per_offspring=None):
     """One variant of the consumer-resource population (N = 10^6, L = 128),
     `gens` generations after 64, L2 flushed before, CUDA events on its stream."""
     stream = torch.cuda.Stream()
@@ -281,24 +305,11 @@ def variant_population(spegg, torch, w, label: str, gens: int = 256, bytes_per_o
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     with torch.cuda.stream(stream):
         flush.fill_(7)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        a.record(stream)
-    pop.step(gens)
-    with torch.cuda.stream(stream):
-        b.record(stream)
-    stream.synchronize()
-    ms = a.elapsed_time(b)
-    peak, source = load_peaks()
+    ms = timed_on(stream, torch, lambda: pop.step(gens))
+    peak, _ = load_peaks()
     per = bytes_per_offspring if bytes_per_offspring is not None else 12 + 24 * w.words
-    achieved = w.n * per * gens / (ms / 1e3) / 1e9
-    out = {"workload": f"{w.name.split('+')[0]} N={w.n} L={w.n_loci}, {label}, "
-                       f"{gens} generations after 64 (L2 flushed before)",
-           "value": w.n * gens / (ms / 1e3), "unit": "individual-generations/s", "us_per_generation": ms * 1e3 / gens,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "note": f"{per} B per offspring (algorithmic), of {source}"}}
     pop.close()
-    return out
+    return {"us": ms * 1e3 / gens, "frac": w.n * per * gens / (ms / 1e3) / 1e9 / peak}
 
 
 def spatial_community(spegg, torch, steps: int = 200, oracle_cpu: bool = False):
@@ -310,14 +321,7 @@ def spatial_community(spegg, torch, steps: int = 200, oracle_cpu: bool = False):
     g = spegg.Space(c, stream=stream, stats_capacity=steps + 8)
     g.step(3)
     g.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        a.record(stream)
-    g.step(steps)
-    with torch.cuda.stream(stream):
-        b.record(stream)
-    stream.synchronize()
-    ms = a.elapsed_time(b)
+    ms = timed_on(stream, torch, lambda: g.step(steps))
     st = g.read_stats(4, steps)
     ind = int(st["n_before"].sum())
     births = int(st["births"].sum())
@@ -326,16 +330,10 @@ def spatial_community(spegg, torch, steps: int = 200, oracle_cpu: bool = False):
     # written once at its new place; every newborn reads two parent records
     # and is written once with its age
     algo = ind * (16 * words + 2) + births * (24 * words + 1)
-    peak, source = load_peaks()
-    achieved = algo / (ms / 1e3) / 1e9
-    out = {"workload": f"3 species on a 64 x 64 torus, {c.species[0].n0} founders per species and patch, "
-                       f"L={c.n_loci}, dispersal 0.05, {steps} steps after 3",
-           "value": ind / (ms / 1e3), "unit": "individual-steps/s", "ms_per_step": ms / steps,
-           "individuals_first_step": int(st[0]["n_before"].sum()), "individuals_last_step": int(st[-1]["n_after"].sum()),
-           "births": births,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "note": f"whole step (8 launches), of {source}"},
-           "cpu_baseline": oracle_spatial_baseline() if oracle_cpu else None}
+    peak, _ = load_peaks()
+    out = {"value": ind / (ms / 1e3), "ms": ms / steps, "frac": algo / (ms / 1e3) / 1e9 / peak}
+    if oracle_cpu:
+        out["cpu"] = oracle_spatial_baseline()["value"]
     g.close()
     return out
 
@@ -362,9 +360,7 @@ def oracle_batched_baseline(ws, members: int = 64, gens: int = 2):
         res = pool.map(_oracle_generations, [(w, gens) for w in sample], chunksize=1)
     ind = sum(r[0] for r in res)
     busy = sum(r[1] for r in res)
-    return {"value": ind / busy * cores, "unit": "individual-generations/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {members} replicates ({sum(w.n for w in sample)} individuals), {gens} generations "
-                      f"each, {cores} processes; value = individual-generations / step seconds x processes"}
+    return {"value": ind / busy * cores, "cores": cores}
 
 
 def oracle_spatial_baseline(X: int = 8, Y: int = 8, steps: int = 4):
@@ -379,9 +375,7 @@ def oracle_spatial_baseline(X: int = 8, Y: int = 8, steps: int = 4):
     dt = time.perf_counter() - t0
     ind = int(st["n_before"].sum())
     sp.close()
-    return {"value": ind / dt, "unit": "individual-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{X} x {Y} torus, same species and per-patch density ({ind // steps} individuals), "
-                      f"{steps} steps after 1, single thread, {dt:.1f} s"}
+    return {"value": ind / dt}
 
 
 def cpu_baseline(workload, target_seconds=12.0):
@@ -394,8 +388,21 @@ def cpu_baseline(workload, target_seconds=12.0):
         gens += 1
     dt = time.perf_counter() - t0
     return {"value": workload.n * gens / dt, "unit": "individual-generations/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {gens} generations of the N={workload.n}, L={workload.n_loci} consumer-resource "
-                      f"population, single thread, {dt:.1f} s"}
+            "sample": f"first {gens} generations of the headline population, 1 thread, {dt:.1f} s"}
+
+
+def r3(x):
+    """Three significant digits (the bench line is kept short)."""
+    if isinstance(x, float):
+        return float(f"{x:.3g}")
+    if isinstance(x, dict):
+        return {k: r3(v) for k, v in x.items()}
+    if isinstance(x, list):
+        return [r3(v) for v in x]
+    return x
+
+
+SECTIONS = ("single", "batched", "served", "spatial", "linked", "weighted", "dominance", "continuous")
 
 
 def main():
@@ -404,30 +411,26 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true", help="omit the CPU oracle baseline measurement")
-    ap.add_argument("--no-batched", action="store_true", help="omit the batched-replicates measurement")
-    ap.add_argument("--no-served", action="store_true", help="omit the served-sweep measurement")
-    ap.add_argument("--no-spatial", action="store_true", help="omit the spatial-community measurement")
-    ap.add_argument("--no-linked", action="store_true", help="omit the linkage-map measurement")
-    ap.add_argument("--no-weighted", action="store_true", help="omit the weighted-parents measurement")
-    ap.add_argument("--no-dominance", action="store_true", help="omit the dominance measurement")
-    ap.add_argument("--no-continuous", action="store_true", help="omit the continuous-allele measurement")
-    ap.add_argument("--shape", default="", metavar="B,I",
-                    help="launch shape of the headline population: threads per block, offspring per thread; "
-                         "results do not depend on it")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="omit the CPU oracle baselines")
+    for name in SECTIONS:
+        ap.add_argument(f"--no-{name}", action="store_true", help=f"omit the {name} measurement")
+    ap.add_argument("--shape", default="", metavar="B,I,P",
+                    help="launch shape of the headline population: threads per block, offspring per thread, lanes "
+                         "per offspring; results do not depend on it")
     ap.add_argument("--only-batched", type=int, default=0, metavar="R",
                     help="run only the batched-replicates measurement on the first R replicates (profiling)")
+    ap.add_argument("--served-jobs", type=int, default=1000, help="jobs of the served trace")
     args = ap.parse_args()
     workload = S.consumer_resource()
+    if args.impl == "reference":
+        reference_arm(args, workload)
+        return
     if args.only_batched:
         import torch
         from paper_1603_09255_gb300 import build as pkg_build
         pkg_build.build()
         from paper_1603_09255_gb300 import spegg
         print(json.dumps(batched_replicates(spegg, torch, gens=args.steps, count=args.only_batched)))
-        return
-    if args.impl == "reference":
-        reference_arm(args, workload)
         return
 
     import torch
@@ -470,35 +473,18 @@ def main():
         stream.synchronize()
         barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    total_ms = max_over_ranks(total_ms, device="cuda")
+    total_ms = max_over_ranks(sum(step_ms), device="cuda")
     st = pop.state()
     assert st["status"] == 0, f"population status {st['status']}"
-    ind_gen = workload.n * GENERATIONS * args.steps
-    value = ind_gen * ws / (total_ms / 1000.0)
+    value = workload.n * GENERATIONS * args.steps * ws / (total_ms / 1000.0)
 
-    # each generation is one offspring launch and one compaction launch; the
-    # offspring kernel dominates, the pair is timed together
+    # roofline of one generation (offspring + compaction launches, timed together)
     launches = GENERATIONS * args.steps
-    avg_launch_s = total_ms / 1000.0 / launches
+    avg_gen_s = total_ms / 1000.0 / launches
     peak, peak_kind = load_peaks()
-    bytes_per_launch = algorithmic_bytes(workload.words) * workload.n
-    achieved = bytes_per_launch / avg_launch_s / 1e9
+    achieved = algorithmic_bytes(workload.words) * workload.n / avg_gen_s / 1e9
     traffic = MEASURED_TRAFFIC.get(kernel_source_hash())
-
-    # kernel-only duration and per-generation latency: single generations
-    # (direct launches) bracketed by events, after 3 untimed ones
-    pop.step(3)
-    k_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
-    for a, b in k_ev:
-        with torch.cuda.stream(stream):
-            a.record(stream)
-        pop.step(1)
-        with torch.cuda.stream(stream):
-            b.record(stream)
-    stream.synchronize()
-    gen_us = [a.elapsed_time(b) * 1000.0 for a, b in k_ev]
-    kernel_ms = statistics.median(gen_us) / 1000.0
+    gen_p50, gen_p99 = per_generation_ms(stream, torch, lambda: pop.step(1), repeats=50)
 
     # end to end through the C ABI with host buffers: restore the population
     # from pinned host memory, run the generations, read the statistics back
@@ -516,60 +502,49 @@ def main():
         e2e_times.append(time.perf_counter() - t0)
     e2e_value = workload.n * GENERATIONS * ws / (sum(e2e_times) / len(e2e_times))
     assert len(stats) == GENERATIONS
+    shape = pop.launch_shape()
+    pop.close()
 
-    oracle_cpu = rank == 0 and not args.no_cpu_baseline
-    batched = None if args.no_batched else batched_replicates(spegg, torch, oracle_cpu=oracle_cpu)
-    served = None if args.no_served else served_sweep(spegg, torch)
-    spatial = None if args.no_spatial else spatial_community(spegg, torch, oracle_cpu=oracle_cpu)
-    linked = None if args.no_linked else variant_population(
-        spegg, torch, S.with_linkage(S.consumer_resource(), 4, 1.0), "linkage map 4 chromosomes x 1 Morgan")
-    weighted = None if args.no_weighted else variant_population(
-        spegg, torch, S.with_weights(S.consumer_resource()), "parents weighted by trait (1 + tanh z; fathers 2z)")
-    dominance = None if args.no_dominance else variant_population(
-        spegg, torch, S.with_dominance(S.consumer_resource()), "dominance deviations N(0, 0.1) at every locus")
-    continuous = None if args.no_continuous else variant_population(
-        spegg, torch, S.continuous_trait(n=1_000_000, n_loci=128, mu=1e-3, mut_sd=0.05, env_sd=0.2),
-        "continuous allelic values (int16 Q8), mu 1e-3, mutation sd 0.05, environmental sd 0.2, no resource",
-        gens=64, bytes_per_offspring=12 + 12 * 128)
+    cpu = rank == 0 and not args.no_cpu_baseline
+    extra = {}
+    if not args.no_single:
+        extra["single"] = single_species(spegg, torch, cpu)
+    if not args.no_batched:
+        extra["batched"] = batched_replicates(spegg, torch, oracle_cpu=cpu)
+    if not args.no_served:
+        extra["served"] = served_sweep(spegg, torch, count=args.served_jobs)
+    if not args.no_spatial:
+        extra["spatial"] = spatial_community(spegg, torch, oracle_cpu=cpu)
+    if not args.no_linked:
+        extra["linked"] = variant_population(spegg, torch, S.with_linkage(S.consumer_resource(), 4, 1.0))
+    if not args.no_weighted:
+        extra["weighted"] = variant_population(spegg, torch, S.with_weights(S.consumer_resource()))
+    if not args.no_dominance:
+        extra["dominance"] = variant_population(spegg, torch, S.with_dominance(S.consumer_resource()))
+    if not args.no_continuous:
+        extra["continuous"] = variant_population(
+            spegg, torch, S.continuous_trait(n=1_000_000, n_loci=128, mu=1e-3, mut_sd=0.05, env_sd=0.2), gens=64,
+            bytes_per_offspring=12 + 12 * 128)
     if rank != 0:
         return
     line = {
         "metric": "individual-generations/s", "value": value, "unit": "individual-generations/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "p50_ms_per_step": float(np.percentile(step_ms, 50)), "p99_ms_per_step": float(np.percentile(step_ms, 99)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": bench_config(workload, "flushed before every step (256 MB write)"),
+        "config": bench_config(workload, "flushed"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": f"k_offspring<W={workload.words}> + k_compact (one generation)",
-                     "shape": pop.launch_shape(),
-                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6,
-                     "isolated_launch_us": kernel_ms * 1000.0},
+                     "traffic": traffic, "peak_kind": peak_kind, "shape": list(shape)},
         "e2e": {"value": e2e_value, "unit": "individual-generations/s", "h2d_bytes_per_step": len(blob),
                 "d2h_bytes_per_step": int(stats.nbytes)},
         "gpu_launches": 2 * launches,
         "clocks": clocks.summary(),
-        "per_generation": {"p50_us": float(np.percentile(gen_us, 50)), "p99_us": float(np.percentile(gen_us, 99)),
-                           "repeats": len(gen_us), "warmup": 3,
-                           "note": "one generation (two launches, no graph) bracketed by CUDA events"},
+        "gen_ms": {"p50": gen_p50, "p99": gen_p99},
     }
-    if batched is not None:
-        line["batched"] = batched
-    if served is not None:
-        line["served"] = served
-    if spatial is not None:
-        line["spatial"] = spatial
-    if linked is not None:
-        line["linked"] = linked
-    if weighted is not None:
-        line["weighted"] = weighted
-    if dominance is not None:
-        line["dominance"] = dominance
-    if continuous is not None:
-        line["continuous"] = continuous
-    if not args.no_cpu_baseline:
+    if cpu:
         line["cpu_baseline"] = cpu_baseline(workload)
-    print(json.dumps(line))
+    line["gen_ms"] = r3(line["gen_ms"])
+    line.update(r3(extra))
+    print(json.dumps(line, separators=(",", ":")))
 
 
 if __name__ == "__main__":
