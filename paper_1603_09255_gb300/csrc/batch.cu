@@ -57,24 +57,12 @@ struct MultiChain {
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
         for (const Group &g : groups) {
             if (g.members.empty() || g.gl.blocks == 0) continue;
-            GenArgs a = g.gl.args;
+            GenArgs a = g.gl.args;  // copied into the node parameters
             void *params[] = {&a};
-            cudaGraphNode_t prev = nullptr;
-            for (uint32_t i = 0; i < 2 * len; ++i) {
-                const bool off = (i % 2) == 0;
-                cudaKernelNodeParams kp{};
-                kp.func = reinterpret_cast<void *>(off ? g.gl.offspring.fn : g.gl.compact);
-                kp.gridDim = dim3(off ? g.gl.blocks : g.gl.buckets);
-                kp.blockDim = dim3(off ? g.gl.offspring.block : kCompactThreads);
-                kp.sharedMemBytes = off ? g.gl.offspring.smem : 0;
-                kp.kernelParams = params;
-                cudaGraphNode_t node;
-                e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
-                if (e != cudaSuccess) {
-                    reset();
-                    return cuda_fail(e, "cudaGraphAddKernelNode");
-                }
-                prev = node;
+            const int rc = add_generation_nodes(graph, g.gl, params, len);
+            if (rc != SPG_OK) {
+                reset();
+                return rc;
             }
         }
         e = cudaGraphInstantiate(&exec, graph, 0);

@@ -260,5 +260,14 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// ------------------------------------------- programmatic dependent launch
+// The generation kernels are launched so that a kernel may start while its
+// predecessor in the stream finishes.  griddep_wait() returns once the
+// predecessor grid has completed and its memory is visible: every read of a
+// predecessor's results comes after it.  griddep_release() lets the next
+// kernel's blocks be scheduled as this grid's blocks leave the SMs.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace
 }  // namespace spg

@@ -385,6 +385,51 @@ void GraphChain::reset() {
     length = 0;
 }
 
+// The launches of a generation kernel: grid, block, shared memory, and
+// whether it may start while its predecessor finishes (programmatic
+// dependent launch: the kernel waits with griddepcontrol.wait before reading
+// the predecessor's results).  The continuous-allele kernel does not.
+namespace {
+struct KernelLaunch {
+    void *fn;
+    dim3 grid, block;
+    unsigned smem;
+    bool programmatic;
+};
+KernelLaunch offspring_launch(const GenLaunch &gl) {
+    return {reinterpret_cast<void *>(gl.offspring.fn), dim3(gl.blocks), dim3(gl.offspring.block), gl.offspring.smem,
+            gl.offspring.persistent};
+}
+KernelLaunch compact_launch(const GenLaunch &gl) {
+    return {reinterpret_cast<void *>(gl.compact), dim3(gl.buckets), dim3(kCompactThreads), 0u, true};
+}
+}  // namespace
+
+int add_generation_nodes(cudaGraph_t graph, const GenLaunch &gl, void **params, uint32_t len) {
+    cudaGraphNode_t prev = nullptr;
+    for (uint32_t i = 0; i < 2 * len; ++i) {
+        const KernelLaunch k = (i % 2) == 0 ? offspring_launch(gl) : compact_launch(gl);
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeKernel;
+        np.kernel.func = k.fn;
+        np.kernel.gridDim = k.grid;
+        np.kernel.blockDim = k.block;
+        np.kernel.sharedMemBytes = k.smem;
+        np.kernel.kernelParams = params;
+        cudaGraphEdgeData edge{};
+        if (k.programmatic) {
+            edge.from_port = cudaGraphKernelNodePortProgrammatic;
+            edge.type = cudaGraphDependencyTypeProgrammatic;
+        }
+        cudaGraphNode_t node;
+        const cudaError_t e = cudaGraphAddNode(&node, graph, prev ? &prev : nullptr, prev ? &edge : nullptr,
+                                               prev ? 1 : 0, &np);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddNode");
+        prev = node;
+    }
+    return SPG_OK;
+}
+
 // A graph of `len` generations: offspring -> compaction -> offspring -> ...
 int GraphChain::build(const GenLaunch &gl, uint32_t len) {
     reset();
@@ -392,22 +437,10 @@ int GraphChain::build(const GenLaunch &gl, uint32_t len) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
     GenArgs a = gl.args;
     void *params[] = {&a};
-    cudaGraphNode_t prev = nullptr;
-    for (uint32_t i = 0; i < 2 * len; ++i) {
-        const bool off = (i % 2) == 0;
-        cudaKernelNodeParams kp{};
-        kp.func = reinterpret_cast<void *>(off ? gl.offspring.fn : gl.compact);
-        kp.gridDim = dim3(off ? gl.blocks : gl.buckets);
-        kp.blockDim = dim3(off ? gl.offspring.block : kCompactThreads);
-        kp.sharedMemBytes = off ? gl.offspring.smem : 0;
-        kp.kernelParams = params;
-        cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
-        if (e != cudaSuccess) {
-            reset();
-            return cuda_fail(e, "cudaGraphAddKernelNode");
-        }
-        prev = node;
+    const int rc = add_generation_nodes(graph, gl, params, len);
+    if (rc != SPG_OK) {
+        reset();
+        return rc;
     }
     e = cudaGraphInstantiate(&exec, graph, 0);
     if (e != cudaSuccess) {
@@ -419,9 +452,23 @@ int GraphChain::build(const GenLaunch &gl, uint32_t len) {
 }
 
 int launch_generation(const GenLaunch &gl, cudaStream_t stream) {
-    gl.offspring.fn<<<gl.blocks, gl.offspring.block, gl.offspring.smem, stream>>>(gl.args);
-    gl.compact<<<gl.buckets, kCompactThreads, 0, stream>>>(gl.args);
-    const cudaError_t e = cudaGetLastError();
+    GenArgs a = gl.args;
+    void *params[] = {&a};
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaError_t e = cudaSuccess;
+    for (const KernelLaunch &k : {offspring_launch(gl), compact_launch(gl)}) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = k.grid;
+        cfg.blockDim = k.block;
+        cfg.dynamicSmemBytes = k.smem;
+        cfg.stream = stream;
+        cfg.attrs = &attr;
+        cfg.numAttrs = k.programmatic ? 1u : 0u;
+        e = cudaLaunchKernelExC(&cfg, k.fn, params);
+        if (e != cudaSuccess) break;
+    }
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "generation launch");
 }
 

@@ -603,6 +603,8 @@ __device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
 
 template <int W>
 __global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const __grid_constant__ GenArgs a) {
+    griddep_release();  // the next generation's blocks may take this grid's place as its blocks finish
+    griddep_wait();     // everything below reads the offspring kernel's results
     const uint32_t bkt = blockIdx.x;
     if (a.nsegs == 1u) {
         compact_bucket<W>(a.one, bkt);

@@ -660,18 +660,13 @@ __global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspri
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t dyn_addr = (uint32_t)__cvta_generic_to_shared(s_dyn);
 
+    griddep_release();  // the next kernel's blocks may take this grid's place as its blocks finish
     uint32_t r = 0, r_end = 1;
     if (a.nsegs != 1u) {
         r = __ldg(a.block_runs + blockIdx.x);
         r_end = __ldg(a.block_runs + blockIdx.x + 1u);
-        if (r < r_end) {  // the first run's parents: this block's share of them, now
-            const Run run = a.runs[r];
-            const Segment &sg = a.segs[run.seg];
-            if (sg.dense)
-                prefetch_parents<W, BLOCK>(sg.dense, (uint32_t)(((unsigned long long)sg.n * run.share) / run.shares),
-                                           (uint32_t)(((unsigned long long)sg.n * (run.share + 1u)) / run.shares), tid);
-        }
     }
+    bool first = true;  // the first run's tables are copied while the previous kernel finishes
     for (; r < r_end; ++r) {
         uint32_t lt0, lt1;
         const Segment *sgp;
@@ -685,23 +680,53 @@ __global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspri
             sgp = a.segs + run.seg;
             lt0 = run.tile0;
             lt1 = run.tile0 + run.count;
-            if (r + 1u < r_end) {  // the next run's parents into L2 while this run is formed
-                const Run nx = a.runs[r + 1u];
-                const Segment &sn = a.segs[nx.seg];
-                if (sn.dense)
-                    prefetch_parents<W, BLOCK>(sn.dense, (uint32_t)(((unsigned long long)sn.n * nx.share) / nx.shares),
-                                               (uint32_t)(((unsigned long long)sn.n * (nx.share + 1u)) / nx.shares),
-                                               tid);
-            }
         }
         if (lt0 >= lt1) continue;
         const Segment &sg = *sgp;
+        // the run's tables (parameters only: nothing the previous kernel writes)
+        const PopParams *P = sg.prm;
+        const uint32_t dlut = P->has_dom ? a.smem_dlut : 0u;  // 0 also when the launch has no dominance tables
+        cp_async_wait<0>();  // a skipped run's copies have landed
+        __syncthreads();     // the previous run's tables and statistics scratch are no longer read
+        copy_tables<W, BLOCK>(P, a.eco_table != 0u, P->has_eco != 0u, dyn_addr, a.smem_dlut, dlut != 0u, tid);
+        if (tid < kMaxKmax) s_cdf[tid] = (uint32_t)tid < P->kmax ? P->cdf[tid] : 0u;
+        if constexpr (LINKED) {
+            const LinkParams *lp = P->link;
+            lk.kmax = lp->kmax;
+            lk.nchrom = lp->nchrom;
+            for (uint32_t i = tid; i < 32u * W; i += BLOCK) {
+                s_lcum[i] = lp->cum[i];
+                s_lchrom[i] = lp->chrom[i];
+            }
+            if (tid < kMaxKmax) s_lcdf[tid] = lp->cdf[tid];
+            for (uint32_t i = tid; i < (uint32_t)kLinkGuide; i += BLOCK) s_lguide[i] = lp->guide[i];
+            if (tid < kMaxChrom) {
+                s_lfirst[tid] = lp->first[tid];
+                s_lclast[tid] = lp->clast[tid];
+            }
+        }
+        if (first) {  // from here on: the previous kernel's state, records and counters
+            griddep_wait();
+            first = false;
+            if (a.nsegs != 1u && sg.dense) {  // the first run's parents: this block's share of them, now
+                const Run run = a.runs[r];
+                prefetch_parents<W, BLOCK>(sg.dense, (uint32_t)(((unsigned long long)sg.n * run.share) / run.shares),
+                                           (uint32_t)(((unsigned long long)sg.n * (run.share + 1u)) / run.shares), tid);
+            }
+        }
+        if (a.nsegs != 1u && r + 1u < r_end) {  // the next run's parents into L2 while this run is formed
+            const Run nx = a.runs[r + 1u];
+            const Segment &sn = a.segs[nx.seg];
+            if (sn.dense)
+                prefetch_parents<W, BLOCK>(sn.dense, (uint32_t)(((unsigned long long)sn.n * nx.share) / nx.shares),
+                                           (uint32_t)(((unsigned long long)sn.n * (nx.share + 1u)) / nx.shares), tid);
+        }
         const PopNow now = read_state(sg.state);
         if (!now.active) continue;
         SegCtx c;
-        c.P = sg.prm;
+        c.P = P;
         c.n = sg.n;
-        c.S = now.S;
+        c.S = min(now.S, sg.n);  // parent ranks stay inside the buffers whatever the state holds
         c.f = now.f;
         c.g = now.gen + 1u;
         c.sin = sg.dense ? nullptr : sg.surv[now.gen & 1u];
@@ -719,26 +744,7 @@ __global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspri
         c.shift = c.P->shift;
         c.bias = c.P->bias;
         c.eco = a.eco_table != 0u;
-        c.dlut = c.P->has_dom ? a.smem_dlut : 0u;  // 0 also when the launch has no dominance tables
-
-        __syncthreads();  // the previous run's tables and statistics scratch are no longer read
-        copy_tables<W, BLOCK>(c.P, c.eco, c.P->has_eco != 0u, dyn_addr, a.smem_dlut, c.dlut != 0u, tid);
-        if (tid < kMaxKmax) s_cdf[tid] = (uint32_t)tid < c.kmax ? c.P->cdf[tid] : 0u;
-        if constexpr (LINKED) {
-            const LinkParams *lp = c.P->link;
-            lk.kmax = lp->kmax;
-            lk.nchrom = lp->nchrom;
-            for (uint32_t i = tid; i < 32u * W; i += BLOCK) {
-                s_lcum[i] = lp->cum[i];
-                s_lchrom[i] = lp->chrom[i];
-            }
-            if (tid < kMaxKmax) s_lcdf[tid] = lp->cdf[tid];
-            for (uint32_t i = tid; i < (uint32_t)kLinkGuide; i += BLOCK) s_lguide[i] = lp->guide[i];
-            if (tid < kMaxChrom) {
-                s_lfirst[tid] = lp->first[tid];
-                s_lclast[tid] = lp->clast[tid];
-            }
-        }
+        c.dlut = dlut;
 
         ThreadStats ts;
         uint32_t warp_alive = 0;

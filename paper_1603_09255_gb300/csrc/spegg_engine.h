@@ -91,7 +91,12 @@ Shape default_shape(uint32_t words);
 constexpr uint32_t kAutotuneCandidates = SPG_AUTOTUNE_CANDIDATES;  // launch shapes timed per group
 Shape autotune_candidate(uint32_t words, uint32_t c);
 int shape_from_abi(uint32_t words, const spg_launch_shape *in, Shape &out);
+// One generation's launches (each kernel may start while its predecessor in
+// the stream finishes; see griddep_wait in the kernels).
 int launch_generation(const GenLaunch &gl, cudaStream_t stream);
+// Append a chain of `len` generations of one launch group to a graph
+// (kernel nodes joined by programmatic edges); params: the GenArgs pointer.
+int add_generation_nodes(cudaGraph_t graph, const GenLaunch &gl, void **params, uint32_t len);
 size_t group_table_bytes(uint32_t members, uint64_t offspring, uint32_t buckets);
 uint32_t tiles_for(uint32_t n, const Shape &shape);
 void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_run, std::vector<Run> &runs,
