@@ -260,6 +260,46 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// ------------------------------------- bulk copies and shared barriers
+// mbarrier objects (8 bytes of shared memory each) completing when their
+// arrivals and expected bytes are in; bulk asynchronous copies (the non-tensor
+// TMA path) from global to shared memory completing on one of them.  Every
+// wait is bounded.
+constexpr uint32_t kMbarTries = 1u << 22;  // try_wait calls before a wait gives up
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// Make initialised barriers visible to the asynchronous (bulk copy) proxy.
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Whether the phase of parity `parity` completed within kMbarTries tries.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kMbarTries; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// One thread: `bytes` (a multiple of 16; both addresses 16-byte aligned) from
+// global src to shared dst, completing the current phase of barrier bar
+// (count 1) once they have landed.  Shared memory that generic loads read
+// before is ordered ahead of the copy by the proxy fence.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // ------------------------------------------- programmatic dependent launch
 // The generation kernels are launched so that a kernel may start while its
 // predecessor in the stream finishes.  griddep_wait() returns once the

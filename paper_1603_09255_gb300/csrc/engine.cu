@@ -401,7 +401,7 @@ KernelLaunch offspring_launch(const GenLaunch &gl) {
             gl.offspring.persistent};
 }
 KernelLaunch compact_launch(const GenLaunch &gl) {
-    return {reinterpret_cast<void *>(gl.compact), dim3(gl.buckets), dim3(kCompactThreads), 0u, true};
+    return {reinterpret_cast<void *>(gl.compact), dim3(gl.buckets), dim3(kCompactThreads), compact_smem(), true};
 }
 }  // namespace
 

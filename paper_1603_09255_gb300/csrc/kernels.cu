@@ -484,17 +484,187 @@ __global__ void k_founders_cont(const PopParams *__restrict__ P, uint32_t *__res
 // One block per bucket of kBucket offspring.  Its first kBucketWords threads
 // read the bucket's bitmap words and the survivor counts of all earlier
 // buckets and scan the words' popcounts; then kCompactCopyThreads threads
-// (8 warps, 16 bitmap words each) write every survivor's index, in offspring
-// order, at its rank = (survivors of earlier buckets) + (survivors before it
-// in the bucket), and, for populations with a dense parent buffer, its record
-// at the same rank (the parents of the next generation, read by rank without
-// an index hop).  In a population's first bucket an extra warp closes the
-// generation meanwhile (finalize_warp).  The block that finishes the last
-// bucket commits the new state.  Every load that does not depend on the
-// population state is issued together with it (both parities of the bucket
-// counts are summed; the state picks one).
+// (8 warps) write every survivor's index, in offspring order, at its rank =
+// (survivors of earlier buckets) + (survivors before it in the bucket), and,
+// for populations with a dense parent buffer, its record at the same rank
+// (the parents of the next generation, read by rank without an index hop).
+// The bucket's child records reach shared memory by bulk asynchronous copies
+// of kChunkBytes each into a ring of kRingSlots slots (issued by one thread
+// before the scan, the next chunk into a slot as soon as the copy threads are
+// done with it), so the record copy is a stream of large reads instead of a
+// dependent load per survivor; the survivors are stored from shared memory
+// with whole-sector stores.  In a population's first bucket an extra warp
+// closes the generation meanwhile (finalize_warp).  The block that finishes
+// the last bucket commits the new state.  Every load that does not depend on
+// the population state is issued together with it (both parities of the
+// bucket counts are summed; the state picks one).
+// 32 KB of ring per block: rings of 64 KB and more measured up to 40%
+// slower, alone and next to other launch groups' offspring kernels
+constexpr uint32_t kChunkBytes = 16384;  // bytes of one bulk copy of child records (one ring slot)
+constexpr uint32_t kRingSlots = 2;       // chunks in flight per block
+
 __device__ __forceinline__ void compaction_barrier() {
     asm volatile("bar.sync 1, %0;" ::"n"(kCompactCopyThreads) : "memory");  // the compaction threads
+}
+
+// A record of 2W words from shared memory (16-byte chunks, 8-byte for W = 1).
+template <int W>
+__device__ __forceinline__ void ring_record(uint32_t addr, uint32_t (&r)[2 * W]) {
+    if constexpr (W == 1) {
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(addr) : "memory");
+    } else {
+#pragma unroll
+        for (int q = 0; q < W / 2; ++q)
+            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r[4 * q]), "=r"(r[4 * q + 1]), "=r"(r[4 * q + 2]), "=r"(r[4 * q + 3])
+                         : "r"(addr + 16u * q)
+                         : "memory");
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
+    constexpr int NW = kBucketWords / 32;          // warps that scan the bitmap words
+    constexpr uint32_t REC = 8u * W;               // bytes per record
+    constexpr uint32_t CHUNK = kChunkBytes / REC;  // offspring per ring slot
+    constexpr uint32_t SLOT = kChunkBytes;         // bytes per ring slot
+    constexpr uint32_t NCHUNK = kBucket / CHUNK;   // ring fills per bucket
+    constexpr int CW = (int)(CHUNK / 32);          // bitmap words per chunk
+    constexpr int WPW = CW / (int)(kCompactCopyThreads / 32);  // bitmap words per copying warp and chunk
+    static_assert(kBucket % CHUNK == 0 && WPW >= 1, "chunks split the bucket among the copying warps");
+    extern __shared__ __align__(128) unsigned char s_ring[];  // [kRingSlots][SLOT]
+    __shared__ alignas(8) unsigned long long s_bar[kRingSlots];
+    __shared__ uint32_t s_warp[NW];
+    __shared__ uint32_t s_prev[NW];
+    __shared__ uint32_t s_bits[kBucketWords], s_incl[kBucketWords];
+    __shared__ uint32_t s_last, s_timeout;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool closer = tid >= (int)kCompactCopyThreads;  // the generation-closing warp
+    const bool scanner = tid < (int)kBucketWords;
+    const uint32_t valid_words = (sg.n + 31u) >> 5;
+    const uint32_t w = b * kBucketWords + (uint32_t)tid;
+    const uint32_t bits = (scanner && w < valid_words) ? __ldcg(sg.alive + w) : 0u;
+    uint32_t prev0 = 0, prev1 = 0;
+    for (uint32_t i = (uint32_t)tid; scanner && i < b; i += kBucketWords) {
+        prev0 += __ldcg(sg.bucket_sum + i);
+        prev1 += __ldcg(sg.bucket_sum + sg.nbuckets + i);
+    }
+    const PopNow now = read_state(sg.state);
+    const uint32_t g = now.gen + 1u;
+    const uint32_t first = b * kBucket, nb = min(kBucket, sg.n - first);  // the bucket's offspring
+    const uint32_t nchunks = (nb + CHUNK - 1u) / CHUNK;
+    const bool ring = sg.dense != nullptr && now.active;
+    const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(s_ring);
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&s_bar[0]);
+    const uint32_t *__restrict__ chi = sg.geno[g & 1u];
+    // chunk c of the bucket into ring slot c % kRingSlots (a partial last
+    // chunk rounded up to 16 bytes: record buffers are padded to 256 bytes)
+    auto fill = [&](uint32_t c) {
+        const uint32_t off = first + c * CHUNK, cnt = min(CHUNK, nb - c * CHUNK);
+        bulk_load(ring0 + (c % kRingSlots) * SLOT, chi + (size_t)off * (2 * W), (cnt * REC + 15u) & ~15u,
+                  bar0 + 8u * (c % kRingSlots));
+    };
+    if (tid == 0) {
+        s_timeout = 0u;
+        if (ring) {
+            for (uint32_t k = 0; k < kRingSlots; ++k) mbar_init(bar0 + 8u * k, 1u);
+            mbar_init_fence();
+            for (uint32_t c = 0; c < kRingSlots && c < nchunks; ++c) fill(c);
+        }
+    }
+    __syncthreads();  // barriers initialised
+    if (!now.active) return;
+    if (closer) {
+        if (b == 0u) finalize_warp(sg, sg.prm, g, now.f);
+        __threadfence();
+    } else {
+        if (scanner) {
+            const uint32_t prev = __reduce_add_sync(0xFFFFFFFFu, (g & 1u) ? prev1 : prev0);
+            uint32_t incl = __popc(bits);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            s_bits[tid] = bits;
+            s_incl[tid] = incl;
+            if (lane == 31) s_warp[warp] = incl;
+            if (lane == 0) s_prev[warp] = prev;
+        }
+        compaction_barrier();
+        uint32_t before = 0;  // survivors of all earlier buckets
+#pragma unroll
+        for (int q = 0; q < NW; ++q) before += s_prev[q];
+        uint32_t *__restrict__ sout = sg.surv[g & 1u];
+        uint32_t *__restrict__ dense = sg.dense;
+        const uint32_t lt = (1u << lane) - 1u;
+        for (uint32_t c = 0; c < NCHUNK; ++c) {
+            if (c >= nchunks) break;
+            if (ring && !mbar_wait(bar0 + 8u * (c % kRingSlots), (c / kRingSlots) & 1u)) s_timeout = 1u;
+            const uint32_t slot = ring0 + (c % kRingSlots) * SLOT;
+#pragma unroll
+            for (int k = 0; k < WPW; ++k) {
+                const int q = (int)c * CW + warp * WPW + k;  // bitmap word of the bucket
+                const uint32_t word = s_bits[q];
+                uint32_t r0 = before + s_incl[q] - __popc(word);
+#pragma unroll
+                for (int v = 0; v < NW; ++v) r0 += v < q / 32 ? s_warp[v] : 0u;
+                if ((word >> lane) & 1u) {
+                    const uint32_t rank = r0 + __popc(word & lt), idx = first + (uint32_t)q * 32u + lane;
+                    sout[rank] = idx;
+                    if (ring) {
+                        uint32_t rec[2 * W];
+                        ring_record<W>(slot + ((uint32_t)(q - (int)c * CW) * 32u + lane) * REC, rec);
+                        store_record<W>(dense + (size_t)rank * (2 * W), rec);
+                    }
+                    if (sg.survw) {  // the survivor's acceptance thresholds as mother and as father
+                        const uint32_t bin = __ldcg(sg.obin + idx);
+                        const WeightParams *wt = sg.prm->weights;
+                        sg.survw[rank] = (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[0][bin]) << 32);
+                        sg.survw[sg.n + rank] =
+                            (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[1][bin]) << 32);
+                    }
+                }
+            }
+            if (ring && c + kRingSlots < nchunks) {  // the slot is free once every copying thread is past it
+                compaction_barrier();
+                if (tid == 0 && !s_timeout) fill(c + kRingSlots);
+            }
+        }
+    }
+    // every block has read the state by now (its values fed the stores
+    // above), and the closing warp of bucket 0 has published the next state
+    __syncthreads();
+    if (tid == 0) {
+        if (s_timeout) {  // a copy did not land in time: the generation fails; wait (bounded) for
+                          // the last copy issued into each slot before the block's memory goes away
+            atomicExch(reinterpret_cast<int *>(&sg.state->status), SPG_ERR_TIMEOUT);
+            for (uint32_t k = 0; k < kRingSlots && k < nchunks; ++k) {
+                uint32_t lastc = k;
+                while (lastc + kRingSlots < nchunks) lastc += kRingSlots;
+                mbar_wait(bar0 + 8u * k, (lastc / kRingSlots) & 1u);
+            }
+        }
+        s_last = (atomicAdd(&sg.state->done, 1u) == sg.nbuckets - 1u) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last && tid == 0) {
+        __threadfence();
+        commit_state(sg.state, g);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kCompactThreads, 3) k_compact(const __grid_constant__ GenArgs a) {
+    griddep_release();  // the next generation's blocks may take this grid's place as its blocks finish
+    griddep_wait();     // everything below reads the offspring kernel's results
+    const uint32_t bkt = blockIdx.x;
+    if (a.nsegs == 1u) {
+        compact_bucket<W>(a.one, bkt);
+    } else {
+        const Segment &sg = a.segs[__ldg(a.bucket_seg + bkt)];
+        compact_bucket<W>(sg, bkt - sg.bucket_begin);
+    }
 }
 
 // A record of 2W words read through L2 and written with whole-sector stores.
@@ -520,98 +690,6 @@ __device__ __forceinline__ void copy_record(const uint32_t *__restrict__ src, ui
                          : "l"(src + 8 * q));
     }
     store_record<W>(dst, r);
-}
-
-template <int W>
-__device__ __forceinline__ void compact_bucket(const Segment &sg, uint32_t b) {
-    constexpr int NW = kBucketWords / 32;                     // warps that scan the bitmap words
-    constexpr int WPW = kBucketWords / (kCompactCopyThreads / 32);  // bitmap words per copying warp
-    __shared__ uint32_t s_warp[NW];
-    __shared__ uint32_t s_prev[NW];
-    __shared__ uint32_t s_bits[kBucketWords], s_incl[kBucketWords];
-    __shared__ uint32_t s_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool closer = tid >= (int)kCompactCopyThreads;  // the generation-closing warp
-    const bool scanner = tid < (int)kBucketWords;
-    const uint32_t valid_words = (sg.n + 31u) >> 5;
-    const uint32_t w = b * kBucketWords + (uint32_t)tid;
-    const uint32_t bits = (scanner && w < valid_words) ? __ldcg(sg.alive + w) : 0u;
-    uint32_t prev0 = 0, prev1 = 0;
-    for (uint32_t i = (uint32_t)tid; scanner && i < b; i += kBucketWords) {
-        prev0 += __ldcg(sg.bucket_sum + i);
-        prev1 += __ldcg(sg.bucket_sum + sg.nbuckets + i);
-    }
-    const PopNow now = read_state(sg.state);
-    if (!now.active) return;
-    const uint32_t g = now.gen + 1u;
-    if (closer) {
-        if (b == 0u) finalize_warp(sg, sg.prm, g, now.f);
-        __threadfence();
-    } else {
-        if (scanner) {
-            const uint32_t prev = __reduce_add_sync(0xFFFFFFFFu, (g & 1u) ? prev1 : prev0);
-            uint32_t incl = __popc(bits);
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            s_bits[tid] = bits;
-            s_incl[tid] = incl;
-            if (lane == 31) s_warp[warp] = incl;
-            if (lane == 0) s_prev[warp] = prev;
-        }
-        compaction_barrier();
-        uint32_t before = 0;  // survivors of all earlier buckets
-#pragma unroll
-        for (int q = 0; q < NW; ++q) before += s_prev[q];
-        uint32_t *__restrict__ sout = sg.surv[g & 1u];
-        const uint32_t *__restrict__ chi = sg.geno[g & 1u];
-        uint32_t *__restrict__ dense = sg.dense;
-        const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll 4
-        for (int k = 0; k < WPW; ++k) {
-            const int q = warp * WPW + k;  // bitmap word of the bucket
-            const uint32_t word = s_bits[q];
-            uint32_t r0 = before + s_incl[q] - __popc(word);
-#pragma unroll
-            for (int v = 0; v < NW; ++v) r0 += v < q / 32 ? s_warp[v] : 0u;
-            if ((word >> lane) & 1u) {
-                const uint32_t rank = r0 + __popc(word & lt), idx = (b * kBucketWords + (uint32_t)q) * 32u + lane;
-                sout[rank] = idx;
-                if (dense) copy_record<W>(chi + (size_t)idx * (2 * W), dense + (size_t)rank * (2 * W));
-                if (sg.survw) {  // the survivor's acceptance thresholds as mother and as father
-                    const uint32_t bin = __ldcg(sg.obin + idx);
-                    const WeightParams *wt = sg.prm->weights;
-                    sg.survw[rank] = (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[0][bin]) << 32);
-                    sg.survw[sg.n + rank] =
-                        (unsigned long long)idx | ((unsigned long long)__ldg(&wt->acc[1][bin]) << 32);
-                }
-            }
-        }
-    }
-    // every block has read the state by now (its values fed the stores
-    // above), and the closing warp of bucket 0 has published the next state
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&sg.state->done, 1u) == sg.nbuckets - 1u) ? 1u : 0u;
-    __syncthreads();
-    if (s_last && tid == 0) {
-        __threadfence();
-        commit_state(sg.state, g);
-    }
-}
-
-template <int W>
-__global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const __grid_constant__ GenArgs a) {
-    griddep_release();  // the next generation's blocks may take this grid's place as its blocks finish
-    griddep_wait();     // everything below reads the offspring kernel's results
-    const uint32_t bkt = blockIdx.x;
-    if (a.nsegs == 1u) {
-        compact_bucket<W>(a.one, bkt);
-    } else {
-        const Segment &sg = a.segs[__ldg(a.bucket_seg + bkt)];
-        compact_bucket<W>(sg, bkt - sg.bucket_begin);
-    }
 }
 
 // dense[r] = geno[surv[r]] (surv null: r) for r < S: the dense parent buffer
@@ -723,13 +801,20 @@ bool supported_shape(uint32_t words, const Shape &s) {
 
 uint32_t tile_size(const Shape &s) { return s.block * s.items / s.lanes; }
 
+uint32_t compact_smem() { return kRingSlots * kChunkBytes; }
+
 GenKernel compact_kernel(uint32_t words) {
+    GenKernel k;
     switch (words) {
-        case 2: return &k_compact<2>;
-        case 4: return &k_compact<4>;
-        case 8: return &k_compact<8>;
-        default: return &k_compact<1>;  // and populations without a dense buffer (no record copies)
+        case 2: k = &k_compact<2>; break;
+        case 4: k = &k_compact<4>; break;
+        case 8: k = &k_compact<8>; break;
+        default: k = &k_compact<1>; break;  // and populations without a dense buffer (no record copies)
     }
+    // the ring of bulk-copied child records is dynamic shared memory
+    cudaFuncSetAttribute(reinterpret_cast<const void *>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)compact_smem());
+    return k;
 }
 
 int launch_dense_gather(uint32_t words, const uint32_t *geno, const uint32_t *surv, uint32_t S, uint32_t *dense,

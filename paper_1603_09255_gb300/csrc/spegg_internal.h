@@ -204,6 +204,7 @@ bool supported_shape(uint32_t words, const Shape &shape);
 OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom);
 int prepare_offspring(OffspringKernel &k);  // sets the shared-memory limit, fills `resident`
 GenKernel compact_kernel(uint32_t words);  // the compaction kernel for records of 2W words
+uint32_t compact_smem();                   // its dynamic shared memory (the ring of child records)
 uint32_t tile_size(const Shape &shape);  // offspring per tile: block * items / lanes
 // Copy the offspring kernel's shape and shared-memory layout into a launch.
 void apply_kernel(const OffspringKernel &k, GenArgs &a);
