@@ -25,8 +25,10 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
     constexpr uint32_t WA = 0x9E3779B9u, WB = 0xBB67AE85u;
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t hi0 = __umulhi(A, c.x), lo0 = A * c.x;
-        const uint32_t hi1 = __umulhi(B, c.z), lo1 = B * c.z;
+        // each 32 x 32 -> 64-bit product as one wide multiply (both halves)
+        const unsigned long long p0 = (unsigned long long)A * c.x, p1 = (unsigned long long)B * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += WA;
         k1 += WB;
