@@ -555,7 +555,7 @@ int build_group_launch(const std::vector<const PopView *> &members, uint32_t wor
         return fail(SPG_ERR_INVALID,
                     "unsupported launch shape (%u threads, %u offspring per thread, %u lanes per offspring) for %u loci",
                     shape.block, shape.items, shape.lanes, 32u * words);
-    OffspringKernel k = offspring_kernel(words, shape, false, false, eco, dom);
+    OffspringKernel k = offspring_kernel(words, shape, false, false, eco, dom, true);  // members in HBM: staged
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
     std::vector<Segment> segs;

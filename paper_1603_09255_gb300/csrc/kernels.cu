@@ -787,10 +787,10 @@ __global__ void k_set_state(DevState *st, StatAcc *acc, uint32_t gen, uint32_t S
 
 }  // namespace
 
-OffspringKernel offspring_kernel_w1(const Shape &shape, bool linked, bool weighted);
-OffspringKernel offspring_kernel_w2(const Shape &shape, bool linked, bool weighted);
-OffspringKernel offspring_kernel_w4(const Shape &shape, bool linked, bool weighted);
-OffspringKernel offspring_kernel_w8(const Shape &shape, bool linked, bool weighted);
+OffspringKernel offspring_kernel_w1(const Shape &shape, bool linked, bool weighted, bool staged);
+OffspringKernel offspring_kernel_w2(const Shape &shape, bool linked, bool weighted, bool staged);
+OffspringKernel offspring_kernel_w4(const Shape &shape, bool linked, bool weighted, bool staged);
+OffspringKernel offspring_kernel_w8(const Shape &shape, bool linked, bool weighted, bool staged);
 
 bool supported_shape(uint32_t words, const Shape &s) {
     if (!(s.block == 128 || s.block == 256 || s.block == 512)) return false;
@@ -832,13 +832,15 @@ int launch_dense_gather(uint32_t words, const uint32_t *geno, const uint32_t *su
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
 }
 
-OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom) {
+OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom,
+                                 bool staged) {
+    staged = staged && kStagedParents && words <= 4 && shape.lanes == 1 && !linked && !weighted;
     OffspringKernel k;
     switch (words) {
-        case 1: k = offspring_kernel_w1(shape, linked, weighted); break;
-        case 2: k = offspring_kernel_w2(shape, linked, weighted); break;
-        case 4: k = offspring_kernel_w4(shape, linked, weighted); break;
-        case 8: k = offspring_kernel_w8(shape, linked, weighted); break;
+        case 1: k = offspring_kernel_w1(shape, linked, weighted, staged); break;
+        case 2: k = offspring_kernel_w2(shape, linked, weighted, staged); break;
+        case 4: k = offspring_kernel_w4(shape, linked, weighted, staged); break;
+        case 8: k = offspring_kernel_w8(shape, linked, weighted, staged); break;
         default: return OffspringKernel{};
     }
     if (!k.fn) return k;
@@ -851,6 +853,10 @@ OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked
     k.eco_table = eco ? 1u : 0u;
     k.smem_dlut = dom ? lut + tab : 0u;
     k.smem = lut + tab + (dom ? lut : 0u);
+    if (staged) {  // the ring of staged parent records
+        k.smem_parents = k.smem;
+        k.smem += kParentStages * 2u * k.block * k.items * 8u * words;
+    }
     return k;
 }
 
@@ -892,6 +898,7 @@ int prepare_offspring(OffspringKernel &k) {
 void apply_kernel(const OffspringKernel &k, GenArgs &a) {
     a.eco_table = k.eco_table;
     a.smem_dlut = k.smem_dlut;
+    a.smem_parents = k.smem_parents;
 }
 
 int launch_founders_cont(const PopParams *prm, uint32_t n_loci, uint32_t *geno, uint32_t *surv, uint32_t n,

@@ -101,7 +101,7 @@ extern "C" int spg_generation_noalloc(const spg_noalloc_generation *a, void *str
     prm.stats_cap = 1;  // the caller's single statistics record
     prm.has_eco = 0;
 
-    OffspringKernel k = offspring_kernel(W, shape, false, false, false, false);
+    OffspringKernel k = offspring_kernel(W, shape, false, false, false, false, false);
     rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
     const uint32_t ntiles = tiles_for(a->n, shape), nbuckets = bucket_count(a->n);

@@ -400,6 +400,118 @@ __device__ __forceinline__ void offspring_run(const SegCtx &c, uint32_t lt0, uin
     if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
 }
 
+// ------------------------------------------------- staged parent records
+// The single-lane kernels without linkage or weights keep their parents'
+// records in a shared-memory ring of kParentStages tiles instead of
+// registers: each thread copies its own items' records with cp.async
+// kParentStages - 1 tiles ahead and reads them back when it forms the tile,
+// so the loads in flight hold no registers and need no block barrier.  Slot
+// x = it * BLOCK + tid of stage s, parent p: 16-byte planes q (8-byte slots
+// for W = 1), plane-major so a warp's accesses are conflict-free.
+template <int W, int ITEMS, int BLOCK>
+__device__ __forceinline__ uint32_t parent_slot(uint32_t ring, uint32_t s, uint32_t p, uint32_t q, uint32_t x) {
+    constexpr uint32_t TILE = (uint32_t)(BLOCK * ITEMS);
+    if constexpr (W == 1) return ring + ((s * 2u + p) * TILE + x) * 8u;
+    else return ring + (((s * 2u + p) * (uint32_t)(W / 2) + q) * TILE + x) * 16u;
+}
+
+template <int W, int ITEMS, int BLOCK>
+__device__ __forceinline__ void stage_parents(const SegCtx &c, uint32_t base, int tid, const TileDraws<ITEMS> &d,
+                                              uint32_t ring, uint32_t s) {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t j = base + (uint32_t)(it * BLOCK + tid), x = (uint32_t)(it * BLOCK + tid);
+        if (j < c.n) {
+#pragma unroll
+            for (uint32_t p = 0; p < 2u; ++p) {
+                const uint32_t *src = c.par + (size_t)(p ? d.dad[it] : d.mom[it]) * (2 * W);
+                if constexpr (W == 1) {
+                    cp_async_8(parent_slot<W, ITEMS, BLOCK>(ring, s, p, 0u, x), src);
+                } else {
+#pragma unroll
+                    for (uint32_t q = 0; q < (uint32_t)(W / 2); ++q)
+                        cp_async_16(parent_slot<W, ITEMS, BLOCK>(ring, s, p, q, x), src + 4u * q);
+                }
+            }
+        }
+    }
+    cp_async_commit();  // one group per tile (empty past the run's end), so group counts stay uniform
+}
+
+template <int W, int ITEMS, int BLOCK>
+__device__ __forceinline__ void read_parents(uint32_t ring, uint32_t s, int tid, TileRecs<W, ITEMS> &rec) {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t x = (uint32_t)(it * BLOCK + tid);
+#pragma unroll
+        for (uint32_t p = 0; p < 2u; ++p) {
+            uint32_t(&r)[2 * W] = p ? rec.f[it] : rec.m[it];
+            if constexpr (W == 1) {
+                asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                             : "=r"(r[0]), "=r"(r[1])
+                             : "r"(parent_slot<W, ITEMS, BLOCK>(ring, s, p, 0u, x))
+                             : "memory");
+            } else {
+#pragma unroll
+                for (uint32_t q = 0; q < (uint32_t)(W / 2); ++q)
+                    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                                 : "=r"(r[4 * q]), "=r"(r[4 * q + 1]), "=r"(r[4 * q + 2]), "=r"(r[4 * q + 3])
+                                 : "r"(parent_slot<W, ITEMS, BLOCK>(ring, s, p, q, x))
+                                 : "memory");
+            }
+        }
+    }
+}
+
+// Tiles [lt0, lt1) of one run with staged parents: at tile t the records of
+// tile t+2 are requested, those of tile t (requested two tiles earlier) read
+// back, and the draws of tile t+3 made.
+template <int W, int ITEMS, int BLOCK>
+__device__ __forceinline__ void offspring_run_staged(const SegCtx &c, uint32_t lt0, uint32_t lt1,
+                                                     uint32_t *bucket_next, int tid, int lane, int warp,
+                                                     const uint32_t *s_cdf, ThreadStats &ts, const LinkSmem &lk,
+                                                     uint32_t &warp_alive, uint32_t ring) {
+    static_assert(kParentStages == 3, "the draws rotate through three tiles");
+    constexpr uint32_t TILE = (uint32_t)(BLOCK * ITEMS);
+    TileDraws<ITEMS> d0, d1, d2;
+    draw_parents<ITEMS, BLOCK, false>(c, lt0 * TILE, tid, d0);
+    draw_parents<ITEMS, BLOCK, false>(c, (lt0 + 1) * TILE, tid, d1);  // past the run: no effect (j >= n) or unused
+    draw_parents<ITEMS, BLOCK, false>(c, (lt0 + 2) * TILE, tid, d2);
+    stage_parents<W, ITEMS, BLOCK>(c, lt0 * TILE, tid, d0, ring, 0u);
+    if (lt0 + 1 < lt1) stage_parents<W, ITEMS, BLOCK>(c, (lt0 + 1) * TILE, tid, d1, ring, 1u);
+    else cp_async_commit();
+    cp_async_wait<2>();  // the run's tables (committed before the two parent groups)
+    __syncthreads();     // ... and the cdf are visible to every thread
+
+    uint32_t bucket_alive = 0, bucket_cur = (lt0 * TILE) / kBucket;
+    uint32_t s = 0;  // ring stage of tile lt
+    for (uint32_t lt = lt0; lt < lt1; ++lt) {
+        const uint32_t base = lt * TILE;
+        const uint32_t s2 = s >= 1u ? s - 1u : 2u;  // stage of tile lt + 2
+        if (lt + 2 < lt1) stage_parents<W, ITEMS, BLOCK>(c, base + 2 * TILE, tid, d2, ring, s2);
+        else cp_async_commit();
+        if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
+        const uint32_t bkt = base / kBucket;
+        if (bkt != bucket_cur) {
+            if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
+            bucket_alive = 0;
+            bucket_cur = bkt;
+        }
+        cp_async_wait<2>();  // this thread's records of tile lt have landed
+        TileRecs<W, ITEMS> rec;
+        read_parents<W, ITEMS, BLOCK>(ring, s, tid, rec);
+        const uint32_t cnt =
+            offspring_tile<W, ITEMS, BLOCK, false, false>(c, base, tid, lane, warp, rec, d0, s_cdf, ts, lk);
+        bucket_alive += cnt;
+        warp_alive += cnt;
+        d0 = d1;
+        d1 = d2;
+        if (lt + 3 < lt1) draw_parents<ITEMS, BLOCK, false>(c, base + 3 * TILE, tid, d2);
+        s = s == 2u ? 0u : s + 1u;
+    }
+    if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
+}
+
 // ----------------------------------------------------------- lane pairs
 // The second launch shape for L = 128 and 256 ("words per thread"): two lanes
 // per offspring.  Lane h of a pair (h = 0 mother, 1 father) draws that
@@ -639,9 +751,10 @@ __device__ __forceinline__ void pair_run(const SegCtx &c, uint32_t lt0, uint32_t
     if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
 }
 
-template <int W, int ITEMS, int BLOCK, bool LINKED, bool WEIGHTED, bool PAIR>
+template <int W, int ITEMS, int BLOCK, bool LINKED, bool WEIGHTED, bool PAIR, bool STAGED>
 __global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspring_min_blocks(BLOCK))
     k_offspring(const __grid_constant__ GenArgs a) {
+    static_assert(!STAGED || (W <= 4 && !LINKED && !WEIGHTED && !PAIR), "staged parents: plain single-lane kernels");
     constexpr int NW = BLOCK / 32;
     constexpr uint32_t TILE = (uint32_t)(BLOCK * ITEMS) / (PAIR ? 2u : 1u);
     static_assert(kBucket % TILE == 0, "tiles must not straddle compaction buckets");
@@ -749,6 +862,9 @@ __global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspri
         uint32_t warp_alive = 0;
         if constexpr (PAIR)
             pair_run<W, ITEMS, BLOCK>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, warp_alive);
+        else if constexpr (STAGED)
+            offspring_run_staged<W, ITEMS, BLOCK>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, lk, warp_alive,
+                                                  dyn_addr + a.smem_parents);
         else
             offspring_run<W, ITEMS, BLOCK, LINKED, WEIGHTED>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, lk,
                                                              warp_alive);
@@ -807,10 +923,11 @@ __global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspri
 }
 
 // Host-side description of one instance: entry and shape.
-template <int W, int ITEMS, int BLOCK, bool LINKED = false, bool WEIGHTED = false, bool PAIR = false>
+template <int W, int ITEMS, int BLOCK, bool LINKED = false, bool WEIGHTED = false, bool PAIR = false,
+          bool STAGED = false>
 OffspringKernel offspring_instance() {
     OffspringKernel k;
-    k.fn = &k_offspring<W, ITEMS, BLOCK, LINKED, WEIGHTED, PAIR>;
+    k.fn = &k_offspring<W, ITEMS, BLOCK, LINKED, WEIGHTED, PAIR, STAGED>;
     k.block = BLOCK;
     k.items = ITEMS;
     k.lanes = PAIR ? 2u : 1u;

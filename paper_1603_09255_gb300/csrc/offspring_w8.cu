@@ -1,11 +1,12 @@
 // Offspring kernel instances for L = 256 loci (W = 8 words per haplotype):
-// every supported launch shape of the plain kernel, and the linkage-map and
-// weighted-parent variants (256 threads, one offspring each).
+// every supported launch shape of the plain kernel,
+// and the linkage-map and weighted-parent variants (256 threads, one
+// offspring each).
 #include "offspring.cuh"
 
 namespace spg {
 
-OffspringKernel offspring_kernel_w8(const Shape &s, bool linked, bool weighted) {
+OffspringKernel offspring_kernel_w8(const Shape &s, bool linked, bool weighted, bool staged) {
     if (linked || weighted) {
         if (s.block != 256 || s.items != 1 || s.lanes != 1) return OffspringKernel{};
         if (linked && weighted) return offspring_instance<8, 1, 256, true, true>();

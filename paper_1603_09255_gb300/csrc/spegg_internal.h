@@ -21,6 +21,11 @@ constexpr uint32_t kBucketWords = kBucket / 32;    // bitmap words per bucket = 
 constexpr uint32_t kCompactCopyThreads = 256;  // threads that write a bucket's survivors (8 warps)
 constexpr uint32_t kCompactThreads = kCompactCopyThreads + 32;  // + one warp that closes the generation
 constexpr uint32_t kCertain = 0xFFFFFFFFu;
+// Single-lane offspring kernels for L <= 128 without linkage or weights copy their parent
+// records into a shared-memory ring of kParentStages tiles with cp.async
+// (each thread its own records, kParentStages - 1 tiles ahead).
+constexpr bool kStagedParents = true;
+constexpr uint32_t kParentStages = 3;
 constexpr int kAccCopies = 16;    // copies of the statistics accumulators (spread atomics)
 
 constexpr int kMaxLoci = 256;
@@ -172,6 +177,7 @@ struct GenArgs {
     // eco_table, the dominance byte tables at smem_dlut (0: none)
     uint32_t eco_table;
     uint32_t smem_dlut;
+    uint32_t smem_parents;  // the ring of staged parent records (single-lane kernels without linkage or weights)
     Segment one;           // the segment itself when nsegs == 1 (read from kernel parameters)
 };
 
@@ -191,7 +197,7 @@ struct Shape {
 struct OffspringKernel {
     GenKernel fn = nullptr;
     uint32_t words = 0, block = 256, items = 1, lanes = 1;
-    uint32_t eco_table = 0, smem_dlut = 0;
+    uint32_t eco_table = 0, smem_dlut = 0, smem_parents = 0;
     uint32_t smem = 0;
     uint32_t resident = 0;
     bool persistent = true;
@@ -201,7 +207,13 @@ struct OffspringKernel {
 bool supported_shape(uint32_t words, const Shape &shape);
 // The offspring kernel of a shape; eco: some population of the launch has an
 // ecology (the survival table carries attack rates), dom: some has dominance.
-OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom);
+// staged: stage the parents through shared memory where the kernel supports
+// it (for parents resident in HBM rather than L2).
+OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom,
+                                 bool staged);
+// Parent records above this many bytes (N x 8W) are staged in a single
+// population's launch; launch groups always stage.
+constexpr size_t kStageParentBytes = (size_t)48 << 20;
 int prepare_offspring(OffspringKernel &k);  // sets the shared-memory limit, fills `resident`
 GenKernel compact_kernel(uint32_t words);  // the compaction kernel for records of 2W words
 uint32_t compact_smem();                   // its dynamic shared memory (the ring of child records)
