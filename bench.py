@@ -290,6 +290,12 @@ def served_sweep(spegg, torch, count: int = 1000, rate: float = 200.0):
     work = sum(w.n * i["gen"] for w, i in zip(ws, infos))
     makespan = max(i["t_finish"] for i in infos) - min(i["t_arrival"] for i in infos)
     value = work / makespan
+    # steady state: the work of the jobs finishing between the 10th and 90th
+    # percentile completion times, over that window (the ramp-up and the drain
+    # of the last long jobs excluded)
+    fin = sorted((i["t_finish"], w.n * i["gen"]) for w, i in zip(ws, infos))
+    lo, hi = len(fin) // 10, (9 * len(fin)) // 10
+    steady = sum(x for _, x in fin[lo + 1:hi + 1]) / max(fin[hi][0] - fin[lo][0], 1e-9)
     # the plain path on the same mix: each job created, stepped and read alone
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
@@ -300,7 +306,7 @@ def served_sweep(spegg, torch, count: int = 1000, rate: float = 200.0):
         p.read_stats(1, g)
         p.close()
     plain = work / (time.perf_counter() - t0)
-    return {"value": value, "vs_plain": value / plain, "p50_s": float(np.percentile(lat, 50)),
+    return {"value": value, "steady": steady, "vs_plain": value / plain, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "jobs": count, "load": rate * (work / count) / value,
             "resident": c["peak_resident"]}
 

@@ -40,6 +40,7 @@ namespace spg {
 namespace {
 
 constexpr int kSpBlock = 256;
+constexpr int kSpClassBlock = 128;  // threads of the per-deme classify blocks
 constexpr uint32_t kMaxSpecies = 4;
 enum SpPurpose : uint32_t { kSpFounder = 1, kSpMate = 2, kSpRecomb = 3, kSpMutPos = 4, kSpSurv = 5, kSpDisp = 6 };
 constexpr uint32_t kDead = 15u;
@@ -320,9 +321,9 @@ __global__ void k_sp_scan(SpaceArgs a, int which) {
 template <int IPT, int Q0, int Q1>
 __device__ __forceinline__ void class_ranks(const uint32_t (&cls)[IPT], uint32_t (&rk)[IPT], uint32_t *s_carry,
                                             uint32_t (*s_wt)[8]) {
-    constexpr int NQ = Q1 - Q0, NW = kSpBlock / 32;
+    constexpr int NQ = Q1 - Q0, NW = kSpClassBlock / 32;
     constexpr uint32_t C0 = 2u * Q0;
-    static_assert(kSpBlock * IPT <= 65535 && Q1 <= 8 && IPT <= 7 && NQ <= 5, "field widths");
+    static_assert(kSpClassBlock * IPT <= 65535 && Q1 <= 8 && IPT <= 7 && NQ <= 5, "field widths");
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t mine = 0, before[IPT];
 #pragma unroll
@@ -385,13 +386,17 @@ __device__ __forceinline__ void class_ranks(const uint32_t (&cls)[IPT], uint32_t
 // direction of every newborn (its mate and dispersal draws), and each item's
 // stable rank within its (age class, direction) class.  Members (classes
 // 0-9) go kSpIPT consecutive ones per thread, so all their loads are in
-// flight together; newborns (classes 10-14) one per thread.  The newborns'
-// records are formed by k_sp_births.
-constexpr int kSpIPT = 4;
+// flight together; newborns (classes 10-14) kSpNbIPT per thread.  A block
+// of kSpClassBlock threads ranks a typical deme (~800 members, ~150
+// newborns) in one pass each, so the fixed cost of the two class scans is
+// spread over all of its items.  The newborns' records are formed by
+// k_sp_births.
+constexpr int kSpIPT = 7;
+constexpr int kSpNbIPT = 2;  // newborns per thread
 
-__global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
+__global__ void __launch_bounds__(kSpClassBlock) k_sp_classify(SpaceArgs a) {
     __shared__ uint32_t s_carry[16];
-    __shared__ uint32_t s_wt[kSpBlock / 32][8];
+    __shared__ uint32_t s_wt[kSpClassBlock / 32][8];
     if (a.state->status != SPG_OK) return;
     const uint32_t d = blockIdx.x, s = d / a.P, tid = threadIdx.x;
     const uint32_t t = a.state->t + 1u, par = a.state->t & 1u;
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
     long long sum_raw = 0;
     uint32_t surv = 0, moved = 0;
     // pre-existing members, in rank order
-    for (uint32_t p0 = 0; p0 < n; p0 += kSpBlock * kSpIPT) {
+    for (uint32_t p0 = 0; p0 < n; p0 += kSpClassBlock * kSpIPT) {
         const uint32_t r0 = p0 + tid * kSpIPT;
         uint32_t ag[kSpIPT], cls[kSpIPT], rk[kSpIPT];
         int32_t raw[kSpIPT];
@@ -443,22 +448,30 @@ __global__ void __launch_bounds__(kSpBlock) k_sp_classify(SpaceArgs a) {
     }
     // newborns, in birth order: dispersal from the mate draw's third lane,
     // direction from the dispersal draw
-    for (uint32_t c0 = 0; c0 < B; c0 += kSpBlock) {
-        const uint32_t k = c0 + tid;
-        uint32_t cls[1] = {kDead}, rk[1];
-        const bool fits = nb0 + k < a.staging_cap;
-        if (k < B && fits) {
-            const uint4 u = sp_philox(make_uint4(k, t, d, kSpMate << 24), a.key0, a.key1);
-            uint32_t dir = 0;
-            if (u.z < a.disp_q32) dir = 1u + __umulhi(sp_philox(make_uint4(k, t, d, kSpDisp << 24), a.key0, a.key1).x, 4u);
-            cls[0] = 2u * 5u + dir;
-            moved += dir != 0;
+    for (uint32_t c0 = 0; c0 < B; c0 += kSpClassBlock * kSpNbIPT) {
+        uint32_t cls[kSpNbIPT], rk[kSpNbIPT];
+#pragma unroll
+        for (int i = 0; i < kSpNbIPT; ++i) {
+            const uint32_t k = c0 + tid * kSpNbIPT + (uint32_t)i;
+            cls[i] = kDead;
+            if (k < B && nb0 + k < a.staging_cap) {
+                const uint4 u = sp_philox(make_uint4(k, t, d, kSpMate << 24), a.key0, a.key1);
+                uint32_t dir = 0;
+                if (u.z < a.disp_q32)
+                    dir = 1u + __umulhi(sp_philox(make_uint4(k, t, d, kSpDisp << 24), a.key0, a.key1).x, 4u);
+                cls[i] = 2u * 5u + dir;
+                moved += dir != 0;
+            }
         }
-        class_ranks<1, 5, 8>(cls, rk, s_carry, s_wt);
-        if (k < B && fits) {
-            a.nb_cls[nb0 + k] = (uint8_t)cls[0];
-            a.nb_rank[nb0 + k] = rk[0];
-            a.nb_deme[nb0 + k] = d;
+        class_ranks<kSpNbIPT, 5, 8>(cls, rk, s_carry, s_wt);
+#pragma unroll
+        for (int i = 0; i < kSpNbIPT; ++i) {
+            const uint32_t k = c0 + tid * kSpNbIPT + (uint32_t)i;
+            if (k < B && nb0 + k < a.staging_cap) {
+                a.nb_cls[nb0 + k] = (uint8_t)cls[i];
+                a.nb_rank[nb0 + k] = rk[i];
+                a.nb_deme[nb0 + k] = d;
+            }
         }
     }
     if (tid < 15) a.cnt[(size_t)d * 15 + tid] = s_carry[tid];
@@ -724,7 +737,7 @@ int launch_step(spg_space *c) {
     const uint32_t g = (a.nd + 255) / 256;
     k_sp_plan<<<g, 256, 0, s>>>(a);
     k_sp_scan<<<1, 1024, 0, s>>>(a, 0);
-    k_sp_classify<<<a.nd, kSpBlock, 0, s>>>(a);
+    k_sp_classify<<<a.nd, kSpClassBlock, 0, s>>>(a);
     k_sp_totals<<<g, 256, 0, s>>>(a);
     k_sp_scan<<<1, 1024, 0, s>>>(a, 1);
     k_sp_births<W><<<c->births_grid, kSpBlock, 0, s>>>(a);
