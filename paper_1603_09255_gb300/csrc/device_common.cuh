@@ -132,6 +132,7 @@ struct LinkSmem {
     const uint16_t *first, *clast;
     const uint32_t *guide;
     uint32_t kmax, nchrom;
+    uint32_t *tog;  // warp-cooperative crossovers: per warp, gamete and lane, W toggle words + 3 parity words
 };
 
 template <int W>
@@ -141,72 +142,118 @@ __device__ __forceinline__ void toggle_bit(uint32_t (&t)[W], uint32_t pos) {
         if ((uint32_t)w == (pos >> 5)) t[w] ^= 1u << (pos & 31u);
 }
 
-// Origin mask of one gamete under the linkage map (bit set: the locus comes
-// from the parent's haplotype 1): every chromosome whose coin is 1 and every
-// crossover flips the loci from its start to the chromosome's end.  Each
-// flip is two toggles (at the first flipped locus and one past the last); a
-// crossover toggles its start and flips its chromosome's parity bit, and the
-// end toggles, which cancel in pairs, are applied once per chromosome whose
-// coin and parity differ.  A prefix XOR over the L bits turns the toggles
-// into the mask.
+// Origin masks of both gametes of a warp's 32 offspring under the linkage
+// map (bit set: the locus comes from the parent's haplotype 1); all lanes
+// take part, valid = false gives a lane no crossovers.  Every chromosome
+// whose coin is 1 and every crossover flips the loci from its start to the
+// chromosome's end.  Each flip is two toggles (at the first flipped locus and
+// one past the last); a crossover toggles its start and flips its
+// chromosome's parity bit, and the end toggles, which cancel in pairs, are
+// applied once per chromosome whose coin and parity differ.  A prefix XOR
+// over the L bits turns the toggles into the mask.  The crossovers are dealt
+// to the warp's lanes one Philox block (up to four crossovers of one gamete)
+// at a time instead of each lane looping over its own, which would run the
+// warp to its lanes' largest count; a crossover's toggle and parity flip go
+// to the owner's words in shared memory by atomic XOR (flips commute, so the
+// order does not matter), and each lane then finishes its own two masks.
 template <int W>
-__device__ __forceinline__ void linked_mask(const LinkSmem &lk, uint32_t j, uint32_t g, uint32_t rep, uint32_t pi,
-                                            uint32_t k0, uint32_t k1, uint32_t (&m)[W]) {
-    constexpr uint32_t L = 32u * W;
-    const uint4 d0 = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8)), k0, k1);
-    uint32_t t[W];
+__device__ __forceinline__ void linked_masks_warp(const LinkSmem &lk, uint32_t j, bool valid, uint32_t g, uint32_t rep,
+                                                  uint32_t k0, uint32_t k1, uint32_t (&mm)[W], uint32_t (&mf)[W]) {
+    constexpr uint32_t L = 32u * W, NWD = (uint32_t)W + 3u;  // words per gamete: toggles, parity
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t *tog = lk.tog + warp * (2u * 32u * NWD);        // [gamete][lane][NWD]
+    uint4 d0[2];
+    uint32_t K[2];
 #pragma unroll
-    for (int w = 0; w < W; ++w) t[w] = 0u;
-    uint32_t par0 = 0, par1 = 0, par2 = 0;  // crossovers per chromosome, mod 2 (chromosomes 0-31, 32-63, 64-95)
-    uint32_t K = 0;
-    if (lk.kmax != 0u && d0.x >= lk.cdf[0]) {  // K = #{i < kmax : cdf[i] <= u} by bisection (the CDF is non-decreasing)
-        K = 1u;
+    for (uint32_t pi = 0; pi < 2u; ++pi) {
+        d0[pi] = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8)), k0, k1);
+        uint32_t k = 0;
+        if (valid && lk.kmax != 0u && d0[pi].x >= lk.cdf[0]) {
+            k = 1u;
 #pragma unroll
-        for (uint32_t step = 16u; step > 0u; step >>= 1)
-            if (K + step <= lk.kmax && lk.cdf[K + step - 1u] <= d0.x) K += step;
-    }
-    uint4 d = d0;
-    for (uint32_t a = 0; a < K; ++a) {
-        if ((a & 3u) == 0u) d = philox(make_uint4(j, g, rep, (kLink << 24) | (pi << 8) | (1u + a / 4u)), k0, k1);
-        const uint32_t u = lane_of(d, (int)(a & 3u));
-        // interval I = #{l <= L-2 : cum[l] <= u} and its chromosome: the guide
-        // entry of u's top bits when no boundary lies inside that bucket, one
-        // comparison when one does, a forward search otherwise
-        const uint32_t ge = lk.guide[u >> (32 - kLinkGuideBits)], nb = ge >> 26;
-        uint32_t I = ge & 0xFFu, ch = (ge >> 8) & 0x7Fu;
-        if (nb == 1u) {
-            if (lk.cum[I] <= u) {
-                ++I;
-                ch = (ge >> 15) & 0x7Fu;
-            }
-        } else if (nb > 1u) {
-            while (I + 1u < L && lk.cum[I] <= u) ++I;
-            ch = lk.chrom[I];
+            for (uint32_t step = 16u; step > 0u; step >>= 1)
+                if (k + step <= lk.kmax && lk.cdf[k + step - 1u] <= d0[pi].x) k += step;
         }
-        toggle_bit<W>(t, I);
-        const uint32_t cb = 1u << (ch & 31u);
-        par0 ^= ch < 32u ? cb : 0u;
-        par1 ^= (ch >= 32u && ch < 64u) ? cb : 0u;
-        par2 ^= ch >= 64u ? cb : 0u;
-    }
-    for (uint32_t c = 0; c < lk.nchrom; ++c) {
-        const uint32_t coin = ((c < 32u ? d0.y : c < 64u ? d0.z : d0.w) >> (c & 31u)) & 1u;
-        const uint32_t par = ((c < 32u ? par0 : c < 64u ? par1 : par2) >> (c & 31u)) & 1u;
-        if (coin) toggle_bit<W>(t, lk.first[c]);
-        if ((coin ^ par) && lk.clast[c] + 1u < L) toggle_bit<W>(t, lk.clast[c] + 1u);
-    }
-    uint32_t carry = 0;
+        K[pi] = k;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-        uint32_t x = t[w];
-        x ^= x << 1;
-        x ^= x << 2;
-        x ^= x << 4;
-        x ^= x << 8;
-        x ^= x << 16;
-        x ^= 0u - carry;
-        m[w] = x;
-        carry = x >> 31;
+        for (uint32_t w = 0; w < NWD; ++w) tog[(pi * 32u + lane) * NWD + w] = 0u;
+    }
+    // this lane's Philox blocks of crossovers, both gametes, and the warp's offsets
+    const uint32_t nb0 = (K[0] + 3u) >> 2, nb = nb0 + ((K[1] + 3u) >> 2);
+    uint32_t off = nb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, off, o);
+        if ((int)lane >= o) off += y;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, off, 31);
+    off -= nb;  // exclusive
+    __syncwarp();
+    for (uint32_t f0 = 0; f0 < total; f0 += 32u) {
+        const uint32_t f = f0 + lane;
+        uint32_t o = 0;  // the owner: the last lane whose offset is <= f
+#pragma unroll
+        for (uint32_t step = 16u; step > 0u; step >>= 1) {
+            const uint32_t v = __shfl_sync(0xFFFFFFFFu, off, (int)(o + step));
+            if (v <= f) o += step;
+        }
+        const uint32_t oj = __shfl_sync(0xFFFFFFFFu, j, (int)o), ooff = __shfl_sync(0xFFFFFFFFu, off, (int)o);
+        const uint32_t onb0 = __shfl_sync(0xFFFFFFFFu, nb0, (int)o);
+        const uint32_t oK0 = __shfl_sync(0xFFFFFFFFu, K[0], (int)o), oK1 = __shfl_sync(0xFFFFFFFFu, K[1], (int)o);
+        if (f < total) {
+            const uint32_t b = f - ooff, pi = b < onb0 ? 0u : 1u, blk = pi ? b - onb0 : b, Kp = pi ? oK1 : oK0;
+            const uint4 d = philox(make_uint4(oj, g, rep, (kLink << 24) | (pi << 8) | (1u + blk)), k0, k1);
+            uint32_t *ot = tog + (pi * 32u + o) * NWD;
+#pragma unroll
+            for (uint32_t l = 0; l < 4u; ++l) {
+                if (4u * blk + l < Kp) {
+                    const uint32_t u = lane_of(d, (int)l);
+                    const uint32_t ge = lk.guide[u >> (32 - kLinkGuideBits)], nbd = ge >> 26;
+                    uint32_t I = ge & 0xFFu, ch = (ge >> 8) & 0x7Fu;
+                    if (nbd == 1u) {
+                        if (lk.cum[I] <= u) {
+                            ++I;
+                            ch = (ge >> 15) & 0x7Fu;
+                        }
+                    } else if (nbd > 1u) {
+                        while (I + 1u < L && lk.cum[I] <= u) ++I;
+                        ch = lk.chrom[I];
+                    }
+                    atomicXor(ot + (I >> 5), 1u << (I & 31u));
+                    atomicXor(ot + W + (ch >> 5), 1u << (ch & 31u));
+                }
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (uint32_t pi = 0; pi < 2u; ++pi) {
+        const uint32_t *mt = tog + (pi * 32u + lane) * NWD;
+        uint32_t t[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) t[w] = mt[w];
+        const uint32_t par0 = mt[W], par1 = mt[W + 1], par2 = mt[W + 2];
+        const uint4 dd = d0[pi];
+        for (uint32_t c = 0; c < lk.nchrom; ++c) {
+            const uint32_t coin = ((c < 32u ? dd.y : c < 64u ? dd.z : dd.w) >> (c & 31u)) & 1u;
+            const uint32_t par = ((c < 32u ? par0 : c < 64u ? par1 : par2) >> (c & 31u)) & 1u;
+            if (coin) toggle_bit<W>(t, lk.first[c]);
+            if ((coin ^ par) && lk.clast[c] + 1u < L) toggle_bit<W>(t, lk.clast[c] + 1u);
+        }
+        uint32_t carry = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint32_t x = t[w];
+            x ^= x << 1;
+            x ^= x << 2;
+            x ^= x << 4;
+            x ^= x << 8;
+            x ^= x << 16;
+            x ^= 0u - carry;
+            if (pi == 0u) mm[w] = x;
+            else mf[w] = x;
+            carry = x >> 31;
+        }
     }
 }
 

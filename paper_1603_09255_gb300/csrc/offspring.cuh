@@ -260,15 +260,15 @@ __device__ __forceinline__ uint32_t offspring_tile(const SegCtx &c, uint32_t bas
     for (int it = 0; it < ITEMS; ++it) {
         const uint32_t j = base + (uint32_t)(it * BLOCK + tid);
         bool alive = false;
+        uint32_t mm[LINKED ? W : 1], mf[LINKED ? W : 1];
+        if constexpr (LINKED)  // (B) the linkage-map masks, by the whole warp
+            linked_masks_warp<W>(lk, j, j < c.n, c.g, c.rep, c.k0, c.k1, mm, mf);
         if (j < c.n) {
             const uint32_t(&pm)[2 * W] = rec.m[it];
             const uint32_t(&pf)[2 * W] = rec.f[it];
             uint32_t ch[2 * W];
             if constexpr (LINKED) {
                 // (B) gametes under the linkage map
-                uint32_t mm[W], mf[W];
-                linked_mask<W>(lk, j, c.g, c.rep, 0u, c.k0, c.k1, mm);
-                linked_mask<W>(lk, j, c.g, c.rep, 1u, c.k0, c.k1, mf);
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
                     ch[w] = (pm[w] & ~mm[w]) | (pm[W + w] & mm[w]);
@@ -768,7 +768,8 @@ __global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspri
     __shared__ uint8_t s_lchrom[LK * kMaxLoci + 1];
     __shared__ uint16_t s_lfirst[LK * kMaxChrom + 1], s_lclast[LK * kMaxChrom + 1];
     __shared__ uint32_t s_lguide[LK * kLinkGuide + 1];
-    LinkSmem lk{s_lcdf, s_lcum, s_lchrom, s_lfirst, s_lclast, s_lguide, 0u, 0u};
+    __shared__ uint32_t s_ltog[LK * NW * 2 * 32 * (W + 3) + 1];
+    LinkSmem lk{s_lcdf, s_lcum, s_lchrom, s_lfirst, s_lclast, s_lguide, 0u, 0u, s_ltog};
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t dyn_addr = (uint32_t)__cvta_generic_to_shared(s_dyn);
