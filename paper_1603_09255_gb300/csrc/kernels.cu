@@ -834,7 +834,7 @@ int launch_dense_gather(uint32_t words, const uint32_t *geno, const uint32_t *su
 
 OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom,
                                  bool staged) {
-    staged = staged && kStagedParents && words <= 4 && shape.lanes == 1 && !linked && !weighted;
+    staged = staged && kStagedParents && words <= 4 && shape.lanes == 1 && !linked;
     OffspringKernel k;
     switch (words) {
         case 1: k = offspring_kernel_w1(shape, linked, weighted, staged); break;

@@ -466,7 +466,7 @@ __device__ __forceinline__ void read_parents(uint32_t ring, uint32_t s, int tid,
 // Tiles [lt0, lt1) of one run with staged parents: at tile t the records of
 // tile t+2 are requested, those of tile t (requested two tiles earlier) read
 // back, and the draws of tile t+3 made.
-template <int W, int ITEMS, int BLOCK>
+template <int W, int ITEMS, int BLOCK, bool WEIGHTED>
 __device__ __forceinline__ void offspring_run_staged(const SegCtx &c, uint32_t lt0, uint32_t lt1,
                                                      uint32_t *bucket_next, int tid, int lane, int warp,
                                                      const uint32_t *s_cdf, ThreadStats &ts, const LinkSmem &lk,
@@ -474,9 +474,9 @@ __device__ __forceinline__ void offspring_run_staged(const SegCtx &c, uint32_t l
     static_assert(kParentStages == 3, "the draws rotate through three tiles");
     constexpr uint32_t TILE = (uint32_t)(BLOCK * ITEMS);
     TileDraws<ITEMS> d0, d1, d2;
-    draw_parents<ITEMS, BLOCK, false>(c, lt0 * TILE, tid, d0);
-    draw_parents<ITEMS, BLOCK, false>(c, (lt0 + 1) * TILE, tid, d1);  // past the run: no effect (j >= n) or unused
-    draw_parents<ITEMS, BLOCK, false>(c, (lt0 + 2) * TILE, tid, d2);
+    draw_parents<ITEMS, BLOCK, WEIGHTED>(c, lt0 * TILE, tid, d0);
+    draw_parents<ITEMS, BLOCK, WEIGHTED>(c, (lt0 + 1) * TILE, tid, d1);  // past the run: no effect (j >= n) or unused
+    draw_parents<ITEMS, BLOCK, WEIGHTED>(c, (lt0 + 2) * TILE, tid, d2);
     stage_parents<W, ITEMS, BLOCK>(c, lt0 * TILE, tid, d0, ring, 0u);
     if (lt0 + 1 < lt1) stage_parents<W, ITEMS, BLOCK>(c, (lt0 + 1) * TILE, tid, d1, ring, 1u);
     else cp_async_commit();
@@ -501,12 +501,12 @@ __device__ __forceinline__ void offspring_run_staged(const SegCtx &c, uint32_t l
         TileRecs<W, ITEMS> rec;
         read_parents<W, ITEMS, BLOCK>(ring, s, tid, rec);
         const uint32_t cnt =
-            offspring_tile<W, ITEMS, BLOCK, false, false>(c, base, tid, lane, warp, rec, d0, s_cdf, ts, lk);
+            offspring_tile<W, ITEMS, BLOCK, false, WEIGHTED>(c, base, tid, lane, warp, rec, d0, s_cdf, ts, lk);
         bucket_alive += cnt;
         warp_alive += cnt;
         d0 = d1;
         d1 = d2;
-        if (lt + 3 < lt1) draw_parents<ITEMS, BLOCK, false>(c, base + 3 * TILE, tid, d2);
+        if (lt + 3 < lt1) draw_parents<ITEMS, BLOCK, WEIGHTED>(c, base + 3 * TILE, tid, d2);
         s = s == 2u ? 0u : s + 1u;
     }
     if (lane == 0 && bucket_alive) atomicAdd(&c.bucket_now[bucket_cur], bucket_alive);
@@ -754,7 +754,7 @@ __device__ __forceinline__ void pair_run(const SegCtx &c, uint32_t lt0, uint32_t
 template <int W, int ITEMS, int BLOCK, bool LINKED, bool WEIGHTED, bool PAIR, bool STAGED>
 __global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspring_min_blocks(BLOCK))
     k_offspring(const __grid_constant__ GenArgs a) {
-    static_assert(!STAGED || (W <= 4 && !LINKED && !WEIGHTED && !PAIR), "staged parents: plain single-lane kernels");
+    static_assert(!STAGED || (W <= 4 && !LINKED && !PAIR), "staged parents: single-lane kernels without linkage");
     constexpr int NW = BLOCK / 32;
     constexpr uint32_t TILE = (uint32_t)(BLOCK * ITEMS) / (PAIR ? 2u : 1u);
     static_assert(kBucket % TILE == 0, "tiles must not straddle compaction buckets");
@@ -864,7 +864,8 @@ __global__ void __launch_bounds__(BLOCK, PAIR ? pair_min_blocks(BLOCK) : offspri
         if constexpr (PAIR)
             pair_run<W, ITEMS, BLOCK>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, warp_alive);
         else if constexpr (STAGED)
-            offspring_run_staged<W, ITEMS, BLOCK>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, lk, warp_alive,
+            offspring_run_staged<W, ITEMS, BLOCK, WEIGHTED>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, lk,
+                                                            warp_alive,
                                                   dyn_addr + a.smem_parents);
         else
             offspring_run<W, ITEMS, BLOCK, LINKED, WEIGHTED>(c, lt0, lt1, bucket_next, tid, lane, warp, s_cdf, ts, lk,

@@ -10,7 +10,9 @@ OffspringKernel offspring_kernel_w2(const Shape &s, bool linked, bool weighted, 
     if (linked || weighted) {
         if (s.block != 256 || s.items != 1 || s.lanes != 1) return OffspringKernel{};
         if (linked && weighted) return offspring_instance<2, 1, 256, true, true>();
-        return linked ? offspring_instance<2, 1, 256, true, false>() : offspring_instance<2, 1, 256, false, true>();
+        if (linked) return offspring_instance<2, 1, 256, true, false>();
+        return staged ? offspring_instance<2, 1, 256, false, true, false, true>()
+                      : offspring_instance<2, 1, 256, false, true>();
     }
     if (s.block == 128 && s.items == 1 && s.lanes == 1)
         return staged ? offspring_instance<2, 1, 128, false, false, false, true>()

@@ -68,7 +68,7 @@ int configure_launch(spg_pop *p, const Shape &shape) {
             return fail(SPG_ERR_INVALID,
                         "a population with a linkage map or parent weights runs 256 threads, one offspring each");
         k = offspring_kernel(p->words, shape, prm.linked != 0u, prm.weighted != 0u, prm.has_eco != 0u,
-                             prm.has_dom != 0u, (size_t)p->n * 8u * p->words > kStageParentBytes);
+                             prm.has_dom != 0u, prm.weighted != 0u || (size_t)p->n * 8u * p->words > kStageParentBytes);
     }
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");

@@ -21,7 +21,7 @@ constexpr uint32_t kBucketWords = kBucket / 32;    // bitmap words per bucket = 
 constexpr uint32_t kCompactCopyThreads = 256;  // threads that write a bucket's survivors (8 warps)
 constexpr uint32_t kCompactThreads = kCompactCopyThreads + 32;  // + one warp that closes the generation
 constexpr uint32_t kCertain = 0xFFFFFFFFu;
-// Single-lane offspring kernels for L <= 128 without linkage or weights copy their parent
+// Single-lane offspring kernels for L <= 128 without linkage copy their parent
 // records into a shared-memory ring of kParentStages tiles with cp.async
 // (each thread its own records, kParentStages - 1 tiles ahead).
 constexpr bool kStagedParents = true;
@@ -212,7 +212,7 @@ bool supported_shape(uint32_t words, const Shape &shape);
 OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked, bool weighted, bool eco, bool dom,
                                  bool staged);
 // Parent records above this many bytes (N x 8W) are staged in a single
-// population's launch; launch groups always stage.
+// population's launch; launch groups and weighted populations always stage.
 constexpr size_t kStageParentBytes = (size_t)48 << 20;
 int prepare_offspring(OffspringKernel &k);  // sets the shared-memory limit, fills `resident`
 GenKernel compact_kernel(uint32_t words);  // the compaction kernel for records of 2W words
