@@ -18,7 +18,8 @@
 // two for L = 256): random reads are bounded by the number of L2 requests, and
 // one request per 32-byte sector is the minimum.  The records of tile t+1 are
 // loaded into registers while tile t is formed, the draws of tile t+2 made
-// before that.  In a launch over many populations a block also prefetches its
+// before that; or, for parents in HBM, they go through a shared-memory ring
+// two tiles ahead (staged parent records, below).  In a launch over many populations a block also prefetches its
 // next run's parent records into L2 with one bulk prefetch per 16 KB, so the
 // random reads of a population resident in HBM hit L2 (random 32-byte reads
 // from DRAM run at a fraction of the sequential bandwidth).
@@ -401,11 +402,14 @@ __device__ __forceinline__ void offspring_run(const SegCtx &c, uint32_t lt0, uin
 }
 
 // ------------------------------------------------- staged parent records
-// The single-lane kernels without linkage or weights keep their parents'
+// The single-lane kernels for L <= 128 without linkage keep their parents'
 // records in a shared-memory ring of kParentStages tiles instead of
 // registers: each thread copies its own items' records with cp.async
 // kParentStages - 1 tiles ahead and reads them back when it forms the tile,
-// so the loads in flight hold no registers and need no block barrier.  Slot
+// so the loads in flight hold no registers and need no block barrier.  Used
+// where the parents come from HBM (launch groups, weighted populations,
+// populations with more than kStageParentBytes of parents); an L2-resident
+// population is faster with the register prefetch.  Slot
 // x = it * BLOCK + tid of stage s, parent p: 16-byte planes q (8-byte slots
 // for W = 1), plane-major so a warp's accesses are conflict-free.
 template <int W, int ITEMS, int BLOCK>
