@@ -174,6 +174,14 @@ def test_consumer_resource_full_size_first_generations():
     assert_identical(*run_both(w, 2))
 
 
+def test_large_population_staged_parents():
+    """N = 1,600,000, L = 128 (51 MB of parent records, above the size where a
+    population stages its parents through shared memory): three generations
+    bit-exact against the oracle, through a direct launch and a chunk."""
+    w = S.consumer_resource(n=1_600_000)
+    assert_identical(*run_both(w, 3, chunks=[1, 2]))
+
+
 def test_consumer_resource_full_size_graph_path_invariants():
     """Full size through the cached-graph launches: properties that hold at
     any size, checked with numpy against the GPU's own outputs."""
