@@ -374,9 +374,10 @@ __device__ __forceinline__ void offspring_run(const SegCtx &c, uint32_t lt0, uin
     __syncthreads();  // the run's tables (and cdf) are visible to every thread
 
     uint32_t bucket_alive = 0, bucket_cur = (lt0 * TILE) / kBucket;
-    // one tile: prefetch the next tile's records, form this one, draw the one
-    // after next (parent ranks need no memory access, so only the records'
-    // latency has to be covered)
+    // one tile: prefetch the next tile's records, draw the one after next
+    // (before forming this one, so the compiler can interleave its Philox
+    // rounds with the tile's; parent ranks need no memory access, so only the
+    // records' latency has to be covered), form this one
     auto step = [&](uint32_t lt, const TileRecs<W, ITEMS> &cur, TileRecs<W, ITEMS> &nxt) {
         const uint32_t base = lt * TILE;
         if (lt + 1 < lt1) load_parents<W, ITEMS, BLOCK>(c, base + TILE, tid, d1, nxt);
@@ -387,12 +388,14 @@ __device__ __forceinline__ void offspring_run(const SegCtx &c, uint32_t lt0, uin
             bucket_alive = 0;
             bucket_cur = bkt;
         }
+        TileDraws<ITEMS> d2;
+        draw_parents<ITEMS, BLOCK, WEIGHTED>(c, base + 2 * TILE, tid, d2);  // past the run: unused
         const uint32_t cnt =
             offspring_tile<W, ITEMS, BLOCK, LINKED, WEIGHTED>(c, base, tid, lane, warp, cur, d0, s_cdf, ts, lk);
         bucket_alive += cnt;
         warp_alive += cnt;
         d0 = d1;
-        if (lt + 2 < lt1) draw_parents<ITEMS, BLOCK, WEIGHTED>(c, base + 2 * TILE, tid, d1);
+        d1 = d2;
     };
     for (uint32_t lt = lt0; lt < lt1; lt += 2) {  // record sets alternate, so no register copies
         step(lt, ra, rb);
@@ -742,11 +745,13 @@ __device__ __forceinline__ void pair_run(const SegCtx &c, uint32_t lt0, uint32_t
             bucket_alive = 0;
             bucket_cur = bkt;
         }
+        PairDraws<ITEMS> d2;  // drawn before the tile is formed (see offspring_run)
+        pair_draw<ITEMS, BLOCK>(c, base + 2 * TILE, tid, h, d2);  // past the run: unused
         const uint32_t cnt = pair_tile<W, ITEMS, BLOCK>(c, base, tid, lane, warp, cur, d0, s_cdf, ts);
         bucket_alive += cnt;
         warp_alive += cnt;
         d0 = d1;
-        if (lt + 2 < lt1) pair_draw<ITEMS, BLOCK>(c, base + 2 * TILE, tid, h, d1);
+        d1 = d2;
     };
     for (uint32_t lt = lt0; lt < lt1; lt += 2) {
         step(lt, ra, rb);
