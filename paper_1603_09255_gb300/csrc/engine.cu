@@ -492,11 +492,11 @@ int enqueue_generations(const GenLaunch &gl, uint32_t n_gen, GraphChain &chain, 
 }
 
 // ------------------------------------------------- launch groups
-// Bytes of a launch group's table: segments, runs (at most two per member plus
-// one per kMinRunOffspring offspring, whatever the tile size), the blocks' run
-// offsets and the bucket map.
+// Bytes of a launch group's table: segments, runs (at most one per member plus
+// one per piece: one round of blocks, or pieces of kPieceOffspring offspring
+// or more), the blocks' run offsets and the bucket map.
 size_t group_table_bytes(uint32_t members, uint64_t offspring, uint32_t buckets) {
-    const uint64_t runs = 2ull * members + offspring / kMinRunOffspring + 1ull;
+    const uint64_t runs = 2ull * members + offspring / kPieceOffspring + kMaxGridBlocks + 1ull;
     return align_up((size_t)members * sizeof(Segment), 256) + align_up((size_t)runs * sizeof(Run), 256) +
            align_up((size_t)(kMaxGridBlocks + 1) * 4, 256) + align_up((size_t)buckets * 4, 256);
 }
@@ -506,41 +506,55 @@ uint32_t tiles_for(uint32_t n, const Shape &shape) {
     return (n + t - 1) / t;
 }
 
-// Runs of a launch group (see GenArgs): member m's tiles[m] tiles dealt out to
-// G blocks.  Members in order, each to the k = clamp(tiles / min_run, 1, G)
-// blocks with the least work so far, as k contiguous runs of near-equal
-// length: all blocks sweep the members together, so the populations being
-// formed at any moment are few and their parent records stay in L2 (the
-// flattened replicate loop of Fig. S5 B, scheduled for locality).  A run's
-// set-up (tables, pipeline start) counts as one tile of work.
-void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_run, std::vector<Run> &runs,
+// Runs of a launch group (see GenArgs): the members' tiles, in member order,
+// with one unit of set-up (tables, pipeline start) before each member, cut
+// into P pieces of equal work dealt round-robin to the G blocks (block b
+// forms pieces b, b + G, ...: rounds of G pieces of at least min_piece tiles,
+// each round a contiguous window of the member list, so the populations being
+// formed at any moment are few and their parent records stay in L2 -- the
+// flattened replicate loop of Fig. S5 B, scheduled for locality).  A piece is
+// one run per member it touches, so every block's work is within a set-up or
+// two of the others'.
+void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_piece, std::vector<Run> &runs,
                    std::vector<uint32_t> &block_runs) {
-    std::vector<std::vector<Run>> per(G);
-    using Load = std::pair<uint64_t, uint32_t>;  // (work so far, block)
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (uint32_t b = 0; b < G; ++b) heap.push({0ull, b});
-    std::vector<Load> picked;
-    for (uint32_t m = 0; m < (uint32_t)tiles.size(); ++m) {
-        const uint32_t T = tiles[m];
-        if (T == 0) continue;
-        const uint32_t k = std::max(1u, std::min(G, T / std::max(1u, min_run)));
-        picked.clear();
-        for (uint32_t i = 0; i < k; ++i) {
-            picked.push_back(heap.top());
-            heap.pop();
-        }
-        std::sort(picked.begin(), picked.end(), [](const Load &x, const Load &y) { return x.second < y.second; });
-        for (uint32_t i = 0; i < k; ++i) {
-            const uint32_t t0 = (uint32_t)((uint64_t)T * i / k), t1 = (uint32_t)((uint64_t)T * (i + 1) / k);
-            per[picked[i].second].push_back(Run{m, t0, t1 - t0, i, k, {0u, 0u, 0u}});
-            heap.push({picked[i].first + (t1 - t0) + 1u, picked[i].second});
+    const uint32_t M = (uint32_t)tiles.size();
+    std::vector<uint64_t> ustart(M + 1, 0ull), tstart(M + 1, 0ull);  // prefix units, prefix tiles
+    for (uint32_t m = 0; m < M; ++m) {
+        ustart[m + 1] = ustart[m] + (tiles[m] ? tiles[m] + 1ull : 0ull);
+        tstart[m + 1] = tstart[m] + tiles[m];
+    }
+    const uint64_t U = ustart[M], T = tstart[M];
+    // rounds of G pieces of min_piece tiles or more (one round at least)
+    const uint64_t P = (uint64_t)G * std::max<uint64_t>(1ull, T / ((uint64_t)G * std::max(1u, min_piece)));
+    std::vector<uint64_t> cut(P + 1);  // cut p (0..P) as a flattened tile coordinate
+    uint32_t m = 0;
+    for (uint64_t p = 0; p < P; ++p) {
+        const uint64_t x = U * p / P;
+        while (m < M && x >= ustart[m + 1]) ++m;
+        const uint64_t off = m < M && x > ustart[m] ? x - ustart[m] - 1ull : 0ull;  // tiles of m before the cut
+        cut[p] = m < M ? tstart[m] + std::min<uint64_t>(off, tiles[m]) : T;
+    }
+    cut[P] = T;
+    std::vector<std::vector<Run>> piece_runs(P);
+    std::vector<uint32_t> nruns(M, 0u);
+    m = 0;
+    for (uint64_t p = 0; p < P; ++p) {
+        for (uint64_t g = cut[p]; g < cut[p + 1];) {
+            while (g >= tstart[m + 1]) ++m;
+            const uint64_t e = std::min(cut[p + 1], tstart[m + 1]);
+            piece_runs[p].push_back(Run{m, (uint32_t)(g - tstart[m]), (uint32_t)(e - g), nruns[m]++, 0u, {0u, 0u, 0u}});
+            g = e;
         }
     }
     runs.clear();
     block_runs.assign(G + 1, 0u);
     for (uint32_t b = 0; b < G; ++b) {
         block_runs[b] = (uint32_t)runs.size();
-        runs.insert(runs.end(), per[b].begin(), per[b].end());
+        for (uint64_t p = b; p < P; p += G)
+            for (Run r : piece_runs[p]) {
+                r.shares = nruns[r.seg];  // the member's parents prefetched in shares, one per run
+                runs.push_back(r);
+            }
     }
     block_runs[G] = (uint32_t)runs.size();
 }
@@ -574,10 +588,10 @@ int build_group_launch(const std::vector<const PopView *> &members, uint32_t wor
         offspring += v.n;
     }
     const uint32_t G = std::max(1u, std::min(k.resident, kMaxGridBlocks));
-    const uint32_t min_run = std::max(1u, kMinRunOffspring / tile_size(shape));
+    const uint32_t min_piece = std::max(1u, kPieceOffspring / tile_size(shape));
     std::vector<Run> runs;
     std::vector<uint32_t> block_runs;
-    schedule_runs(tiles, G, min_run, runs, block_runs);
+    schedule_runs(tiles, G, min_piece, runs, block_runs);
     if (group_table_bytes((uint32_t)segs.size(), offspring, buckets) > table_capacity)
         return fail(SPG_ERR_INVALID, "launch table does not fit its buffer");
     const size_t off_runs = align_up(segs.size() * sizeof(Segment), 256);

@@ -14,7 +14,7 @@
 namespace spg {
 
 constexpr uint32_t kGraphChunk = 32;          // generations per cached graph
-constexpr uint32_t kMinRunOffspring = 8192;   // offspring of a run of a launch group (members that have them)
+constexpr uint32_t kPieceOffspring = 8192;     // least offspring of a piece of a launch group's work (one round excepted)
 constexpr uint32_t kMaxGridBlocks = 8192;     // offspring blocks of a launch group, at most
 constexpr uint32_t kCheckpointMagic = 0x43475053u;  // "SPGC"
 
@@ -99,7 +99,7 @@ int launch_generation(const GenLaunch &gl, cudaStream_t stream);
 int add_generation_nodes(cudaGraph_t graph, const GenLaunch &gl, void **params, uint32_t len);
 size_t group_table_bytes(uint32_t members, uint64_t offspring, uint32_t buckets);
 uint32_t tiles_for(uint32_t n, const Shape &shape);
-void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_run, std::vector<Run> &runs,
+void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_piece, std::vector<Run> &runs,
                    std::vector<uint32_t> &block_runs);
 // Segment table, runs and bucket map of one launch group, uploaded into
 // `table` (device memory; synchronous), and the group's launch description.
