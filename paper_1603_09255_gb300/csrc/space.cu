@@ -697,6 +697,8 @@ struct spg_space {
     uint32_t births_grid = 0;  // resident blocks of k_sp_births
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;                     // the newborns' kernel, beside the survivors' move
+    cudaEvent_t fork = nullptr, join = nullptr;     // side stream after the step's scans / stream after the newborns
     bool own_stream = false;
     Allocator alloc;
     char *arena = nullptr;
@@ -740,10 +742,21 @@ int launch_step(spg_space *c) {
     k_sp_classify<<<a.nd, kSpClassBlock, 0, s>>>(a);
     k_sp_totals<<<g, 256, 0, s>>>(a);
     k_sp_scan<<<1, 1024, 0, s>>>(a, 1);
-    k_sp_births<W><<<c->births_grid, kSpBlock, 0, s>>>(a);
+    // the newborns on the side stream beside the survivors' move: both only
+    // read the current generation and write disjoint places of the next; the
+    // newborns' kernel goes first so that its resident grid is placed before
+    // the move's blocks take the rest of each SM
+    cudaError_t e = cudaEventRecord(c->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "space step fork");
+    k_sp_births<W><<<c->births_grid, kSpBlock, 0, c->side>>>(a);
+    e = cudaEventRecord(c->join, c->side);
+    if (e != cudaSuccess) return cuda_fail(e, "space step join");
     k_sp_scatter<W><<<a.nd, kSpBlock, 0, s>>>(a);
+    e = cudaStreamWaitEvent(s, c->join, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "space step join");
     k_sp_finish<<<1, 32, 0, s>>>(a);
-    const cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "space step launch");
 }
 
@@ -841,6 +854,13 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
         e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
         c->own_stream = true;
+    }
+    e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        spg_space_destroy(c.release());
+        return cuda_fail(e, "side stream");
     }
     c->arena = static_cast<char *>(c->alloc.alloc(off, c->stream));
     if (!c->arena) {
@@ -1027,7 +1047,11 @@ void spg_space_destroy(spg_space *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->arena) c->alloc.release(c->arena, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->side) cudaStreamSynchronize(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     delete c;
 }
 
