@@ -153,12 +153,13 @@ typedef struct {
     double mu;                      /* per-locus mutation probability, 0 <= mu < 1      */
     uint32_t stats_capacity;        /* most recent generations kept readable (0: 1024)  */
     const double *map_morgans;      /* [L] linkage map (see above), copied; NULL: free  */
-                                    /* recombination.  Single populations only: batch   */
-                                    /* and server calls reject a map (SPG_ERR_INVALID). */
+                                    /* recombination.  Populations, batch members and   */
+                                    /* server jobs (those run the variant shape: 256    */
+                                    /* threads, one offspring per thread, one lane).    */
     const uint32_t *mother_weights; /* [4096] parent weights by bin (see above), copied;*/
-    const uint32_t *father_weights; /* NULL: uniform for that role.  Single populations */
-                                    /* only, like map_morgans; a table whose weights   */
-                                    /* are all 0 is SPG_ERR_INVALID.                    */
+    const uint32_t *father_weights; /* NULL: uniform for that role.  Like map_morgans;  */
+                                    /* a table whose weights are all 0 is               */
+                                    /* SPG_ERR_INVALID.                                 */
     const int16_t *dominance;       /* [L] dominance deviations (Q8) of heterozygous    */
                                     /* loci, copied; NULL: additive.  Every population, */
                                     /* batch member and job; bin_bias / bin_shift must  */
@@ -167,7 +168,8 @@ typedef struct {
     double mut_sd;                  /* continuous: sd of a mutation step (trait units)  */
     double env_sd;                  /* continuous: sd of the environmental step         */
     const int16_t *init_values;     /* continuous: [N * 2L] generation-0 values or NULL */
-                                    /* Continuous populations: single populations only, */
+                                    /* Continuous populations: single populations only  */
+                                    /* (batch and server calls: SPG_ERR_INVALID),       */
                                     /* no linkage map, weights or dominance, 0 <= sd < 64.*/
 } spg_pop_desc;
 
@@ -284,9 +286,12 @@ int spg_get_tiling(spg_pop *pop, uint32_t *items_per_thread);
 /* ---- Batched replicates ---------------------------------------------------
  * Many independent populations advanced by shared launches: the flattened
  * loop over replicates of the paper's Fig. S5 B.  Members are grouped by
- * locus count; each generation is one offspring launch and one compaction
- * launch per group, groups run as independent branches of one cached CUDA
- * graph.  Every member keeps its own parameters, state, buffers and
+ * locus count and variant (plain; linkage map; parent weights; both); each
+ * generation is one offspring launch and one compaction launch per group,
+ * groups run as independent branches of one cached CUDA graph.  Members with
+ * a linkage map or parent weights run the variant shape (256 threads, one
+ * offspring per thread, one lane); launch shapes and the autotuner apply to
+ * the plain members of each locus count.  Every member keeps its own parameters, state, buffers and
  * statistics ring, and its results are identical to the same population
  * created with spg_create_population and stepped alone.  Member i is
  * descs[i]; the descriptions are copied.  Errors as for a population;
@@ -304,7 +309,9 @@ int spg_batch_set_launch_shape(spg_batch *batch, uint32_t n_loci, const spg_laun
 int spg_batch_get_launch_shape(spg_batch *batch, uint32_t n_loci, spg_launch_shape *out);
 int spg_batch_set_tiling(spg_batch *batch, uint32_t n_loci, uint32_t items_per_thread);
 int spg_batch_get_tiling(spg_batch *batch, uint32_t n_loci, uint32_t *items_per_thread);
-/* Launch-shape autotuner: for each locus-count group, runs one untimed
+/* Launch-shape autotuner: for each locus-count group of plain members (no
+ * linkage map or parent weights: those run their one shape for as many
+ * generations), runs one untimed
  * generation and then times gens_per_trial real generations with each of
  * SPG_AUTOTUNE_CANDIDATES launch shapes -- threads per block (128, 256, 512)
  * x offspring per thread (1, 2) for L <= 64, x lanes per offspring (1, 2) for

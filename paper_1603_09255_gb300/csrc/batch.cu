@@ -1,8 +1,10 @@
 // Batched replicates (spg_batch): many independent populations advanced by
 // shared launches -- the flattened replicate loop of the paper's Fig. S5 B.
 //
-// Members are grouped by locus count (the offspring kernel is specialised
-// on W).  A group's members are the segments of one launch: every
+// Members are grouped by locus count and variant (the offspring kernel is
+// specialised on W, linkage map and parent weights; members with a linkage
+// map or parent weights run at the variant shape, the others' shape is tuned
+// per locus count).  A group's members are the segments of one launch: every
 // generation is one offspring launch and one compaction launch per group,
 // the groups' chains are independent branches of one CUDA graph (so groups
 // overlap on the GPU), and the graph of kGraphChunk generations is replayed.
@@ -28,11 +30,14 @@ namespace {
 struct Member {
     PopView v;
     std::unique_ptr<PopParams> prm;
+    std::unique_ptr<LinkParams> link;       // linkage-map tables (host copy, until uploaded)
+    std::unique_ptr<WeightParams> weights;  // parent acceptance thresholds (host copy, until uploaded)
     uint32_t group = 0;
 };
 
 struct Group {
     uint32_t words = 0;
+    bool linked = false, weighted = false;  // the members' variant
     Shape shape;
     std::vector<uint32_t> members;
     size_t table_off = 0, table_bytes = 0;  // launch table in the batch arena (sized for every shape)
@@ -76,11 +81,21 @@ struct MultiChain {
 
 uint32_t group_of_words(uint32_t words) { return words == 1 ? 0u : words == 2 ? 1u : words == 4 ? 2u : 3u; }
 
+// Groups 0-3: plain members by locus count; 4 + 4v + (locus count): variant v
+// (0: linkage map, 1: parent weights, 2: both).
+constexpr uint32_t kBatchGroups = 16;
+uint32_t group_index(uint32_t words, bool linked, bool weighted) {
+    return group_of_words(words) + 4u * ((linked ? 1u : 0u) + (weighted ? 2u : 0u));
+}
+Shape group_shape(const Group &g) {
+    return (g.linked || g.weighted) ? Shape{(uint32_t)kBlock, 1u, 1u} : default_shape(g.words);
+}
+
 }  // namespace
 
 struct spg_batch {
     std::vector<Member> members;
-    std::vector<Group> groups;  // indexed by group_of_words
+    std::vector<Group> groups;  // indexed by group_index
     Allocator alloc;
     char *arena = nullptr;
     size_t arena_bytes = 0;
@@ -102,7 +117,8 @@ int configure_group(spg_batch *b, Group &g, const Shape &shape) {
         eco |= b->members[mi].prm->has_eco != 0u;
         dom |= b->members[mi].prm->has_dom != 0u;
     }
-    const int rc = build_group_launch(views, g.words, shape, eco, dom, b->arena + g.table_off, g.table_bytes, g.gl);
+    const int rc = build_group_launch(views, g.words, shape, eco, dom, b->arena + g.table_off, g.table_bytes, g.gl,
+                                      g.linked, g.weighted);
     if (rc != SPG_OK) return rc;
     g.shape = shape;
     b->chains.clear();
@@ -141,15 +157,18 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
     for (uint32_t i = 0; i < count; ++i) {
         const int rc = validate_desc(descs + i);
         if (rc != SPG_OK) return fail(rc, "member %u: %s", i, spg_last_error());
-        if (descs[i].map_morgans || descs[i].mother_weights || descs[i].father_weights || descs[i].allele_model)
-            return fail(SPG_ERR_INVALID,
-                        "member %u: linkage maps and parent weights are supported for single populations", i);
+        if (descs[i].allele_model)
+            return fail(SPG_ERR_INVALID, "member %u: continuous alleles are supported for single populations", i);
     }
     std::unique_ptr<spg_batch> b(new (std::nothrow) spg_batch());
     if (!b) return fail(SPG_ERR_OOM, "host allocation failed");
     b->members.resize(count);
-    b->groups.resize(4);
-    for (uint32_t gi = 0; gi < 4; ++gi) b->groups[gi].words = 1u << gi;
+    b->groups.resize(kBatchGroups);
+    for (uint32_t gi = 0; gi < kBatchGroups; ++gi) {
+        b->groups[gi].words = 1u << (gi % 4u);
+        b->groups[gi].linked = ((gi / 4u) & 1u) != 0u;
+        b->groups[gi].weighted = ((gi / 4u) & 2u) != 0u;
+    }
     size_t off = 0;
     for (uint32_t i = 0; i < count; ++i) {
         Member &m = b->members[i];
@@ -158,13 +177,23 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
         if (!m.prm) return fail(SPG_ERR_OOM, "host allocation failed");
         const uint32_t words = d.n_loci / 32;
         int rc = build_params(&d, *m.prm);
+        const bool linked = m.prm->linked != 0u, weighted = m.prm->weighted != 0u;
+        if (rc == SPG_OK && linked) {
+            m.link.reset(new (std::nothrow) LinkParams());
+            rc = m.link ? build_link(d.map_morgans, d.n_loci, *m.link) : fail(SPG_ERR_OOM, "host allocation failed");
+        }
+        if (rc == SPG_OK && weighted) {
+            m.weights.reset(new (std::nothrow) WeightParams());
+            rc = m.weights ? build_weights(d.mother_weights, d.father_weights, *m.weights)
+                           : fail(SPG_ERR_OOM, "host allocation failed");
+        }
         if (rc != SPG_OK) return fail(rc, "member %u: %s", i, spg_last_error());
         m.v.n = d.n;
         m.v.words = words;
         m.v.cap = m.prm->stats_cap;
         m.v.nbuckets = bucket_count(d.n);
-        m.v.L = layout_for(d.n, words, m.v.nbuckets, m.v.cap);
-        m.group = group_of_words(words);
+        m.v.L = layout_for(d.n, words, m.v.nbuckets, m.v.cap, weighted);
+        m.group = group_index(words, linked, weighted);
         b->groups[m.group].members.push_back(i);
         m.v.base = reinterpret_cast<char *>(off);  // offset until the arena exists
         off = align_up(off + m.v.L.total, 256);
@@ -199,6 +228,21 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
         Member &m = b->members[i];
         m.v.base = b->arena + reinterpret_cast<size_t>(m.v.base);
         m.v.stream = b->stream;
+        cudaError_t e = cudaSuccess;
+        if (m.link) {  // the variant tables in the member's memory (read by its parameters)
+            m.prm->link = reinterpret_cast<const LinkParams *>(m.v.base + m.v.L.link);
+            e = cudaMemcpyAsync(m.v.base + m.v.L.link, m.link.get(), sizeof(LinkParams), cudaMemcpyHostToDevice,
+                                b->stream);
+        }
+        if (e == cudaSuccess && m.weights) {
+            m.prm->weights = reinterpret_cast<const WeightParams *>(m.v.base + m.v.L.weights);
+            e = cudaMemcpyAsync(m.v.base + m.v.L.weights, m.weights.get(), sizeof(WeightParams),
+                                cudaMemcpyHostToDevice, b->stream);
+        }
+        if (e != cudaSuccess) {
+            spg_batch_destroy(b.release());
+            return cuda_fail(e, "upload a member's variant tables");
+        }
         const int rc = view_init(m.v, *m.prm, descs[i].init_genotypes, descs[i].p0_q32);
         if (rc != SPG_OK) {
             spg_batch *raw = b.release();
@@ -208,7 +252,7 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
     }
     int rc = view_sync(b->members[0].v);  // caller arrays and host parameters have been read
     for (Group &g : b->groups)
-        if (rc == SPG_OK) rc = configure_group(b.get(), g, default_shape(g.words));
+        if (rc == SPG_OK) rc = configure_group(b.get(), g, group_shape(g));
     if (rc != SPG_OK) {
         spg_batch_destroy(b.release());
         return rc;
@@ -286,7 +330,7 @@ int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, spg_autotune_repor
     // every group runs the same number of trials (kAutotuneCandidates), each
     // one untimed generation (the new shape's first launches) then
     // gens_per_trial timed ones, so all members advance equally
-    for (uint32_t gi = 0; gi < (uint32_t)b->groups.size() && rc == SPG_OK; ++gi) {
+    for (uint32_t gi = 0; gi < 4u && rc == SPG_OK; ++gi) {  // the plain groups (variants: one shape)
         Group &g = b->groups[gi];
         if (g.members.empty()) continue;
         float best_ms = 0.f, worst_ms = 0.f;
@@ -316,6 +360,14 @@ int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, spg_autotune_repor
             rep.best_ms[gi] = best_ms / (float)gens_per_trial;
             rep.worst_ms[gi] = worst_ms / (float)gens_per_trial;
         }
+    }
+    // members with a linkage map or parent weights keep the variant shape and
+    // advance by as many generations as the tuned ones
+    for (uint32_t gi = 4; gi < (uint32_t)b->groups.size() && rc == SPG_OK; ++gi) {
+        const Group &g = b->groups[gi];
+        if (g.members.empty()) continue;
+        for (uint32_t i = 0; i < kAutotuneCandidates * (gens_per_trial + 1u) && rc == SPG_OK; ++i)
+            rc = launch_generation(g.gl, b->stream);
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);

@@ -560,16 +560,18 @@ void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_
 }
 
 int build_group_launch(const std::vector<const PopView *> &members, uint32_t words, const Shape &shape, bool eco,
-                       bool dom, char *table, size_t table_capacity, GenLaunch &gl) {
+                       bool dom, char *table, size_t table_capacity, GenLaunch &gl, bool linked, bool weighted) {
     if (members.empty()) {
         gl = GenLaunch{};
         return SPG_OK;
     }
-    if (!supported_shape(words, shape))
+    if (!supported_shape(words, shape) ||
+        ((linked || weighted) && (shape.block != (uint32_t)kBlock || shape.items != 1u || shape.lanes != 1u)))
         return fail(SPG_ERR_INVALID,
                     "unsupported launch shape (%u threads, %u offspring per thread, %u lanes per offspring) for %u loci",
                     shape.block, shape.items, shape.lanes, 32u * words);
-    OffspringKernel k = offspring_kernel(words, shape, false, false, eco, dom, true);  // members in HBM: staged
+    // members in HBM: staged parents (where an instance has them)
+    OffspringKernel k = offspring_kernel(words, shape, linked, weighted, eco, dom, true);
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
     std::vector<Segment> segs;

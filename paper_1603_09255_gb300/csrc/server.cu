@@ -31,12 +31,16 @@ using namespace spg;
 
 namespace {
 
-constexpr int kGroups = 4;  // W = 1, 2, 4, 8
+// Groups by locus count (W = 1, 2, 4, 8) and variant: 0-3 plain, 4 + 4v + W
+// index for v = 0 linkage map, 1 parent weights, 2 both (the variant shape).
+constexpr int kGroups = 16;
 
 struct Job {
     spg_pop_desc desc{};
     std::vector<int16_t> effects, dominance;
     std::vector<uint32_t> table, founders, attack;
+    std::unique_ptr<LinkParams> link;       // linkage-map tables (built at submission)
+    std::unique_ptr<WeightParams> weights;  // parent acceptance thresholds (built at submission)
     bool has_eco = false;
     spg_ecology eco{};
     uint32_t n_gen = 0;
@@ -54,7 +58,9 @@ struct Job {
     uint32_t final_gen = 0;
 };
 
-uint32_t group_of(uint32_t words) { return words == 1 ? 0u : words == 2 ? 1u : words == 4 ? 2u : 3u; }
+uint32_t group_of(uint32_t words, bool linked, bool weighted) {
+    return (words == 1 ? 0u : words == 2 ? 1u : words == 4 ? 2u : 3u) + 4u * ((linked ? 1u : 0u) + (weighted ? 2u : 0u));
+}
 
 }  // namespace
 
@@ -102,6 +108,8 @@ int retire(spg_server *s, Job &j) {
     s->alloc.release(j.arena, s->stream);
     j.arena = nullptr;
     j.prm.reset();
+    j.link.reset();
+    j.weights.reset();
     s->used -= j.footprint;
     j.state = SPG_JOB_FINISHED;
     j.t_finish = s->now();
@@ -120,13 +128,26 @@ int admit(spg_server *s, Job &j) {
     if (!j.prm) return fail(SPG_ERR_OOM, "host allocation failed");
     int rc = build_params(&j.desc, *j.prm);
     if (rc != SPG_OK) return rc;
+    j.prm->linked = j.link ? 1u : 0u;
+    j.prm->weighted = j.weights ? 1u : 0u;
     j.v.base = j.arena;
     j.v.n = j.desc.n;
     j.v.words = words;
     j.v.cap = j.prm->stats_cap;
     j.v.nbuckets = bucket_count(j.desc.n);
-    j.v.L = layout_for(j.desc.n, words, j.v.nbuckets, j.v.cap);
+    j.v.L = layout_for(j.desc.n, words, j.v.nbuckets, j.v.cap, j.weights != nullptr);
     j.v.stream = s->stream;
+    cudaError_t e = cudaSuccess;
+    if (j.link) {  // the variant tables in the job's memory (read by its parameters)
+        j.prm->link = reinterpret_cast<const LinkParams *>(j.arena + j.v.L.link);
+        e = cudaMemcpyAsync(j.arena + j.v.L.link, j.link.get(), sizeof(LinkParams), cudaMemcpyHostToDevice, s->stream);
+    }
+    if (e == cudaSuccess && j.weights) {
+        j.prm->weights = reinterpret_cast<const WeightParams *>(j.arena + j.v.L.weights);
+        e = cudaMemcpyAsync(j.arena + j.v.L.weights, j.weights.get(), sizeof(WeightParams), cudaMemcpyHostToDevice,
+                            s->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "upload a job's variant tables");
     rc = view_init(j.v, *j.prm, j.founders.empty() ? nullptr : j.founders.data(), j.desc.p0_q32);
     if (rc == SPG_OK && j.has_eco) rc = view_set_ecology(j.v, *j.prm, &j.eco);
     DevState st;
@@ -148,9 +169,11 @@ int rebuild(spg_server *s) {
         uint64_t offspring = 0;
         uint32_t buckets = 0;
         bool eco = false, dom = false;
+        const uint32_t words = 1u << (gi % 4);
+        const bool linked = ((gi / 4) & 1) != 0, weighted = ((gi / 4) & 2) != 0;
         for (uint64_t id : s->resident) {
             const Job &j = *s->jobs[id];
-            if (group_of(j.v.words) != (uint32_t)gi) continue;
+            if (group_of(j.v.words, j.link != nullptr, j.weights != nullptr) != (uint32_t)gi) continue;
             views.push_back(&j.v);
             offspring += j.v.n;
             buckets += j.v.nbuckets;
@@ -167,8 +190,9 @@ int rebuild(spg_server *s) {
             if (!s->table[gi]) return fail(SPG_ERR_OOM, "launch table allocation failed");
             s->table_cap[gi] = cap;
         }
-        rc = build_group_launch(views, 1u << gi, default_shape(1u << gi), eco, dom, s->table[gi], s->table_cap[gi],
-                                s->gl[gi]);
+        const Shape shape = (linked || weighted) ? Shape{(uint32_t)kBlock, 1u, 1u} : default_shape(words);
+        rc = build_group_launch(views, words, shape, eco, dom, s->table[gi], s->table_cap[gi], s->gl[gi], linked,
+                                weighted);
         if (rc != SPG_OK) return rc;
     }
     s->dirty = false;
@@ -243,11 +267,23 @@ int spg_server_submit(spg_server *s, const spg_pop_desc *desc, const spg_ecology
     if (rc != SPG_OK) return rc;
     if (eco && (rc = check_ecology(eco)) != SPG_OK) return rc;
     if (n_gen == 0) return fail(SPG_ERR_INVALID, "a job needs at least one generation");
-    if (desc->map_morgans || desc->mother_weights || desc->father_weights || desc->allele_model)
-        return fail(SPG_ERR_INVALID, "linkage maps and parent weights are supported for single populations");
+    if (desc->allele_model)
+        return fail(SPG_ERR_INVALID, "continuous alleles are supported for single populations");
     std::unique_ptr<Job> j(new (std::nothrow) Job());
     if (!j) return fail(SPG_ERR_OOM, "host allocation failed");
+    if (desc->map_morgans) {  // built (and checked) now: the caller's arrays need not outlive the call
+        j->link.reset(new (std::nothrow) LinkParams());
+        if (!j->link) return fail(SPG_ERR_OOM, "host allocation failed");
+        if ((rc = build_link(desc->map_morgans, desc->n_loci, *j->link)) != SPG_OK) return rc;
+    }
+    if (desc->mother_weights || desc->father_weights) {
+        j->weights.reset(new (std::nothrow) WeightParams());
+        if (!j->weights) return fail(SPG_ERR_OOM, "host allocation failed");
+        if ((rc = build_weights(desc->mother_weights, desc->father_weights, *j->weights)) != SPG_OK) return rc;
+    }
     j->desc = *desc;
+    j->desc.map_morgans = nullptr;
+    j->desc.mother_weights = j->desc.father_weights = nullptr;
     j->effects.assign(desc->effects, desc->effects + desc->n_loci);
     j->table.assign(desc->surv_table, desc->surv_table + SPG_N_BINS);
     if (desc->init_genotypes)
@@ -269,7 +305,7 @@ int spg_server_submit(spg_server *s, const spg_pop_desc *desc, const spg_ecology
     j->n_gen = n_gen;
     j->t_arrival = t_arrival;
     const uint32_t words = desc->n_loci / 32;
-    j->footprint = align_up(layout_for(desc->n, words, bucket_count(desc->n), n_gen).total, 256);
+    j->footprint = align_up(layout_for(desc->n, words, bucket_count(desc->n), n_gen, j->weights != nullptr).total, 256);
     if (j->footprint > s->cfg.memory_budget)
         return fail(SPG_ERR_BUDGET, "job needs %zu bytes, the budget is %zu", j->footprint, s->cfg.memory_budget);
     *job = s->jobs.size();

@@ -136,3 +136,66 @@ def test_batch_full_size_sampled_members_equal_oracle():
         so = orc.step(3)
         assert_member_equals(b, i, so, orc.genotypes(), orc.survivors(), orc.state())
     b.close()
+
+
+def variant_workloads():
+    """Every (locus count, variant) pair once: plain, linkage map, parent
+    weights, both; ragged sizes, some with the logistic resource."""
+    out = []
+    sizes = [1, 33, 1000, 4097, 9001, 20000, 2049]
+    for r in range(16):
+        n_loci, kind, n = [32, 64, 128, 256][r % 4], r // 4, sizes[r % len(sizes)]
+        if r % 3 == 0:
+            w = S.consumer_resource(n=n, n_loci=n_loci, mu=2e-3, s=1.0, K=max(4.0 * n, 100.0), seed=13, replicate=r,
+                                    effects_seed=300 + r)
+        else:
+            w = S.single_species(n=n, n_loci=n_loci, mu=2e-3, s=1.5, seed=13, replicate=r, effects_seed=300 + r)
+        if kind & 1:
+            w = S.with_linkage(w, [1, 2, 4][r % 3], 0.5 + 0.5 * (r % 3))
+        if kind & 2:
+            w = S.with_weights(w, slope=1.0 + 0.25 * (r % 3))
+        out.append(w)
+    return out
+
+
+def test_batch_variant_members_equal_standalone_populations():
+    """Members with a linkage map, parent weights or both share launches with
+    plain members and equal the same populations stepped alone."""
+    ws = variant_workloads()
+    n_gen = 40
+    b = sp().Batch(ws, stats_capacity=64)
+    b.step(n_gen)
+    for i, w in enumerate(ws):
+        p = sp().Population.from_workload(w, stats_capacity=64)
+        p.step(n_gen)
+        st = p.state()
+        ref = p.read_stats(1, st["gen"]) if st["gen"] else np.zeros(0, sp().STATS_DTYPE)
+        assert_member_equals(b, i, ref, p.genotypes(), p.survivors(), st)
+        p.close()
+    b.close()
+
+
+@pytest.mark.parametrize("member", [5, 6, 10, 11, 12, 13, 15])
+def test_batch_variant_members_equal_oracle(member):
+    ws = variant_workloads()
+    b = sp().Batch(ws, stats_capacity=16)
+    b.step(5)
+    orc = oracle.OraclePopulation.from_workload(ws[member])
+    so = orc.step(5)
+    assert_member_equals(b, member, so, orc.genotypes(), orc.survivors(), orc.state())
+    b.close()
+
+
+def test_autotune_advances_variant_members_alike():
+    ws = variant_workloads()
+    b = sp().Batch(ws, stats_capacity=64)
+    ran = b.autotune(1)
+    b.step(3)
+    for i, w in enumerate(ws):
+        p = sp().Population.from_workload(w, stats_capacity=64)
+        p.step(ran + 3)
+        st = p.state()
+        ref = p.read_stats(1, st["gen"]) if st["gen"] else np.zeros(0, sp().STATS_DTYPE)
+        assert_member_equals(b, i, ref, p.genotypes(), p.survivors(), st)
+        p.close()
+    b.close()

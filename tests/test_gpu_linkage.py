@@ -108,5 +108,11 @@ def test_linkage_map_validation_through_the_abi():
     p = sp.Population.from_workload(dataclasses.replace(w, map_morgans=S.linkage_map(64, 2, 1.0)))
     with pytest.raises(sp.SpeggError):
         p.set_tiling(2)
+    # batches and served jobs take a map and check it like a population
     with pytest.raises(sp.SpeggError):
-        sp.Batch([dataclasses.replace(w, map_morgans=S.linkage_map(64, 2, 1.0))])
+        sp.Batch([w, dataclasses.replace(w, map_morgans=np.full(64, np.nan))])
+    srv = sp.Server()
+    with pytest.raises(sp.SpeggError):
+        srv.submit(dataclasses.replace(w, map_morgans=np.full(64, 1.0)), 4)
+    srv.close()
+    sp.Batch([dataclasses.replace(w, map_morgans=S.linkage_map(64, 2, 1.0))]).close()

@@ -109,3 +109,24 @@ def test_measured_trace_jobs_equal_jobs_run_alone():
         got = srv.job_stats(int(jobs[i]), 1, info["gen"]) if info["gen"] else ref
         assert got.tobytes() == ref.tobytes(), f"job {i} differs from the same population run alone"
     srv.close()
+
+
+def test_served_variant_jobs_equal_jobs_run_alone():
+    """Jobs with a linkage map, parent weights or both are served beside plain
+    jobs and equal the same populations run alone."""
+    ws, gens, arrivals = small_trace(count=12, seed=9)
+    for i, w in enumerate(ws):
+        if i % 4 in (1, 3):
+            w = S.with_linkage(w, 2, 1.0)
+        if i % 4 in (2, 3):
+            w = S.with_weights(w, slope=1.25)
+        ws[i] = w
+    srv = sp().Server(memory_budget=64 << 20, max_resident=5, gens_per_tick=8)
+    jobs = srv.run_trace(ws, gens, arrivals)
+    for i, (w, g) in enumerate(zip(ws, gens)):
+        info = srv.job_info(int(jobs[i]))
+        ref, st = alone(w, g)
+        assert info["state"] == 2 and info["gen"] == st["gen"] and info["status"] == st["status"]
+        got = srv.job_stats(int(jobs[i]), 1, info["gen"]) if info["gen"] else ref
+        assert got.tobytes() == ref.tobytes(), f"job {i} differs from the same population run alone"
+    srv.close()

@@ -116,5 +116,11 @@ def test_weight_validation_through_the_abi():
     p = sp.Population.from_workload(ok)
     with pytest.raises(sp.SpeggError):
         p.set_tiling(4)
+    zero = dataclasses.replace(w, mother_weights=np.zeros(4096, np.uint32))
     with pytest.raises(sp.SpeggError):
-        sp.Batch([ok])
+        sp.Batch([ok, zero])
+    srv = sp.Server()
+    with pytest.raises(sp.SpeggError):
+        srv.submit(zero, 4)
+    srv.close()
+    sp.Batch([ok]).close()
