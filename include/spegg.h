@@ -168,9 +168,9 @@ typedef struct {
     double mut_sd;                  /* continuous: sd of a mutation step (trait units)  */
     double env_sd;                  /* continuous: sd of the environmental step         */
     const int16_t *init_values;     /* continuous: [N * 2L] generation-0 values or NULL */
-                                    /* Continuous populations: single populations only  */
-                                    /* (batch and server calls: SPG_ERR_INVALID),       */
-                                    /* no linkage map, weights or dominance, 0 <= sd < 64.*/
+                                    /* Continuous populations (also batch members and   */
+                                    /* served jobs, at the variant shape): no linkage   */
+                                    /* map, weights or dominance, 0 <= sd < 64.         */
 } spg_pop_desc;
 
 /* Consumer-resource ecology (Fig. 1F; S2 "Resource Consumption"): after the
@@ -286,10 +286,12 @@ int spg_get_tiling(spg_pop *pop, uint32_t *items_per_thread);
 /* ---- Batched replicates ---------------------------------------------------
  * Many independent populations advanced by shared launches: the flattened
  * loop over replicates of the paper's Fig. S5 B.  Members are grouped by
- * locus count and variant (plain; linkage map; parent weights; both); each
+ * locus count and variant (plain; linkage map; parent weights; both;
+ * continuous values); each
  * generation is one offspring launch and one compaction launch per group,
  * groups run as independent branches of one cached CUDA graph.  Members with
- * a linkage map or parent weights run the variant shape (256 threads, one
+ * a linkage map, parent weights or continuous values run the variant shape
+ * (256 threads, one
  * offspring per thread, one lane); launch shapes and the autotuner apply to
  * the plain members of each locus count.  Every member keeps its own parameters, state, buffers and
  * statistics ring, and its results are identical to the same population

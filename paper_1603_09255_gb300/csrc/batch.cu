@@ -2,9 +2,10 @@
 // shared launches -- the flattened replicate loop of the paper's Fig. S5 B.
 //
 // Members are grouped by locus count and variant (the offspring kernel is
-// specialised on W, linkage map and parent weights; members with a linkage
-// map or parent weights run at the variant shape, the others' shape is tuned
-// per locus count).  A group's members are the segments of one launch: every
+// specialised on W, linkage map and parent weights, and continuous values
+// have a kernel of their own; members with a linkage map, parent weights or
+// continuous values run at the variant shape, the others' shape is tuned per
+// locus count).  A group's members are the segments of one launch: every
 // generation is one offspring launch and one compaction launch per group,
 // the groups' chains are independent branches of one CUDA graph (so groups
 // overlap on the GPU), and the graph of kGraphChunk generations is replayed.
@@ -37,7 +38,7 @@ struct Member {
 
 struct Group {
     uint32_t words = 0;
-    bool linked = false, weighted = false;  // the members' variant
+    bool linked = false, weighted = false, continuous = false;  // the members' variant
     Shape shape;
     std::vector<uint32_t> members;
     size_t table_off = 0, table_bytes = 0;  // launch table in the batch arena (sized for every shape)
@@ -81,14 +82,16 @@ struct MultiChain {
 
 uint32_t group_of_words(uint32_t words) { return words == 1 ? 0u : words == 2 ? 1u : words == 4 ? 2u : 3u; }
 
-// Groups 0-3: plain members by locus count; 4 + 4v + (locus count): variant v
-// (0: linkage map, 1: parent weights, 2: both).
-constexpr uint32_t kBatchGroups = 16;
-uint32_t group_index(uint32_t words, bool linked, bool weighted) {
-    return group_of_words(words) + 4u * ((linked ? 1u : 0u) + (weighted ? 2u : 0u));
+// Groups 0-3: plain members by locus count (L = 32, 64, 128, 256);
+// 4 + 4v + that index: variant v (0: linkage map, 1: parent weights, 2: both);
+// 16 + that index: continuous values.
+constexpr uint32_t kBatchGroups = 20;
+uint32_t group_index(uint32_t n_loci, bool linked, bool weighted, bool continuous) {
+    const uint32_t l = group_of_words(n_loci / 32);
+    return continuous ? 16u + l : l + 4u * ((linked ? 1u : 0u) + (weighted ? 2u : 0u));
 }
 Shape group_shape(const Group &g) {
-    return (g.linked || g.weighted) ? Shape{(uint32_t)kBlock, 1u, 1u} : default_shape(g.words);
+    return (g.linked || g.weighted || g.continuous) ? Shape{(uint32_t)kBlock, 1u, 1u} : default_shape(g.words);
 }
 
 }  // namespace
@@ -118,7 +121,7 @@ int configure_group(spg_batch *b, Group &g, const Shape &shape) {
         dom |= b->members[mi].prm->has_dom != 0u;
     }
     const int rc = build_group_launch(views, g.words, shape, eco, dom, b->arena + g.table_off, g.table_bytes, g.gl,
-                                      g.linked, g.weighted);
+                                      g.linked, g.weighted, g.continuous);
     if (rc != SPG_OK) return rc;
     g.shape = shape;
     b->chains.clear();
@@ -157,17 +160,17 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
     for (uint32_t i = 0; i < count; ++i) {
         const int rc = validate_desc(descs + i);
         if (rc != SPG_OK) return fail(rc, "member %u: %s", i, spg_last_error());
-        if (descs[i].allele_model)
-            return fail(SPG_ERR_INVALID, "member %u: continuous alleles are supported for single populations", i);
     }
     std::unique_ptr<spg_batch> b(new (std::nothrow) spg_batch());
     if (!b) return fail(SPG_ERR_OOM, "host allocation failed");
     b->members.resize(count);
     b->groups.resize(kBatchGroups);
     for (uint32_t gi = 0; gi < kBatchGroups; ++gi) {
-        b->groups[gi].words = 1u << (gi % 4u);
-        b->groups[gi].linked = ((gi / 4u) & 1u) != 0u;
-        b->groups[gi].weighted = ((gi / 4u) & 2u) != 0u;
+        Group &g = b->groups[gi];
+        g.continuous = gi >= 16u;
+        g.words = g.continuous ? (32u << (gi % 4u)) / 2u : 1u << (gi % 4u);
+        g.linked = !g.continuous && ((gi / 4u) & 1u) != 0u;
+        g.weighted = !g.continuous && ((gi / 4u) & 2u) != 0u;
     }
     size_t off = 0;
     for (uint32_t i = 0; i < count; ++i) {
@@ -175,7 +178,8 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
         const spg_pop_desc &d = descs[i];
         m.prm.reset(new (std::nothrow) PopParams());
         if (!m.prm) return fail(SPG_ERR_OOM, "host allocation failed");
-        const uint32_t words = d.n_loci / 32;
+        const bool continuous = d.allele_model == 1u;
+        const uint32_t words = continuous ? d.n_loci / 2 : d.n_loci / 32;  // record words per haplotype
         int rc = build_params(&d, *m.prm);
         const bool linked = m.prm->linked != 0u, weighted = m.prm->weighted != 0u;
         if (rc == SPG_OK && linked) {
@@ -192,8 +196,8 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
         m.v.words = words;
         m.v.cap = m.prm->stats_cap;
         m.v.nbuckets = bucket_count(d.n);
-        m.v.L = layout_for(d.n, words, m.v.nbuckets, m.v.cap, weighted);
-        m.group = group_index(words, linked, weighted);
+        m.v.L = layout_for(d.n, words, m.v.nbuckets, m.v.cap, weighted, !continuous);
+        m.group = group_index(d.n_loci, linked, weighted, continuous);
         b->groups[m.group].members.push_back(i);
         m.v.base = reinterpret_cast<char *>(off);  // offset until the arena exists
         off = align_up(off + m.v.L.total, 256);
@@ -243,7 +247,10 @@ int spg_batch_create(const spg_pop_desc *descs, uint32_t count, const spg_alloca
             spg_batch_destroy(b.release());
             return cuda_fail(e, "upload a member's variant tables");
         }
-        const int rc = view_init(m.v, *m.prm, descs[i].init_genotypes, descs[i].p0_q32);
+        const int rc = view_init(m.v, *m.prm,
+                                 descs[i].allele_model == 1u ? reinterpret_cast<const uint32_t *>(descs[i].init_values)
+                                                             : descs[i].init_genotypes,
+                                 descs[i].p0_q32);
         if (rc != SPG_OK) {
             spg_batch *raw = b.release();
             spg_batch_destroy(raw);
@@ -361,8 +368,8 @@ int spg_batch_autotune(spg_batch *b, uint32_t gens_per_trial, spg_autotune_repor
             rep.worst_ms[gi] = worst_ms / (float)gens_per_trial;
         }
     }
-    // members with a linkage map or parent weights keep the variant shape and
-    // advance by as many generations as the tuned ones
+    // members with a linkage map, parent weights or continuous values keep the
+    // variant shape and advance by as many generations as the tuned ones
     for (uint32_t gi = 4; gi < (uint32_t)b->groups.size() && rc == SPG_OK; ++gi) {
         const Group &g = b->groups[gi];
         if (g.members.empty()) continue;

@@ -494,11 +494,12 @@ int enqueue_generations(const GenLaunch &gl, uint32_t n_gen, GraphChain &chain, 
 // ------------------------------------------------- launch groups
 // Bytes of a launch group's table: segments, runs (at most one per member plus
 // one per piece: one round of blocks, or pieces of kPieceOffspring offspring
-// or more), the blocks' run offsets and the bucket map.
+// or more), the blocks' run offsets, the bucket map and the tile map.
 size_t group_table_bytes(uint32_t members, uint64_t offspring, uint32_t buckets) {
     const uint64_t runs = 2ull * members + offspring / kPieceOffspring + kMaxGridBlocks + 1ull;
     return align_up((size_t)members * sizeof(Segment), 256) + align_up((size_t)runs * sizeof(Run), 256) +
-           align_up((size_t)(kMaxGridBlocks + 1) * 4, 256) + align_up((size_t)buckets * 4, 256);
+           align_up((size_t)(kMaxGridBlocks + 1) * 4, 256) + align_up((size_t)buckets * 4, 256) +
+           align_up((size_t)(offspring / kBlock + members + 1) * 4, 256);  // tile map (continuous groups)
 }
 
 uint32_t tiles_for(uint32_t n, const Shape &shape) {
@@ -560,30 +561,35 @@ void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_
 }
 
 int build_group_launch(const std::vector<const PopView *> &members, uint32_t words, const Shape &shape, bool eco,
-                       bool dom, char *table, size_t table_capacity, GenLaunch &gl, bool linked, bool weighted) {
+                       bool dom, char *table, size_t table_capacity, GenLaunch &gl, bool linked, bool weighted,
+                       bool continuous) {
     if (members.empty()) {
         gl = GenLaunch{};
         return SPG_OK;
     }
-    if (!supported_shape(words, shape) ||
-        ((linked || weighted) && (shape.block != (uint32_t)kBlock || shape.items != 1u || shape.lanes != 1u)))
+    const bool one_shape = linked || weighted || continuous;
+    if ((!continuous && !supported_shape(words, shape)) ||
+        (one_shape && (shape.block != (uint32_t)kBlock || shape.items != 1u || shape.lanes != 1u)))
         return fail(SPG_ERR_INVALID,
                     "unsupported launch shape (%u threads, %u offspring per thread, %u lanes per offspring) for %u loci",
-                    shape.block, shape.items, shape.lanes, 32u * words);
-    // members in HBM: staged parents (where an instance has them)
-    OffspringKernel k = offspring_kernel(words, shape, linked, weighted, eco, dom, true);
+                    shape.block, shape.items, shape.lanes, continuous ? 2u * words : 32u * words);
+    // members in HBM: staged parents (where an instance has them); continuous
+    // values (records of 2L int16, words = L / 2): one block per 256 offspring
+    OffspringKernel k = continuous ? continuous_kernel(2u * words)
+                                   : offspring_kernel(words, shape, linked, weighted, eco, dom, true);
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");
     std::vector<Segment> segs;
-    std::vector<uint32_t> tiles, bucket_map;
+    std::vector<uint32_t> tiles, bucket_map, tile_map;
     segs.reserve(members.size());
     uint32_t total_tiles = 0, buckets = 0;
     uint64_t offspring = 0;
     for (uint32_t si = 0; si < members.size(); ++si) {
         const PopView &v = *members[si];
-        const uint32_t nt = tiles_for(v.n, shape);
+        const uint32_t nt = continuous ? (v.n + kBlock - 1) / kBlock : tiles_for(v.n, shape);
         segs.push_back(segment_at(v.base, v.L, v.n, nt, total_tiles, v.nbuckets, buckets));
         tiles.push_back(nt);
+        if (continuous) tile_map.insert(tile_map.end(), nt, si);
         bucket_map.insert(bucket_map.end(), v.nbuckets, si);
         total_tiles += nt;
         buckets += v.nbuckets;
@@ -593,18 +599,21 @@ int build_group_launch(const std::vector<const PopView *> &members, uint32_t wor
     const uint32_t min_piece = std::max(1u, kPieceOffspring / tile_size(shape));
     std::vector<Run> runs;
     std::vector<uint32_t> block_runs;
-    schedule_runs(tiles, G, min_piece, runs, block_runs);
+    if (!continuous) schedule_runs(tiles, G, min_piece, runs, block_runs);
     if (group_table_bytes((uint32_t)segs.size(), offspring, buckets) > table_capacity)
         return fail(SPG_ERR_INVALID, "launch table does not fit its buffer");
     const size_t off_runs = align_up(segs.size() * sizeof(Segment), 256);
     const size_t off_block = off_runs + align_up(runs.size() * sizeof(Run), 256);
     const size_t off_buckets = off_block + align_up((size_t)(kMaxGridBlocks + 1) * 4, 256);
+    const size_t off_tiles = off_buckets + align_up((size_t)buckets * 4, 256);
     cudaError_t e = cudaMemcpy(table, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(table + off_runs, runs.data(), runs.size() * sizeof(Run), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(table + off_block, block_runs.data(), block_runs.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(table + off_buckets, bucket_map.data(), bucket_map.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !tile_map.empty())
+        e = cudaMemcpy(table + off_tiles, tile_map.data(), tile_map.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload launch table");
     gl = GenLaunch{};
     gl.offspring = k;
@@ -613,6 +622,7 @@ int build_group_launch(const std::vector<const PopView *> &members, uint32_t wor
     gl.args.runs = reinterpret_cast<const Run *>(table + off_runs);
     gl.args.block_runs = reinterpret_cast<const uint32_t *>(table + off_block);
     gl.args.bucket_seg = reinterpret_cast<const uint32_t *>(table + off_buckets);
+    gl.args.tile_seg = reinterpret_cast<const uint32_t *>(table + off_tiles);
     gl.args.nsegs = (uint32_t)segs.size();
     if (segs.size() == 1) {
         // one member: contiguous shares of its tiles per block (no run table)
@@ -621,8 +631,12 @@ int build_group_launch(const std::vector<const PopView *> &members, uint32_t wor
     }
     gl.args.total_tiles = total_tiles;
     gl.args.total_buckets = buckets;
-    apply_kernel(k, gl.args);
-    gl.blocks = segs.size() == 1 ? std::min(total_tiles, G) : G;
+    if (continuous) {
+        gl.blocks = total_tiles;  // not persistent
+    } else {
+        apply_kernel(k, gl.args);
+        gl.blocks = segs.size() == 1 ? std::min(total_tiles, G) : G;
+    }
     gl.buckets = buckets;
     return SPG_OK;
 }

@@ -249,7 +249,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_offspring_cont(const __grid_const
     __shared__ unsigned long long s_ull[4][NW];
     __shared__ uint32_t s_u32[2][NW];
     __shared__ int s_mm[2][NW];
-    const Segment &sg = a.one;
+    // the block's population and its tile there (a launch group: from the
+    // tile map, one block per launch-wide tile of 256 offspring)
+    const Segment *sgp = &a.one;
+    uint32_t tile = blockIdx.x;
+    if (a.nsegs != 1u) {
+        sgp = a.segs + __ldg(a.tile_seg + tile);
+        tile -= sgp->tile_begin;
+    }
+    const Segment &sg = *sgp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const PopNow now = read_state(sg.state);
     if (!now.active) return;
@@ -266,7 +274,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_offspring_cont(const __grid_const
     uint32_t *bucket_next = sg.bucket_sum + ((g + 1u) & 1u) * sg.nbuckets;
     if (tid < kMaxKmax) s_cdf[tid] = (uint32_t)tid < kmax ? P->cdf[tid] : 0u;
     __syncthreads();
-    const uint32_t base = blockIdx.x * (uint32_t)kBlock;
+    const uint32_t base = tile * (uint32_t)kBlock;
     if (tid == 0 && base % kBucket == 0u) bucket_next[base / kBucket] = 0u;
     const uint32_t wbase = base + (uint32_t)warp * 32u;
     const uint32_t grp = (uint32_t)lane / G, li = (uint32_t)lane % G;

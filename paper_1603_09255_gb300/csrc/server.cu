@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <deque>
 #include <memory>
 #include <new>
@@ -31,9 +32,10 @@ using namespace spg;
 
 namespace {
 
-// Groups by locus count (W = 1, 2, 4, 8) and variant: 0-3 plain, 4 + 4v + W
-// index for v = 0 linkage map, 1 parent weights, 2 both (the variant shape).
-constexpr int kGroups = 16;
+// Groups by locus count (L = 32, 64, 128, 256: index 0-3) and variant: the
+// index for plain jobs, 4 + 4v + index for v = 0 linkage map, 1 parent
+// weights, 2 both, 16 + index for continuous values (variants: one shape).
+constexpr int kGroups = 20;
 
 struct Job {
     spg_pop_desc desc{};
@@ -58,9 +60,12 @@ struct Job {
     uint32_t final_gen = 0;
 };
 
-uint32_t group_of(uint32_t words, bool linked, bool weighted) {
-    return (words == 1 ? 0u : words == 2 ? 1u : words == 4 ? 2u : 3u) + 4u * ((linked ? 1u : 0u) + (weighted ? 2u : 0u));
+uint32_t group_of(uint32_t n_loci, bool linked, bool weighted, bool continuous) {
+    const uint32_t l = n_loci == 32 ? 0u : n_loci == 64 ? 1u : n_loci == 128 ? 2u : 3u;
+    return continuous ? 16u + l : l + 4u * ((linked ? 1u : 0u) + (weighted ? 2u : 0u));
 }
+bool continuous_job(const spg_pop_desc &d) { return d.allele_model == 1u; }
+uint32_t job_words(const spg_pop_desc &d) { return continuous_job(d) ? d.n_loci / 2 : d.n_loci / 32; }
 
 }  // namespace
 
@@ -123,7 +128,7 @@ int admit(spg_server *s, Job &j) {
     if (s->used + j.footprint > s->cfg.memory_budget) return 0;
     j.arena = static_cast<char *>(s->alloc.alloc(j.footprint, s->stream));
     if (!j.arena) return 0;  // the allocator is full right now; retry next tick
-    const uint32_t words = j.desc.n_loci / 32;
+    const uint32_t words = job_words(j.desc);
     j.prm.reset(new (std::nothrow) PopParams());
     if (!j.prm) return fail(SPG_ERR_OOM, "host allocation failed");
     int rc = build_params(&j.desc, *j.prm);
@@ -135,7 +140,7 @@ int admit(spg_server *s, Job &j) {
     j.v.words = words;
     j.v.cap = j.prm->stats_cap;
     j.v.nbuckets = bucket_count(j.desc.n);
-    j.v.L = layout_for(j.desc.n, words, j.v.nbuckets, j.v.cap, j.weights != nullptr);
+    j.v.L = layout_for(j.desc.n, words, j.v.nbuckets, j.v.cap, j.weights != nullptr, !continuous_job(j.desc));
     j.v.stream = s->stream;
     cudaError_t e = cudaSuccess;
     if (j.link) {  // the variant tables in the job's memory (read by its parameters)
@@ -169,11 +174,14 @@ int rebuild(spg_server *s) {
         uint64_t offspring = 0;
         uint32_t buckets = 0;
         bool eco = false, dom = false;
-        const uint32_t words = 1u << (gi % 4);
-        const bool linked = ((gi / 4) & 1) != 0, weighted = ((gi / 4) & 2) != 0;
+        const bool continuous = gi >= 16;
+        const uint32_t words = continuous ? (32u << (gi % 4)) / 2u : 1u << (gi % 4);
+        const bool linked = !continuous && ((gi / 4) & 1) != 0, weighted = !continuous && ((gi / 4) & 2) != 0;
         for (uint64_t id : s->resident) {
             const Job &j = *s->jobs[id];
-            if (group_of(j.v.words, j.link != nullptr, j.weights != nullptr) != (uint32_t)gi) continue;
+            if (group_of(j.desc.n_loci, j.link != nullptr, j.weights != nullptr, continuous_job(j.desc)) !=
+                (uint32_t)gi)
+                continue;
             views.push_back(&j.v);
             offspring += j.v.n;
             buckets += j.v.nbuckets;
@@ -190,9 +198,9 @@ int rebuild(spg_server *s) {
             if (!s->table[gi]) return fail(SPG_ERR_OOM, "launch table allocation failed");
             s->table_cap[gi] = cap;
         }
-        const Shape shape = (linked || weighted) ? Shape{(uint32_t)kBlock, 1u, 1u} : default_shape(words);
+        const Shape shape = (linked || weighted || continuous) ? Shape{(uint32_t)kBlock, 1u, 1u} : default_shape(words);
         rc = build_group_launch(views, words, shape, eco, dom, s->table[gi], s->table_cap[gi], s->gl[gi], linked,
-                                weighted);
+                                weighted, continuous);
         if (rc != SPG_OK) return rc;
     }
     s->dirty = false;
@@ -267,8 +275,6 @@ int spg_server_submit(spg_server *s, const spg_pop_desc *desc, const spg_ecology
     if (rc != SPG_OK) return rc;
     if (eco && (rc = check_ecology(eco)) != SPG_OK) return rc;
     if (n_gen == 0) return fail(SPG_ERR_INVALID, "a job needs at least one generation");
-    if (desc->allele_model)
-        return fail(SPG_ERR_INVALID, "continuous alleles are supported for single populations");
     std::unique_ptr<Job> j(new (std::nothrow) Job());
     if (!j) return fail(SPG_ERR_OOM, "host allocation failed");
     if (desc->map_morgans) {  // built (and checked) now: the caller's arrays need not outlive the call
@@ -288,6 +294,10 @@ int spg_server_submit(spg_server *s, const spg_pop_desc *desc, const spg_ecology
     j->table.assign(desc->surv_table, desc->surv_table + SPG_N_BINS);
     if (desc->init_genotypes)
         j->founders.assign(desc->init_genotypes, desc->init_genotypes + (size_t)desc->n * 2 * (desc->n_loci / 32));
+    if (continuous_job(*desc) && desc->init_values) {  // [N * 2L] int16, kept as the records' words
+        j->founders.resize((size_t)desc->n * desc->n_loci);
+        std::memcpy(j->founders.data(), desc->init_values, j->founders.size() * 4);
+    }
     j->desc.effects = j->effects.data();
     if (desc->dominance) {
         j->dominance.assign(desc->dominance, desc->dominance + desc->n_loci);
@@ -295,6 +305,7 @@ int spg_server_submit(spg_server *s, const spg_pop_desc *desc, const spg_ecology
     }
     j->desc.surv_table = j->table.data();
     j->desc.init_genotypes = nullptr;
+    j->desc.init_values = nullptr;
     j->desc.stats_capacity = n_gen;  // every generation's statistics stay readable
     if (eco) {
         j->has_eco = true;
@@ -304,8 +315,10 @@ int spg_server_submit(spg_server *s, const spg_pop_desc *desc, const spg_ecology
     }
     j->n_gen = n_gen;
     j->t_arrival = t_arrival;
-    const uint32_t words = desc->n_loci / 32;
-    j->footprint = align_up(layout_for(desc->n, words, bucket_count(desc->n), n_gen, j->weights != nullptr).total, 256);
+    j->footprint = align_up(layout_for(desc->n, job_words(*desc), bucket_count(desc->n), n_gen, j->weights != nullptr,
+                                       !continuous_job(*desc))
+                                .total,
+                            256);
     if (j->footprint > s->cfg.memory_budget)
         return fail(SPG_ERR_BUDGET, "job needs %zu bytes, the budget is %zu", j->footprint, s->cfg.memory_budget);
     *job = s->jobs.size();

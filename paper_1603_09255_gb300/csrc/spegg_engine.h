@@ -104,11 +104,12 @@ void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_
 // Segment table, runs and bucket map of one launch group, uploaded into
 // `table` (device memory; synchronous), and the group's launch description.
 // eco / dom: some member has an ecology / dominance deviations.
-// linked / weighted: the members' variant (all alike; such groups take the
-// variant shape only: kBlock threads, one offspring per thread, one lane).
+// linked / weighted / continuous: the members' variant (all alike; such
+// groups take the variant shape only: kBlock threads, one offspring per
+// thread, one lane; continuous: words = L / 2, the int16 records' words).
 int build_group_launch(const std::vector<const PopView *> &members, uint32_t words, const Shape &shape, bool eco,
                        bool dom, char *table, size_t table_capacity, GenLaunch &gl, bool linked = false,
-                       bool weighted = false);
+                       bool weighted = false, bool continuous = false);
 int view_sync(const PopView &v);
 int view_state(const PopView &v, DevState &st);
 int view_set_state(const PopView &v, uint32_t gen, uint32_t S, uint32_t f, double R, int32_t status,

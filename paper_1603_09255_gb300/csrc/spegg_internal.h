@@ -169,6 +169,7 @@ struct GenArgs {
     const Run *runs;             // runs of all offspring blocks, block by block (nsegs > 1)
     const uint32_t *block_runs;  // runs of block b: runs[block_runs[b] .. block_runs[b + 1]) (nsegs > 1)
     const uint32_t *bucket_seg;  // segment of each launch-wide bucket (nsegs > 1)
+    const uint32_t *tile_seg;    // segment of each launch-wide tile (continuous-allele groups, nsegs > 1)
     uint32_t nsegs;
     uint32_t total_tiles;        // tiles of the single segment (nsegs == 1: contiguous shares per block)
     uint32_t total_buckets;

@@ -441,13 +441,19 @@ def _desc_for(w, keep: list, stats_capacity: int = 0) -> spg_pop_desc:
     mw = None if getattr(w, "mother_weights", None) is None else _u32(w.mother_weights)
     fw = None if getattr(w, "father_weights", None) is None else _u32(w.father_weights)
     dm = None if getattr(w, "dominance", None) is None else np.ascontiguousarray(w.dominance, dtype=np.int16)
-    keep.extend([e, t, g, m, mw, fw, dm])
+    iv = getattr(w, "init_values", None)
+    if iv is not None:
+        iv = np.ascontiguousarray(iv, dtype=np.int16).reshape(-1)
+        if iv.size != int(w.n) * 2 * int(w.n_loci):
+            raise ValueError("init_values must have n * 2 * n_loci entries")
+    keep.extend([e, t, g, m, mw, fw, dm, iv])
     return spg_pop_desc(int(w.n), int(w.n_loci), int(w.seed), int(w.replicate), e.ctypes.data,
                         None if g is None else g.ctypes.data, int(w.p0_q32), t.ctypes.data, int(w.bias),
                         int(w.shift), float(w.mu), int(stats_capacity), None if m is None else m.ctypes.data,
                         None if mw is None else mw.ctypes.data, None if fw is None else fw.ctypes.data,
                         None if dm is None else dm.ctypes.data, int(getattr(w, "allele_model", 0)),
-                        float(getattr(w, "mut_sd", 0.0)), float(getattr(w, "env_sd", 0.0)), None)
+                        float(getattr(w, "mut_sd", 0.0)), float(getattr(w, "env_sd", 0.0)),
+                        None if iv is None else iv.ctypes.data)
 
 
 class Batch:
@@ -518,10 +524,18 @@ class Batch:
 
     def genotypes(self, member: int) -> np.ndarray:
         w = self.workloads[member]
-        out = np.zeros((w.n, 2 * (w.n_loci // 32)), np.uint32)
+        words = w.n_loci // 2 if int(getattr(w, "allele_model", 0)) == 1 else w.n_loci // 32
+        out = np.zeros((w.n, 2 * words), np.uint32)
         check(lib().spg_batch_read_genotypes(self._h, int(member), out.ctypes.data, out.size),
               "spg_batch_read_genotypes")
         return out
+
+    def values(self, member: int) -> np.ndarray:
+        """Allelic values [n, 2, L] (int16 Q8) of a continuous-allele member."""
+        w = self.workloads[member]
+        if int(getattr(w, "allele_model", 0)) != 1:
+            raise ValueError("not a continuous-allele member")
+        return self.genotypes(member).view(np.int16).reshape(w.n, 2, w.n_loci)
 
     def survivors(self, member: int) -> np.ndarray:
         S = ctypes.c_uint32(0)

@@ -1,6 +1,8 @@
 """Batched replicates (spg_batch_*) through the C ABI: every member equals
 the same population stepped alone (and, for a sample, the CPU oracle) bit for
 bit; the launch-shape autotuner and tilings never change results."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -194,6 +196,65 @@ def test_autotune_advances_variant_members_alike():
     for i, w in enumerate(ws):
         p = sp().Population.from_workload(w, stats_capacity=64)
         p.step(ran + 3)
+        st = p.state()
+        ref = p.read_stats(1, st["gen"]) if st["gen"] else np.zeros(0, sp().STATS_DTYPE)
+        assert_member_equals(b, i, ref, p.genotypes(), p.survivors(), st)
+        p.close()
+    b.close()
+
+
+def continuous_workloads():
+    """Continuous-allele members at every locus count (ragged sizes, one with
+    the logistic resource, one with caller founders) among plain members."""
+    out = []
+    sizes = [1, 300, 2500, 4097, 9001]
+    for r in range(10):
+        n_loci, n = [32, 64, 128, 256][r % 4], sizes[r % len(sizes)]
+        if r % 2 == 0:
+            w = S.continuous_trait(n=n, n_loci=n_loci, mu=1e-2, mut_sd=0.1, env_sd=0.2 * (r % 3), seed=21,
+                                   replicate=r, effects_seed=700 + r)
+            if r == 4:
+                w = dataclasses.replace(w, eco_r=0.5, eco_K=4.0 * n, eco_R0=2.0 * n, eco_R_half=0.4 * n,
+                                        attack=S.attack_table(w.bias, w.shift))
+            if r == 6:
+                rng = np.random.default_rng(6)
+                w = dataclasses.replace(w, init_values=rng.integers(-300, 300, (n, 2 * n_loci)).astype(np.int16))
+        else:
+            w = S.single_species(n=n, n_loci=n_loci, mu=1e-3, s=1.0, seed=21, replicate=r, effects_seed=700 + r)
+        out.append(w)
+    return out
+
+
+def test_batch_continuous_members_equal_oracle():
+    """Continuous-allele members share launches (one block per 256 offspring,
+    the block's member from the launch's tile map) and equal the oracle."""
+    ws = continuous_workloads()
+    b = sp().Batch(ws, stats_capacity=16)
+    b.step(6)
+    for i, w in enumerate(ws):
+        orc = oracle.OraclePopulation.from_workload(w)
+        so = orc.step(6)
+        st = b.state(i)
+        assert {k: st[k] for k in ("gen", "S", "status", "f", "R")} == \
+            {k: orc.state()[k] for k in ("gen", "S", "status", "f", "R")}, i
+        got = b.read_stats(i, 1, st["gen"]) if st["gen"] else np.zeros(0, sp().STATS_DTYPE)
+        assert got.tobytes() == so.tobytes(), i
+        assert np.array_equal(b.survivors(i), orc.survivors()), i
+        if int(getattr(w, "allele_model", 0)) == 1:
+            assert np.array_equal(b.values(i), orc.values()), i
+        else:
+            assert np.array_equal(b.genotypes(i), orc.genotypes()), i
+    b.close()
+
+
+def test_batch_continuous_members_equal_standalone_over_a_graph():
+    ws = continuous_workloads()
+    b = sp().Batch(ws, stats_capacity=64)
+    ran = b.autotune(1) + 40
+    b.step(40)
+    for i, w in enumerate(ws):
+        p = sp().Population.from_workload(w, stats_capacity=64)
+        p.step(ran)
         st = p.state()
         ref = p.read_stats(1, st["gen"]) if st["gen"] else np.zeros(0, sp().STATS_DTYPE)
         assert_member_equals(b, i, ref, p.genotypes(), p.survivors(), st)

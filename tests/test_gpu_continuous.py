@@ -102,8 +102,14 @@ def test_continuous_validation_through_the_abi():
         sp.Population.from_workload(dataclasses.replace(w, map_morgans=S.linkage_map(64, 2, 1.0)))
     with pytest.raises(sp.SpeggError):
         sp.Population.from_workload(dataclasses.replace(w, mut_sd=100.0))
+    # batch members and served jobs are checked alike
     with pytest.raises(sp.SpeggError):
-        sp.Batch([w])
+        sp.Batch([w, dataclasses.replace(w, mut_sd=100.0)])
+    srv = sp.Server()
+    with pytest.raises(sp.SpeggError):
+        srv.submit(dataclasses.replace(w, map_morgans=S.linkage_map(64, 2, 1.0)), 4)
+    srv.close()
+    sp.Batch([w]).close()
 
 
 def test_continuous_full_size_two_generations():

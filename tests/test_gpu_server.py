@@ -130,3 +130,20 @@ def test_served_variant_jobs_equal_jobs_run_alone():
         got = srv.job_stats(int(jobs[i]), 1, info["gen"]) if info["gen"] else ref
         assert got.tobytes() == ref.tobytes(), f"job {i} differs from the same population run alone"
     srv.close()
+
+
+def test_served_continuous_jobs_equal_jobs_run_alone():
+    ws, gens, arrivals = small_trace(count=10, seed=13)
+    for i, w in enumerate(ws):
+        if i % 2 == 0:  # continuous-allele jobs of the same size and locus count
+            ws[i] = S.continuous_trait(n=w.n, n_loci=w.n_loci, mu=1e-2, mut_sd=0.1, env_sd=0.1 * (i % 3),
+                                       seed=w.seed, replicate=w.replicate, effects_seed=900 + i)
+    srv = sp().Server(memory_budget=64 << 20, max_resident=4, gens_per_tick=8)
+    jobs = srv.run_trace(ws, gens, arrivals)
+    for i, (w, g) in enumerate(zip(ws, gens)):
+        info = srv.job_info(int(jobs[i]))
+        ref, st = alone(w, g)
+        assert info["state"] == 2 and info["gen"] == st["gen"] and info["status"] == st["status"]
+        got = srv.job_stats(int(jobs[i]), 1, info["gen"]) if info["gen"] else ref
+        assert got.tobytes() == ref.tobytes(), f"job {i} differs from the same population run alone"
+    srv.close()
