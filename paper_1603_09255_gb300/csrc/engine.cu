@@ -575,7 +575,7 @@ int build_group_launch(const std::vector<const PopView *> &members, uint32_t wor
                     shape.block, shape.items, shape.lanes, continuous ? 2u * words : 32u * words);
     // members in HBM: staged parents (where an instance has them); continuous
     // values (records of 2L int16, words = L / 2): one block per 256 offspring
-    OffspringKernel k = continuous ? continuous_kernel(2u * words)
+    OffspringKernel k = continuous ? continuous_kernel(2u * words, members.size() > 1)
                                    : offspring_kernel(words, shape, linked, weighted, eco, dom, true);
     int rc = prepare_offspring(k);
     if (rc != SPG_OK) return fail(rc, "offspring kernel setup failed");

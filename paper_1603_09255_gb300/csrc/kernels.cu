@@ -235,7 +235,7 @@ __device__ __forceinline__ void add_step(uint4 &c, uint32_t k, int32_t step) {
 // feed the same compaction kernel as the biallelic model.
 constexpr int kContInFlight = 1;  // offspring a group of lanes forms at a time (four blocks per SM)
 
-template <int G, int U>
+template <int G, int U, bool GROUP>
 __global__ void __launch_bounds__(kBlock, 4) k_offspring_cont(const __grid_constant__ GenArgs a) {
     constexpr uint32_t L = 8u * G;
     constexpr int NW = kBlock / 32, NO = 32 / G;
@@ -249,11 +249,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_offspring_cont(const __grid_const
     __shared__ unsigned long long s_ull[4][NW];
     __shared__ uint32_t s_u32[2][NW];
     __shared__ int s_mm[2][NW];
-    // the block's population and its tile there (a launch group: from the
-    // tile map, one block per launch-wide tile of 256 offspring)
+    // the block's population and its tile there (GROUP: a launch group of
+    // several populations, from the tile map, one block per launch-wide tile of
+    // 256 offspring; otherwise the segment in the kernel parameters)
     const Segment *sgp = &a.one;
     uint32_t tile = blockIdx.x;
-    if (a.nsegs != 1u) {
+    if constexpr (GROUP) {
         sgp = a.segs + __ldg(a.tile_seg + tile);
         tile -= sgp->tile_begin;
     }
@@ -868,13 +869,13 @@ OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked
     return k;
 }
 
-OffspringKernel continuous_kernel(uint32_t n_loci) {
+OffspringKernel continuous_kernel(uint32_t n_loci, bool group) {
     OffspringKernel k;
     switch (n_loci) {
-        case 32: k.fn = &k_offspring_cont<4, kContInFlight>; break;
-        case 64: k.fn = &k_offspring_cont<8, kContInFlight>; break;
-        case 128: k.fn = &k_offspring_cont<16, kContInFlight>; break;
-        case 256: k.fn = &k_offspring_cont<32, kContInFlight>; break;
+        case 32: k.fn = group ? &k_offspring_cont<4, kContInFlight, true> : &k_offspring_cont<4, kContInFlight, false>; break;
+        case 64: k.fn = group ? &k_offspring_cont<8, kContInFlight, true> : &k_offspring_cont<8, kContInFlight, false>; break;
+        case 128: k.fn = group ? &k_offspring_cont<16, kContInFlight, true> : &k_offspring_cont<16, kContInFlight, false>; break;
+        case 256: k.fn = group ? &k_offspring_cont<32, kContInFlight, true> : &k_offspring_cont<32, kContInFlight, false>; break;
         default: return OffspringKernel{};
     }
     k.block = kBlock;

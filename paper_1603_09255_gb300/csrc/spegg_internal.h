@@ -232,7 +232,7 @@ int launch_dense_gather(uint32_t words, const uint32_t *geno, const uint32_t *su
                         void *stream);
 // The generation kernel of a continuous-allele population (one warp per
 // offspring at a time, 256 offspring per block, no persistent grid).
-OffspringKernel continuous_kernel(uint32_t n_loci);
+OffspringKernel continuous_kernel(uint32_t n_loci, bool group = false);  // group: several populations (tile map)
 // Enqueue continuous founders: value = effect[l] * allele of the biallelic
 // founder draws (records of 2L int16), survivors = 0..n-1.
 int launch_founders_cont(const PopParams *prm, uint32_t n_loci, uint32_t *geno, uint32_t *surv, uint32_t n,
