@@ -699,6 +699,7 @@ struct spg_space {
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;                     // the newborns' kernel, beside the survivors' move
     cudaEvent_t fork = nullptr, join = nullptr;     // side stream after the step's scans / stream after the newborns
+    cudaGraphExec_t chunk = nullptr;                // kSpGraphSteps steps, captured on first use
     bool own_stream = false;
     Allocator alloc;
     char *arena = nullptr;
@@ -758,6 +759,54 @@ int launch_step(spg_space *c) {
     k_sp_finish<<<1, 32, 0, s>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "space step launch");
+}
+
+// Steps in a cached graph: every step's kernels take their parameters from
+// the (fixed) SpaceArgs and their per-step state from device memory, so one
+// captured chunk replays any kSpGraphSteps consecutive steps.
+constexpr uint32_t kSpGraphSteps = 32;
+
+int launch_steps(spg_space *c, uint32_t n) {
+    for (uint32_t i = 0; i < n; ++i) {
+        int rc;
+        switch (c->W) {
+            case 1: rc = launch_step<1>(c); break;
+            case 2: rc = launch_step<2>(c); break;
+            case 4: rc = launch_step<4>(c); break;
+            default: rc = launch_step<8>(c); break;
+        }
+        if (rc != SPG_OK) return rc;
+    }
+    return SPG_OK;
+}
+
+// One chunk of kSpGraphSteps steps through the cached graph (captured from
+// the step launches on first use).  A stream that is being captured already
+// (the caller building a graph of its own) gets the launches themselves.
+int launch_chunk(spg_space *c) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(c->stream, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone) return launch_steps(c, kSpGraphSteps);
+    if (!c->chunk) {
+        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        const int rc = launch_steps(c, kSpGraphSteps);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->stream, &g);  // ends the capture whatever the launches returned
+        if (rc != SPG_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return rc != SPG_OK ? rc : cuda_fail(e, "cudaStreamEndCapture");
+        }
+        e = cudaGraphInstantiate(&c->chunk, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->chunk = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+    }
+    e = cudaGraphLaunch(c->chunk, c->stream);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "cudaGraphLaunch");
 }
 
 }  // namespace
@@ -961,17 +1010,12 @@ int spg_space_create(const spg_space_desc *desc, const spg_allocator *alloc, voi
 
 int spg_space_step(spg_space *c, uint32_t n_steps) {
     if (!c) return fail(SPG_ERR_INVALID, "community is NULL");
-    for (uint32_t i = 0; i < n_steps; ++i) {
-        int rc;
-        switch (c->W) {
-            case 1: rc = launch_step<1>(c); break;
-            case 2: rc = launch_step<2>(c); break;
-            case 4: rc = launch_step<4>(c); break;
-            default: rc = launch_step<8>(c); break;
-        }
+    uint32_t i = 0;
+    for (; i + kSpGraphSteps <= n_steps; i += kSpGraphSteps) {
+        const int rc = launch_chunk(c);
         if (rc != SPG_OK) return rc;
     }
-    return SPG_OK;
+    return launch_steps(c, n_steps - i);
 }
 
 int spg_space_get_state(spg_space *c, uint32_t *t, int32_t *status, uint32_t *total) {
@@ -1048,6 +1092,7 @@ void spg_space_destroy(spg_space *c) {
     if (c->arena) c->alloc.release(c->arena, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->side) cudaStreamSynchronize(c->side);
+    if (c->chunk) cudaGraphExecDestroy(c->chunk);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->fork) cudaEventDestroy(c->fork);

@@ -56,6 +56,19 @@ def test_space_matches_oracle(X, Y, n0, L, steps, disp):
     assert gpu.state()["t"] == steps and gpu.state()["status"] == 0
 
 
+def test_space_graph_chunks_match_oracle():
+    """Steps in chunks of 32 replay one captured graph: 70 steps (two chunks
+    and 6 direct steps), then a call that replays the cached graph again."""
+    c = S.spatial_community(X=3, Y=3, n0=70, n_loci=64, mu=1e-3, disp=0.2, seed=17)
+    gpu = sp().Space(c, capacity=60_000, staging_capacity=30_000, stats_capacity=128)  # grows to ~2.1e4
+    orc = oracle.OracleSpace(c)
+    gpu.step(70)
+    assert_same(gpu, orc, 70)
+    gpu.step(32)
+    assert_same(gpu, orc, 32)
+    assert gpu.state()["t"] == 102 and gpu.state()["status"] == 0
+
+
 def test_space_founders_match_and_stepwise_calls():
     c = S.spatial_community(X=5, Y=4, n0=90, n_loci=128, mu=1e-2, seed=9)
     gpu = sp().Space(c, stats_capacity=32)
