@@ -75,6 +75,9 @@ int main() {
         // uncounted set-up (a member continued from the previous piece)
         const uint64_t rounds = std::max<uint64_t>(1, T / ((uint64_t)G * piece));
         if (work_max > (double)units / G + 3.0 * rounds + 1.0) return fail(c, "block work above the bound");
+        // the launch table holds one run per member plus one per piece: G
+        // pieces, or pieces of min_piece tiles or more
+        if (runs.size() > (size_t)M + std::max<uint64_t>(G, T / piece)) return fail(c, "more runs than the table holds");
         std::printf("%u %u %u %llu %zu %.4f\n", M, G, piece, (unsigned long long)T, runs.size(),
                     work_sum > 0 ? work_max / (work_sum / G) : 1.0);
     }
