@@ -347,9 +347,12 @@ void spg_batch_destroy(spg_batch *batch);
  * memory is freed), admits queued jobs in arrival order while a resident slot
  * is free and the job's device footprint fits the memory budget, and advances
  * every resident job by up to gens_per_tick generations in shared launches
- * (jobs of different lengths and locus counts run together; each stops at its
- * own count).  A job's results are identical to the same population run
- * alone.  Times are seconds on the server's clock (spg_server_clock). */
+ * (jobs of different lengths, locus counts and variants run together, one
+ * launch group per locus count and variant; each stops at its own count).  A
+ * job's results are identical to the same population run alone.  A job's
+ * linkage map and parent weights are built and checked when it is submitted
+ * (the caller's arrays need not outlive spg_server_submit).  Times are
+ * seconds on the server's clock (spg_server_clock). */
 #define SPG_JOB_QUEUED 0u
 #define SPG_JOB_RESIDENT 1u
 #define SPG_JOB_FINISHED 2u
