@@ -62,6 +62,8 @@ def lib():
         L.orc_step.restype = ctypes.c_int
         L.orc_read_genotypes.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.orc_read_genotypes.restype = ctypes.c_int
+        L.orc_locus_counts.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_locus_counts.restype = ctypes.c_int
         L.orc_read_survivors.argtypes = [ctypes.c_void_p, ctypes.c_void_p, u32p]
         L.orc_read_survivors.restype = ctypes.c_int
         L.orc_get_state.argtypes = [ctypes.c_void_p, u32p, u32p, ctypes.POINTER(ctypes.c_int32),
@@ -210,6 +212,16 @@ class OraclePopulation:
     def genotypes(self) -> np.ndarray:
         out = np.zeros((self.n, self.n_loci if self.continuous else 2 * self.words), np.uint32)
         lib().orc_read_genotypes(self._h, out.ctypes.data)
+        return out
+
+    def locus_counts(self) -> np.ndarray:
+        """Allele-1 copies per locus over both haplotypes of the current
+        generation's N individuals (biallelic populations)."""
+        if self.continuous:
+            raise ValueError("per-locus allele counts are for biallelic populations")
+        out = np.zeros(self.n_loci, np.uint32)
+        if lib().orc_locus_counts(self._h, out.ctypes.data) != 0:
+            raise RuntimeError("oracle per-locus counts failed")
         return out
 
     def survivors(self) -> np.ndarray:

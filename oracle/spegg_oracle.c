@@ -832,6 +832,22 @@ int orc_read_genotypes(const orc_pop *p, uint32_t *out)
     return ORC_OK;
 }
 
+/* Per-locus allele counts of the current generation (the offspring formed
+ * last, all N of them): out[l] = the allele-1 copies at locus l over both
+ * haplotypes of every individual, so that out[l] / 2N is the allele frequency
+ * of locus l (S2 "Genetics": biallelic loci, diploid individuals).
+ * Biallelic populations only. */
+int orc_locus_counts(const orc_pop *p, uint32_t *out)
+{
+    if (!p || !out || p->continuous) return ORC_ERR_INVALID;
+    for (uint32_t l = 0; l < p->L; ++l) out[l] = 0;
+    for (uint32_t i = 0; i < p->n; ++i)
+        for (uint32_t h = 0; h < 2; ++h)
+            for (uint32_t l = 0; l < p->L; ++l)
+                if (p->par[((size_t)i * 2 + h) * p->L + l]) out[l] += 1u;
+    return ORC_OK;
+}
+
 int orc_read_survivors(const orc_pop *p, uint32_t *out, uint32_t *S)
 {
     if (!p || !S) return ORC_ERR_INVALID;
