@@ -242,6 +242,24 @@ int spg_step_generations(spg_pop *pop, uint32_t n_gen);
  * left the ring. */
 int spg_read_stats(spg_pop *pop, uint32_t first_gen, uint32_t count, spg_stats *out);
 
+/* Per-locus allele counts (S2 "Genetics": biallelic diploid loci; the allele
+ * frequency of locus l is count[l] / 2N).  With enable != 0, every generation
+ * formed from now on also counts, over both haplotypes of its N offspring,
+ * the allele-1 copies of each locus, kept in a ring of stats_capacity rows of
+ * L uint32 (one more kernel after each compaction; enable = 0 stops it).  The
+ * first call allocates that ring through the population's allocator; the
+ * call waits for the stream.  Biallelic populations only (SPG_ERR_INVALID
+ * for continuous values).  Counts are not part of a checkpoint: after
+ * spg_restore they start again with the next generation formed.
+ * spg_read_locus_counts copies generations first_gen .. first_gen+count-1
+ * to out ([count][L] uint32, row i for generation first_gen + i; waits for
+ * the stream).  Readable: the generations formed since the latest enabling
+ * call (or restore) while counting was on, still in the ring.  SPG_ERR_INVALID
+ * while counts have never been enabled, SPG_ERR_RANGE for any other
+ * generation. */
+int spg_set_locus_counts(spg_pop *pop, int enable);
+int spg_read_locus_counts(spg_pop *pop, uint32_t first_gen, uint32_t count, uint32_t *out);
+
 /* Copy the current generation's N records (N * 2W words) to host memory;
  * n_words must be at least N * 2W.  Waits for the stream. */
 int spg_read_genotypes(spg_pop *pop, uint32_t *host, size_t n_words);

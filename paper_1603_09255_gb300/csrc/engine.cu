@@ -403,19 +403,27 @@ KernelLaunch offspring_launch(const GenLaunch &gl) {
 KernelLaunch compact_launch(const GenLaunch &gl) {
     return {reinterpret_cast<void *>(gl.compact), dim3(gl.buckets), dim3(kCompactThreads), compact_smem(), true};
 }
+// after the compaction has finished (it reads the committed state)
+KernelLaunch locus_launch(const GenLaunch &gl) {
+    return {reinterpret_cast<void *>(gl.locus), dim3(gl.la.blocks), dim3(kLocusBlock), 0u, false};
+}
 }  // namespace
 
 int add_generation_nodes(cudaGraph_t graph, const GenLaunch &gl, void **params, uint32_t len) {
     cudaGraphNode_t prev = nullptr;
-    for (uint32_t i = 0; i < 2 * len; ++i) {
-        const KernelLaunch k = (i % 2) == 0 ? offspring_launch(gl) : compact_launch(gl);
+    LocusArgs la = gl.la;
+    void *locus_params[] = {params[0], &la};  // argument values are copied into the nodes
+    const uint32_t per_gen = gl.locus ? 3u : 2u;
+    for (uint32_t i = 0; i < per_gen * len; ++i) {
+        const uint32_t step = i % per_gen;
+        const KernelLaunch k = step == 0 ? offspring_launch(gl) : step == 1 ? compact_launch(gl) : locus_launch(gl);
         cudaGraphNodeParams np{};
         np.type = cudaGraphNodeTypeKernel;
         np.kernel.func = k.fn;
         np.kernel.gridDim = k.grid;
         np.kernel.blockDim = k.block;
         np.kernel.sharedMemBytes = k.smem;
-        np.kernel.kernelParams = params;
+        np.kernel.kernelParams = step == 2 ? locus_params : params;
         cudaGraphEdgeData edge{};
         if (k.programmatic) {
             edge.from_port = cudaGraphKernelNodePortProgrammatic;
@@ -457,8 +465,11 @@ int launch_generation(const GenLaunch &gl, cudaStream_t stream) {
     cudaLaunchAttribute attr{};
     attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr.val.programmaticStreamSerializationAllowed = 1;
+    LocusArgs la = gl.la;
+    void *locus_params[] = {&a, &la};
     cudaError_t e = cudaSuccess;
-    for (const KernelLaunch &k : {offspring_launch(gl), compact_launch(gl)}) {
+    for (uint32_t step = 0; step < (gl.locus ? 3u : 2u); ++step) {
+        const KernelLaunch k = step == 0 ? offspring_launch(gl) : step == 1 ? compact_launch(gl) : locus_launch(gl);
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = k.grid;
         cfg.blockDim = k.block;
@@ -466,7 +477,7 @@ int launch_generation(const GenLaunch &gl, cudaStream_t stream) {
         cfg.stream = stream;
         cfg.attrs = &attr;
         cfg.numAttrs = k.programmatic ? 1u : 0u;
-        e = cudaLaunchKernelExC(&cfg, k.fn, params);
+        e = cudaLaunchKernelExC(&cfg, k.fn, step == 2 ? locus_params : params);
         if (e != cudaSuccess) break;
     }
     return e == cudaSuccess ? SPG_OK : cuda_fail(e, "generation launch");

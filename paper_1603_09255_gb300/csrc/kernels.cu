@@ -826,6 +826,89 @@ GenKernel compact_kernel(uint32_t words) {
     return k;
 }
 
+// ------------------------------------------------- per-locus allele counts
+// 32 x 32 bit transpose across a warp: afterwards bit b of lane i is what bit
+// i of lane b was.  Stage s swaps the off-diagonal s x s blocks between lanes
+// i and i ^ s (masks keep the low s bits of each 2s-bit group).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, uint32_t lane) {
+    constexpr uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const uint32_t s = 16u >> k;
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, (int)s);
+        x = (lane & s) ? (((y >> s) & M[k]) | (x & ~M[k])) : ((x & M[k]) | ((y << s) & ~M[k]));
+    }
+    return x;
+}
+
+// Allele-1 copies of every locus over both haplotypes of the generation just
+// formed (all N offspring; S2 "Genetics": count / 2N is the locus's allele
+// frequency).  A warp takes 32 records at a time, one per lane, transposes
+// each record word so that lane b holds bit b of the 32 records, and adds its
+// population count to locus 32w + b; the warps of a block add theirs in
+// shared memory and leave the block's row of partial counts; the block that
+// finishes last writes the rows' sum to the generation's ring slot and
+// re-arms the counter.  Counting a generation again writes the same values,
+// so a launch after the population has stopped changes nothing.
+template <int W>
+__global__ void __launch_bounds__(kLocusBlock) k_locus_counts(const __grid_constant__ GenArgs a, const LocusArgs la) {
+    constexpr uint32_t L = 32u * W, NW = kLocusBlock / 32u;
+    __shared__ uint32_t s_cnt[L];
+    __shared__ uint32_t s_last;
+    const Segment &sg = a.one;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t g = ld_relaxed_u32(&sg.state->gen);  // the generation the compaction just committed
+    if (g == 0u) return;                                 // the founders: no generation formed yet
+    for (uint32_t i = tid; i < L; i += kLocusBlock) s_cnt[i] = 0u;
+    __syncthreads();
+    const uint32_t *rec = sg.geno[g & 1u];
+    uint32_t acc[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[w] = 0u;
+    const uint32_t groups = (sg.n + 31u) >> 5;
+    for (uint32_t q = blockIdx.x * NW + warp; q < groups; q += gridDim.x * NW) {
+        const uint32_t i = q * 32u + lane;
+        uint32_t r[2 * W];
+        if (i < sg.n) {
+            load_record<W>(rec + (size_t)i * (2 * W), r);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 2 * W; ++c) r[c] = 0u;
+        }
+#pragma unroll
+        for (int c = 0; c < 2 * W; ++c) acc[c % W] += __popc(warp_transpose32(r[c], lane));
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) atomicAdd(&s_cnt[32u * w + lane], acc[w]);
+    __syncthreads();
+    uint32_t *part = la.part + (size_t)blockIdx.x * L;
+    for (uint32_t i = tid; i < L; i += kLocusBlock) part[i] = s_cnt[i];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(la.done, 1u) == gridDim.x - 1u ? 1u : 0u;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        uint32_t *slot = la.ring + (size_t)((g - 1u) % la.cap) * L;
+        for (uint32_t i = tid; i < L; i += kLocusBlock) {
+            uint32_t sum = 0u;
+            for (uint32_t b = 0; b < gridDim.x; ++b) sum += __ldcg(la.part + (size_t)b * L + i);
+            slot[i] = sum;
+        }
+        if (tid == 0) *la.done = 0u;
+    }
+}
+
+LocusKernel locus_kernel(uint32_t words) {
+    switch (words) {
+        case 1: return &k_locus_counts<1>;
+        case 2: return &k_locus_counts<2>;
+        case 4: return &k_locus_counts<4>;
+        case 8: return &k_locus_counts<8>;
+        default: return nullptr;
+    }
+}
+
 int launch_dense_gather(uint32_t words, const uint32_t *geno, const uint32_t *surv, uint32_t S, uint32_t *dense,
                         void *stream) {
     if (S == 0) return SPG_OK;

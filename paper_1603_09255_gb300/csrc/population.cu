@@ -33,6 +33,12 @@ struct spg_pop {
     WeightParams *weights = nullptr;  // parent acceptance thresholds (when host_prm->weighted)
     GenLaunch gl;
     GraphChain chain;
+    // per-locus allele counts (off until spg_set_locus_counts): ring, partial
+    // rows and counter in one allocation; readable from generation locus_from
+    char *locus_mem = nullptr;
+    LocusArgs locus{};
+    bool locus_on = false;
+    uint32_t locus_from = 0, locus_until = 0;  // counted generations: locus_from .. (on ? now : locus_until)
 
     PopView view() const {
         PopView v;
@@ -48,6 +54,13 @@ struct spg_pop {
 };
 
 namespace {
+
+// The per-locus count kernel after each compaction, or none.
+void attach_locus(spg_pop *p) {
+    p->gl.locus = p->locus_on ? locus_kernel(p->words) : nullptr;
+    p->gl.la = p->locus;
+    p->chain.reset();
+}
 
 // Point the launch at the population's single segment with a launch shape
 // (uploads the device copy of the segment; synchronous).
@@ -90,7 +103,7 @@ int configure_launch(spg_pop *p, const Shape &shape) {
     if (!continuous) apply_kernel(k, p->gl.args);
     p->gl.blocks = continuous ? p->ntiles : std::min(p->ntiles, k.resident);  // continuous: not persistent
     p->gl.buckets = p->nbuckets;
-    p->chain.reset();
+    attach_locus(p);  // also drops the cached graph
     return SPG_OK;
 }
 
@@ -209,6 +222,61 @@ int spg_read_stats(spg_pop *p, uint32_t first_gen, uint32_t count, spg_stats *ou
     return view_read_stats(p->view(), first_gen, count, out);
 }
 
+int spg_set_locus_counts(spg_pop *p, int enable) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    if (p->host_prm->continuous) return fail(SPG_ERR_INVALID, "per-locus allele counts are for biallelic populations");
+    DevState st;
+    int rc = view_state(p->view(), st);  // synchronises: no generation in flight
+    if (rc != SPG_OK) return rc;
+    if (enable && !p->locus_mem) {
+        const uint32_t L = p->n_loci, groups = (p->n + 31u) / 32u;
+        const uint32_t blocks = std::max(1u, std::min(kLocusMaxGrid, (groups + kLocusBlock / 32u - 1u) / (kLocusBlock / 32u)));
+        const size_t ring = align_up((size_t)p->cap * L * 4u, 256), part = align_up((size_t)blocks * L * 4u, 256);
+        p->locus_mem = static_cast<char *>(p->alloc.alloc(ring + part + 256u, p->stream));
+        if (!p->locus_mem) return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", ring + part + 256u);
+        p->locus.ring = reinterpret_cast<uint32_t *>(p->locus_mem);
+        p->locus.part = reinterpret_cast<uint32_t *>(p->locus_mem + ring);
+        p->locus.done = reinterpret_cast<uint32_t *>(p->locus_mem + ring + part);
+        p->locus.cap = p->cap;
+        p->locus.blocks = blocks;
+        const cudaError_t e = cudaMemsetAsync(p->locus.done, 0, 4, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "clear per-locus counter");
+    }
+    if (enable) {
+        if (!p->locus_on) p->locus_from = st.gen + 1u;  // the first generation formed from now on
+    } else if (p->locus_on) {
+        p->locus_until = st.gen;  // the last generation counted
+    }
+    p->locus_on = enable != 0;
+    attach_locus(p);
+    return view_sync(p->view());
+}
+
+int spg_read_locus_counts(spg_pop *p, uint32_t first_gen, uint32_t count, uint32_t *out) {
+    if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
+    if (!out && count) return fail(SPG_ERR_INVALID, "NULL argument");
+    if (!p->locus_mem) return fail(SPG_ERR_INVALID, "per-locus allele counts are off");
+    DevState st;
+    const int rc = view_state(p->view(), st);
+    if (rc != SPG_OK) return rc;
+    if (count == 0) return SPG_OK;
+    const uint64_t last = (uint64_t)first_gen + count - 1;
+    const uint32_t until = p->locus_on ? st.gen : std::min(p->locus_until, st.gen);
+    if (first_gen == 0 || first_gen < p->locus_from || last > until || (uint64_t)st.gen - first_gen >= p->cap)
+        return fail(SPG_ERR_RANGE, "per-locus counts of generations %u..%llu not kept (counted %u..%u, capacity %u)",
+                    first_gen, (unsigned long long)last, p->locus_from, until, p->cap);
+    const size_t row = p->n_loci;
+    for (uint32_t i = 0; i < count;) {
+        const uint32_t slot = (first_gen - 1 + i) % p->cap;
+        const uint32_t run = std::min(count - i, p->cap - slot);
+        const cudaError_t e = cudaMemcpy(out + (size_t)i * row, p->locus.ring + (size_t)slot * row, run * row * 4u,
+                                         cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read per-locus counts");
+        i += run;
+    }
+    return st.status < 0 ? fail(st.status, "device status %d", st.status) : SPG_OK;
+}
+
 int spg_read_genotypes(spg_pop *p, uint32_t *host, size_t n_words) {
     if (!p) return fail(SPG_ERR_INVALID, "population is NULL");
     return view_read_genotypes(p->view(), host, n_words);
@@ -313,6 +381,8 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
     }
     rc = view_set_state(p->view(), h.gen, h.S, h.f, h.R, h.status, 0xFFFFFFFFu);
     if (rc != SPG_OK) return rc;
+    p->locus_from = h.gen + 1u;  // counts of the restored run start with its next generation
+    p->locus_until = h.gen;
     return view_sync(p->view());
 }
 
@@ -354,6 +424,7 @@ void spg_destroy(spg_pop *p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
     p->chain.reset();
+    if (p->locus_mem) p->alloc.release(p->locus_mem, p->stream);
     if (p->arena) p->alloc.release(p->arena, p->stream);
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);

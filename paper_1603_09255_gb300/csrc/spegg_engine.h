@@ -56,9 +56,12 @@ struct GenLaunch {
     GenArgs args{};
     uint32_t blocks = 0;   // offspring grid: min(tiles, resident blocks)
     uint32_t buckets = 0;  // compaction grid
+    LocusKernel locus = nullptr;  // per-locus allele counts after the compaction (single populations; null: off)
+    LocusArgs la{};
 };
 
-// A cached CUDA graph of `length` generations (2 dependent launches each).
+// A cached CUDA graph of `length` generations (2 dependent launches each, 3
+// with per-locus counts).
 struct GraphChain {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -218,6 +218,19 @@ constexpr size_t kStageParentBytes = (size_t)48 << 20;
 int prepare_offspring(OffspringKernel &k);  // sets the shared-memory limit, fills `resident`
 GenKernel compact_kernel(uint32_t words);  // the compaction kernel for records of 2W words
 uint32_t compact_smem();                   // its dynamic shared memory (the ring of child records)
+
+// Per-locus allele counts of a population (optional, biallelic records):
+// the counts of the generations kept in a ring [cap][L] (generation g in slot
+// (g - 1) % cap), the count kernel's per-block partials [blocks][L] and the
+// counter of its blocks that are done.
+struct LocusArgs {
+    uint32_t *ring, *part, *done;
+    uint32_t cap, blocks;
+};
+constexpr uint32_t kLocusBlock = 256;     // threads per block of the per-locus count kernel
+constexpr uint32_t kLocusMaxGrid = 608;   // its blocks, at most (four per SM)
+using LocusKernel = void (*)(GenArgs, LocusArgs);
+LocusKernel locus_kernel(uint32_t words);  // the count kernel for records of 2W words
 uint32_t tile_size(const Shape &shape);  // offspring per tile: block * items / lanes
 // Copy the offspring kernel's shape and shared-memory layout into a launch.
 void apply_kernel(const OffspringKernel &k, GenArgs &a);

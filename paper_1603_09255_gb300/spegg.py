@@ -143,6 +143,8 @@ _SIGNATURES = {
     "spg_set_ecology": ([ctypes.c_void_p, ctypes.POINTER(spg_ecology)], ctypes.c_int),
     "spg_step_generations": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
     "spg_read_stats": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
+    "spg_set_locus_counts": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "spg_read_locus_counts": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
     "spg_read_genotypes": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
     "spg_read_survivors": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint32)],
                            ctypes.c_int),
@@ -368,6 +370,19 @@ class Population:
     def genotypes(self) -> np.ndarray:
         out = np.zeros((self.n, 2 * self.words), np.uint32)
         check(lib().spg_read_genotypes(self._h, out.ctypes.data, out.size), "spg_read_genotypes")
+        return out
+
+    def set_locus_counts(self, enable: bool = True) -> None:
+        """Count the allele-1 copies of every locus in each generation formed
+        from now on (spg_set_locus_counts)."""
+        check(lib().spg_set_locus_counts(self._h, 1 if enable else 0), "spg_set_locus_counts")
+
+    def locus_counts(self, first_gen: int, count: int) -> np.ndarray:
+        """Per-locus allele counts [count, L] of generations first_gen ..
+        first_gen + count - 1 (spg_read_locus_counts)."""
+        out = np.zeros((max(int(count), 0), self.n_loci), np.uint32)
+        check(lib().spg_read_locus_counts(self._h, int(first_gen), int(count), out.ctypes.data if count else None),
+              "spg_read_locus_counts")
         return out
 
     def values(self) -> np.ndarray:
