@@ -843,13 +843,16 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, uint32_t lane) 
 
 // Allele-1 copies of every locus over both haplotypes of the generation just
 // formed (all N offspring; S2 "Genetics": count / 2N is the locus's allele
-// frequency).  A warp takes 32 records at a time, one per lane, transposes
-// each record word so that lane b holds bit b of the 32 records, and adds its
-// population count to locus 32w + b; the warps of a block add theirs in
-// shared memory and leave the block's row of partial counts; the block that
-// finishes last writes the rows' sum to the generation's ring slot and
-// re-arms the counter.  Counting a generation again writes the same values,
-// so a launch after the population has stopped changes nothing.
+// frequency).  A warp takes 32 records at a time, one per lane; each lane
+// adds its record's words into bit-sliced counters (plane k holds bit k of
+// every locus's count among the lane's records), and every kLocusPlanes
+// records' worth of room (and at the end) the warp transposes each plane
+// across its lanes, so that lane b holds bit b of the 32 lanes' planes, and
+// adds 2^k times its population count to locus 32w + b; the warps of a block add theirs in
+// shared memory, blocks add theirs into the accumulator row, and the block
+// that finishes last moves the row to the generation's ring slot, clears it
+// and re-arms the counter.  A generation already counted (a launch after the
+// population has stopped forms none) is left as it is.
 template <int W>
 __global__ void __launch_bounds__(kLocusBlock) k_locus_counts(const __grid_constant__ GenArgs a, const LocusArgs la) {
     constexpr uint32_t L = 32u * W, NW = kLocusBlock / 32u;
@@ -858,44 +861,82 @@ __global__ void __launch_bounds__(kLocusBlock) k_locus_counts(const __grid_const
     const Segment &sg = a.one;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t g = ld_relaxed_u32(&sg.state->gen);  // the generation the compaction just committed
-    if (g == 0u) return;                                 // the founders: no generation formed yet
+    if (g == 0u || ld_relaxed_u32(la.last) == g) return;  // the founders, or counted already
     for (uint32_t i = tid; i < L; i += kLocusBlock) s_cnt[i] = 0u;
     __syncthreads();
     const uint32_t *rec = sg.geno[g & 1u];
-    uint32_t acc[W];
+    constexpr int K = kLocusPlanes;
+    uint32_t acc[W], v[2 * W][K];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] = 0u;
-    const uint32_t groups = (sg.n + 31u) >> 5;
-    for (uint32_t q = blockIdx.x * NW + warp; q < groups; q += gridDim.x * NW) {
-        const uint32_t i = q * 32u + lane;
-        uint32_t r[2 * W];
-        if (i < sg.n) {
-            load_record<W>(rec + (size_t)i * (2 * W), r);
-        } else {
 #pragma unroll
-            for (int c = 0; c < 2 * W; ++c) r[c] = 0u;
+    for (int c = 0; c < 2 * W; ++c)
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[c][k] = 0u;
+    auto flush = [&]() {  // the whole warp: every lane's planes into the counts
+#pragma unroll
+        for (int c = 0; c < 2 * W; ++c)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                acc[c % W] += (uint32_t)__popc(warp_transpose32(v[c][k], lane)) << k;
+                v[c][k] = 0u;
+            }
+    };
+    const uint32_t groups = (sg.n + 31u) >> 5, stride = gridDim.x * NW;
+    constexpr uint32_t U = kLocusBatch;  // groups whose records are loaded before any is added
+    uint32_t held = 0;  // records each lane has added since the last flush (the same in the whole warp)
+    for (uint32_t q0 = blockIdx.x * NW + warp; q0 < groups; q0 += U * stride) {
+        uint32_t r[U][2 * W];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) {
+            const uint32_t q = q0 + u * stride, i = q * 32u + lane;
+            if (q < groups && i < sg.n) {
+                load_record<W>(rec + (size_t)i * (2 * W), r[u]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 2 * W; ++c) r[u][c] = 0u;
+            }
+        }
+        if (held + U > (1u << K) - 1u) {  // the counters hold up to 2^K - 1
+            flush();
+            held = 0;
         }
 #pragma unroll
-        for (int c = 0; c < 2 * W; ++c) acc[c % W] += __popc(warp_transpose32(r[c], lane));
+        for (uint32_t u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < 2 * W; ++c) {  // ripple-carry add of one bit per locus
+                uint32_t x = r[u][c];
+#pragma unroll
+                for (int k = 0; k < K - 1; ++k) {
+                    const uint32_t carry = v[c][k] & x;
+                    v[c][k] ^= x;
+                    x = carry;
+                }
+                v[c][K - 1] ^= x;
+            }
+        held += U;
     }
+    if (held) flush();
 #pragma unroll
     for (int w = 0; w < W; ++w) atomicAdd(&s_cnt[32u * w + lane], acc[w]);
     __syncthreads();
-    uint32_t *part = la.part + (size_t)blockIdx.x * L;
-    for (uint32_t i = tid; i < L; i += kLocusBlock) part[i] = s_cnt[i];
+    for (uint32_t i = tid; i < L; i += kLocusBlock)
+        if (s_cnt[i]) atomicAdd(la.acc + i, s_cnt[i]);
     __threadfence();
     __syncthreads();
     if (tid == 0) s_last = atomicAdd(la.done, 1u) == gridDim.x - 1u ? 1u : 0u;
     __syncthreads();
-    if (s_last) {
+    if (s_last) {  // every block has added its counts
         __threadfence();
         uint32_t *slot = la.ring + (size_t)((g - 1u) % la.cap) * L;
         for (uint32_t i = tid; i < L; i += kLocusBlock) {
-            uint32_t sum = 0u;
-            for (uint32_t b = 0; b < gridDim.x; ++b) sum += __ldcg(la.part + (size_t)b * L + i);
-            slot[i] = sum;
+            slot[i] = __ldcg(la.acc + i);
+            la.acc[i] = 0u;
         }
-        if (tid == 0) *la.done = 0u;
+        if (tid == 0) {
+            *la.done = 0u;
+            *la.last = g;
+        }
     }
 }
 

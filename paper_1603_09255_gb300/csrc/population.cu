@@ -230,17 +230,23 @@ int spg_set_locus_counts(spg_pop *p, int enable) {
     if (rc != SPG_OK) return rc;
     if (enable && !p->locus_mem) {
         const uint32_t L = p->n_loci, groups = (p->n + 31u) / 32u;
-        const uint32_t blocks = std::max(1u, std::min(kLocusMaxGrid, (groups + kLocusBlock / 32u - 1u) / (kLocusBlock / 32u)));
-        const size_t ring = align_up((size_t)p->cap * L * 4u, 256), part = align_up((size_t)blocks * L * 4u, 256);
-        p->locus_mem = static_cast<char *>(p->alloc.alloc(ring + part + 256u, p->stream));
-        if (!p->locus_mem) return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", ring + part + 256u);
+        const uint32_t per_block = kLocusGroupsPerWarp * (kLocusBlock / 32u);
+        const uint32_t blocks = std::max(1u, std::min(kLocusMaxGrid, (groups + per_block - 1u) / per_block));
+        const size_t ring = align_up((size_t)p->cap * L * 4u, 256), row = align_up((size_t)L * 4u, 256);
+        p->locus_mem = static_cast<char *>(p->alloc.alloc(ring + row + 256u, p->stream));
+        if (!p->locus_mem) return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", ring + row + 256u);
         p->locus.ring = reinterpret_cast<uint32_t *>(p->locus_mem);
-        p->locus.part = reinterpret_cast<uint32_t *>(p->locus_mem + ring);
-        p->locus.done = reinterpret_cast<uint32_t *>(p->locus_mem + ring + part);
+        p->locus.acc = reinterpret_cast<uint32_t *>(p->locus_mem + ring);
+        p->locus.done = reinterpret_cast<uint32_t *>(p->locus_mem + ring + row);
+        p->locus.last = p->locus.done + 1;
         p->locus.cap = p->cap;
         p->locus.blocks = blocks;
-        const cudaError_t e = cudaMemsetAsync(p->locus.done, 0, 4, p->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "clear per-locus counter");
+        const cudaError_t e = cudaMemsetAsync(p->locus.acc, 0, row + 8u, p->stream);  // row, counter, last
+        if (e != cudaSuccess) return cuda_fail(e, "clear per-locus counts");
+    }
+    if (enable && !p->locus_on && p->locus_mem) {  // the next generation is counted whatever was counted before
+        const cudaError_t e = cudaMemsetAsync(p->locus.last, 0, 4, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "clear per-locus counts");
     }
     if (enable) {
         if (!p->locus_on) p->locus_from = st.gen + 1u;  // the first generation formed from now on
@@ -383,6 +389,10 @@ int spg_restore(spg_pop *p, const void *host, size_t bytes) {
     if (rc != SPG_OK) return rc;
     p->locus_from = h.gen + 1u;  // counts of the restored run start with its next generation
     p->locus_until = h.gen;
+    if (p->locus_mem) {  // that generation is counted even if a generation of that number was before
+        const cudaError_t e = cudaMemsetAsync(p->locus.last, 0, 4, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "clear per-locus counts");
+    }
     return view_sync(p->view());
 }
 

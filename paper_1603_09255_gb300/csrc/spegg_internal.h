@@ -221,14 +221,18 @@ uint32_t compact_smem();                   // its dynamic shared memory (the rin
 
 // Per-locus allele counts of a population (optional, biallelic records):
 // the counts of the generations kept in a ring [cap][L] (generation g in slot
-// (g - 1) % cap), the count kernel's per-block partials [blocks][L] and the
-// counter of its blocks that are done.
+// (g - 1) % cap), the count kernel's accumulator row [L] (zero between
+// launches), the counter of its blocks that are done and the last generation
+// it counted (0: none).
 struct LocusArgs {
-    uint32_t *ring, *part, *done;
+    uint32_t *ring, *acc, *done, *last;
     uint32_t cap, blocks;
 };
 constexpr uint32_t kLocusBlock = 256;     // threads per block of the per-locus count kernel
 constexpr uint32_t kLocusMaxGrid = 608;   // its blocks, at most (four per SM)
+constexpr uint32_t kLocusGroupsPerWarp = 16;  // groups of 32 records a warp counts, at least (grid size)
+constexpr int kLocusPlanes = 5;           // bit-sliced counter planes per lane (31 records between flushes)
+constexpr uint32_t kLocusBatch = 4;       // groups a warp loads before adding them (loads in flight)
 using LocusKernel = void (*)(GenArgs, LocusArgs);
 LocusKernel locus_kernel(uint32_t words);  // the count kernel for records of 2W words
 uint32_t tile_size(const Shape &shape);  // offspring per tile: block * items / lanes
