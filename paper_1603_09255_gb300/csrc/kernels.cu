@@ -993,13 +993,18 @@ OffspringKernel offspring_kernel(uint32_t words, const Shape &shape, bool linked
     return k;
 }
 
+template <int G>
+GenKernel cont_instance(bool group) {
+    return group ? &k_offspring_cont<G, kContInFlight, true> : &k_offspring_cont<G, kContInFlight, false>;
+}
+
 OffspringKernel continuous_kernel(uint32_t n_loci, bool group) {
     OffspringKernel k;
     switch (n_loci) {
-        case 32: k.fn = group ? &k_offspring_cont<4, kContInFlight, true> : &k_offspring_cont<4, kContInFlight, false>; break;
-        case 64: k.fn = group ? &k_offspring_cont<8, kContInFlight, true> : &k_offspring_cont<8, kContInFlight, false>; break;
-        case 128: k.fn = group ? &k_offspring_cont<16, kContInFlight, true> : &k_offspring_cont<16, kContInFlight, false>; break;
-        case 256: k.fn = group ? &k_offspring_cont<32, kContInFlight, true> : &k_offspring_cont<32, kContInFlight, false>; break;
+        case 32: k.fn = cont_instance<4>(group); break;
+        case 64: k.fn = cont_instance<8>(group); break;
+        case 128: k.fn = cont_instance<16>(group); break;
+        case 256: k.fn = cont_instance<32>(group); break;
         default: return OffspringKernel{};
     }
     k.block = kBlock;

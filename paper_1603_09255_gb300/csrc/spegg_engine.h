@@ -14,7 +14,7 @@
 namespace spg {
 
 constexpr uint32_t kGraphChunk = 32;          // generations per cached graph
-constexpr uint32_t kPieceOffspring = 8192;     // least offspring of a piece of a launch group's work (one round excepted)
+constexpr uint32_t kPieceOffspring = 8192;     // least offspring of a launch group's piece of work (but one round)
 constexpr uint32_t kMaxGridBlocks = 8192;     // offspring blocks of a launch group, at most
 constexpr uint32_t kCheckpointMagic = 0x43475053u;  // "SPGC"
 
