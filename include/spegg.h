@@ -351,6 +351,15 @@ typedef struct {
 
 int spg_batch_autotune(spg_batch *batch, uint32_t gens_per_trial, spg_autotune_report *report);
 int spg_batch_read_stats(spg_batch *batch, uint32_t member, uint32_t first_gen, uint32_t count, spg_stats *out);
+/* Per-locus allele counts of every biallelic member (as
+ * spg_set_locus_counts / spg_read_locus_counts for each member; a group of
+ * several members counts them all in one more launch after its compaction;
+ * continuous-allele members are not counted and their reads are
+ * SPG_ERR_INVALID).  The first enabling call allocates every member's ring
+ * through the batch's allocator; both calls wait for the stream. */
+int spg_batch_set_locus_counts(spg_batch *batch, int enable);
+int spg_batch_read_locus_counts(spg_batch *batch, uint32_t member, uint32_t first_gen, uint32_t count,
+                                uint32_t *out);
 int spg_batch_read_genotypes(spg_batch *batch, uint32_t member, uint32_t *host, size_t n_words);
 int spg_batch_read_survivors(spg_batch *batch, uint32_t member, uint32_t *host, size_t capacity, uint32_t *S);
 int spg_batch_get_state(spg_batch *batch, uint32_t member, spg_state *out);

@@ -34,6 +34,8 @@ struct Member {
     std::unique_ptr<LinkParams> link;       // linkage-map tables (host copy, until uploaded)
     std::unique_ptr<WeightParams> weights;  // parent acceptance thresholds (host copy, until uploaded)
     uint32_t group = 0;
+    LocusArgs locus{};                      // per-locus counts (when the batch counts them)
+    uint32_t locus_from = 0, locus_until = 0;  // generations counted: from .. (on ? now : until)
 };
 
 struct Group {
@@ -43,6 +45,7 @@ struct Group {
     std::vector<uint32_t> members;
     size_t table_off = 0, table_bytes = 0;  // launch table in the batch arena (sized for every shape)
     GenLaunch gl;
+    LocusArgs locus{};  // the group's per-locus count launch (several members: member table and block map)
 };
 
 // A graph of `len` generations for every group: one dependent chain of
@@ -105,11 +108,26 @@ struct spg_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::map<uint32_t, std::unique_ptr<MultiChain>> chains;  // by length
+    char *locus_mem = nullptr;  // per-locus counts: every member's ring, row and counters, the groups' tables
+    bool locus_on = false;
 };
 
 namespace {
 
 // (Re)build a group's launch table for a launch shape (synchronous upload).
+// The per-locus count launch after each of the group's compactions, or none
+// (counts off, continuous values).  One member: its own arguments (the
+// launch's segment is the member); several: the group's member table.
+void attach_group_locus(spg_batch *b, Group &g) {
+    g.gl.locus = nullptr;
+    g.gl.la = LocusArgs{};
+    if (!b->locus_on || g.continuous || g.members.empty()) return;
+    const bool several = g.members.size() > 1;
+    g.gl.locus = locus_kernel(g.words, several);
+    g.gl.la = several ? g.locus : b->members[g.members[0]].locus;
+    if (!several) g.gl.la.first = 0u;
+}
+
 int configure_group(spg_batch *b, Group &g, const Shape &shape) {
     if (g.members.empty()) return SPG_OK;
     std::vector<const PopView *> views;
@@ -124,6 +142,7 @@ int configure_group(spg_batch *b, Group &g, const Shape &shape) {
                                       g.linked, g.weighted, g.continuous);
     if (rc != SPG_OK) return rc;
     g.shape = shape;
+    attach_group_locus(b, g);
     b->chains.clear();
     return SPG_OK;
 }
@@ -389,6 +408,109 @@ int spg_batch_read_stats(spg_batch *b, uint32_t member, uint32_t first_gen, uint
     return rc != SPG_OK ? rc : view_read_stats(v, first_gen, count, out);
 }
 
+int spg_batch_set_locus_counts(spg_batch *b, int enable) {
+    if (!b) return fail(SPG_ERR_INVALID, "batch is NULL");
+    cudaError_t e = cudaStreamSynchronize(b->stream);  // no generation in flight
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const uint32_t M = (uint32_t)b->members.size();
+    if (enable && !b->locus_mem) {
+        // layout: every biallelic member's ring and row, the members' counter
+        // pairs (blocks done, last generation counted), each group's tables
+        size_t off = 0;
+        std::vector<size_t> ring_off(M, 0), row_off(M, 0);
+        for (uint32_t m = 0; m < M; ++m) {
+            const Member &mb = b->members[m];
+            if (mb.prm->continuous) continue;
+            ring_off[m] = off;
+            off = align_up(off + (size_t)mb.v.cap * 32u * mb.v.words * 4u, 256);
+            row_off[m] = off;
+            off = align_up(off + (size_t)32u * mb.v.words * 4u, 256);
+        }
+        const size_t counters = off;
+        off = align_up(off + (size_t)M * 8u, 256);
+        std::vector<size_t> args_off(b->groups.size(), 0), map_off(b->groups.size(), 0);
+        std::vector<uint32_t> group_blocks(b->groups.size(), 0);
+        for (uint32_t gi = 0; gi < (uint32_t)b->groups.size(); ++gi) {
+            const Group &g = b->groups[gi];
+            if (g.continuous || g.members.size() < 2) continue;
+            for (uint32_t mi : g.members) group_blocks[gi] += locus_blocks(b->members[mi].v.n);
+            args_off[gi] = off;
+            off = align_up(off + g.members.size() * sizeof(LocusArgs), 256);
+            map_off[gi] = off;
+            off = align_up(off + (size_t)group_blocks[gi] * 4u, 256);
+        }
+        b->locus_mem = static_cast<char *>(b->alloc.alloc(off, b->stream));
+        if (!b->locus_mem) return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", off);
+        e = cudaMemsetAsync(b->locus_mem, 0, off, b->stream);  // rows and counters start at zero
+        for (uint32_t m = 0; m < M && e == cudaSuccess; ++m) {
+            Member &mb = b->members[m];
+            if (mb.prm->continuous) continue;
+            LocusArgs &la = mb.locus;
+            la.ring = reinterpret_cast<uint32_t *>(b->locus_mem + ring_off[m]);
+            la.acc = reinterpret_cast<uint32_t *>(b->locus_mem + row_off[m]);
+            la.done = reinterpret_cast<uint32_t *>(b->locus_mem + counters) + 2u * m;
+            la.last = la.done + 1;
+            la.cap = mb.v.cap;
+            la.blocks = locus_blocks(mb.v.n);
+        }
+        for (uint32_t gi = 0; gi < (uint32_t)b->groups.size() && e == cudaSuccess; ++gi) {
+            Group &g = b->groups[gi];
+            if (g.continuous || g.members.size() < 2) continue;
+            std::vector<LocusArgs> args;
+            std::vector<uint32_t> map;
+            for (uint32_t k = 0; k < (uint32_t)g.members.size(); ++k) {
+                LocusArgs la = b->members[g.members[k]].locus;
+                la.first = (uint32_t)map.size();
+                map.insert(map.end(), la.blocks, k);  // k: the member's segment in the group's launch
+                args.push_back(la);
+            }
+            e = cudaMemcpy(b->locus_mem + args_off[gi], args.data(), args.size() * sizeof(LocusArgs),
+                           cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(b->locus_mem + map_off[gi], map.data(), map.size() * 4u, cudaMemcpyHostToDevice);
+            g.locus = LocusArgs{};
+            g.locus.blocks = (uint32_t)map.size();
+            g.locus.member = reinterpret_cast<const LocusArgs *>(b->locus_mem + args_off[gi]);
+            g.locus.block_member = reinterpret_cast<const uint32_t *>(b->locus_mem + map_off[gi]);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "set up per-locus counts");
+    }
+    for (uint32_t m = 0; m < M; ++m) {
+        Member &mb = b->members[m];
+        if (mb.prm->continuous || !b->locus_mem) continue;
+        DevState st;
+        const int rc = view_state(mb.v, st);
+        if (rc != SPG_OK) return rc;
+        if (enable && !b->locus_on) {
+            mb.locus_from = st.gen + 1u;  // the first generation formed from now on
+            e = cudaMemsetAsync(mb.locus.last, 0, 4, b->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "clear per-locus counts");
+        } else if (!enable && b->locus_on) {
+            mb.locus_until = st.gen;  // the last generation counted
+        }
+    }
+    b->locus_on = enable != 0;
+    for (Group &g : b->groups) attach_group_locus(b, g);
+    b->chains.clear();
+    e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
+
+int spg_batch_read_locus_counts(spg_batch *b, uint32_t member, uint32_t first_gen, uint32_t count, uint32_t *out) {
+    PopView v;
+    int rc = member_view(b, member, v);
+    if (rc != SPG_OK) return rc;
+    if (!out && count) return fail(SPG_ERR_INVALID, "NULL argument");
+    const Member &mb = b->members[member];
+    if (mb.prm->continuous) return fail(SPG_ERR_INVALID, "per-locus allele counts are for biallelic members");
+    if (!b->locus_mem) return fail(SPG_ERR_INVALID, "per-locus allele counts are off");
+    DevState st;
+    rc = view_state(v, st);
+    if (rc != SPG_OK) return rc;
+    return read_locus_rows(mb.locus, 32u * v.words, mb.locus_from, b->locus_on ? st.gen : mb.locus_until, st,
+                           first_gen, count, out);
+}
+
 int spg_batch_read_genotypes(spg_batch *b, uint32_t member, uint32_t *host, size_t n_words) {
     PopView v;
     const int rc = member_view(b, member, v);
@@ -419,6 +541,7 @@ void spg_batch_destroy(spg_batch *b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     b->chains.clear();
+    if (b->locus_mem) b->alloc.release(b->locus_mem, b->stream);
     if (b->arena) b->alloc.release(b->arena, b->stream);
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);

@@ -764,6 +764,34 @@ int view_read_stats(const PopView &v, uint32_t first_gen, uint32_t count, spg_st
     return st.status < 0 ? fail(st.status, "device status %d", st.status) : SPG_OK;
 }
 
+uint32_t locus_blocks(uint32_t n) {
+    const uint32_t groups = (n + 31u) / 32u, per_block = kLocusGroupsPerWarp * (kLocusBlock / 32u);
+    return std::max(1u, std::min(kLocusMaxGrid, (groups + per_block - 1u) / per_block));
+}
+
+// Rows of per-locus counts of generations first_gen .. first_gen+count-1
+// from a population's ring: counted generations are from .. min(until, the
+// current one) and the ring keeps the last la.cap of them.
+int read_locus_rows(const LocusArgs &la, uint32_t n_loci, uint32_t from, uint32_t until, const DevState &st,
+                    uint32_t first_gen, uint32_t count, uint32_t *out) {
+    if (count == 0) return SPG_OK;
+    const uint64_t last = (uint64_t)first_gen + count - 1;
+    until = std::min(until, st.gen);
+    if (first_gen == 0 || first_gen < from || last > until || (uint64_t)st.gen - first_gen >= la.cap)
+        return fail(SPG_ERR_RANGE, "per-locus counts of generations %u..%llu not kept (counted %u..%u, capacity %u)",
+                    first_gen, (unsigned long long)last, from, until, la.cap);
+    const size_t row = n_loci;
+    for (uint32_t i = 0; i < count;) {
+        const uint32_t slot = (first_gen - 1 + i) % la.cap;
+        const uint32_t run = std::min(count - i, la.cap - slot);
+        const cudaError_t e = cudaMemcpy(out + (size_t)i * row, la.ring + (size_t)slot * row, run * row * 4u,
+                                         cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read per-locus counts");
+        i += run;
+    }
+    return st.status < 0 ? fail(st.status, "device status %d", st.status) : SPG_OK;
+}
+
 int view_read_genotypes(const PopView &v, uint32_t *host, size_t n_words) {
     if (!host) return fail(SPG_ERR_INVALID, "NULL argument");
     const size_t need = (size_t)v.n * 2 * v.words;

@@ -853,12 +853,25 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, uint32_t lane) 
 // that finishes last moves the row to the generation's ring slot, clears it
 // and re-arms the counter.  A generation already counted (a launch after the
 // population has stopped forms none) is left as it is.
-template <int W>
-__global__ void __launch_bounds__(kLocusBlock) k_locus_counts(const __grid_constant__ GenArgs a, const LocusArgs la) {
+template <int W, bool GROUP>
+__global__ void __launch_bounds__(kLocusBlock) k_locus_counts(const __grid_constant__ GenArgs a, const LocusArgs la_) {
     constexpr uint32_t L = 32u * W, NW = kLocusBlock / 32u;
     __shared__ uint32_t s_cnt[L];
     __shared__ uint32_t s_last;
-    const Segment &sg = a.one;
+    // the block's population, its arguments and the block's place among its
+    // blocks (GROUP: a launch group, from the block map)
+    const Segment *sgp = &a.one;
+    const LocusArgs *lap = &la_;
+    uint32_t blk = blockIdx.x, nblk = gridDim.x;
+    if constexpr (GROUP) {
+        const uint32_t m = __ldg(la_.block_member + blockIdx.x);
+        sgp = a.segs + m;
+        lap = la_.member + m;
+        blk = blockIdx.x - lap->first;
+        nblk = lap->blocks;
+    }
+    const Segment &sg = *sgp;
+    const LocusArgs &la = *lap;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t g = ld_relaxed_u32(&sg.state->gen);  // the generation the compaction just committed
     if (g == 0u || ld_relaxed_u32(la.last) == g) return;  // the founders, or counted already
@@ -882,10 +895,10 @@ __global__ void __launch_bounds__(kLocusBlock) k_locus_counts(const __grid_const
                 v[c][k] = 0u;
             }
     };
-    const uint32_t groups = (sg.n + 31u) >> 5, stride = gridDim.x * NW;
+    const uint32_t groups = (sg.n + 31u) >> 5, stride = nblk * NW;
     constexpr uint32_t U = kLocusBatch;  // groups whose records are loaded before any is added
     uint32_t held = 0;  // records each lane has added since the last flush (the same in the whole warp)
-    for (uint32_t q0 = blockIdx.x * NW + warp; q0 < groups; q0 += U * stride) {
+    for (uint32_t q0 = blk * NW + warp; q0 < groups; q0 += U * stride) {
         uint32_t r[U][2 * W];
 #pragma unroll
         for (uint32_t u = 0; u < U; ++u) {
@@ -924,7 +937,7 @@ __global__ void __launch_bounds__(kLocusBlock) k_locus_counts(const __grid_const
         if (s_cnt[i]) atomicAdd(la.acc + i, s_cnt[i]);
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(la.done, 1u) == gridDim.x - 1u ? 1u : 0u;
+    if (tid == 0) s_last = atomicAdd(la.done, 1u) == nblk - 1u ? 1u : 0u;
     __syncthreads();
     if (s_last) {  // every block has added its counts
         __threadfence();
@@ -940,12 +953,17 @@ __global__ void __launch_bounds__(kLocusBlock) k_locus_counts(const __grid_const
     }
 }
 
-LocusKernel locus_kernel(uint32_t words) {
+template <int W>
+LocusKernel locus_instance(bool group) {
+    return group ? &k_locus_counts<W, true> : &k_locus_counts<W, false>;
+}
+
+LocusKernel locus_kernel(uint32_t words, bool group) {
     switch (words) {
-        case 1: return &k_locus_counts<1>;
-        case 2: return &k_locus_counts<2>;
-        case 4: return &k_locus_counts<4>;
-        case 8: return &k_locus_counts<8>;
+        case 1: return locus_instance<1>(group);
+        case 2: return locus_instance<2>(group);
+        case 4: return locus_instance<4>(group);
+        case 8: return locus_instance<8>(group);
         default: return nullptr;
     }
 }

@@ -229,9 +229,7 @@ int spg_set_locus_counts(spg_pop *p, int enable) {
     int rc = view_state(p->view(), st);  // synchronises: no generation in flight
     if (rc != SPG_OK) return rc;
     if (enable && !p->locus_mem) {
-        const uint32_t L = p->n_loci, groups = (p->n + 31u) / 32u;
-        const uint32_t per_block = kLocusGroupsPerWarp * (kLocusBlock / 32u);
-        const uint32_t blocks = std::max(1u, std::min(kLocusMaxGrid, (groups + per_block - 1u) / per_block));
+        const uint32_t L = p->n_loci, blocks = locus_blocks(p->n);
         const size_t ring = align_up((size_t)p->cap * L * 4u, 256), row = align_up((size_t)L * 4u, 256);
         p->locus_mem = static_cast<char *>(p->alloc.alloc(ring + row + 256u, p->stream));
         if (!p->locus_mem) return fail(SPG_ERR_OOM, "device allocation of %zu bytes failed", ring + row + 256u);
@@ -266,21 +264,8 @@ int spg_read_locus_counts(spg_pop *p, uint32_t first_gen, uint32_t count, uint32
     const int rc = view_state(p->view(), st);
     if (rc != SPG_OK) return rc;
     if (count == 0) return SPG_OK;
-    const uint64_t last = (uint64_t)first_gen + count - 1;
-    const uint32_t until = p->locus_on ? st.gen : std::min(p->locus_until, st.gen);
-    if (first_gen == 0 || first_gen < p->locus_from || last > until || (uint64_t)st.gen - first_gen >= p->cap)
-        return fail(SPG_ERR_RANGE, "per-locus counts of generations %u..%llu not kept (counted %u..%u, capacity %u)",
-                    first_gen, (unsigned long long)last, p->locus_from, until, p->cap);
-    const size_t row = p->n_loci;
-    for (uint32_t i = 0; i < count;) {
-        const uint32_t slot = (first_gen - 1 + i) % p->cap;
-        const uint32_t run = std::min(count - i, p->cap - slot);
-        const cudaError_t e = cudaMemcpy(out + (size_t)i * row, p->locus.ring + (size_t)slot * row, run * row * 4u,
-                                         cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(e, "read per-locus counts");
-        i += run;
-    }
-    return st.status < 0 ? fail(st.status, "device status %d", st.status) : SPG_OK;
+    return read_locus_rows(p->locus, p->n_loci, p->locus_from, p->locus_on ? st.gen : p->locus_until, st, first_gen,
+                           count, out);
 }
 
 int spg_read_genotypes(spg_pop *p, uint32_t *host, size_t n_words) {

@@ -101,6 +101,11 @@ int launch_generation(const GenLaunch &gl, cudaStream_t stream);
 // (kernel nodes joined by programmatic edges); params: the GenArgs pointer.
 int add_generation_nodes(cudaGraph_t graph, const GenLaunch &gl, void **params, uint32_t len);
 size_t group_table_bytes(uint32_t members, uint64_t offspring, uint32_t buckets);
+int read_locus_rows(const LocusArgs &la, uint32_t n_loci, uint32_t from, uint32_t until, const DevState &st,
+                    uint32_t first_gen, uint32_t count, uint32_t *out);
+// Blocks of the per-locus count kernel for a population of n (16 groups of
+// 32 records per warp at least, at most kLocusMaxGrid).
+uint32_t locus_blocks(uint32_t n);
 uint32_t tiles_for(uint32_t n, const Shape &shape);
 void schedule_runs(const std::vector<uint32_t> &tiles, uint32_t G, uint32_t min_piece, std::vector<Run> &runs,
                    std::vector<uint32_t> &block_runs);

@@ -224,9 +224,14 @@ uint32_t compact_smem();                   // its dynamic shared memory (the rin
 // (g - 1) % cap), the count kernel's accumulator row [L] (zero between
 // launches), the counter of its blocks that are done and the last generation
 // it counted (0: none).
+// A launch group counts every member at once: `member` holds each member's
+// own arguments (its blocks are first .. first + blocks - 1 of the launch)
+// and `block_member` the member of each block of the launch.
 struct LocusArgs {
     uint32_t *ring, *acc, *done, *last;
-    uint32_t cap, blocks;
+    uint32_t cap, blocks, first;
+    const LocusArgs *member;        // launch groups: [members] (null: one population, the fields above)
+    const uint32_t *block_member;   // launch groups: [blocks]
 };
 constexpr uint32_t kLocusBlock = 256;     // threads per block of the per-locus count kernel
 constexpr uint32_t kLocusMaxGrid = 608;   // its blocks, at most (four per SM)
@@ -234,7 +239,7 @@ constexpr uint32_t kLocusGroupsPerWarp = 16;  // groups of 32 records a warp cou
 constexpr int kLocusPlanes = 5;           // bit-sliced counter planes per lane (31 records between flushes)
 constexpr uint32_t kLocusBatch = 4;       // groups a warp loads before adding them (loads in flight)
 using LocusKernel = void (*)(GenArgs, LocusArgs);
-LocusKernel locus_kernel(uint32_t words);  // the count kernel for records of 2W words
+LocusKernel locus_kernel(uint32_t words, bool group = false);  // the count kernel for records of 2W words
 uint32_t tile_size(const Shape &shape);  // offspring per tile: block * items / lanes
 // Copy the offspring kernel's shape and shared-memory layout into a launch.
 void apply_kernel(const OffspringKernel &k, GenArgs &a);

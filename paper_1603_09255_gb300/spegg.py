@@ -171,6 +171,9 @@ _SIGNATURES = {
                                    ctypes.c_int),
     "spg_set_launch_shape": ([ctypes.c_void_p, ctypes.POINTER(spg_launch_shape)], ctypes.c_int),
     "spg_get_launch_shape": ([ctypes.c_void_p, ctypes.POINTER(spg_launch_shape)], ctypes.c_int),
+    "spg_batch_set_locus_counts": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "spg_batch_read_locus_counts": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                     ctypes.c_void_p], ctypes.c_int),
     "spg_batch_read_stats": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p],
                              ctypes.c_int),
     "spg_batch_read_genotypes": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
@@ -536,6 +539,20 @@ class Batch:
         check(lib().spg_batch_read_stats(self._h, int(member), int(first_gen), int(count), out.ctypes.data),
               "spg_batch_read_stats")
         return out[:count]
+
+    def set_locus_counts(self, enable: bool = True) -> None:
+        """Per-locus allele counts of every biallelic member from now on
+        (spg_batch_set_locus_counts)."""
+        check(lib().spg_batch_set_locus_counts(self._h, 1 if enable else 0), "spg_batch_set_locus_counts")
+
+    def locus_counts(self, member: int, first_gen: int, count: int) -> np.ndarray:
+        """Per-locus allele counts [count, L] of one member's generations
+        first_gen .. first_gen + count - 1 (spg_batch_read_locus_counts)."""
+        n_loci = self.workloads[member].n_loci
+        out = np.zeros((max(int(count), 0), n_loci), np.uint32)
+        check(lib().spg_batch_read_locus_counts(self._h, int(member), int(first_gen), int(count),
+                                                out.ctypes.data if count else None), "spg_batch_read_locus_counts")
+        return out
 
     def genotypes(self, member: int) -> np.ndarray:
         w = self.workloads[member]

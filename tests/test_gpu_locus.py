@@ -132,3 +132,39 @@ def test_locus_counts_restore_and_continuous():
         c.set_locus_counts(True)
     assert e.value.code == sp().ERR_INVALID
     c.close()
+
+
+def test_batch_locus_counts_match_oracle():
+    """Batch members in groups of one and of two (plain, linkage map, parent
+    weights, an extinct one): counts from the enabling call on, through the
+    autotuner's reshaped launches and a cached graph, equal the oracle's; a
+    continuous-allele member is not counted."""
+    ws = [
+        S.single_species(n=1000, n_loci=32, mu=2e-3, s=1.0, seed=41, replicate=0),
+        S.consumer_resource(n=4097, n_loci=32, mu=2e-3, s=1.0, K=2e4, seed=41, replicate=1),
+        S.single_species(n=20011, n_loci=64, mu=1e-3, s=1.0, seed=41, replicate=2),
+        S.with_linkage(S.single_species(n=3000, n_loci=128, mu=1e-3, s=1.0, seed=41, replicate=3), 4, 1.0),
+        S.with_linkage(S.single_species(n=33, n_loci=128, mu=1e-2, s=1.0, seed=41, replicate=4), 2, 0.5),
+        S.with_weights(S.single_species(n=5000, n_loci=256, mu=1e-3, s=1.0, seed=41, replicate=5)),
+        S.single_species(n=700, n_loci=64, seed=41, replicate=6),
+        S.continuous_trait(n=500, n_loci=64, seed=41, replicate=7),
+    ]
+    ws[6].surv_table = S.constant_table(0)  # extinct in its first generation
+    b = sp().Batch(ws, stats_capacity=64)
+    b.set_locus_counts(True)
+    ran = b.autotune(1)
+    b.step(40)
+    for i, w in enumerate(ws[:7]):
+        gen = b.state(i)["gen"]
+        want, orc = oracle_rows(w, ran + 40)
+        assert gen == orc.state()["gen"], i
+        assert np.array_equal(b.locus_counts(i, 1, gen), want[:gen]), i
+    with pytest.raises(sp().SpeggError) as e:
+        b.locus_counts(7, 1, 1)
+    assert e.value.code == sp().ERR_INVALID
+    b.set_locus_counts(False)
+    b.step(2)
+    with pytest.raises(sp().SpeggError) as e:
+        b.locus_counts(0, ran + 41, 1)
+    assert e.value.code == sp().ERR_RANGE
+    b.close()
