@@ -59,3 +59,28 @@ def test_locus_counts_refuse_continuous_populations():
     orc = oracle.OraclePopulation.from_workload(S.continuous_trait(n=50, n_loci=32))
     with pytest.raises(ValueError):
         orc.locus_counts()
+
+
+def test_locus_counts_follow_binomial_sampling_under_neutrality():
+    """Wright-Fisher with certain survival and no mutation: each of the next
+    generation's 2N copies of a locus is a copy of a uniformly drawn parental
+    copy, so given c the next count is Binomial(2N, c / 2N).  Pooled over 256
+    loci and 30 generations, the changes have mean 0 (z within 5) and their
+    squares average 2N p(1 - p) (ratio within 10 %)."""
+    n, n_loci = 500, 256
+    w = S.single_species(n=n, n_loci=n_loci, mu=0.0, seed=17)
+    w.surv_table = S.constant_table(S.CERTAIN)
+    orc = oracle.OraclePopulation.from_workload(w)
+    prev = orc.locus_counts().astype(np.float64)
+    dsum = var = sq = 0.0
+    for _ in range(30):
+        orc.step(1)
+        cur = orc.locus_counts().astype(np.float64)
+        p = prev / (2 * n)
+        v = 2 * n * p * (1 - p)
+        dsum += (cur - prev).sum()
+        var += v.sum()
+        sq += ((cur - prev) ** 2).sum()
+        prev = cur
+    assert abs(dsum) / np.sqrt(var) < 5.0
+    assert abs(sq / var - 1.0) < 0.10
