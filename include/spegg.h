@@ -305,14 +305,13 @@ int spg_get_tiling(spg_pop *pop, uint32_t *items_per_thread);
  * Many independent populations advanced by shared launches: the flattened
  * loop over replicates of the paper's Fig. S5 B.  Members are grouped by
  * locus count and variant (plain; linkage map; parent weights; both;
- * continuous values); each
- * generation is one offspring launch and one compaction launch per group,
- * groups run as independent branches of one cached CUDA graph.  Members with
- * a linkage map, parent weights or continuous values run the variant shape
- * (256 threads, one
- * offspring per thread, one lane); launch shapes and the autotuner apply to
- * the plain members of each locus count.  Every member keeps its own parameters, state, buffers and
- * statistics ring, and its results are identical to the same population
+ * continuous values); each generation is one offspring launch and one
+ * compaction launch per group, groups run as independent branches of one
+ * cached CUDA graph.  Members with a linkage map, parent weights or
+ * continuous values run the variant shape (256 threads, one offspring per
+ * thread, one lane); launch shapes and the autotuner apply to the plain
+ * members of each locus count.  Every member keeps its own parameters,
+ * state, buffers and statistics ring, and its results are identical to the same population
  * created with spg_create_population and stepped alone.  Member i is
  * descs[i]; the descriptions are copied.  Errors as for a population;
  * SPG_ERR_INVALID names the first invalid member. */
@@ -330,9 +329,9 @@ int spg_batch_get_launch_shape(spg_batch *batch, uint32_t n_loci, spg_launch_sha
 int spg_batch_set_tiling(spg_batch *batch, uint32_t n_loci, uint32_t items_per_thread);
 int spg_batch_get_tiling(spg_batch *batch, uint32_t n_loci, uint32_t *items_per_thread);
 /* Launch-shape autotuner: for each locus-count group of plain members (no
- * linkage map or parent weights: those run their one shape for as many
- * generations), runs one untimed
- * generation and then times gens_per_trial real generations with each of
+ * linkage map, parent weights or continuous values: those run their one
+ * shape for as many generations), runs one untimed generation and then
+ * times gens_per_trial real generations with each of
  * SPG_AUTOTUNE_CANDIDATES launch shapes -- threads per block (128, 256, 512)
  * x offspring per thread (1, 2) for L <= 64, x lanes per offspring (1, 2) for
  * L >= 128 -- and keeps the fastest.  Every
